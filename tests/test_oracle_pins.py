@@ -1,0 +1,409 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test ties one part of the oracle to a value worked by hand from the paper,
+a closed form, a library routine, a brute-force recount or an invariant the paper
+states, so that a dropped term, a wrong sign/index or a transposed operand in the
+oracle fails at least one of them.
+"""
+import json
+import math
+import os
+import subprocess
+import sys
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from conftest import golden, ROOT
+
+MASK32 = 0xFFFFFFFF
+
+
+# ------------------------------------------------------------------ Philox ----
+_TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+cases = json.loads(sys.stdin.read())
+@triton.jit
+def k(out_ptr, c_ptr, seed, N: tl.constexpr):
+    o = tl.arange(0, N)
+    a, b, c, d = tl.philox(seed, tl.load(c_ptr + o * 4 + 0), tl.load(c_ptr + o * 4 + 1),
+                           tl.load(c_ptr + o * 4 + 2), tl.load(c_ptr + o * 4 + 3), 10)
+    tl.store(out_ptr + o * 4 + 0, a); tl.store(out_ptr + o * 4 + 1, b)
+    tl.store(out_ptr + o * 4 + 2, c); tl.store(out_ptr + o * 4 + 3, d)
+res = []
+for seed, ctr in cases:
+    c = torch.tensor(np.array(ctr, dtype=np.uint32).view(np.int32).reshape(1, 4).repeat(2, 0).reshape(-1))
+    out = torch.zeros(8, dtype=torch.int32)
+    k[(1,)](out, c, seed, N=2)
+    res.append([int(v) & 0xFFFFFFFF for v in out.tolist()[:4]])
+print(json.dumps(res))
+"""
+
+
+def test_philox_matches_library_philox(oracle_mod):
+    """The oracle's Philox4x32-10 equals Triton's library Philox (run by its CPU
+    interpreter) on edge and random counters/keys."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(123)
+    cases = [(0, [0, 0, 0, 0]), ((1 << 64) - 1, [MASK32] * 4),
+             (0x0123456789ABCDEF, [1, 2, 3, 4])]
+    for _ in range(12):
+        seed = int(rng.integers(0, 1 << 63)) * 2 + int(rng.integers(0, 2))
+        cases.append((seed, [int(x) for x in rng.integers(0, 1 << 32, size=4)]))
+    proc = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT], input=json.dumps(cases),
+                          capture_output=True, text=True, timeout=600)
+    assert proc.returncode == 0, proc.stderr[-2000:]
+    ref = json.loads(proc.stdout.strip().splitlines()[-1])
+    for (seed, ctr), want in zip(cases, ref):
+        got = oracle_mod.philox(ctr, [seed & MASK32, seed >> 32])
+        assert [int(v) for v in got] == want, (seed, ctr)
+
+
+def _level(oracle_mod, seed, traj, step, word, level):
+    """Level `level` (64 lanes) of the PERT stream, from the Philox block alone."""
+    c2 = ((step >> 32) & 0xFFFF) | (((traj >> 32) & 0xFFFF) << 16)
+    x = oracle_mod.philox([traj & MASK32, step & MASK32, c2, (1 << 28) | (word << 4) | (level // 2)],
+                          [seed & MASK32, seed >> 32])
+    x = [int(v) for v in x]
+    return (x[1] << 32 | x[0]) if level % 2 == 0 else (x[3] << 32 | x[2])
+
+
+def _net_const(n, p):
+    """n nodes, each with the single function 'copy myself'."""
+    lines = [f"pbn {n} {float(p).hex()}"] + [f"f {i} 0x1p+0 1 {i} 2" for i in range(n)]
+    return "\n".join(lines) + "\n"
+
+
+# ------------------------------------------------------------ perturbation ----
+@pytest.mark.parametrize("p,fn", [
+    (0.5, lambda L0, L1: ~L0),           # u < 2^31      <=> bit 31 of u is 0
+    (0.25, lambda L0, L1: ~L0 & ~L1),    # u < 2^30      <=> bits 31, 30 are 0
+    (0.75, lambda L0, L1: ~(L0 & L1)),   # u < 3 * 2^30  <=> not both set
+])
+def test_perturbation_closed_forms(oracle_mod, p, fn):
+    """For dyadic p the Bernoulli comparison u < P reduces to Boolean functions of
+    the top levels; the last word's lanes beyond n are absent (Theorem 1's masking)."""
+    n = 70
+    text = _net_const(n, p)
+    for seed, traj, step in [(7, 0, 0), (2**40 + 5, 2**33 + 9, 2**35 + 11), (99, 12345, 678)]:
+        g, _, _, _ = oracle_mod.draws(text, seed, traj, step)
+        for w in range(2):
+            L0 = _level(oracle_mod, seed, traj, step, w, 0)
+            L1 = _level(oracle_mod, seed, traj, step, w, 1)
+            want = fn(L0, L1) & ((1 << 64) - 1)
+            for b in range(64):
+                i = 64 * w + b
+                if i < n:
+                    assert g[i] == (want >> b) & 1, (seed, traj, step, i)
+
+
+def test_perturbation_p_zero_never(oracle_mod):
+    text = _net_const(10, 0.0)
+    for t in range(50):
+        g, _, _, any_ = oracle_mod.draws(text, 1, t, t)
+        assert not any_ and g.sum() == 0
+
+
+def test_perturbation_rate_binomial(oracle_mod):
+    """Per-lane rate P / 2^32 on full and partial words (Theorem 1 analogue),
+    and pairwise independence of two lanes, within 5 sigma."""
+    n, p = 70, 0.05
+    text = _net_const(n, p)
+    P = math.floor(p * 2**32)
+    pe = P / 2**32
+    hits = np.zeros(n)
+    pair = 0
+    T = 3000
+    for t in range(T):
+        g, _, _, _ = oracle_mod.draws(text, 5, t, 3 * t + 1)
+        hits += g
+        pair += int(g[3]) * int(g[66])
+    sd = math.sqrt(pe * (1 - pe) / T)
+    for i in range(n):
+        assert abs(hits[i] / T - pe) < 5 * sd + 1e-12, i
+    sd2 = math.sqrt(pe * pe * (1 - pe * pe) / T)
+    assert abs(pair / T - pe * pe) < 5 * sd2 + 1e-12
+
+
+# ---------------------------------------------------------------- selection ----
+def test_selection_thresholds_dyadic(oracle_mod):
+    text = golden("tiny2.pbn")
+    P, T = oracle_mod.thresholds(text, 0)
+    assert P == 2**28 and T == [2**30]
+    P, T = oracle_mod.thresholds(text, 1)
+    assert T == []
+
+
+def test_selection_rank_and_lane(oracle_mod):
+    """Only nodes 1 and 3 have >= 2 functions, so they take ranks 0 and 1 and read
+    words x0 and x1 of the first SEL block.  Node 3 has three functions with
+    c = (1/2, 1/4, 1/4): T_1 = 2^31, T_2 = 3 * 2^30."""
+    text = ("pbn 4 0x1p-5\n"
+            "f 0 0x1p+0 1 0 2\n"
+            "f 1 0x1p-1 1 0 2\nf 1 0x1p-1 1 0 1\n"
+            "f 2 0x1p+0 1 1 2\n"
+            "f 3 0x1p-1 1 2 2\nf 3 0x1p-2 1 2 1\nf 3 0x1p-2 0 1\n")
+    for seed, traj, step in [(3, 0, 0), (11, 77, 5), (2**50, 2**34, 2**33 + 1)]:
+        _, ch, _, _ = oracle_mod.draws(text, seed, traj, step)
+        c2 = ((step >> 32) & 0xFFFF) | (((traj >> 32) & 0xFFFF) << 16)
+        x = [int(v) for v in oracle_mod.philox([traj & MASK32, step & MASK32, c2, 2 << 28],
+                                               [seed & MASK32, seed >> 32])]
+        assert ch[0] == 0 and ch[2] == 0
+        assert ch[1] == (1 if x[0] >= 2**31 else 0)
+        assert ch[3] == (x[1] >= 2**31) + (x[1] >= 3 * 2**30)
+
+
+def test_selection_frequencies(oracle_mod):
+    text = ("pbn 2 0x1p-5\n"
+            "f 0 0x1.3333333333333p-2 1 0 2\nf 0 0x1p-1 1 0 1\n"
+            "f 0 0x1.999999999999ap-3 0 1\n"
+            "f 1 0x1p+0 1 0 2\n")
+    c = [float.fromhex("0x1.3333333333333p-2"), float.fromhex("0x1p-1"),
+         float.fromhex("0x1.999999999999ap-3")]
+    T = 4000
+    cnt = np.zeros(3)
+    for t in range(T):
+        _, ch, _, _ = oracle_mod.draws(text, 17, t, 2 * t)
+        cnt[ch[0]] += 1
+    for j in range(3):
+        sd = math.sqrt(c[j] * (1 - c[j]) / T)
+        assert abs(cnt[j] / T - c[j]) < 5 * sd
+
+
+def test_initial_state_words(oracle_mod):
+    """s(0): word w is x1:x0 (even w) or x3:x2 (odd w) of INIT block w / 2."""
+    n = 130
+    text = _net_const(n, 0.01)
+    seed, traj = 42, 2**33 + 3
+    _, _, s0, _ = oracle_mod.draws(text, seed, traj, 999)
+    for w in range(3):
+        x = [int(v) for v in oracle_mod.philox([traj & MASK32, 0, ((traj >> 32) & 0xFFFF) << 16,
+                                                (3 << 28) | (w >> 1)], [seed & MASK32, seed >> 32])]
+        word = (x[1] << 32 | x[0]) if w % 2 == 0 else (x[3] << 32 | x[2])
+        for b in range(64):
+            if 64 * w + b < n:
+                assert s0[64 * w + b] == (word >> b) & 1
+
+
+# ------------------------------------------------------ Eq. 1 transition law ----
+def _golden_matrix():
+    rows = [l.split() for l in golden("tiny2_matrix.txt").splitlines()
+            if l.strip() and not l.startswith("#")]
+    return [[Fraction(int(v), 1024) for v in r] for r in rows]
+
+
+def test_transition_matrix_hand_worked(oracle_mod):
+    M = oracle_mod.transition_matrix(golden("tiny2.pbn"))
+    want = _golden_matrix()
+    for s in range(4):
+        for t in range(4):
+            assert M[s, t] == float(want[s][t]), (s, t)
+
+
+def _exact_stationary(Q):
+    """Solve pi Q = pi, sum pi = 1 with exact rationals (Gauss-Jordan)."""
+    S = len(Q)
+    A = [[Q[j][i] - (1 if i == j else 0) for j in range(S)] for i in range(S)]
+    A[-1] = [Fraction(1)] * S
+    b = [Fraction(0)] * (S - 1) + [Fraction(1)]
+    for c in range(S):
+        piv = next(r for r in range(c, S) if A[r][c] != 0)
+        A[c], A[piv] = A[piv], A[c]
+        b[c], b[piv] = b[piv], b[c]
+        for r in range(S):
+            if r != c and A[r][c] != 0:
+                f = A[r][c] / A[c][c]
+                A[r] = [x - f * y for x, y in zip(A[r], A[c])]
+                b[r] -= f * b[c]
+    return [b[i] / A[i][i] for i in range(S)]
+
+
+def test_stationary_matches_exact_solution(oracle_mod):
+    """Power iteration on the oracle's matrix equals the exact rational solution of
+    pi Q = pi built from the hand-worked matrix (the limiting distribution that
+    ergodicity guarantees, Sec. 2.1)."""
+    pi_exact = _exact_stationary(_golden_matrix())
+    pi, it = oracle_mod.stationary(oracle_mod.transition_matrix(golden("tiny2.pbn")))
+    for s in range(4):
+        assert abs(pi[s] - float(pi_exact[s])) < 1e-14
+
+
+@pytest.mark.parametrize("p", [0.01, 0.3])
+def test_stationary_single_node_closed_forms(oracle_mod, p):
+    """One node with f = constant 1: pi(1) = 1 / (1 + p').  One node with f = x:
+    pi = (1/2, 1/2)."""
+    pe = math.floor(p * 2**32) / 2**32
+    M = oracle_mod.transition_matrix(f"pbn 1 {p.hex()}\nf 0 0x1p+0 0 1\n")
+    pi, _ = oracle_mod.stationary(M)
+    assert abs(pi[1] - 1 / (1 + pe)) < 1e-13
+    M = oracle_mod.transition_matrix(f"pbn 1 {p.hex()}\nf 0 0x1p+0 1 0 2\n")
+    pi, _ = oracle_mod.stationary(M)
+    assert abs(pi[0] - 0.5) < 1e-13
+
+
+def test_one_step_empirical_law(oracle_mod):
+    """Many independent keyed trajectories, one step from each fixed state: the
+    next-state frequencies follow the hand-worked row within 5 sigma."""
+    text = golden("tiny2.pbn")
+    Q = _golden_matrix()
+    T = 20000
+    for s in range(4):
+        init = np.array([[s & 1, (s >> 1) & 1]] * T, dtype=np.uint8)
+        out = oracle_mod.simulate(text, 1234 + s, 0, T, 1, init_states=init)["final"]
+        idx = out[:, 0].astype(int) + 2 * out[:, 1].astype(int)
+        for t in range(4):
+            q = float(Q[s][t])
+            sd = math.sqrt(q * (1 - q) / T)
+            assert abs((idx == t).mean() - q) <= 5 * sd + 1e-12, (s, t)
+
+
+# ---------------------------------------------------------------- counting ----
+def _recount(trace_states, s_start, meta, start_index, count_from):
+    """Brute-force counts from a list of states s(start_index), s(start_index+1)..."""
+    z = [int(all(st[m] for m in meta)) for st in [s_start] + list(trace_states)]
+    V = sum(zi for k, zi in enumerate(z) if start_index + k >= count_from)
+    n = [0, 0, 0, 0]
+    for k in range(1, len(z)):
+        if start_index + k - 1 >= count_from:
+            n[2 * z[k - 1] + z[k]] += 1
+    return [V] + n
+
+
+@pytest.mark.parametrize("count_from", [0, 1, 37])
+def test_counts_match_bruteforce_recount(oracle_mod, count_from):
+    from paper_1605_00854_gb300 import synth
+    text = synth.tiny12(1).to_text()
+    meta = [0, 1, 2]
+    r = oracle_mod.simulate(text, 9, 0, 6, 300, meta_ids=meta, count_from=count_from, trace=True)
+    init = np.zeros((6, 12), dtype=np.uint8)
+    for t in range(6):
+        init[t] = oracle_mod.draws(text, 9, t, 0)[2]
+    for t in range(6):
+        want = _recount(r["trace"][t], init[t], meta, 0, count_from)
+        assert list(map(int, r["counts"][t])) == want
+        c = r["counts"][t]
+        L = 300 + 1 - count_from
+        assert int(c[1] + c[2] + c[3] + c[4]) == L - 1
+
+
+def test_resume_equals_one_run(oracle_mod):
+    """S steps, then S more from the saved state, equals 2S steps in one run
+    (states at every step and the summed counts)."""
+    from paper_1605_00854_gb300 import synth
+    text = synth.tiny12(1).to_text()
+    meta = [0, 1, 2]
+    full = oracle_mod.simulate(text, 4, 100, 5, 400, meta_ids=meta, trace=True, count_from=50)
+    a = oracle_mod.simulate(text, 4, 100, 5, 200, meta_ids=meta, trace=True, count_from=50)
+    b = oracle_mod.simulate(text, 4, 100, 5, 200, meta_ids=meta, trace=True, count_from=50,
+                            step_begin=200, init_states=a["final"])
+    assert np.array_equal(full["trace"], np.concatenate([a["trace"], b["trace"]], axis=1))
+    assert np.array_equal(full["counts"], a["counts"] + b["counts"])
+
+
+# ------------------------------------------------------------------ leaves ----
+def test_leaves_hand_worked(oracle_mod):
+    leaf = oracle_mod.leaves(golden("leaves7.pbn"), [1])
+    assert sorted(np.flatnonzero(leaf).tolist()) == [2, 3, 6]
+
+
+def test_leaf_tables_do_not_affect_retained_nodes(oracle_mod):
+    """Sec. 3.1: removing leaves leaves every other node's simulation unchanged.
+    Rewriting the truth tables of the oracle's leaves keeps the retained nodes'
+    trajectories bit-identical; rewriting one retained node's table changes them."""
+    from paper_1605_00854_gb300 import synth
+    net = synth.paper100(seed=5, n=60, p=0.01)
+    text = net.to_text()
+    meta = [0, 1, 2]
+    leaf = oracle_mod.leaves(text, meta)
+    assert leaf.sum() >= 10 and not leaf[meta].any()
+    base = oracle_mod.simulate(text, 3, 0, 4, 500, meta_ids=meta, trace=True)
+    rng = np.random.default_rng(0)
+    for i in np.flatnonzero(leaf):
+        for f in net.funcs[i]:
+            f.tt = int(rng.integers(0, 1 << (1 << len(f.parents))))
+    alt = oracle_mod.simulate(net.to_text(), 3, 0, 4, 500, meta_ids=meta, trace=True)
+    keep = ~leaf
+    assert np.array_equal(base["trace"][:, :, keep], alt["trace"][:, :, keep])
+    assert np.array_equal(base["counts"], alt["counts"])
+    j = int(np.flatnonzero(keep & (np.arange(60) > 2))[0])
+    net.funcs[j][0].tt ^= (1 << (1 << len(net.funcs[j][0].parents))) - 1
+    bad = oracle_mod.simulate(net.to_text(), 3, 0, 4, 500, meta_ids=meta, trace=True)
+    assert not np.array_equal(base["trace"][:, :, keep], bad["trace"][:, :, keep])
+
+
+# ----------------------------------------------------- stationary vs simulation ----
+def test_simulation_meets_exact_stationary_probability(oracle_mod):
+    """Tiny n = 12 network: the meta-state frequency of 64 keyed trajectories of
+    10^4 steps agrees with pi(meta) from power iteration on the 4096 x 4096
+    matrix within 5 standard errors of the per-trajectory means."""
+    from paper_1605_00854_gb300 import synth
+    text = synth.tiny12(1).to_text()
+    meta = [0, 1, 2]
+    M = oracle_mod.transition_matrix(text)
+    assert np.allclose(M.sum(axis=1), 1.0, atol=1e-12)
+    pi, _ = oracle_mod.stationary(M)
+    target = oracle_mod.meta_probability(pi, 12, meta)
+    r = oracle_mod.simulate(text, 1, 0, 64, 10000, meta_ids=meta, count_from=100, nthreads=8)
+    c = r["counts"].astype(np.float64)
+    per = c[:, 0] / (c[:, 1:].sum(axis=1) + 1)
+    se = per.std(ddof=1) / math.sqrt(len(per))
+    assert abs(per.mean() - target) < 5 * se + 1e-3
+
+
+# --------------------------------------------------------------- estimator ----
+@pytest.mark.parametrize("a,b", [(0.1, 0.1), (0.02, 0.3), (0.4, 0.7), (0.05, 0.01)])
+def test_estimator_burn_in_against_matrix_powers(oracle_mod, a, b):
+    """m* of the two-state chain: after m* steps every row of Q^m is within eps of
+    the limit, and m* - 1 steps are not enough (checked with numpy matrix powers)."""
+    N = 10**6
+    n01, n00 = round(a * N), N - round(a * N)
+    n10, n11 = round(b * N), N - round(b * N)
+    eps = 1e-3
+    est = oracle_mod.estimate([0, n00, n01, n10, n11], 1, 0.01, 0.95, eps)
+    aa, bb = n01 / N, n10 / N
+    Q = np.array([[1 - aa, aa], [bb, 1 - bb]])
+    lim = np.array([bb, aa]) / (aa + bb)
+    m = est["m_star"]
+    dev = lambda k: np.abs(np.linalg.matrix_power(Q, k) - lim[None, :]).max()
+    assert dev(m) <= eps * (1 + 1e-9)
+    if m > 1:
+        assert dev(m - 1) > eps
+
+
+@pytest.mark.parametrize("a,b", [(0.1, 0.1), (0.02, 0.3), (0.4, 0.7)])
+def test_estimator_sample_size_against_exact_variance(oracle_mod, a, b):
+    """N* of the two-state chain: the exact variance of the mean of N stationary
+    steps, summed from the autocovariances lambda^|i-j|, times N tends to the
+    asymptotic variance the estimator uses; N* is the smallest N with
+    z * sqrt(var / N) <= r."""
+    r, s = 0.01, 0.95
+    M = 10**6
+    counts = [0, M - round(a * M), round(a * M), round(b * M), M - round(b * M)]
+    est = oracle_mod.estimate(counts, 1, r, s, 1e-3)
+    aa, bb = counts[2] / M, counts[3] / M
+    lam = 1 - aa - bb
+    pi = aa / (aa + bb)
+    N = est["n_star"]
+    k = np.arange(1, N)
+    exact = pi * (1 - pi) * (N + 2 * np.sum((N - k) * lam ** k)) / N**2
+    z = est["z"]
+    assert z * math.sqrt(exact) <= r * (1 + 5.0 / N * (1 + abs(lam)) / (1 - abs(lam)) ** 2)
+    asym = est["n_star_real"]
+    assert asym <= N < asym + 1
+
+
+def test_worked_sample_size_number(oracle_mod):
+    """alpha = beta = 0.1, r = 0.01, s = 0.95: a b (2-a-b)/(a+b)^3 = 2.25 and
+    (1.959964 / 0.01)^2 = 38414.59, so N* = ceil(86432.82) = 86433 (worked by hand)."""
+    est = oracle_mod.estimate([0, 900, 100, 100, 900], 1, 0.01, 0.95, 1e-3)
+    assert est["n_star"] == 86433
+
+
+def test_normal_quantile_matches_library(oracle_mod):
+    sp = pytest.importorskip("scipy.special")
+    for s in [0.5, 0.8, 0.9, 0.95, 0.99, 0.999999]:
+        est = oracle_mod.estimate([1, 10, 5, 5, 10], 1, 0.01, s, 1e-3)
+        assert abs(est["z"] - sp.ndtri((1 + s) / 2)) < 1e-12
