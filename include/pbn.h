@@ -1,0 +1,254 @@
+/*
+ * pbn.h -- C ABI of the GB300-native probabilistic Boolean network simulator.
+ *
+ * The library implements the structure-based simulation of Mizera, Pang and Yuan,
+ * "Fast Simulation of Probabilistic Boolean Networks": leaf-node reduction
+ * (Sec. 3.1, Definition 1), node grouping into merged predictor functions
+ * (Sec. 3.3, Eq. 2, Algorithms 3-4) and the per-step simulation of Algorithm 5,
+ * run for many trajectories at once by CUDA kernels for sm_103a.  Every step
+ * follows Eq. 1 (Sec. 2.1): each node is flipped with probability p; if any node
+ * flipped, the next state is s XOR gamma, otherwise every node applies a predictor
+ * function drawn from its selection probabilities.  The kernels also count the
+ * visits and transitions of a meta-state that the two-state Markov chain
+ * estimator (Sec. 4.2) consumes.
+ *
+ * Random draws are keyed: draw = Philox4x32-10(key = seed, counter = (trajectory,
+ * step, domain, index)) with indices defined on ORIGINAL node ids, so results do
+ * not depend on launch shape, reduction or grouping.  Domains:
+ *   PERT (1): node i = 64w + b, index w << 4 | h gives levels 2h (x1:x0) and
+ *             2h+1 (x3:x2); u_i has bit 31-l equal to bit b of level l, and node i
+ *             is perturbed iff u_i < P = floor(p * 2^32).
+ *   SEL  (2): nodes with >= 2 functions ranked by ascending id; rank r reads word
+ *             x_{r mod 4} of index r / 4; the 0-based choice is the number of
+ *             thresholds T_j = min(floor(C_j 2^32), 2^32), C_j = c_1 + ... + c_j
+ *             summed left to right in fp64, j = 1..l-1, with u >= T_j.
+ *   INIT (3): step 0; word w of s(0) is x1:x0 (w even) or x3:x2 (w odd) of
+ *             index w / 2.
+ * Counter: c0 = trajectory bits 0..31, c1 = step bits 0..31,
+ * c2 = step bits 32..47 | trajectory bits 32..47 << 16, c3 = domain << 28 | index.
+ *
+ * Conventions.
+ *  - Every function returns a pbn status (0 = PBN_OK, negative = error).  No C++
+ *    exception crosses this boundary.  pbn_last_error_detail() gives a message
+ *    for the calling thread's last error.
+ *  - pbn_net and pbn_plan are opaque, created by the library, freed with the
+ *    matching *_free call, and immutable after creation: concurrent
+ *    pbn_simulate calls on one plan are safe.
+ *  - Device buffers are owned by the caller and passed as raw device pointers
+ *    together with a cudaStream_t (as void*).  The library allocates no device
+ *    memory and never synchronises the caller's stream.
+ */
+#ifndef PBN_H
+#define PBN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define PBN_OK 0
+#define PBN_EINVAL (-1)   /* an argument is out of range or inconsistent */
+#define PBN_EPARSE (-2)   /* the network text is malformed */
+#define PBN_ENOMEM (-3)   /* host allocation failed */
+#define PBN_ECUDA (-4)    /* a CUDA runtime call or kernel launch failed */
+#define PBN_ETOOBIG (-5)  /* a plan does not fit the device limits (tables, shared memory) */
+#define PBN_ETIMEOUT (-6) /* a bounded device wait gave up (see PBN_DEV_* bits) */
+#define PBN_EDEVICE (-7)  /* a kernel reported an error in its status word */
+
+/* Bits a kernel ORs into the caller's device status word. */
+#define PBN_DEV_STAGE_TIMEOUT 0x1u /* the bulk copy of plan tables into shared memory did not complete in time */
+#define PBN_DEV_BAD_PLAN 0x2u      /* the device image does not carry the expected header */
+
+/* ---- networks ---------------------------------------------------------------- */
+typedef struct pbn_net pbn_net;
+typedef struct pbn_plan pbn_plan;
+
+/* Parse a PBN G(X, F) with perturbation rate p (Sec. 2.1) from text:
+ *     pbn <n> <p>
+ *     f <node> <c> <k> <a_0> ... <a_{k-1}> <truth table hex>
+ * one 'f' line per predictor function f_j of node <node> (in order j = 1, 2, ...),
+ * with selection probability c, k distinct parents and a truth table whose bit
+ * x = sum_b s[a_b] 2^b is the output.  Numbers may be decimal or C99 hex floats.
+ * Requires 1 <= n <= 2^24, 0 <= p < 1, k <= 24, 1..16 functions per node, c >= 0
+ * and |sum_j c_j - 1| <= 1e-9 per node.  text need not be NUL-terminated.
+ * On success *out owns a new network (free with pbn_net_free).
+ * Errors: PBN_EINVAL (NULL argument), PBN_EPARSE (malformed text), PBN_ENOMEM. */
+int pbn_load(const char* text, size_t len, pbn_net** out);
+
+typedef struct {
+    uint32_t n;            /* nodes of the original network */
+    uint32_t n_retained;   /* nodes kept by pbn_reduce (n for an unreduced network) */
+    uint32_t n_functions;  /* N_F, total number of predictor functions */
+    uint32_t n_multi;      /* nodes with >= 2 predictor functions (SEL ranks) */
+    double p;              /* perturbation rate as given */
+    uint64_t P;            /* floor(p * 2^32): node perturbed iff its u < P */
+    double density;        /* D(G) = (1/n) sum_i phi(i), Sec. 2.1 */
+} pbn_net_info;
+
+/* Shape of a network.  Errors: PBN_EINVAL. */
+int pbn_net_info_get(const pbn_net* net, pbn_net_info* out);
+
+/* Leaf-node reduction (Sec. 3.1, Definition 1).  A node is a leaf iff it is not
+ * in interest[] and each of its children (nodes having it as a parent of some
+ * function; self-edges not counted) is a leaf, applied until nothing changes.
+ * *reduced is a new network that keeps every node of net (leaves still take part
+ * in the perturbation draw, Sec. 3.1) but marks only the retained nodes for
+ * simulation.  retained_ids (capacity net's n, may be NULL) receives the retained
+ * original ids in ascending order and *n_retained their number (may be NULL).
+ * The nodes of interest are the meta-state nodes of the analysis; they are always
+ * retained.  Errors: PBN_EINVAL (NULL net/reduced, interest id out of range),
+ * PBN_ENOMEM. */
+int pbn_reduce(const pbn_net* net, const uint32_t* interest, uint32_t n_interest,
+               pbn_net** reduced, uint32_t* retained_ids, uint32_t* n_retained);
+
+/* ---- plans ------------------------------------------------------------------- */
+#define PBN_PLAN_GROUPED 0u /* node grouping of Sec. 3.3 (Eq. 2, Algorithms 3-4) */
+#define PBN_PLAN_PLAIN 1u   /* one node per group: the unmerged per-node method */
+
+typedef struct {
+    uint32_t mode;          /* PBN_PLAN_GROUPED or PBN_PLAN_PLAIN */
+    uint32_t max_inputs;    /* max distinct input nodes of a merged group (1..24, default 8) */
+    uint32_t max_width;     /* max nodes per group (1..32, default 32) */
+    uint32_t reserved;
+    double theta;           /* memory limit of Sec. 3.3 on sum over groups of the
+                               number of combined functions (default 65536) */
+    uint64_t smem_budget;   /* bytes of plan image that may be staged into shared
+                               memory (0 = default 160 KiB); larger tables are read
+                               from global memory */
+} pbn_group_params;
+
+/* Fill *prm with the defaults above. */
+void pbn_group_params_default(pbn_group_params* prm);
+
+/* Build a simulation plan (Algorithm 5, Preparation) for the retained nodes of net.
+ * GROUPED: nodes with >= 2 functions are split into m groups, m starting from the
+ * lower bound of Eq. 2 and grown by one until the greedy partition of Algorithm 3
+ * satisfies sum_i prod_{v in S_i} l(v) <= theta and every group has at most
+ * max_inputs distinct inputs and max_width nodes (when only the input or width cap
+ * fails, m grows by the number of nodes the greedy could not place); nodes with one
+ * function are grouped greedily by most shared parents under the same caps
+ * (Algorithm 4).  Each group's functions are merged into one table T[c][x]
+ * (Sec. 3.3): c = mixed-radix combined choice, x = packed input pattern, output bit
+ * i = node i of the group (right to left).  Groups are packed into 32-bit words of
+ * the state (a group never straddles a word); the state is exposed as uint64 words.
+ * prm may be NULL (defaults).  On success *out owns a new plan.
+ * Errors: PBN_EINVAL, PBN_ETOOBIG (a table exceeds 2^30 bits), PBN_ENOMEM. */
+int pbn_group(const pbn_net* net, const pbn_group_params* prm, pbn_plan** out);
+
+typedef struct {
+    uint32_t n;              /* original nodes */
+    uint32_t n_retained;     /* simulated nodes */
+    uint32_t n_groups;       /* groups, i.e. table lookups per non-perturbed step */
+    uint32_t n_groups_multi; /* groups made of nodes with >= 2 functions */
+    uint32_t state_words;    /* uint64 words per trajectory of the grouped state */
+    uint32_t n_sel_blocks;   /* SEL Philox blocks drawn per non-perturbed step */
+    uint32_t m_lower_bound;  /* m^_min of Eq. 2 (0 if there are no multi-function nodes) */
+    uint32_t m_found;        /* m used by Algorithm 4 for the multi-function nodes */
+    uint64_t sum_weights;    /* sum over multi groups of prod l(v) (Sec. 3.3) */
+    uint64_t table_bytes;    /* bytes of merged tables */
+    uint64_t image_bytes;    /* bytes of the device image (pbn_plan_image) */
+    uint64_t stage_bytes;    /* leading bytes of the image staged into shared memory */
+    uint32_t tables_in_smem; /* 1 if the tables are staged into shared memory */
+    uint32_t total_inputs;   /* sum over groups of their distinct inputs */
+} pbn_plan_info;
+
+/* Errors: PBN_EINVAL. */
+int pbn_plan_info_get(const pbn_plan* plan, pbn_plan_info* out);
+
+/* Serialise the plan's device image (group specs, thresholds, maps, tables) into
+ * host memory host_dst of cap bytes (cap >= image_bytes).  The caller copies it
+ * to a device buffer of its own that is 16-byte aligned and passes that buffer to
+ * pbn_simulate.  Errors: PBN_EINVAL (NULL or cap too small). */
+int pbn_plan_image(const pbn_plan* plan, void* host_dst, size_t cap);
+
+/* Layout of the grouped state: pos[i] (capacity n) = 32 * word32 + bit of
+ * original node i in the state, where word32 = 2 * (uint64 word) + (bit >= 32),
+ * or UINT32_MAX for a node removed by reduction.  Errors: PBN_EINVAL. */
+int pbn_plan_layout(const pbn_plan* plan, uint32_t* pos);
+
+/* Group of every original node (UINT32_MAX if removed), in evaluation order.
+ * Errors: PBN_EINVAL. */
+int pbn_plan_groups(const pbn_plan* plan, uint32_t* group_of);
+
+/* ---- simulation ----------------------------------------------------------------- */
+#define PBN_INIT_KEYED 0u /* s(0) from the INIT draws (step_begin must be 0) */
+#define PBN_INIT_STATE 1u /* start from d_state */
+
+typedef struct {
+    uint64_t seed;         /* Philox key */
+    uint64_t traj_begin;   /* global id of the first trajectory (< 2^48) */
+    uint64_t n_traj;       /* trajectories in this call (< 2^31) */
+    uint64_t step_begin;   /* index t of the first step: maps s(t) -> s(t+1) */
+    uint64_t n_steps;      /* steps in this call (< 2^32; step_begin + n_steps <= 2^48) */
+    uint64_t count_from;   /* states s(u) with u >= count_from are counted */
+    uint32_t init;         /* PBN_INIT_KEYED or PBN_INIT_STATE */
+    uint32_t n_meta;       /* meta-state nodes (1..1024) */
+    const uint32_t* meta_ids;  /* host: original ids of the meta-state nodes (retained) */
+    const uint8_t* meta_vals;  /* host: required value of each (NULL: all 1) */
+    void* d_state;   /* device uint64 [state_words][n_traj], SoA; read if init is
+                        PBN_INIT_STATE, always written with s(step_begin + n_steps) */
+    void* d_counts;  /* device uint64 [5][n_traj] or NULL: rows V, n00, n01, n10, n11
+                        accumulated (+=) over counted states and consecutive counted
+                        pairs (z_prev, z) of the meta-state indicator z */
+    void* d_pooled;  /* device uint64 [5] or NULL: the same counts summed over the
+                        trajectories of this call, accumulated with atomics */
+    void* d_status;  /* device uint32 or NULL: ORed with PBN_DEV_* bits on error */
+    void* d_trace;   /* device uint64 [n_steps][state_words][n_traj] or NULL: the
+                        state after every step (for checking; slows the kernel) */
+    uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8 */
+    uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj */
+} pbn_sim_args;
+
+/* Simulate trajectories traj_begin .. traj_begin + n_traj - 1 for steps
+ * step_begin .. step_begin + n_steps - 1 (Algorithm 5, ParallelSimulation, with
+ * Eq. 1 semantics), enqueued on the CUDA stream `stream` (cudaStream_t, NULL =
+ * legacy default stream).  d_image is the caller's 16-byte aligned device copy of
+ * pbn_plan_image(plan).  Results are bit-identical to the unreduced, ungrouped
+ * definition for any launch shape.  Returns after enqueueing; device-side errors
+ * appear in *d_status.  n_traj == 0 enqueues nothing.
+ * Errors: PBN_EINVAL (bad pointer, alignment, range, meta node removed or too many
+ * distinct meta words (> 16)), PBN_ETOOBIG (shared memory), PBN_ECUDA. */
+int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn_sim_args* args,
+                 void* stream);
+
+/* ---- estimation ------------------------------------------------------------------ */
+typedef struct {
+    double alpha;        /* n01 / (n00 + n01), NaN if undefined */
+    double beta;         /* n10 / (n10 + n11), NaN if undefined */
+    double pi;           /* V / L, the steady-state probability estimate */
+    double var;          /* alpha beta (2 - alpha - beta) / ((alpha + beta)^3 L) */
+    double z;            /* Phi^-1((1 + s) / 2) */
+    double n_star_real;  /* alpha beta (2-alpha-beta)/(alpha+beta)^3 (z/r)^2 */
+    uint64_t L;          /* counted states: n00 + n01 + n10 + n11 + n_traj */
+    uint64_t m_star;     /* burn-in; UINT64_MAX if undefined */
+    uint64_t n_star;     /* required counted states; UINT64_MAX if undefined */
+    int32_t defined;     /* 1 if alpha, beta > 0 and both are defined */
+    int32_t done;        /* 1 if defined, L >= n_star and burn_in_used >= m_star */
+} pbn_estimate_out;
+
+/* Two-state Markov chain estimate (Sec. 4.2, the Raftery-Lewis approach the paper
+ * cites): from the pooled counts [V, n00, n01, n10, n11] of n_traj trajectories,
+ * precision r, confidence s and burn-in tolerance eps:
+ *   m* = max(1, ceil(log(eps (alpha+beta) / max(alpha, beta)) / log|1-alpha-beta|))
+ *        (1 if alpha + beta = 1; undefined if |1 - alpha - beta| = 1),
+ *   N* = ceil(alpha beta (2 - alpha - beta) / (alpha + beta)^3 (z / r)^2).
+ * burn_in_used is the number of initial states the caller excluded per trajectory.
+ * Errors: PBN_EINVAL (NULL, r <= 0, s not in (0,1), eps <= 0, n_traj == 0). */
+int pbn_estimate(const uint64_t counts[5], uint64_t n_traj, uint64_t burn_in_used,
+                 double r, double s, double eps, pbn_estimate_out* out);
+
+/* ---- misc ------------------------------------------------------------------------ */
+const char* pbn_strerror(int status);
+const char* pbn_last_error_detail(void);
+void pbn_net_free(pbn_net* net);
+void pbn_plan_free(pbn_plan* plan);
+/* Library version string. */
+const char* pbn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBN_H */

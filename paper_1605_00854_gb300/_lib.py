@@ -1,0 +1,116 @@
+"""ctypes binding of libpbn.so (declared in include/pbn.h): argument marshalling only.
+
+The library is loaded on first use.  If it is missing it is built in-tree; if that
+fails an error is raised: there is no CPU fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+u32, u64, i32, f64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_double
+vp, cp = ctypes.c_void_p, ctypes.c_char_p
+
+PBN_OK = 0
+PBN_PLAN_GROUPED = 0
+PBN_PLAN_PLAIN = 1
+PBN_INIT_KEYED = 0
+PBN_INIT_STATE = 1
+PBN_DEV_STAGE_TIMEOUT = 0x1
+PBN_DEV_BAD_PLAN = 0x2
+
+
+class NetInfo(ctypes.Structure):
+    _fields_ = [("n", u32), ("n_retained", u32), ("n_functions", u32), ("n_multi", u32),
+                ("p", f64), ("P", u64), ("density", f64)]
+
+
+class GroupParams(ctypes.Structure):
+    _fields_ = [("mode", u32), ("max_inputs", u32), ("max_width", u32), ("reserved", u32),
+                ("theta", f64), ("smem_budget", u64)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n", u32), ("n_retained", u32), ("n_groups", u32), ("n_groups_multi", u32),
+                ("state_words", u32), ("n_sel_blocks", u32), ("m_lower_bound", u32),
+                ("m_found", u32), ("sum_weights", u64), ("table_bytes", u64),
+                ("image_bytes", u64), ("stage_bytes", u64), ("tables_in_smem", u32),
+                ("total_inputs", u32)]
+
+
+class SimArgs(ctypes.Structure):
+    _fields_ = [("seed", u64), ("traj_begin", u64), ("n_traj", u64), ("step_begin", u64),
+                ("n_steps", u64), ("count_from", u64), ("init", u32), ("n_meta", u32),
+                ("meta_ids", vp), ("meta_vals", vp), ("d_state", vp), ("d_counts", vp),
+                ("d_pooled", vp), ("d_status", vp), ("d_trace", vp),
+                ("lanes_per_traj", u32), ("trajs_per_block", u32)]
+
+
+class EstimateOut(ctypes.Structure):
+    _fields_ = [("alpha", f64), ("beta", f64), ("pi", f64), ("var", f64), ("z", f64),
+                ("n_star_real", f64), ("L", u64), ("m_star", u64), ("n_star", u64),
+                ("defined", i32), ("done", i32)]
+
+
+#: every symbol include/pbn.h declares, with (restype, argtypes)
+SIGNATURES = {
+    "pbn_load": (i32, [cp, ctypes.c_size_t, ctypes.POINTER(vp)]),
+    "pbn_net_info_get": (i32, [vp, ctypes.POINTER(NetInfo)]),
+    "pbn_reduce": (i32, [vp, vp, u32, ctypes.POINTER(vp), vp, ctypes.POINTER(u32)]),
+    "pbn_group_params_default": (None, [ctypes.POINTER(GroupParams)]),
+    "pbn_group": (i32, [vp, ctypes.POINTER(GroupParams), ctypes.POINTER(vp)]),
+    "pbn_plan_info_get": (i32, [vp, ctypes.POINTER(PlanInfo)]),
+    "pbn_plan_image": (i32, [vp, vp, ctypes.c_size_t]),
+    "pbn_plan_layout": (i32, [vp, vp]),
+    "pbn_plan_groups": (i32, [vp, vp]),
+    "pbn_simulate": (i32, [vp, vp, ctypes.POINTER(SimArgs), vp]),
+    "pbn_estimate": (i32, [vp, u64, u64, f64, f64, f64, ctypes.POINTER(EstimateOut)]),
+    "pbn_strerror": (cp, [i32]),
+    "pbn_last_error_detail": (cp, []),
+    "pbn_net_free": (None, [vp]),
+    "pbn_plan_free": (None, [vp]),
+    "pbn_version": (cp, []),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libpbn.so (building it in-tree if absent)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libpbn.so not built at {path}")
+            _build.build()
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return L
+
+
+class PbnError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = load()
+        detail = L.pbn_last_error_detail().decode()
+        super().__init__(f"{where}: {L.pbn_strerror(status).decode()} ({status}): {detail}")
+        self.status = status
+
+
+def check(status: int, where: str):
+    if status != PBN_OK:
+        raise PbnError(status, where)

@@ -1,0 +1,188 @@
+"""Python API over the C ABI: networks, plans, simulation and estimation.
+
+Device memory and streams come from PyTorch; every step of the simulation runs in
+the library's CUDA kernels.  Buffers holding 64-bit words are torch.int64 tensors
+(bit patterns; view them as uint64 on the host).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import _lib
+from ._lib import check
+
+
+def _ptr(t):
+    """Raw data pointer of a torch tensor / numpy array, or None."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Net:
+    """A PBN G(X, F) with perturbation rate p (opaque pbn_net handle)."""
+
+    def __init__(self, handle, text: str | None = None):
+        self._h = handle
+        self.text = text
+
+    @classmethod
+    def load(cls, text: str) -> "Net":
+        L = _lib.load()
+        h = ctypes.c_void_p()
+        b = text.encode()
+        check(L.pbn_load(b, len(b), ctypes.byref(h)), "pbn_load")
+        return cls(h, text)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.load().pbn_net_free(self._h)
+            self._h = None
+
+    def info(self) -> _lib.NetInfo:
+        out = _lib.NetInfo()
+        check(_lib.load().pbn_net_info_get(self._h, ctypes.byref(out)), "pbn_net_info_get")
+        return out
+
+    def reduce(self, interest):
+        """Leaf-node reduction (Definition 1) for the given nodes of interest.
+        Returns (reduced Net, retained original ids)."""
+        L = _lib.load()
+        n = self.info().n
+        it = np.ascontiguousarray(interest, dtype=np.uint32)
+        ids = np.zeros(n, dtype=np.uint32)
+        cnt = ctypes.c_uint32()
+        h = ctypes.c_void_p()
+        check(L.pbn_reduce(self._h, _ptr(it), len(it), ctypes.byref(h), _ptr(ids),
+                           ctypes.byref(cnt)), "pbn_reduce")
+        return Net(h, self.text), ids[: cnt.value].copy()
+
+
+def group_params(mode: int = _lib.PBN_PLAN_GROUPED, max_inputs: int = 8, max_width: int = 32,
+                 theta: float = 65536.0, smem_budget: int = 0) -> _lib.GroupParams:
+    p = _lib.GroupParams()
+    _lib.load().pbn_group_params_default(ctypes.byref(p))
+    p.mode, p.max_inputs, p.max_width, p.theta = mode, max_inputs, max_width, theta
+    if smem_budget:
+        p.smem_budget = smem_budget
+    return p
+
+
+class Plan:
+    """Simulation plan (Algorithm 5, Preparation) and its device image."""
+
+    def __init__(self, net: Net, params: _lib.GroupParams | None = None, **kw):
+        L = _lib.load()
+        prm = params if params is not None else group_params(**kw)
+        h = ctypes.c_void_p()
+        check(L.pbn_group(net._h, ctypes.byref(prm), ctypes.byref(h)), "pbn_group")
+        self._h = h
+        self.net = net
+        self.info = _lib.PlanInfo()
+        check(L.pbn_plan_info_get(self._h, ctypes.byref(self.info)), "pbn_plan_info_get")
+        self._dev = None
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.load().pbn_plan_free(self._h)
+            self._h = None
+
+    def image(self) -> np.ndarray:
+        buf = np.zeros(self.info.image_bytes, dtype=np.uint8)
+        check(_lib.load().pbn_plan_image(self._h, _ptr(buf), buf.size), "pbn_plan_image")
+        return buf
+
+    def layout(self) -> np.ndarray:
+        pos = np.zeros(self.info.n, dtype=np.uint32)
+        check(_lib.load().pbn_plan_layout(self._h, _ptr(pos)), "pbn_plan_layout")
+        return pos
+
+    def groups(self) -> np.ndarray:
+        g = np.zeros(self.info.n, dtype=np.uint32)
+        check(_lib.load().pbn_plan_groups(self._h, _ptr(g)), "pbn_plan_groups")
+        return g
+
+    def device_image(self, device="cuda"):
+        """The image uploaded once to device memory (cached)."""
+        import torch
+        if self._dev is None:
+            self._dev = torch.from_numpy(self.image()).to(device)
+        return self._dev
+
+    def unpack(self, words: np.ndarray) -> np.ndarray:
+        """Grouped state words [state_words, T] (uint64) -> bits [T, n] in original node
+        order, with 0 in the columns of removed nodes."""
+        words = np.asarray(words).view(np.uint64)
+        pos = self.layout()
+        T = words.shape[-1]
+        out = np.zeros((T, self.info.n), dtype=np.uint8)
+        keep = pos != np.uint32(0xFFFFFFFF)
+        rows = (pos[keep] >> 5).astype(np.int64)
+        bits = (pos[keep] & 31).astype(np.uint64)
+        w64 = words[rows >> 1, :]  # [k, T]
+        sh = (bits + np.uint64(32) * (rows & 1).astype(np.uint64))[:, None]
+        out[:, keep] = ((w64 >> sh) & np.uint64(1)).astype(np.uint8).T
+        return out
+
+
+@dataclass
+class SimBuffers:
+    state: "object"       # torch.int64 [state_words, T]
+    counts: "object"      # torch.int64 [5, T]
+    pooled: "object"      # torch.int64 [5]
+    status: "object"      # torch.int32 [1]
+
+
+def alloc_buffers(plan: Plan, n_traj: int, device="cuda") -> SimBuffers:
+    import torch
+    return SimBuffers(
+        state=torch.zeros((plan.info.state_words, n_traj), dtype=torch.int64, device=device),
+        counts=torch.zeros((5, n_traj), dtype=torch.int64, device=device),
+        pooled=torch.zeros(5, dtype=torch.int64, device=device),
+        status=torch.zeros(1, dtype=torch.int32, device=device))
+
+
+def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids, meta_vals=None,
+             traj_begin: int = 0, step_begin: int = 0, count_from: int = 0, init: int | None = None,
+             trace=None, lanes_per_traj: int = 0, trajs_per_block: int = 0, stream=None,
+             d_image=None, n_traj: int | None = None):
+    """Enqueue pbn_simulate on `stream` (default: torch's current stream)."""
+    import torch
+    L = _lib.load()
+    T = bufs.state.shape[1] if n_traj is None else n_traj
+    a = _lib.SimArgs()
+    a.seed, a.traj_begin, a.n_traj = seed, traj_begin, T
+    a.step_begin, a.n_steps, a.count_from = step_begin, n_steps, count_from
+    if init is None:
+        init = _lib.PBN_INIT_KEYED if step_begin == 0 else _lib.PBN_INIT_STATE
+    a.init = init
+    mi = np.ascontiguousarray(meta_ids, dtype=np.uint32)
+    mv = None if meta_vals is None else np.ascontiguousarray(meta_vals, dtype=np.uint8)
+    a.n_meta = len(mi)
+    a.meta_ids = mi.ctypes.data
+    a.meta_vals = None if mv is None else mv.ctypes.data
+    a.d_state = bufs.state.data_ptr()
+    a.d_counts = None if bufs.counts is None else bufs.counts.data_ptr()
+    a.d_pooled = None if bufs.pooled is None else bufs.pooled.data_ptr()
+    a.d_status = None if bufs.status is None else bufs.status.data_ptr()
+    a.d_trace = None if trace is None else trace.data_ptr()
+    a.lanes_per_traj, a.trajs_per_block = lanes_per_traj, trajs_per_block
+    img = plan.device_image(bufs.state.device) if d_image is None else d_image
+    st = torch.cuda.current_stream(bufs.state.device) if stream is None else stream
+    check(L.pbn_simulate(plan._h, ctypes.c_void_p(img.data_ptr()), ctypes.byref(a),
+                         ctypes.c_void_p(st.cuda_stream)), "pbn_simulate")
+
+
+def estimate(counts5, n_traj: int, r: float, s: float, eps: float = 1e-3,
+             burn_in_used: int = 0) -> _lib.EstimateOut:
+    """Two-state Markov chain estimate (pbn_estimate) from pooled counts."""
+    c = np.ascontiguousarray([int(x) for x in counts5], dtype=np.uint64)
+    out = _lib.EstimateOut()
+    check(_lib.load().pbn_estimate(_ptr(c), n_traj, burn_in_used, r, s, eps, ctypes.byref(out)),
+          "pbn_estimate")
+    return out

@@ -1,0 +1,824 @@
+/*
+ * pbn_host.cpp -- host-side preparation of the structure-based PBN simulation.
+ *
+ *   pbn_load      network text -> model G(X, F) with probabilities C_i      (Sec. 2.1)
+ *   pbn_reduce    leaf-node reduction                             (Sec. 3.1, Definition 1)
+ *   pbn_group     node grouping and merged predictor functions    (Sec. 3.3, Eq. 2, Alg. 3-4)
+ *                 and the device image of Algorithm 5's Preparation
+ *   pbn_estimate  two-state Markov chain estimate                  (Sec. 4.2)
+ */
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "pbn_internal.h"
+
+namespace {
+thread_local std::string g_detail;
+}
+
+namespace pbn {
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_detail = buf;
+    return code;
+}
+
+/* Node i is perturbed iff its 32-bit draw u < P = floor(p * 2^32); p * 2^32 is exact. */
+uint64_t pert_threshold(double p) { return (uint64_t)std::floor(p * 4294967296.0); }
+}  // namespace pbn
+
+using pbn::fail;
+
+extern "C" const char* pbn_last_error_detail(void) { return g_detail.c_str(); }
+
+extern "C" const char* pbn_strerror(int s) {
+    switch (s) {
+        case PBN_OK: return "ok";
+        case PBN_EINVAL: return "invalid argument";
+        case PBN_EPARSE: return "malformed network text";
+        case PBN_ENOMEM: return "out of host memory";
+        case PBN_ECUDA: return "CUDA error";
+        case PBN_ETOOBIG: return "plan exceeds device limits";
+        case PBN_ETIMEOUT: return "bounded device wait timed out";
+        case PBN_EDEVICE: return "kernel reported an error";
+        default: return "unknown status";
+    }
+}
+
+extern "C" const char* pbn_version(void) { return "pbn-gb300 1.0 (sm_103a)"; }
+
+/* ------------------------------------------------------------------------- */
+/* Parsing                                                                    */
+/* ------------------------------------------------------------------------- */
+namespace {
+
+bool parse_u64(const std::string& t, uint64_t* v) {
+    if (t.empty()) return false;
+    char* end = nullptr;
+    errno = 0;
+    unsigned long long x = std::strtoull(t.c_str(), &end, 10);
+    if (errno || *end || t[0] == '-') return false;
+    *v = x;
+    return true;
+}
+
+bool parse_f64(const std::string& t, double* v) {
+    if (t.empty()) return false;
+    char* end = nullptr;
+    double x = std::strtod(t.c_str(), &end);
+    if (*end) return false;
+    *v = x;
+    return true;
+}
+
+int nibble(char ch) {
+    if (ch >= '0' && ch <= '9') return ch - '0';
+    if (ch >= 'a' && ch <= 'f') return 10 + ch - 'a';
+    if (ch >= 'A' && ch <= 'F') return 10 + ch - 'A';
+    return -1;
+}
+
+/* Split one line into whitespace-separated tokens, dropping a '#' comment. */
+void tokenize(const char* b, const char* e, std::vector<std::string>* out) {
+    out->clear();
+    const char* hash = static_cast<const char*>(memchr(b, '#', (size_t)(e - b)));
+    if (hash) e = hash;
+    const char* p = b;
+    while (p < e) {
+        while (p < e && (*p == ' ' || *p == '\t' || *p == '\r')) ++p;
+        const char* q = p;
+        while (q < e && *q != ' ' && *q != '\t' && *q != '\r') ++q;
+        if (q > p) out->emplace_back(p, q);
+        p = q;
+    }
+}
+
+int load_impl(const char* text, size_t len, pbn_net** out) {
+    pbn_net* g = new pbn_net();
+    std::vector<std::string> tok;
+    const char* p = text;
+    const char* end = text + len;
+    bool have_header = false;
+    size_t lineno = 0;
+    while (p < end) {
+        const char* nl = static_cast<const char*>(memchr(p, '\n', (size_t)(end - p)));
+        const char* le = nl ? nl : end;
+        ++lineno;
+        tokenize(p, le, &tok);
+        p = nl ? nl + 1 : end;
+        if (tok.empty()) continue;
+        if (tok[0] == "pbn") {
+            uint64_t n;
+            double pr;
+            if (have_header || tok.size() != 3 || !parse_u64(tok[1], &n) || !parse_f64(tok[2], &pr) ||
+                n < 1 || n > (1u << 24) || !(pr >= 0.0 && pr < 1.0)) {
+                delete g;
+                return fail(PBN_EPARSE, "line %zu: bad 'pbn <n> <p>' header", lineno);
+            }
+            have_header = true;
+            g->n = (uint32_t)n;
+            g->p = pr;
+            g->node.assign(n, {});
+        } else if (tok[0] == "f") {
+            uint64_t i, k;
+            double c;
+            if (!have_header || tok.size() < 5 || !parse_u64(tok[1], &i) || !parse_f64(tok[2], &c) ||
+                !parse_u64(tok[3], &k) || i >= g->n || k > 24 || !(c >= 0.0 && c <= 1.0) ||
+                tok.size() != 5 + k) {
+                delete g;
+                return fail(PBN_EPARSE, "line %zu: bad function record", lineno);
+            }
+            pbn_fun f;
+            f.c = c;
+            for (uint64_t b = 0; b < k; ++b) {
+                uint64_t a;
+                if (!parse_u64(tok[4 + b], &a) || a >= g->n ||
+                    std::find(f.par.begin(), f.par.end(), (uint32_t)a) != f.par.end()) {
+                    delete g;
+                    return fail(PBN_EPARSE, "line %zu: bad or repeated parent", lineno);
+                }
+                f.par.push_back((uint32_t)a);
+            }
+            std::string hex = tok[4 + k];
+            if (hex.size() > 2 && hex[0] == '0' && (hex[1] == 'x' || hex[1] == 'X')) hex = hex.substr(2);
+            const uint64_t nbits = 1ull << k;
+            f.tt.assign((nbits + 63) / 64, 0);
+            if (hex.empty()) {
+                delete g;
+                return fail(PBN_EPARSE, "line %zu: empty truth table", lineno);
+            }
+            for (size_t d = 0; d < hex.size(); ++d) {
+                int v = nibble(hex[hex.size() - 1 - d]);
+                if (v < 0) {
+                    delete g;
+                    return fail(PBN_EPARSE, "line %zu: bad hex digit", lineno);
+                }
+                for (int b = 0; b < 4; ++b) {
+                    if (!((v >> b) & 1)) continue;
+                    uint64_t bit = 4 * (uint64_t)d + (uint64_t)b;
+                    if (bit >= nbits) {
+                        delete g;
+                        return fail(PBN_EPARSE, "line %zu: truth table wider than 2^k bits", lineno);
+                    }
+                    f.tt[bit >> 6] |= 1ull << (bit & 63);
+                }
+            }
+            g->node[i].push_back(std::move(f));
+        } else {
+            delete g;
+            return fail(PBN_EPARSE, "line %zu: unknown record '%s'", lineno, tok[0].c_str());
+        }
+    }
+    if (!have_header) {
+        delete g;
+        return fail(PBN_EPARSE, "missing 'pbn' header");
+    }
+    for (uint32_t i = 0; i < g->n; ++i) {
+        const auto& fl = g->node[i];
+        if (fl.empty() || fl.size() > 16) {
+            delete g;
+            return fail(PBN_EPARSE, "node %u has %zu functions (need 1..16)", i, fl.size());
+        }
+        double s = 0.0;
+        for (const auto& f : fl) s += f.c;
+        if (std::fabs(s - 1.0) > 1e-9) {
+            delete g;
+            return fail(PBN_EPARSE, "selection probabilities of node %u sum to %.17g", i, s);
+        }
+    }
+    g->retained.assign(g->n, 1);
+    *out = g;
+    return PBN_OK;
+}
+
+}  // namespace
+
+extern "C" int pbn_load(const char* text, size_t len, pbn_net** out) {
+    if (!text || !out) return fail(PBN_EINVAL, "pbn_load: NULL argument");
+    *out = nullptr;
+    try {
+        return load_impl(text, len, out);
+    } catch (const std::bad_alloc&) {
+        return fail(PBN_ENOMEM, "pbn_load: out of memory");
+    }
+}
+
+extern "C" void pbn_net_free(pbn_net* net) { delete net; }
+
+extern "C" int pbn_net_info_get(const pbn_net* g, pbn_net_info* out) {
+    if (!g || !out) return fail(PBN_EINVAL, "pbn_net_info_get: NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->n = g->n;
+    out->p = g->p;
+    out->P = pbn::pert_threshold(g->p);
+    uint64_t sum_par = 0;
+    for (uint32_t i = 0; i < g->n; ++i) {
+        out->n_retained += g->retained[i];
+        out->n_functions += (uint32_t)g->node[i].size();
+        out->n_multi += g->node[i].size() >= 2;
+        for (const auto& f : g->node[i]) sum_par += f.par.size();
+    }
+    out->density = (double)sum_par / (double)g->n;
+    return PBN_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Leaf-node reduction, Definition 1 (Sec. 3.1).  Peeling: a node not of       */
+/* interest whose count of not-yet-removed children (self-edges excluded)     */
+/* reaches zero is a leaf; removing it decrements its parents' counts.        */
+/* ------------------------------------------------------------------------- */
+extern "C" int pbn_reduce(const pbn_net* net, const uint32_t* interest, uint32_t n_interest,
+                          pbn_net** reduced, uint32_t* retained_ids, uint32_t* n_retained) {
+    if (!net || !reduced || (n_interest && !interest)) return fail(PBN_EINVAL, "pbn_reduce: NULL argument");
+    *reduced = nullptr;
+    try {
+        const uint32_t n = net->n;
+        std::vector<uint8_t> intr(n, 0);
+        for (uint32_t m = 0; m < n_interest; ++m) {
+            if (interest[m] >= n) return fail(PBN_EINVAL, "pbn_reduce: node of interest %u >= n", interest[m]);
+            intr[interest[m]] = 1;
+        }
+        std::vector<std::vector<uint32_t>> parents(n);  /* distinct parents of u, u excluded */
+        std::vector<uint32_t> live_children(n, 0);
+        for (uint32_t u = 0; u < n; ++u) {
+            auto& pu = parents[u];
+            for (const auto& f : net->node[u])
+                for (uint32_t a : f.par)
+                    if (a != u) pu.push_back(a);
+            std::sort(pu.begin(), pu.end());
+            pu.erase(std::unique(pu.begin(), pu.end()), pu.end());
+            for (uint32_t a : pu) live_children[a]++;
+        }
+        std::vector<uint8_t> leaf(n, 0);
+        std::vector<uint32_t> stack;
+        for (uint32_t v = 0; v < n; ++v)
+            if (!intr[v] && live_children[v] == 0) { leaf[v] = 1; stack.push_back(v); }
+        while (!stack.empty()) {
+            uint32_t v = stack.back();
+            stack.pop_back();
+            for (uint32_t a : parents[v]) {
+                if (--live_children[a] == 0 && !intr[a] && !leaf[a]) {
+                    leaf[a] = 1;
+                    stack.push_back(a);
+                }
+            }
+        }
+        pbn_net* r = new pbn_net(*net);
+        uint32_t cnt = 0;
+        for (uint32_t v = 0; v < n; ++v) {
+            r->retained[v] = (uint8_t)(net->retained[v] && !leaf[v]);
+            if (r->retained[v]) {
+                if (retained_ids) retained_ids[cnt] = v;
+                ++cnt;
+            }
+        }
+        r->interest.assign(interest, interest + n_interest);
+        if (n_retained) *n_retained = cnt;
+        *reduced = r;
+        return PBN_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(PBN_ENOMEM, "pbn_reduce: out of memory");
+    }
+}
+
+/* ------------------------------------------------------------------------- */
+/* Grouping (Sec. 3.3)                                                        */
+/* ------------------------------------------------------------------------- */
+namespace {
+
+struct Item {
+    uint32_t id;
+    uint32_t ell;                  /* l(v) = omega(mu) */
+    std::vector<uint32_t> inputs;  /* sorted distinct parents over all functions */
+};
+
+struct Grp {
+    std::vector<uint32_t> nodes;   /* in output bit order (right to left) */
+    std::vector<uint32_t> inputs;  /* sorted distinct inputs */
+    uint64_t weight = 0;           /* prod l(v) over members; 0 when empty */
+    bool multi = false;
+};
+
+uint64_t sat_mul(uint64_t a, uint64_t b) {
+    if (a == 0 || b == 0) return 0;
+    if (a > (UINT64_C(1) << 62) / b) return UINT64_C(1) << 62;
+    return a * b;
+}
+
+size_t union_size(const std::vector<uint32_t>& a, const std::vector<uint32_t>& b) {
+    size_t i = 0, j = 0, u = 0;
+    while (i < a.size() && j < b.size()) {
+        if (a[i] == b[j]) { ++i; ++j; }
+        else if (a[i] < b[j]) ++i;
+        else ++j;
+        ++u;
+    }
+    return u + (a.size() - i) + (b.size() - j);
+}
+
+size_t inter_size(const std::vector<uint32_t>& a, const std::vector<uint32_t>& b) {
+    return a.size() + b.size() - union_size(a, b);
+}
+
+void merge_into(std::vector<uint32_t>* a, const std::vector<uint32_t>& b) {
+    std::vector<uint32_t> out;
+    out.reserve(a->size() + b.size());
+    std::set_union(a->begin(), a->end(), b.begin(), b.end(), std::back_inserter(out));
+    a->swap(out);
+}
+
+uint32_t log2_entry_bits(uint32_t width) {
+    uint32_t l = 0;
+    while ((1u << l) < width) ++l;
+    return l;
+}
+
+/* Bits of a merged table: prod l(v) * 2^q entries of 2^ceil(log2 width) bits. */
+double table_bits(uint64_t prod_ell, size_t q, size_t width) {
+    return (double)prod_ell * std::ldexp(1.0, (int)q) * (double)(1u << log2_entry_bits((uint32_t)width));
+}
+
+constexpr double kMaxTableBits = 1073741824.0; /* 2^30 */
+
+struct Caps {
+    uint32_t max_inputs, max_width;
+};
+
+bool can_join(const Grp& g, const Item& it, const Caps& cp) {
+    if (g.nodes.empty()) return true;
+    if (g.nodes.size() + 1 > cp.max_width) return false;
+    size_t q = union_size(g.inputs, it.inputs);
+    if (q > cp.max_inputs) return false;
+    return table_bits(sat_mul(g.weight, it.ell), q, g.nodes.size() + 1) <= kMaxTableBits;
+}
+
+void join(Grp* g, const Item& it) {
+    g->weight = g->nodes.empty() ? it.ell : sat_mul(g->weight, it.ell);
+    g->nodes.push_back(it.id);
+    merge_into(&g->inputs, it.inputs);
+}
+
+/* Algorithm 3 (FindPartitions): items sorted by descending weight (ties: ascending
+ * id); each goes to the lightest of the m groups (an empty group weighs 0; ties:
+ * lowest index) among those it may join under the GPU caps.  Returns the number of
+ * items no group could take. */
+size_t find_partitions(const std::vector<Item>& S, size_t m, const Caps& cp, std::vector<Grp>* out) {
+    std::vector<Grp> A(m);
+    size_t unplaced = 0;
+    for (const Item& it : S) {
+        size_t best = SIZE_MAX;
+        for (size_t i = 0; i < m; ++i) {
+            if (!can_join(A[i], it, cp)) continue;
+            if (best == SIZE_MAX || A[i].weight < A[best].weight) best = i;
+        }
+        if (best == SIZE_MAX) { ++unplaced; continue; }
+        join(&A[best], it);
+    }
+    out->swap(A);
+    return unplaced;
+}
+
+/* Eq. 2: the smallest m^ with m^ * (prod omega)^(1/m^) <= theta (Theorem 2: a lower
+ * bound on any feasible m).  Evaluated in logarithms; m^ (prod)^(1/m^) is smallest
+ * near m^ = ln(prod), so the scan stops there.  Returns 0 if no m^ satisfies it. */
+uint32_t eq2_lower_bound(const std::vector<Item>& S, double theta) {
+    double L = 0.0;
+    for (const Item& it : S) L += std::log((double)it.ell);
+    const double lt = std::log(theta);
+    const uint64_t stop = std::max<uint64_t>((uint64_t)S.size(), (uint64_t)std::ceil(L) + 2);
+    for (uint64_t m = 1; m <= stop; ++m)
+        if (std::log((double)m) + L / (double)m <= lt + 1e-12) return (uint32_t)m;
+    return 0;
+}
+
+struct PlanParts {
+    std::vector<Grp> groups;
+    uint32_t m_lower = 0, m_found = 0;
+    uint64_t sum_w = 0;
+};
+
+/* Algorithm 4 (Partition) for the retained nodes, plus the common-parent greedy for
+ * single-function nodes (Sec. 3.3). */
+void partition(const pbn_net& g, const pbn_group_params& prm, PlanParts* pp) {
+    Caps cp{prm.max_inputs, prm.max_width};
+    std::vector<Item> S, S1;
+    for (uint32_t v = 0; v < g.n; ++v) {
+        if (!g.retained[v]) continue;
+        Item it;
+        it.id = v;
+        it.ell = (uint32_t)g.node[v].size();
+        for (const auto& f : g.node[v]) it.inputs.insert(it.inputs.end(), f.par.begin(), f.par.end());
+        std::sort(it.inputs.begin(), it.inputs.end());
+        it.inputs.erase(std::unique(it.inputs.begin(), it.inputs.end()), it.inputs.end());
+        (it.ell >= 2 ? S : S1).push_back(std::move(it));
+    }
+    if (prm.mode == PBN_PLAN_PLAIN) {
+        std::vector<Item> all;
+        all.insert(all.end(), S.begin(), S.end());
+        all.insert(all.end(), S1.begin(), S1.end());
+        std::sort(all.begin(), all.end(), [](const Item& a, const Item& b) { return a.id < b.id; });
+        for (const Item& it : all) {
+            Grp gr;
+            join(&gr, it);
+            gr.multi = it.ell >= 2;
+            pp->groups.push_back(std::move(gr));
+        }
+        return;
+    }
+    /* multi-function nodes: Eq. 2 lower bound, then Algorithm 3 with m grown until
+     * the weight sum is within theta (and the caps hold) */
+    std::stable_sort(S.begin(), S.end(), [](const Item& a, const Item& b) {
+        return a.ell != b.ell ? a.ell > b.ell : a.id < b.id;
+    });
+    if (!S.empty()) {
+        pp->m_lower = eq2_lower_bound(S, prm.theta);
+        size_t m = pp->m_lower ? std::min<size_t>(pp->m_lower, S.size()) : S.size();
+        std::vector<Grp> A;
+        for (;;) {
+            size_t unplaced = find_partitions(S, m, cp, &A);
+            uint64_t sum = 0;
+            for (const Grp& gr : A) sum += gr.weight;
+            if ((unplaced == 0 && (double)sum <= prm.theta) || m >= S.size()) {
+                pp->sum_w = sum;
+                break;
+            }
+            m = std::min(S.size(), m + std::max<size_t>(1, unplaced));
+        }
+        pp->m_found = (uint32_t)m;
+        for (Grp& gr : A) {
+            if (gr.nodes.empty()) continue;
+            gr.multi = true;
+            pp->groups.push_back(std::move(gr));
+        }
+    }
+    /* single-function nodes: visit by descending number of parents (ties: id); join
+     * the feasible group sharing most parents (ties: lowest index), else open one */
+    std::stable_sort(S1.begin(), S1.end(), [](const Item& a, const Item& b) {
+        return a.inputs.size() != b.inputs.size() ? a.inputs.size() > b.inputs.size() : a.id < b.id;
+    });
+    std::vector<Grp> A2;
+    for (const Item& it : S1) {
+        size_t best = SIZE_MAX, best_shared = 0;
+        for (size_t i = 0; i < A2.size(); ++i) {
+            if (!can_join(A2[i], it, cp)) continue;
+            size_t sh = inter_size(A2[i].inputs, it.inputs);
+            if (best == SIZE_MAX || sh > best_shared) { best = i; best_shared = sh; }
+        }
+        if (best == SIZE_MAX) {
+            A2.emplace_back();
+            best = A2.size() - 1;
+        }
+        join(&A2[best], it);
+    }
+    for (Grp& gr : A2) pp->groups.push_back(std::move(gr));
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
+    PlanParts pp;
+    partition(g, prm, &pp);
+    const uint32_t n = g.n;
+    const uint32_t W = (n + 63) / 64;
+
+    /* SEL ranks over every node with >= 2 functions, leaves included */
+    std::vector<uint32_t> rank(n, UINT32_MAX);
+    uint32_t r = 0;
+    for (uint32_t v = 0; v < n; ++v)
+        if (g.node[v].size() >= 2) rank[v] = r++;
+
+    /* pack groups into 32-bit state words: first fit by decreasing width */
+    std::vector<size_t> order(pp.groups.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+        return pp.groups[a].nodes.size() > pp.groups[b].nodes.size();
+    });
+    std::vector<uint32_t> fill;                 /* used bits per word */
+    std::vector<std::vector<size_t>> in_word;   /* groups of each word in placement order */
+    std::vector<uint32_t> gword(pp.groups.size()), gshift(pp.groups.size());
+    for (size_t gi : order) {
+        uint32_t w = (uint32_t)pp.groups[gi].nodes.size();
+        size_t k = 0;
+        while (k < fill.size() && fill[k] + w > 32) ++k;
+        if (k == fill.size()) { fill.push_back(0); in_word.emplace_back(); }
+        gword[gi] = (uint32_t)k;
+        gshift[gi] = fill[k];
+        fill[k] += w;
+        in_word[k].push_back(gi);
+    }
+    uint32_t W32 = (uint32_t)fill.size();
+    if (W32 == 0) W32 = 2;
+    W32 = (W32 + 1) & ~1u;
+    in_word.resize(W32);
+
+    plan->pos.assign(n, UINT32_MAX);
+    plan->group_of.assign(n, UINT32_MAX);
+    /* evaluation order: word by word */
+    std::vector<size_t> eval;
+    for (uint32_t k = 0; k < W32; ++k)
+        for (size_t gi : in_word[k]) eval.push_back(gi);
+    for (size_t e = 0; e < eval.size(); ++e) {
+        const Grp& gr = pp.groups[eval[e]];
+        for (size_t i = 0; i < gr.nodes.size(); ++i) {
+            plan->pos[gr.nodes[i]] = 32 * gword[eval[e]] + gshift[eval[e]] + (uint32_t)i;
+            plan->group_of[gr.nodes[i]] = (uint32_t)e;
+        }
+    }
+
+    /* selection blocks: the SEL Philox blocks holding retained multi-function ranks */
+    std::vector<uint32_t> selblk;
+    for (uint32_t v = 0; v < n; ++v)
+        if (g.retained[v] && rank[v] != UINT32_MAX) selblk.push_back(rank[v] >> 2);
+    std::sort(selblk.begin(), selblk.end());
+    selblk.erase(std::unique(selblk.begin(), selblk.end()), selblk.end());
+    auto sel_slot = [&](uint32_t v) {
+        uint32_t b = rank[v] >> 2;
+        uint32_t idx = (uint32_t)(std::lower_bound(selblk.begin(), selblk.end(), b) - selblk.begin());
+        return 4 * idx + (rank[v] & 3);
+    };
+
+    std::vector<uint32_t> words(2 * W32);
+    std::vector<pbn_img_group> grec;
+    std::vector<pbn_img_multi> mrec;
+    std::vector<uint32_t> thr, inrec, tables;
+    uint64_t total_inputs = 0;
+    uint32_t n_groups_multi = 0;
+    for (uint32_t k = 0; k < W32; ++k) {
+        words[2 * k] = (uint32_t)grec.size();
+        words[2 * k + 1] = (uint32_t)in_word[k].size();
+        for (size_t gi : in_word[k]) {
+            const Grp& gr = pp.groups[gi];
+            n_groups_multi += gr.multi;
+            /* inputs sorted by state position */
+            std::vector<uint32_t> ins = gr.inputs;
+            std::sort(ins.begin(), ins.end(), [&](uint32_t a, uint32_t b) { return plan->pos[a] < plan->pos[b]; });
+            const size_t q = ins.size();
+            if (q > 24) return fail(PBN_ETOOBIG, "group with %zu inputs (max 24)", q);
+            std::vector<int> inpos(n, -1);
+            for (size_t b = 0; b < q; ++b) {
+                uint32_t ps = plan->pos[ins[b]];
+                if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", ins[b]);
+                inpos[ins[b]] = (int)b;
+                inrec.push_back(((ps >> 5) << 5) | (((ps & 31) - (uint32_t)b) & 31));
+            }
+            /* multi-function members, mixed radix in group bit order */
+            std::vector<uint32_t> radix(gr.nodes.size(), 0);
+            uint64_t prod = 1;
+            pbn_img_group G{};
+            G.mul_first = (uint32_t)mrec.size();
+            for (size_t i = 0; i < gr.nodes.size(); ++i) {
+                uint32_t v = gr.nodes[i];
+                const auto& fl = g.node[v];
+                if (fl.size() < 2) continue;
+                radix[i] = (uint32_t)prod;
+                pbn_img_multi M{};
+                M.u_slot = sel_slot(v);
+                M.radix = (uint32_t)prod;
+                M.thr_first = (uint32_t)thr.size();
+                double C = 0.0;
+                for (size_t j = 1; j < fl.size(); ++j) {
+                    C = C + fl[j - 1].c;
+                    double t = std::floor(C * 4294967296.0);
+                    if (t >= 4294967296.0) break; /* T_j = 2^32 never fires */
+                    thr.push_back((uint32_t)t);
+                    M.n_thr++;
+                }
+                mrec.push_back(M);
+                prod *= fl.size();
+                if (prod > (UINT64_C(1) << 30)) return fail(PBN_ETOOBIG, "group with too many combined functions");
+            }
+            const uint32_t width = (uint32_t)gr.nodes.size();
+            const uint32_t l2w = log2_entry_bits(width);
+            const uint64_t entries = prod << q;
+            const uint64_t bits = entries << l2w;
+            if ((double)bits > kMaxTableBits) return fail(PBN_ETOOBIG, "merged table of %llu bits exceeds 2^30", (unsigned long long)bits);
+            G.tab_off = (uint32_t)tables.size();
+            G.in_first = (uint32_t)(inrec.size() - q);
+            G.q = (uint8_t)q;
+            G.l2w = (uint8_t)l2w;
+            G.n_mul = (uint8_t)(mrec.size() - G.mul_first);
+            G.shift = (uint8_t)gshift[gi];
+            grec.push_back(G);
+            total_inputs += q;
+            /* the merged table (Sec. 3.3): entry (c << q) | x, bit i = node i's selected
+             * function evaluated on the inputs packed in x */
+            tables.resize(tables.size() + (size_t)((bits + 31) / 32), 0);
+            uint32_t* tab = tables.data() + G.tab_off;
+            std::vector<std::vector<uint8_t>> argpos(width);
+            for (uint64_t c = 0; c < prod; ++c) {
+                for (uint64_t x = 0; x < (1ull << q); ++x) {
+                    uint32_t v_out = 0;
+                    for (size_t i = 0; i < width; ++i) {
+                        uint32_t v = gr.nodes[i];
+                        const auto& fl = g.node[v];
+                        size_t j = fl.size() >= 2 ? (size_t)((c / radix[i]) % fl.size()) : 0;
+                        const pbn_fun& f = fl[j];
+                        uint64_t idx = 0;
+                        for (size_t b = 0; b < f.par.size(); ++b)
+                            idx |= (uint64_t)((x >> inpos[f.par[b]]) & 1u) << b;
+                        v_out |= (uint32_t)f.bit(idx) << i;
+                    }
+                    uint64_t e = (c << q) | x;
+                    uint64_t bo = e << l2w;
+                    tab[bo >> 5] |= v_out << (bo & 31);
+                }
+            }
+        }
+    }
+
+    std::vector<uint64_t> ret(W, 0);
+    for (uint32_t v = 0; v < n; ++v)
+        if (g.retained[v]) ret[v >> 6] |= 1ull << (v & 63);
+
+    /* assemble the image */
+    pbn_img_header H{};
+    H.magic = PBN_IMG_MAGIC;
+    H.n = n;
+    H.W = W;
+    H.W32 = W32;
+    H.n_groups = (uint32_t)grec.size();
+    H.n_multi = (uint32_t)mrec.size();
+    H.n_sel = (uint32_t)selblk.size();
+    H.P = (uint32_t)pbn::pert_threshold(g.p);
+    size_t off = align16(sizeof(pbn_img_header));
+    H.off_words = (uint32_t)off; off = align16(off + words.size() * 4);
+    H.off_groups = (uint32_t)off; off = align16(off + grec.size() * sizeof(pbn_img_group));
+    H.off_multi = (uint32_t)off; off = align16(off + mrec.size() * sizeof(pbn_img_multi));
+    H.off_thr = (uint32_t)off; off = align16(off + thr.size() * 4);
+    H.off_inputs = (uint32_t)off; off = align16(off + inrec.size() * 4);
+    H.off_selblk = (uint32_t)off; off = align16(off + selblk.size() * 4);
+    H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
+    H.off_pos = (uint32_t)off; off = align16(off + plan->pos.size() * 4);
+    H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
+    if (off >= (UINT64_C(1) << 31)) return fail(PBN_ETOOBIG, "device image of %zu bytes", off);
+    H.image_bytes = (uint32_t)off;
+    const uint64_t budget = prm.smem_budget ? prm.smem_budget : 160 * 1024;
+    H.tables_in_smem = off <= budget ? 1u : 0u;
+    H.stage_bytes = H.tables_in_smem ? H.image_bytes : H.off_tables;
+    if (H.stage_bytes > budget) return fail(PBN_ETOOBIG, "plan specs of %u bytes exceed the shared-memory budget", H.stage_bytes);
+
+    plan->image.assign(off, 0);
+    uint8_t* img = plan->image.data();
+    memcpy(img, &H, sizeof(H));
+    memcpy(img + H.off_words, words.data(), words.size() * 4);
+    if (!grec.empty()) memcpy(img + H.off_groups, grec.data(), grec.size() * sizeof(pbn_img_group));
+    if (!mrec.empty()) memcpy(img + H.off_multi, mrec.data(), mrec.size() * sizeof(pbn_img_multi));
+    if (!thr.empty()) memcpy(img + H.off_thr, thr.data(), thr.size() * 4);
+    if (!inrec.empty()) memcpy(img + H.off_inputs, inrec.data(), inrec.size() * 4);
+    if (!selblk.empty()) memcpy(img + H.off_selblk, selblk.data(), selblk.size() * 4);
+    memcpy(img + H.off_ret, ret.data(), ret.size() * 8);
+    memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
+    if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);
+    plan->hdr = H;
+    plan->per_traj_smem = 4 * (2 * W32 + 4 * H.n_sel);
+
+    pbn_plan_info& I = plan->info;
+    memset(&I, 0, sizeof(I));
+    I.n = n;
+    for (uint32_t v = 0; v < n; ++v) I.n_retained += g.retained[v];
+    I.n_groups = H.n_groups;
+    I.n_groups_multi = n_groups_multi;
+    I.state_words = W32 / 2;
+    I.n_sel_blocks = H.n_sel;
+    I.m_lower_bound = pp.m_lower;
+    I.m_found = pp.m_found;
+    I.sum_weights = pp.sum_w;
+    I.table_bytes = tables.size() * 4;
+    I.image_bytes = H.image_bytes;
+    I.stage_bytes = H.stage_bytes;
+    I.tables_in_smem = H.tables_in_smem;
+    I.total_inputs = (uint32_t)total_inputs;
+    return PBN_OK;
+}
+
+}  // namespace
+
+extern "C" void pbn_group_params_default(pbn_group_params* prm) {
+    if (!prm) return;
+    memset(prm, 0, sizeof(*prm));
+    prm->mode = PBN_PLAN_GROUPED;
+    prm->max_inputs = 8;
+    prm->max_width = 32;
+    prm->theta = 65536.0;
+    prm->smem_budget = 160 * 1024;
+}
+
+extern "C" int pbn_group(const pbn_net* net, const pbn_group_params* prm_in, pbn_plan** out) {
+    if (!net || !out) return fail(PBN_EINVAL, "pbn_group: NULL argument");
+    *out = nullptr;
+    pbn_group_params prm;
+    pbn_group_params_default(&prm);
+    if (prm_in) prm = *prm_in;
+    if (prm.mode != PBN_PLAN_GROUPED && prm.mode != PBN_PLAN_PLAIN)
+        return fail(PBN_EINVAL, "pbn_group: unknown mode %u", prm.mode);
+    if (prm.max_inputs < 1 || prm.max_inputs > 24 || prm.max_width < 1 || prm.max_width > 32 ||
+        !(prm.theta >= 1.0) || (prm.smem_budget && prm.smem_budget < 1024))
+        return fail(PBN_EINVAL, "pbn_group: parameter out of range");
+    try {
+        pbn_plan* plan = new pbn_plan();
+        int rc = build_plan(*net, prm, plan);
+        if (rc) { delete plan; return rc; }
+        *out = plan;
+        return PBN_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(PBN_ENOMEM, "pbn_group: out of memory");
+    }
+}
+
+extern "C" void pbn_plan_free(pbn_plan* plan) { delete plan; }
+
+extern "C" int pbn_plan_info_get(const pbn_plan* plan, pbn_plan_info* out) {
+    if (!plan || !out) return fail(PBN_EINVAL, "pbn_plan_info_get: NULL argument");
+    *out = plan->info;
+    return PBN_OK;
+}
+
+extern "C" int pbn_plan_image(const pbn_plan* plan, void* dst, size_t cap) {
+    if (!plan || !dst) return fail(PBN_EINVAL, "pbn_plan_image: NULL argument");
+    if (cap < plan->image.size()) return fail(PBN_EINVAL, "pbn_plan_image: need %zu bytes", plan->image.size());
+    memcpy(dst, plan->image.data(), plan->image.size());
+    return PBN_OK;
+}
+
+extern "C" int pbn_plan_layout(const pbn_plan* plan, uint32_t* pos) {
+    if (!plan || !pos) return fail(PBN_EINVAL, "pbn_plan_layout: NULL argument");
+    memcpy(pos, plan->pos.data(), plan->pos.size() * 4);
+    return PBN_OK;
+}
+
+extern "C" int pbn_plan_groups(const pbn_plan* plan, uint32_t* group_of) {
+    if (!plan || !group_of) return fail(PBN_EINVAL, "pbn_plan_groups: NULL argument");
+    memcpy(group_of, plan->group_of.data(), plan->group_of.size() * 4);
+    return PBN_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Two-state Markov chain estimate (Sec. 4.2)                                 */
+/* ------------------------------------------------------------------------- */
+namespace {
+/* Standard normal quantile: bisection on Phi(x) = erfc(-x / sqrt 2) / 2 to bracket
+ * the root, then Newton steps with the normal density. */
+double norm_quantile(double prob) {
+    double lo = -40.0, hi = 40.0;
+    auto Phi = [](double x) { return 0.5 * std::erfc(-x / std::sqrt(2.0)); };
+    for (int it = 0; it < 80; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (Phi(mid) < prob) lo = mid; else hi = mid;
+    }
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 3; ++it) {
+        double pdf = std::exp(-0.5 * x * x) / std::sqrt(2.0 * M_PI);
+        if (pdf <= 0.0) break;
+        x -= (Phi(x) - prob) / pdf;
+    }
+    return x;
+}
+}  // namespace
+
+extern "C" int pbn_estimate(const uint64_t counts[5], uint64_t n_traj, uint64_t burn_in_used, double r,
+                            double s, double eps, pbn_estimate_out* out) {
+    if (!counts || !out || !(r > 0.0) || !(s > 0.0 && s < 1.0) || !(eps > 0.0) || n_traj == 0)
+        return fail(PBN_EINVAL, "pbn_estimate: argument out of range");
+    const uint64_t V = counts[0], n00 = counts[1], n01 = counts[2], n10 = counts[3], n11 = counts[4];
+    pbn_estimate_out o;
+    memset(&o, 0, sizeof(o));
+    o.L = n00 + n01 + n10 + n11 + n_traj;
+    o.alpha = (n00 + n01) ? (double)n01 / (double)(n00 + n01) : NAN;
+    o.beta = (n10 + n11) ? (double)n10 / (double)(n10 + n11) : NAN;
+    o.pi = (double)V / (double)o.L;
+    o.z = norm_quantile((1.0 + s) / 2.0);
+    o.m_star = UINT64_MAX;
+    o.n_star = UINT64_MAX;
+    o.var = NAN;
+    o.n_star_real = NAN;
+    const double a = o.alpha, b = o.beta;
+    if (!std::isnan(a) && !std::isnan(b) && a + b > 0.0) {
+        o.defined = (a > 0.0 && b > 0.0) ? 1 : 0;
+        const double lam = std::fabs(1.0 - a - b);
+        if (lam == 0.0) {
+            o.m_star = 1;
+        } else if (lam < 1.0) {
+            double m = std::ceil(std::log(eps * (a + b) / std::max(a, b)) / std::log(lam));
+            o.m_star = m < 1.0 ? 1 : (uint64_t)m;
+        }
+        const double ab = a * b * (2.0 - a - b) / ((a + b) * (a + b) * (a + b));
+        o.n_star_real = ab * (o.z / r) * (o.z / r);
+        o.n_star = (uint64_t)std::ceil(o.n_star_real);
+        o.var = ab / (double)o.L;
+    }
+    o.done = (o.defined && o.m_star != UINT64_MAX && o.L >= o.n_star && burn_in_used >= o.m_star) ? 1 : 0;
+    *out = o;
+    return PBN_OK;
+}

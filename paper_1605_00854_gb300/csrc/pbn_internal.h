@@ -1,0 +1,42 @@
+/* pbn_internal.h -- host-side model and plan objects shared by the library's
+ * C++ preparation code and its CUDA launch code. */
+#ifndef PBN_INTERNAL_H
+#define PBN_INTERNAL_H
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "pbn.h"
+#include "pbn_image.h"
+
+struct pbn_fun {
+    double c = 0.0;                 /* selection probability */
+    std::vector<uint32_t> par;      /* parents a_0..a_{k-1} */
+    std::vector<uint64_t> tt;       /* 2^k output bits, bit x in word x / 64 */
+    bool bit(uint64_t x) const { return (tt[x >> 6] >> (x & 63)) & 1u; }
+};
+
+struct pbn_net {
+    uint32_t n = 0;
+    double p = 0.0;
+    std::vector<std::vector<pbn_fun>> node;   /* node[i][j] = f_{j+1}^{(i)} */
+    std::vector<uint8_t> retained;             /* 1 = simulated */
+    std::vector<uint32_t> interest;            /* nodes of interest given to pbn_reduce */
+};
+
+struct pbn_plan {
+    pbn_plan_info info{};
+    pbn_img_header hdr{};
+    std::vector<uint8_t> image;      /* device image, 16-byte padded */
+    std::vector<uint32_t> pos;       /* per original node: 32 * row + bit, or UINT32_MAX */
+    std::vector<uint32_t> group_of;  /* per original node: group index, or UINT32_MAX */
+    uint32_t per_traj_smem = 0;      /* shared-memory bytes per trajectory slot */
+};
+
+namespace pbn {
+int fail(int code, const char* fmt, ...);
+uint64_t pert_threshold(double p);
+}  // namespace pbn
+
+#endif

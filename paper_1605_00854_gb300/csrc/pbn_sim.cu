@@ -1,0 +1,594 @@
+/*
+ * pbn_sim.cu -- sm_103a kernel of the structure-based PBN simulation
+ * (Algorithm 5, ParallelSimulation, with the step semantics of Eq. 1).
+ *
+ * One trajectory is handled by LG lanes of a warp (a lane group).  Per CTA:
+ *   - the plan image (group specs, thresholds, maps and, when they fit, the merged
+ *     tables) is bulk-copied global -> shared by one thread with cp.async.bulk,
+ *     completion tracked by an mbarrier (bounded wait);
+ *   - the grouped state of each trajectory lives in shared memory as 32-bit rows
+ *     S[buf][row][slot] (double buffered), so that all lanes of a warp reading the
+ *     same row touch consecutive banks.
+ * Per step t and trajectory (Philox4x32-10 keyed by (seed, trajectory, t)):
+ *   1. perturbation (Sec. 3.2, Step 2): every original 64-node word draws its
+ *      Bernoulli(P / 2^32) lanes bit-sliced, most significant level first, and
+ *      stops once every lane is decided.  Any set lane means a perturbed step
+ *      (leaves included, which replaces Algorithm 1's single draw); the set lanes
+ *      of retained nodes are flipped in the grouped state.
+ *   2. otherwise (Sec. 3.3, Step 3): the SEL blocks of the retained multi-function
+ *      nodes are drawn into shared memory; for every group the combined choice c
+ *      (mixed radix over its multi-function nodes), the input pattern x and the
+ *      table entry T[c][x] give the group's new bits, ORed into the next state at
+ *      the group's offset (cum in Algorithm 5).
+ *   3. the meta-state indicator z of the new state updates the per-trajectory
+ *      counts V, n01, n10, n11 of the two-state chain (Sec. 4.2).
+ * Perturbed steps only flip bits; they never evaluate predictor functions (Eq. 1).
+ */
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "pbn_internal.h"
+
+namespace {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kWeyl0 = 0x9E3779B9u;
+constexpr uint32_t kWeyl1 = 0xBB67AE85u;
+constexpr uint32_t kDomPert = 1u, kDomSel = 2u, kDomInit = 3u;
+constexpr int kMaxMetaRows = 16;
+constexpr uint32_t kStageWaitLimit = 1u << 22;
+
+struct SimParams {
+    const uint8_t* image;      /* device copy of the plan image */
+    uint64_t* state;           /* [W64][n_traj] */
+    uint64_t* counts;          /* [5][n_traj] or null */
+    unsigned long long* pooled;/* [5] or null */
+    uint32_t* status;          /* or null */
+    uint64_t* trace;           /* [n_steps][W64][n_traj] or null */
+    uint64_t traj_begin;
+    uint64_t step_begin;
+    uint32_t key0[10];         /* Philox key schedule, round r: seed + r * Weyl */
+    uint32_t key1[10];
+    uint32_t n_traj;
+    uint32_t n_steps;
+    uint32_t kv0;              /* first step whose resulting state is counted */
+    uint32_t kp0;              /* first step whose (before, after) pair is counted */
+    uint32_t pairs;            /* counted pairs of this launch (n00 = pairs - others) */
+    uint32_t count_first;      /* 1: s(step_begin) itself is counted */
+    uint32_t init;             /* 0: keyed s(0), 1: read state */
+    uint32_t nt;               /* trajectory slots per CTA */
+    uint32_t stage_bytes;      /* image bytes staged into shared memory */
+    uint32_t image_bytes;      /* total image bytes (checked against the header) */
+    uint32_t smem_state_off;   /* byte offset of the state rows in dynamic smem */
+    uint32_t n, W, W32, n_sel, P;
+    uint32_t off_words, off_groups, off_multi, off_thr, off_inputs, off_selblk, off_ret, off_pos, off_tables;
+    uint32_t n_meta_rows;
+    uint32_t meta_row[kMaxMetaRows];
+    uint32_t meta_mask[kMaxMetaRows];
+    uint32_t meta_val[kMaxMetaRows];
+};
+
+/* ---- Philox4x32-10 ------------------------------------------------------------
+ * Round: (x0, x1, x2, x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1,
+ * lo(M0 x0)); the key is bumped by the Weyl constants between rounds.  Within one
+ * (trajectory, step) the counter words c0, c1, c2 are fixed and only c3 (domain,
+ * index) changes, and c3 enters round 1 only through an XOR, so round 1's products
+ * are computed once per step. */
+struct PhiloxStep {
+    uint32_t y0, y1, y2_base, y3;
+};
+
+__device__ __forceinline__ PhiloxStep philox_step(const SimParams& P, uint64_t traj, uint64_t t) {
+    const uint32_t c0 = (uint32_t)traj;
+    const uint32_t c1 = (uint32_t)t;
+    const uint32_t c2 = (uint32_t)((t >> 32) & 0xFFFFu) | ((uint32_t)((traj >> 32) & 0xFFFFu) << 16);
+    PhiloxStep s;
+    s.y0 = __umulhi(kPhiloxM1, c2) ^ c1 ^ P.key0[0];
+    s.y1 = kPhiloxM1 * c2;
+    s.y2_base = __umulhi(kPhiloxM0, c0) ^ P.key1[0];
+    s.y3 = kPhiloxM0 * c0;
+    return s;
+}
+
+__device__ __forceinline__ uint4 philox_draw(const SimParams& P, const PhiloxStep& s, uint32_t c3) {
+    uint32_t x0 = s.y0, x1 = s.y1, x2 = s.y2_base ^ c3, x3 = s.y3;
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const uint32_t h0 = __umulhi(kPhiloxM0, x0), l0 = kPhiloxM0 * x0;
+        const uint32_t h1 = __umulhi(kPhiloxM1, x2), l1 = kPhiloxM1 * x2;
+        x0 = h1 ^ x1 ^ P.key0[r];
+        x2 = h0 ^ x3 ^ P.key1[r];
+        x1 = l1;
+        x3 = l0;
+    }
+    return make_uint4(x0, x1, x2, x3);
+}
+
+/* ---- mbarrier + bulk copy (global -> shared), inline PTX ------------------------ */
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+/* Bounded wait for phase 0 of the staging barrier. */
+__device__ __forceinline__ bool stage_wait(uint64_t* bar) {
+    for (uint32_t it = 0; it < kStageWaitLimit; ++it) {
+        if (mbar_try_wait(bar, 0)) return true;
+        if (it > 64) __nanosleep(128);
+    }
+    return false;
+}
+
+template <int LG>
+__device__ __forceinline__ uint32_t group_mask() {
+    if (LG == 32) return 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    return ((1u << LG) - 1u) << (lane & ~(uint32_t)(LG - 1));
+}
+
+template <int LG>
+__device__ __forceinline__ void group_sync() {
+    if (LG > 1) __syncwarp(group_mask<LG>());
+}
+
+template <int LG>
+__device__ __forceinline__ void xor_bit(uint32_t* w, uint32_t bit) {
+    if (LG == 1) *w ^= bit;
+    else atomicXor(w, bit);
+}
+
+template <int LG>
+__device__ __forceinline__ void or_bit(uint32_t* w, uint32_t bit) {
+    if (LG == 1) *w |= bit;
+    else atomicOr(w, bit);
+}
+
+template <int LG, bool TRACE, bool TAB_SMEM>
+__global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t stage_bar;
+
+    /* ---- stage the plan image into shared memory (bulk copy, bounded wait) ---- */
+    if (threadIdx.x == 0) mbar_init(&stage_bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&stage_bar, P.stage_bytes);
+        for (uint32_t off = 0; off < P.stage_bytes; off += 65536u) {
+            const uint32_t sz = min(65536u, P.stage_bytes - off);
+            bulk_copy_g2s(smem + off, P.image + off, sz, &stage_bar);
+        }
+    }
+    const bool staged = stage_wait(&stage_bar);
+    if (__syncthreads_or(!staged)) {
+        if (threadIdx.x == 0 && P.status) atomicOr(P.status, PBN_DEV_STAGE_TIMEOUT);
+        stage_wait(&stage_bar); /* let copies in flight land before the CTA exits */
+        return;
+    }
+    const pbn_img_header* hdr = reinterpret_cast<const pbn_img_header*>(smem);
+    if (hdr->magic != PBN_IMG_MAGIC || hdr->image_bytes != P.image_bytes || hdr->n != P.n ||
+        hdr->W32 != P.W32 || hdr->n_sel != P.n_sel || hdr->off_tables != P.off_tables) {
+        if (threadIdx.x == 0 && P.status) atomicOr(P.status, PBN_DEV_BAD_PLAN);
+        return;
+    }
+
+    const uint2* WORDS = reinterpret_cast<const uint2*>(smem + P.off_words);
+    const pbn_img_group* GROUPS = reinterpret_cast<const pbn_img_group*>(smem + P.off_groups);
+    const pbn_img_multi* MULTI = reinterpret_cast<const pbn_img_multi*>(smem + P.off_multi);
+    const uint32_t* THR = reinterpret_cast<const uint32_t*>(smem + P.off_thr);
+    const uint32_t* INPUTS = reinterpret_cast<const uint32_t*>(smem + P.off_inputs);
+    const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(smem + P.off_selblk);
+    const uint64_t* RET = reinterpret_cast<const uint64_t*>(smem + P.off_ret);
+    const uint32_t* POS = reinterpret_cast<const uint32_t*>(smem + P.off_pos);
+    const uint32_t* TAB = TAB_SMEM ? reinterpret_cast<const uint32_t*>(smem + P.off_tables)
+                                   : reinterpret_cast<const uint32_t*>(P.image + P.off_tables);
+
+    const uint32_t NT = P.nt;
+    const uint32_t W32 = P.W32;
+    uint32_t* SROWS = reinterpret_cast<uint32_t*>(smem + P.smem_state_off); /* [2][W32][NT] */
+    uint32_t* UROWS = SROWS + 2 * W32 * NT;                                  /* [4 n_sel][NT] */
+
+    const uint32_t slot = threadIdx.x / LG;
+    const uint32_t lane = LG == 1 ? 0u : (threadIdx.x % LG);
+    const uint64_t lt = (uint64_t)blockIdx.x * NT + slot;
+    const bool active = lt < P.n_traj;
+    const uint64_t traj = P.traj_begin + lt;
+
+    uint32_t* const S0 = SROWS + slot;      /* buffer b at S0 + b * bufstride */
+    const uint32_t bufstride = W32 * NT;
+    uint32_t* U = UROWS + slot;
+    uint32_t cur = 0;
+
+    uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;
+
+    if (active) {
+        /* ---- initial state ---- */
+        if (P.init == 0) {
+            for (uint32_t r = lane; r < W32; r += LG) S0[r * NT] = 0u;
+            group_sync<LG>();
+            const PhiloxStep ps = philox_step(P, traj, 0);
+            for (uint32_t w = lane; w < P.W; w += LG) {
+                const uint4 x = philox_draw(P, ps, (kDomInit << 28) | (w >> 1));
+                uint64_t word = (w & 1u) ? (((uint64_t)x.w << 32) | x.z) : (((uint64_t)x.y << 32) | x.x);
+                word &= RET[w];
+                while (word) {
+                    const uint32_t b = __ffsll((long long)word) - 1;
+                    word &= word - 1;
+                    const uint32_t ps_ = POS[64 * w + b];
+                    or_bit<LG>(&S0[(ps_ >> 5) * NT], 1u << (ps_ & 31));
+                }
+            }
+        } else {
+            for (uint32_t r = lane; r < W32; r += LG) {
+                const uint64_t v = P.state[(uint64_t)(r >> 1) * P.n_traj + lt];
+                S0[r * NT] = (r & 1u) ? (uint32_t)(v >> 32) : (uint32_t)v;
+            }
+        }
+        group_sync<LG>();
+
+        /* meta-state indicator of a state buffer (read by lane 0 of the group) */
+        auto meta_z = [&](const uint32_t* Sb) -> uint32_t {
+            uint32_t ok = 1u;
+            for (uint32_t m = 0; m < P.n_meta_rows; ++m)
+                ok &= ((Sb[P.meta_row[m] * NT] & P.meta_mask[m]) == P.meta_val[m]) ? 1u : 0u;
+            return ok;
+        };
+        uint32_t zp = meta_z(S0);
+        if (P.count_first) cV += zp;
+
+        const uint64_t last_lanes = (P.n & 63u) ? ((1ull << (P.n & 63u)) - 1ull) : ~0ull;
+
+        for (uint32_t k = 0; k < P.n_steps; ++k) {
+            const uint64_t t = P.step_begin + k;
+            const PhiloxStep ps = philox_step(P, traj, t);
+            uint32_t* Sc = S0 + cur * bufstride;
+
+            /* ---- 1. perturbation: bit-sliced u < P with early exit ---- */
+            uint32_t any_l = 0;
+            if (P.P != 0u) {
+                for (uint32_t w = lane; w < P.W; w += LG) {
+                    uint64_t und = (w == P.W - 1) ? last_lanes : ~0ull;
+                    uint64_t pert = 0;
+                    for (uint32_t h = 0; h < 16u && und; ++h) {
+                        const uint4 x = philox_draw(P, ps, (kDomPert << 28) | (w << 4) | h);
+                        const uint64_t L0 = ((uint64_t)x.y << 32) | x.x;
+                        const uint64_t L1 = ((uint64_t)x.w << 32) | x.z;
+                        const uint64_t m0 = ((P.P >> (31u - 2u * h)) & 1u) ? ~0ull : 0ull;
+                        const uint64_t m1 = ((P.P >> (30u - 2u * h)) & 1u) ? ~0ull : 0ull;
+                        pert |= und & ~L0 & m0;
+                        und &= ~(L0 ^ m0);
+                        pert |= und & ~L1 & m1;
+                        und &= ~(L1 ^ m1);
+                    }
+                    if (pert) {
+                        any_l = 1u;
+                        uint64_t f = pert & RET[w];
+                        while (f) {
+                            const uint32_t b = __ffsll((long long)f) - 1;
+                            f &= f - 1;
+                            const uint32_t ps_ = POS[64 * w + b];
+                            xor_bit<LG>(&Sc[(ps_ >> 5) * NT], 1u << (ps_ & 31));
+                        }
+                    }
+                }
+            }
+            uint32_t any = any_l;
+            if (LG > 1) {
+                group_sync<LG>();
+                any = (__ballot_sync(group_mask<LG>(), any_l) & group_mask<LG>()) ? 1u : 0u;
+            }
+
+            if (!any) {
+                /* ---- 2a. selection draws of the retained multi-function nodes ---- */
+                for (uint32_t i = lane; i < P.n_sel; i += LG) {
+                    const uint4 x = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
+                    U[(4 * i + 0) * NT] = x.x;
+                    U[(4 * i + 1) * NT] = x.y;
+                    U[(4 * i + 2) * NT] = x.z;
+                    U[(4 * i + 3) * NT] = x.w;
+                }
+                group_sync<LG>();
+                /* ---- 2b. merged-table evaluation, word by word ---- */
+                uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
+                for (uint32_t w = lane; w < W32; w += LG) {
+                    const uint2 wr = WORDS[w];
+                    uint32_t acc = 0;
+                    for (uint32_t gi = wr.x; gi < wr.x + wr.y; ++gi) {
+                        const pbn_img_group G = GROUPS[gi];
+                        uint32_t c = 0;
+                        for (uint32_t m = 0; m < G.n_mul; ++m) {
+                            const pbn_img_multi M = MULTI[G.mul_first + m];
+                            const uint32_t u = U[M.u_slot * NT];
+                            uint32_t j = 0;
+                            for (uint32_t q = 0; q < M.n_thr; ++q) j += (u >= THR[M.thr_first + q]) ? 1u : 0u;
+                            c += j * M.radix;
+                        }
+                        uint32_t x = 0;
+                        const uint32_t* in = INPUTS + G.in_first;
+                        for (uint32_t b = 0; b < G.q; ++b) {
+                            const uint32_t rec = in[b];
+                            const uint32_t v = Sc[(rec >> 5) * NT];
+                            x |= __funnelshift_r(v, v, rec) & (1u << b);
+                        }
+                        const uint32_t bo = ((c << G.q) | x) << G.l2w;
+                        const uint32_t tw = TAB_SMEM ? TAB[G.tab_off + (bo >> 5)] : __ldg(TAB + G.tab_off + (bo >> 5));
+                        const uint32_t ebits = 1u << G.l2w;
+                        const uint32_t emask = (2u << (ebits - 1u)) - 1u;
+                        acc |= ((tw >> (bo & 31u)) & emask) << G.shift;
+                    }
+                    Sn[w * NT] = acc;
+                }
+                group_sync<LG>();
+                cur ^= 1u;
+            }
+
+            /* ---- 3. meta-state counts ---- */
+            if (lane == 0) {
+                const uint32_t z = meta_z(S0 + cur * bufstride);
+                const uint32_t cv = k >= P.kv0 ? 1u : 0u;
+                const uint32_t cp = k >= P.kp0 ? 1u : 0u;
+                cV += cv & z;
+                c11 += cp & zp & z;
+                c01 += cp & (zp ^ 1u) & z;
+                c10 += cp & zp & (z ^ 1u);
+                zp = z;
+                if (TRACE) {
+                    const uint32_t* Sb = S0 + cur * bufstride;
+                    for (uint32_t r = 0; r < W32; r += 2) {
+                        const uint64_t v = ((uint64_t)Sb[(r + 1) * NT] << 32) | Sb[r * NT];
+                        P.trace[((uint64_t)k * (W32 / 2) + r / 2) * P.n_traj + lt] = v;
+                    }
+                }
+            }
+            group_sync<LG>();
+        }
+
+        /* ---- epilogue: state and counts ---- */
+        const uint32_t* Sb = S0 + cur * bufstride;
+        for (uint32_t r = lane * 2; r < W32; r += 2 * LG) {
+            const uint64_t v = ((uint64_t)Sb[(r + 1) * NT] << 32) | Sb[r * NT];
+            P.state[(uint64_t)(r >> 1) * P.n_traj + lt] = v;
+        }
+        if (lane == 0 && P.counts) {
+            const uint32_t c00 = P.pairs - c01 - c10 - c11;
+            const uint64_t nt = P.n_traj;
+            P.counts[0 * nt + lt] += cV;
+            P.counts[1 * nt + lt] += c00;
+            P.counts[2 * nt + lt] += c01;
+            P.counts[3 * nt + lt] += c10;
+            P.counts[4 * nt + lt] += c11;
+        }
+    }
+
+    /* ---- pooled counts: warp reduction, one atomic per warp and count ---- */
+    if (P.pooled) {
+        const bool lead = active && lane == 0;
+        uint64_t v[5] = {lead ? cV : 0u, lead ? (uint64_t)(P.pairs - c01 - c10 - c11) : 0u,
+                         lead ? c01 : 0u, lead ? c10 : 0u, lead ? c11 : 0u};
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], o);
+        }
+        if ((threadIdx.x & 31u) == 0) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (v[i]) atomicAdd(P.pooled + i, (unsigned long long)v[i]);
+        }
+    }
+}
+
+template <int LG, bool TRACE, bool TAB_SMEM>
+cudaError_t launch_t(const SimParams& P, uint32_t grid, uint32_t tpb, size_t smem, cudaStream_t st) {
+    auto kern = pbn_sim_kernel<LG, TRACE, TAB_SMEM>;
+    static size_t configured = 48 * 1024;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    kern<<<grid, tpb, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int LG>
+cudaError_t launch_lg(const SimParams& P, bool trace, bool tab_smem, uint32_t grid, uint32_t tpb, size_t smem,
+                      cudaStream_t st) {
+    if (trace) return tab_smem ? launch_t<LG, true, true>(P, grid, tpb, smem, st)
+                               : launch_t<LG, true, false>(P, grid, tpb, smem, st);
+    return tab_smem ? launch_t<LG, false, true>(P, grid, tpb, smem, st)
+                    : launch_t<LG, false, false>(P, grid, tpb, smem, st);
+}
+
+int device_smem_limit() {
+    static int lim = 0;
+    if (!lim) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || lim <= 0)
+            lim = 48 * 1024;
+    }
+    return lim;
+}
+
+int device_sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace
+
+extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn_sim_args* a, void* stream) {
+    using pbn::fail;
+    if (!plan || !a) return fail(PBN_EINVAL, "pbn_simulate: NULL argument");
+    if (a->n_traj == 0) return PBN_OK;
+    if (!d_image || ((uintptr_t)d_image & 15u)) return fail(PBN_EINVAL, "pbn_simulate: d_image must be 16-byte aligned device memory");
+    if (!a->d_state) return fail(PBN_EINVAL, "pbn_simulate: d_state is required");
+    if (a->n_traj >= (1ull << 31)) return fail(PBN_EINVAL, "pbn_simulate: n_traj must be < 2^31");
+    if (a->n_steps >= (1ull << 32)) return fail(PBN_EINVAL, "pbn_simulate: n_steps must be < 2^32");
+    if (a->traj_begin + a->n_traj > (1ull << 48)) return fail(PBN_EINVAL, "pbn_simulate: trajectory ids must be < 2^48");
+    if (a->step_begin + a->n_steps > (1ull << 48)) return fail(PBN_EINVAL, "pbn_simulate: step indices must be < 2^48");
+    if (a->init != PBN_INIT_KEYED && a->init != PBN_INIT_STATE) return fail(PBN_EINVAL, "pbn_simulate: bad init mode");
+    if (a->init == PBN_INIT_KEYED && a->step_begin != 0) return fail(PBN_EINVAL, "pbn_simulate: keyed initial state needs step_begin == 0");
+    if (a->n_meta < 1 || a->n_meta > 1024 || !a->meta_ids) return fail(PBN_EINVAL, "pbn_simulate: need 1..1024 meta-state nodes");
+    if (a->d_trace && a->n_steps * (uint64_t)plan->info.state_words * a->n_traj >= (1ull << 40))
+        return fail(PBN_EINVAL, "pbn_simulate: trace too large");
+
+    const pbn_img_header& H = plan->hdr;
+    SimParams P;
+    memset(&P, 0, sizeof(P));
+    /* meta-state: mask and value per state row */
+    for (uint32_t m = 0; m < a->n_meta; ++m) {
+        const uint32_t id = a->meta_ids[m];
+        if (id >= H.n || plan->pos[id] == UINT32_MAX)
+            return fail(PBN_EINVAL, "pbn_simulate: meta node %u is not a retained node", id);
+        const uint32_t row = plan->pos[id] >> 5, bit = plan->pos[id] & 31u;
+        const uint32_t val = a->meta_vals ? (a->meta_vals[m] ? 1u : 0u) : 1u;
+        uint32_t k = 0;
+        while (k < P.n_meta_rows && P.meta_row[k] != row) ++k;
+        if (k == P.n_meta_rows) {
+            if (k == kMaxMetaRows) return fail(PBN_EINVAL, "pbn_simulate: meta nodes span more than %d state words", kMaxMetaRows);
+            P.meta_row[k] = row;
+            P.n_meta_rows++;
+        }
+        if ((P.meta_mask[k] >> bit) & 1u) {
+            if (((P.meta_val[k] >> bit) & 1u) != val) return fail(PBN_EINVAL, "pbn_simulate: contradictory meta values");
+        }
+        P.meta_mask[k] |= 1u << bit;
+        P.meta_val[k] |= val << bit;
+    }
+
+    P.image = static_cast<const uint8_t*>(d_image);
+    P.state = static_cast<uint64_t*>(a->d_state);
+    P.counts = static_cast<uint64_t*>(a->d_counts);
+    P.pooled = static_cast<unsigned long long*>(a->d_pooled);
+    P.status = static_cast<uint32_t*>(a->d_status);
+    P.trace = static_cast<uint64_t*>(a->d_trace);
+    P.traj_begin = a->traj_begin;
+    P.step_begin = a->step_begin;
+    const uint32_t k0 = (uint32_t)a->seed, k1 = (uint32_t)(a->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        P.key0[r] = k0 + (uint32_t)r * kWeyl0;
+        P.key1[r] = k1 + (uint32_t)r * kWeyl1;
+    }
+    P.n_traj = (uint32_t)a->n_traj;
+    P.n_steps = (uint32_t)a->n_steps;
+    /* counting window: state s(u) counted iff u >= count_from; pair (s(t), s(t+1))
+     * counted iff t >= count_from */
+    const uint64_t sb = a->step_begin, cf = a->count_from, ns = a->n_steps;
+    const uint64_t kv0 = cf > sb + 1 ? cf - sb - 1 : 0;
+    const uint64_t kp0 = cf > sb ? cf - sb : 0;
+    P.kv0 = (uint32_t)(kv0 < ns ? kv0 : ns);
+    P.kp0 = (uint32_t)(kp0 < ns ? kp0 : ns);
+    P.pairs = (uint32_t)(ns - P.kp0);
+    P.count_first = sb == cf ? 1u : 0u;
+    P.init = a->init;
+    P.n = H.n;
+    P.W = H.W;
+    P.W32 = H.W32;
+    P.n_sel = H.n_sel;
+    P.P = H.P;
+    P.off_words = H.off_words;
+    P.off_groups = H.off_groups;
+    P.off_multi = H.off_multi;
+    P.off_thr = H.off_thr;
+    P.off_inputs = H.off_inputs;
+    P.off_selblk = H.off_selblk;
+    P.off_ret = H.off_ret;
+    P.off_pos = H.off_pos;
+    P.off_tables = H.off_tables;
+    P.stage_bytes = H.stage_bytes;
+    P.image_bytes = H.image_bytes;
+    P.smem_state_off = (H.stage_bytes + 127u) & ~127u;
+
+    /* launch shape: lanes per trajectory and trajectory slots per CTA */
+    const int sms = device_sm_count();
+    const size_t smem_lim = (size_t)device_smem_limit();
+    uint32_t LG = a->lanes_per_traj;
+    if (LG == 0) {
+        LG = 1;
+        /* aim for >= 16 resident warps per SM when there are few trajectories */
+        while (LG < 8 && a->n_traj * LG < (uint64_t)sms * 512 && LG * 2 <= H.W32) LG *= 2;
+    }
+    if (LG != 1 && LG != 2 && LG != 4 && LG != 8) return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4 or 8");
+    const size_t per_traj = plan->per_traj_smem;
+    const size_t fixed = P.smem_state_off;
+    if (fixed + per_traj * (32 / LG) > smem_lim)
+        return fail(PBN_ETOOBIG, "pbn_simulate: plan needs %zu bytes of shared memory for one warp", fixed + per_traj * (32 / LG));
+    uint32_t nt = a->trajs_per_block;
+    if (nt == 0) {
+        /* k CTAs per SM, trajectories spread evenly: the grid is close to a multiple
+         * of the SM count, with at most 512 threads per CTA */
+        const uint32_t unit = 32 / LG; /* trajectories per warp */
+        for (uint64_t k = 1;; ++k) {
+            uint64_t want = (a->n_traj + (uint64_t)sms * k - 1) / ((uint64_t)sms * k);
+            want = ((want + unit - 1) / unit) * unit;
+            if (want * LG <= 512 && fixed + per_traj * want <= smem_lim) {
+                nt = (uint32_t)want;
+                break;
+            }
+            if (want <= unit) {
+                nt = unit;
+                break;
+            }
+        }
+    }
+    if ((nt * LG) % 32 != 0 || nt * LG > 512 || nt == 0)
+        return fail(PBN_EINVAL, "pbn_simulate: trajs_per_block * lanes_per_traj must be a multiple of 32 and <= 512");
+    const size_t smem = fixed + per_traj * nt;
+    if (smem > smem_lim) return fail(PBN_ETOOBIG, "pbn_simulate: %zu bytes of shared memory exceed the device limit", smem);
+    P.nt = nt;
+    const uint64_t grid = (a->n_traj + nt - 1) / nt;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    const bool tr = a->d_trace != nullptr;
+    const bool ts = H.tables_in_smem != 0;
+    switch (LG) {
+        case 1: e = launch_lg<1>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+        case 2: e = launch_lg<2>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+        case 4: e = launch_lg<4>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+        default: e = launch_lg<8>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+    }
+    if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_simulate: %s", cudaGetErrorString(e));
+    return PBN_OK;
+}

@@ -1,0 +1,48 @@
+"""Test helper: decode a plan's device image (layout of csrc/pbn_image.h) in Python."""
+import struct
+
+import numpy as np
+
+HEADER_FIELDS = ["magic", "n", "W", "W32", "n_groups", "n_multi", "n_sel", "P",
+                 "off_words", "off_groups", "off_multi", "off_thr", "off_inputs",
+                 "off_selblk", "off_ret", "off_pos", "off_tables", "image_bytes",
+                 "stage_bytes", "tables_in_smem"]
+
+
+def decode(img: np.ndarray) -> dict:
+    b = img.tobytes()
+    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<20I", b, 0)))
+    u32 = np.frombuffer(b, dtype=np.uint32)
+    words = u32[H["off_words"] // 4: H["off_words"] // 4 + 2 * H["W32"]].reshape(-1, 2)
+    groups = []
+    for g in range(H["n_groups"]):
+        tab_off, in_first, mul_first, q, l2w, n_mul, shift = struct.unpack_from(
+            "<3I4B", b, H["off_groups"] + 16 * g)
+        groups.append(dict(tab_off=tab_off, in_first=in_first, mul_first=mul_first, q=q, l2w=l2w,
+                           n_mul=n_mul, shift=shift))
+    multi = [dict(zip(["u_slot", "radix", "thr_first", "n_thr"],
+                      struct.unpack_from("<4I", b, H["off_multi"] + 16 * m)))
+             for m in range(H["n_multi"])]
+    sel = u32[H["off_selblk"] // 4: H["off_selblk"] // 4 + H["n_sel"]]
+    pos = u32[H["off_pos"] // 4: H["off_pos"] // 4 + H["n"]]
+    ret = np.frombuffer(b, dtype=np.uint64)[H["off_ret"] // 8: H["off_ret"] // 8 + H["W"]]
+    return dict(H=H, u32=u32, words=words, groups=groups, multi=multi, sel=sel, pos=pos, ret=ret)
+
+
+def thresholds(D, m):
+    M = D["multi"][m]
+    o = D["H"]["off_thr"] // 4 + M["thr_first"]
+    return [int(v) for v in D["u32"][o: o + M["n_thr"]]]
+
+
+def inputs(D, g):
+    G = D["groups"][g]
+    o = D["H"]["off_inputs"] // 4 + G["in_first"]
+    return [int(v) for v in D["u32"][o: o + G["q"]]]
+
+
+def entry(D, g, e):
+    G = D["groups"][g]
+    bo = e << G["l2w"]
+    w = int(D["u32"][D["H"]["off_tables"] // 4 + G["tab_off"] + (bo >> 5)])
+    return (w >> (bo & 31)) & ((1 << (1 << G["l2w"])) - 1)

@@ -1,0 +1,171 @@
+"""Parity of the CUDA path with the CPU oracle: bit-exact states and counts.
+
+The oracle simulates the unreduced, ungrouped network by Eq. 1; the kernels run the
+reduced, grouped plan (or the plain one-node-per-group plan).  Because every draw is
+keyed by (trajectory, step, original node), every retained node's bit at every step
+and every meta-state count must agree exactly.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import plan_for, run
+from paper_1605_00854_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+NCPU = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _compare(gpu, orc, ids, trace=True):
+    assert gpu["status"] == 0
+    assert np.array_equal(gpu["final"][:, ids], orc["final"][:, ids])
+    assert np.array_equal(gpu["counts"], orc["counts"])
+    assert np.array_equal(gpu["pooled"], orc["counts"].sum(axis=0).astype(np.uint64))
+    if trace:
+        assert np.array_equal(gpu["trace"][:, :, ids], orc["trace"][:, :, ids])
+
+
+@pytest.mark.parametrize("mode,reduce", [(0, True), (1, False), (1, True), (0, False)])
+def test_tiny12_full_run_every_step(oracle_mod, mode, reduce):
+    """n = 12, 64 trajectories x 10^4 steps, meta = nodes 0,1,2 ON: every state of
+    every trajectory and every count equals the oracle's."""
+    text = synth.tiny12(1).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta, mode=mode, reduce=reduce)
+    orc = oracle_mod.simulate(text, 1, 0, 64, 10000, meta_ids=meta, trace=True, nthreads=NCPU)
+    gpu = run(plan, seed=1, n_traj=64, n_steps=10000, meta=meta, trace=True)
+    _compare(gpu, orc, ids)
+
+
+@pytest.mark.parametrize("lanes,tpb", [(1, 32), (1, 96), (2, 16), (2, 64), (4, 8), (4, 40), (8, 4), (8, 64), (0, 0)])
+def test_launch_shape_invariance(oracle_mod, lanes, tpb):
+    """Lanes per trajectory and trajectories per CTA change nothing (ragged last CTA)."""
+    net = synth.paper100(seed=2, p=2e-3)
+    text = net.to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta)
+    T, S = 333, 600
+    orc = oracle_mod.simulate(text, 77, 1000, T, S, meta_ids=meta, count_from=13, nthreads=NCPU)
+    gpu = run(plan, seed=77, traj_begin=1000, n_traj=T, n_steps=S, meta=meta, count_from=13,
+              lanes=lanes, tpb=tpb)
+    _compare(gpu, orc, ids, trace=False)
+
+
+def test_resume_in_chunks_and_split_ranges(oracle_mod):
+    """Chunked launches resumed from the device state, and disjoint trajectory ranges,
+    reproduce one oracle run (checkpoint / resume and sharding by trajectory id)."""
+    net = synth.paper100(seed=4, n=90, p=5e-3)
+    text = net.to_text()
+    meta = [0, 2]
+    plan, ids = plan_for(text, meta)
+    T, S = 200, 900
+    orc = oracle_mod.simulate(text, 5, 0, T, S, meta_ids=meta, count_from=250, trace=True, nthreads=NCPU)
+    a = run(plan, seed=5, n_traj=T, n_steps=S, meta=meta, count_from=250, chunks=[100, 150, 1, 649],
+            trace=True)
+    _compare(a, orc, ids)
+    lo = run(plan, seed=5, n_traj=120, n_steps=S, meta=meta, count_from=250)
+    hi = run(plan, seed=5, traj_begin=120, n_traj=80, n_steps=S, meta=meta, count_from=250)
+    assert np.array_equal(np.concatenate([lo["final"], hi["final"]])[:, ids], orc["final"][:, ids])
+    assert np.array_equal(np.concatenate([lo["counts"], hi["counts"]]), orc["counts"])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_paper100_against_oracle(oracle_mod, mode):
+    """Paper-scale network (n = 100, 25% sinks, p = 1e-4) grouped and plain."""
+    text = synth.paper100(seed=2).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta, mode=mode)
+    T, S = 384, 4000
+    orc = oracle_mod.simulate(text, 11, 0, T, S, meta_ids=meta, nthreads=NCPU)
+    gpu = run(plan, seed=11, n_traj=T, n_steps=S, meta=meta)
+    _compare(gpu, orc, ids, trace=False)
+
+
+def test_scalefree2000_against_oracle(oracle_mod):
+    """Large scale-free network (n = 2000, p = 1e-5, meta = 4 nodes)."""
+    text = synth.scalefree2000(seed=3).to_text()
+    meta = [0, 1, 2, 3]
+    plan, ids = plan_for(text, meta)
+    T, S = 64, 150
+    orc = oracle_mod.simulate(text, 3, 0, T, S, meta_ids=meta, trace=True, nthreads=NCPU)
+    gpu = run(plan, seed=3, n_traj=T, n_steps=S, meta=meta, trace=True)
+    _compare(gpu, orc, ids)
+
+
+def test_tables_in_global_memory(oracle_mod):
+    """A plan whose tables exceed the shared-memory budget reads them from global
+    memory and gives the same bits."""
+    text = synth.paper100(seed=6, p=1e-3).to_text()
+    meta = [1]
+    plan, ids = plan_for(text, meta, smem_budget=8192)
+    assert plan.info.tables_in_smem == 0
+    orc = oracle_mod.simulate(text, 8, 0, 256, 800, meta_ids=meta, nthreads=NCPU)
+    gpu = run(plan, seed=8, n_traj=256, n_steps=800, meta=meta)
+    _compare(gpu, orc, ids, trace=False)
+
+
+@pytest.mark.parametrize("p", [0.0, 0.05, 0.3, 0.75])
+def test_perturbation_regimes(oracle_mod, p):
+    """No perturbation, frequent, mostly and almost always perturbed steps."""
+    text = synth.paper100(seed=9, n=70, p=p).to_text()
+    meta = [0, 1]
+    plan, ids = plan_for(text, meta)
+    orc = oracle_mod.simulate(text, 2, 0, 96, 300, meta_ids=meta, trace=True, nthreads=NCPU)
+    gpu = run(plan, seed=2, n_traj=96, n_steps=300, meta=meta, trace=True)
+    _compare(gpu, orc, ids)
+
+
+def test_edge_cases(oracle_mod):
+    # one node, one trajectory
+    text = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n"
+    plan, ids = plan_for(text, [0])
+    orc = oracle_mod.simulate(text, 1, 0, 1, 500, meta_ids=[0], trace=True)
+    _compare(run(plan, seed=1, n_traj=1, n_steps=500, meta=[0], trace=True), orc, ids)
+    # zero steps: s(0) and the count of the first state only
+    text = synth.tiny12(3).to_text()
+    plan, ids = plan_for(text, [0, 1, 2])
+    orc = oracle_mod.simulate(text, 4, 0, 50, 0, meta_ids=[0, 1, 2])
+    _compare(run(plan, seed=4, n_traj=50, n_steps=0, meta=[0, 1, 2]), orc, ids, trace=False)
+    # counting window beyond the end; meta values 0/1 mixed
+    orc = oracle_mod.simulate(text, 4, 0, 50, 100, meta_ids=[0, 1, 2], meta_vals=[0, 1, 0],
+                              count_from=1000)
+    g = run(plan, seed=4, n_traj=50, n_steps=100, meta=[0, 1, 2], meta_vals=[0, 1, 0], count_from=1000)
+    _compare(g, orc, ids, trace=False)
+    assert int(g["counts"].sum()) == 0
+    # large trajectory ids and step indices above 2^32, resumed from given states
+    rng = np.random.default_rng(0)
+    init = rng.integers(0, 2, size=(40, 12)).astype(np.uint8)
+    tb, sb = 2**40 + 17, 2**33 + 5
+    orc = oracle_mod.simulate(text, 2**63 + 9, tb, 40, 200, meta_ids=[1], step_begin=sb,
+                              init_states=init, count_from=sb + 3, trace=True)
+    g = run(plan, seed=2**63 + 9, traj_begin=tb, n_traj=40, n_steps=200, meta=[1], step_begin=sb,
+            init_bits=init, count_from=sb + 3, trace=True)
+    _compare(g, orc, ids)
+
+
+def test_status_and_argument_errors():
+    import torch
+    from paper_1605_00854_gb300 import _lib, api
+    text = synth.tiny12(1).to_text()
+    plan, ids = plan_for(text, [0, 1, 2])
+    bufs = api.alloc_buffers(plan, 64)
+    with pytest.raises(_lib.PbnError):          # removed meta node
+        removed = [i for i in range(12) if i not in set(ids.tolist())]
+        if not removed:
+            raise _lib.PbnError(-1, "skip")
+        api.simulate(plan, bufs, seed=1, n_steps=10, meta_ids=[removed[0]])
+    with pytest.raises(_lib.PbnError):          # keyed init needs step_begin == 0
+        api.simulate(plan, bufs, seed=1, n_steps=10, meta_ids=[0], step_begin=5, init=0)
+    with pytest.raises(_lib.PbnError):          # bad lanes
+        api.simulate(plan, bufs, seed=1, n_steps=10, meta_ids=[0], lanes_per_traj=3)
+    api.simulate(plan, bufs, seed=1, n_steps=10, meta_ids=[0])
+    torch.cuda.synchronize()
+    assert int(bufs.status.item()) == 0

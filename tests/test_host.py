@@ -1,0 +1,314 @@
+"""CPU tests of the library's host side: the C ABI, parsing, Definition 1 reduction,
+grouping (Eq. 2, Algorithms 3-4), merged tables, thresholds and the estimator."""
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, golden
+import imgdecode
+from paper_1605_00854_gb300 import _lib, api, synth
+
+
+@pytest.fixture(scope="module")
+def L():
+    return _lib.load()
+
+
+def test_library_exports_every_declared_symbol(L):
+    """libpbn.so loads without a GPU and exports every function include/pbn.h declares."""
+    hdr = open(os.path.join(ROOT, "include", "pbn.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    declared = set(re.findall(r"\b(pbn_[a-z0-9_]+)\s*\(", hdr))
+    assert declared, "no declarations found"
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+        assert name in _lib.SIGNATURES, name
+    assert set(_lib.SIGNATURES) == declared
+
+
+def test_version_and_errors(L):
+    assert b"sm_103a" in L.pbn_version()
+    with pytest.raises(_lib.PbnError) as e:
+        api.Net.load("pbn 2 0.1\nf 0 1.0 1 5 2\nf 1 1.0 0 1\n")
+    assert e.value.status == -2 and "parent" in str(e.value)
+
+
+@pytest.mark.parametrize("text", [
+    "",                                          # no header
+    "pbn 0 0.1\n",                               # n < 1
+    "pbn 2 1.0\nf 0 1 0 1\nf 1 1 0 1\n",         # p = 1
+    "pbn 2 0.1\nf 0 1 0 1\n",                    # node 1 has no function
+    "pbn 2 0.1\nf 0 0.5 0 1\nf 1 1 0 1\n",       # probabilities sum to 0.5
+    "pbn 2 0.1\nf 0 1 1 0 4\nf 1 1 0 1\n",       # truth table wider than 2^k bits
+    "pbn 2 0.1\nf 0 1 2 1 1 3\nf 1 1 0 1\n",     # repeated parent
+    "pbn 2 0.1\nf 0 1 1 0 z\nf 1 1 0 1\n",       # bad hex digit
+    "pbn 2 0.1\nq 0\n",                          # unknown record
+])
+def test_parse_errors(text):
+    with pytest.raises(_lib.PbnError) as e:
+        api.Net.load(text)
+    assert e.value.status == -2
+
+
+def test_info_matches_oracle_shape(oracle_mod):
+    for seed in range(3):
+        net = synth.paper100(seed=seed, n=80)
+        text = net.to_text()
+        info = api.Net.load(text).info()
+        n, nf, sp, p = oracle_mod.shape(text)
+        assert (info.n, info.n_functions, info.p) == (n, nf, p)
+        assert info.density == pytest.approx(sp / n, rel=1e-15) == net.density()
+        assert info.P == math.floor(p * 2**32)
+
+
+# ---------------------------------------------------------------- reduction ----
+def test_reduce_hand_worked():
+    net, ids = api.Net.load(golden("leaves7.pbn")).reduce([1])
+    assert ids.tolist() == [0, 1, 4, 5]
+    assert net.info().n_retained == 4
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_reduce_matches_oracle_definition(oracle_mod, seed):
+    """The library's peeling reduction equals the oracle's literal iteration of
+    Definition 1 on random networks with sinks, self-loops and cycles."""
+    n = [30, 60, 100, 12, 200, 45][seed]
+    net = synth.paper100(seed=100 + seed, n=n, p=0.01) if seed != 3 else synth.tiny12(seed)
+    text = net.to_text()
+    interest = [0, 1, 2][: 1 + seed % 3]
+    leaf = oracle_mod.leaves(text, interest)
+    _, ids = api.Net.load(text).reduce(interest)
+    assert ids.tolist() == np.flatnonzero(~leaf).tolist()
+
+
+# ----------------------------------------------------------------- grouping ----
+def _plan(text, interest=(0, 1, 2), **kw):
+    net = api.Net.load(text)
+    red, ids = net.reduce(list(interest))
+    return api.Plan(red, **kw), ids
+
+
+@pytest.mark.parametrize("mode,max_inputs", [(0, 8), (0, 4), (0, 12), (1, 8)])
+def test_layout_is_a_valid_grouping(mode, max_inputs):
+    net = synth.paper100(seed=2)
+    plan, ids = _plan(net.to_text(), mode=mode, max_inputs=max_inputs)
+    pos = plan.layout()
+    grp = plan.groups()
+    retained = set(ids.tolist())
+    for i in range(net.n):
+        assert (pos[i] != 0xFFFFFFFF) == (i in retained)
+    kept = pos[pos != 0xFFFFFFFF]
+    assert len(set(kept.tolist())) == len(kept)
+    assert kept.max() < 32 * 2 * plan.info.state_words
+    # a group occupies consecutive bits of one 32-bit word
+    for g in set(grp[grp != 0xFFFFFFFF].tolist()):
+        members = sorted(pos[grp == g].tolist())
+        assert members[-1] - members[0] == len(members) - 1
+        assert members[0] // 32 == members[-1] // 32
+        assert len(members) <= 32
+        if mode == 1:
+            assert len(members) == 1
+    # the merge caps hold for every merged group
+    D = imgdecode.decode(plan.image())
+    for g, G in enumerate(D["groups"]):
+        width = int((grp == g).sum())
+        if width > 1:
+            assert G["q"] <= max_inputs
+
+
+def test_plain_mode_unreduced_is_identity_layout():
+    net = synth.tiny12(1)
+    plan = api.Plan(api.Net.load(net.to_text()), mode=1)
+    assert plan.layout().tolist() == list(range(12))
+    assert plan.info.n_groups == 12
+
+
+def _eq2(omegas, theta):
+    L = sum(math.log(w) for w in omegas)
+    m = 1
+    while m <= max(len(omegas), math.ceil(L) + 2):
+        if math.log(m) + L / m <= math.log(theta) + 1e-12:
+            return m
+        m += 1
+    return 0
+
+
+@pytest.mark.parametrize("seed,theta", [(1, 64.0), (2, 200.0), (3, 1000.0), (4, 30.0)])
+def test_theorem2_lower_bound_by_brute_force(seed, theta):
+    """Eq. 2 / Theorem 2: no partition into fewer than m^_min groups keeps
+    sum_i prod omega <= theta (checked by enumerating all set partitions of a small S),
+    and the library's m is at least m^_min whenever its weight sum is within theta."""
+    rng = np.random.default_rng(seed)
+    om = [int(x) for x in rng.integers(2, 4, size=7)]
+    mhat = _eq2(om, theta)
+
+    def partitions(items):
+        if not items:
+            yield []
+            return
+        first, rest = items[0], items[1:]
+        for p in partitions(rest):
+            for i in range(len(p)):
+                yield p[:i] + [[first] + p[i]] + p[i + 1:]
+            yield [[first]] + p
+
+    best = None
+    for part in partitions(list(range(len(om)))):
+        s = sum(math.prod(om[i] for i in blk) for blk in part)
+        if s <= theta and (best is None or len(part) < best):
+            best = len(part)
+    if best is not None:
+        assert mhat >= 1 and best >= mhat
+    # the library on a network whose multi-function nodes have exactly these omegas
+    lines = [f"pbn {len(om) + 1} {0.01.hex()}"]
+    for i, w in enumerate(om):
+        for j in range(w):
+            lines.append(f"f {i} {(1.0 / w).hex()} 1 {len(om)} {1 + (j % 2)}")
+    lines.append(f"f {len(om)} 0x1p+0 0 1")
+    net = api.Net.load("\n".join(lines) + "\n")
+    plan = api.Plan(net, theta=theta, max_inputs=24)
+    assert plan.info.m_lower_bound == mhat
+    if plan.info.sum_weights <= theta:
+        assert plan.info.m_found >= mhat
+
+
+def test_greedy_partition_hand_worked():
+    """Algorithm 3 on omega = (3, 3, 2, 2, 2) with m = 2: sorted descending, each to
+    the lightest group (empty groups weigh 0): 3 -> A, 3 -> B, 2 -> A (3 <= 3, lowest
+    index), 2 -> B (6 > 3), 2 -> A (6 <= 6): weights 12 and 6, sum 18.  With
+    theta = 18, Eq. 2 gives m^ = 2 (2 * sqrt(72) = 16.97 <= 18) and the partition
+    is accepted at m = 2."""
+    om = [3, 3, 2, 2, 2]
+    lines = [f"pbn 6 {0.01.hex()}"]
+    for i, w in enumerate(om):
+        for j in range(w):
+            lines.append(f"f {i} {(1.0 / w).hex()} 1 5 {1 + (j % 2)}")
+    lines.append("f 5 0x1p+0 0 1")
+    plan = api.Plan(api.Net.load("\n".join(lines) + "\n"), theta=18.0, max_inputs=24)
+    assert plan.info.m_lower_bound == 2 and plan.info.m_found == 2
+    assert plan.info.sum_weights == 18
+    g = plan.groups()
+    assert g[0] == g[2] == g[4] and g[1] == g[3] and g[0] != g[1]
+
+
+def _eval_fun(f, state_bits):
+    x = 0
+    for b, a in enumerate(f.parents):
+        x |= int(state_bits[a]) << b
+    return (f.tt >> x) & 1
+
+
+@pytest.mark.parametrize("mode,seed", [(0, 2), (0, 7), (1, 2)])
+def test_merged_tables_equal_member_functions(mode, seed):
+    """Sec. 3.3: entry (c, x) of a group's merged table holds, in bit i, the output of
+    member i's function selected by the mixed-radix choice c on the inputs packed in
+    x, for every c and x."""
+    net = synth.paper100(seed=seed, n=60)
+    plan, ids = _plan(net.to_text(), mode=mode)
+    D = imgdecode.decode(plan.image())
+    pos = plan.layout()
+    grp = plan.groups()
+    for g, G in enumerate(D["groups"]):
+        members = sorted(np.flatnonzero(grp == g).tolist(), key=lambda v: pos[v])
+        assert (pos[members[0]] & 31) == G["shift"]
+        recs = imgdecode.inputs(D, g)
+        # recover input node ids from the records
+        inv = {int(pos[v]): v for v in range(net.n) if pos[v] != 0xFFFFFFFF}
+        ins = []
+        for b, rec in enumerate(recs):
+            row, rot = rec >> 5, rec & 31
+            ins.append(inv[32 * row + ((b + rot) & 31)])
+        multi = [v for v in members if len(net.funcs[v]) >= 2]
+        assert len(multi) == G["n_mul"]
+        radix = [D["multi"][G["mul_first"] + m]["radix"] for m in range(G["n_mul"])]
+        ells = [len(net.funcs[v]) for v in multi]
+        prod = math.prod(ells)
+        assert radix == [math.prod(ells[:m]) for m in range(len(ells))]
+        rng = np.random.default_rng(g)
+        cs = range(prod) if prod * (1 << G["q"]) <= 4096 else rng.integers(0, prod, 8)
+        xs = range(1 << G["q"]) if prod * (1 << G["q"]) <= 4096 else rng.integers(0, 1 << G["q"], 64)
+        for c in cs:
+            js = {v: (int(c) // radix[m]) % ells[m] for m, v in enumerate(multi)}
+            for x in xs:
+                bits = np.zeros(net.n, dtype=np.uint8)
+                for b, a in enumerate(ins):
+                    bits[a] = (int(x) >> b) & 1
+                want = 0
+                for i, v in enumerate(members):
+                    f = net.funcs[v][js.get(v, 0)]
+                    want |= _eval_fun(f, bits) << i
+                assert imgdecode.entry(D, g, (int(c) << G["q"]) | int(x)) == want
+
+
+def test_thresholds_and_sel_slots_match_oracle(oracle_mod):
+    net = synth.paper100(seed=3)
+    text = net.to_text()
+    plan, ids = _plan(text)
+    D = imgdecode.decode(plan.image())
+    grp = plan.groups()
+    pos = plan.layout()
+    rank = {}
+    for v in range(net.n):
+        if len(net.funcs[v]) >= 2:
+            rank[v] = len(rank)
+    for g, G in enumerate(D["groups"]):
+        members = sorted(np.flatnonzero(grp == g).tolist(), key=lambda v: pos[v])
+        multi = [v for v in members if len(net.funcs[v]) >= 2]
+        for m, v in enumerate(multi):
+            rec = D["multi"][G["mul_first"] + m]
+            P, T = oracle_mod.thresholds(text, v)
+            assert imgdecode.thresholds(D, G["mul_first"] + m) == [t for t in T if t < 2**32]
+            blk = int(D["sel"][rec["u_slot"] // 4])
+            assert blk == rank[v] // 4 and rec["u_slot"] % 4 == rank[v] % 4
+    assert D["H"]["P"] == math.floor(net.p * 2**32)
+
+
+def test_plan_specs_over_budget_are_rejected():
+    """Group specs must fit the shared-memory staging budget (tables may stay in
+    global memory, specs may not)."""
+    net = synth.paper100(seed=2)
+    red, _ = api.Net.load(net.to_text()).reduce([0, 1, 2])
+    with pytest.raises(_lib.PbnError) as e:
+        api.Plan(red, smem_budget=1024)
+    assert e.value.status == -5
+    plan = api.Plan(red, smem_budget=4096)
+    assert plan.info.tables_in_smem == 0 and plan.info.stage_bytes <= 4096
+
+
+# ---------------------------------------------------------------- estimator ----
+@pytest.mark.parametrize("counts,ntraj", [
+    ([100, 900, 100, 100, 900], 1), ([5000, 80000, 1200, 1300, 3500], 64),
+    ([37, 1000, 3, 40, 7], 3), ([0, 500, 0, 0, 0], 1), ([10, 0, 0, 5, 5], 1),
+    ([123456, 10**7, 12345, 12345, 98765], 1024), ([50, 50, 50, 50, 0], 2),
+])
+@pytest.mark.parametrize("r,s", [(0.01, 0.95), (1e-5, 0.95), (0.001, 0.99)])
+def test_estimate_matches_oracle(oracle_mod, counts, ntraj, r, s):
+    got = api.estimate(counts, ntraj, r, s, 1e-3)
+    want = oracle_mod.estimate(counts, ntraj, r, s, 1e-3)
+    for k in ["alpha", "beta", "pi"]:
+        a, b = getattr(got, k), want[k]
+        assert (math.isnan(a) and math.isnan(b)) or abs(a - b) <= 1e-12 * max(1.0, abs(b))
+    assert abs(got.z - want["z"]) < 1e-12
+    assert got.L == want["L"]
+    if want["n_star"] is None:
+        assert got.n_star == 2**64 - 1
+    else:
+        assert abs(got.n_star_real - want["n_star_real"]) <= 1e-12 * want["n_star_real"]
+        assert got.n_star == want["n_star"]
+    if want["m_star"] is None:
+        assert got.m_star == 2**64 - 1
+    else:
+        assert got.m_star == want["m_star"]
+
+
+def test_estimate_rejects_bad_arguments():
+    with pytest.raises(_lib.PbnError):
+        api.estimate([1, 2, 3, 4, 5], 0, 0.01, 0.95)
+    with pytest.raises(_lib.PbnError):
+        api.estimate([1, 2, 3, 4, 5], 1, 0.0, 0.95)
+    with pytest.raises(_lib.PbnError):
+        api.estimate([1, 2, 3, 4, 5], 1, 0.01, 1.0)
