@@ -1,0 +1,341 @@
+"""Benchmark: PBN node-updates/s of the reduced + grouped CUDA simulation.
+
+Workload (one bench step = one pass of the whole hot path): the paper-scale network
+(n = 100, 70% single-function nodes, in-degree 1-5, 25% sinks, p = 1e-4, meta-state
+= nodes 0,1,2 ON), reduced and grouped (max 8 inputs per merged group), 2^16
+trajectories x 10^6 steps per GPU from the keyed initial state, with per-trajectory
+and pooled meta-state counts.  node-updates = n x trajectories x steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n-steps S] [--n-traj T]
+
+Under torchrun each rank simulates its own trajectory-id range (weak scaling); the
+timed region is bracketed by a barrier and device synchronisation and the maximum
+over ranks is reported.  --impl reference times the CPU oracle (the plain Eq. 1
+simulator of the unreduced network) on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1605_00854_gb300 import api, synth  # noqa: E402
+
+SEED = 20160503
+META = [0, 1, 2]
+WORKLOAD = "paper-scale PBN n=100 (70% 1 function, 30% 2-3; in-degree 1-5; 25% sinks; p=1e-4), reduced+grouped (<=8 inputs/group)"
+
+
+# ------------------------------------------------------------------ helpers ----
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def expected_blocks(k: int) -> float:
+    """Expected Philox blocks (2 levels each) to decide every lane of a k-lane
+    perturbation word under early exit: a lane is undecided after L levels with
+    probability 2^-L, independently, so E = sum_h P(some lane undecided after 2h levels)."""
+    return sum(1.0 - (1.0 - 2.0 ** (-2 * h)) ** k for h in range(16))
+
+
+def ops_per_traj_step(info, n: int, P: int) -> float:
+    """Algorithmic 32-bit integer operations of one trajectory-step of the method
+    (the per-unit figure of the roofline): Philox blocks at 56 ops (9 full rounds of
+    2 mul.hi + 2 mul.lo + 2 xor3; round 1's products are shared per step), 12 ops per
+    bit-sliced level pair, and in non-perturbed steps the SEL blocks, 2 ops per
+    threshold compare-accumulate and 1 per multi node, 3 ops per group input
+    (load, rotate, insert) and 5 per group (index, load, extract, shift, or), plus
+    8 ops of counting."""
+    pe = P / 2**32
+    W = (n + 63) // 64
+    blocks = sum(expected_blocks(64 if w < W - 1 or n % 64 == 0 else n % 64) for w in range(W)) if P else 0.0
+    pert = blocks * (56 + 12) + 4
+    nonpert = (info.n_sel_blocks * 56 + 2 * info.total_thresholds + info.n_multi
+               + 3 * info.total_inputs + 5 * info.n_groups + 2 * info.state_words)
+    return pert + (1.0 - pe) ** n * nonpert + 8
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- CPU oracle ----
+def oracle_rate(text: str, n: int, target_s: float, meta=META):
+    """Time the oracle on the host cores over a bounded sample: nthreads trajectories
+    (one per core) for a number of steps calibrated to take about target_s."""
+    from oracle import oracle
+    cores = os.cpu_count() or 1
+    oracle.build()
+    steps = 200
+    t0 = time.perf_counter()
+    oracle.simulate(text, SEED, 0, cores, steps, meta_ids=meta, nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    steps = max(200, int(steps * target_s / dt))
+    t0 = time.perf_counter()
+    oracle.simulate(text, SEED, 0, cores, steps, meta_ids=meta, nthreads=cores)
+    dt = time.perf_counter() - t0
+    return n * cores * steps / dt, cores, f"{cores} trajectories x {steps} steps of the same network (unreduced, ungrouped Eq. 1 simulator)", dt
+
+
+# ------------------------------------------------------------------- ours ----
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", init_method="env://")
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    net_obj = synth.paper100(seed=2)
+    text = net_obj.to_text()
+    n = net_obj.n
+    t_prep = time.perf_counter()
+    red, retained = api.Net.load(text).reduce(META)
+    plan = api.Plan(red)
+    prep_s = time.perf_counter() - t_prep
+    P = api.Net.load(text).info().P
+    info = plan.info
+    T, S = args.n_traj, args.n_steps
+    traj_begin = rank * T
+    d_img = plan.device_image(dev)
+    bufs = api.alloc_buffers(plan, T, dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
+
+    def one_step():
+        api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=META, traj_begin=traj_begin,
+                     stream=stream, d_image=d_img)
+
+    for _ in range(args.warmup):
+        bufs.counts.zero_(); bufs.pooled.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    assert int(bufs.status.item()) == 0, "kernel status word set"
+
+    times = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index if ws == 1 else local) as clk:
+        for _ in range(args.steps):
+            bufs.counts.zero_(); bufs.pooled.zero_()
+            flush.fill_(1)  # write 256 MiB (> L2) between timed steps
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    total = sum(times)
+    if ws > 1:
+        t = torch.tensor([total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    node_updates = n * T * S * ws * args.steps
+    value = node_updates / total
+    kernel_s = total / args.steps
+
+    # end to end through the public API with host buffers: H2D of the plan image,
+    # the simulation, D2H of states, counts and pooled counts, per step
+    img_host = torch.from_numpy(plan.image()).pin_memory()
+    st_h = torch.empty_like(bufs.state, device="cpu").pin_memory()
+    cnt_h = torch.empty_like(bufs.counts, device="cpu").pin_memory()
+    pool_h = torch.empty_like(bufs.pooled, device="cpu").pin_memory()
+    e2e_steps = max(1, min(args.steps, 2))
+    e_times = []
+    for _ in range(e2e_steps):
+        bufs.counts.zero_(); bufs.pooled.zero_()
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        d_img.copy_(img_host, non_blocking=True)
+        one_step()
+        st_h.copy_(bufs.state, non_blocking=True)
+        cnt_h.copy_(bufs.counts, non_blocking=True)
+        pool_h.copy_(bufs.pooled, non_blocking=True)
+        torch.cuda.synchronize()
+        e_times.append(time.perf_counter() - w0)
+    e2e_total = sum(e_times)
+    if ws > 1:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = n * T * S * ws * e2e_steps / e2e_total
+
+    out = None
+    if rank == 0:
+        pk, src = peaks()
+        sm_max = float(pk.get("sm_max_mhz", 2070.0))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        ops = ops_per_traj_step(info, n, P)
+        achieved = ops * T * S / kernel_s / 1e12
+        peak = sms * 128 * sm_max * 1e6 / 1e12
+        clk_sum = clk.summary()
+        pooled = bufs.pooled.cpu().numpy().view(np.uint64)
+        est = api.estimate(pooled, T, 0.01, 0.95)
+        out = {
+            "metric": "PBN node-updates/s (reduced+grouped kernel, bit-exact keyed draws)",
+            "value": value, "unit": "node-updates/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": kernel_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "n_retained": int(info.n_retained),
+                       "groups": int(info.n_groups), "n_traj_per_gpu": T, "n_steps": S,
+                       "seed": SEED, "meta": META, "l2": "flushed between timed steps (256 MiB write)",
+                       "parallelism": f"replicas{ws} (disjoint trajectory ids)",
+                       "host_prep_s": round(prep_s, 4)},
+            "traj_steps_per_s": T * S * ws * args.steps / total,
+            "retained_node_updates_per_s": int(info.n_retained) * T * S * ws * args.steps / total,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "ops_per_traj_step": ops,
+                         "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz ({src} max SM clock)"},
+            "e2e": {"value": e2e_value, "unit": "node-updates/s",
+                    "h2d_bytes_per_step": int(img_host.numel()),
+                    "d2h_bytes_per_step": int(st_h.numel() * 8 + cnt_h.numel() * 8 + pool_h.numel() * 8)},
+            "gpu_launches": args.steps,
+            "clocks": clk_sum,
+            "estimate": {"pi": est.pi, "alpha": est.alpha, "beta": est.beta, "n_star": est.n_star,
+                         "L": est.L},
+        }
+    if ws > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-traj", type=int, default=1 << 16)
+    ap.add_argument("--n-steps", type=int, default=10**6)
+    ap.add_argument("--oracle-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, _ = dist_env()
+
+    net_obj = synth.paper100(seed=2)
+    text = net_obj.to_text()
+    n = net_obj.n
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        vals = []
+        last = None
+        for i in range(args.warmup + args.steps):
+            rate, cores, sample, dt = oracle_rate(text, n, args.oracle_seconds / 2)
+            if i >= args.warmup:
+                vals.append((rate, dt))
+            last = (cores, sample)
+        total_t = sum(d for _, d in vals)
+        value = sum(r * d for r, d in vals) / total_t
+        line = {"metric": "PBN node-updates/s (reduced+grouped kernel, bit-exact keyed draws)",
+                "value": value, "unit": "node-updates/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(vals),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+                "data": "synthetic", "impl": "reference",
+                "config": {"workload": WORKLOAD, "n": n, "n_traj_per_gpu": args.n_traj,
+                           "n_steps": args.n_steps, "seed": SEED, "meta": META,
+                           "parallelism": "host cores (trajectories split over threads)"},
+                "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": last[0],
+                                 "kind": "oracle", "sample": last[1]},
+                "e2e": {"value": value, "unit": "node-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    out = run_ours(args)
+    if rank == 0 and out is not None:
+        if not args.no_cpu_baseline and ws == 1:
+            rate, cores, sample, dt = oracle_rate(text, n, args.oracle_seconds)
+            out["cpu_baseline"] = {"value": rate, "unit": "node-updates/s", "cores": cores,
+                                   "kind": "oracle", "sample": sample, "seconds": round(dt, 2)}
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

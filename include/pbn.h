@@ -153,6 +153,8 @@ typedef struct {
     uint64_t stage_bytes;    /* leading bytes of the image staged into shared memory */
     uint32_t tables_in_smem; /* 1 if the tables are staged into shared memory */
     uint32_t total_inputs;   /* sum over groups of their distinct inputs */
+    uint32_t n_multi;        /* retained nodes with >= 2 functions */
+    uint32_t total_thresholds; /* selection thresholds below 2^32 over those nodes */
 } pbn_plan_info;
 
 /* Errors: PBN_EINVAL. */

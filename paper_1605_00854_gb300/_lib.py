@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
                 ("state_words", u32), ("n_sel_blocks", u32), ("m_lower_bound", u32),
                 ("m_found", u32), ("sum_weights", u64), ("table_bytes", u64),
                 ("image_bytes", u64), ("stage_bytes", u64), ("tables_in_smem", u32),
-                ("total_inputs", u32)]
+                ("total_inputs", u32), ("n_multi", u32), ("total_thresholds", u32)]
 
 
 class SimArgs(ctypes.Structure):

@@ -700,6 +700,8 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     I.stage_bytes = H.stage_bytes;
     I.tables_in_smem = H.tables_in_smem;
     I.total_inputs = (uint32_t)total_inputs;
+    I.n_multi = (uint32_t)mrec.size();
+    I.total_thresholds = (uint32_t)thr.size();
     return PBN_OK;
 }
 

@@ -1,0 +1,48 @@
+"""Full-size parity at the benchmark configuration: the paper-scale network, 2^16
+trajectories x 10^6 steps in one launch with the default (autotuned) launch shape,
+exactly as bench.py runs it.  The oracle recomputes sampled trajectories at full
+length; every trajectory is checked against the count invariants."""
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+
+from paper_1605_00854_gb300 import api, synth
+
+pytestmark = pytest.mark.gpu
+
+SEED = 20160503  # the benchmark's seed
+META = [0, 1, 2]
+
+
+def test_paper100_full_size_sampled_trajectories(oracle_mod):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    text = synth.paper100(seed=2).to_text()
+    red, ids = api.Net.load(text).reduce(META)
+    plan = api.Plan(red)
+    T, S = 1 << 16, 10**6
+    bufs = api.alloc_buffers(plan, T)
+    api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=META)
+    torch.cuda.synchronize()
+    assert int(bufs.status.item()) == 0
+    counts = bufs.counts.cpu().numpy().view(np.uint64).T          # [T, 5]
+    final = plan.unpack(bufs.state.cpu().numpy().view(np.uint64))  # [T, n]
+    pooled = bufs.pooled.cpu().numpy().view(np.uint64)
+    # invariants for every trajectory: S pairs; V = visits over S + 1 states
+    pairs = counts[:, 1:].sum(axis=1)
+    assert np.all(pairs == S)
+    z_first_last = counts[:, 0].astype(np.int64) - (counts[:, 3] + counts[:, 4]).astype(np.int64)
+    assert np.all((z_first_last >= 0) & (z_first_last <= 1))   # V - (n10 + n11) = z_last
+    assert np.array_equal(pooled, counts.sum(axis=0))
+    # sampled trajectories recomputed by the oracle at full length
+    sample = [0, 1, 12345, 40000, 65535, 31337, 777, 50001]
+    def one(t):
+        return oracle_mod.simulate(text, SEED, t, 1, S, meta_ids=META)
+    with ThreadPoolExecutor(max_workers=min(len(sample), os.cpu_count() or 1)) as ex:
+        outs = list(ex.map(one, sample))
+    for t, o in zip(sample, outs):
+        assert np.array_equal(final[t, ids], o["final"][0, ids]), t
+        assert np.array_equal(counts[t], o["counts"][0]), t

@@ -105,8 +105,11 @@ def test_tables_in_global_memory(oracle_mod):
     memory and gives the same bits."""
     text = synth.paper100(seed=6, p=1e-3).to_text()
     meta = [1]
-    plan, ids = plan_for(text, meta, smem_budget=8192)
-    assert plan.info.tables_in_smem == 0
+    import imgdecode
+    base, _ = plan_for(text, meta)
+    specs = imgdecode.decode(base.image())["H"]["off_tables"]
+    plan, ids = plan_for(text, meta, smem_budget=max(1024, specs))
+    assert plan.info.tables_in_smem == 0 and plan.info.stage_bytes == specs
     orc = oracle_mod.simulate(text, 8, 0, 256, 800, meta_ids=meta, nthreads=NCPU)
     gpu = run(plan, seed=8, n_traj=256, n_steps=800, meta=meta)
     _compare(gpu, orc, ids, trace=False)
