@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1605_00854_gb300 import api, synth  # noqa: E402
+from paper_1605_00854_gb300 import api, shard, synth  # noqa: E402
 
 SEED = 20160503
 META = [0, 1, 2]
@@ -175,7 +175,7 @@ def run_ours(args):
     P = api.Net.load(text).info().P
     info = plan.info
     T, S = args.n_traj, args.n_steps
-    traj_begin = rank * T
+    traj_begin, _ = shard.weak_range(rank, ws, T)
     d_img = plan.device_image(dev)
     bufs = api.alloc_buffers(plan, T, dev)
     stream = torch.cuda.current_stream(dev)

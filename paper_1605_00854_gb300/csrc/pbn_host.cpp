@@ -567,12 +567,16 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
             const size_t q = ins.size();
             if (q > 24) return fail(PBN_ETOOBIG, "group with %zu inputs (max 24)", q);
             std::vector<int> inpos(n, -1);
+            const uint32_t in_chunk = (uint32_t)(inrec.size() / 4);
             for (size_t b = 0; b < q; ++b) {
                 uint32_t ps = plan->pos[ins[b]];
                 if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", ins[b]);
                 inpos[ins[b]] = (int)b;
-                inrec.push_back(((ps >> 5) << 5) | (((ps & 31) - (uint32_t)b) & 31));
+                /* word offset of the row (row * 4 bytes) above 5 rotation bits; the
+                 * rotation brings the bit to position b mod 4 of its 4-input chunk */
+                inrec.push_back(((ps >> 5) << 7) | (((ps & 31) - (uint32_t)(b & 3)) & 31));
             }
+            while (inrec.size() % 4) inrec.push_back(W32 << 7); /* the always-zero row */
             /* multi-function members, mixed radix in group bit order */
             std::vector<uint32_t> radix(gr.nodes.size(), 0);
             uint64_t prod = 1;
@@ -584,16 +588,23 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
                 if (fl.size() < 2) continue;
                 radix[i] = (uint32_t)prod;
                 pbn_img_multi M{};
-                M.u_slot = sel_slot(v);
-                M.radix = (uint32_t)prod;
-                M.thr_first = (uint32_t)thr.size();
+                const uint32_t first = (uint32_t)thr.size();
                 double C = 0.0;
+                uint32_t n_thr = 0;
                 for (size_t j = 1; j < fl.size(); ++j) {
                     C = C + fl[j - 1].c;
                     double t = std::floor(C * 4294967296.0);
                     if (t >= 4294967296.0) break; /* T_j = 2^32 never fires */
                     thr.push_back((uint32_t)t);
-                    M.n_thr++;
+                    n_thr++;
+                }
+                M.u_off = 4 * sel_slot(v) | (n_thr << 24);
+                M.radix = (uint32_t)prod;
+                if (n_thr <= 2) {
+                    M.t1 = n_thr >= 1 ? thr[first] : 0u;
+                    M.t2 = n_thr >= 2 ? thr[first + 1] : 0u;
+                } else {
+                    M.t1 = first; /* more than two thresholds: index into the thresholds */
                 }
                 mrec.push_back(M);
                 prod *= fl.size();
@@ -605,7 +616,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
             const uint64_t bits = entries << l2w;
             if ((double)bits > kMaxTableBits) return fail(PBN_ETOOBIG, "merged table of %llu bits exceeds 2^30", (unsigned long long)bits);
             G.tab_off = (uint32_t)tables.size();
-            G.in_first = (uint32_t)(inrec.size() - q);
+            G.in_chunk = in_chunk;
             G.q = (uint8_t)q;
             G.l2w = (uint8_t)l2w;
             G.n_mul = (uint8_t)(mrec.size() - G.mul_first);
@@ -682,7 +693,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
     if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);
     plan->hdr = H;
-    plan->per_traj_smem = 4 * (2 * W32 + 4 * H.n_sel);
+    plan->per_traj_smem = 4 * (2 * (W32 + 1) + (4 * H.n_sel + 1));
 
     pbn_plan_info& I = plan->info;
     memset(&I, 0, sizeof(I));

@@ -13,9 +13,11 @@
  *                        group bit order
  *   thr     [...]        uint32 selection thresholds T_j < 2^32 (Sec. 2.2 via
  *                        integer cumulative thresholds)
- *   inputs  [...]        uint32 input records: row << 5 | rot, where row is the
- *                        state word holding the input and rot = (bit - b) mod 32
- *                        rotates that bit to position b of the pattern x
+ *   inputs  [...]        uint32 input records, 4 per chunk, each group starting a
+ *                        chunk and padded with records of the always-zero row
+ *                        W32: (4 * row) << 5 | rot, where row is the state word
+ *                        holding input b and rot = (bit - b mod 4) mod 32 rotates
+ *                        that bit to position b mod 4 of its chunk
  *   selblk  [n_sel]      uint32 SEL block indices r / 4 drawn per step
  *   ret     [W]          uint64 mask of retained lanes of original word w
  *   pos     [n]          uint32 state position (32 * row + bit) of original node i,
@@ -50,7 +52,7 @@ typedef struct {
 
 typedef struct {
     uint32_t tab_off;   /* table offset in uint32 words from the tables section */
-    uint32_t in_first;  /* first input record */
+    uint32_t in_chunk;  /* first 4-record input chunk */
     uint32_t mul_first; /* first multi record */
     uint8_t q;          /* number of inputs */
     uint8_t l2w;        /* log2 of entry bits (0..5) */
@@ -59,10 +61,12 @@ typedef struct {
 } pbn_img_group; /* 16 bytes */
 
 typedef struct {
-    uint32_t u_slot;    /* SEL uniform slot: 4 * (index in selblk) + (rank mod 4) */
+    uint32_t u_off;     /* bits 0..23: byte offset of the node's SEL uniform in a
+                           trajectory's uniform row (4 * (4 * selblk index + rank mod 4));
+                           bits 24..31: number of thresholds below 2^32 */
     uint32_t radix;     /* mixed-radix weight of this node's choice */
-    uint32_t thr_first; /* first threshold */
-    uint32_t n_thr;     /* thresholds below 2^32 */
+    uint32_t t1, t2;    /* the thresholds when there are at most two; otherwise t1 is
+                           the index of the first one in the thresholds section */
 } pbn_img_multi; /* 16 bytes */
 
 #endif

@@ -97,12 +97,12 @@ __device__ __forceinline__ uint4 philox_draw(const SimParams& P, const PhiloxSte
     uint32_t x0 = s.y0, x1 = s.y1, x2 = s.y2_base ^ c3, x3 = s.y3;
 #pragma unroll
     for (int r = 1; r < 10; ++r) {
-        const uint32_t h0 = __umulhi(kPhiloxM0, x0), l0 = kPhiloxM0 * x0;
-        const uint32_t h1 = __umulhi(kPhiloxM1, x2), l1 = kPhiloxM1 * x2;
-        x0 = h1 ^ x1 ^ P.key0[r];
-        x2 = h0 ^ x3 ^ P.key1[r];
-        x1 = l1;
-        x3 = l0;
+        const uint64_t p0 = (uint64_t)kPhiloxM0 * x0;
+        const uint64_t p1 = (uint64_t)kPhiloxM1 * x2;
+        x0 = (uint32_t)(p1 >> 32) ^ x1 ^ P.key0[r];
+        x2 = (uint32_t)(p0 >> 32) ^ x3 ^ P.key1[r];
+        x1 = (uint32_t)p1;
+        x3 = (uint32_t)p0;
     }
     return make_uint4(x0, x1, x2, x3);
 }
@@ -208,10 +208,10 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
     }
 
     const uint2* WORDS = reinterpret_cast<const uint2*>(smem + P.off_words);
-    const pbn_img_group* GROUPS = reinterpret_cast<const pbn_img_group*>(smem + P.off_groups);
-    const pbn_img_multi* MULTI = reinterpret_cast<const pbn_img_multi*>(smem + P.off_multi);
+    const uint4* GROUPS = reinterpret_cast<const uint4*>(smem + P.off_groups);
+    const uint4* MULTI = reinterpret_cast<const uint4*>(smem + P.off_multi);
     const uint32_t* THR = reinterpret_cast<const uint32_t*>(smem + P.off_thr);
-    const uint32_t* INPUTS = reinterpret_cast<const uint32_t*>(smem + P.off_inputs);
+    const uint4* INPUTS = reinterpret_cast<const uint4*>(smem + P.off_inputs);
     const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(smem + P.off_selblk);
     const uint64_t* RET = reinterpret_cast<const uint64_t*>(smem + P.off_ret);
     const uint32_t* POS = reinterpret_cast<const uint32_t*>(smem + P.off_pos);
@@ -220,8 +220,10 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
 
     const uint32_t NT = P.nt;
     const uint32_t W32 = P.W32;
-    uint32_t* SROWS = reinterpret_cast<uint32_t*>(smem + P.smem_state_off); /* [2][W32][NT] */
-    uint32_t* UROWS = SROWS + 2 * W32 * NT;                                  /* [4 n_sel][NT] */
+    const uint32_t W32P = W32 + 1;            /* odd stride: row r of every slot in its own bank */
+    const uint32_t UP = 4 * P.n_sel + 1;      /* odd stride of the SEL uniform rows */
+    uint32_t* SBASE = reinterpret_cast<uint32_t*>(smem + P.smem_state_off); /* [2][NT][W32P] */
+    uint32_t* UBASE = SBASE + 2 * NT * W32P;                                 /* [NT][UP] */
 
     const uint32_t slot = threadIdx.x / LG;
     const uint32_t lane = LG == 1 ? 0u : (threadIdx.x % LG);
@@ -229,18 +231,22 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
     const bool active = lt < P.n_traj;
     const uint64_t traj = P.traj_begin + lt;
 
-    uint32_t* const S0 = SROWS + slot;      /* buffer b at S0 + b * bufstride */
-    const uint32_t bufstride = W32 * NT;
-    uint32_t* U = UROWS + slot;
+    uint32_t* const S0 = SBASE + slot * W32P;  /* buffer b at S0 + b * bufstride; row W32 stays 0 */
+    const uint32_t bufstride = NT * W32P;
+    uint32_t* const Ut = UBASE + slot * UP;
+    const uint8_t* const Ub = reinterpret_cast<const uint8_t*>(Ut);
     uint32_t cur = 0;
 
     uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;
 
     if (active) {
-        /* ---- initial state ---- */
+        /* ---- initial state (both buffers' zero rows cleared) ---- */
+        for (uint32_t r = lane; r <= W32; r += LG) {
+            S0[bufstride + r] = 0u;
+            if (P.init == 0 || r == W32) S0[r] = 0u;
+        }
+        group_sync<LG>();
         if (P.init == 0) {
-            for (uint32_t r = lane; r < W32; r += LG) S0[r * NT] = 0u;
-            group_sync<LG>();
             const PhiloxStep ps = philox_step(P, traj, 0);
             for (uint32_t w = lane; w < P.W; w += LG) {
                 const uint4 x = philox_draw(P, ps, (kDomInit << 28) | (w >> 1));
@@ -250,13 +256,13 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
                     const uint32_t b = __ffsll((long long)word) - 1;
                     word &= word - 1;
                     const uint32_t ps_ = POS[64 * w + b];
-                    or_bit<LG>(&S0[(ps_ >> 5) * NT], 1u << (ps_ & 31));
+                    or_bit<LG>(&S0[ps_ >> 5], 1u << (ps_ & 31));
                 }
             }
         } else {
             for (uint32_t r = lane; r < W32; r += LG) {
                 const uint64_t v = P.state[(uint64_t)(r >> 1) * P.n_traj + lt];
-                S0[r * NT] = (r & 1u) ? (uint32_t)(v >> 32) : (uint32_t)v;
+                S0[r] = (r & 1u) ? (uint32_t)(v >> 32) : (uint32_t)v;
             }
         }
         group_sync<LG>();
@@ -265,44 +271,51 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
         auto meta_z = [&](const uint32_t* Sb) -> uint32_t {
             uint32_t ok = 1u;
             for (uint32_t m = 0; m < P.n_meta_rows; ++m)
-                ok &= ((Sb[P.meta_row[m] * NT] & P.meta_mask[m]) == P.meta_val[m]) ? 1u : 0u;
+                ok &= ((Sb[P.meta_row[m]] & P.meta_mask[m]) == P.meta_val[m]) ? 1u : 0u;
             return ok;
         };
         uint32_t zp = meta_z(S0);
         if (P.count_first) cV += zp;
 
-        const uint64_t last_lanes = (P.n & 63u) ? ((1ull << (P.n & 63u)) - 1ull) : ~0ull;
+        const uint32_t nl = P.n & 63u;
+        const uint64_t last_lanes = nl ? ((1ull << nl) - 1ull) : ~0ull;
 
         for (uint32_t k = 0; k < P.n_steps; ++k) {
             const uint64_t t = P.step_begin + k;
             const PhiloxStep ps = philox_step(P, traj, t);
             uint32_t* Sc = S0 + cur * bufstride;
 
-            /* ---- 1. perturbation: bit-sliced u < P with early exit ---- */
+            /* ---- 1. perturbation: bit-sliced u < P, most significant level first,
+             *         stopping once every lane of the word is decided ---- */
             uint32_t any_l = 0;
             if (P.P != 0u) {
                 for (uint32_t w = lane; w < P.W; w += LG) {
-                    uint64_t und = (w == P.W - 1) ? last_lanes : ~0ull;
-                    uint64_t pert = 0;
-                    for (uint32_t h = 0; h < 16u && und; ++h) {
+                    const uint64_t valid = (w == P.W - 1) ? last_lanes : ~0ull;
+                    uint32_t und_lo = (uint32_t)valid, und_hi = (uint32_t)(valid >> 32);
+                    uint32_t pert_lo = 0, pert_hi = 0;
+                    uint32_t pp = P.P; /* level 2h uses bit 31 of pp, level 2h+1 bit 30 */
+                    for (uint32_t h = 0; h < 16u && (und_lo | und_hi); ++h) {
                         const uint4 x = philox_draw(P, ps, (kDomPert << 28) | (w << 4) | h);
-                        const uint64_t L0 = ((uint64_t)x.y << 32) | x.x;
-                        const uint64_t L1 = ((uint64_t)x.w << 32) | x.z;
-                        const uint64_t m0 = ((P.P >> (31u - 2u * h)) & 1u) ? ~0ull : 0ull;
-                        const uint64_t m1 = ((P.P >> (30u - 2u * h)) & 1u) ? ~0ull : 0ull;
-                        pert |= und & ~L0 & m0;
-                        und &= ~(L0 ^ m0);
-                        pert |= und & ~L1 & m1;
-                        und &= ~(L1 ^ m1);
+                        const uint32_t m0 = (uint32_t)((int32_t)pp >> 31);
+                        const uint32_t m1 = (uint32_t)((int32_t)(pp << 1) >> 31);
+                        pp <<= 2;
+                        pert_lo |= und_lo & ~x.x & m0;
+                        pert_hi |= und_hi & ~x.y & m0;
+                        und_lo &= ~(x.x ^ m0);
+                        und_hi &= ~(x.y ^ m0);
+                        pert_lo |= und_lo & ~x.z & m1;
+                        pert_hi |= und_hi & ~x.w & m1;
+                        und_lo &= ~(x.z ^ m1);
+                        und_hi &= ~(x.w ^ m1);
                     }
-                    if (pert) {
+                    if (pert_lo | pert_hi) {
                         any_l = 1u;
-                        uint64_t f = pert & RET[w];
+                        uint64_t f = ((((uint64_t)pert_hi) << 32) | pert_lo) & RET[w];
                         while (f) {
                             const uint32_t b = __ffsll((long long)f) - 1;
                             f &= f - 1;
                             const uint32_t ps_ = POS[64 * w + b];
-                            xor_bit<LG>(&Sc[(ps_ >> 5) * NT], 1u << (ps_ & 31));
+                            xor_bit<LG>(&Sc[ps_ >> 5], 1u << (ps_ & 31));
                         }
                     }
                 }
@@ -315,43 +328,67 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
 
             if (!any) {
                 /* ---- 2a. selection draws of the retained multi-function nodes ---- */
-                for (uint32_t i = lane; i < P.n_sel; i += LG) {
+                uint32_t i = lane;
+                for (; i + LG < P.n_sel; i += 2 * LG) {
                     const uint4 x = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
-                    U[(4 * i + 0) * NT] = x.x;
-                    U[(4 * i + 1) * NT] = x.y;
-                    U[(4 * i + 2) * NT] = x.z;
-                    U[(4 * i + 3) * NT] = x.w;
+                    const uint4 y = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i + LG]);
+                    uint32_t* a = Ut + 4 * i;
+                    uint32_t* b = Ut + 4 * (i + LG);
+                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                    b[0] = y.x; b[1] = y.y; b[2] = y.z; b[3] = y.w;
+                }
+                if (i < P.n_sel) {
+                    const uint4 x = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
+                    uint32_t* a = Ut + 4 * i;
+                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
                 }
                 group_sync<LG>();
                 /* ---- 2b. merged-table evaluation, word by word ---- */
+                const uint8_t* Sc8 = reinterpret_cast<const uint8_t*>(Sc);
                 uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
                 for (uint32_t w = lane; w < W32; w += LG) {
                     const uint2 wr = WORDS[w];
                     uint32_t acc = 0;
                     for (uint32_t gi = wr.x; gi < wr.x + wr.y; ++gi) {
-                        const pbn_img_group G = GROUPS[gi];
+                        const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
+                        const uint32_t q = G.w & 0xFFu;
+                        const uint32_t l2w = (G.w >> 8) & 0xFFu;
+                        const uint32_t n_mul = (G.w >> 16) & 0xFFu;
+                        const uint32_t shift = G.w >> 24;
                         uint32_t c = 0;
-                        for (uint32_t m = 0; m < G.n_mul; ++m) {
-                            const pbn_img_multi M = MULTI[G.mul_first + m];
-                            const uint32_t u = U[M.u_slot * NT];
-                            uint32_t j = 0;
-                            for (uint32_t q = 0; q < M.n_thr; ++q) j += (u >= THR[M.thr_first + q]) ? 1u : 0u;
-                            c += j * M.radix;
+                        for (uint32_t m = 0; m < n_mul; ++m) {
+                            const uint4 M = MULTI[G.z + m]; /* u_off|n_thr, radix, t1, t2 */
+                            const uint32_t u = *reinterpret_cast<const uint32_t*>(Ub + (M.x & 0xFFFFFFu));
+                            const uint32_t n_thr = M.x >> 24;
+                            uint32_t j;
+                            if (n_thr <= 2u) {
+                                j = ((n_thr >= 1u) & (u >= M.z)) + ((n_thr >= 2u) & (u >= M.w));
+                            } else {
+                                j = 0;
+                                for (uint32_t q2 = 0; q2 < n_thr; ++q2) j += (u >= THR[M.z + q2]) ? 1u : 0u;
+                            }
+                            c += j * M.y;
                         }
                         uint32_t x = 0;
-                        const uint32_t* in = INPUTS + G.in_first;
-                        for (uint32_t b = 0; b < G.q; ++b) {
-                            const uint32_t rec = in[b];
-                            const uint32_t v = Sc[(rec >> 5) * NT];
-                            x |= __funnelshift_r(v, v, rec) & (1u << b);
+                        const uint4* ch = INPUTS + G.y;
+                        for (uint32_t b0 = 0; b0 < q; b0 += 4) {
+                            const uint4 R = *ch++;
+                            const uint32_t v0 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.x >> 5));
+                            const uint32_t v1 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.y >> 5));
+                            const uint32_t v2 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.z >> 5));
+                            const uint32_t v3 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.w >> 5));
+                            uint32_t x4 = __funnelshift_r(v0, v0, R.x) & 1u;
+                            x4 |= __funnelshift_r(v1, v1, R.y) & 2u;
+                            x4 |= __funnelshift_r(v2, v2, R.z) & 4u;
+                            x4 |= __funnelshift_r(v3, v3, R.w) & 8u;
+                            x |= x4 << b0;
                         }
-                        const uint32_t bo = ((c << G.q) | x) << G.l2w;
-                        const uint32_t tw = TAB_SMEM ? TAB[G.tab_off + (bo >> 5)] : __ldg(TAB + G.tab_off + (bo >> 5));
-                        const uint32_t ebits = 1u << G.l2w;
-                        const uint32_t emask = (2u << (ebits - 1u)) - 1u;
-                        acc |= ((tw >> (bo & 31u)) & emask) << G.shift;
+                        const uint32_t bo = ((c << q) | x) << l2w;
+                        const uint32_t tw = TAB_SMEM ? TAB[G.x + (bo >> 5)] : __ldg(TAB + G.x + (bo >> 5));
+                        const uint32_t emask = (2u << ((1u << l2w) - 1u)) - 1u;
+                        acc |= ((tw >> (bo & 31u)) & emask) << shift;
                     }
-                    Sn[w * NT] = acc;
+                    Sn[w] = acc;
                 }
                 group_sync<LG>();
                 cur ^= 1u;
@@ -359,7 +396,8 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
 
             /* ---- 3. meta-state counts ---- */
             if (lane == 0) {
-                const uint32_t z = meta_z(S0 + cur * bufstride);
+                const uint32_t* Sb = S0 + cur * bufstride;
+                const uint32_t z = meta_z(Sb);
                 const uint32_t cv = k >= P.kv0 ? 1u : 0u;
                 const uint32_t cp = k >= P.kp0 ? 1u : 0u;
                 cV += cv & z;
@@ -368,9 +406,8 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
                 c10 += cp & zp & (z ^ 1u);
                 zp = z;
                 if (TRACE) {
-                    const uint32_t* Sb = S0 + cur * bufstride;
                     for (uint32_t r = 0; r < W32; r += 2) {
-                        const uint64_t v = ((uint64_t)Sb[(r + 1) * NT] << 32) | Sb[r * NT];
+                        const uint64_t v = ((uint64_t)Sb[r + 1] << 32) | Sb[r];
                         P.trace[((uint64_t)k * (W32 / 2) + r / 2) * P.n_traj + lt] = v;
                     }
                 }
@@ -381,7 +418,7 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
         /* ---- epilogue: state and counts ---- */
         const uint32_t* Sb = S0 + cur * bufstride;
         for (uint32_t r = lane * 2; r < W32; r += 2 * LG) {
-            const uint64_t v = ((uint64_t)Sb[(r + 1) * NT] << 32) | Sb[r * NT];
+            const uint64_t v = ((uint64_t)Sb[r + 1] << 32) | Sb[r];
             P.state[(uint64_t)(r >> 1) * P.n_traj + lt] = v;
         }
         if (lane == 0 && P.counts) {
@@ -547,8 +584,10 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     uint32_t LG = a->lanes_per_traj;
     if (LG == 0) {
         LG = 1;
-        /* aim for >= 16 resident warps per SM when there are few trajectories */
-        while (LG < 8 && a->n_traj * LG < (uint64_t)sms * 512 && LG * 2 <= H.W32) LG *= 2;
+        /* lanes of a group take different state words, so they diverge in the
+         * evaluation: split a trajectory only when its state is wide and there are
+         * too few trajectories to fill the SMs */
+        while (LG < 8 && H.W32 >= 16 * LG && a->n_traj * LG < (uint64_t)sms * 512) LG *= 2;
     }
     if (LG != 1 && LG != 2 && LG != 4 && LG != 8) return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4 or 8");
     const size_t per_traj = plan->per_traj_smem;

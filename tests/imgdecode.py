@@ -16,13 +16,14 @@ def decode(img: np.ndarray) -> dict:
     words = u32[H["off_words"] // 4: H["off_words"] // 4 + 2 * H["W32"]].reshape(-1, 2)
     groups = []
     for g in range(H["n_groups"]):
-        tab_off, in_first, mul_first, q, l2w, n_mul, shift = struct.unpack_from(
+        tab_off, in_chunk, mul_first, q, l2w, n_mul, shift = struct.unpack_from(
             "<3I4B", b, H["off_groups"] + 16 * g)
-        groups.append(dict(tab_off=tab_off, in_first=in_first, mul_first=mul_first, q=q, l2w=l2w,
+        groups.append(dict(tab_off=tab_off, in_chunk=in_chunk, mul_first=mul_first, q=q, l2w=l2w,
                            n_mul=n_mul, shift=shift))
-    multi = [dict(zip(["u_slot", "radix", "thr_first", "n_thr"],
-                      struct.unpack_from("<4I", b, H["off_multi"] + 16 * m)))
-             for m in range(H["n_multi"])]
+    multi = []
+    for m in range(H["n_multi"]):
+        u_off, radix, t1, t2 = struct.unpack_from("<4I", b, H["off_multi"] + 16 * m)
+        multi.append(dict(u_slot=(u_off & 0xFFFFFF) // 4, n_thr=u_off >> 24, radix=radix, t1=t1, t2=t2))
     sel = u32[H["off_selblk"] // 4: H["off_selblk"] // 4 + H["n_sel"]]
     pos = u32[H["off_pos"] // 4: H["off_pos"] // 4 + H["n"]]
     ret = np.frombuffer(b, dtype=np.uint64)[H["off_ret"] // 8: H["off_ret"] // 8 + H["W"]]
@@ -31,14 +32,21 @@ def decode(img: np.ndarray) -> dict:
 
 def thresholds(D, m):
     M = D["multi"][m]
-    o = D["H"]["off_thr"] // 4 + M["thr_first"]
+    if M["n_thr"] <= 2:
+        return [M["t1"], M["t2"]][: M["n_thr"]]
+    o = D["H"]["off_thr"] // 4 + M["t1"]
     return [int(v) for v in D["u32"][o: o + M["n_thr"]]]
 
 
 def inputs(D, g):
+    """(row, bit) of each input b of group g, decoded from its chunked record."""
     G = D["groups"][g]
-    o = D["H"]["off_inputs"] // 4 + G["in_first"]
-    return [int(v) for v in D["u32"][o: o + G["q"]]]
+    o = D["H"]["off_inputs"] // 4 + 4 * G["in_chunk"]
+    out = []
+    for b, rec in enumerate(int(v) for v in D["u32"][o: o + G["q"]]):
+        row, rot = rec >> 7, rec & 31
+        out.append((row, ((b & 3) + rot) & 31))
+    return out
 
 
 def entry(D, g, e):

@@ -215,13 +215,9 @@ def test_merged_tables_equal_member_functions(mode, seed):
     for g, G in enumerate(D["groups"]):
         members = sorted(np.flatnonzero(grp == g).tolist(), key=lambda v: pos[v])
         assert (pos[members[0]] & 31) == G["shift"]
-        recs = imgdecode.inputs(D, g)
         # recover input node ids from the records
         inv = {int(pos[v]): v for v in range(net.n) if pos[v] != 0xFFFFFFFF}
-        ins = []
-        for b, rec in enumerate(recs):
-            row, rot = rec >> 5, rec & 31
-            ins.append(inv[32 * row + ((b + rot) & 31)])
+        ins = [inv[32 * row + bit] for row, bit in imgdecode.inputs(D, g)]
         multi = [v for v in members if len(net.funcs[v]) >= 2]
         assert len(multi) == G["n_mul"]
         radix = [D["multi"][G["mul_first"] + m]["radix"] for m in range(G["n_mul"])]
