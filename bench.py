@@ -31,7 +31,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1605_00854_gb300 import api, shard, synth  # noqa: E402
+from paper_1605_00854_gb300 import _lib, api, shard, synth  # noqa: E402
 
 SEED = 20160503
 META = [0, 1, 2]
@@ -171,7 +171,9 @@ def run_ours(args):
     t_prep = time.perf_counter()
     red, retained = api.Net.load(text).reduce(META)
     plan = api.Plan(red)
+    compile_ms = plan.compile() if args.kernel == "compiled" else 0.0
     prep_s = time.perf_counter() - t_prep
+    kern = _lib.PBN_KERNEL_COMPILED if args.kernel == "compiled" else _lib.PBN_KERNEL_INTERP
     P = api.Net.load(text).info().P
     info = plan.info
     T, S = args.n_traj, args.n_steps
@@ -183,7 +185,7 @@ def run_ours(args):
 
     def one_step():
         api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=META, traj_begin=traj_begin,
-                     stream=stream, d_image=d_img)
+                     stream=stream, d_image=d_img, kernel=kern)
 
     for _ in range(args.warmup):
         bufs.counts.zero_(); bufs.pooled.zero_()
@@ -244,6 +246,30 @@ def run_ours(args):
         e2e_total = float(t.item())
     e2e_value = n * T * S * ws * e2e_steps / e2e_total
 
+    compare = {}
+    if rank == 0 and args.compare_steps > 0:
+        # the same workload on shorter passes: interpreter and the unmerged method
+        plain_plan = api.Plan(api.Net.load(text), mode=_lib.PBN_PLAN_PLAIN)
+        variants = [("interpreter_grouped", plan, _lib.PBN_KERNEL_INTERP),
+                    ("compiled_plain_unreduced", plain_plan, _lib.PBN_KERNEL_COMPILED),
+                    ("interpreter_plain_unreduced", plain_plan, _lib.PBN_KERNEL_INTERP)]
+        for name, pl, kk in variants:
+            b2 = api.alloc_buffers(pl, T, dev)
+            img2 = pl.device_image(dev)
+            api.simulate(pl, b2, seed=SEED, n_steps=1000, meta_ids=META, stream=stream, d_image=img2, kernel=kk)
+            torch.cuda.synchronize()
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            api.simulate(pl, b2, seed=SEED, n_steps=args.compare_steps, meta_ids=META, stream=stream,
+                         d_image=img2, kernel=kk)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dt = e0.elapsed_time(e1) / 1e3
+            compare[name] = {"value": n * T * args.compare_steps / dt, "unit": "node-updates/s",
+                             "n_steps": args.compare_steps, "groups": int(pl.info.n_groups)}
+            del b2
+
     out = None
     if rank == 0:
         pk, src = peaks()
@@ -264,7 +290,9 @@ def run_ours(args):
                        "groups": int(info.n_groups), "n_traj_per_gpu": T, "n_steps": S,
                        "seed": SEED, "meta": META, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas{ws} (disjoint trajectory ids)",
-                       "host_prep_s": round(prep_s, 4)},
+                       "host_prep_s": round(prep_s, 4), "compile_ms": round(compile_ms, 1),
+                       "kernel": args.kernel},
+            "compare": compare,
             "traj_steps_per_s": T * S * ws * args.steps / total,
             "retained_node_updates_per_s": int(info.n_retained) * T * S * ws * args.steps / total,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
@@ -294,6 +322,9 @@ def main():
     ap.add_argument("--n-steps", type=int, default=10**6)
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter"])
+    ap.add_argument("--compare-steps", type=int, default=100000,
+                    help="steps of the comparison passes (interpreter, plain method); 0 = skip")
     args = ap.parse_args()
     ws, rank, _ = dist_env()
 

@@ -202,7 +202,13 @@ typedef struct {
                         state after every step (for checking; slows the kernel) */
     uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8 */
     uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj */
+    uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP or PBN_KERNEL_COMPILED */
+    uint32_t reserved;
 } pbn_sim_args;
+
+#define PBN_KERNEL_AUTO 0u     /* the compiled plan kernel if pbn_plan_compile succeeded, else the interpreter */
+#define PBN_KERNEL_INTERP 1u   /* the generic kernel that reads the plan image */
+#define PBN_KERNEL_COMPILED 2u /* the plan's own kernel (compiled on first use) */
 
 /* Simulate trajectories traj_begin .. traj_begin + n_traj - 1 for steps
  * step_begin .. step_begin + n_steps - 1 (Algorithm 5, ParallelSimulation, with
@@ -215,6 +221,21 @@ typedef struct {
  * distinct meta words (> 16)), PBN_ETOOBIG (shared memory), PBN_ECUDA. */
 int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn_sim_args* args,
                  void* stream);
+
+/* Compile the plan into a kernel of its own (Algorithm 5's Preparation output as
+ * constants: group input positions, selection thresholds, the levels of P and the
+ * small merged tables become immediates, the state lives in registers), with NVRTC
+ * for sm_103a, and keep it with the plan.  Idempotent and thread-safe.  Plans with
+ * more than 1024 original nodes, 64 state words or 24 SEL blocks are not compiled
+ * (the interpreter kernel runs them).  *compile_ms (may be NULL) receives the host
+ * time spent.  Errors: PBN_EINVAL (plan not compilable), PBN_ECUDA (NVRTC missing,
+ * compilation or module load failed; pbn_last_error_detail() has the log). */
+int pbn_plan_compile(const pbn_plan* plan, double* compile_ms);
+
+/* The CUDA source generated for the plan's own kernel: *len receives its length;
+ * dst (capacity cap, may be NULL) receives it NUL-terminated.
+ * Errors: PBN_EINVAL (plan not compilable, cap too small). */
+int pbn_plan_source(const pbn_plan* plan, char* dst, size_t cap, size_t* len);
 
 /* ---- estimation ------------------------------------------------------------------ */
 typedef struct {

@@ -19,6 +19,9 @@ PBN_PLAN_GROUPED = 0
 PBN_PLAN_PLAIN = 1
 PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
+PBN_KERNEL_AUTO = 0
+PBN_KERNEL_INTERP = 1
+PBN_KERNEL_COMPILED = 2
 PBN_DEV_STAGE_TIMEOUT = 0x1
 PBN_DEV_BAD_PLAN = 0x2
 
@@ -46,7 +49,7 @@ class SimArgs(ctypes.Structure):
                 ("n_steps", u64), ("count_from", u64), ("init", u32), ("n_meta", u32),
                 ("meta_ids", vp), ("meta_vals", vp), ("d_state", vp), ("d_counts", vp),
                 ("d_pooled", vp), ("d_status", vp), ("d_trace", vp),
-                ("lanes_per_traj", u32), ("trajs_per_block", u32)]
+                ("lanes_per_traj", u32), ("trajs_per_block", u32), ("kernel", u32), ("reserved", u32)]
 
 
 class EstimateOut(ctypes.Structure):
@@ -67,6 +70,8 @@ SIGNATURES = {
     "pbn_plan_layout": (i32, [vp, vp]),
     "pbn_plan_groups": (i32, [vp, vp]),
     "pbn_simulate": (i32, [vp, vp, ctypes.POINTER(SimArgs), vp]),
+    "pbn_plan_compile": (i32, [vp, ctypes.POINTER(f64)]),
+    "pbn_plan_source": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "pbn_estimate": (i32, [vp, u64, u64, f64, f64, f64, ctypes.POINTER(EstimateOut)]),
     "pbn_strerror": (cp, [i32]),
     "pbn_last_error_detail": (cp, []),

@@ -107,6 +107,21 @@ class Plan:
         check(_lib.load().pbn_plan_groups(self._h, _ptr(g)), "pbn_plan_groups")
         return g
 
+    def compile(self) -> float:
+        """Compile the plan into its own kernel (pbn_plan_compile); returns host ms."""
+        ms = ctypes.c_double()
+        check(_lib.load().pbn_plan_compile(self._h, ctypes.byref(ms)), "pbn_plan_compile")
+        return ms.value
+
+    def source(self) -> str:
+        """CUDA source of the plan's own kernel (pbn_plan_source)."""
+        L = _lib.load()
+        n = ctypes.c_size_t()
+        check(L.pbn_plan_source(self._h, None, 0, ctypes.byref(n)), "pbn_plan_source")
+        buf = ctypes.create_string_buffer(n.value + 1)
+        check(L.pbn_plan_source(self._h, buf, n.value + 1, ctypes.byref(n)), "pbn_plan_source")
+        return buf.value.decode()
+
     def device_image(self, device="cuda"):
         """The image uploaded once to device memory (cached)."""
         import torch
@@ -150,7 +165,7 @@ def alloc_buffers(plan: Plan, n_traj: int, device="cuda") -> SimBuffers:
 def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids, meta_vals=None,
              traj_begin: int = 0, step_begin: int = 0, count_from: int = 0, init: int | None = None,
              trace=None, lanes_per_traj: int = 0, trajs_per_block: int = 0, stream=None,
-             d_image=None, n_traj: int | None = None):
+             d_image=None, n_traj: int | None = None, kernel: int = _lib.PBN_KERNEL_AUTO):
     """Enqueue pbn_simulate on `stream` (default: torch's current stream)."""
     import torch
     L = _lib.load()
@@ -172,6 +187,7 @@ def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids,
     a.d_status = None if bufs.status is None else bufs.status.data_ptr()
     a.d_trace = None if trace is None else trace.data_ptr()
     a.lanes_per_traj, a.trajs_per_block = lanes_per_traj, trajs_per_block
+    a.kernel = kernel
     img = plan.device_image(bufs.state.device) if d_image is None else d_image
     st = torch.cuda.current_stream(bufs.state.device) if stream is None else stream
     check(L.pbn_simulate(plan._h, ctypes.c_void_p(img.data_ptr()), ctypes.byref(a),

@@ -21,8 +21,20 @@ LIB = os.path.join(OUT, "libpbn.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 CU_SOURCES = ["pbn_sim.cu"]
-CPP_SOURCES = ["pbn_host.cpp"]
-HEADERS = ["pbn_internal.h", "pbn_image.h"]
+CPP_SOURCES = ["pbn_host.cpp", "pbn_jit.cpp"]
+HEADERS = ["pbn_internal.h", "pbn_image.h", "pbn_device.cuh"]
+CUDA_INC = "/usr/local/cuda/include"
+
+
+def _embed_device_header():
+    """Write the device header as a C++ raw string for the plan compiler."""
+    src = os.path.join(CSRC, "pbn_device.cuh")
+    dst = os.path.join(OUT, "pbn_device_cuh.inc")
+    text = open(src).read()
+    body = 'R"PBNSRC(' + text + ')PBNSRC"\n'
+    if not os.path.exists(dst) or open(dst).read() != body:
+        with open(dst, "w") as f:
+            f.write(body)
 
 
 def _nvcc() -> str:
@@ -49,7 +61,8 @@ def _run(cmd):
 def build(force: bool = False, verbose: bool = False) -> str:
     """Compile and link libpbn.so if any source changed; return its path."""
     os.makedirs(OUT, exist_ok=True)
-    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    _embed_device_header()
+    inc = ["-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", OUT]
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(ROOT, "include", "pbn.h")]
     nvcc = _nvcc()
     jobs = []
@@ -65,8 +78,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT, src + ".o")
         objs.append(o)
-        if force or _newer(o, [s] + hdrs):
-            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-c", s, "-o", o])
+        if force or _newer(o, [s] + hdrs + [os.path.join(OUT, "pbn_device_cuh.inc")]):
+            jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-I", CUDA_INC, "-c", s, "-o", o])
     logs = []
     if jobs:
         with ThreadPoolExecutor(max_workers=len(jobs)) as ex:

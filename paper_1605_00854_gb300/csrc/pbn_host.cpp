@@ -750,6 +750,8 @@ extern "C" int pbn_group(const pbn_net* net, const pbn_group_params* prm_in, pbn
     }
 }
 
+pbn_plan::~pbn_plan() { pbn::jit_free(jit); }
+
 extern "C" void pbn_plan_free(pbn_plan* plan) { delete plan; }
 
 extern "C" int pbn_plan_info_get(const pbn_plan* plan, pbn_plan_info* out) {

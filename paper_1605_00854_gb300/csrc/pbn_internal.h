@@ -25,6 +25,8 @@ struct pbn_net {
     std::vector<uint32_t> interest;            /* nodes of interest given to pbn_reduce */
 };
 
+struct pbn_jit_state;
+
 struct pbn_plan {
     pbn_plan_info info{};
     pbn_img_header hdr{};
@@ -32,11 +34,20 @@ struct pbn_plan {
     std::vector<uint32_t> pos;       /* per original node: 32 * row + bit, or UINT32_MAX */
     std::vector<uint32_t> group_of;  /* per original node: group index, or UINT32_MAX */
     uint32_t per_traj_smem = 0;      /* shared-memory bytes per trajectory slot */
+    mutable pbn_jit_state* jit = nullptr; /* compiled-plan cache (pbn_jit.cpp) */
+    ~pbn_plan();
 };
+
+struct pbn_jit_params_s;
 
 namespace pbn {
 int fail(int code, const char* fmt, ...);
 uint64_t pert_threshold(double p);
+/* compiled plans (pbn_jit.cpp) */
+pbn_jit_state* jit_state(const pbn_plan* plan);
+void jit_free(pbn_jit_state* J);
+int jit_compile(const pbn_plan* plan);
+bool jit_ready(const pbn_plan* plan);
 }  // namespace pbn
 
 #endif

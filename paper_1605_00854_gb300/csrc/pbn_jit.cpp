@@ -1,0 +1,466 @@
+/*
+ * pbn_jit.cpp -- compiled plans: a plan's Preparation output (Algorithm 5: the
+ * groups, their merged tables, the selection thresholds and the perturbation
+ * threshold) is turned into the source of a kernel in which all of it is constant,
+ * compiled for sm_103a with NVRTC and launched with the runtime's library API.
+ *
+ * Compared with the interpreter kernel (pbn_sim.cu), the state lives in registers,
+ * input gathers are constant shifts and masks, the selection thresholds and the
+ * levels of P are immediates, and merged tables of at most 64 bits are immediates
+ * too; larger tables are staged into shared memory by a bulk copy.  The step
+ * semantics (Eq. 1) and the keyed draws are identical, so the results are bit for
+ * bit those of the interpreter and of the unreduced definition.
+ *
+ * Compilation costs host time (tens to hundreds of milliseconds), which pays off
+ * for long runs of one network, as the paper observes for its own pre-processing
+ * (Sec. 4.1, Table 1).
+ */
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "pbn_device.cuh"
+#include "pbn_internal.h"
+
+namespace {
+
+const char kDeviceHeader[] =
+#include "pbn_device_cuh.inc"
+    ;
+
+/* ---- NVRTC, loaded on first use --------------------------------------------------- */
+typedef int nvrtcResult_t;
+typedef struct _nvrtcProgram* nvrtcProgram_t;
+struct Nvrtc {
+    nvrtcResult_t (*create)(nvrtcProgram_t*, const char*, const char*, int, const char* const*, const char* const*);
+    nvrtcResult_t (*compile)(nvrtcProgram_t, int, const char* const*);
+    nvrtcResult_t (*log_size)(nvrtcProgram_t, size_t*);
+    nvrtcResult_t (*log)(nvrtcProgram_t, char*);
+    nvrtcResult_t (*cubin_size)(nvrtcProgram_t, size_t*);
+    nvrtcResult_t (*cubin)(nvrtcProgram_t, char*);
+    nvrtcResult_t (*destroy)(nvrtcProgram_t*);
+    bool ok = false;
+    std::string err;
+};
+
+Nvrtc& nvrtc() {
+    static Nvrtc N;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char* names[] = {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                               "/usr/local/cuda/lib64/libnvrtc.so"};
+        void* h = nullptr;
+        for (const char* nm : names)
+            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) {
+            N.err = "libnvrtc not found";
+            return;
+        }
+#define PBN_SYM(field, name)                                          \
+    *reinterpret_cast<void**>(&N.field) = dlsym(h, name);             \
+    if (!N.field) {                                                   \
+        N.err = std::string("libnvrtc lacks ") + name;                \
+        return;                                                       \
+    }
+        PBN_SYM(create, "nvrtcCreateProgram");
+        PBN_SYM(compile, "nvrtcCompileProgram");
+        PBN_SYM(log_size, "nvrtcGetProgramLogSize");
+        PBN_SYM(log, "nvrtcGetProgramLog");
+        PBN_SYM(cubin_size, "nvrtcGetCUBINSize");
+        PBN_SYM(cubin, "nvrtcGetCUBIN");
+        PBN_SYM(destroy, "nvrtcDestroyProgram");
+#undef PBN_SYM
+        N.ok = true;
+    });
+    return N;
+}
+
+/* ---- plan decoding ------------------------------------------------------------------- */
+struct View {
+    const pbn_img_header* H;
+    const uint8_t* img;
+    template <class T>
+    const T* at(uint32_t off) const { return reinterpret_cast<const T*>(img + off); }
+};
+
+std::string hex32(uint32_t v) {
+    char b[16];
+    snprintf(b, sizeof b, "0x%08xu", v);
+    return b;
+}
+
+std::string fmt(const char* f, ...) {
+    char b[512];
+    va_list ap;
+    va_start(ap, f);
+    vsnprintf(b, sizeof b, f, ap);
+    va_end(ap);
+    return b;
+}
+
+/* Expression selecting bit `bit` of state word s<row> into position b. */
+std::string gather(uint32_t row, uint32_t bit, uint32_t b) {
+    if (bit == b) return fmt("(s%u & %s)", row, hex32(1u << b).c_str());
+    if (bit > b) return fmt("((s%u >> %u) & %s)", row, bit - b, hex32(1u << b).c_str());
+    return fmt("((s%u << %u) & %s)", row, b - bit, hex32(1u << b).c_str());
+}
+
+const char* lanes = "xyzw";
+
+struct Generated {
+    std::string src;
+    uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
+};
+
+bool generate(const pbn_plan& plan, Generated* out, std::string* why) {
+    View V{&plan.hdr, plan.image.data()};
+    const pbn_img_header& H = plan.hdr;
+    if (H.W32 > PBN_JIT_MAX_ROWS) {
+        *why = "state wider than 64 words";
+        return false;
+    }
+    if (H.W > 16) {
+        *why = "more than 1024 original nodes";
+        return false;
+    }
+    if (H.n_sel > 24) {
+        *why = "more than 24 selection blocks per step";
+        return false;
+    }
+    const uint2* words = V.at<uint2>(H.off_words);
+    const pbn_img_group* groups = V.at<pbn_img_group>(H.off_groups);
+    const pbn_img_multi* multi = V.at<pbn_img_multi>(H.off_multi);
+    const uint32_t* thr = V.at<uint32_t>(H.off_thr);
+    const uint32_t* inrec = V.at<uint32_t>(H.off_inputs);
+    const uint32_t* selblk = V.at<uint32_t>(H.off_selblk);
+    const uint64_t* ret = V.at<uint64_t>(H.off_ret);
+    const uint32_t* pos = V.at<uint32_t>(H.off_pos);
+    const uint32_t* tab = V.at<uint32_t>(H.off_tables);
+    const uint32_t table_bytes = H.image_bytes - H.off_tables;
+    const bool tab_smem = table_bytes <= 48u * 1024u;
+    out->tab_bytes = tab_smem ? table_bytes : 0u;
+
+    std::ostringstream o;
+    o << "#include \"pbn_device.cuh\"\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(512) pbn_plan_kernel(const pbn_jit_params P) {\n";
+    o << "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n";
+    if (tab_smem) {
+        o << "  if (!pbn_stage(smem, P.image + P.off_tables, P.tab_bytes, &bar)) {\n"
+             "    if (threadIdx.x == 0 && P.status) atomicOr(P.status, 1u);\n    return;\n  }\n"
+             "  const uint32_t* TAB = reinterpret_cast<const uint32_t*>(smem);\n";
+    } else {
+        o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(P.image + P.off_tables);\n";
+    }
+    o << "  const uint32_t lt = blockIdx.x * blockDim.x + threadIdx.x;\n"
+         "  const bool active = lt < P.n_traj;\n"
+         "  const uint64_t traj = P.traj_begin + lt;\n"
+         "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n";
+    o << "  uint32_t";
+    for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "s" << r << " = 0";
+    o << ";\n  if (active) {\n";
+    /* initial state */
+    o << "    if (P.init == 0) {\n      const pbn_philox_step ps = pbn_philox_begin(P, traj, 0);\n";
+    for (uint32_t pr = 0; 2 * pr < H.W; ++pr) {
+        const uint64_t r0 = ret[2 * pr], r1 = (2 * pr + 1 < H.W) ? ret[2 * pr + 1] : 0;
+        if (!(r0 | r1)) continue;
+        o << "      const uint4 I" << pr << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_INIT << 28) | pr) << ");\n";
+        for (uint32_t half = 0; half < 2; ++half) {
+            const uint32_t w = 2 * pr + half;
+            const uint64_t rw = half ? r1 : r0;
+            for (uint32_t b = 0; b < 64; ++b) {
+                if (!((rw >> b) & 1u)) continue;
+                const uint32_t ps = pos[64 * w + b], row = ps >> 5, bit = ps & 31;
+                const char comp = lanes[2 * half + (b >= 32 ? 1 : 0)];
+                o << fmt("      s%u |= ((I%u.%c >> %u) & 1u) << %u;\n", row, pr, comp, b & 31, bit);
+            }
+        }
+    }
+    o << "    } else {\n";
+    for (uint32_t r = 0; r < H.W32; r += 2)
+        o << "      { const uint64_t v = P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt]; s" << r
+          << " = (uint32_t)v; s" << r + 1 << " = (uint32_t)(v >> 32); }\n";
+    o << "    }\n";
+    /* meta indicator */
+    std::string z = "1u";
+    {
+        std::ostringstream zs;
+        zs << "(";
+        for (uint32_t r = 0; r < H.W32; ++r)
+            zs << (r ? " & " : "") << "(uint32_t)((s" << r << " & P.meta_mask[" << r << "]) == P.meta_val[" << r << "])";
+        zs << ")";
+        z = zs.str();
+    }
+    o << "    uint32_t zp = " << z << ";\n    if (P.count_first) cV += zp;\n";
+    o << "    for (uint32_t k = 0; k < P.n_steps; ++k) {\n"
+         "      const uint64_t t = P.step_begin + k;\n"
+         "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
+         "      uint32_t any = 0;\n";
+    /* 1. perturbation, levels of P compiled in */
+    const uint32_t Pv = H.P;
+    if (Pv) {
+        const uint32_t hmax = (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u;
+        for (uint32_t w = 0; w < H.W; ++w) {
+            const uint32_t nl = (w == H.W - 1) ? (H.n - 64 * w) : 64u;
+            const uint64_t valid = nl >= 64 ? ~0ull : ((1ull << nl) - 1ull);
+            o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
+              << ", pl = 0, ph = 0;\n";
+            for (uint32_t h = 0; h < hmax; ++h) {
+                const uint32_t b0 = (Pv >> (31 - 2 * h)) & 1u;
+                const uint32_t b1 = (Pv >> (30 - 2 * h)) & 1u;
+                o << "        if (ul | uh) { const uint4 x = pbn_philox_draw(P, ps, "
+                  << hex32((PBN_DOM_PERT << 28) | (w << 4) | h) << ");";
+                if (b0) o << " pl |= ul & ~x.x; ph |= uh & ~x.y; ul &= x.x; uh &= x.y;";
+                else o << " ul &= ~x.x; uh &= ~x.y;";
+                if (2 * h + 1 < 32) {
+                    if (b1) o << " pl |= ul & ~x.z; ph |= uh & ~x.w; ul &= x.z; uh &= x.w;";
+                    else o << " ul &= ~x.z; uh &= ~x.w;";
+                }
+                o << " }\n";
+            }
+            o << "        if (pl | ph) {\n          any = 1u;\n";
+            const uint32_t rl = (uint32_t)ret[w], rh = (uint32_t)(ret[w] >> 32);
+            for (int half = 0; half < 2; ++half) {
+                const uint32_t rm = half ? rh : rl;
+                if (!rm) continue;
+                o << "          uint32_t f" << half << " = " << (half ? "ph" : "pl") << " & " << hex32(rm) << ";\n"
+                  << "          while (f" << half << ") { const uint32_t b = __ffs(f" << half << ") - 1; f" << half
+                  << " &= f" << half << " - 1; switch (b) {\n";
+                for (uint32_t b = 0; b < 32; ++b) {
+                    if (!((rm >> b) & 1u)) continue;
+                    const uint32_t ps = pos[64 * w + 32 * half + b];
+                    o << "            case " << b << ": s" << (ps >> 5) << " ^= " << hex32(1u << (ps & 31)) << "; break;\n";
+                }
+                o << "          } }\n";
+            }
+            o << "        }\n      }\n";
+        }
+    }
+    /* 2. selection draws and merged-table evaluation */
+    o << "      if (!any) {\n";
+    for (uint32_t i = 0; i < H.n_sel; ++i)
+        o << "        const uint4 U" << i << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
+    for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
+    for (uint32_t r = 0; r < H.W32; ++r) {
+        for (uint32_t gi = words[r].x; gi < words[r].x + words[r].y; ++gi) {
+            const pbn_img_group& G = groups[gi];
+            o << "        { ";
+            /* combined choice */
+            std::string cexpr;
+            for (uint32_t m = 0; m < G.n_mul; ++m) {
+                const pbn_img_multi& M = multi[G.mul_first + m];
+                const uint32_t slot = (M.u_off & 0xFFFFFFu) / 4u;
+                const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
+                const uint32_t n_thr = M.u_off >> 24;
+                std::string j;
+                for (uint32_t q = 0; q < n_thr; ++q) {
+                    const uint32_t T = n_thr <= 2 ? (q == 0 ? M.t1 : M.t2) : thr[M.t1 + q];
+                    j += (q ? " + " : "") + fmt("(uint32_t)(%s >= %s)", u.c_str(), hex32(T).c_str());
+                }
+                if (j.empty()) continue;
+                cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
+            }
+            /* input pattern */
+            std::string xexpr;
+            const uint32_t q = G.q;
+            for (uint32_t b = 0; b < q; ++b) {
+                const uint32_t rec = inrec[4 * G.in_chunk + b];
+                const uint32_t row = rec >> 7, bit = ((b & 3) + (rec & 31)) & 31;
+                xexpr += (b ? " | " : "") + gather(row, bit, b);
+            }
+            if (xexpr.empty()) xexpr = "0u";
+            o << "const uint32_t x = " << xexpr << "; ";
+            if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
+            else o << "const uint32_t e = x; ";
+            /* table entry */
+            const uint32_t l2w = G.l2w;
+            const uint32_t ebits = 1u << l2w;
+            const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
+            /* size of this group's table in bits: from the next group's offset, or the end */
+            uint32_t next_off = table_bytes / 4;
+            for (uint32_t g2 = 0; g2 < H.n_groups; ++g2)
+                if (groups[g2].tab_off > G.tab_off && groups[g2].tab_off < next_off) next_off = groups[g2].tab_off;
+            const uint32_t tab_words = next_off - G.tab_off;
+            std::string v;
+            if (tab_words == 1) {
+                v = fmt("((%s >> (e << %u)) & %s)", hex32(tab[G.tab_off]).c_str(), l2w, hex32(emask).c_str());
+            } else if (tab_words == 2) {
+                const uint64_t t64 = ((uint64_t)tab[G.tab_off + 1] << 32) | tab[G.tab_off];
+                v = fmt("((uint32_t)(0x%016llxull >> (e << %u)) & %s)", (unsigned long long)t64, l2w, hex32(emask).c_str());
+            } else if (tab_smem) {
+                v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w, hex32(emask).c_str());
+            } else {
+                v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w,
+                        hex32(emask).c_str());
+            }
+            o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
+        }
+    }
+    for (uint32_t r = 0; r < H.W32; ++r) o << "        s" << r << " = n" << r << ";\n";
+    o << "      }\n";
+    /* 3. counts */
+    o << "      { const uint32_t z = " << z << ";\n"
+         "        const uint32_t cv = k >= P.kv0 ? 1u : 0u, cp = k >= P.kp0 ? 1u : 0u;\n"
+         "        cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u); zp = z; }\n";
+    o << "      if (P.trace) {\n";
+    for (uint32_t r = 0; r < H.W32; r += 2)
+        o << "        P.trace[((uint64_t)k * " << H.W32 / 2 << "u + " << r / 2 << "u) * P.n_traj + lt] = ((uint64_t)s"
+          << r + 1 << " << 32) | s" << r << ";\n";
+    o << "      }\n    }\n";
+    /* epilogue */
+    for (uint32_t r = 0; r < H.W32; r += 2)
+        o << "    P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt] = ((uint64_t)s" << r + 1 << " << 32) | s" << r << ";\n";
+    o << "    if (P.counts) {\n"
+         "      const uint64_t nt = P.n_traj;\n"
+         "      P.counts[lt] += cV; P.counts[nt + lt] += P.pairs - c01 - c10 - c11;\n"
+         "      P.counts[2 * nt + lt] += c01; P.counts[3 * nt + lt] += c10; P.counts[4 * nt + lt] += c11;\n"
+         "    }\n  }\n";
+    o << "  if (P.pooled) {\n"
+         "    uint64_t v[5] = {active ? cV : 0u, active ? (uint64_t)(P.pairs - c01 - c10 - c11) : 0u,\n"
+         "                     active ? c01 : 0u, active ? c10 : 0u, active ? c11 : 0u};\n"
+         "#pragma unroll\n    for (int i = 0; i < 5; ++i) {\n"
+         "#pragma unroll\n      for (int d = 16; d > 0; d >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], d);\n    }\n"
+         "    if ((threadIdx.x & 31u) == 0) {\n"
+         "      for (int i = 0; i < 5; ++i) if (v[i]) atomicAdd(P.pooled + i, (unsigned long long)v[i]);\n    }\n  }\n";
+    o << "}\n";
+    out->src = o.str();
+    return true;
+}
+
+}  // namespace
+
+/* ---- compiled-plan cache and launch (called from pbn_sim.cu and the C ABI) --------- */
+struct pbn_jit_state {
+    std::mutex mu;
+    int state = 0;  /* 0: not tried, 1: compiled, -1: failed */
+    std::string log;
+    std::string src;
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    uint32_t tab_bytes = 0;
+    double compile_ms = 0;
+};
+
+namespace pbn {
+
+pbn_jit_state* jit_state(const pbn_plan* plan) {
+    static std::mutex g;
+    std::lock_guard<std::mutex> lk(g);
+    if (!plan->jit) plan->jit = new pbn_jit_state();
+    return plan->jit;
+}
+
+void jit_free(pbn_jit_state* J) {
+    if (!J) return;
+    if (J->lib) cudaLibraryUnload(J->lib);
+    delete J;
+}
+
+int jit_compile(const pbn_plan* plan) {
+    pbn_jit_state* J = jit_state(plan);
+    std::lock_guard<std::mutex> g(J->mu);
+    if (J->state == 1) return PBN_OK;
+    if (J->state == -1) return fail(PBN_EINVAL, "plan compilation failed earlier: %s", J->log.c_str());
+    Generated gen;
+    std::string why;
+    if (!generate(*plan, &gen, &why)) {
+        J->state = -1;
+        J->log = why;
+        return fail(PBN_EINVAL, "plan cannot be compiled: %s", why.c_str());
+    }
+    Nvrtc& N = nvrtc();
+    if (!N.ok) {
+        J->state = -1;
+        J->log = N.err;
+        return fail(PBN_ECUDA, "NVRTC unavailable: %s", N.err.c_str());
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    nvrtcProgram_t prog = nullptr;
+    const char* hdrs[] = {kDeviceHeader};
+    const char* hnames[] = {"pbn_device.cuh"};
+    if (N.create(&prog, gen.src.c_str(), "pbn_plan_kernel.cu", 1, hdrs, hnames) != 0) {
+        J->state = -1;
+        J->log = "nvrtcCreateProgram failed";
+        return fail(PBN_ECUDA, "nvrtcCreateProgram failed");
+    }
+    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
+    const int rc = N.compile(prog, 3, opts);
+    size_t ls = 0;
+    N.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) N.log(prog, &log[0]);
+    if (rc != 0) {
+        N.destroy(&prog);
+        J->state = -1;
+        J->log = log;
+        return fail(PBN_ECUDA, "NVRTC compilation failed: %.400s", log.c_str());
+    }
+    size_t cs = 0;
+    N.cubin_size(prog, &cs);
+    std::vector<char> cubin(cs);
+    N.cubin(prog, cubin.data());
+    N.destroy(&prog);
+    cudaError_t e = cudaLibraryLoadData(&J->lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&J->kern, J->lib, "pbn_plan_kernel");
+    if (e != cudaSuccess) {
+        J->state = -1;
+        J->log = cudaGetErrorString(e);
+        return fail(PBN_ECUDA, "loading the compiled plan failed: %s", cudaGetErrorString(e));
+    }
+    J->tab_bytes = gen.tab_bytes;
+    J->src = std::move(gen.src);
+    J->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    J->state = 1;
+    return PBN_OK;
+}
+
+bool jit_ready(const pbn_plan* plan) {
+    pbn_jit_state* J = jit_state(plan);
+    std::lock_guard<std::mutex> g(J->mu);
+    return J->state == 1;
+}
+
+int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms, cudaStream_t st) {
+    pbn_jit_state* J = jit_state(plan);
+    if (!jit_ready(plan)) return fail(PBN_EINVAL, "plan is not compiled");
+    P->tab_bytes = J->tab_bytes;
+    uint64_t per_sm = (n_traj + (uint64_t)sms - 1) / (uint64_t)sms;
+    uint64_t tpb = ((per_sm + 31) / 32) * 32;
+    if (tpb > 512) tpb = 512;
+    if (tpb < 64) tpb = 64;
+    const uint64_t grid = (n_traj + tpb - 1) / tpb;
+    void* args[] = {P};
+    cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(J->kern), dim3((unsigned)grid), dim3((unsigned)tpb), args,
+                                     J->tab_bytes, st);
+    if (e != cudaSuccess) return fail(PBN_ECUDA, "compiled plan launch: %s", cudaGetErrorString(e));
+    return PBN_OK;
+}
+
+}  // namespace pbn
+
+extern "C" int pbn_plan_compile(const pbn_plan* plan, double* compile_ms) {
+    if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
+    const int rc = pbn::jit_compile(plan);
+    if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;
+    return rc;
+}
+
+extern "C" int pbn_plan_source(const pbn_plan* plan, char* dst, size_t cap, size_t* len) {
+    if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_source: NULL plan");
+    Generated gen;
+    std::string why;
+    if (!generate(*plan, &gen, &why)) return pbn::fail(PBN_EINVAL, "plan cannot be compiled: %s", why.c_str());
+    if (len) *len = gen.src.size();
+    if (dst) {
+        if (cap < gen.src.size() + 1) return pbn::fail(PBN_EINVAL, "pbn_plan_source: need %zu bytes", gen.src.size() + 1);
+        memcpy(dst, gen.src.c_str(), gen.src.size() + 1);
+    }
+    return PBN_OK;
+}

@@ -29,17 +29,15 @@
 #include <cstdint>
 #include <cstring>
 
+#include "pbn_device.cuh"
 #include "pbn_internal.h"
 
 namespace {
 
-constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
-constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
 constexpr uint32_t kWeyl0 = 0x9E3779B9u;
 constexpr uint32_t kWeyl1 = 0xBB67AE85u;
-constexpr uint32_t kDomPert = 1u, kDomSel = 2u, kDomInit = 3u;
+constexpr uint32_t kDomPert = PBN_DOM_PERT, kDomSel = PBN_DOM_SEL, kDomInit = PBN_DOM_INIT;
 constexpr int kMaxMetaRows = 16;
-constexpr uint32_t kStageWaitLimit = 1u << 22;
 
 struct SimParams {
     const uint8_t* image;      /* device copy of the plan image */
@@ -63,6 +61,7 @@ struct SimParams {
     uint32_t stage_bytes;      /* image bytes staged into shared memory */
     uint32_t image_bytes;      /* total image bytes (checked against the header) */
     uint32_t smem_state_off;   /* byte offset of the state rows in dynamic smem */
+    uint32_t hmax;             /* level pairs that can still decide a perturbation */
     uint32_t n, W, W32, n_sel, P;
     uint32_t off_words, off_groups, off_multi, off_thr, off_inputs, off_selblk, off_ret, off_pos, off_tables;
     uint32_t n_meta_rows;
@@ -70,90 +69,6 @@ struct SimParams {
     uint32_t meta_mask[kMaxMetaRows];
     uint32_t meta_val[kMaxMetaRows];
 };
-
-/* ---- Philox4x32-10 ------------------------------------------------------------
- * Round: (x0, x1, x2, x3) -> (hi(M1 x2) ^ x1 ^ k0, lo(M1 x2), hi(M0 x0) ^ x3 ^ k1,
- * lo(M0 x0)); the key is bumped by the Weyl constants between rounds.  Within one
- * (trajectory, step) the counter words c0, c1, c2 are fixed and only c3 (domain,
- * index) changes, and c3 enters round 1 only through an XOR, so round 1's products
- * are computed once per step. */
-struct PhiloxStep {
-    uint32_t y0, y1, y2_base, y3;
-};
-
-__device__ __forceinline__ PhiloxStep philox_step(const SimParams& P, uint64_t traj, uint64_t t) {
-    const uint32_t c0 = (uint32_t)traj;
-    const uint32_t c1 = (uint32_t)t;
-    const uint32_t c2 = (uint32_t)((t >> 32) & 0xFFFFu) | ((uint32_t)((traj >> 32) & 0xFFFFu) << 16);
-    PhiloxStep s;
-    s.y0 = __umulhi(kPhiloxM1, c2) ^ c1 ^ P.key0[0];
-    s.y1 = kPhiloxM1 * c2;
-    s.y2_base = __umulhi(kPhiloxM0, c0) ^ P.key1[0];
-    s.y3 = kPhiloxM0 * c0;
-    return s;
-}
-
-__device__ __forceinline__ uint4 philox_draw(const SimParams& P, const PhiloxStep& s, uint32_t c3) {
-    uint32_t x0 = s.y0, x1 = s.y1, x2 = s.y2_base ^ c3, x3 = s.y3;
-#pragma unroll
-    for (int r = 1; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)kPhiloxM0 * x0;
-        const uint64_t p1 = (uint64_t)kPhiloxM1 * x2;
-        x0 = (uint32_t)(p1 >> 32) ^ x1 ^ P.key0[r];
-        x2 = (uint32_t)(p0 >> 32) ^ x3 ^ P.key1[r];
-        x1 = (uint32_t)p1;
-        x3 = (uint32_t)p0;
-    }
-    return make_uint4(x0, x1, x2, x3);
-}
-
-/* ---- mbarrier + bulk copy (global -> shared), inline PTX ------------------------ */
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile(
-        "{\n\t.reg .b64 st;\n\t"
-        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
-        "r"(bytes)
-        : "memory");
-}
-
-__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-/* Bounded wait for phase 0 of the staging barrier. */
-__device__ __forceinline__ bool stage_wait(uint64_t* bar) {
-    for (uint32_t it = 0; it < kStageWaitLimit; ++it) {
-        if (mbar_try_wait(bar, 0)) return true;
-        if (it > 64) __nanosleep(128);
-    }
-    return false;
-}
 
 template <int LG>
 __device__ __forceinline__ uint32_t group_mask() {
@@ -185,19 +100,8 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
     __shared__ __align__(8) uint64_t stage_bar;
 
     /* ---- stage the plan image into shared memory (bulk copy, bounded wait) ---- */
-    if (threadIdx.x == 0) mbar_init(&stage_bar, 1);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(&stage_bar, P.stage_bytes);
-        for (uint32_t off = 0; off < P.stage_bytes; off += 65536u) {
-            const uint32_t sz = min(65536u, P.stage_bytes - off);
-            bulk_copy_g2s(smem + off, P.image + off, sz, &stage_bar);
-        }
-    }
-    const bool staged = stage_wait(&stage_bar);
-    if (__syncthreads_or(!staged)) {
+    if (!pbn_stage(smem, P.image, P.stage_bytes, &stage_bar)) {
         if (threadIdx.x == 0 && P.status) atomicOr(P.status, PBN_DEV_STAGE_TIMEOUT);
-        stage_wait(&stage_bar); /* let copies in flight land before the CTA exits */
         return;
     }
     const pbn_img_header* hdr = reinterpret_cast<const pbn_img_header*>(smem);
@@ -247,9 +151,9 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
         }
         group_sync<LG>();
         if (P.init == 0) {
-            const PhiloxStep ps = philox_step(P, traj, 0);
+            const pbn_philox_step ps = pbn_philox_begin(P, traj, 0);
             for (uint32_t w = lane; w < P.W; w += LG) {
-                const uint4 x = philox_draw(P, ps, (kDomInit << 28) | (w >> 1));
+                const uint4 x = pbn_philox_draw(P, ps, (kDomInit << 28) | (w >> 1));
                 uint64_t word = (w & 1u) ? (((uint64_t)x.w << 32) | x.z) : (((uint64_t)x.y << 32) | x.x);
                 word &= RET[w];
                 while (word) {
@@ -282,7 +186,7 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
 
         for (uint32_t k = 0; k < P.n_steps; ++k) {
             const uint64_t t = P.step_begin + k;
-            const PhiloxStep ps = philox_step(P, traj, t);
+            const pbn_philox_step ps = pbn_philox_begin(P, traj, t);
             uint32_t* Sc = S0 + cur * bufstride;
 
             /* ---- 1. perturbation: bit-sliced u < P, most significant level first,
@@ -294,8 +198,8 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
                     uint32_t und_lo = (uint32_t)valid, und_hi = (uint32_t)(valid >> 32);
                     uint32_t pert_lo = 0, pert_hi = 0;
                     uint32_t pp = P.P; /* level 2h uses bit 31 of pp, level 2h+1 bit 30 */
-                    for (uint32_t h = 0; h < 16u && (und_lo | und_hi); ++h) {
-                        const uint4 x = philox_draw(P, ps, (kDomPert << 28) | (w << 4) | h);
+                    for (uint32_t h = 0; h < P.hmax && (und_lo | und_hi); ++h) {
+                        const uint4 x = pbn_philox_draw(P, ps, (kDomPert << 28) | (w << 4) | h);
                         const uint32_t m0 = (uint32_t)((int32_t)pp >> 31);
                         const uint32_t m1 = (uint32_t)((int32_t)(pp << 1) >> 31);
                         pp <<= 2;
@@ -330,15 +234,15 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
                 /* ---- 2a. selection draws of the retained multi-function nodes ---- */
                 uint32_t i = lane;
                 for (; i + LG < P.n_sel; i += 2 * LG) {
-                    const uint4 x = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
-                    const uint4 y = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i + LG]);
+                    const uint4 x = pbn_philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
+                    const uint4 y = pbn_philox_draw(P, ps, (kDomSel << 28) | SELBLK[i + LG]);
                     uint32_t* a = Ut + 4 * i;
                     uint32_t* b = Ut + 4 * (i + LG);
                     a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
                     b[0] = y.x; b[1] = y.y; b[2] = y.z; b[3] = y.w;
                 }
                 if (i < P.n_sel) {
-                    const uint4 x = philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
+                    const uint4 x = pbn_philox_draw(P, ps, (kDomSel << 28) | SELBLK[i]);
                     uint32_t* a = Ut + 4 * i;
                     a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
                 }
@@ -495,6 +399,10 @@ int device_sm_count() {
 
 }  // namespace
 
+namespace pbn {
+int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms, cudaStream_t st);
+}
+
 extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn_sim_args* a, void* stream) {
     using pbn::fail;
     if (!plan || !a) return fail(PBN_EINVAL, "pbn_simulate: NULL argument");
@@ -507,6 +415,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     if (a->step_begin + a->n_steps > (1ull << 48)) return fail(PBN_EINVAL, "pbn_simulate: step indices must be < 2^48");
     if (a->init != PBN_INIT_KEYED && a->init != PBN_INIT_STATE) return fail(PBN_EINVAL, "pbn_simulate: bad init mode");
     if (a->init == PBN_INIT_KEYED && a->step_begin != 0) return fail(PBN_EINVAL, "pbn_simulate: keyed initial state needs step_begin == 0");
+    if (a->kernel > PBN_KERNEL_COMPILED) return fail(PBN_EINVAL, "pbn_simulate: unknown kernel selector %u", a->kernel);
     if (a->n_meta < 1 || a->n_meta > 1024 || !a->meta_ids) return fail(PBN_EINVAL, "pbn_simulate: need 1..1024 meta-state nodes");
     if (a->d_trace && a->n_steps * (uint64_t)plan->info.state_words * a->n_traj >= (1ull << 40))
         return fail(PBN_EINVAL, "pbn_simulate: trace too large");
@@ -577,9 +486,48 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.stage_bytes = H.stage_bytes;
     P.image_bytes = H.image_bytes;
     P.smem_state_off = (H.stage_bytes + 127u) & ~127u;
+    /* levels after the last set bit of P only retire lanes: the outcome is fixed */
+    P.hmax = H.P ? (31u - (uint32_t)__builtin_ctz(H.P)) / 2u + 1u : 0u;
+
+    const int sms = device_sm_count();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (a->kernel == PBN_KERNEL_COMPILED) {
+        const int rc = pbn::jit_compile(plan);
+        if (rc) return rc;
+    }
+    if (a->kernel == PBN_KERNEL_COMPILED ||
+        (a->kernel == PBN_KERNEL_AUTO && a->lanes_per_traj <= 1 && a->trajs_per_block == 0 && pbn::jit_ready(plan))) {
+        pbn_jit_params J;
+        memset(&J, 0, sizeof(J));
+        J.image = P.image;
+        J.state = P.state;
+        J.counts = P.counts;
+        J.pooled = P.pooled;
+        J.status = P.status;
+        J.trace = P.trace;
+        J.traj_begin = P.traj_begin;
+        J.step_begin = P.step_begin;
+        memcpy(J.key0, P.key0, sizeof(J.key0));
+        memcpy(J.key1, P.key1, sizeof(J.key1));
+        J.n_traj = P.n_traj;
+        J.n_steps = P.n_steps;
+        J.kv0 = P.kv0;
+        J.kp0 = P.kp0;
+        J.pairs = P.pairs;
+        J.count_first = P.count_first;
+        J.init = P.init;
+        J.off_tables = P.off_tables;
+        J.off_ret = P.off_ret;
+        J.off_pos = P.off_pos;
+        J.image_bytes = P.image_bytes;
+        for (uint32_t m = 0; m < P.n_meta_rows; ++m) {
+            J.meta_mask[P.meta_row[m]] = P.meta_mask[m];
+            J.meta_val[P.meta_row[m]] = P.meta_val[m];
+        }
+        return pbn::jit_launch(plan, &J, P.n_traj, sms, st);
+    }
 
     /* launch shape: lanes per trajectory and trajectory slots per CTA */
-    const int sms = device_sm_count();
     const size_t smem_lim = (size_t)device_smem_limit();
     uint32_t LG = a->lanes_per_traj;
     if (LG == 0) {
@@ -618,7 +566,6 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     if (smem > smem_lim) return fail(PBN_ETOOBIG, "pbn_simulate: %zu bytes of shared memory exceed the device limit", smem);
     P.nt = nt;
     const uint64_t grid = (a->n_traj + nt - 1) / nt;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     const bool tr = a->d_trace != nullptr;
     const bool ts = H.tables_in_smem != 0;

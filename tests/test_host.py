@@ -308,3 +308,41 @@ def test_estimate_rejects_bad_arguments():
         api.estimate([1, 2, 3, 4, 5], 1, 0.0, 0.95)
     with pytest.raises(_lib.PbnError):
         api.estimate([1, 2, 3, 4, 5], 1, 0.01, 1.0)
+
+
+# ------------------------------------------------------------ compiled plans ----
+@pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half"])
+def test_generated_plan_kernels_compile(tmp_path, which):
+    """The source generated for a plan's own kernel compiles for sm_103a."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    if which.startswith("paper100"):
+        text, meta = synth.paper100(seed=2).to_text(), [0, 1, 2]
+    elif which == "tiny12":
+        text, meta = synth.tiny12(1).to_text(), [0, 1, 2]
+    elif which == "p0":
+        text, meta = synth.paper100(seed=9, n=70, p=0.0).to_text(), [0, 1]
+    elif which == "p_half":
+        text, meta = synth.paper100(seed=9, n=70, p=0.5).to_text(), [0, 1]
+    else:
+        text, meta = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n", [0]
+    red, _ = api.Net.load(text).reduce(meta)
+    plan = api.Plan(red, mode=1 if which.endswith("plain") else 0)
+    (tmp_path / "k.cu").write_text(plan.source())
+    shutil.copy(os.path.join(ROOT, "paper_1605_00854_gb300", "csrc", "pbn_device.cuh"), tmp_path)
+    proc = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c",
+                           str(tmp_path / "k.cu"), "-o", str(tmp_path / "k.o")],
+                          capture_output=True, text=True)
+    assert proc.returncode == 0, proc.stderr[-3000:]
+
+
+def test_large_plans_are_not_compiled():
+    net = synth.scalefree2000(seed=3)
+    red, _ = api.Net.load(net.to_text()).reduce([0, 1, 2, 3])
+    plan = api.Plan(red)
+    with pytest.raises(_lib.PbnError) as e:
+        plan.source()
+    assert e.value.status == -1
