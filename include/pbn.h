@@ -155,6 +155,13 @@ typedef struct {
     uint32_t total_inputs;   /* sum over groups of their distinct inputs */
     uint32_t n_multi;        /* retained nodes with >= 2 functions */
     uint32_t total_thresholds; /* selection thresholds below 2^32 over those nodes */
+    double ops_per_step;     /* algorithmic 32-bit integer operations of one trajectory-step:
+                                Philox blocks at 56 ops (9 rounds of 2 mul.hi, 2 mul.lo,
+                                2 xor3), 12 per bit-sliced level pair, the expected number of
+                                level pairs until every lane of each 64-node word is decided;
+                                weighted by the probability (1-p')^n of an unperturbed step:
+                                56 per SEL block, 2 per threshold, 1 per multi-function node,
+                                3 per group input, 5 per group, 2 per state word; 8 for counts */
 } pbn_plan_info;
 
 /* Errors: PBN_EINVAL. */
@@ -236,6 +243,64 @@ int pbn_plan_compile(const pbn_plan* plan, double* compile_ms);
  * dst (capacity cap, may be NULL) receives it NUL-terminated.
  * Errors: PBN_EINVAL (plan not compilable, cap too small). */
 int pbn_plan_source(const pbn_plan* plan, char* dst, size_t cap, size_t* len);
+
+/* ---- batched form: many networks, one persistent launch ------------------------------ */
+typedef struct pbn_batch pbn_batch;
+
+typedef struct {
+    const pbn_plan* plan;      /* plan of this network (kept alive by the caller) */
+    const void* d_image;       /* caller's 16-byte aligned device copy of pbn_plan_image(plan) */
+    uint64_t seed;             /* Philox key of this network's draws */
+    uint64_t traj_begin;       /* global id of its first trajectory (< 2^48) */
+    uint64_t n_traj;           /* trajectories (1 .. 2^31 - 1) */
+    uint64_t step_begin;       /* index of its first step */
+    uint64_t count_from;       /* states s(u) with u >= count_from are counted */
+    uint32_t init;             /* PBN_INIT_KEYED (step_begin must be 0) or PBN_INIT_STATE */
+    uint32_t n_meta;           /* meta-state nodes (1..1024, retained, within 16 state words) */
+    const uint32_t* meta_ids;  /* host */
+    const uint8_t* meta_vals;  /* host, NULL = all 1 */
+    void* d_state;             /* device uint64 [state_words][n_traj] */
+    void* d_counts;            /* device uint64 [5][n_traj] or NULL (accumulated) */
+    void* d_pooled;            /* device uint64 [5] or NULL (accumulated) */
+} pbn_batch_net;
+
+typedef struct {
+    uint32_t n_nets;
+    uint32_t n_items;          /* work items (up to `threads` trajectories of one network) */
+    uint32_t threads;          /* threads per CTA = trajectories per work item */
+    uint32_t reserved;
+    uint64_t desc_bytes;       /* bytes of pbn_batch_image */
+    uint64_t smem_bytes;       /* dynamic shared memory per CTA */
+    double est_ops_per_step;   /* sum over networks of n_traj x ops_per_step */
+} pbn_batch_info;
+
+/* Describe a batch of networks for the persistent work-queue kernel: each network
+ * is cut into work items of up to `threads` trajectories and the items are ordered
+ * by descending estimated work.  The networks' plans and device buffers must stay
+ * valid while the batch is used.  On success *out owns the batch (pbn_batch_free).
+ * Errors: PBN_EINVAL (missing or misaligned buffer, range, meta node), PBN_ETOOBIG
+ * (a network's specs and trajectory rows exceed the per-CTA shared memory),
+ * PBN_ENOMEM. */
+int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out);
+int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
+
+/* Serialise the batch's device table (network descriptors, then work items) into
+ * host memory (cap >= desc_bytes); the caller copies it to a 16-byte aligned device
+ * buffer.  Errors: PBN_EINVAL. */
+int pbn_batch_image(const pbn_batch* batch, void* host_dst, size_t cap);
+
+/* One persistent launch on `stream`: every network advances n_steps steps, from
+ * step_begin + step_offset (keyed initial states only when step_offset == 0), with
+ * the same results as pbn_simulate on each network alone.  d_queue is caller scratch
+ * of two uint32 counters (the next work item and the CTAs that found the queue
+ * empty) that must be zero before the first launch; the last CTA of every launch
+ * resets them, so launches can follow each other (or be captured in a CUDA graph)
+ * without a reset.  Launches sharing one d_queue must not overlap.  ctas_per_sm = 0
+ * uses the occupancy limit.  d_status (may be NULL) receives PBN_DEV_* bits.
+ * Errors: PBN_EINVAL, PBN_ETOOBIG, PBN_ECUDA. */
+int pbn_batch_run(const pbn_batch* batch, const void* d_desc, uint32_t* d_queue, uint64_t step_offset,
+                  uint64_t n_steps, uint32_t ctas_per_sm, uint32_t* d_status, void* stream);
+void pbn_batch_free(pbn_batch* batch);
 
 /* ---- estimation ------------------------------------------------------------------ */
 typedef struct {

@@ -41,7 +41,20 @@ class PlanInfo(ctypes.Structure):
                 ("state_words", u32), ("n_sel_blocks", u32), ("m_lower_bound", u32),
                 ("m_found", u32), ("sum_weights", u64), ("table_bytes", u64),
                 ("image_bytes", u64), ("stage_bytes", u64), ("tables_in_smem", u32),
-                ("total_inputs", u32), ("n_multi", u32), ("total_thresholds", u32)]
+                ("total_inputs", u32), ("n_multi", u32), ("total_thresholds", u32),
+                ("ops_per_step", f64)]
+
+
+class BatchNet(ctypes.Structure):
+    _fields_ = [("plan", vp), ("d_image", vp), ("seed", u64), ("traj_begin", u64), ("n_traj", u64),
+                ("step_begin", u64), ("count_from", u64), ("init", u32), ("n_meta", u32),
+                ("meta_ids", vp), ("meta_vals", vp), ("d_state", vp), ("d_counts", vp),
+                ("d_pooled", vp)]
+
+
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("n_nets", u32), ("n_items", u32), ("threads", u32), ("reserved", u32),
+                ("desc_bytes", u64), ("smem_bytes", u64), ("est_ops_per_step", f64)]
 
 
 class SimArgs(ctypes.Structure):
@@ -71,6 +84,11 @@ SIGNATURES = {
     "pbn_plan_groups": (i32, [vp, vp]),
     "pbn_simulate": (i32, [vp, vp, ctypes.POINTER(SimArgs), vp]),
     "pbn_plan_compile": (i32, [vp, ctypes.POINTER(f64)]),
+    "pbn_batch_create": (i32, [ctypes.POINTER(BatchNet), u32, ctypes.POINTER(vp)]),
+    "pbn_batch_info_get": (i32, [vp, ctypes.POINTER(BatchInfo)]),
+    "pbn_batch_image": (i32, [vp, vp, ctypes.c_size_t]),
+    "pbn_batch_run": (i32, [vp, vp, vp, u64, u64, u32, vp, vp]),
+    "pbn_batch_free": (None, [vp]),
     "pbn_plan_source": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "pbn_estimate": (i32, [vp, u64, u64, f64, f64, f64, ctypes.POINTER(EstimateOut)]),
     "pbn_strerror": (cp, [i32]),

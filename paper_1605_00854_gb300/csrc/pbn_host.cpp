@@ -713,6 +713,21 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     I.total_inputs = (uint32_t)total_inputs;
     I.n_multi = (uint32_t)mrec.size();
     I.total_thresholds = (uint32_t)thr.size();
+    /* algorithmic work of one trajectory-step (the roofline's per-unit figure) */
+    {
+        const double pe = (double)H.P / 4294967296.0;
+        double blocks = 0.0;
+        if (H.P) {
+            for (uint32_t w = 0; w < W; ++w) {
+                const uint32_t k = (w == W - 1 && (n & 63u)) ? (n & 63u) : 64u;
+                for (int h = 0; h < 16; ++h) blocks += 1.0 - std::pow(1.0 - std::ldexp(1.0, -2 * h), (double)k);
+            }
+        }
+        const double pert = blocks * (56.0 + 12.0) + 4.0;
+        const double nonpert = 56.0 * H.n_sel + 2.0 * (double)thr.size() + (double)mrec.size() +
+                               3.0 * (double)total_inputs + 5.0 * (double)H.n_groups + 2.0 * (double)(W32 / 2);
+        I.ops_per_step = pert + std::pow(1.0 - pe, (double)n) * nonpert + 8.0;
+    }
     return PBN_OK;
 }
 

@@ -1,0 +1,289 @@
+/*
+ * pbn_interp.cuh -- the interpreter's per-trajectory simulation loop (Algorithm 5,
+ * ParallelSimulation, with the step semantics of Eq. 1), shared by the
+ * single-network kernel (pbn_sim.cu) and the batched work-queue kernel
+ * (pbn_batch.cu).
+ *
+ * Per CTA the staged plan image sits at the start of shared memory; each
+ * trajectory slot owns two state buffers of W32 + 1 32-bit words (the last one
+ * always zero; odd stride, so a warp reading one row of 32 slots hits 32 banks)
+ * and a row of 4 * n_sel + 1 SEL uniforms.  Per step:
+ *   1. perturbation (Sec. 3.2, Step 2): every original 64-node word draws its
+ *      Bernoulli(P / 2^32) lanes bit-sliced, most significant level first, and
+ *      stops once every lane is decided or no later level can change the outcome.
+ *      Any set lane means a perturbed step (leaves included, which replaces
+ *      Algorithm 1's single draw); the set lanes of retained nodes are flipped.
+ *   2. otherwise (Sec. 3.3, Step 3): the SEL blocks of the retained multi-function
+ *      nodes are drawn; for every group the combined choice c (mixed radix), the
+ *      input pattern x (4-input chunks) and the table entry T[c][x] give the
+ *      group's new bits, ORed into the next state at the group's offset (cum).
+ *   3. the meta-state indicator z of the new state updates V, n01, n10, n11.
+ */
+#ifndef PBN_INTERP_CUH
+#define PBN_INTERP_CUH
+
+#include "pbn_device.cuh"
+#include "pbn_image.h"
+
+template <int LG>
+__device__ __forceinline__ uint32_t group_mask() {
+    if (LG == 32) return 0xFFFFFFFFu;
+    const uint32_t lane = threadIdx.x & 31u;
+    return ((1u << LG) - 1u) << (lane & ~(uint32_t)(LG - 1));
+}
+
+template <int LG>
+__device__ __forceinline__ void group_sync() {
+    if (LG > 1) __syncwarp(group_mask<LG>());
+}
+
+template <int LG>
+__device__ __forceinline__ void xor_bit(uint32_t* w, uint32_t bit) {
+    if (LG == 1) *w ^= bit;
+    else atomicXor(w, bit);
+}
+
+template <int LG>
+__device__ __forceinline__ void or_bit(uint32_t* w, uint32_t bit) {
+    if (LG == 1) *w |= bit;
+    else atomicOr(w, bit);
+}
+
+/* Simulate one trajectory slot of a CTA for P.n_steps steps (Algorithm 5 with
+ * Eq. 1 semantics): initial or loaded state, per-step perturbation, selection and
+ * merged-table evaluation, meta-state counts; writes the final state and the
+ * per-trajectory counts and returns the four counters (V, n01, n10, n11) in out[]
+ * for the caller's pooled reduction.  `smem` holds the staged plan image; the
+ * trajectory rows start at smem_state_off.  VT is any type with the fields of
+ * the launch parameters (kernel parameters or a per-network descriptor). */
+template <int LG, bool TRACE, bool TAB_SMEM, class VT>
+__device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint32_t smem_state_off, uint32_t NT,
+                                               uint32_t slot, uint32_t lane, uint64_t lt, bool active,
+                                               uint32_t out[4]) {
+    const uint2* WORDS = reinterpret_cast<const uint2*>(smem + P.off_words);
+    const uint4* GROUPS = reinterpret_cast<const uint4*>(smem + P.off_groups);
+    const uint4* MULTI = reinterpret_cast<const uint4*>(smem + P.off_multi);
+    const uint32_t* THR = reinterpret_cast<const uint32_t*>(smem + P.off_thr);
+    const uint4* INPUTS = reinterpret_cast<const uint4*>(smem + P.off_inputs);
+    const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(smem + P.off_selblk);
+    const uint64_t* RET = reinterpret_cast<const uint64_t*>(smem + P.off_ret);
+    const uint32_t* POS = reinterpret_cast<const uint32_t*>(smem + P.off_pos);
+    const uint32_t* TAB = TAB_SMEM ? reinterpret_cast<const uint32_t*>(smem + P.off_tables)
+                                   : reinterpret_cast<const uint32_t*>(P.image + P.off_tables);
+
+    const uint32_t W32 = P.W32;
+    const uint32_t W32P = W32 + 1;            /* odd stride: row r of every slot in its own bank */
+    const uint32_t UP = 4 * P.n_sel + 1;      /* odd stride of the SEL uniform rows */
+    uint32_t* SBASE = reinterpret_cast<uint32_t*>(smem + smem_state_off); /* [2][NT][W32P] */
+    uint32_t* UBASE = SBASE + 2 * NT * W32P;                                 /* [NT][UP] */
+
+    const uint64_t traj = P.traj_begin + lt;
+
+    uint32_t* const S0 = SBASE + slot * W32P;  /* buffer b at S0 + b * bufstride; row W32 stays 0 */
+    const uint32_t bufstride = NT * W32P;
+    uint32_t* const Ut = UBASE + slot * UP;
+    const uint8_t* const Ub = reinterpret_cast<const uint8_t*>(Ut);
+    uint32_t cur = 0;
+
+    uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;
+
+    if (active) {
+        /* ---- initial state (both buffers' zero rows cleared) ---- */
+        for (uint32_t r = lane; r <= W32; r += LG) {
+            S0[bufstride + r] = 0u;
+            if (P.init == 0 || r == W32) S0[r] = 0u;
+        }
+        group_sync<LG>();
+        if (P.init == 0) {
+            const pbn_philox_step ps = pbn_philox_begin(P, traj, 0);
+            for (uint32_t w = lane; w < P.W; w += LG) {
+                const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_INIT << 28) | (w >> 1));
+                uint64_t word = (w & 1u) ? (((uint64_t)x.w << 32) | x.z) : (((uint64_t)x.y << 32) | x.x);
+                word &= RET[w];
+                while (word) {
+                    const uint32_t b = __ffsll((long long)word) - 1;
+                    word &= word - 1;
+                    const uint32_t ps_ = POS[64 * w + b];
+                    or_bit<LG>(&S0[ps_ >> 5], 1u << (ps_ & 31));
+                }
+            }
+        } else {
+            for (uint32_t r = lane; r < W32; r += LG) {
+                const uint64_t v = P.state[(uint64_t)(r >> 1) * P.n_traj + lt];
+                S0[r] = (r & 1u) ? (uint32_t)(v >> 32) : (uint32_t)v;
+            }
+        }
+        group_sync<LG>();
+
+        /* meta-state indicator of a state buffer (read by lane 0 of the group) */
+        auto meta_z = [&](const uint32_t* Sb) -> uint32_t {
+            uint32_t ok = 1u;
+            for (uint32_t m = 0; m < P.n_meta_rows; ++m)
+                ok &= ((Sb[P.meta_row[m]] & P.meta_mask[m]) == P.meta_val[m]) ? 1u : 0u;
+            return ok;
+        };
+        uint32_t zp = meta_z(S0);
+        if (P.count_first) cV += zp;
+
+        const uint32_t nl = P.n & 63u;
+        const uint64_t last_lanes = nl ? ((1ull << nl) - 1ull) : ~0ull;
+
+        for (uint32_t k = 0; k < P.n_steps; ++k) {
+            const uint64_t t = P.step_begin + k;
+            const pbn_philox_step ps = pbn_philox_begin(P, traj, t);
+            uint32_t* Sc = S0 + cur * bufstride;
+
+            /* ---- 1. perturbation: bit-sliced u < P, most significant level first,
+             *         stopping once every lane of the word is decided ---- */
+            uint32_t any_l = 0;
+            if (P.P != 0u) {
+                for (uint32_t w = lane; w < P.W; w += LG) {
+                    const uint64_t valid = (w == P.W - 1) ? last_lanes : ~0ull;
+                    uint32_t und_lo = (uint32_t)valid, und_hi = (uint32_t)(valid >> 32);
+                    uint32_t pert_lo = 0, pert_hi = 0;
+                    uint32_t pp = P.P; /* level 2h uses bit 31 of pp, level 2h+1 bit 30 */
+                    for (uint32_t h = 0; h < P.hmax && (und_lo | und_hi); ++h) {
+                        const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_PERT << 28) | (w << 4) | h);
+                        const uint32_t m0 = (uint32_t)((int32_t)pp >> 31);
+                        const uint32_t m1 = (uint32_t)((int32_t)(pp << 1) >> 31);
+                        pp <<= 2;
+                        pert_lo |= und_lo & ~x.x & m0;
+                        pert_hi |= und_hi & ~x.y & m0;
+                        und_lo &= ~(x.x ^ m0);
+                        und_hi &= ~(x.y ^ m0);
+                        pert_lo |= und_lo & ~x.z & m1;
+                        pert_hi |= und_hi & ~x.w & m1;
+                        und_lo &= ~(x.z ^ m1);
+                        und_hi &= ~(x.w ^ m1);
+                    }
+                    if (pert_lo | pert_hi) {
+                        any_l = 1u;
+                        uint64_t f = ((((uint64_t)pert_hi) << 32) | pert_lo) & RET[w];
+                        while (f) {
+                            const uint32_t b = __ffsll((long long)f) - 1;
+                            f &= f - 1;
+                            const uint32_t ps_ = POS[64 * w + b];
+                            xor_bit<LG>(&Sc[ps_ >> 5], 1u << (ps_ & 31));
+                        }
+                    }
+                }
+            }
+            uint32_t any = any_l;
+            if (LG > 1) {
+                group_sync<LG>();
+                any = (__ballot_sync(group_mask<LG>(), any_l) & group_mask<LG>()) ? 1u : 0u;
+            }
+
+            if (!any) {
+                /* ---- 2a. selection draws of the retained multi-function nodes ---- */
+                uint32_t i = lane;
+                for (; i + LG < P.n_sel; i += 2 * LG) {
+                    const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_SEL << 28) | SELBLK[i]);
+                    const uint4 y = pbn_philox_draw(P, ps, (PBN_DOM_SEL << 28) | SELBLK[i + LG]);
+                    uint32_t* a = Ut + 4 * i;
+                    uint32_t* b = Ut + 4 * (i + LG);
+                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                    b[0] = y.x; b[1] = y.y; b[2] = y.z; b[3] = y.w;
+                }
+                if (i < P.n_sel) {
+                    const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_SEL << 28) | SELBLK[i]);
+                    uint32_t* a = Ut + 4 * i;
+                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                }
+                group_sync<LG>();
+                /* ---- 2b. merged-table evaluation, word by word ---- */
+                const uint8_t* Sc8 = reinterpret_cast<const uint8_t*>(Sc);
+                uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
+                for (uint32_t w = lane; w < W32; w += LG) {
+                    const uint2 wr = WORDS[w];
+                    uint32_t acc = 0;
+                    for (uint32_t gi = wr.x; gi < wr.x + wr.y; ++gi) {
+                        const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
+                        const uint32_t q = G.w & 0xFFu;
+                        const uint32_t l2w = (G.w >> 8) & 0xFFu;
+                        const uint32_t n_mul = (G.w >> 16) & 0xFFu;
+                        const uint32_t shift = G.w >> 24;
+                        uint32_t c = 0;
+                        for (uint32_t m = 0; m < n_mul; ++m) {
+                            const uint4 M = MULTI[G.z + m]; /* u_off|n_thr, radix, t1, t2 */
+                            const uint32_t u = *reinterpret_cast<const uint32_t*>(Ub + (M.x & 0xFFFFFFu));
+                            const uint32_t n_thr = M.x >> 24;
+                            uint32_t j;
+                            if (n_thr <= 2u) {
+                                j = ((n_thr >= 1u) & (u >= M.z)) + ((n_thr >= 2u) & (u >= M.w));
+                            } else {
+                                j = 0;
+                                for (uint32_t q2 = 0; q2 < n_thr; ++q2) j += (u >= THR[M.z + q2]) ? 1u : 0u;
+                            }
+                            c += j * M.y;
+                        }
+                        uint32_t x = 0;
+                        const uint4* ch = INPUTS + G.y;
+                        for (uint32_t b0 = 0; b0 < q; b0 += 4) {
+                            const uint4 R = *ch++;
+                            const uint32_t v0 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.x >> 5));
+                            const uint32_t v1 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.y >> 5));
+                            const uint32_t v2 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.z >> 5));
+                            const uint32_t v3 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.w >> 5));
+                            uint32_t x4 = __funnelshift_r(v0, v0, R.x) & 1u;
+                            x4 |= __funnelshift_r(v1, v1, R.y) & 2u;
+                            x4 |= __funnelshift_r(v2, v2, R.z) & 4u;
+                            x4 |= __funnelshift_r(v3, v3, R.w) & 8u;
+                            x |= x4 << b0;
+                        }
+                        const uint32_t bo = ((c << q) | x) << l2w;
+                        const uint32_t tw = TAB_SMEM ? TAB[G.x + (bo >> 5)] : __ldg(TAB + G.x + (bo >> 5));
+                        const uint32_t emask = (2u << ((1u << l2w) - 1u)) - 1u;
+                        acc |= ((tw >> (bo & 31u)) & emask) << shift;
+                    }
+                    Sn[w] = acc;
+                }
+                group_sync<LG>();
+                cur ^= 1u;
+            }
+
+            /* ---- 3. meta-state counts ---- */
+            if (lane == 0) {
+                const uint32_t* Sb = S0 + cur * bufstride;
+                const uint32_t z = meta_z(Sb);
+                const uint32_t cv = k >= P.kv0 ? 1u : 0u;
+                const uint32_t cp = k >= P.kp0 ? 1u : 0u;
+                cV += cv & z;
+                c11 += cp & zp & z;
+                c01 += cp & (zp ^ 1u) & z;
+                c10 += cp & zp & (z ^ 1u);
+                zp = z;
+                if (TRACE) {
+                    for (uint32_t r = 0; r < W32; r += 2) {
+                        const uint64_t v = ((uint64_t)Sb[r + 1] << 32) | Sb[r];
+                        P.trace[((uint64_t)k * (W32 / 2) + r / 2) * P.n_traj + lt] = v;
+                    }
+                }
+            }
+            group_sync<LG>();
+        }
+
+        /* ---- epilogue: state and counts ---- */
+        const uint32_t* Sb = S0 + cur * bufstride;
+        for (uint32_t r = lane * 2; r < W32; r += 2 * LG) {
+            const uint64_t v = ((uint64_t)Sb[r + 1] << 32) | Sb[r];
+            P.state[(uint64_t)(r >> 1) * P.n_traj + lt] = v;
+        }
+        if (lane == 0 && P.counts) {
+            const uint32_t c00 = P.pairs - c01 - c10 - c11;
+            const uint64_t nt = P.n_traj;
+            P.counts[0 * nt + lt] += cV;
+            P.counts[1 * nt + lt] += c00;
+            P.counts[2 * nt + lt] += c01;
+            P.counts[3 * nt + lt] += c10;
+            P.counts[4 * nt + lt] += c11;
+        }
+    }
+
+    out[0] = cV;
+    out[1] = c01;
+    out[2] = c10;
+    out[3] = c11;
+}
+
+#endif
