@@ -202,3 +202,84 @@ def estimate(counts5, n_traj: int, r: float, s: float, eps: float = 1e-3,
     check(_lib.load().pbn_estimate(_ptr(c), n_traj, burn_in_used, r, s, eps, ctypes.byref(out)),
           "pbn_estimate")
     return out
+
+
+class Batch:
+    """Many networks simulated by one persistent launch per step chunk, fed by a
+    device work queue (pbn_batch_create / pbn_batch_run).
+
+    `entries` is a list of dicts with keys plan, bufs (SimBuffers), seed, meta_ids and
+    optionally meta_vals, traj_begin, step_begin, count_from, init."""
+
+    def __init__(self, entries, device="cuda"):
+        import torch
+        L = _lib.load()
+        self.entries = entries
+        self._keep = []
+        arr = (_lib.BatchNet * len(entries))()
+        for i, e in enumerate(entries):
+            plan, bufs = e["plan"], e["bufs"]
+            mi = np.ascontiguousarray(e["meta_ids"], dtype=np.uint32)
+            mv = None if e.get("meta_vals") is None else np.ascontiguousarray(e["meta_vals"], dtype=np.uint8)
+            self._keep += [mi, mv]
+            b = arr[i]
+            b.plan = plan._h
+            b.d_image = plan.device_image(device).data_ptr()
+            b.seed = e["seed"]
+            b.traj_begin = e.get("traj_begin", 0)
+            b.n_traj = bufs.state.shape[1]
+            b.step_begin = e.get("step_begin", 0)
+            b.count_from = e.get("count_from", 0)
+            b.init = e.get("init", _lib.PBN_INIT_KEYED if b.step_begin == 0 else _lib.PBN_INIT_STATE)
+            b.n_meta = len(mi)
+            b.meta_ids = mi.ctypes.data
+            b.meta_vals = None if mv is None else mv.ctypes.data
+            b.d_state = bufs.state.data_ptr()
+            b.d_counts = None if bufs.counts is None else bufs.counts.data_ptr()
+            b.d_pooled = None if bufs.pooled is None else bufs.pooled.data_ptr()
+        h = ctypes.c_void_p()
+        check(L.pbn_batch_create(arr, len(entries), ctypes.byref(h)), "pbn_batch_create")
+        self._h = h
+        self.info = _lib.BatchInfo()
+        check(L.pbn_batch_info_get(self._h, ctypes.byref(self.info)), "pbn_batch_info_get")
+        host = np.zeros(self.info.desc_bytes, dtype=np.uint8)
+        check(L.pbn_batch_image(self._h, _ptr(host), host.size), "pbn_batch_image")
+        self.desc = torch.from_numpy(host).to(device)
+        self.queue = torch.zeros(2, dtype=torch.int32, device=device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.steps_done = 0
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.load().pbn_batch_free(self._h)
+            self._h = None
+
+    def run(self, n_steps: int, step_offset: int | None = None, ctas_per_sm: int = 0, stream=None):
+        """One persistent launch advancing every network by n_steps steps."""
+        import torch
+        st = torch.cuda.current_stream(self.desc.device) if stream is None else stream
+        off = self.steps_done if step_offset is None else step_offset
+        check(_lib.load().pbn_batch_run(self._h, ctypes.c_void_p(self.desc.data_ptr()),
+                                        ctypes.c_void_p(self.queue.data_ptr()), off, n_steps,
+                                        ctas_per_sm, ctypes.c_void_p(self.status.data_ptr()),
+                                        ctypes.c_void_p(st.cuda_stream)), "pbn_batch_run")
+        self.steps_done = off + n_steps
+
+    def capture(self, chunks, step_offset: int = 0):
+        """Capture the launches of `chunks` (list of step counts) starting at
+        step_offset in a CUDA graph; returns the torch.cuda.CUDAGraph to replay."""
+        import torch
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(self.desc.device)
+        s.wait_stream(torch.cuda.current_stream(self.desc.device))
+        with torch.cuda.stream(s):
+            # launch configuration queries happen outside the capture
+            pass
+        off = step_offset
+        with torch.cuda.graph(g, stream=s):
+            for c in chunks:
+                self.run(c, step_offset=off, stream=s)
+                off += c
+        torch.cuda.current_stream(self.desc.device).wait_stream(s)
+        self.steps_done = step_offset
+        return g

@@ -239,6 +239,8 @@ struct pbn_batch {
     std::vector<WorkItem> items;
     std::vector<uint8_t> image; /* nets then items */
     uint32_t threads = 256;
+    mutable int occ_per_sm = 0;  /* occupancy of the batch kernel, queried on the first run */
+    mutable int sms = 0;
 };
 
 extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out) {
@@ -396,17 +398,24 @@ extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
     const size_t smem = b->info.smem_bytes;
-    static size_t configured = 48 * 1024;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(pbn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
-        configured = smem;
+    cudaError_t e;
+    if (!b->occ_per_sm) {
+        /* device queries once per batch, so later launches can be graph-captured */
+        static size_t configured = 48 * 1024;
+        if (smem > configured) {
+            e = cudaFuncSetAttribute(pbn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
+            configured = smem;
+        }
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pbn_batch_kernel, (int)b->threads, smem);
+        if (e != cudaSuccess || per_sm < 1) return fail(PBN_ETOOBIG, "pbn_batch_run: the batch kernel does not fit an SM");
+        b->occ_per_sm = per_sm;
+        b->sms = sm_count();
     }
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pbn_batch_kernel, (int)b->threads, smem);
-    if (e != cudaSuccess || per_sm < 1) return fail(PBN_ETOOBIG, "pbn_batch_run: the batch kernel does not fit an SM");
+    int per_sm = b->occ_per_sm;
     if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)sm_count() * per_sm, std::max<uint32_t>(1u, b->info.n_items));
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)b->sms * per_sm, std::max<uint32_t>(1u, b->info.n_items));
     pbn_batch_kernel<<<grid, b->threads, smem, static_cast<cudaStream_t>(stream)>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));

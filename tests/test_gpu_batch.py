@@ -1,0 +1,110 @@
+"""The batched persistent kernel (device work queue, CUDA-graph step chunks):
+every network's states and counts equal those of its own single-network launch and
+of the CPU oracle, whatever the mix."""
+import os
+
+import numpy as np
+import pytest
+
+from gpu_helpers import plan_for, run
+from paper_1605_00854_gb300 import _lib, api, synth
+
+pytestmark = pytest.mark.gpu
+NCPU = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _networks(seed=40, count=10):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.integers(20, 400))
+        T = int(rng.integers(50, 1200))
+        p = float(10 ** rng.uniform(-5, -2))
+        text = synth.paper100(seed=1000 + i, n=n, p=p).to_text()
+        meta = sorted(set(int(x) for x in rng.choice(3, size=int(rng.integers(1, 4)), replace=False)))
+        out.append(dict(text=text, T=T, meta=meta, seed=int(rng.integers(0, 2**63)), n=n))
+    return out
+
+
+def _collect(plan, bufs):
+    import torch
+    torch.cuda.synchronize()
+    return dict(final=plan.unpack(bufs.state.cpu().numpy().view(np.uint64)),
+                counts=bufs.counts.cpu().numpy().view(np.uint64).T.copy(),
+                pooled=bufs.pooled.cpu().numpy().view(np.uint64).copy())
+
+
+@pytest.mark.parametrize("chunks", [[400], [150, 1, 249], [200, 200]])
+def test_batch_equals_single_network_launches(chunks):
+    nets = _networks()
+    S = sum(chunks)
+    entries, plans = [], []
+    for k, d in enumerate(nets):
+        plan, ids = plan_for(d["text"], d["meta"])
+        bufs = api.alloc_buffers(plan, d["T"])
+        entries.append(dict(plan=plan, bufs=bufs, seed=d["seed"], meta_ids=d["meta"],
+                            traj_begin=k * 10**6, count_from=37))
+        plans.append((plan, ids))
+    B = api.Batch(entries)
+    assert B.info.n_nets == len(nets) and B.info.n_items >= len(nets)
+    for c in chunks:
+        B.run(c)
+    assert int(B.status.item()) == 0 and B.queue.cpu().tolist() == [0, 0]
+    for k, (d, (plan, ids), e) in enumerate(zip(nets, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        ref = run(plan, seed=d["seed"], traj_begin=k * 10**6, n_traj=d["T"], n_steps=S, meta=d["meta"],
+                  count_from=37, kernel=_lib.PBN_KERNEL_INTERP)
+        assert np.array_equal(got["final"][:, ids], ref["final"][:, ids]), k
+        assert np.array_equal(got["counts"], ref["counts"]), k
+        assert np.array_equal(got["pooled"], ref["pooled"]), k
+
+
+def test_batch_against_oracle(oracle_mod):
+    nets = _networks(seed=7, count=4)
+    entries, plans = [], []
+    for d in nets:
+        d["T"] = min(d["T"], 150)
+        plan, ids = plan_for(d["text"], d["meta"])
+        entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, d["T"]), seed=d["seed"], meta_ids=d["meta"]))
+        plans.append((plan, ids))
+    B = api.Batch(entries)
+    B.run(300)
+    B.run(200)
+    for d, (plan, ids), e in zip(nets, plans, entries):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(d["text"], d["seed"], 0, d["T"], 500, meta_ids=d["meta"], nthreads=NCPU)
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids])
+        assert np.array_equal(got["counts"], orc["counts"])
+
+
+def test_batch_graph_capture_replays_the_chunk_loop():
+    import torch
+    nets = _networks(seed=3, count=6)
+    def build():
+        entries, plans = [], []
+        for d in nets:
+            plan, ids = plan_for(d["text"], d["meta"])
+            entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, d["T"]), seed=d["seed"], meta_ids=d["meta"]))
+            plans.append((plan, ids))
+        return api.Batch(entries), entries, plans
+    B1, e1, p1 = build()
+    for _ in range(4):
+        B1.run(100)
+    B2, e2, p2 = build()
+    B2.run(1)                 # warm up (attribute setting) outside the capture
+    for e in e2:
+        e["bufs"].state.zero_(); e["bufs"].counts.zero_(); e["bufs"].pooled.zero_()
+    g = B2.capture([100, 100, 100, 100])
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(B2.status.item()) == 0
+    for (plan, ids), a, b in zip(p1, e1, e2):
+        ga, gb = _collect(plan, a["bufs"]), _collect(plan, b["bufs"])
+        assert np.array_equal(ga["final"], gb["final"]) and np.array_equal(ga["counts"], gb["counts"])
