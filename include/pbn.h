@@ -237,12 +237,18 @@ int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn_sim_args* 
  * (the interpreter kernel runs them).  *compile_ms (may be NULL) receives the host
  * time spent.  Errors: PBN_EINVAL (plan not compilable), PBN_ECUDA (NVRTC missing,
  * compilation or module load failed; pbn_last_error_detail() has the log). */
-int pbn_plan_compile(const pbn_plan* plan, double* compile_ms);
+int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
+
+/* pbn_plan_compile flags.  Default (0): the perturbation words are drawn in pairs
+ * by one rolled loop (two independent Philox chains, small code).
+ * PBN_COMPILE_PERT_UNROLLED: one word at a time, every level pair unrolled with
+ * the bits of P as constants.  Compiling with other flags replaces the kernel. */
+#define PBN_COMPILE_PERT_UNROLLED 0x1u
 
 /* The CUDA source generated for the plan's own kernel: *len receives its length;
  * dst (capacity cap, may be NULL) receives it NUL-terminated.
  * Errors: PBN_EINVAL (plan not compilable, cap too small). */
-int pbn_plan_source(const pbn_plan* plan, char* dst, size_t cap, size_t* len);
+int pbn_plan_source(const pbn_plan* plan, uint32_t flags, char* dst, size_t cap, size_t* len);
 
 /* ---- batched form: many networks, one persistent launch ------------------------------ */
 typedef struct pbn_batch pbn_batch;

@@ -19,6 +19,7 @@ PBN_PLAN_GROUPED = 0
 PBN_PLAN_PLAIN = 1
 PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
+PBN_COMPILE_PERT_UNROLLED = 0x1
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1
 PBN_KERNEL_COMPILED = 2
@@ -83,13 +84,13 @@ SIGNATURES = {
     "pbn_plan_layout": (i32, [vp, vp]),
     "pbn_plan_groups": (i32, [vp, vp]),
     "pbn_simulate": (i32, [vp, vp, ctypes.POINTER(SimArgs), vp]),
-    "pbn_plan_compile": (i32, [vp, ctypes.POINTER(f64)]),
+    "pbn_plan_compile": (i32, [vp, u32, ctypes.POINTER(f64)]),
     "pbn_batch_create": (i32, [ctypes.POINTER(BatchNet), u32, ctypes.POINTER(vp)]),
     "pbn_batch_info_get": (i32, [vp, ctypes.POINTER(BatchInfo)]),
     "pbn_batch_image": (i32, [vp, vp, ctypes.c_size_t]),
     "pbn_batch_run": (i32, [vp, vp, vp, u64, u64, u32, vp, vp]),
     "pbn_batch_free": (None, [vp]),
-    "pbn_plan_source": (i32, [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "pbn_plan_source": (i32, [vp, u32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "pbn_estimate": (i32, [vp, u64, u64, f64, f64, f64, ctypes.POINTER(EstimateOut)]),
     "pbn_strerror": (cp, [i32]),
     "pbn_last_error_detail": (cp, []),

@@ -107,19 +107,19 @@ class Plan:
         check(_lib.load().pbn_plan_groups(self._h, _ptr(g)), "pbn_plan_groups")
         return g
 
-    def compile(self) -> float:
+    def compile(self, flags: int = 0) -> float:
         """Compile the plan into its own kernel (pbn_plan_compile); returns host ms."""
         ms = ctypes.c_double()
-        check(_lib.load().pbn_plan_compile(self._h, ctypes.byref(ms)), "pbn_plan_compile")
+        check(_lib.load().pbn_plan_compile(self._h, flags, ctypes.byref(ms)), "pbn_plan_compile")
         return ms.value
 
-    def source(self) -> str:
+    def source(self, flags: int = 0) -> str:
         """CUDA source of the plan's own kernel (pbn_plan_source)."""
         L = _lib.load()
         n = ctypes.c_size_t()
-        check(L.pbn_plan_source(self._h, None, 0, ctypes.byref(n)), "pbn_plan_source")
+        check(L.pbn_plan_source(self._h, flags, None, 0, ctypes.byref(n)), "pbn_plan_source")
         buf = ctypes.create_string_buffer(n.value + 1)
-        check(L.pbn_plan_source(self._h, buf, n.value + 1, ctypes.byref(n)), "pbn_plan_source")
+        check(L.pbn_plan_source(self._h, flags, buf, n.value + 1, ctypes.byref(n)), "pbn_plan_source")
         return buf.value.decode()
 
     def device_image(self, device="cuda"):

@@ -46,8 +46,9 @@ uint64_t pert_threshold(double p);
 /* compiled plans (pbn_jit.cpp) */
 pbn_jit_state* jit_state(const pbn_plan* plan);
 void jit_free(pbn_jit_state* J);
-int jit_compile(const pbn_plan* plan);
+int jit_compile(const pbn_plan* plan, uint32_t flags);
 bool jit_ready(const pbn_plan* plan);
+uint32_t jit_current_flags(const pbn_plan* plan); /* flags of the compiled kernel, else 0 */
 }  // namespace pbn
 
 #endif

@@ -120,7 +120,7 @@ struct Generated {
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
 };
 
-bool generate(const pbn_plan& plan, Generated* out, std::string* why) {
+bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string* why) {
     View V{&plan.hdr, plan.image.data()};
     const pbn_img_header& H = plan.hdr;
     if (H.W32 > PBN_JIT_MAX_ROWS) {
@@ -203,13 +203,33 @@ bool generate(const pbn_plan& plan, Generated* out, std::string* why) {
          "      const uint64_t t = P.step_begin + k;\n"
          "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
          "      uint32_t any = 0;\n";
-    /* 1. perturbation, levels of P compiled in */
+    /* 1. perturbation: the levels of P compiled in */
     const uint32_t Pv = H.P;
-    if (Pv) {
+    auto emit_flips = [&](uint32_t w, const char* pl, const char* ph, const char* sfx) {
+        const uint32_t rl = (uint32_t)ret[w], rh = (uint32_t)(ret[w] >> 32);
+        for (int half = 0; half < 2; ++half) {
+            const uint32_t rm = half ? rh : rl;
+            if (!rm) continue;
+            o << "          { uint32_t f = " << (half ? ph : pl) << " & " << hex32(rm) << ";\n"
+              << "          while (f) { const uint32_t b = __ffs(f) - 1; f &= f - 1; switch (b) {\n";
+            for (uint32_t b = 0; b < 32; ++b) {
+                if (!((rm >> b) & 1u)) continue;
+                const uint32_t ps = pos[64 * w + 32 * half + b];
+                o << "            case " << b << ": s" << (ps >> 5) << " ^= " << hex32(1u << (ps & 31)) << "; break;\n";
+            }
+            o << "          } } }\n";
+        }
+        (void)sfx;
+    };
+    auto valid_of = [&](uint32_t w) {
+        const uint32_t nl = (w == H.W - 1) ? (H.n - 64 * w) : 64u;
+        return nl >= 64 ? ~0ull : ((1ull << nl) - 1ull);
+    };
+    if (Pv && (flags & PBN_COMPILE_PERT_UNROLLED)) {
+        /* one word at a time, every level pair unrolled with its P bits as constants */
         const uint32_t hmax = (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u;
         for (uint32_t w = 0; w < H.W; ++w) {
-            const uint32_t nl = (w == H.W - 1) ? (H.n - 64 * w) : 64u;
-            const uint64_t valid = nl >= 64 ? ~0ull : ((1ull << nl) - 1ull);
+            const uint64_t valid = valid_of(w);
             o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
               << ", pl = 0, ph = 0;\n";
             for (uint32_t h = 0; h < hmax; ++h) {
@@ -219,28 +239,49 @@ bool generate(const pbn_plan& plan, Generated* out, std::string* why) {
                   << hex32((PBN_DOM_PERT << 28) | (w << 4) | h) << ");";
                 if (b0) o << " pl |= ul & ~x.x; ph |= uh & ~x.y; ul &= x.x; uh &= x.y;";
                 else o << " ul &= ~x.x; uh &= ~x.y;";
-                if (2 * h + 1 < 32) {
-                    if (b1) o << " pl |= ul & ~x.z; ph |= uh & ~x.w; ul &= x.z; uh &= x.w;";
-                    else o << " ul &= ~x.z; uh &= ~x.w;";
-                }
+                if (b1) o << " pl |= ul & ~x.z; ph |= uh & ~x.w; ul &= x.z; uh &= x.w;";
+                else o << " ul &= ~x.z; uh &= ~x.w;";
                 o << " }\n";
             }
             o << "        if (pl | ph) {\n          any = 1u;\n";
-            const uint32_t rl = (uint32_t)ret[w], rh = (uint32_t)(ret[w] >> 32);
-            for (int half = 0; half < 2; ++half) {
-                const uint32_t rm = half ? rh : rl;
-                if (!rm) continue;
-                o << "          uint32_t f" << half << " = " << (half ? "ph" : "pl") << " & " << hex32(rm) << ";\n"
-                  << "          while (f" << half << ") { const uint32_t b = __ffs(f" << half << ") - 1; f" << half
-                  << " &= f" << half << " - 1; switch (b) {\n";
-                for (uint32_t b = 0; b < 32; ++b) {
-                    if (!((rm >> b) & 1u)) continue;
-                    const uint32_t ps = pos[64 * w + 32 * half + b];
-                    o << "            case " << b << ": s" << (ps >> 5) << " ^= " << hex32(1u << (ps & 31)) << "; break;\n";
-                }
-                o << "          } }\n";
-            }
+            emit_flips(w, "pl", "ph", "");
             o << "        }\n      }\n";
+        }
+    } else if (Pv) {
+        /* words in pairs: one rolled loop draws both words' level pairs, two
+         * independent Philox chains per iteration; the P bit of each level comes
+         * from a shifted copy of P */
+        const uint32_t hmax = (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u;
+        for (uint32_t w = 0; w < H.W; w += 2) {
+            const bool two = w + 1 < H.W;
+            const uint64_t v0 = valid_of(w), v1 = two ? valid_of(w + 1) : 0ull;
+            o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
+              << ", pl0 = 0, ph0 = 0";
+            if (two) o << ", ul1 = " << hex32((uint32_t)v1) << ", uh1 = " << hex32((uint32_t)(v1 >> 32)) << ", pl1 = 0, ph1 = 0";
+            o << ";\n        uint32_t pp = " << hex32(Pv) << ";\n"
+              << "#pragma unroll 1\n"
+              << "        for (uint32_t h = 0; h < " << hmax << "u; ++h) {\n"
+              << "          if (!(ul0 | uh0" << (two ? " | ul1 | uh1" : "") << ")) break;\n"
+              << "          const uint32_t m0 = (uint32_t)((int32_t)pp >> 31), m1 = (uint32_t)((int32_t)(pp << 1) >> 31);\n"
+              << "          pp <<= 2;\n"
+              << "          const uint4 x0 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_PERT << 28) | (w << 4)) << " | h);\n";
+            if (two) o << "          const uint4 x1 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_PERT << 28) | ((w + 1) << 4)) << " | h);\n";
+            for (int k = 0; k < (two ? 2 : 1); ++k) {
+                o << fmt("          pl%d |= ul%d & ~x%d.x & m0; ph%d |= uh%d & ~x%d.y & m0; ul%d &= ~(x%d.x ^ m0); uh%d &= ~(x%d.y ^ m0);\n",
+                         k, k, k, k, k, k, k, k, k, k)
+                  << fmt("          pl%d |= ul%d & ~x%d.z & m1; ph%d |= uh%d & ~x%d.w & m1; ul%d &= ~(x%d.z ^ m1); uh%d &= ~(x%d.w ^ m1);\n",
+                         k, k, k, k, k, k, k, k, k, k);
+            }
+            o << "        }\n";
+            o << "        if (pl0 | ph0) {\n          any = 1u;\n";
+            emit_flips(w, "pl0", "ph0", "");
+            o << "        }\n";
+            if (two) {
+                o << "        if (pl1 | ph1) {\n          any = 1u;\n";
+                emit_flips(w + 1, "pl1", "ph1", "");
+                o << "        }\n";
+            }
+            o << "      }\n";
         }
     }
     /* 2. selection draws and merged-table evaluation */
@@ -340,6 +381,7 @@ bool generate(const pbn_plan& plan, Generated* out, std::string* why) {
 struct pbn_jit_state {
     std::mutex mu;
     int state = 0;  /* 0: not tried, 1: compiled, -1: failed */
+    uint32_t flags = 0;
     std::string log;
     std::string src;
     cudaLibrary_t lib = nullptr;
@@ -363,14 +405,21 @@ void jit_free(pbn_jit_state* J) {
     delete J;
 }
 
-int jit_compile(const pbn_plan* plan) {
+int jit_compile(const pbn_plan* plan, uint32_t flags) {
     pbn_jit_state* J = jit_state(plan);
     std::lock_guard<std::mutex> g(J->mu);
-    if (J->state == 1) return PBN_OK;
-    if (J->state == -1) return fail(PBN_EINVAL, "plan compilation failed earlier: %s", J->log.c_str());
+    if (J->state == 1 && J->flags == flags) return PBN_OK;
+    if (J->state == -1 && J->flags == flags) return fail(PBN_EINVAL, "plan compilation failed earlier: %s", J->log.c_str());
+    if (J->lib) {
+        cudaLibraryUnload(J->lib);
+        J->lib = nullptr;
+        J->kern = nullptr;
+    }
+    J->state = 0;
+    J->flags = flags;
     Generated gen;
     std::string why;
-    if (!generate(*plan, &gen, &why)) {
+    if (!generate(*plan, flags, &gen, &why)) {
         J->state = -1;
         J->log = why;
         return fail(PBN_EINVAL, "plan cannot be compiled: %s", why.c_str());
@@ -421,6 +470,12 @@ int jit_compile(const pbn_plan* plan) {
     return PBN_OK;
 }
 
+uint32_t jit_current_flags(const pbn_plan* plan) {
+    pbn_jit_state* J = jit_state(plan);
+    std::lock_guard<std::mutex> g(J->mu);
+    return J->state == 1 ? J->flags : 0u;
+}
+
 bool jit_ready(const pbn_plan* plan) {
     pbn_jit_state* J = jit_state(plan);
     std::lock_guard<std::mutex> g(J->mu);
@@ -445,18 +500,19 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 
 }  // namespace pbn
 
-extern "C" int pbn_plan_compile(const pbn_plan* plan, double* compile_ms) {
+extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
-    const int rc = pbn::jit_compile(plan);
+    if (flags & ~PBN_COMPILE_PERT_UNROLLED) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
+    const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;
     return rc;
 }
 
-extern "C" int pbn_plan_source(const pbn_plan* plan, char* dst, size_t cap, size_t* len) {
+extern "C" int pbn_plan_source(const pbn_plan* plan, uint32_t flags, char* dst, size_t cap, size_t* len) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_source: NULL plan");
     Generated gen;
     std::string why;
-    if (!generate(*plan, &gen, &why)) return pbn::fail(PBN_EINVAL, "plan cannot be compiled: %s", why.c_str());
+    if (!generate(*plan, flags, &gen, &why)) return pbn::fail(PBN_EINVAL, "plan cannot be compiled: %s", why.c_str());
     if (len) *len = gen.src.size();
     if (dst) {
         if (cap < gen.src.size() + 1) return pbn::fail(PBN_EINVAL, "pbn_plan_source: need %zu bytes", gen.src.size() + 1);

@@ -250,7 +250,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     const int sms = device_sm_count();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (a->kernel == PBN_KERNEL_COMPILED) {
-        const int rc = pbn::jit_compile(plan);
+        const int rc = pbn::jit_compile(plan, pbn::jit_current_flags(plan));
         if (rc) return rc;
     }
     if (a->kernel == PBN_KERNEL_COMPILED ||

@@ -64,11 +64,13 @@ def test_compiled_resume_and_keyed_init(oracle_mod):
     _compare(a, orc, ids)
 
 
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PERT_UNROLLED])
 @pytest.mark.parametrize("p", [0.0, 0.05, 0.3, 0.75])
-def test_compiled_perturbation_regimes(oracle_mod, p):
-    text = synth.paper100(seed=9, n=70, p=p).to_text()
+def test_compiled_perturbation_regimes(oracle_mod, p, flags):
+    text = synth.paper100(seed=9, n=170, p=p).to_text()
     meta = [0, 1]
     plan, ids = plan_for(text, meta)
+    plan.compile(flags)
     orc = oracle_mod.simulate(text, 2, 0, 96, 300, meta_ids=meta, trace=True, nthreads=NCPU)
     _compare(run(plan, seed=2, n_traj=96, n_steps=300, meta=meta, trace=True, kernel=COMPILED), orc, ids)
 

@@ -311,8 +311,9 @@ def test_estimate_rejects_bad_arguments():
 
 
 # ------------------------------------------------------------ compiled plans ----
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half"])
-def test_generated_plan_kernels_compile(tmp_path, which):
+def test_generated_plan_kernels_compile(tmp_path, which, flags):
     """The source generated for a plan's own kernel compiles for sm_103a."""
     import shutil
     import subprocess
@@ -331,7 +332,7 @@ def test_generated_plan_kernels_compile(tmp_path, which):
         text, meta = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n", [0]
     red, _ = api.Net.load(text).reduce(meta)
     plan = api.Plan(red, mode=1 if which.endswith("plain") else 0)
-    (tmp_path / "k.cu").write_text(plan.source())
+    (tmp_path / "k.cu").write_text(plan.source(flags))
     shutil.copy(os.path.join(ROOT, "paper_1605_00854_gb300", "csrc", "pbn_device.cuh"), tmp_path)
     proc = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c",
                            str(tmp_path / "k.cu"), "-o", str(tmp_path / "k.o")],
