@@ -308,6 +308,23 @@ int pbn_batch_run(const pbn_batch* batch, const void* d_desc, uint32_t* d_queue,
                   uint64_t n_steps, uint32_t ctas_per_sm, uint32_t* d_status, void* stream);
 void pbn_batch_free(pbn_batch* batch);
 
+/* Same launch as pbn_batch_run, for callers that cannot allocate device memory when
+ * they run a batch (an allocator that owns the device, a CUDA graph being recorded,
+ * a latency-critical loop that must not call cudaMalloc or cudaFree, which can
+ * synchronise the device).  The paper has no counterpart: this is a deployment
+ * option of the batched form.  The work-queue scratch comes from a static array the
+ * library keeps in device memory: PBN_STATIC_QUEUE_SLOTS queues of two uint32
+ * counters, selected by `slot`; the call clears its slot (cudaMemsetAsync on
+ * `stream`) before the launch and allocates nothing.  Calls that use the same slot
+ * and overlap on the GPU race; concurrent batches must use different slots.  The
+ * first call on a device looks up the array's device address (once per device, with
+ * that device current), so make that first call before any stream capture.
+ * Errors: PBN_EINVAL (slot >= PBN_STATIC_QUEUE_SLOTS, NULL or misaligned table,
+ * range), PBN_ETOOBIG, PBN_ECUDA. */
+#define PBN_STATIC_QUEUE_SLOTS 16u
+int pbn_batch_run_static(const pbn_batch* batch, const void* d_desc, uint32_t slot, uint64_t step_offset,
+                         uint64_t n_steps, uint32_t ctas_per_sm, uint32_t* d_status, void* stream);
+
 /* ---- estimation ------------------------------------------------------------------ */
 typedef struct {
     double alpha;        /* n01 / (n00 + n01), NaN if undefined */

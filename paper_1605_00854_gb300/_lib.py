@@ -20,6 +20,7 @@ PBN_PLAN_PLAIN = 1
 PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
 PBN_COMPILE_PERT_UNROLLED = 0x1
+PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1
 PBN_KERNEL_COMPILED = 2
@@ -90,6 +91,7 @@ SIGNATURES = {
     "pbn_batch_image": (i32, [vp, vp, ctypes.c_size_t]),
     "pbn_batch_run": (i32, [vp, vp, vp, u64, u64, u32, vp, vp]),
     "pbn_batch_free": (None, [vp]),
+    "pbn_batch_run_static": (i32, [vp, vp, u32, u64, u64, u32, vp, vp]),
     "pbn_plan_source": (i32, [vp, u32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     "pbn_estimate": (i32, [vp, u64, u64, f64, f64, f64, ctypes.POINTER(EstimateOut)]),
     "pbn_strerror": (cp, [i32]),

@@ -265,6 +265,18 @@ class Batch:
                                         ctypes.c_void_p(st.cuda_stream)), "pbn_batch_run")
         self.steps_done = off + n_steps
 
+    def run_static(self, n_steps: int, slot: int = 0, step_offset: int | None = None,
+                   ctas_per_sm: int = 0, stream=None):
+        """Like run(), with the work-queue scratch taken from the library's static
+        device array (pbn_batch_run_static): allocates nothing."""
+        import torch
+        st = torch.cuda.current_stream(self.desc.device) if stream is None else stream
+        off = self.steps_done if step_offset is None else step_offset
+        check(_lib.load().pbn_batch_run_static(self._h, ctypes.c_void_p(self.desc.data_ptr()), slot, off, n_steps,
+                                               ctas_per_sm, ctypes.c_void_p(self.status.data_ptr()),
+                                               ctypes.c_void_p(st.cuda_stream)), "pbn_batch_run_static")
+        self.steps_done = off + n_steps
+
     def capture(self, chunks, step_offset: int = 0):
         """Capture the launches of `chunks` (list of step counts) starting at
         step_offset in a CUDA graph; returns the torch.cuda.CUDAGraph to replay."""

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -419,5 +420,90 @@ extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d
     pbn_batch_kernel<<<grid, b->threads, smem, static_cast<cudaStream_t>(stream)>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
+    return PBN_OK;
+}
+
+/* ---- allocation-free variant of pbn_batch_run ------------------------------------------
+ * Some callers cannot allocate device memory at the point where they run a batch: a
+ * serving loop or an embedding framework whose allocator owns the whole device, code
+ * that records its launches into a CUDA graph (allocation is not allowed during stream
+ * capture), and latency-critical loops that must not call cudaMalloc or cudaFree,
+ * which can synchronise the whole device.  This entry point takes the work-queue
+ * scratch from a small array the library owns in device memory instead of from the
+ * caller.  The array has PBN_STATIC_QUEUE_SLOTS independent queues of two counters
+ * (128 bytes in all); every GPU that loads the library keeps it until the process
+ * exits. */
+namespace {
+__device__ __align__(256) uint32_t g_pbn_static_queues[2 * PBN_STATIC_QUEUE_SLOTS];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+uint32_t* g_static_addr[kMaxDevices] = {nullptr};
+}  // namespace
+
+extern "C" int pbn_batch_run_static(const pbn_batch* b, const void* d_desc, uint32_t slot, uint64_t step_offset,
+                                    uint64_t n_steps, uint32_t ctas_per_sm, uint32_t* d_status, void* stream) {
+    using pbn::fail;
+    if (!b || !d_desc) return fail(PBN_EINVAL, "pbn_batch_run_static: NULL argument");
+    if (slot >= PBN_STATIC_QUEUE_SLOTS)
+        return fail(PBN_EINVAL, "pbn_batch_run_static: queue slot %u is beyond the library's %u static slots", slot,
+                    (unsigned)PBN_STATIC_QUEUE_SLOTS);
+    if ((uintptr_t)d_desc & 15u) return fail(PBN_EINVAL, "pbn_batch_run_static: misaligned descriptor table");
+    if (n_steps >= (1ull << 32)) return fail(PBN_EINVAL, "pbn_batch_run_static: n_steps must be < 2^32");
+    for (const NetDesc& D : b->nets)
+        if (D.step_begin + step_offset + n_steps > (1ull << 48))
+            return fail(PBN_EINVAL, "pbn_batch_run_static: step index >= 2^48");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PBN_EINVAL, "pbn_batch_run_static: device %d beyond %d", dev, kMaxDevices);
+    uint32_t* base = nullptr;
+    {
+        /* once per device, with that device current: the host-side name of the array
+         * is not a device address, so ask the runtime for the address */
+        std::lock_guard<std::mutex> g(g_static_mu);
+        if (!g_static_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_pbn_static_queues);
+            if (e != cudaSuccess || !p)
+                return fail(PBN_ECUDA, "pbn_batch_run_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_static_addr[dev] = static_cast<uint32_t*>(p);
+        }
+        base = g_static_addr[dev];
+    }
+    uint32_t* q = base + 2 * slot;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    /* the array keeps the last call's counters: start this launch's queue at zero */
+    e = cudaMemsetAsync(q, 0, 2 * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
+    BatchParams P;
+    P.nets = static_cast<const NetDesc*>(d_desc);
+    P.items = reinterpret_cast<const WorkItem*>(static_cast<const uint8_t*>(d_desc) + b->nets.size() * sizeof(NetDesc));
+    P.queue = q;
+    P.status = d_status;
+    P.step_offset = step_offset;
+    P.n_items = b->info.n_items;
+    P.n_steps = (uint32_t)n_steps;
+    const size_t smem = b->info.smem_bytes;
+    static size_t configured_static = 48 * 1024;
+    if (smem > configured_static) {
+        e = cudaFuncSetAttribute(pbn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
+        configured_static = smem;
+    }
+    if (!b->occ_per_sm) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pbn_batch_kernel, (int)b->threads, smem);
+        if (e != cudaSuccess || per_sm < 1)
+            return fail(PBN_ETOOBIG, "pbn_batch_run_static: the batch kernel does not fit an SM");
+        b->occ_per_sm = per_sm;
+        b->sms = sm_count();
+    }
+    int per_sm = b->occ_per_sm;
+    if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)b->sms * per_sm, std::max<uint32_t>(1u, b->info.n_items));
+    pbn_batch_kernel<<<grid, b->threads, smem, st>>>(P);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
     return PBN_OK;
 }
