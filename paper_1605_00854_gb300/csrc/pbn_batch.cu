@@ -38,6 +38,7 @@ namespace {
 constexpr uint32_t kWeyl0 = 0x9E3779B9u;
 constexpr uint32_t kWeyl1 = 0xBB67AE85u;
 constexpr uint32_t kMetaRows = 16;
+constexpr uint64_t kSmemCap = 72u * 1024u; /* per-CTA shared memory target: three CTAs per SM */
 
 /* Per-network descriptor in device memory (written by the host, read-only). */
 struct alignas(16) NetDesc {
@@ -50,8 +51,9 @@ struct alignas(16) NetDesc {
     uint32_t smem_state_off, hmax, tables_in_smem, n_meta_rows;
     uint32_t n, W, W32, n_sel;
     uint32_t P, off_words, off_groups, off_multi;
-    uint32_t off_thr, off_inputs, off_selblk, off_ret;
-    uint32_t off_pos, off_tables, pad0, pad1;
+    uint32_t off_selslot, off_thr, off_inputs, off_selblk;
+    uint32_t off_ret, off_pos, off_tables, specs_in_smem;
+    uint32_t nt, pad0, pad1, pad2;
     uint32_t meta_row[kMetaRows];
     uint32_t meta_mask[kMetaRows];
     uint32_t meta_val[kMetaRows];
@@ -82,7 +84,8 @@ struct ItemView {
     uint32_t key0[10], key1[10];
     uint32_t n_traj, n_steps, kv0, kp0, pairs, count_first, init;
     uint32_t n, W, W32, n_sel, P, hmax;
-    uint32_t off_words, off_groups, off_multi, off_thr, off_inputs, off_selblk, off_ret, off_pos, off_tables;
+    uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_ret, off_pos,
+        off_tables;
     uint32_t n_meta_rows;
     const uint32_t* meta_row;
     const uint32_t* meta_mask;
@@ -123,7 +126,7 @@ __global__ void __launch_bounds__(256) pbn_batch_kernel(const BatchParams B) {
         const WorkItem W = B.items[it];
         const NetDesc& D = B.nets[W.net];
         if (W.net != staged) {
-            if (threadIdx.x == 0) {
+            if (threadIdx.x == 0 && D.stage_bytes) {
                 pbn_mbar_arrive_expect_tx(&bar, D.stage_bytes);
                 for (uint32_t off = 0; off < D.stage_bytes; off += 65536u) {
                     const uint32_t sz = (D.stage_bytes - off) < 65536u ? (D.stage_bytes - off) : 65536u;
@@ -135,16 +138,19 @@ __global__ void __launch_bounds__(256) pbn_batch_kernel(const BatchParams B) {
                 meta_sh[k] = k < kMetaRows ? D.meta_row[k] : (k < 2 * kMetaRows ? D.meta_mask[k - kMetaRows]
                                                                                   : D.meta_val[k - 2 * kMetaRows]);
             }
-            bool ok = false;
-            for (uint32_t i = 0; i < (1u << 22); ++i) {
-                if (pbn_mbar_try_wait(&bar, phase)) { ok = true; break; }
-                if (i > 64) __nanosleep(128);
+            bool ok = true;
+            if (D.stage_bytes) {
+                ok = false;
+                for (uint32_t i = 0; i < (1u << 22); ++i) {
+                    if (pbn_mbar_try_wait(&bar, phase)) { ok = true; break; }
+                    if (i > 64) __nanosleep(128);
+                }
             }
             if (__syncthreads_or(!ok)) {
                 failed = true;
                 break;
             }
-            phase ^= 1u;
+            if (D.stage_bytes) phase ^= 1u;
             staged = W.net;
         }
         /* the view of this item */
@@ -180,6 +186,7 @@ __global__ void __launch_bounds__(256) pbn_batch_kernel(const BatchParams B) {
         V.off_words = D.off_words;
         V.off_groups = D.off_groups;
         V.off_multi = D.off_multi;
+        V.off_selslot = D.off_selslot;
         V.off_thr = D.off_thr;
         V.off_inputs = D.off_inputs;
         V.off_selblk = D.off_selblk;
@@ -194,10 +201,12 @@ __global__ void __launch_bounds__(256) pbn_batch_kernel(const BatchParams B) {
         const bool active = slot < W.n;
         const uint64_t lt = (uint64_t)W.t0 + slot;
         uint32_t c[4] = {0, 0, 0, 0};
-        if (D.tables_in_smem)
-            pbn_interp_run<1, false, true>(V, smem, D.smem_state_off, blockDim.x, slot, 0u, lt, active, c);
+        if (D.specs_in_smem && D.tables_in_smem)
+            pbn_interp_run<1, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, 0u, lt, active, c);
+        else if (D.specs_in_smem)
+            pbn_interp_run<1, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, 0u, lt, active, c);
         else
-            pbn_interp_run<1, false, false>(V, smem, D.smem_state_off, blockDim.x, slot, 0u, lt, active, c);
+            pbn_interp_run<1, false, false, false>(V, smem, D.smem_state_off, D.nt, slot, 0u, lt, active, c);
         warp_pool(D.pooled, active, c, V.pairs);
     }
     if (failed) {
@@ -251,7 +260,6 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
     try {
         pbn_batch* B = new pbn_batch();
         const uint32_t T = B->threads;
-        const uint64_t smem_lim = 227u * 1024u; /* per-CTA opt-in shared memory of sm_103a */
         uint64_t smem_max = 0;
         std::vector<double> cost_per_traj(n_nets);
         for (uint32_t i = 0; i < n_nets; ++i) {
@@ -311,11 +319,8 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
             D.seed = a.seed;
             D.n_traj = (uint32_t)a.n_traj;
             D.init = a.init;
-            D.stage_bytes = H.stage_bytes;
             D.image_bytes = H.image_bytes;
-            D.smem_state_off = (H.stage_bytes + 127u) & ~127u;
             D.hmax = H.P ? (31u - (uint32_t)__builtin_ctz(H.P)) / 2u + 1u : 0u;
-            D.tables_in_smem = H.tables_in_smem;
             D.n = H.n;
             D.W = H.W;
             D.W32 = H.W32;
@@ -324,23 +329,44 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
             D.off_words = H.off_words;
             D.off_groups = H.off_groups;
             D.off_multi = H.off_multi;
+            D.off_selslot = H.off_selslot;
             D.off_thr = H.off_thr;
             D.off_inputs = H.off_inputs;
             D.off_selblk = H.off_selblk;
             D.off_ret = H.off_ret;
             D.off_pos = H.off_pos;
             D.off_tables = H.off_tables;
-            const uint64_t need = D.smem_state_off + (uint64_t)plan->per_traj_smem * T;
-            if (need > smem_lim) {
+            /* staging mode and trajectories per work item under the per-CTA cap:
+             * specs and tables staged, specs only, or nothing (read through L1) */
+            const uint64_t per = plan->per_traj_smem;
+            auto fit = [&](uint64_t staged) -> uint32_t {
+                const uint64_t off = (staged + 127u) & ~(uint64_t)127u;
+                if (off + per * 32 > kSmemCap) return 0u;
+                uint64_t nt = (kSmemCap - off) / per;
+                nt = std::min<uint64_t>(T, nt & ~(uint64_t)31);
+                return (uint32_t)nt;
+            };
+            const uint32_t nt_all = H.tables_in_smem ? fit(H.off_ret) : 0u;
+            const uint32_t nt_specs = fit(H.off_tables);
+            const uint32_t nt_none = fit(0);
+            if (nt_all >= std::min<uint32_t>(T, 128u) || (nt_all && nt_all >= nt_specs)) {
+                D.specs_in_smem = 1; D.tables_in_smem = 1; D.stage_bytes = H.off_ret; D.nt = nt_all;
+            } else if (nt_specs >= std::min<uint32_t>(T, 64u) || (nt_specs && nt_specs >= nt_none)) {
+                D.specs_in_smem = 1; D.tables_in_smem = 0; D.stage_bytes = H.off_tables; D.nt = nt_specs;
+            } else if (nt_none) {
+                D.specs_in_smem = 0; D.tables_in_smem = 0; D.stage_bytes = 0; D.nt = nt_none;
+            } else {
                 delete B;
-                return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per CTA", i,
-                            (unsigned long long)need);
+                return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per trajectory", i,
+                            (unsigned long long)per);
             }
+            D.smem_state_off = D.stage_bytes ? ((D.stage_bytes + 127u) & ~127u) : 0u;
+            const uint64_t need = D.smem_state_off + per * D.nt;
             smem_max = std::max(smem_max, need);
             cost_per_traj[i] = plan->info.ops_per_step;
             B->nets.push_back(D);
-            for (uint64_t t0 = 0; t0 < a.n_traj; t0 += T) {
-                WorkItem w{i, (uint32_t)t0, (uint32_t)std::min<uint64_t>(T, a.n_traj - t0), 0u};
+            for (uint64_t t0 = 0; t0 < a.n_traj; t0 += D.nt) {
+                WorkItem w{i, (uint32_t)t0, (uint32_t)std::min<uint64_t>(D.nt, a.n_traj - t0), 0u};
                 B->items.push_back(w);
             }
         }

@@ -553,6 +553,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     std::vector<pbn_img_group> grec;
     std::vector<pbn_img_multi> mrec;
     std::vector<uint32_t> thr, inrec, tables;
+    std::vector<uint32_t> selslot(16 * selblk.size(), 0u);
     uint64_t total_inputs = 0;
     uint32_t n_groups_multi = 0;
     for (uint32_t k = 0; k < W32; ++k) {
@@ -598,14 +599,14 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
                     thr.push_back((uint32_t)t);
                     n_thr++;
                 }
-                M.u_off = 4 * sel_slot(v) | (n_thr << 24);
+                const uint32_t slot = sel_slot(v);
+                M.ch_off = slot;
                 M.radix = (uint32_t)prod;
-                if (n_thr <= 2) {
-                    M.t1 = n_thr >= 1 ? thr[first] : 0u;
-                    M.t2 = n_thr >= 2 ? thr[first + 1] : 0u;
-                } else {
-                    M.t1 = first; /* more than two thresholds: index into the thresholds */
-                }
+                uint32_t* ss = &selslot[4 * slot];
+                ss[0] = n_thr >= 1 ? thr[first] : 0u;
+                ss[1] = n_thr >= 2 ? thr[first + 1] : 0u;
+                ss[2] = n_thr;
+                ss[3] = first;
                 mrec.push_back(M);
                 prod *= fl.size();
                 if (prod > (UINT64_C(1) << 30)) return fail(PBN_ETOOBIG, "group with too many combined functions");
@@ -667,17 +668,18 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.off_words = (uint32_t)off; off = align16(off + words.size() * 4);
     H.off_groups = (uint32_t)off; off = align16(off + grec.size() * sizeof(pbn_img_group));
     H.off_multi = (uint32_t)off; off = align16(off + mrec.size() * sizeof(pbn_img_multi));
+    H.off_selslot = (uint32_t)off; off = align16(off + selslot.size() * 4);
     H.off_thr = (uint32_t)off; off = align16(off + thr.size() * 4);
     H.off_inputs = (uint32_t)off; off = align16(off + inrec.size() * 4);
     H.off_selblk = (uint32_t)off; off = align16(off + selblk.size() * 4);
+    H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
     H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
     H.off_pos = (uint32_t)off; off = align16(off + plan->pos.size() * 4);
-    H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
     if (off >= (UINT64_C(1) << 31)) return fail(PBN_ETOOBIG, "device image of %zu bytes", off);
     H.image_bytes = (uint32_t)off;
     const uint64_t budget = prm.smem_budget ? prm.smem_budget : 160 * 1024;
-    H.tables_in_smem = off <= budget ? 1u : 0u;
-    H.stage_bytes = H.tables_in_smem ? H.image_bytes : H.off_tables;
+    H.tables_in_smem = H.off_ret <= budget ? 1u : 0u;
+    H.stage_bytes = H.tables_in_smem ? H.off_ret : H.off_tables;
     if (H.stage_bytes > budget) return fail(PBN_ETOOBIG, "plan specs of %u bytes exceed the shared-memory budget", H.stage_bytes);
 
     plan->image.assign(off, 0);
@@ -686,6 +688,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     memcpy(img + H.off_words, words.data(), words.size() * 4);
     if (!grec.empty()) memcpy(img + H.off_groups, grec.data(), grec.size() * sizeof(pbn_img_group));
     if (!mrec.empty()) memcpy(img + H.off_multi, mrec.data(), mrec.size() * sizeof(pbn_img_multi));
+    if (!selslot.empty()) memcpy(img + H.off_selslot, selslot.data(), selslot.size() * 4);
     if (!thr.empty()) memcpy(img + H.off_thr, thr.data(), thr.size() * 4);
     if (!inrec.empty()) memcpy(img + H.off_inputs, inrec.data(), inrec.size() * 4);
     if (!selblk.empty()) memcpy(img + H.off_selblk, selblk.data(), selblk.size() * 4);
@@ -693,7 +696,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
     if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);
     plan->hdr = H;
-    plan->per_traj_smem = 4 * (2 * (W32 + 1) + (4 * H.n_sel + 1));
+    plan->per_traj_smem = 4 * (2 * (W32 + 1) + (H.n_sel | 1u));
 
     pbn_plan_info& I = plan->info;
     memset(&I, 0, sizeof(I));

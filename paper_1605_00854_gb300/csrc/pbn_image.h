@@ -10,21 +10,27 @@
  *   words   [W32]        uint2 {first group, number of groups} of state word k
  *   groups  [n_groups]   pbn_img_group, sorted by output word
  *   multi   [n_multi]    pbn_img_multi, the multi-function nodes of each group in
- *                        group bit order
- *   thr     [...]        uint32 selection thresholds T_j < 2^32 (Sec. 2.2 via
- *                        integer cumulative thresholds)
+ *                        group bit order: where their choice is and its radix
+ *   selslot [4 n_sel]    uint4 {t1, t2, n_thr, thr_first} per SEL slot (4 per drawn
+ *                        block, slot = 4 * block index + rank mod 4): the node's
+ *                        integer thresholds (inline when n_thr <= 2); n_thr = 0 for a
+ *                        slot without a retained multi-function node
+ *   thr     [...]        uint32 selection thresholds T_j < 2^32 of every slot
  *   inputs  [...]        uint32 input records, 4 per chunk, each group starting a
  *                        chunk and padded with records of the always-zero row
  *                        W32: (4 * row) << 5 | rot, where row is the state word
  *                        holding input b and rot = (bit - b mod 4) mod 32 rotates
  *                        that bit to position b mod 4 of its chunk
  *   selblk  [n_sel]      uint32 SEL block indices r / 4 drawn per step
- *   ret     [W]          uint64 mask of retained lanes of original word w
- *   pos     [n]          uint32 state position (32 * row + bit) of original node i,
- *                        0xFFFFFFFF for a leaf
  *   tables  [...]        uint32 words of packed table entries; entry e of a group
  *                        with log2 entry width l2w occupies bits
  *                        [e << l2w, (e + 1) << l2w) of its table
+ *   ret     [W]          uint64 mask of retained lanes of original word w
+ *   pos     [n]          uint32 state position (32 * row + bit) of original node i,
+ *                        0xFFFFFFFF for a leaf
+ * ret and pos serve only the initial state and perturbed steps and are read from
+ * global memory; the staged prefix ends at off_tables (specs) or off_ret (specs
+ * and tables).
  */
 #ifndef PBN_IMAGE_H
 #define PBN_IMAGE_H
@@ -42,13 +48,13 @@ typedef struct {
     uint32_t n_multi;    /* multi records */
     uint32_t n_sel;      /* SEL blocks per step */
     uint32_t P;          /* perturbation threshold */
-    uint32_t off_words, off_groups, off_multi, off_thr;
-    uint32_t off_inputs, off_selblk, off_ret, off_pos;
-    uint32_t off_tables;
+    uint32_t off_words, off_groups, off_multi, off_selslot, off_thr;
+    uint32_t off_inputs, off_selblk, off_tables, off_ret, off_pos;
     uint32_t image_bytes;
     uint32_t stage_bytes;
     uint32_t tables_in_smem;
-} pbn_img_header; /* 80 bytes */
+    uint32_t reserved;
+} pbn_img_header; /* 88 bytes */
 
 typedef struct {
     uint32_t tab_off;   /* table offset in uint32 words from the tables section */
@@ -61,12 +67,9 @@ typedef struct {
 } pbn_img_group; /* 16 bytes */
 
 typedef struct {
-    uint32_t u_off;     /* bits 0..23: byte offset of the node's SEL uniform in a
-                           trajectory's uniform row (4 * (4 * selblk index + rank mod 4));
-                           bits 24..31: number of thresholds below 2^32 */
+    uint32_t ch_off;    /* SEL slot of the node = byte offset of its choice in a
+                           trajectory's choice row */
     uint32_t radix;     /* mixed-radix weight of this node's choice */
-    uint32_t t1, t2;    /* the thresholds when there are at most two; otherwise t1 is
-                           the index of the first one in the thresholds section */
-} pbn_img_multi; /* 16 bytes */
+} pbn_img_multi; /* 8 bytes */
 
 #endif

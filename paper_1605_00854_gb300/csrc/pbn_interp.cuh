@@ -56,33 +56,35 @@ __device__ __forceinline__ void or_bit(uint32_t* w, uint32_t bit) {
  * for the caller's pooled reduction.  `smem` holds the staged plan image; the
  * trajectory rows start at smem_state_off.  VT is any type with the fields of
  * the launch parameters (kernel parameters or a per-network descriptor). */
-template <int LG, bool TRACE, bool TAB_SMEM, class VT>
+template <int LG, bool TRACE, bool TAB_SMEM, bool SPEC_SMEM, class VT>
 __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint32_t smem_state_off, uint32_t NT,
                                                uint32_t slot, uint32_t lane, uint64_t lt, bool active,
                                                uint32_t out[4]) {
-    const uint2* WORDS = reinterpret_cast<const uint2*>(smem + P.off_words);
-    const uint4* GROUPS = reinterpret_cast<const uint4*>(smem + P.off_groups);
-    const uint4* MULTI = reinterpret_cast<const uint4*>(smem + P.off_multi);
-    const uint32_t* THR = reinterpret_cast<const uint32_t*>(smem + P.off_thr);
-    const uint4* INPUTS = reinterpret_cast<const uint4*>(smem + P.off_inputs);
-    const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(smem + P.off_selblk);
-    const uint64_t* RET = reinterpret_cast<const uint64_t*>(smem + P.off_ret);
-    const uint32_t* POS = reinterpret_cast<const uint32_t*>(smem + P.off_pos);
+    const uint8_t* SP = SPEC_SMEM ? smem : P.image; /* specs: staged copy or the global image */
+    const uint2* WORDS = reinterpret_cast<const uint2*>(SP + P.off_words);
+    const uint4* GROUPS = reinterpret_cast<const uint4*>(SP + P.off_groups);
+    const uint2* MULTI = reinterpret_cast<const uint2*>(SP + P.off_multi);
+    const uint4* SELSLOT = reinterpret_cast<const uint4*>(SP + P.off_selslot);
+    const uint32_t* THR = reinterpret_cast<const uint32_t*>(SP + P.off_thr);
+    const uint4* INPUTS = reinterpret_cast<const uint4*>(SP + P.off_inputs);
+    const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(SP + P.off_selblk);
+    const uint64_t* RET = reinterpret_cast<const uint64_t*>(P.image + P.off_ret);
+    const uint32_t* POS = reinterpret_cast<const uint32_t*>(P.image + P.off_pos);
     const uint32_t* TAB = TAB_SMEM ? reinterpret_cast<const uint32_t*>(smem + P.off_tables)
                                    : reinterpret_cast<const uint32_t*>(P.image + P.off_tables);
 
     const uint32_t W32 = P.W32;
     const uint32_t W32P = W32 + 1;            /* odd stride: row r of every slot in its own bank */
-    const uint32_t UP = 4 * P.n_sel + 1;      /* odd stride of the SEL uniform rows */
+    const uint32_t CHP = P.n_sel | 1u;        /* odd stride of the choice rows (one word per SEL block) */
     uint32_t* SBASE = reinterpret_cast<uint32_t*>(smem + smem_state_off); /* [2][NT][W32P] */
-    uint32_t* UBASE = SBASE + 2 * NT * W32P;                                 /* [NT][UP] */
+    uint32_t* CBASE = SBASE + 2 * NT * W32P;                                 /* [NT][CHP] */
 
     const uint64_t traj = P.traj_begin + lt;
 
     uint32_t* const S0 = SBASE + slot * W32P;  /* buffer b at S0 + b * bufstride; row W32 stays 0 */
     const uint32_t bufstride = NT * W32P;
-    uint32_t* const Ut = UBASE + slot * UP;
-    const uint8_t* const Ub = reinterpret_cast<const uint8_t*>(Ut);
+    uint32_t* const Ct = CBASE + slot * CHP;  /* byte 4 i + l: choice of SEL slot 4 i + l */
+    const uint8_t* const Cb = reinterpret_cast<const uint8_t*>(Ct);
     uint32_t cur = 0;
 
     uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;
@@ -175,20 +177,35 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
             }
 
             if (!any) {
-                /* ---- 2a. selection draws of the retained multi-function nodes ---- */
+                /* ---- 2a. selection: draw the SEL blocks, turn each slot's uniform into
+                 *          the node's 0-based choice (integer thresholds), one byte each ---- */
+                auto choices = [&](const uint4 x, uint32_t i) -> uint32_t {
+                    const uint32_t u[4] = {x.x, x.y, x.z, x.w};
+                    uint32_t word = 0;
+#pragma unroll
+                    for (int l = 0; l < 4; ++l) {
+                        const uint4 S = SELSLOT[4 * i + l]; /* t1, t2, n_thr, first */
+                        uint32_t j;
+                        if (S.z <= 2u) {
+                            j = ((S.z >= 1u) & (u[l] >= S.x)) + ((S.z >= 2u) & (u[l] >= S.y));
+                        } else {
+                            j = 0;
+                            for (uint32_t q2 = 0; q2 < S.z; ++q2) j += (u[l] >= THR[S.w + q2]) ? 1u : 0u;
+                        }
+                        word |= j << (8 * l);
+                    }
+                    return word;
+                };
                 uint32_t i = lane;
                 for (; i + LG < P.n_sel; i += 2 * LG) {
                     const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_SEL << 28) | SELBLK[i]);
                     const uint4 y = pbn_philox_draw(P, ps, (PBN_DOM_SEL << 28) | SELBLK[i + LG]);
-                    uint32_t* a = Ut + 4 * i;
-                    uint32_t* b = Ut + 4 * (i + LG);
-                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
-                    b[0] = y.x; b[1] = y.y; b[2] = y.z; b[3] = y.w;
+                    Ct[i] = choices(x, i);
+                    Ct[i + LG] = choices(y, i + LG);
                 }
                 if (i < P.n_sel) {
                     const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_SEL << 28) | SELBLK[i]);
-                    uint32_t* a = Ut + 4 * i;
-                    a[0] = x.x; a[1] = x.y; a[2] = x.z; a[3] = x.w;
+                    Ct[i] = choices(x, i);
                 }
                 group_sync<LG>();
                 /* ---- 2b. merged-table evaluation, word by word ---- */
@@ -205,17 +222,8 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                         const uint32_t shift = G.w >> 24;
                         uint32_t c = 0;
                         for (uint32_t m = 0; m < n_mul; ++m) {
-                            const uint4 M = MULTI[G.z + m]; /* u_off|n_thr, radix, t1, t2 */
-                            const uint32_t u = *reinterpret_cast<const uint32_t*>(Ub + (M.x & 0xFFFFFFu));
-                            const uint32_t n_thr = M.x >> 24;
-                            uint32_t j;
-                            if (n_thr <= 2u) {
-                                j = ((n_thr >= 1u) & (u >= M.z)) + ((n_thr >= 2u) & (u >= M.w));
-                            } else {
-                                j = 0;
-                                for (uint32_t q2 = 0; q2 < n_thr; ++q2) j += (u >= THR[M.z + q2]) ? 1u : 0u;
-                            }
-                            c += j * M.y;
+                            const uint2 M = MULTI[G.z + m]; /* choice byte, radix */
+                            c += (uint32_t)Cb[M.x] * M.y;
                         }
                         uint32_t x = 0;
                         const uint4* ch = INPUTS + G.y;

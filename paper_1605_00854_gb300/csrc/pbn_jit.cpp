@@ -144,7 +144,8 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     const uint64_t* ret = V.at<uint64_t>(H.off_ret);
     const uint32_t* pos = V.at<uint32_t>(H.off_pos);
     const uint32_t* tab = V.at<uint32_t>(H.off_tables);
-    const uint32_t table_bytes = H.image_bytes - H.off_tables;
+    const uint32_t table_bytes = H.off_ret - H.off_tables;
+    const uint32_t* selslot = V.at<uint32_t>(H.off_selslot);
     const bool tab_smem = table_bytes <= 48u * 1024u;
     out->tab_bytes = tab_smem ? table_bytes : 0u;
 
@@ -297,12 +298,13 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             std::string cexpr;
             for (uint32_t m = 0; m < G.n_mul; ++m) {
                 const pbn_img_multi& M = multi[G.mul_first + m];
-                const uint32_t slot = (M.u_off & 0xFFFFFFu) / 4u;
+                const uint32_t slot = M.ch_off;
                 const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
-                const uint32_t n_thr = M.u_off >> 24;
+                const uint32_t* ss = selslot + 4 * slot; /* t1, t2, n_thr, first */
+                const uint32_t n_thr = ss[2];
                 std::string j;
                 for (uint32_t q = 0; q < n_thr; ++q) {
-                    const uint32_t T = n_thr <= 2 ? (q == 0 ? M.t1 : M.t2) : thr[M.t1 + q];
+                    const uint32_t T = n_thr <= 2 ? ss[q] : thr[ss[3] + q];
                     j += (q ? " + " : "") + fmt("(uint32_t)(%s >= %s)", u.c_str(), hex32(T).c_str());
                 }
                 if (j.empty()) continue;

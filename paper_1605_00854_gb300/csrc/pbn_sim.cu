@@ -63,7 +63,7 @@ struct SimParams {
     uint32_t smem_state_off;   /* byte offset of the state rows in dynamic smem */
     uint32_t hmax;             /* level pairs that can still decide a perturbation */
     uint32_t n, W, W32, n_sel, P;
-    uint32_t off_words, off_groups, off_multi, off_thr, off_inputs, off_selblk, off_ret, off_pos, off_tables;
+    uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_ret, off_pos, off_tables;
     uint32_t n_meta_rows;
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
     const uint64_t lt = (uint64_t)blockIdx.x * P.nt + slot;
     const bool active = lt < P.n_traj;
     uint32_t c[4] = {0, 0, 0, 0};
-    pbn_interp_run<LG, TRACE, TAB_SMEM>(P, smem, P.smem_state_off, P.nt, slot, lane, lt, active, c);
+    pbn_interp_run<LG, TRACE, TAB_SMEM, true>(P, smem, P.smem_state_off, P.nt, slot, lane, lt, active, c);
     const uint32_t cV = c[0], c01 = c[1], c10 = c[2], c11 = c[3];
 
     /* ---- pooled counts: warp reduction, one atomic per warp and count ---- */
@@ -235,6 +235,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.off_words = H.off_words;
     P.off_groups = H.off_groups;
     P.off_multi = H.off_multi;
+    P.off_selslot = H.off_selslot;
     P.off_thr = H.off_thr;
     P.off_inputs = H.off_inputs;
     P.off_selblk = H.off_selblk;

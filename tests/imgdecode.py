@@ -4,14 +4,14 @@ import struct
 import numpy as np
 
 HEADER_FIELDS = ["magic", "n", "W", "W32", "n_groups", "n_multi", "n_sel", "P",
-                 "off_words", "off_groups", "off_multi", "off_thr", "off_inputs",
-                 "off_selblk", "off_ret", "off_pos", "off_tables", "image_bytes",
-                 "stage_bytes", "tables_in_smem"]
+                 "off_words", "off_groups", "off_multi", "off_selslot", "off_thr", "off_inputs",
+                 "off_selblk", "off_tables", "off_ret", "off_pos", "image_bytes",
+                 "stage_bytes", "tables_in_smem", "reserved"]
 
 
 def decode(img: np.ndarray) -> dict:
     b = img.tobytes()
-    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<20I", b, 0)))
+    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<22I", b, 0)))
     u32 = np.frombuffer(b, dtype=np.uint32)
     words = u32[H["off_words"] // 4: H["off_words"] // 4 + 2 * H["W32"]].reshape(-1, 2)
     groups = []
@@ -22,8 +22,9 @@ def decode(img: np.ndarray) -> dict:
                            n_mul=n_mul, shift=shift))
     multi = []
     for m in range(H["n_multi"]):
-        u_off, radix, t1, t2 = struct.unpack_from("<4I", b, H["off_multi"] + 16 * m)
-        multi.append(dict(u_slot=(u_off & 0xFFFFFF) // 4, n_thr=u_off >> 24, radix=radix, t1=t1, t2=t2))
+        ch_off, radix = struct.unpack_from("<2I", b, H["off_multi"] + 8 * m)
+        t1, t2, n_thr, first = struct.unpack_from("<4I", b, H["off_selslot"] + 16 * ch_off)
+        multi.append(dict(u_slot=ch_off, n_thr=n_thr, radix=radix, t1=t1, t2=t2, first=first))
     sel = u32[H["off_selblk"] // 4: H["off_selblk"] // 4 + H["n_sel"]]
     pos = u32[H["off_pos"] // 4: H["off_pos"] // 4 + H["n"]]
     ret = np.frombuffer(b, dtype=np.uint64)[H["off_ret"] // 8: H["off_ret"] // 8 + H["W"]]
@@ -34,7 +35,7 @@ def thresholds(D, m):
     M = D["multi"][m]
     if M["n_thr"] <= 2:
         return [M["t1"], M["t2"]][: M["n_thr"]]
-    o = D["H"]["off_thr"] // 4 + M["t1"]
+    o = D["H"]["off_thr"] // 4 + M["first"]
     return [int(v) for v in D["u32"][o: o + M["n_thr"]]]
 
 
