@@ -153,6 +153,15 @@ def oracle_rate(text: str, n: int, target_s: float, meta=META):
     return n * cores * steps / dt, cores, f"{cores} trajectories x {steps} steps of the same network (unreduced, ungrouped Eq. 1 simulator)", dt
 
 
+def workload_network(args):
+    """(network, meta nodes, description) of the single-network workloads."""
+    if args.workload == "scalefree2000":
+        return (synth.scalefree2000(seed=3), [0, 1, 2, 3],
+                "scale-free PBN n=2000 (power-law out-degree 2.5; in-degree 1-6; 1-3 functions; p=1e-5), "
+                "reduced+grouped (<=8 inputs/group)")
+    return synth.paper100(seed=2), META, WORKLOAD
+
+
 # ------------------------------------------------------------------- ours ----
 def run_ours(args):
     import torch
@@ -165,15 +174,23 @@ def run_ours(args):
     dev = torch.device("cuda", local if ws > 1 else 0)
     torch.cuda.set_device(dev)
 
-    net_obj = synth.paper100(seed=2)
+    net_obj, meta, workload = workload_network(args)
     text = net_obj.to_text()
     n = net_obj.n
     t_prep = time.perf_counter()
-    red, retained = api.Net.load(text).reduce(META)
+    red, retained = api.Net.load(text).reduce(meta)
     plan = api.Plan(red)
-    compile_ms = plan.compile() if args.kernel == "compiled" else 0.0
+    compile_ms = 0.0
+    if args.kernel == "compiled":
+        try:
+            compile_ms = plan.compile()
+        except _lib.PbnError:
+            args.kernel = "interpreter"  # plan too wide to compile: the interpreter runs it
     prep_s = time.perf_counter() - t_prep
     kern = _lib.PBN_KERNEL_COMPILED if args.kernel == "compiled" else _lib.PBN_KERNEL_INTERP
+    T = args.n_traj if args.n_traj else (1 << 16 if args.workload == "paper100" else 1 << 14)
+    S = args.n_steps if args.n_steps else (10**6 if args.workload == "paper100" else 10**5)
+    args.n_traj, args.n_steps = T, S
     P = api.Net.load(text).info().P
     info = plan.info
     T, S = args.n_traj, args.n_steps
@@ -184,7 +201,7 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)
 
     def one_step():
-        api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=META, traj_begin=traj_begin,
+        api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=meta, traj_begin=traj_begin,
                      stream=stream, d_image=d_img, kernel=kern)
 
     for _ in range(args.warmup):
@@ -247,7 +264,7 @@ def run_ours(args):
     e2e_value = n * T * S * ws * e2e_steps / e2e_total
 
     compare = {}
-    if rank == 0 and args.compare_steps > 0:
+    if rank == 0 and args.compare_steps > 0 and args.workload == "paper100":
         # the same workload on shorter passes: interpreter and the unmerged method
         plain_plan = api.Plan(api.Net.load(text), mode=_lib.PBN_PLAN_PLAIN)
         variants = [("interpreter_grouped", plan, _lib.PBN_KERNEL_INTERP),
@@ -256,12 +273,12 @@ def run_ours(args):
         for name, pl, kk in variants:
             b2 = api.alloc_buffers(pl, T, dev)
             img2 = pl.device_image(dev)
-            api.simulate(pl, b2, seed=SEED, n_steps=1000, meta_ids=META, stream=stream, d_image=img2, kernel=kk)
+            api.simulate(pl, b2, seed=SEED, n_steps=1000, meta_ids=meta, stream=stream, d_image=img2, kernel=kk)
             torch.cuda.synchronize()
             flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            api.simulate(pl, b2, seed=SEED, n_steps=args.compare_steps, meta_ids=META, stream=stream,
+            api.simulate(pl, b2, seed=SEED, n_steps=args.compare_steps, meta_ids=meta, stream=stream,
                          d_image=img2, kernel=kk)
             e1.record(stream)
             torch.cuda.synchronize()
@@ -286,9 +303,9 @@ def run_ours(args):
             "value": value, "unit": "node-updates/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": kernel_s * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "n_retained": int(info.n_retained),
+            "config": {"workload": workload, "n": n, "n_retained": int(info.n_retained),
                        "groups": int(info.n_groups), "n_traj_per_gpu": T, "n_steps": S,
-                       "seed": SEED, "meta": META, "l2": "flushed between timed steps (256 MiB write)",
+                       "seed": SEED, "meta": meta, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas{ws} (disjoint trajectory ids)",
                        "host_prep_s": round(prep_s, 4), "compile_ms": round(compile_ms, 1),
                        "kernel": args.kernel},
@@ -312,21 +329,125 @@ def run_ours(args):
     return out
 
 
+# ------------------------------------------------------------- batched form ----
+def run_batch(args):
+    """256 networks of the paper-scale generator with n log-uniform in [20, 4000],
+    trajectories log-uniform in [1024, 65536] and p log-uniform in [1e-5, 1e-2]:
+    one persistent launch per step chunk (device work queue), against one launch per
+    network of the interpreter and of the compiled plain (unmerged) method."""
+    import torch
+    shapes = synth.batch_shapes(seed=4, count=args.batch_count)
+    S = args.n_steps if args.n_steps else 10**4
+    entries, plain = [], []
+    t0 = time.perf_counter()
+    tot = 0.0
+    for i, (n, T, p) in enumerate(shapes):
+        text = synth.batch_network(seed=5000 + i, n=n, p=p).to_text()
+        red, _ = api.Net.load(text).reduce(META)
+        plan = api.Plan(red)
+        entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=SEED + i, meta_ids=META))
+        plain.append(text)
+        tot += n * T * S
+    prep = time.perf_counter() - t0
+    B = api.Batch(entries)
+    chunk = args.chunk_steps
+    B.run(min(chunk, S))
+    torch.cuda.synchronize()
+    for e in entries:
+        e["bufs"].counts.zero_(); e["bufs"].pooled.zero_()
+    g = B.capture([chunk] * (S // chunk) + ([S % chunk] if S % chunk else []))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(); g.replay(); e1.record(); torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) / 1e3
+    assert int(B.status.item()) == 0
+    # one interpreter launch per network (grouped plans), same steps
+    e0.record()
+    for e in entries:
+        api.simulate(e["plan"], e["bufs"], seed=e["seed"], n_steps=S, meta_ids=META, kernel=_lib.PBN_KERNEL_INTERP)
+    e1.record(); torch.cuda.synchronize()
+    t_each = e0.elapsed_time(e1) / 1e3
+    line = {"metric": "PBN node-updates/s, batched persistent launch (256 networks)", "value": tot / t_batch,
+            "unit": "node-updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": t_batch * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "batch of 256 paper-scale PBNs, n log-uniform [20,4000], trajectories log-uniform "
+                       "[1024,65536], p log-uniform [1e-5,1e-2]", "n_steps": S, "chunk_steps": chunk,
+                       "work_items": int(B.info.n_items), "smem_per_cta": int(B.info.smem_bytes),
+                       "host_prep_s": round(prep, 2), "graph": "chunk launches captured in one CUDA graph"},
+            "per_network_launches": {"value": tot / t_each, "unit": "node-updates/s", "seconds": t_each},
+            "speedup_vs_per_network": t_each / t_batch}
+    print(json.dumps(line), flush=True)
+
+
+def run_serve(args):
+    """Poisson query arrivals (rate per second for a duration), each a fresh PBN of the
+    paper-scale generator with n log-uniform in [30, 3000] and a meta-state of 1-4
+    nodes, precision r = 0.01 at 95% confidence, served with continuous batching."""
+    from paper_1605_00854_gb300 import serve
+    import numpy as np
+    rng = np.random.default_rng(5)
+    n_q = int(args.serve_rate * args.serve_seconds)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=n_q)
+    queries = []
+    for i in range(n_q):
+        n = int(round(math.exp(rng.uniform(math.log(30), math.log(3000)))))
+        k = int(rng.integers(1, 5))
+        meta = sorted(int(x) for x in rng.choice(4, size=k, replace=False))
+        text = synth.paper100(seed=9000 + i, n=n, p=float(10 ** rng.uniform(-4, -2))).to_text()
+        queries.append(serve.Query(qid=i, text=text, meta_ids=meta, seed=SEED + i, r=0.01, s=0.95))
+    srv = serve.Server(n_traj=args.serve_traj, chunk_steps=args.chunk_steps, mem_cap_bytes=100e9,
+                       workers=os.cpu_count() or 8)
+    t_start = time.perf_counter()
+    due = t_start + np.cumsum(gaps)
+    k = 0
+    while k < n_q or srv.pending:
+        now = time.perf_counter()
+        while k < n_q and due[k] <= now:
+            queries[k].arrival = due[k]
+            srv.submit(queries[k])
+            k += 1
+        if not srv.step():
+            time.sleep(0.0005)
+    makespan = time.perf_counter() - t_start
+    srv.close()
+    lat = serve.latency_summary(srv.done)
+    line = {"metric": "served steady-state queries: p50/p99 latency, queries/s, node-updates/s",
+            "value": lat.get("p99_s"), "unit": "s (p99 latency)", "higher_is_better": False, "n_gpus": 1,
+            "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95",
+                       "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "queries": n_q,
+                       "trajectories_per_query": args.serve_traj, "chunk_steps": args.chunk_steps,
+                       "memory_cap_bytes": 100e9},
+            "latency": lat, "queries_per_s": len(srv.done) / makespan,
+            "node_updates_per_s": srv.node_updates / makespan, "makespan_s": makespan,
+            "completed": len(srv.done), "rejected": len(srv.rejected)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n-traj", type=int, default=1 << 16)
-    ap.add_argument("--n-steps", type=int, default=10**6)
+    ap.add_argument("--n-traj", type=int, default=0, help="trajectories per GPU (default per workload)")
+    ap.add_argument("--n-steps", type=int, default=0, help="steps per pass (default per workload)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter"])
+    ap.add_argument("--workload", default="paper100", choices=["paper100", "scalefree2000", "batch", "serve"])
+    ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--chunk-steps", type=int, default=1000)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-traj", type=int, default=512)
     ap.add_argument("--compare-steps", type=int, default=100000,
                     help="steps of the comparison passes (interpreter, plain method); 0 = skip")
     args = ap.parse_args()
     ws, rank, _ = dist_env()
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     net_obj = synth.paper100(seed=2)
     text = net_obj.to_text()
@@ -349,8 +470,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(vals),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
                 "data": "synthetic", "impl": "reference",
-                "config": {"workload": WORKLOAD, "n": n, "n_traj_per_gpu": args.n_traj,
-                           "n_steps": args.n_steps, "seed": SEED, "meta": META,
+                "config": {"workload": WORKLOAD, "n": n, "n_traj_per_gpu": args.n_traj or (1 << 16),
+                           "n_steps": args.n_steps or 10**6, "seed": SEED, "meta": META,
                            "parallelism": "host cores (trajectories split over threads)"},
                 "cpu_baseline": {"value": value, "unit": "node-updates/s", "cores": last[0],
                                  "kind": "oracle", "sample": last[1]},

@@ -38,7 +38,8 @@ namespace {
 constexpr uint32_t kWeyl0 = 0x9E3779B9u;
 constexpr uint32_t kWeyl1 = 0xBB67AE85u;
 constexpr uint32_t kMetaRows = 16;
-constexpr uint64_t kSmemCap = 72u * 1024u; /* per-CTA shared memory target: three CTAs per SM */
+constexpr uint64_t kSmemCap = 224u * 1024u; /* per-CTA shared memory: one 512-thread CTA per SM, so
+                                                 the specs of every network fit in shared memory */
 
 /* Per-network descriptor in device memory (written by the host, read-only). */
 struct alignas(16) NetDesc {
@@ -107,7 +108,7 @@ __device__ __forceinline__ void warp_pool(unsigned long long* pooled, bool lead,
     }
 }
 
-__global__ void __launch_bounds__(256) pbn_batch_kernel(const BatchParams B) {
+__global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t item_sh;
@@ -248,7 +249,7 @@ struct pbn_batch {
     std::vector<NetDesc> nets;
     std::vector<WorkItem> items;
     std::vector<uint8_t> image; /* nets then items */
-    uint32_t threads = 256;
+    uint32_t threads = 512;
     mutable int occ_per_sm = 0;  /* occupancy of the batch kernel, queried on the first run */
     mutable int sms = 0;
 };
@@ -349,9 +350,9 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
             const uint32_t nt_all = H.tables_in_smem ? fit(H.off_ret) : 0u;
             const uint32_t nt_specs = fit(H.off_tables);
             const uint32_t nt_none = fit(0);
-            if (nt_all >= std::min<uint32_t>(T, 128u) || (nt_all && nt_all >= nt_specs)) {
+            if (nt_all >= std::min<uint32_t>(T, 256u) || (nt_all && nt_all >= nt_specs)) {
                 D.specs_in_smem = 1; D.tables_in_smem = 1; D.stage_bytes = H.off_ret; D.nt = nt_all;
-            } else if (nt_specs >= std::min<uint32_t>(T, 64u) || (nt_specs && nt_specs >= nt_none)) {
+            } else if (nt_specs) {
                 D.specs_in_smem = 1; D.tables_in_smem = 0; D.stage_bytes = H.off_tables; D.nt = nt_specs;
             } else if (nt_none) {
                 D.specs_in_smem = 0; D.tables_in_smem = 0; D.stage_bytes = 0; D.nt = nt_none;

@@ -15,6 +15,7 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -376,15 +377,23 @@ void join(Grp* g, const Item& it) {
  * items no group could take. */
 size_t find_partitions(const std::vector<Item>& S, size_t m, const Caps& cp, std::vector<Grp>* out) {
     std::vector<Grp> A(m);
+    /* groups ordered by (weight, index): the first feasible one in this order is the
+     * lightest feasible group with ties to the lowest index */
+    std::set<std::pair<uint64_t, size_t>> order;
+    for (size_t i = 0; i < m; ++i) order.insert({0, i});
     size_t unplaced = 0;
     for (const Item& it : S) {
         size_t best = SIZE_MAX;
-        for (size_t i = 0; i < m; ++i) {
-            if (!can_join(A[i], it, cp)) continue;
-            if (best == SIZE_MAX || A[i].weight < A[best].weight) best = i;
+        for (auto o = order.begin(); o != order.end(); ++o) {
+            if (can_join(A[o->second], it, cp)) {
+                best = o->second;
+                order.erase(o);
+                break;
+            }
         }
         if (best == SIZE_MAX) { ++unplaced; continue; }
         join(&A[best], it);
+        order.insert({A[best].weight, best});
     }
     out->swap(A);
     return unplaced;
