@@ -399,7 +399,8 @@ def run_serve(args):
     t_start = time.perf_counter()
     due = t_start + np.cumsum(gaps)
     k = 0
-    while k < n_q or srv.pending:
+    t_limit = t_start + args.serve_seconds * 20 + 120
+    while (k < n_q or srv.pending) and time.perf_counter() < t_limit:
         now = time.perf_counter()
         while k < n_q and due[k] <= now:
             queries[k].arrival = due[k]
@@ -419,7 +420,8 @@ def run_serve(args):
                        "memory_cap_bytes": 100e9},
             "latency": lat, "queries_per_s": len(srv.done) / makespan,
             "node_updates_per_s": srv.node_updates / makespan, "makespan_s": makespan,
-            "completed": len(srv.done), "rejected": len(srv.rejected)}
+            "completed": len(srv.done), "rejected": len(srv.rejected), "failed": len(srv.failed),
+            "unfinished": n_q - len(srv.done) - len(srv.rejected) - len(srv.failed)}
     print(json.dumps(line), flush=True)
 
 

@@ -54,7 +54,7 @@ struct alignas(16) NetDesc {
     uint32_t P, off_words, off_groups, off_multi;
     uint32_t off_selslot, off_thr, off_inputs, off_selblk;
     uint32_t off_ret, off_pos, off_tables, specs_in_smem;
-    uint32_t nt, pad0, pad1, pad2;
+    uint32_t nt, off_gorder, n_groups, lg;
     uint32_t meta_row[kMetaRows];
     uint32_t meta_mask[kMetaRows];
     uint32_t meta_val[kMetaRows];
@@ -85,8 +85,8 @@ struct ItemView {
     uint32_t key0[10], key1[10];
     uint32_t n_traj, n_steps, kv0, kp0, pairs, count_first, init;
     uint32_t n, W, W32, n_sel, P, hmax;
-    uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_ret, off_pos,
-        off_tables;
+    uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret,
+        off_pos, off_tables, n_groups;
     uint32_t n_meta_rows;
     const uint32_t* meta_row;
     const uint32_t* meta_mask;
@@ -188,6 +188,8 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
         V.off_groups = D.off_groups;
         V.off_multi = D.off_multi;
         V.off_selslot = D.off_selslot;
+        V.off_gorder = D.off_gorder;
+        V.n_groups = D.n_groups;
         V.off_thr = D.off_thr;
         V.off_inputs = D.off_inputs;
         V.off_selblk = D.off_selblk;
@@ -198,17 +200,31 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
         V.meta_row = meta_sh;
         V.meta_mask = meta_sh + kMetaRows;
         V.meta_val = meta_sh + 2 * kMetaRows;
-        const uint32_t slot = threadIdx.x;
+        /* D.lg lanes per trajectory, D.nt trajectory slots per item */
+        const uint32_t lg = D.lg;
+        const uint32_t slot = threadIdx.x / lg;
+        const uint32_t lane = threadIdx.x % lg;
         const bool active = slot < W.n;
         const uint64_t lt = (uint64_t)W.t0 + slot;
         uint32_t c[4] = {0, 0, 0, 0};
-        if (D.specs_in_smem && D.tables_in_smem)
-            pbn_interp_run<1, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, 0u, lt, active, c);
-        else if (D.specs_in_smem)
-            pbn_interp_run<1, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, 0u, lt, active, c);
-        else
-            pbn_interp_run<1, false, false, false>(V, smem, D.smem_state_off, D.nt, slot, 0u, lt, active, c);
-        warp_pool(D.pooled, active, c, V.pairs);
+        if (!D.specs_in_smem) {
+            pbn_interp_run<1, false, false, false>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c);
+        } else if (D.tables_in_smem) {
+            switch (lg) {
+                case 1: pbn_interp_run<1, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+                case 2: pbn_interp_run<2, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+                case 4: pbn_interp_run<4, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+                default: pbn_interp_run<8, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+            }
+        } else {
+            switch (lg) {
+                case 1: pbn_interp_run<1, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+                case 2: pbn_interp_run<2, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+                case 4: pbn_interp_run<4, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+                default: pbn_interp_run<8, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
+            }
+        }
+        warp_pool(D.pooled, active && lane == 0, c, V.pairs);
     }
     if (failed) {
         for (uint32_t i = 0; i < (1u << 22); ++i) /* let copies in flight land */
@@ -331,6 +347,8 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
             D.off_groups = H.off_groups;
             D.off_multi = H.off_multi;
             D.off_selslot = H.off_selslot;
+            D.off_gorder = H.off_gorder;
+            D.n_groups = H.n_groups;
             D.off_thr = H.off_thr;
             D.off_inputs = H.off_inputs;
             D.off_selblk = H.off_selblk;
@@ -362,6 +380,11 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
                             (unsigned long long)per);
             }
             D.smem_state_off = D.stage_bytes ? ((D.stage_bytes + 127u) & ~127u) : 0u;
+            /* lanes per trajectory: fill the CTA's threads when few trajectories fit
+             * (wide states); lane groups evaluate groups in shape order */
+            D.lg = 1;
+            if (D.specs_in_smem)
+                while (D.lg < 8 && D.nt * D.lg * 2 <= T && D.W32 >= 8 * D.lg) D.lg *= 2;
             const uint64_t need = D.smem_state_off + per * D.nt;
             smem_max = std::max(smem_max, need);
             cost_per_traj[i] = plan->info.ops_per_step;

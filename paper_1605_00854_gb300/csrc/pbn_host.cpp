@@ -659,6 +659,21 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
         }
     }
 
+    /* evaluation order for lane groups: by shape, so lanes run in step */
+    std::vector<uint32_t> gorder(grec.size());
+    {
+        std::vector<uint32_t> gword(grec.size());
+        for (uint32_t k = 0; k < W32; ++k)
+            for (uint32_t gi = words[2 * k]; gi < words[2 * k] + words[2 * k + 1]; ++gi) gword[gi] = k;
+        std::vector<uint32_t> idx(grec.size());
+        std::iota(idx.begin(), idx.end(), 0u);
+        std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+            const uint32_t qa = (grec[a].q + 3) / 4, qb = (grec[b].q + 3) / 4;
+            if (qa != qb) return qa > qb;
+            return grec[a].n_mul > grec[b].n_mul;
+        });
+        for (size_t k = 0; k < idx.size(); ++k) gorder[k] = idx[k] | (gword[idx[k]] << 20);
+    }
     std::vector<uint64_t> ret(W, 0);
     for (uint32_t v = 0; v < n; ++v)
         if (g.retained[v]) ret[v >> 6] |= 1ull << (v & 63);
@@ -681,6 +696,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.off_thr = (uint32_t)off; off = align16(off + thr.size() * 4);
     H.off_inputs = (uint32_t)off; off = align16(off + inrec.size() * 4);
     H.off_selblk = (uint32_t)off; off = align16(off + selblk.size() * 4);
+    H.off_gorder = (uint32_t)off; off = align16(off + gorder.size() * 4);
     H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
     H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
     H.off_pos = (uint32_t)off; off = align16(off + plan->pos.size() * 4);
@@ -701,6 +717,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     if (!thr.empty()) memcpy(img + H.off_thr, thr.data(), thr.size() * 4);
     if (!inrec.empty()) memcpy(img + H.off_inputs, inrec.data(), inrec.size() * 4);
     if (!selblk.empty()) memcpy(img + H.off_selblk, selblk.data(), selblk.size() * 4);
+    if (!gorder.empty()) memcpy(img + H.off_gorder, gorder.data(), gorder.size() * 4);
     memcpy(img + H.off_ret, ret.data(), ret.size() * 8);
     memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
     if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);

@@ -22,6 +22,9 @@
  *                        holding input b and rot = (bit - b mod 4) mod 32 rotates
  *                        that bit to position b mod 4 of its chunk
  *   selblk  [n_sel]      uint32 SEL block indices r / 4 drawn per step
+ *   gorder  [n_groups]   uint32 group index | output word << 20, groups sorted by
+ *                        shape (inputs, multi-function nodes): the evaluation order
+ *                        when several lanes share a trajectory
  *   tables  [...]        uint32 words of packed table entries; entry e of a group
  *                        with log2 entry width l2w occupies bits
  *                        [e << l2w, (e + 1) << l2w) of its table
@@ -49,11 +52,10 @@ typedef struct {
     uint32_t n_sel;      /* SEL blocks per step */
     uint32_t P;          /* perturbation threshold */
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr;
-    uint32_t off_inputs, off_selblk, off_tables, off_ret, off_pos;
+    uint32_t off_inputs, off_selblk, off_gorder, off_tables, off_ret, off_pos;
     uint32_t image_bytes;
     uint32_t stage_bytes;
     uint32_t tables_in_smem;
-    uint32_t reserved;
 } pbn_img_header; /* 88 bytes */
 
 typedef struct {

@@ -68,6 +68,7 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
     const uint32_t* THR = reinterpret_cast<const uint32_t*>(SP + P.off_thr);
     const uint4* INPUTS = reinterpret_cast<const uint4*>(SP + P.off_inputs);
     const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(SP + P.off_selblk);
+    const uint32_t* GORDER = reinterpret_cast<const uint32_t*>(SP + P.off_gorder);
     const uint64_t* RET = reinterpret_cast<const uint64_t*>(P.image + P.off_ret);
     const uint32_t* POS = reinterpret_cast<const uint32_t*>(P.image + P.off_pos);
     const uint32_t* TAB = TAB_SMEM ? reinterpret_cast<const uint32_t*>(smem + P.off_tables)
@@ -208,43 +209,57 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                     Ct[i] = choices(x, i);
                 }
                 group_sync<LG>();
-                /* ---- 2b. merged-table evaluation, word by word ---- */
+                /* ---- 2b. merged-table evaluation ---- */
                 const uint8_t* Sc8 = reinterpret_cast<const uint8_t*>(Sc);
                 uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
-                for (uint32_t w = lane; w < W32; w += LG) {
-                    const uint2 wr = WORDS[w];
-                    uint32_t acc = 0;
-                    for (uint32_t gi = wr.x; gi < wr.x + wr.y; ++gi) {
-                        const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
-                        const uint32_t q = G.w & 0xFFu;
-                        const uint32_t l2w = (G.w >> 8) & 0xFFu;
-                        const uint32_t n_mul = (G.w >> 16) & 0xFFu;
-                        const uint32_t shift = G.w >> 24;
-                        uint32_t c = 0;
-                        for (uint32_t m = 0; m < n_mul; ++m) {
-                            const uint2 M = MULTI[G.z + m]; /* choice byte, radix */
-                            c += (uint32_t)Cb[M.x] * M.y;
-                        }
-                        uint32_t x = 0;
-                        const uint4* ch = INPUTS + G.y;
-                        for (uint32_t b0 = 0; b0 < q; b0 += 4) {
-                            const uint4 R = *ch++;
-                            const uint32_t v0 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.x >> 5));
-                            const uint32_t v1 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.y >> 5));
-                            const uint32_t v2 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.z >> 5));
-                            const uint32_t v3 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.w >> 5));
-                            uint32_t x4 = __funnelshift_r(v0, v0, R.x) & 1u;
-                            x4 |= __funnelshift_r(v1, v1, R.y) & 2u;
-                            x4 |= __funnelshift_r(v2, v2, R.z) & 4u;
-                            x4 |= __funnelshift_r(v3, v3, R.w) & 8u;
-                            x |= x4 << b0;
-                        }
-                        const uint32_t bo = ((c << q) | x) << l2w;
-                        const uint32_t tw = TAB_SMEM ? TAB[G.x + (bo >> 5)] : __ldg(TAB + G.x + (bo >> 5));
-                        const uint32_t emask = (2u << ((1u << l2w) - 1u)) - 1u;
-                        acc |= ((tw >> (bo & 31u)) & emask) << shift;
+                /* new bits of group gi, already at their place in the output word */
+                auto group_bits = [&](uint32_t gi) -> uint32_t {
+                    const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
+                    const uint32_t q = G.w & 0xFFu;
+                    const uint32_t l2w = (G.w >> 8) & 0xFFu;
+                    const uint32_t n_mul = (G.w >> 16) & 0xFFu;
+                    const uint32_t shift = G.w >> 24;
+                    uint32_t c = 0;
+                    for (uint32_t m = 0; m < n_mul; ++m) {
+                        const uint2 M = MULTI[G.z + m]; /* choice byte, radix */
+                        c += (uint32_t)Cb[M.x] * M.y;
                     }
-                    Sn[w] = acc;
+                    uint32_t x = 0;
+                    const uint4* ch = INPUTS + G.y;
+                    for (uint32_t b0 = 0; b0 < q; b0 += 4) {
+                        const uint4 R = *ch++;
+                        const uint32_t v0 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.x >> 5));
+                        const uint32_t v1 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.y >> 5));
+                        const uint32_t v2 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.z >> 5));
+                        const uint32_t v3 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.w >> 5));
+                        uint32_t x4 = __funnelshift_r(v0, v0, R.x) & 1u;
+                        x4 |= __funnelshift_r(v1, v1, R.y) & 2u;
+                        x4 |= __funnelshift_r(v2, v2, R.z) & 4u;
+                        x4 |= __funnelshift_r(v3, v3, R.w) & 8u;
+                        x |= x4 << b0;
+                    }
+                    const uint32_t bo = ((c << q) | x) << l2w;
+                    const uint32_t tw = TAB_SMEM ? TAB[G.x + (bo >> 5)] : __ldg(TAB + G.x + (bo >> 5));
+                    const uint32_t emask = (2u << ((1u << l2w) - 1u)) - 1u;
+                    return ((tw >> (bo & 31u)) & emask) << shift;
+                };
+                if (LG == 1) {
+                    /* word by word, the word's groups ORed in a register */
+                    for (uint32_t w = 0; w < W32; ++w) {
+                        const uint2 wr = WORDS[w];
+                        uint32_t acc = 0;
+                        for (uint32_t gi = wr.x; gi < wr.x + wr.y; ++gi) acc |= group_bits(gi);
+                        Sn[w] = acc;
+                    }
+                } else {
+                    /* the lanes of a trajectory take the groups in shape order (so they
+                     * run in step) and OR their bits into the shared next-state words */
+                    for (uint32_t w = lane; w < W32; w += LG) Sn[w] = 0u;
+                    group_sync<LG>();
+                    for (uint32_t k = lane; k < P.n_groups; k += LG) {
+                        const uint32_t go = GORDER[k];
+                        atomicOr(&Sn[go >> 20], group_bits(go & 0xFFFFFu));
+                    }
                 }
                 group_sync<LG>();
                 cur ^= 1u;

@@ -99,6 +99,7 @@ class Server:
         self.active = []
         self.done = []
         self.rejected = []         # queries needing more bytes than the cap
+        self.failed = []           # (qid, error) of queries whose preparation failed
         self.in_use = 0
         self.stream = torch.cuda.Stream(self.dev)
         self.pending = 0
@@ -107,16 +108,21 @@ class Server:
 
     # -- preparation (host worker threads) -------------------------------------------
     def _prepare(self, q: Query):
-        t0 = time.perf_counter()
-        net = api.Net.load(q.text)
-        red, _ = net.reduce(q.meta_ids)
-        plan = api.Plan(red)
-        n = net.info().n
-        with self.torch.cuda.stream(self.stream):
-            plan.device_image(self.dev)
-            bufs = api.alloc_buffers(plan, self.n_traj, self.dev)
-        nbytes = query_bytes(plan, self.n_traj)
-        self.prepared.put((q, plan, bufs, n, time.perf_counter() - t0, nbytes))
+        try:
+            t0 = time.perf_counter()
+            net = api.Net.load(q.text)
+            red, _ = net.reduce(q.meta_ids)
+            plan = api.Plan(red)
+            n = net.info().n
+            with self.torch.cuda.stream(self.stream):
+                plan.device_image(self.dev)
+                bufs = api.alloc_buffers(plan, self.n_traj, self.dev)
+            nbytes = query_bytes(plan, self.n_traj)
+            self.prepared.put((q, plan, bufs, n, time.perf_counter() - t0, nbytes))
+        except Exception as exc:  # a query that cannot be prepared fails alone
+            with self.lock:
+                self.failed.append((q.qid, repr(exc)))
+                self.pending -= 1
 
     def submit(self, q: Query):
         if not q.arrival:

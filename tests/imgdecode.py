@@ -5,8 +5,8 @@ import numpy as np
 
 HEADER_FIELDS = ["magic", "n", "W", "W32", "n_groups", "n_multi", "n_sel", "P",
                  "off_words", "off_groups", "off_multi", "off_selslot", "off_thr", "off_inputs",
-                 "off_selblk", "off_tables", "off_ret", "off_pos", "image_bytes",
-                 "stage_bytes", "tables_in_smem", "reserved"]
+                 "off_selblk", "off_gorder", "off_tables", "off_ret", "off_pos", "image_bytes",
+                 "stage_bytes", "tables_in_smem"]
 
 
 def decode(img: np.ndarray) -> dict:

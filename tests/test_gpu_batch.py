@@ -108,3 +108,26 @@ def test_batch_graph_capture_replays_the_chunk_loop():
     for (plan, ids), a, b in zip(p1, e1, e2):
         ga, gb = _collect(plan, a["bufs"]), _collect(plan, b["bufs"])
         assert np.array_equal(ga["final"], gb["final"]) and np.array_equal(ga["counts"], gb["counts"])
+
+
+def test_batch_wide_networks_use_lane_groups():
+    """Wide networks get several lanes per trajectory inside the batch (group-parallel
+    evaluation) and still reproduce their single-network launches exactly."""
+    rng = np.random.default_rng(12)
+    entries, plans, refs = [], [], []
+    for i, n in enumerate([1500, 2500, 60, 900]):
+        text = synth.paper100(seed=2000 + i, n=n, p=float(10 ** rng.uniform(-4, -2))).to_text()
+        plan, ids = plan_for(text, [0, 1, 2])
+        T = int(rng.integers(100, 400))
+        seed = int(rng.integers(0, 2**62))
+        entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=seed, meta_ids=[0, 1, 2]))
+        plans.append((plan, ids))
+        refs.append(run(plan, seed=seed, n_traj=T, n_steps=240, meta=[0, 1, 2], kernel=_lib.PBN_KERNEL_INTERP, lanes=1))
+    B = api.Batch(entries)
+    B.run(100)
+    B.run(140)
+    assert int(B.status.item()) == 0
+    for (plan, ids), e, ref in zip(plans, entries, refs):
+        got = _collect(plan, e["bufs"])
+        assert np.array_equal(got["final"][:, ids], ref["final"][:, ids])
+        assert np.array_equal(got["counts"], ref["counts"])

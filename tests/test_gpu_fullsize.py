@@ -46,3 +46,32 @@ def test_paper100_full_size_sampled_trajectories(oracle_mod):
     for t, o in zip(sample, outs):
         assert np.array_equal(final[t, ids], o["final"][0, ids]), t
         assert np.array_equal(counts[t], o["counts"][0]), t
+
+
+def test_scalefree2000_full_size_sampled_trajectories(oracle_mod):
+    """Large network at its benchmark size: n = 2000, 2^14 trajectories x 10^5 steps,
+    default launch shape; sampled trajectories recomputed by the oracle."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    text = synth.scalefree2000(seed=3).to_text()
+    meta = [0, 1, 2, 3]
+    red, ids = api.Net.load(text).reduce(meta)
+    plan = api.Plan(red)
+    T, S = 1 << 14, 10**5
+    bufs = api.alloc_buffers(plan, T)
+    api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=meta)
+    torch.cuda.synchronize()
+    assert int(bufs.status.item()) == 0
+    counts = bufs.counts.cpu().numpy().view(np.uint64).T
+    final = plan.unpack(bufs.state.cpu().numpy().view(np.uint64))
+    assert np.all(counts[:, 1:].sum(axis=1) == S)
+    assert np.array_equal(bufs.pooled.cpu().numpy().view(np.uint64), counts.sum(axis=0))
+    sample = [0, 16383, 4242, 9999]
+    def one(t):
+        return oracle_mod.simulate(text, SEED, t, 1, S, meta_ids=meta)
+    with ThreadPoolExecutor(max_workers=min(len(sample), os.cpu_count() or 1)) as ex:
+        outs = list(ex.map(one, sample))
+    for t, o in zip(sample, outs):
+        assert np.array_equal(final[t, ids], o["final"][0, ids]), t
+        assert np.array_equal(counts[t], o["counts"][0]), t
