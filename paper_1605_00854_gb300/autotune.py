@@ -1,0 +1,157 @@
+"""Autotuner: group size, kernel, lanes per trajectory and steps per launch.
+
+For one network it builds plans with several caps on the inputs of a merged group
+(the group size of Sec. 3.3; larger groups mean fewer table lookups but bigger
+tables), and for each plan times short launches of the candidate kernels on the
+caller's trajectory count: the compiled plan (when the plan can be compiled) and the
+interpreter with 1, 2, 4 or 8 lanes per trajectory, with the tables in shared or in
+global memory.  The fastest configuration is returned and cached by the shape of
+the problem.  For batches it times CUDA-graph replays of the persistent launch with
+several steps per launch.
+
+Every candidate simulates the same keyed trajectories, so the choice changes speed
+only, never results.
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+from dataclasses import asdict, dataclass
+
+from . import _lib, api
+
+_CACHE: dict = {}
+_LOCK = threading.Lock()
+
+
+@dataclass
+class Choice:
+    max_inputs: int
+    kernel: int            # _lib.PBN_KERNEL_COMPILED or _lib.PBN_KERNEL_INTERP
+    lanes_per_traj: int
+    smem_budget: int       # 0 = default (tables staged when they fit)
+    node_updates_per_s: float
+
+
+def _shape_key(net: api.Net, meta, n_traj: int) -> str:
+    info = net.info()
+    tb = max(0, n_traj.bit_length() - 1)
+    return f"n{info.n}-f{info.n_functions}-m{len(meta)}-p{info.P}-t{tb}"
+
+
+def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
+    import torch
+    api.simulate(plan, bufs, seed=seed, n_steps=8, meta_ids=meta, kernel=kernel, lanes_per_traj=lanes)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    api.simulate(plan, bufs, seed=seed, n_steps=steps, meta_ids=meta, kernel=kernel, lanes_per_traj=lanes)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 1,
+                 max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8),
+                 try_compiled: bool = True, cache_file: str | None = None, log=None) -> Choice:
+    """Pick the fastest (group size, kernel, lanes, table placement) for simulating
+    n_traj trajectories of this network."""
+    net = api.Net.load(text)
+    key = _shape_key(net, meta, n_traj)
+    with _LOCK:
+        if key in _CACHE:
+            return _CACHE[key]
+    if cache_file and os.path.exists(cache_file):
+        try:
+            with open(cache_file) as f:
+                saved = json.load(f)
+            if key in saved:
+                ch = Choice(**saved[key])
+                with _LOCK:
+                    _CACHE[key] = ch
+                return ch
+        except (OSError, ValueError, TypeError):
+            pass
+    red, _ = net.reduce(list(meta))
+    n = net.info().n
+    best = None
+    for mi in max_inputs_options:
+        for budget in (0, 1024):
+            try:
+                plan = api.Plan(red, max_inputs=mi, smem_budget=budget) if budget else api.Plan(red, max_inputs=mi)
+            except _lib.PbnError:
+                continue
+            if budget and plan.info.tables_in_smem:
+                continue
+            bufs = api.alloc_buffers(plan, n_traj)
+            cands = []
+            if try_compiled and budget == 0:
+                try:
+                    plan.compile()
+                    cands.append((_lib.PBN_KERNEL_COMPILED, 1))
+                except _lib.PbnError:
+                    pass
+            cands += [(_lib.PBN_KERNEL_INTERP, lg) for lg in lanes_options]
+            for kern, lg in cands:
+                try:
+                    dt = _time(plan, bufs, seed, steps, list(meta), kern, lg)
+                except _lib.PbnError:
+                    continue
+                rate = n * n_traj * steps / dt
+                if log is not None:
+                    log.append(dict(max_inputs=mi, smem_budget=budget, kernel=kern, lanes=lg, rate=rate,
+                                    groups=int(plan.info.n_groups), tables_in_smem=int(plan.info.tables_in_smem)))
+                if best is None or rate > best.node_updates_per_s:
+                    best = Choice(max_inputs=mi, kernel=kern, lanes_per_traj=lg, smem_budget=budget,
+                                  node_updates_per_s=rate)
+            del bufs
+    if best is None:
+        raise RuntimeError("no configuration could run this network")
+    with _LOCK:
+        _CACHE[key] = best
+    if cache_file:
+        try:
+            saved = {}
+            if os.path.exists(cache_file):
+                with open(cache_file) as f:
+                    saved = json.load(f)
+            saved[key] = asdict(best)
+            with open(cache_file, "w") as f:
+                json.dump(saved, f, indent=1)
+        except (OSError, ValueError):
+            pass
+    return best
+
+
+def plan_for_choice(text: str, meta, ch: Choice) -> api.Plan:
+    red, _ = api.Net.load(text).reduce(list(meta))
+    plan = api.Plan(red, max_inputs=ch.max_inputs, smem_budget=ch.smem_budget) if ch.smem_budget \
+        else api.Plan(red, max_inputs=ch.max_inputs)
+    if ch.kernel == _lib.PBN_KERNEL_COMPILED:
+        plan.compile()
+    return plan
+
+
+def tune_chunk(batch: api.Batch, total_steps: int, options=(250, 500, 1000, 2000), trial_steps: int = 2000):
+    """Steps per persistent launch for a batch: time a CUDA-graph replay of
+    trial_steps steps cut into chunks of each size (the batch's state advances; the
+    caller re-initialises it afterwards if needed).  Returns (best chunk, timings)."""
+    import torch
+    timings = {}
+    off = batch.steps_done
+    for c in options:
+        if c > total_steps:
+            continue
+        n = max(1, trial_steps // c)
+        g = batch.capture([c] * n, step_offset=off)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        timings[c] = e0.elapsed_time(e1) / 1e3 / (n * c)
+        off += n * c
+    batch.steps_done = off
+    best = min(timings, key=timings.get) if timings else options[0]
+    return best, timings

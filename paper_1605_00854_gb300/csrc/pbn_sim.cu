@@ -26,6 +26,7 @@
  */
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 
@@ -292,16 +293,20 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     /* launch shape: lanes per trajectory and trajectory slots per CTA */
     const size_t smem_lim = (size_t)device_smem_limit();
     uint32_t LG = a->lanes_per_traj;
-    if (LG == 0) {
-        LG = 1;
-        /* lanes of a group take different state words, so they diverge in the
-         * evaluation: split a trajectory only when its state is wide and there are
-         * too few trajectories to fill the SMs */
-        while (LG < 8 && H.W32 >= 16 * LG && a->n_traj * LG < (uint64_t)sms * 512) LG *= 2;
-    }
-    if (LG != 1 && LG != 2 && LG != 4 && LG != 8) return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4 or 8");
     const size_t per_traj = plan->per_traj_smem;
     const size_t fixed = P.smem_state_off;
+    if (LG == 0) {
+        /* one lane per trajectory when the SMs fill with trajectories; otherwise
+         * lane groups (they split the perturbation words, SEL blocks and groups of
+         * a trajectory) until a CTA holds 8 to 16 warps */
+        LG = 1;
+        const uint64_t per_sm = (a->n_traj + sms - 1) / sms;
+        const uint64_t fit = fixed + per_traj * 32 <= smem_lim ? (smem_lim - fixed) / per_traj : 32;
+        const uint64_t slots = std::min<uint64_t>(per_sm, std::min<uint64_t>(fit, 512));
+        while (LG < 8 && slots * LG < 256 && H.W32 >= 4 * LG) LG *= 2;
+        if (LG > 1 && slots * LG < 512 && LG < 8 && H.W32 >= 4 * LG) LG *= 2;
+    }
+    if (LG != 1 && LG != 2 && LG != 4 && LG != 8) return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4 or 8");
     if (fixed + per_traj * (32 / LG) > smem_lim)
         return fail(PBN_ETOOBIG, "pbn_simulate: plan needs %zu bytes of shared memory for one warp", fixed + per_traj * (32 / LG));
     uint32_t nt = a->trajs_per_block;
