@@ -31,11 +31,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1605_00854_gb300 import _lib, api, shard, synth  # noqa: E402
+from paper_1605_00854_gb300 import _lib, api, autotune, shard, synth  # noqa: E402
 
 SEED = 20160503
 META = [0, 1, 2]
-WORKLOAD = "paper-scale PBN n=100 (70% 1 function, 30% 2-3; in-degree 1-5; 25% sinks; p=1e-4), reduced+grouped (<=8 inputs/group)"
+WORKLOAD = "paper-scale PBN n=100 (70% 1 function, 30% 2-3; in-degree 1-5; 25% sinks; p=1e-4), reduced+grouped"
 
 
 # ------------------------------------------------------------------ helpers ----
@@ -158,7 +158,7 @@ def workload_network(args):
     if args.workload == "scalefree2000":
         return (synth.scalefree2000(seed=3), [0, 1, 2, 3],
                 "scale-free PBN n=2000 (power-law out-degree 2.5; in-degree 1-6; 1-3 functions; p=1e-5), "
-                "reduced+grouped (<=8 inputs/group)")
+                "reduced+grouped")
     return synth.paper100(seed=2), META, WORKLOAD
 
 
@@ -177,9 +177,23 @@ def run_ours(args):
     net_obj, meta, workload = workload_network(args)
     text = net_obj.to_text()
     n = net_obj.n
+    T = args.n_traj if args.n_traj else (1 << 16 if args.workload == "paper100" else 1 << 14)
+    S = args.n_steps if args.n_steps else (10**6 if args.workload == "paper100" else 10**5)
+    args.n_traj, args.n_steps = T, S
+    lanes = 0
+    tune_s = 0.0
+    if args.autotune:
+        # group size, kernel and lanes per trajectory picked by timing short passes
+        t0 = time.perf_counter()
+        choice = autotune.tune_network(text, meta, T, steps=2000 if args.workload == "paper100" else 200)
+        tune_s = time.perf_counter() - t0
+        max_inputs, lanes = choice.max_inputs, choice.lanes_per_traj
+        args.kernel = "compiled" if choice.kernel == _lib.PBN_KERNEL_COMPILED else "interpreter"
+    else:
+        max_inputs = 8
     t_prep = time.perf_counter()
     red, retained = api.Net.load(text).reduce(meta)
-    plan = api.Plan(red)
+    plan = api.Plan(red, max_inputs=max_inputs)
     compile_ms = 0.0
     if args.kernel == "compiled":
         try:
@@ -188,9 +202,6 @@ def run_ours(args):
             args.kernel = "interpreter"  # plan too wide to compile: the interpreter runs it
     prep_s = time.perf_counter() - t_prep
     kern = _lib.PBN_KERNEL_COMPILED if args.kernel == "compiled" else _lib.PBN_KERNEL_INTERP
-    T = args.n_traj if args.n_traj else (1 << 16 if args.workload == "paper100" else 1 << 14)
-    S = args.n_steps if args.n_steps else (10**6 if args.workload == "paper100" else 10**5)
-    args.n_traj, args.n_steps = T, S
     P = api.Net.load(text).info().P
     info = plan.info
     T, S = args.n_traj, args.n_steps
@@ -202,7 +213,7 @@ def run_ours(args):
 
     def one_step():
         api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=meta, traj_begin=traj_begin,
-                     stream=stream, d_image=d_img, kernel=kern)
+                     stream=stream, d_image=d_img, kernel=kern, lanes_per_traj=lanes)
 
     for _ in range(args.warmup):
         bufs.counts.zero_(); bufs.pooled.zero_()
@@ -308,7 +319,8 @@ def run_ours(args):
                        "seed": SEED, "meta": meta, "l2": "flushed between timed steps (256 MiB write)",
                        "parallelism": f"replicas{ws} (disjoint trajectory ids)",
                        "host_prep_s": round(prep_s, 4), "compile_ms": round(compile_ms, 1),
-                       "kernel": args.kernel},
+                       "kernel": args.kernel, "max_inputs_per_group": max_inputs,
+                       "lanes_per_traj": lanes or "auto", "autotune_s": round(tune_s, 2)},
             "compare": compare,
             "traj_steps_per_s": T * S * ws * args.steps / total,
             "retained_node_updates_per_s": int(info.n_retained) * T * S * ws * args.steps / total,
@@ -436,6 +448,8 @@ def main():
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter"])
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="use group size 8 and the default launch shape instead of the autotuner")
     ap.add_argument("--workload", default="paper100", choices=["paper100", "scalefree2000", "batch", "serve"])
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--chunk-steps", type=int, default=1000)
