@@ -117,14 +117,15 @@ def ops_per_traj_step(info, n: int, P: int) -> float:
     2 mul.hi + 2 mul.lo + 2 xor3; round 1's products are shared per step), 12 ops per
     bit-sliced level pair, and in non-perturbed steps the SEL blocks, 2 ops per
     threshold compare-accumulate and 1 per multi node, 3 ops per group input
-    (load, rotate, insert) and 5 per group (index, load, extract, shift, or), plus
-    8 ops of counting."""
+    (load, rotate, insert) and 5 per group (index, load, extract, shift, or; a split
+    node adds 5 for its function record and reads its selected function's inputs),
+    plus 8 ops of counting."""
     pe = P / 2**32
     W = (n + 63) // 64
     blocks = sum(expected_blocks(64 if w < W - 1 or n % 64 == 0 else n % 64) for w in range(W)) if P else 0.0
     pert = blocks * (56 + 12) + 4
     nonpert = (info.n_sel_blocks * 56 + 2 * info.total_thresholds + info.n_multi
-               + 3 * info.total_inputs + 5 * info.n_groups + 2 * info.state_words)
+               + 3 * info.total_inputs + 5 * (info.n_groups + info.n_split) + 2 * info.state_words)
     return pert + (1.0 - pe) ** n * nonpert + 8
 
 
@@ -188,16 +189,17 @@ def run_ours(args):
         choice = autotune.tune_network(text, meta, T, steps=2000 if args.workload == "paper100" else 200)
         tune_s = time.perf_counter() - t0
         max_inputs, lanes = choice.max_inputs, choice.lanes_per_traj
+        budget, cflags = choice.smem_budget, choice.compile_flags
         args.kernel = "compiled" if choice.kernel == _lib.PBN_KERNEL_COMPILED else "interpreter"
     else:
-        max_inputs = 8
+        max_inputs, budget, cflags = 8, 0, 0
     t_prep = time.perf_counter()
     red, retained = api.Net.load(text).reduce(meta)
-    plan = api.Plan(red, max_inputs=max_inputs)
+    plan = api.Plan(red, max_inputs=max_inputs, smem_budget=budget) if budget else api.Plan(red, max_inputs=max_inputs)
     compile_ms = 0.0
     if args.kernel == "compiled":
         try:
-            compile_ms = plan.compile()
+            compile_ms = plan.compile(cflags)
         except _lib.PbnError:
             args.kernel = "interpreter"  # plan too wide to compile: the interpreter runs it
     prep_s = time.perf_counter() - t_prep
@@ -281,6 +283,15 @@ def run_ours(args):
         variants = [("interpreter_grouped", plan, _lib.PBN_KERNEL_INTERP),
                     ("compiled_plain_unreduced", plain_plan, _lib.PBN_KERNEL_COMPILED),
                     ("interpreter_plain_unreduced", plain_plan, _lib.PBN_KERNEL_INTERP)]
+        # the same grouped plan compiled with each code-shape flag
+        for fname, fl in (("rolled", 0), ("unrolled", _lib.PBN_COMPILE_PERT_UNROLLED),
+                          ("interleaved", _lib.PBN_COMPILE_INTERLEAVED)):
+            pf = api.Plan(red, max_inputs=max_inputs)
+            try:
+                pf.compile(fl)
+            except _lib.PbnError:
+                continue
+            variants.append((f"compiled_grouped_{fname}", pf, _lib.PBN_KERNEL_COMPILED))
         for name, pl, kk in variants:
             b2 = api.alloc_buffers(pl, T, dev)
             img2 = pl.device_image(dev)
@@ -320,6 +331,8 @@ def run_ours(args):
                        "parallelism": f"replicas{ws} (disjoint trajectory ids)",
                        "host_prep_s": round(prep_s, 4), "compile_ms": round(compile_ms, 1),
                        "kernel": args.kernel, "max_inputs_per_group": max_inputs,
+                       "compile_flags": cflags if args.kernel == "compiled" else None,
+                       "split_nodes": int(info.n_split),
                        "lanes_per_traj": lanes or "auto", "autotune_s": round(tune_s, 2)},
             "compare": compare,
             "traj_steps_per_s": T * S * ws * args.steps / total,
@@ -437,6 +450,53 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def apoptosis_queries():
+    """The seven meta-states of the apoptosis-shaped workload: for a core node X with
+    three parents A, B, C (the shape of the paper's analysis of one node and its three
+    parents), P(A), P(B), P(C), P(X and A), P(X and B), P(X and C) and P(X), all ON."""
+    net = synth.apoptosis96()
+    core = 60
+    for X in range(core):
+        par = sorted({a for f in net.funcs[X] for a in f.parents if a != X and a < core})
+        if len(par) >= 3:
+            A, B, C = par[:3]
+            break
+    metas = [[A], [B], [C], [X, A], [X, B], [X, C], [X]]
+    return net, X, (A, B, C), metas
+
+
+def run_apoptosis(args):
+    """Seven steady-state probabilities of the apoptosis-shaped network at precision
+    r = 1e-5 and confidence 0.95 (Sec. 4.3's setting), estimated together by the
+    two-state Markov chain stopping rule through the serving loop."""
+    from paper_1605_00854_gb300 import serve
+    net, X, par, metas = apoptosis_queries()
+    text = net.to_text()
+    srv = serve.Server(n_traj=args.apo_traj, chunk_steps=args.apo_chunk, burn_in0=256,
+                       mem_cap_bytes=100e9, workers=8, max_steps=1 << 24)
+    t0 = time.perf_counter()
+    for i, m in enumerate(metas):
+        srv.submit(serve.Query(qid=i, text=text, meta_ids=m, seed=SEED + 17 * i, r=1e-5, s=0.95, eps=1e-3))
+    srv.drain(timeout=args.apo_timeout)
+    wall = time.perf_counter() - t0
+    srv.close()
+    res = sorted(srv.done, key=lambda r: r.qid)
+    samples = sum(r.L for r in res)
+    line = {"metric": "apoptosis-shaped network: 7 steady-state probabilities at r=1e-5, s=0.95 (wall time)",
+            "value": wall, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "u32",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "apoptosis-shaped PBN: n=96, 37.5% leaves, density 1.78, p=1e-4",
+                       "node_X": X, "parents_ABC": list(par), "trajectories_per_query": args.apo_traj,
+                       "chunk_steps": args.apo_chunk, "r": 1e-5, "s": 0.95, "eps": 1e-3},
+            "queries": [{"meta": metas[r.qid], "pi": r.pi, "n_star": r.n_star, "samples": r.L, "m_star": r.m_star,
+                         "steps": r.steps, "rounds": r.rounds, "latency_s": r.latency} for r in res],
+            "total_samples": samples, "node_updates_per_s": srv.node_updates / wall,
+            "completed": len(res), "failed": len(srv.failed),
+            "paper_context": "Sec. 4.3: 7 probabilities, 50-452 million samples each, about 10 minutes "
+                             "in total for the structure-based method on the paper's CPU (other hardware)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -450,7 +510,11 @@ def main():
     ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use group size 8 and the default launch shape instead of the autotuner")
-    ap.add_argument("--workload", default="paper100", choices=["paper100", "scalefree2000", "batch", "serve"])
+    ap.add_argument("--workload", default="paper100",
+                    choices=["paper100", "scalefree2000", "batch", "serve", "apoptosis"])
+    ap.add_argument("--apo-traj", type=int, default=1 << 14)
+    ap.add_argument("--apo-chunk", type=int, default=4096)
+    ap.add_argument("--apo-timeout", type=float, default=600.0)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--chunk-steps", type=int, default=1000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
@@ -464,6 +528,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "apoptosis":
+        return run_apoptosis(args)
 
     net_obj = synth.paper100(seed=2)
     text = net_obj.to_text()

@@ -78,6 +78,29 @@ typedef struct pbn_plan pbn_plan;
  * Errors: PBN_EINVAL (NULL argument), PBN_EPARSE (malformed text), PBN_ENOMEM. */
 int pbn_load(const char* text, size_t len, pbn_net** out);
 
+/* The same network from arrays (Sec. 2.1: node set, predictor functions with
+ * their selection probabilities, perturbation rate p).  Function f (0 <= f <
+ * n_functions) belongs to node fun_node[f]; the functions of one node are its
+ * f_1, f_2, ... in the order they appear.  Its fun_k[f] parents follow those of
+ * function f - 1 in `parents`, and its truth table takes the next ceil(2^k / 64)
+ * 64-bit words of `tt`: bit x (least significant first) is the output on the input
+ * pattern x = sum_b s[a_b] 2^b, and bits at x >= 2^k must be 0.  The arrays are
+ * host memory, read during the call only.  Same requirements as pbn_load.
+ * On success *out owns a new network (free with pbn_net_free).
+ * Errors: PBN_EINVAL (NULL argument or a requirement not met), PBN_ENOMEM. */
+typedef struct {
+    uint32_t n;                /* nodes */
+    uint32_t n_functions;      /* predictor functions of all nodes */
+    double p;                  /* perturbation rate */
+    const uint32_t* fun_node;  /* [n_functions] node of each function */
+    const double* fun_c;       /* [n_functions] selection probability c */
+    const uint32_t* fun_k;     /* [n_functions] number of parents, <= 24 */
+    const uint32_t* parents;   /* [sum fun_k] ordered distinct parents, function by function */
+    const uint64_t* tt;        /* [sum ceil(2^k / 64)] truth tables, function by function */
+} pbn_net_desc;
+
+int pbn_load_arrays(const pbn_net_desc* desc, pbn_net** out);
+
 typedef struct {
     uint32_t n;            /* nodes of the original network */
     uint32_t n_retained;   /* nodes kept by pbn_reduce (n for an unreduced network) */
@@ -103,6 +126,19 @@ int pbn_net_info_get(const pbn_net* net, pbn_net_info* out);
  * PBN_ENOMEM. */
 int pbn_reduce(const pbn_net* net, const uint32_t* interest, uint32_t n_interest,
                pbn_net** reduced, uint32_t* retained_ids, uint32_t* n_retained);
+
+/* pbn_reduce with a choice of rule.  PBN_REDUCE_LEAVES is Definition 1 (the rule
+ * of pbn_reduce).  PBN_REDUCE_REACH retains exactly the nodes from which a node of
+ * interest can be reached along parent -> child edges (the nodes of interest
+ * included): a node that reaches none cannot influence them, so their
+ * trajectories are unchanged (the same argument as Sec. 3.1's for leaves).  It
+ * also removes cycles of such nodes, which Definition 1 keeps; its retained set is
+ * a subset of Definition 1's.  Errors: as pbn_reduce, and PBN_EINVAL for an
+ * unknown rule. */
+#define PBN_REDUCE_LEAVES 0u
+#define PBN_REDUCE_REACH 1u
+int pbn_reduce_rule(const pbn_net* net, const uint32_t* interest, uint32_t n_interest, uint32_t rule,
+                    pbn_net** reduced, uint32_t* retained_ids, uint32_t* n_retained);
 
 /* ---- plans ------------------------------------------------------------------- */
 #define PBN_PLAN_GROUPED 0u /* node grouping of Sec. 3.3 (Eq. 2, Algorithms 3-4) */
@@ -152,9 +188,15 @@ typedef struct {
     uint64_t image_bytes;    /* bytes of the device image (pbn_plan_image) */
     uint64_t stage_bytes;    /* leading bytes of the image staged into shared memory */
     uint32_t tables_in_smem; /* 1 if the tables are staged into shared memory */
-    uint32_t total_inputs;   /* sum over groups of their distinct inputs */
+    uint32_t total_inputs;   /* input bits gathered per non-perturbed step: each merged group's
+                                distinct inputs, plus for a split node the mean in-degree of
+                                its functions (one function is evaluated) */
     uint32_t n_multi;        /* retained nodes with >= 2 functions */
     uint32_t total_thresholds; /* selection thresholds below 2^32 over those nodes */
+    uint32_t n_split;        /* groups that are one multi-function node whose inputs exceed
+                                max_inputs: each of its functions keeps its own table over
+                                its own inputs, and the node's choice selects the output */
+    uint32_t reserved;
     double ops_per_step;     /* algorithmic 32-bit integer operations of one trajectory-step:
                                 Philox blocks at 56 ops (9 rounds of 2 mul.hi, 2 mul.lo,
                                 2 xor3), 12 per bit-sliced level pair, the expected number of
@@ -242,8 +284,15 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
 /* pbn_plan_compile flags.  Default (0): the perturbation words are drawn in pairs
  * by one rolled loop (two independent Philox chains, small code).
  * PBN_COMPILE_PERT_UNROLLED: one word at a time, every level pair unrolled with
- * the bits of P as constants.  Compiling with other flags replaces the kernel. */
+ * the bits of P as constants.
+ * PBN_COMPILE_INTERLEAVED: the SEL blocks are drawn before the perturbation check
+ * and the first three level pairs of every word are straight-line code, so that
+ * these Philox chains can be interleaved (more independent work per thread; the
+ * SEL draws of perturbed steps are discarded).
+ * Every variant consumes the same keyed draws: results are identical.  Compiling
+ * with other flags replaces the kernel. */
 #define PBN_COMPILE_PERT_UNROLLED 0x1u
+#define PBN_COMPILE_INTERLEAVED 0x2u
 
 /* The CUDA source generated for the plan's own kernel: *len receives its length;
  * dst (capacity cap, may be NULL) receives it NUL-terminated.

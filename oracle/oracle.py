@@ -67,6 +67,8 @@ def lib():
             L.orc_transition_matrix.restype = i32
             L.orc_leaves.argtypes = [cp, vp, i32, vp]
             L.orc_leaves.restype = i32
+            L.orc_reach.argtypes = [cp, vp, i32, vp]
+            L.orc_reach.restype = i32
             _lib = L
     return _lib
 
@@ -164,6 +166,18 @@ def leaves(text: str, interest) -> np.ndarray:
     rc = lib().orc_leaves(text.encode(), _ptr(it), len(it), _ptr(out))
     if rc:
         raise ValueError(f"orc_leaves failed (rc={rc})")
+    return out.astype(bool)
+
+
+def reach_removed(text: str, interest) -> np.ndarray:
+    """Nodes from which no node of interest can be reached (the reachability
+    variant of the reduction): True = removed."""
+    n = shape(text)[0]
+    it = np.ascontiguousarray(interest, dtype=np.int32)
+    out = np.zeros(n, dtype=np.uint8)
+    rc = lib().orc_reach(text.encode(), _ptr(it), len(it), _ptr(out))
+    if rc:
+        raise ValueError(f"orc_reach failed (rc={rc})")
     return out.astype(bool)
 
 

@@ -618,3 +618,41 @@ int orc_leaves(const char *text, const int32_t *interest, int n_interest, uint8_
     net_free(g);
     return ORC_OK;
 }
+
+
+/* Reachability variant of the reduction: node v is kept iff it is a node of
+ * interest or one of its children (self-edges ignored) is kept, iterated to the
+ * fixed point, i.e. iff some node of interest can be reached from v along
+ * parent -> child edges.  removed[v] = 1 for the other nodes. */
+int orc_reach(const char *text, const int32_t *interest, int n_interest, uint8_t *removed) {
+    onet *g = NULL;
+    int rc = parse_net(text, &g);
+    if (rc) return rc;
+    int n = g->n;
+    uint8_t *keep = (uint8_t *)calloc((size_t)n, 1);
+    uint8_t *child = (uint8_t *)calloc((size_t)n * (size_t)n, 1); /* child[v*n+u] */
+    if (!keep || !child) { free(keep); free(child); net_free(g); return ORC_ENOMEM; }
+    for (int m = 0; m < n_interest; ++m) {
+        if (interest[m] < 0 || interest[m] >= n) { free(keep); free(child); net_free(g); return ORC_EINVAL; }
+        keep[interest[m]] = 1;
+    }
+    for (int u = 0; u < n; ++u)
+        for (int j = 0; j < g->node[u].nf; ++j)
+            for (int b = 0; b < g->node[u].f[j].k; ++b) {
+                int v = g->node[u].f[j].par[b];
+                if (v != u) child[(size_t)v * n + u] = 1;
+            }
+    int changed = 1;
+    while (changed) {
+        changed = 0;
+        for (int v = 0; v < n; ++v) {
+            if (keep[v]) continue;
+            for (int u = 0; u < n; ++u)
+                if (child[(size_t)v * n + u] && keep[u]) { keep[v] = 1; changed = 1; break; }
+        }
+    }
+    for (int v = 0; v < n; ++v) removed[v] = (uint8_t)!keep[v];
+    free(keep); free(child);
+    net_free(g);
+    return ORC_OK;
+}

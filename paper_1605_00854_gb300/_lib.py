@@ -15,11 +15,21 @@ u32, u64, i32, f64 = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_
 vp, cp = ctypes.c_void_p, ctypes.c_char_p
 
 PBN_OK = 0
+PBN_EINVAL = -1
+PBN_EPARSE = -2
+PBN_ENOMEM = -3
+PBN_ECUDA = -4
+PBN_ETOOBIG = -5
+PBN_ETIMEOUT = -6
+PBN_EDEVICE = -7
+PBN_REDUCE_LEAVES = 0
+PBN_REDUCE_REACH = 1
 PBN_PLAN_GROUPED = 0
 PBN_PLAN_PLAIN = 1
 PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
 PBN_COMPILE_PERT_UNROLLED = 0x1
+PBN_COMPILE_INTERLEAVED = 0x2
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1
@@ -33,6 +43,13 @@ class NetInfo(ctypes.Structure):
                 ("p", f64), ("P", u64), ("density", f64)]
 
 
+class NetDesc(ctypes.Structure):
+    _fields_ = [("n", u32), ("n_functions", u32), ("p", f64),
+                ("fun_node", ctypes.POINTER(u32)), ("fun_c", ctypes.POINTER(f64)),
+                ("fun_k", ctypes.POINTER(u32)), ("parents", ctypes.POINTER(u32)),
+                ("tt", ctypes.POINTER(u64))]
+
+
 class GroupParams(ctypes.Structure):
     _fields_ = [("mode", u32), ("max_inputs", u32), ("max_width", u32), ("reserved", u32),
                 ("theta", f64), ("smem_budget", u64)]
@@ -44,7 +61,7 @@ class PlanInfo(ctypes.Structure):
                 ("m_found", u32), ("sum_weights", u64), ("table_bytes", u64),
                 ("image_bytes", u64), ("stage_bytes", u64), ("tables_in_smem", u32),
                 ("total_inputs", u32), ("n_multi", u32), ("total_thresholds", u32),
-                ("ops_per_step", f64)]
+                ("n_split", u32), ("reserved", u32), ("ops_per_step", f64)]
 
 
 class BatchNet(ctypes.Structure):
@@ -76,8 +93,10 @@ class EstimateOut(ctypes.Structure):
 #: every symbol include/pbn.h declares, with (restype, argtypes)
 SIGNATURES = {
     "pbn_load": (i32, [cp, ctypes.c_size_t, ctypes.POINTER(vp)]),
+    "pbn_load_arrays": (i32, [ctypes.POINTER(NetDesc), ctypes.POINTER(vp)]),
     "pbn_net_info_get": (i32, [vp, ctypes.POINTER(NetInfo)]),
     "pbn_reduce": (i32, [vp, vp, u32, ctypes.POINTER(vp), vp, ctypes.POINTER(u32)]),
+    "pbn_reduce_rule": (i32, [vp, vp, u32, u32, ctypes.POINTER(vp), vp, ctypes.POINTER(u32)]),
     "pbn_group_params_default": (None, [ctypes.POINTER(GroupParams)]),
     "pbn_group": (i32, [vp, ctypes.POINTER(GroupParams), ctypes.POINTER(vp)]),
     "pbn_plan_info_get": (i32, [vp, ctypes.POINTER(PlanInfo)]),

@@ -39,6 +39,46 @@ class Net:
         check(L.pbn_load(b, len(b), ctypes.byref(h)), "pbn_load")
         return cls(h, text)
 
+    @classmethod
+    def from_arrays(cls, n: int, p: float, fun_node, fun_c, fun_k, parents, tt) -> "Net":
+        """pbn_load_arrays: functions as flat arrays (node, c, k per function; parent
+        lists and 64-bit truth-table words concatenated function by function)."""
+        L = _lib.load()
+        arrs = dict(fun_node=np.ascontiguousarray(fun_node, dtype=np.uint32),
+                    fun_c=np.ascontiguousarray(fun_c, dtype=np.float64),
+                    fun_k=np.ascontiguousarray(fun_k, dtype=np.uint32),
+                    parents=np.ascontiguousarray(parents, dtype=np.uint32),
+                    tt=np.ascontiguousarray(tt, dtype=np.uint64))
+        nf = len(arrs["fun_node"])
+        if not (len(arrs["fun_c"]) == len(arrs["fun_k"]) == nf):
+            raise ValueError("fun_node, fun_c and fun_k differ in length")
+        if len(arrs["parents"]) != int(arrs["fun_k"].sum()):
+            raise ValueError("parents must hold sum(fun_k) entries")
+        if len(arrs["tt"]) != sum((1 << int(k)) + 63 >> 6 for k in arrs["fun_k"]):
+            raise ValueError("tt must hold sum(ceil(2^k / 64)) words")
+        d = _lib.NetDesc(n=n, n_functions=nf, p=p)
+        ctype = {np.uint32: ctypes.c_uint32, np.float64: ctypes.c_double, np.uint64: ctypes.c_uint64}
+        for name, a in arrs.items():  # arrs keeps the buffers alive during the call
+            setattr(d, name, a.ctypes.data_as(ctypes.POINTER(ctype[a.dtype.type])))
+        h = ctypes.c_void_p()
+        check(L.pbn_load_arrays(ctypes.byref(d), ctypes.byref(h)), "pbn_load_arrays")
+        return cls(h)
+
+    @classmethod
+    def from_functions(cls, n: int, p: float, funcs) -> "Net":
+        """funcs[i] = [(c, parents, truth table as int), ...] for node i, in order j."""
+        fun_node, fun_c, fun_k, parents, tt = [], [], [], [], []
+        for i, fl in enumerate(funcs):
+            for c, par, table in fl:
+                k = len(par)
+                fun_node.append(i)
+                fun_c.append(c)
+                fun_k.append(k)
+                parents.extend(par)
+                for w in range(((1 << k) + 63) >> 6):
+                    tt.append((int(table) >> (64 * w)) & 0xFFFFFFFFFFFFFFFF)
+        return cls.from_arrays(n, p, fun_node, fun_c, fun_k, parents, tt)
+
     def __del__(self):
         if getattr(self, "_h", None):
             _lib.load().pbn_net_free(self._h)
@@ -49,8 +89,9 @@ class Net:
         check(_lib.load().pbn_net_info_get(self._h, ctypes.byref(out)), "pbn_net_info_get")
         return out
 
-    def reduce(self, interest):
-        """Leaf-node reduction (Definition 1) for the given nodes of interest.
+    def reduce(self, interest, rule: int = _lib.PBN_REDUCE_LEAVES):
+        """Leaf-node reduction (Definition 1) for the given nodes of interest, or with
+        rule=PBN_REDUCE_REACH the removal of every node that reaches none of them.
         Returns (reduced Net, retained original ids)."""
         L = _lib.load()
         n = self.info().n
@@ -58,8 +99,12 @@ class Net:
         ids = np.zeros(n, dtype=np.uint32)
         cnt = ctypes.c_uint32()
         h = ctypes.c_void_p()
-        check(L.pbn_reduce(self._h, _ptr(it), len(it), ctypes.byref(h), _ptr(ids),
-                           ctypes.byref(cnt)), "pbn_reduce")
+        if rule == _lib.PBN_REDUCE_LEAVES:
+            check(L.pbn_reduce(self._h, _ptr(it), len(it), ctypes.byref(h), _ptr(ids),
+                               ctypes.byref(cnt)), "pbn_reduce")
+        else:
+            check(L.pbn_reduce_rule(self._h, _ptr(it), len(it), rule, ctypes.byref(h), _ptr(ids),
+                                    ctypes.byref(cnt)), "pbn_reduce_rule")
         return Net(h, self.text), ids[: cnt.value].copy()
 
 

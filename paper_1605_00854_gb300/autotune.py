@@ -3,9 +3,9 @@
 For one network it builds plans with several caps on the inputs of a merged group
 (the group size of Sec. 3.3; larger groups mean fewer table lookups but bigger
 tables), and for each plan times short launches of the candidate kernels on the
-caller's trajectory count: the compiled plan (when the plan can be compiled) and the
-interpreter with 1, 2, 4 or 8 lanes per trajectory, with the tables in shared or in
-global memory.  The fastest configuration is returned and cached by the shape of
+caller's trajectory count: the compiled plan (when the plan can be compiled, with
+each code-shape flag) and the interpreter with 1, 2, 4 or 8 lanes per trajectory,
+with the tables in shared or in global memory.  The fastest configuration is returned and cached by the shape of
 the problem.  For batches it times CUDA-graph replays of the persistent launch with
 several steps per launch.
 
@@ -32,6 +32,7 @@ class Choice:
     lanes_per_traj: int
     smem_budget: int       # 0 = default (tables staged when they fit)
     node_updates_per_s: float
+    compile_flags: int = 0  # pbn_plan_compile flags of the compiled kernel
 
 
 def _shape_key(net: api.Net, meta, n_traj: int) -> str:
@@ -54,9 +55,10 @@ def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
 
 def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 1,
                  max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8),
+                 compile_flags_options=(0, _lib.PBN_COMPILE_INTERLEAVED),
                  try_compiled: bool = True, cache_file: str | None = None, log=None) -> Choice:
-    """Pick the fastest (group size, kernel, lanes, table placement) for simulating
-    n_traj trajectories of this network."""
+    """Pick the fastest (group size, kernel and its compile flags, lanes, table
+    placement) for simulating n_traj trajectories of this network."""
     net = api.Net.load(text)
     key = _shape_key(net, meta, n_traj)
     with _LOCK:
@@ -87,24 +89,22 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
             bufs = api.alloc_buffers(plan, n_traj)
             cands = []
             if try_compiled and budget == 0:
+                cands += [(_lib.PBN_KERNEL_COMPILED, 1, f) for f in compile_flags_options]
+            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0) for lg in lanes_options]
+            for kern, lg, cf in cands:
                 try:
-                    plan.compile()
-                    cands.append((_lib.PBN_KERNEL_COMPILED, 1))
-                except _lib.PbnError:
-                    pass
-            cands += [(_lib.PBN_KERNEL_INTERP, lg) for lg in lanes_options]
-            for kern, lg in cands:
-                try:
+                    if kern == _lib.PBN_KERNEL_COMPILED:
+                        plan.compile(cf)
                     dt = _time(plan, bufs, seed, steps, list(meta), kern, lg)
                 except _lib.PbnError:
                     continue
                 rate = n * n_traj * steps / dt
                 if log is not None:
-                    log.append(dict(max_inputs=mi, smem_budget=budget, kernel=kern, lanes=lg, rate=rate,
+                    log.append(dict(max_inputs=mi, smem_budget=budget, kernel=kern, lanes=lg, flags=cf, rate=rate,
                                     groups=int(plan.info.n_groups), tables_in_smem=int(plan.info.tables_in_smem)))
                 if best is None or rate > best.node_updates_per_s:
                     best = Choice(max_inputs=mi, kernel=kern, lanes_per_traj=lg, smem_budget=budget,
-                                  node_updates_per_s=rate)
+                                  node_updates_per_s=rate, compile_flags=cf)
             del bufs
     if best is None:
         raise RuntimeError("no configuration could run this network")
@@ -129,7 +129,7 @@ def plan_for_choice(text: str, meta, ch: Choice) -> api.Plan:
     plan = api.Plan(red, max_inputs=ch.max_inputs, smem_budget=ch.smem_budget) if ch.smem_budget \
         else api.Plan(red, max_inputs=ch.max_inputs)
     if ch.kernel == _lib.PBN_KERNEL_COMPILED:
-        plan.compile()
+        plan.compile(ch.compile_flags)
     return plan
 
 

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <numeric>
 #include <set>
@@ -106,6 +107,8 @@ void tokenize(const char* b, const char* e, std::vector<std::string>* out) {
     }
 }
 
+int finish_net(pbn_net* g, int code, pbn_net** out);
+
 int load_impl(const char* text, size_t len, pbn_net** out) {
     pbn_net* g = new pbn_net();
     std::vector<std::string> tok;
@@ -186,22 +189,63 @@ int load_impl(const char* text, size_t len, pbn_net** out) {
         delete g;
         return fail(PBN_EPARSE, "missing 'pbn' header");
     }
+    return finish_net(g, PBN_EPARSE, out);
+}
+
+/* Per-node requirements shared by both loaders; takes ownership of g. */
+int finish_net(pbn_net* g, int code, pbn_net** out) {
     for (uint32_t i = 0; i < g->n; ++i) {
         const auto& fl = g->node[i];
         if (fl.empty() || fl.size() > 16) {
+            const size_t nf = fl.size();
             delete g;
-            return fail(PBN_EPARSE, "node %u has %zu functions (need 1..16)", i, fl.size());
+            return fail(code, "node %u has %zu functions (need 1..16)", i, nf);
         }
         double s = 0.0;
         for (const auto& f : fl) s += f.c;
         if (std::fabs(s - 1.0) > 1e-9) {
             delete g;
-            return fail(PBN_EPARSE, "selection probabilities of node %u sum to %.17g", i, s);
+            return fail(code, "selection probabilities of node %u sum to %.17g", i, s);
         }
     }
     g->retained.assign(g->n, 1);
     *out = g;
     return PBN_OK;
+}
+
+int load_arrays_impl(const pbn_net_desc* d, pbn_net** out) {
+    if (d->n < 1 || d->n > (1u << 24) || !(d->p >= 0.0 && d->p < 1.0))
+        return fail(PBN_EINVAL, "pbn_load_arrays: need 1 <= n <= 2^24 and 0 <= p < 1");
+    if (d->n_functions && (!d->fun_node || !d->fun_c || !d->fun_k || !d->tt))
+        return fail(PBN_EINVAL, "pbn_load_arrays: NULL array");
+    std::unique_ptr<pbn_net> g(new pbn_net());
+    g->n = d->n;
+    g->p = d->p;
+    g->node.assign(d->n, {});
+    uint64_t po = 0, to = 0;
+    for (uint32_t f = 0; f < d->n_functions; ++f) {
+        const uint32_t i = d->fun_node[f], k = d->fun_k[f];
+        const double c = d->fun_c[f];
+        if (i >= d->n || k > 24 || !(c >= 0.0 && c <= 1.0))
+            return fail(PBN_EINVAL, "pbn_load_arrays: function %u: bad node, k or c", f);
+        if (k && !d->parents) return fail(PBN_EINVAL, "pbn_load_arrays: NULL parents");
+        pbn_fun fn;
+        fn.c = c;
+        for (uint32_t b = 0; b < k; ++b) {
+            const uint32_t a = d->parents[po + b];
+            if (a >= d->n || std::find(fn.par.begin(), fn.par.end(), a) != fn.par.end())
+                return fail(PBN_EINVAL, "pbn_load_arrays: function %u: bad or repeated parent", f);
+            fn.par.push_back(a);
+        }
+        po += k;
+        const uint64_t nbits = 1ull << k, nw = (nbits + 63) / 64;
+        fn.tt.assign(d->tt + to, d->tt + to + nw);
+        to += nw;
+        if (nbits < 64 && (fn.tt[0] >> nbits))
+            return fail(PBN_EINVAL, "pbn_load_arrays: function %u: truth table wider than 2^k bits", f);
+        g->node[i].push_back(std::move(fn));
+    }
+    return finish_net(g.release(), PBN_EINVAL, out);
 }
 
 }  // namespace
@@ -213,6 +257,16 @@ extern "C" int pbn_load(const char* text, size_t len, pbn_net** out) {
         return load_impl(text, len, out);
     } catch (const std::bad_alloc&) {
         return fail(PBN_ENOMEM, "pbn_load: out of memory");
+    }
+}
+
+extern "C" int pbn_load_arrays(const pbn_net_desc* desc, pbn_net** out) {
+    if (!desc || !out) return fail(PBN_EINVAL, "pbn_load_arrays: NULL argument");
+    *out = nullptr;
+    try {
+        return load_arrays_impl(desc, out);
+    } catch (const std::bad_alloc&) {
+        return fail(PBN_ENOMEM, "pbn_load_arrays: out of memory");
     }
 }
 
@@ -242,7 +296,13 @@ extern "C" int pbn_net_info_get(const pbn_net* g, pbn_net_info* out) {
 /* ------------------------------------------------------------------------- */
 extern "C" int pbn_reduce(const pbn_net* net, const uint32_t* interest, uint32_t n_interest,
                           pbn_net** reduced, uint32_t* retained_ids, uint32_t* n_retained) {
+    return pbn_reduce_rule(net, interest, n_interest, PBN_REDUCE_LEAVES, reduced, retained_ids, n_retained);
+}
+
+extern "C" int pbn_reduce_rule(const pbn_net* net, const uint32_t* interest, uint32_t n_interest, uint32_t rule,
+                               pbn_net** reduced, uint32_t* retained_ids, uint32_t* n_retained) {
     if (!net || !reduced || (n_interest && !interest)) return fail(PBN_EINVAL, "pbn_reduce: NULL argument");
+    if (rule != PBN_REDUCE_LEAVES && rule != PBN_REDUCE_REACH) return fail(PBN_EINVAL, "pbn_reduce: unknown rule %u", rule);
     *reduced = nullptr;
     try {
         const uint32_t n = net->n;
@@ -264,17 +324,31 @@ extern "C" int pbn_reduce(const pbn_net* net, const uint32_t* interest, uint32_t
         }
         std::vector<uint8_t> leaf(n, 0);
         std::vector<uint32_t> stack;
-        for (uint32_t v = 0; v < n; ++v)
-            if (!intr[v] && live_children[v] == 0) { leaf[v] = 1; stack.push_back(v); }
-        while (!stack.empty()) {
-            uint32_t v = stack.back();
-            stack.pop_back();
-            for (uint32_t a : parents[v]) {
-                if (--live_children[a] == 0 && !intr[a] && !leaf[a]) {
-                    leaf[a] = 1;
-                    stack.push_back(a);
+        if (rule == PBN_REDUCE_LEAVES) {
+            for (uint32_t v = 0; v < n; ++v)
+                if (!intr[v] && live_children[v] == 0) { leaf[v] = 1; stack.push_back(v); }
+            while (!stack.empty()) {
+                uint32_t v = stack.back();
+                stack.pop_back();
+                for (uint32_t a : parents[v]) {
+                    if (--live_children[a] == 0 && !intr[a] && !leaf[a]) {
+                        leaf[a] = 1;
+                        stack.push_back(a);
+                    }
                 }
             }
+        } else {
+            /* search backwards from the nodes of interest along child -> parent */
+            std::vector<uint8_t> reach(n, 0);
+            for (uint32_t v = 0; v < n; ++v)
+                if (intr[v]) { reach[v] = 1; stack.push_back(v); }
+            while (!stack.empty()) {
+                uint32_t v = stack.back();
+                stack.pop_back();
+                for (uint32_t a : parents[v])
+                    if (!reach[a]) { reach[a] = 1; stack.push_back(a); }
+            }
+            for (uint32_t v = 0; v < n; ++v) leaf[v] = !reach[v];
         }
         pbn_net* r = new pbn_net(*net);
         uint32_t cnt = 0;
@@ -563,6 +637,8 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     std::vector<pbn_img_multi> mrec;
     std::vector<uint32_t> thr, inrec, tables;
     std::vector<uint32_t> selslot(16 * selblk.size(), 0u);
+    std::vector<uint32_t> subs; /* uint2 per function of a split node: in_chunk | k << 27, tab_off */
+    uint32_t n_split = 0;
     uint64_t total_inputs = 0;
     uint32_t n_groups_multi = 0;
     for (uint32_t k = 0; k < W32; ++k) {
@@ -575,6 +651,67 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
             std::vector<uint32_t> ins = gr.inputs;
             std::sort(ins.begin(), ins.end(), [&](uint32_t a, uint32_t b) { return plan->pos[a] < plan->pos[b]; });
             const size_t q = ins.size();
+            /* a lone multi-function node whose inputs exceed the merge cap keeps one
+             * table per predictor function (over that function's own inputs) instead of
+             * one table over the union: l * 2^q entries would waste memory */
+            const bool split = gr.nodes.size() == 1 && g.node[gr.nodes[0]].size() >= 2 && q > prm.max_inputs;
+            if (split) {
+                const uint32_t v = gr.nodes[0];
+                const auto& fl = g.node[v];
+                pbn_img_group G{};
+                G.mul_first = (uint32_t)mrec.size();
+                pbn_img_multi M{};
+                const uint32_t first = (uint32_t)thr.size();
+                double C = 0.0;
+                uint32_t n_thr = 0;
+                for (size_t j = 1; j < fl.size(); ++j) {
+                    C = C + fl[j - 1].c;
+                    double t = std::floor(C * 4294967296.0);
+                    if (t >= 4294967296.0) break;
+                    thr.push_back((uint32_t)t);
+                    n_thr++;
+                }
+                const uint32_t slot = sel_slot(v);
+                M.ch_off = slot;
+                M.radix = 1;
+                uint32_t* ss = &selslot[4 * slot];
+                ss[0] = n_thr >= 1 ? thr[first] : 0u;
+                ss[1] = n_thr >= 2 ? thr[first + 1] : 0u;
+                ss[2] = n_thr;
+                ss[3] = first;
+                mrec.push_back(M);
+                G.tab_off = (uint32_t)(subs.size() / 2); /* first sub-function */
+                G.in_chunk = 0;
+                G.q = (uint8_t)fl.size();
+                G.l2w = PBN_IMG_SPLIT;
+                G.n_mul = 1;
+                G.shift = (uint8_t)gshift[gi];
+                for (const pbn_fun& f : fl) {
+                    const uint32_t chunk = (uint32_t)(inrec.size() / 4);
+                    for (size_t b = 0; b < f.par.size(); ++b) {
+                        const uint32_t ps = plan->pos[f.par[b]];
+                        if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", f.par[b]);
+                        inrec.push_back(((ps >> 5) << 7) | (((ps & 31) - (uint32_t)(b & 3)) & 31));
+                    }
+                    while (inrec.size() % 4) inrec.push_back(W32 << 7);
+                    const uint32_t k = (uint32_t)f.par.size();
+                    const uint32_t to = (uint32_t)tables.size();
+                    if (chunk >= (1u << 27)) return fail(PBN_ETOOBIG, "input records beyond 2^27 chunks");
+                    subs.push_back(chunk | (k << 27));
+                    subs.push_back(to);
+                    const uint64_t nb = 1ull << k;
+                    tables.resize(tables.size() + (size_t)((nb + 31) / 32), 0);
+                    uint32_t* tab = tables.data() + to;
+                    for (uint64_t x = 0; x < nb; ++x) tab[x >> 5] |= (uint32_t)f.bit(x) << (x & 31);
+                }
+                /* one function's inputs are read per step: count their mean */
+                uint64_t ksum = 0;
+                for (const pbn_fun& f : fl) ksum += f.par.size();
+                total_inputs += (ksum + fl.size() - 1) / fl.size();
+                grec.push_back(G);
+                n_split++;
+                continue;
+            }
             if (q > 24) return fail(PBN_ETOOBIG, "group with %zu inputs (max 24)", q);
             std::vector<int> inpos(n, -1);
             const uint32_t in_chunk = (uint32_t)(inrec.size() / 4);
@@ -668,6 +805,8 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
         std::vector<uint32_t> idx(grec.size());
         std::iota(idx.begin(), idx.end(), 0u);
         std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+            const bool sa = grec[a].l2w == PBN_IMG_SPLIT, sb = grec[b].l2w == PBN_IMG_SPLIT;
+            if (sa != sb) return sa;
             const uint32_t qa = (grec[a].q + 3) / 4, qb = (grec[b].q + 3) / 4;
             if (qa != qb) return qa > qb;
             return grec[a].n_mul > grec[b].n_mul;
@@ -697,6 +836,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.off_inputs = (uint32_t)off; off = align16(off + inrec.size() * 4);
     H.off_selblk = (uint32_t)off; off = align16(off + selblk.size() * 4);
     H.off_gorder = (uint32_t)off; off = align16(off + gorder.size() * 4);
+    H.off_subs = (uint32_t)off; off = align16(off + subs.size() * 4);
     H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
     H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
     H.off_pos = (uint32_t)off; off = align16(off + plan->pos.size() * 4);
@@ -718,6 +858,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     if (!inrec.empty()) memcpy(img + H.off_inputs, inrec.data(), inrec.size() * 4);
     if (!selblk.empty()) memcpy(img + H.off_selblk, selblk.data(), selblk.size() * 4);
     if (!gorder.empty()) memcpy(img + H.off_gorder, gorder.data(), gorder.size() * 4);
+    if (!subs.empty()) memcpy(img + H.off_subs, subs.data(), subs.size() * 4);
     memcpy(img + H.off_ret, ret.data(), ret.size() * 8);
     memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
     if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);
@@ -741,6 +882,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     I.tables_in_smem = H.tables_in_smem;
     I.total_inputs = (uint32_t)total_inputs;
     I.n_multi = (uint32_t)mrec.size();
+    I.n_split = n_split;
     I.total_thresholds = (uint32_t)thr.size();
     /* algorithmic work of one trajectory-step (the roofline's per-unit figure) */
     {
@@ -754,7 +896,8 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
         }
         const double pert = blocks * (56.0 + 12.0) + 4.0;
         const double nonpert = 56.0 * H.n_sel + 2.0 * (double)thr.size() + (double)mrec.size() +
-                               3.0 * (double)total_inputs + 5.0 * (double)H.n_groups + 2.0 * (double)(W32 / 2);
+                               3.0 * (double)total_inputs + 5.0 * (double)(H.n_groups + n_split) +
+                               2.0 * (double)(W32 / 2);
         I.ops_per_step = pert + std::pow(1.0 - pe, (double)n) * nonpert + 8.0;
     }
     return PBN_OK;

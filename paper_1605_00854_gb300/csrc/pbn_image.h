@@ -25,6 +25,7 @@
  *   gorder  [n_groups]   uint32 group index | output word << 20, groups sorted by
  *                        shape (inputs, multi-function nodes): the evaluation order
  *                        when several lanes share a trajectory
+ *   subs    [...]        uint2 function records of split nodes (see below)
  *   tables  [...]        uint32 words of packed table entries; entry e of a group
  *                        with log2 entry width l2w occupies bits
  *                        [e << l2w, (e + 1) << l2w) of its table
@@ -52,11 +53,18 @@ typedef struct {
     uint32_t n_sel;      /* SEL blocks per step */
     uint32_t P;          /* perturbation threshold */
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr;
-    uint32_t off_inputs, off_selblk, off_gorder, off_tables, off_ret, off_pos;
+    uint32_t off_inputs, off_selblk, off_gorder, off_subs, off_tables, off_ret, off_pos;
     uint32_t image_bytes;
     uint32_t stage_bytes;
     uint32_t tables_in_smem;
-} pbn_img_header; /* 88 bytes */
+} pbn_img_header; /* 92 bytes */
+
+/* A group record with l2w == PBN_IMG_SPLIT is a split node: one multi-function node
+ * whose q functions each keep their own table of 2^k one-bit entries over their own
+ * k inputs; tab_off is then the index of its first function record
+ * (uint2 {first input chunk | k << 27, table offset in words}) and the node's choice
+ * selects which function is evaluated. */
+#define PBN_IMG_SPLIT 0xFFu
 
 typedef struct {
     uint32_t tab_off;   /* table offset in uint32 words from the tables section */

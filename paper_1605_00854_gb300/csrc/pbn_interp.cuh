@@ -17,6 +17,7 @@
  *      nodes are drawn; for every group the combined choice c (mixed radix), the
  *      input pattern x (4-input chunks) and the table entry T[c][x] give the
  *      group's new bits, ORed into the next state at the group's offset (cum).
+ *      A split node evaluates only its selected function's own table.
  *   3. the meta-state indicator z of the new state updates V, n01, n10, n11.
  */
 #ifndef PBN_INTERP_CUH
@@ -69,6 +70,7 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
     const uint4* INPUTS = reinterpret_cast<const uint4*>(SP + P.off_inputs);
     const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(SP + P.off_selblk);
     const uint32_t* GORDER = reinterpret_cast<const uint32_t*>(SP + P.off_gorder);
+    const uint2* SUBS = reinterpret_cast<const uint2*>(SP + P.off_subs);
     const uint64_t* RET = reinterpret_cast<const uint64_t*>(P.image + P.off_ret);
     const uint32_t* POS = reinterpret_cast<const uint32_t*>(P.image + P.off_pos);
     const uint32_t* TAB = TAB_SMEM ? reinterpret_cast<const uint32_t*>(smem + P.off_tables)
@@ -213,19 +215,9 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                 const uint8_t* Sc8 = reinterpret_cast<const uint8_t*>(Sc);
                 uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
                 /* new bits of group gi, already at their place in the output word */
-                auto group_bits = [&](uint32_t gi) -> uint32_t {
-                    const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
-                    const uint32_t q = G.w & 0xFFu;
-                    const uint32_t l2w = (G.w >> 8) & 0xFFu;
-                    const uint32_t n_mul = (G.w >> 16) & 0xFFu;
-                    const uint32_t shift = G.w >> 24;
-                    uint32_t c = 0;
-                    for (uint32_t m = 0; m < n_mul; ++m) {
-                        const uint2 M = MULTI[G.z + m]; /* choice byte, radix */
-                        c += (uint32_t)Cb[M.x] * M.y;
-                    }
+                /* input pattern of q inputs from their chunked records */
+                auto gather = [&](const uint4* ch, uint32_t q) -> uint32_t {
                     uint32_t x = 0;
-                    const uint4* ch = INPUTS + G.y;
                     for (uint32_t b0 = 0; b0 < q; b0 += 4) {
                         const uint4 R = *ch++;
                         const uint32_t v0 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.x >> 5));
@@ -238,6 +230,28 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                         x4 |= __funnelshift_r(v3, v3, R.w) & 8u;
                         x |= x4 << b0;
                     }
+                    return x;
+                };
+                /* new bits of group gi, already at their place in the output word */
+                auto group_bits = [&](uint32_t gi) -> uint32_t {
+                    const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
+                    const uint32_t q = G.w & 0xFFu;
+                    const uint32_t l2w = (G.w >> 8) & 0xFFu;
+                    const uint32_t n_mul = (G.w >> 16) & 0xFFu;
+                    const uint32_t shift = G.w >> 24;
+                    if (l2w == PBN_IMG_SPLIT) {
+                        /* split node: only the selected function is evaluated */
+                        const uint2 F = SUBS[G.x + Cb[MULTI[G.z].x]]; /* in_chunk | k << 27, tab_off */
+                        const uint32_t x = gather(INPUTS + (F.x & 0x7FFFFFFu), F.x >> 27);
+                        const uint32_t tw = TAB_SMEM ? TAB[F.y + (x >> 5)] : __ldg(TAB + F.y + (x >> 5));
+                        return ((tw >> (x & 31u)) & 1u) << shift;
+                    }
+                    uint32_t c = 0;
+                    for (uint32_t m = 0; m < n_mul; ++m) {
+                        const uint2 M = MULTI[G.z + m]; /* choice byte, radix */
+                        c += (uint32_t)Cb[M.x] * M.y;
+                    }
+                    const uint32_t x = gather(INPUTS + G.y, q);
                     const uint32_t bo = ((c << q) | x) << l2w;
                     const uint32_t tw = TAB_SMEM ? TAB[G.x + (bo >> 5)] : __ldg(TAB + G.x + (bo >> 5));
                     const uint32_t emask = (2u << ((1u << l2w) - 1u)) - 1u;

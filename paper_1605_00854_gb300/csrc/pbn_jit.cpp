@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -148,6 +149,15 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     const uint32_t* selslot = V.at<uint32_t>(H.off_selslot);
     const bool tab_smem = table_bytes <= 48u * 1024u;
     out->tab_bytes = tab_smem ? table_bytes : 0u;
+    const uint32_t* subs = V.at<uint32_t>(H.off_subs);
+    /* start offsets of every table (merged groups and split-node functions), sorted */
+    std::vector<uint32_t> tab_starts;
+    for (uint32_t g = 0; g < H.n_groups; ++g) {
+        if (groups[g].l2w != PBN_IMG_SPLIT) tab_starts.push_back(groups[g].tab_off);
+        else
+            for (uint32_t f = 0; f < groups[g].q; ++f) tab_starts.push_back(subs[2 * (groups[g].tab_off + f) + 1]);
+    }
+    std::sort(tab_starts.begin(), tab_starts.end());
 
     std::ostringstream o;
     o << "#include \"pbn_device.cuh\"\n";
@@ -204,6 +214,15 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
          "      const uint64_t t = P.step_begin + k;\n"
          "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
          "      uint32_t any = 0;\n";
+    const bool interleave = (flags & PBN_COMPILE_INTERLEAVED) != 0;
+    auto emit_sel_draws = [&](const char* ind) {
+        for (uint32_t i = 0; i < H.n_sel; ++i)
+            o << ind << "const uint4 U" << i << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
+    };
+    /* interleaved: the SEL blocks are drawn before the perturbation check (they are
+     * needed in every non-perturbed step), so that their Philox chains and the first
+     * perturbation levels form one block of independent work */
+    if (interleave) emit_sel_draws("      ");
     /* 1. perturbation: the levels of P compiled in */
     const uint32_t Pv = H.P;
     auto emit_flips = [&](uint32_t w, const char* pl, const char* ph, const char* sfx) {
@@ -259,9 +278,26 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
               << ", pl0 = 0, ph0 = 0";
             if (two) o << ", ul1 = " << hex32((uint32_t)v1) << ", uh1 = " << hex32((uint32_t)(v1 >> 32)) << ", pl1 = 0, ph1 = 0";
-            o << ";\n        uint32_t pp = " << hex32(Pv) << ";\n"
+            /* interleaved: the first level pairs (needed by a 64-lane word with
+             * probability ~1) are straight-line code without an exit test */
+            const uint32_t npeel = interleave ? std::min<uint32_t>(hmax, 3u) : 0u;
+            o << ";\n";
+            for (uint32_t h = 0; h < npeel; ++h) {
+                const uint32_t b0 = (Pv >> (31 - 2 * h)) & 1u;
+                const uint32_t b1 = (Pv >> (30 - 2 * h)) & 1u;
+                for (int k = 0; k < (two ? 2 : 1); ++k) {
+                    o << fmt("        { const uint4 x = pbn_philox_draw(P, ps, %s);",
+                             hex32((PBN_DOM_PERT << 28) | ((w + k) << 4) | h).c_str());
+                    if (b0) o << fmt(" pl%d |= ul%d & ~x.x; ph%d |= uh%d & ~x.y; ul%d &= x.x; uh%d &= x.y;", k, k, k, k, k, k);
+                    else o << fmt(" ul%d &= ~x.x; uh%d &= ~x.y;", k, k);
+                    if (b1) o << fmt(" pl%d |= ul%d & ~x.z; ph%d |= uh%d & ~x.w; ul%d &= x.z; uh%d &= x.w;", k, k, k, k, k, k);
+                    else o << fmt(" ul%d &= ~x.z; uh%d &= ~x.w;", k, k);
+                    o << " }\n";
+                }
+            }
+            o << "        uint32_t pp = " << hex32(npeel ? (Pv << (2 * npeel)) : Pv) << ";\n"
               << "#pragma unroll 1\n"
-              << "        for (uint32_t h = 0; h < " << hmax << "u; ++h) {\n"
+              << "        for (uint32_t h = " << npeel << "u; h < " << hmax << "u; ++h) {\n"
               << "          if (!(ul0 | uh0" << (two ? " | ul1 | uh1" : "") << ")) break;\n"
               << "          const uint32_t m0 = (uint32_t)((int32_t)pp >> 31), m1 = (uint32_t)((int32_t)(pp << 1) >> 31);\n"
               << "          pp <<= 2;\n"
@@ -287,17 +323,14 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     }
     /* 2. selection draws and merged-table evaluation */
     o << "      if (!any) {\n";
-    for (uint32_t i = 0; i < H.n_sel; ++i)
-        o << "        const uint4 U" << i << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
+    if (!interleave) emit_sel_draws("        ");
     for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
     for (uint32_t r = 0; r < H.W32; ++r) {
         for (uint32_t gi = words[r].x; gi < words[r].x + words[r].y; ++gi) {
             const pbn_img_group& G = groups[gi];
             o << "        { ";
-            /* combined choice */
-            std::string cexpr;
-            for (uint32_t m = 0; m < G.n_mul; ++m) {
-                const pbn_img_multi& M = multi[G.mul_first + m];
+            /* choice of a multi-function node from its SEL slot's thresholds */
+            auto choice_expr = [&](const pbn_img_multi& M) {
                 const uint32_t slot = M.ch_off;
                 const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
                 const uint32_t* ss = selslot + 4 * slot; /* t1, t2, n_thr, first */
@@ -307,30 +340,71 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
                     const uint32_t T = n_thr <= 2 ? ss[q] : thr[ss[3] + q];
                     j += (q ? " + " : "") + fmt("(uint32_t)(%s >= %s)", u.c_str(), hex32(T).c_str());
                 }
+                return j;
+            };
+            /* input pattern of k inputs from chunked records */
+            auto pattern = [&](uint32_t in_chunk, uint32_t k) {
+                std::string xexpr;
+                for (uint32_t b = 0; b < k; ++b) {
+                    const uint32_t rec = inrec[4 * in_chunk + b];
+                    const uint32_t row = rec >> 7, bit = ((b & 3) + (rec & 31)) & 31;
+                    xexpr += (b ? " | " : "") + gather(row, bit, b);
+                }
+                return xexpr.empty() ? std::string("0u") : xexpr;
+            };
+            if (G.l2w == PBN_IMG_SPLIT) {
+                /* split node: every function's pattern is a few register operations;
+                 * the selected one's table bit is kept (immediates when every table
+                 * fits in 64 bits, else one lookup at the selected table) */
+                std::string j = choice_expr(multi[G.mul_first]);
+                if (j.empty()) j = "0u";
+                o << "const uint32_t j = " << j << "; ";
+                bool small = true;
+                for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + f)] >> 27) <= 6;
+                std::string v = "0u";
+                if (small) {
+                    for (uint32_t f = G.q; f-- > 0;) {
+                        const uint32_t* F = subs + 2 * (G.tab_off + f);
+                        const uint32_t k = F[0] >> 27, ch = F[0] & 0x7FFFFFFu;
+                        const uint64_t t64 = (k == 6 ? ((uint64_t)tab[F[1] + 1] << 32) : 0ull) | tab[F[1]];
+                        const std::string vf =
+                            fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k) + ")) & 1ull)";
+                        v = f + 1 == G.q ? vf : fmt("(j == %uu ? ", f) + vf + " : " + v + ")";
+                    }
+                } else {
+                    std::string xs = "0u", offs = "0u";
+                    for (uint32_t f = G.q; f-- > 0;) {
+                        const uint32_t* F = subs + 2 * (G.tab_off + f);
+                        const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27) + ")";
+                        xs = f + 1 == G.q ? xf : fmt("(j == %uu ? ", f) + xf + " : " + xs + ")";
+                        offs = f + 1 == G.q ? fmt("%uu", F[1]) : fmt("(j == %uu ? %uu : ", f, F[1]) + offs + ")";
+                    }
+                    o << "const uint32_t x = " << xs << "; const uint32_t to = " << offs << "; ";
+                    v = tab_smem ? "((TAB[to + (x >> 5)] >> (x & 31u)) & 1u)" : "((__ldg(TAB + to + (x >> 5)) >> (x & 31u)) & 1u)";
+                }
+                o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
+                continue;
+            }
+            /* combined choice */
+            std::string cexpr;
+            for (uint32_t m = 0; m < G.n_mul; ++m) {
+                const pbn_img_multi& M = multi[G.mul_first + m];
+                const std::string j = choice_expr(M);
                 if (j.empty()) continue;
                 cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
             }
             /* input pattern */
-            std::string xexpr;
             const uint32_t q = G.q;
-            for (uint32_t b = 0; b < q; ++b) {
-                const uint32_t rec = inrec[4 * G.in_chunk + b];
-                const uint32_t row = rec >> 7, bit = ((b & 3) + (rec & 31)) & 31;
-                xexpr += (b ? " | " : "") + gather(row, bit, b);
-            }
-            if (xexpr.empty()) xexpr = "0u";
-            o << "const uint32_t x = " << xexpr << "; ";
+            o << "const uint32_t x = " << pattern(G.in_chunk, q) << "; ";
             if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
             else o << "const uint32_t e = x; ";
             /* table entry */
             const uint32_t l2w = G.l2w;
             const uint32_t ebits = 1u << l2w;
             const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
-            /* size of this group's table in bits: from the next group's offset, or the end */
-            uint32_t next_off = table_bytes / 4;
-            for (uint32_t g2 = 0; g2 < H.n_groups; ++g2)
-                if (groups[g2].tab_off > G.tab_off && groups[g2].tab_off < next_off) next_off = groups[g2].tab_off;
-            const uint32_t tab_words = next_off - G.tab_off;
+            /* size of this group's table in words: up to the next table's offset, or the end */
+            auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
+            const uint32_t tab_words = (nx == tab_starts.end() ? table_bytes / 4 : *nx) - G.tab_off;
             std::string v;
             if (tab_words == 1) {
                 v = fmt("((%s >> (e << %u)) & %s)", hex32(tab[G.tab_off]).c_str(), l2w, hex32(emask).c_str());
@@ -504,7 +578,8 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 
 extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
-    if (flags & ~PBN_COMPILE_PERT_UNROLLED) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
+    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED))
+        return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
     const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;
     return rc;

@@ -65,7 +65,7 @@ struct SimParams {
     uint32_t hmax;             /* level pairs that can still decide a perturbation */
     uint32_t n, W, W32, n_sel, P;
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret, off_pos,
-        off_tables, n_groups;
+        off_tables, n_groups, off_subs;
     uint32_t n_meta_rows;
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
@@ -239,6 +239,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.off_multi = H.off_multi;
     P.off_selslot = H.off_selslot;
     P.off_gorder = H.off_gorder;
+    P.off_subs = H.off_subs;
     P.n_groups = H.n_groups;
     P.off_thr = H.off_thr;
     P.off_inputs = H.off_inputs;

@@ -171,6 +171,54 @@ def scalefree2000(seed: int = 3, n: int = 2000, p: float = 1e-5, exponent: float
                       parent_weights=w)
 
 
+def apoptosis96(seed: int = 5, n: int = 96, n_leaves: int = 36, total_inputs: int = 171,
+                p: float = 1e-4) -> Network:
+    """Stand-in with the shape of the paper's apoptosis network (Sec. 4.3: 96 nodes,
+    37.5% leaves, density 1.78); the real model is not available.  60 core nodes
+    lie on one random directed cycle (each core node's first parent in every
+    function is its cycle predecessor, so every core node has a core child and is
+    never a leaf); the other 36 nodes are never parents, so Definition 1 removes
+    exactly them for any meta-state over core nodes.  l = 1 w.p. 0.7 else 2; further
+    parents drawn uniformly from the core; in-degrees adjusted to sum to 171 over
+    all functions (density 171 / 96 = 1.78); truth tables Bernoulli(1/2), with
+    every core function depending on its cycle predecessor; c ~ Dirichlet(1).
+    Core nodes are 0..59 (the meta-state nodes are drawn from them)."""
+    rng = np.random.default_rng(seed + 104729)
+    core = n - n_leaves
+    perm = rng.permutation(core)
+    pred = np.empty(core, dtype=int)
+    pred[perm] = np.roll(perm, 1)
+    ells = [1 if rng.random() < 0.7 else 2 for _ in range(n)]
+    ks = [[int(rng.choice((1, 2, 3), p=(0.72, 0.19, 0.09))) for _ in range(l)] for l in ells]
+    # adjust the in-degrees so that they sum to total_inputs exactly
+    flat = [(i, j) for i in range(n) for j in range(ells[i])]
+    while sum(map(sum, ks)) != total_inputs:
+        i, j = flat[int(rng.integers(len(flat)))]
+        if sum(map(sum, ks)) > total_inputs and ks[i][j] > 1:
+            ks[i][j] -= 1
+        elif sum(map(sum, ks)) < total_inputs and ks[i][j] < 3:
+            ks[i][j] += 1
+    net = Network(n=n, p=p, funcs=[])
+    for i in range(n):
+        cs = _dirichlet(rng, ells[i])
+        fl = []
+        for j in range(ells[i]):
+            k = ks[i][j]
+            first = [int(pred[i])] if i < core else []
+            others = [int(a) for a in rng.permutation(core) if a not in first and a != i][: k - len(first)]
+            par = first + others
+            while True:
+                tt = _tt(rng, k)
+                if i >= core:
+                    break
+                # the output must depend on input 0 (the cycle predecessor)
+                if any(((tt >> x) & 1) != ((tt >> (x | 1)) & 1) for x in range(0, 1 << k, 2)):
+                    break
+            fl.append(Function(c=cs[j], parents=par, tt=tt))
+        net.funcs.append(fl)
+    return net
+
+
 def batch_shapes(seed: int = 4, count: int = 256, n_range=(20, 4000), t_range=(1024, 65536),
                  p_range=(1e-5, 1e-2)):
     """Shapes of the batched workload: (n, n_traj, p) log-uniform per network."""

@@ -5,13 +5,13 @@ import numpy as np
 
 HEADER_FIELDS = ["magic", "n", "W", "W32", "n_groups", "n_multi", "n_sel", "P",
                  "off_words", "off_groups", "off_multi", "off_selslot", "off_thr", "off_inputs",
-                 "off_selblk", "off_gorder", "off_tables", "off_ret", "off_pos", "image_bytes",
+                 "off_selblk", "off_gorder", "off_subs", "off_tables", "off_ret", "off_pos", "image_bytes",
                  "stage_bytes", "tables_in_smem"]
 
 
 def decode(img: np.ndarray) -> dict:
     b = img.tobytes()
-    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<22I", b, 0)))
+    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<23I", b, 0)))
     u32 = np.frombuffer(b, dtype=np.uint32)
     words = u32[H["off_words"] // 4: H["off_words"] // 4 + 2 * H["W32"]].reshape(-1, 2)
     groups = []
@@ -48,6 +48,34 @@ def inputs(D, g):
         row, rot = rec >> 7, rec & 31
         out.append((row, ((b & 3) + rot) & 31))
     return out
+
+
+SPLIT = 0xFF
+
+
+def subs(D, g):
+    """Sub-function records (in_chunk, k, tab_off) of split group g, one per function."""
+    G = D["groups"][g]
+    o = D["H"]["off_subs"] // 4 + 2 * G["tab_off"]
+    out = []
+    for j in range(G["q"]):
+        a, tab_off = int(D["u32"][o + 2 * j]), int(D["u32"][o + 2 * j + 1])
+        out.append((a & 0x7FFFFFF, a >> 27, tab_off))
+    return out
+
+
+def sub_inputs(D, in_chunk, k):
+    o = D["H"]["off_inputs"] // 4 + 4 * in_chunk
+    out = []
+    for b, rec in enumerate(int(v) for v in D["u32"][o: o + k]):
+        row, rot = rec >> 7, rec & 31
+        out.append((row, ((b & 3) + rot) & 31))
+    return out
+
+
+def sub_entry(D, tab_off, x):
+    w = int(D["u32"][D["H"]["off_tables"] // 4 + tab_off + (x >> 5)])
+    return (w >> (x & 31)) & 1
 
 
 def entry(D, g, e):

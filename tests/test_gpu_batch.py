@@ -131,3 +131,23 @@ def test_batch_wide_networks_use_lane_groups():
         got = _collect(plan, e["bufs"])
         assert np.array_equal(got["final"][:, ids], ref["final"][:, ids])
         assert np.array_equal(got["counts"], ref["counts"])
+
+
+def test_batch_with_split_nodes(oracle_mod):
+    """Networks with split nodes in the batched kernel equal the oracle."""
+    texts = [synth.random_pbn(50 + i, 30 + 7 * i, 1e-2, k_choices=tuple(range(1, 11))).to_text() for i in range(3)]
+    entries, plans = [], []
+    for k, text in enumerate(texts):
+        plan, ids = plan_for(text, [0, 1], max_inputs=3)
+        assert plan.info.n_split > 0
+        bufs = api.alloc_buffers(plan, 100 + 50 * k)
+        entries.append(dict(plan=plan, bufs=bufs, seed=9 + k, meta_ids=[0, 1]))
+        plans.append((plan, ids))
+    B = api.Batch(entries)
+    B.run(300)
+    assert int(B.status.item()) == 0
+    for k, (text, (plan, ids), e) in enumerate(zip(texts, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(text, 9 + k, 0, 100 + 50 * k, 300, meta_ids=[0, 1], nthreads=NCPU)
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+        assert np.array_equal(got["counts"], orc["counts"]), k

@@ -64,7 +64,7 @@ def test_compiled_resume_and_keyed_init(oracle_mod):
     _compare(a, orc, ids)
 
 
-@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PERT_UNROLLED])
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PERT_UNROLLED, _lib.PBN_COMPILE_INTERLEAVED])
 @pytest.mark.parametrize("p", [0.0, 0.05, 0.3, 0.75])
 def test_compiled_perturbation_regimes(oracle_mod, p, flags):
     text = synth.paper100(seed=9, n=170, p=p).to_text()
@@ -103,3 +103,16 @@ def test_compiled_global_tables(oracle_mod):
     plan.compile()
     orc = oracle_mod.simulate(text, 3, 0, 128, 400, meta_ids=meta, nthreads=NCPU)
     _compare(run(plan, seed=3, n_traj=128, n_steps=400, meta=meta, kernel=COMPILED), orc, ids, trace=False)
+
+
+@pytest.mark.parametrize("kmax", [5, 10])
+def test_compiled_split_nodes(oracle_mod, kmax):
+    """Split nodes in a compiled plan: function tables as immediates (k <= 6) or one
+    lookup at the selected function's table."""
+    text = synth.random_pbn(5, 40, 1e-2, k_choices=tuple(range(1, kmax + 1))).to_text()
+    meta = [0, 1]
+    plan, ids = plan_for(text, meta, max_inputs=3)
+    assert plan.info.n_split > 0
+    plan.compile()
+    orc = oracle_mod.simulate(text, 21, 0, 160, 400, meta_ids=meta, trace=True, nthreads=NCPU)
+    _compare(run(plan, seed=21, n_traj=160, n_steps=400, meta=meta, trace=True, kernel=COMPILED), orc, ids)

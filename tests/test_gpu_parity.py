@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from gpu_helpers import plan_for, run
-from paper_1605_00854_gb300 import synth
+from paper_1605_00854_gb300 import _lib, synth
 
 pytestmark = pytest.mark.gpu
 NCPU = os.cpu_count() or 1
@@ -115,6 +115,48 @@ def test_tables_in_global_memory(oracle_mod):
     _compare(gpu, orc, ids, trace=False)
 
 
+@pytest.mark.parametrize("lanes", [1, 2, 8])
+@pytest.mark.parametrize("tables", ["smem", "global"])
+def test_split_nodes(oracle_mod, lanes, tables):
+    """Multi-function nodes whose inputs exceed the merge cap keep one table per
+    function (split nodes); only the selected function is evaluated."""
+    text = synth.random_pbn(5, 40, 1e-2, k_choices=tuple(range(1, 11))).to_text()
+    meta = [0, 1]
+    kw = dict(max_inputs=3)
+    if tables == "global":
+        import imgdecode
+        base, _ = plan_for(text, meta, **kw)
+        kw["smem_budget"] = max(1024, imgdecode.decode(base.image())["H"]["off_tables"])
+    plan, ids = plan_for(text, meta, **kw)
+    assert plan.info.n_split > 0
+    assert plan.info.tables_in_smem == (tables == "smem")
+    orc = oracle_mod.simulate(text, 21, 0, 160, 400, meta_ids=meta, trace=True, nthreads=NCPU)
+    gpu = run(plan, seed=21, n_traj=160, n_steps=400, meta=meta, trace=True, lanes=lanes,
+              kernel=_lib.PBN_KERNEL_INTERP)
+    _compare(gpu, orc, ids)
+
+
+@pytest.mark.parametrize("kernel", [_lib.PBN_KERNEL_INTERP, _lib.PBN_KERNEL_COMPILED])
+def test_reach_reduced_plan(oracle_mod, kernel):
+    """The reachability rule (which also drops cycles that reach no meta node)
+    gives the same bits on the kept nodes and the same counts as the oracle's
+    unreduced simulation."""
+    from paper_1605_00854_gb300 import api
+    net = synth.random_pbn(4, 60, 0.01, k_choices=(1, 2, 3), sinks=0.2, protect=(0, 1, 2))
+    # two extra nodes in a cycle that no other node reads: Definition 1 keeps them
+    net.funcs.append([synth.Function(c=0.5, parents=[61, 5], tt=0b0110), synth.Function(c=0.5, parents=[61], tt=0b01)])
+    net.funcs.append([synth.Function(c=1.0, parents=[60, 7], tt=0b1000)])
+    net.n = 62
+    text = net.to_text()
+    meta = [0, 1, 2]
+    red, ids = api.Net.load(text).reduce(meta, rule=_lib.PBN_REDUCE_REACH)
+    _, ids_leaf = api.Net.load(text).reduce(meta)
+    assert len(ids) < len(ids_leaf)
+    plan = api.Plan(red)
+    orc = oracle_mod.simulate(text, 5, 0, 128, 600, meta_ids=meta, trace=True, nthreads=NCPU)
+    _compare(run(plan, seed=5, n_traj=128, n_steps=600, meta=meta, trace=True, kernel=kernel), orc, ids)
+
+
 @pytest.mark.parametrize("p", [0.0, 0.05, 0.3, 0.75])
 def test_perturbation_regimes(oracle_mod, p):
     """No perturbation, frequent, mostly and almost always perturbed steps."""
@@ -172,3 +214,16 @@ def test_status_and_argument_errors():
     api.simulate(plan, bufs, seed=1, n_steps=10, meta_ids=[0])
     torch.cuda.synchronize()
     assert int(bufs.status.item()) == 0
+
+
+def test_apoptosis_stand_in_against_oracle(oracle_mod):
+    """The apoptosis-shaped network (n = 96, 36 leaves) with a two-node meta-state:
+    bit-exact against the oracle."""
+    text = synth.apoptosis96().to_text()
+    meta = [1, 37]
+    plan, ids = plan_for(text, meta)
+    assert len(ids) == 60
+    orc = oracle_mod.simulate(text, 13, 0, 256, 2000, meta_ids=meta, count_from=100, nthreads=NCPU)
+    for kernel in (_lib.PBN_KERNEL_INTERP, _lib.PBN_KERNEL_COMPILED):
+        _compare(run(plan, seed=13, n_traj=256, n_steps=2000, meta=meta, count_from=100, kernel=kernel),
+                 orc, ids, trace=False)

@@ -112,12 +112,21 @@ def test_layout_is_a_valid_grouping(mode, max_inputs):
         assert len(members) <= 32
         if mode == 1:
             assert len(members) == 1
-    # the merge caps hold for every merged group
+    # the merge caps hold for every merged group; a lone multi-function node whose
+    # inputs exceed the cap is split (one table per function)
     D = imgdecode.decode(plan.image())
     for g, G in enumerate(D["groups"]):
         width = int((grp == g).sum())
         if width > 1:
-            assert G["q"] <= max_inputs
+            assert G["q"] <= max_inputs and G["l2w"] != imgdecode.SPLIT
+        if G["l2w"] == imgdecode.SPLIT:
+            (v,) = np.flatnonzero(grp == g).tolist()
+            fs = net.funcs[v]
+            assert G["q"] == len(fs) >= 2 and G["n_mul"] == 1
+            assert len(set(a for f in fs for a in f.parents)) > max_inputs
+        elif width == 1 and G["q"] > max_inputs:
+            assert len(net.funcs[int(np.flatnonzero(grp == g)[0])]) == 1
+    assert plan.info.n_split == sum(G["l2w"] == imgdecode.SPLIT for G in D["groups"])
 
 
 def test_plain_mode_unreduced_is_identity_layout():
@@ -202,21 +211,32 @@ def _eval_fun(f, state_bits):
     return (f.tt >> x) & 1
 
 
-@pytest.mark.parametrize("mode,seed", [(0, 2), (0, 7), (1, 2)])
-def test_merged_tables_equal_member_functions(mode, seed):
+@pytest.mark.parametrize("mode,seed,max_inputs", [(0, 2, 8), (0, 7, 8), (1, 2, 8), (0, 2, 3), (1, 7, 2)])
+def test_merged_tables_equal_member_functions(mode, seed, max_inputs):
     """Sec. 3.3: entry (c, x) of a group's merged table holds, in bit i, the output of
     member i's function selected by the mixed-radix choice c on the inputs packed in
-    x, for every c and x."""
+    x, for every c and x.  A split node's function j has its own inputs and table."""
     net = synth.paper100(seed=seed, n=60)
-    plan, ids = _plan(net.to_text(), mode=mode)
+    plan, ids = _plan(net.to_text(), mode=mode, max_inputs=max_inputs)
     D = imgdecode.decode(plan.image())
     pos = plan.layout()
     grp = plan.groups()
+    inv = {int(pos[v]): v for v in range(net.n) if pos[v] != 0xFFFFFFFF}
+    n_split = 0
     for g, G in enumerate(D["groups"]):
         members = sorted(np.flatnonzero(grp == g).tolist(), key=lambda v: pos[v])
         assert (pos[members[0]] & 31) == G["shift"]
+        if G["l2w"] == imgdecode.SPLIT:
+            n_split += 1
+            (v,) = members
+            assert D["multi"][G["mul_first"]]["radix"] == 1
+            for j, (in_chunk, k, tab_off) in enumerate(imgdecode.subs(D, g)):
+                f = net.funcs[v][j]
+                assert [inv[32 * row + bit] for row, bit in imgdecode.sub_inputs(D, in_chunk, k)] == list(f.parents)
+                for x in range(1 << k):
+                    assert imgdecode.sub_entry(D, tab_off, x) == (f.tt >> x) & 1
+            continue
         # recover input node ids from the records
-        inv = {int(pos[v]): v for v in range(net.n) if pos[v] != 0xFFFFFFFF}
         ins = [inv[32 * row + bit] for row, bit in imgdecode.inputs(D, g)]
         multi = [v for v in members if len(net.funcs[v]) >= 2]
         assert len(multi) == G["n_mul"]
@@ -238,6 +258,8 @@ def test_merged_tables_equal_member_functions(mode, seed):
                     f = net.funcs[v][js.get(v, 0)]
                     want |= _eval_fun(f, bits) << i
                 assert imgdecode.entry(D, g, (int(c) << G["q"]) | int(x)) == want
+    if max_inputs <= 3:
+        assert n_split > 0
 
 
 def test_thresholds_and_sel_slots_match_oracle(oracle_mod):
@@ -311,8 +333,9 @@ def test_estimate_rejects_bad_arguments():
 
 
 # ------------------------------------------------------------ compiled plans ----
-@pytest.mark.parametrize("flags", [0, 1])
-@pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half"])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+@pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half",
+                                   "split_small", "split_wide"])
 def test_generated_plan_kernels_compile(tmp_path, which, flags):
     """The source generated for a plan's own kernel compiles for sm_103a."""
     import shutil
@@ -328,10 +351,17 @@ def test_generated_plan_kernels_compile(tmp_path, which, flags):
         text, meta = synth.paper100(seed=9, n=70, p=0.0).to_text(), [0, 1]
     elif which == "p_half":
         text, meta = synth.paper100(seed=9, n=70, p=0.5).to_text(), [0, 1]
+    elif which.startswith("split"):
+        # split nodes: function tables as immediates (k <= 6) or looked up (k up to 10)
+        kmax = 5 if which == "split_small" else 10
+        text, meta = synth.random_pbn(5, 40, 1e-2, k_choices=tuple(range(1, kmax + 1))).to_text(), [0, 1]
     else:
         text, meta = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n", [0]
     red, _ = api.Net.load(text).reduce(meta)
-    plan = api.Plan(red, mode=1 if which.endswith("plain") else 0)
+    kw = dict(max_inputs=3) if which.startswith("split") else {}
+    plan = api.Plan(red, mode=1 if which.endswith("plain") else 0, **kw)
+    if which.startswith("split"):
+        assert plan.info.n_split > 0
     (tmp_path / "k.cu").write_text(plan.source(flags))
     shutil.copy(os.path.join(ROOT, "paper_1605_00854_gb300", "csrc", "pbn_device.cuh"), tmp_path)
     proc = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-c",
@@ -347,3 +377,74 @@ def test_large_plans_are_not_compiled():
     with pytest.raises(_lib.PbnError) as e:
         plan.source()
     assert e.value.status == -1
+
+
+# ------------------------------------------------------------ array loader ----
+def _funcs_of(net):
+    return [[(f.c, list(f.parents), f.tt) for f in fl] for fl in net.funcs]
+
+
+@pytest.mark.parametrize("which", ["tiny12", "paper100", "wide"])
+def test_load_arrays_equals_text(which):
+    """pbn_load_arrays builds the same network as pbn_load: equal shape and a
+    byte-identical plan image (reduced and grouped)."""
+    net = {"tiny12": synth.tiny12(1), "paper100": synth.paper100(seed=2),
+           "wide": synth.random_pbn(5, 40, 1e-2, k_choices=tuple(range(1, 11)))}[which]
+    a = api.Net.from_functions(net.n, net.p, _funcs_of(net))
+    t = api.Net.load(net.to_text())
+    ia, it = a.info(), t.info()
+    assert (ia.n, ia.n_functions, ia.n_multi, ia.P, ia.density) == (it.n, it.n_functions, it.n_multi, it.P, it.density)
+    ra, _ = a.reduce([0, 1])
+    rt, _ = t.reduce([0, 1])
+    assert np.array_equal(api.Plan(ra).image(), api.Plan(rt).image())
+    assert np.array_equal(api.Plan(a, mode=1).image(), api.Plan(t, mode=1).image())
+
+
+def test_load_arrays_rejects_bad_input():
+    good = [[(0.5, [1], 0b10), (0.5, [0, 1], 0b0110)], [(1.0, [], 1)]]
+    api.Net.from_functions(2, 0.01, good)
+    bad = [
+        (2, 0.01, [[(0.5, [1], 0b10), (0.4, [0, 1], 0b0110)], [(1.0, [], 1)]]),   # sum != 1
+        (2, 0.01, [[(1.0, [1, 1], 0)], [(1.0, [], 1)]]),                           # repeated parent
+        (2, 0.01, [[(1.0, [5], 0)], [(1.0, [], 1)]]),                              # parent >= n
+        (2, 0.01, [[(1.0, [1], 0b100)], [(1.0, [], 1)]]),                          # table wider than 2^k
+        (2, 0.01, [[(1.0, [1], 0)], []]),                                          # node without functions
+        (2, 1.0, [[(1.0, [1], 0)], [(1.0, [], 1)]]),                               # p = 1
+        (2, 0.01, [[(1.5, [1], 0)], [(1.0, [], 1)]]),                              # c > 1
+    ]
+    for n, p, funcs in bad:
+        with pytest.raises(_lib.PbnError) as e:
+            api.Net.from_functions(n, p, funcs)
+        assert e.value.status == _lib.PBN_EINVAL
+    with pytest.raises(_lib.PbnError):   # node index out of range
+        api.Net.from_arrays(2, 0.01, [0, 7], [1.0, 1.0], [0, 0], [], [0, 1])
+
+
+@pytest.mark.parametrize("seed", [1, 2, 5])
+def test_reduce_reach_rule_matches_oracle(oracle_mod, seed):
+    """PBN_REDUCE_REACH keeps exactly the oracle's reachability set; the default rule
+    keeps Definition 1's."""
+    net = synth.random_pbn(seed, 80, 0.01, k_choices=(1, 2, 3), sinks=0.25, protect=(0, 1, 2))
+    text = net.to_text()
+    meta = [0, 1, 2]
+    _, ids_reach = api.Net.load(text).reduce(meta, rule=_lib.PBN_REDUCE_REACH)
+    _, ids_leaf = api.Net.load(text).reduce(meta)
+    assert ids_reach.tolist() == np.flatnonzero(~oracle_mod.reach_removed(text, meta)).tolist()
+    assert ids_leaf.tolist() == np.flatnonzero(~oracle_mod.leaves(text, meta)).tolist()
+    assert set(ids_reach.tolist()) <= set(ids_leaf.tolist())
+    with pytest.raises(_lib.PbnError):
+        api.Net.load(text).reduce(meta, rule=7)
+
+
+# ------------------------------------------------------------ workload shapes ----
+def test_apoptosis_stand_in_has_the_papers_shape(oracle_mod):
+    """Sec. 4.3's apoptosis network: 96 nodes, 37.5% leaves, density 1.78.  The
+    stand-in's leaves (Definition 1, by the oracle) for every meta-state of the
+    workload are exactly its 36 non-core nodes."""
+    import bench
+    net, X, par, metas = bench.apoptosis_queries()
+    assert net.n == 96 and abs(net.density() - 1.78) < 0.005
+    for m in metas:
+        leaf = oracle_mod.leaves(net.to_text(), m)
+        assert leaf.sum() == 36 and not leaf[:60].any()
+    assert len(metas) == 7 and all(a in {x for f in net.funcs[X] for x in f.parents} for a in par)

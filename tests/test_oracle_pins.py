@@ -309,6 +309,53 @@ def test_leaves_hand_worked(oracle_mod):
     assert sorted(np.flatnonzero(leaf).tolist()) == [2, 3, 6]
 
 
+def test_reach_variant_hand_example(oracle_mod):
+    removed = oracle_mod.reach_removed(golden("leaves7.pbn"), [1])
+    assert sorted(np.flatnonzero(removed).tolist()) == [2, 3, 4, 5, 6]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_reach_variant_equals_graph_ancestors(oracle_mod, seed):
+    """The reachability variant keeps exactly the nodes of interest and their
+    ancestors in the parent -> child graph (networkx's ancestors on the same edges),
+    and keeps no more than Definition 1 does."""
+    nx = pytest.importorskip("networkx")
+    from paper_1605_00854_gb300 import synth
+    net = synth.random_pbn(seed, 50, 0.01, k_choices=(1, 2), sinks=0.3, protect=(0, 1))
+    G = nx.DiGraph()
+    G.add_nodes_from(range(net.n))
+    for u, fl in enumerate(net.funcs):
+        for f in fl:
+            for a in f.parents:
+                if a != u:
+                    G.add_edge(a, u)
+    keep = {0, 1} | nx.ancestors(G, 0) | nx.ancestors(G, 1)
+    removed = oracle_mod.reach_removed(net.to_text(), [0, 1])
+    assert set(np.flatnonzero(~removed).tolist()) == keep
+    leaf = oracle_mod.leaves(net.to_text(), [0, 1])
+    assert not np.any(~removed & leaf)      # kept by reachability => kept by Definition 1
+
+
+def test_reach_removed_tables_do_not_affect_kept_nodes(oracle_mod):
+    """Nodes that reach no node of interest cannot influence the kept nodes:
+    rewriting their truth tables keeps the kept nodes' trajectories identical."""
+    from paper_1605_00854_gb300 import synth
+    net = synth.random_pbn(4, 60, 0.01, k_choices=(1, 2, 3), sinks=0.2, protect=(0, 1, 2))
+    text = net.to_text()
+    meta = [0, 1, 2]
+    removed = oracle_mod.reach_removed(text, meta)
+    assert removed.sum() >= 5
+    base = oracle_mod.simulate(text, 3, 0, 4, 500, meta_ids=meta, trace=True)
+    rng = np.random.default_rng(1)
+    for i in np.flatnonzero(removed):
+        for f in net.funcs[i]:
+            f.tt = int(rng.integers(0, 1 << (1 << len(f.parents))))
+    alt = oracle_mod.simulate(net.to_text(), 3, 0, 4, 500, meta_ids=meta, trace=True)
+    keep = ~removed
+    assert np.array_equal(base["trace"][:, :, keep], alt["trace"][:, :, keep])
+    assert np.array_equal(base["counts"], alt["counts"])
+
+
 def test_leaf_tables_do_not_affect_retained_nodes(oracle_mod):
     """Sec. 3.1: removing leaves leaves every other node's simulation unchanged.
     Rewriting the truth tables of the oracle's leaves keeps the retained nodes'
