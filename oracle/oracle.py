@@ -65,6 +65,10 @@ def lib():
             L.orc_shape.restype = i32
             L.orc_transition_matrix.argtypes = [cp, vp]
             L.orc_transition_matrix.restype = i32
+            L.orc_simulate_sem.argtypes = L.orc_simulate.argtypes + [i32]
+            L.orc_simulate_sem.restype = i32
+            L.orc_transition_matrix_sem.argtypes = [cp, i32, vp]
+            L.orc_transition_matrix_sem.restype = i32
             L.orc_leaves.argtypes = [cp, vp, i32, vp]
             L.orc_leaves.restype = i32
             L.orc_reach.argtypes = [cp, vp, i32, vp]
@@ -98,8 +102,9 @@ def shape(text: str):
 
 def simulate(text: str, seed: int, traj_begin: int, n_traj: int, n_steps: int, *,
              meta_ids=(), meta_vals=None, step_begin: int = 0, count_from: int = 0,
-             init_states=None, trace: bool = False, nthreads: int = 1):
-    """Run the Eq. 1 simulator of the unreduced network.
+             init_states=None, trace: bool = False, nthreads: int = 1, semantics: int = 0):
+    """Run the Eq. 1 simulator of the unreduced network (semantics=1: the node-wise
+    variant, a flipped node negates and the others apply their functions).
 
     Returns dict(final=(n_traj, n) uint8, counts=(n_traj, 5) uint64 as
     [V, n00, n01, n10, n11], trace=(n_traj, n_steps, n) uint8 or None)."""
@@ -114,9 +119,9 @@ def simulate(text: str, seed: int, traj_begin: int, n_traj: int, n_steps: int, *
     final = np.zeros((n_traj, n), dtype=np.uint8)
     counts = np.zeros((n_traj, 5), dtype=np.uint64)
     tr = np.zeros((n_traj, n_steps, n), dtype=np.uint8) if trace else None
-    rc = lib().orc_simulate(text.encode(), seed, traj_begin, n_traj, step_begin, n_steps,
-                            count_from, _ptr(meta_ids), _ptr(meta_vals), len(meta_ids),
-                            _ptr(init), _ptr(final), _ptr(counts), _ptr(tr), nthreads)
+    rc = lib().orc_simulate_sem(text.encode(), seed, traj_begin, n_traj, step_begin, n_steps,
+                                count_from, _ptr(meta_ids), _ptr(meta_vals), len(meta_ids),
+                                _ptr(init), _ptr(final), _ptr(counts), _ptr(tr), nthreads, semantics)
     if rc:
         raise ValueError(f"orc_simulate failed (rc={rc})")
     return {"final": final, "counts": counts, "trace": tr}
@@ -146,13 +151,14 @@ def thresholds(text: str, node: int):
     return int(P.value), [int(t) for t in T[: l - 1]]
 
 
-def transition_matrix(text: str) -> np.ndarray:
-    """Exact 2^n x 2^n transition matrix (row = current state) for n <= 14."""
+def transition_matrix(text: str, semantics: int = 0) -> np.ndarray:
+    """Exact 2^n x 2^n transition matrix (row = current state) for n <= 14
+    (semantics=1: the node-wise variant)."""
     n = shape(text)[0]
     if n > 14:
         raise ValueError("transition matrix only for n <= 14")
     M = np.zeros((1 << n, 1 << n), dtype=np.float64)
-    rc = lib().orc_transition_matrix(text.encode(), _ptr(M))
+    rc = lib().orc_transition_matrix_sem(text.encode(), semantics, _ptr(M))
     if rc:
         raise ValueError(f"orc_transition_matrix failed (rc={rc})")
     return M

@@ -12,6 +12,9 @@
  *   - one step of the perturbed PBN, Eq. 1: draw gamma_i ~ Bernoulli(p)
  *     for every node; if gamma != 0 the next state is s XOR gamma, otherwise
  *     every node applies a predictor function chosen by C_i             [Eq. 1]
+ *   - the node-wise variant (semantics 1): node i takes NOT s_i if gamma_i = 1
+ *     and its selected predictor function's value otherwise, whatever the
+ *     other nodes draw                                 [Sec. 2.1, node-wise reading]
  *   - the meta-state visit / transition counts of the two-state Markov
  *     chain estimator, taken over a counting window                     [Sec. 4.2]
  *   - the exact transition matrix of the ergodic DTMC for tiny n          [Sec. 2.1]
@@ -355,6 +358,7 @@ typedef struct {
     uint64_t *counts;
     uint8_t *trace;
     uint64_t t_lo, t_hi; /* local trajectory range of this worker */
+    int per_node;        /* 0: Eq. 1; 1: node-wise flips */
     int rc;
 } sim_job;
 
@@ -384,7 +388,15 @@ static void *sim_worker(void *arg) {
         for (uint64_t k = 0; k < jb->n_steps; ++k) {
             uint64_t t = jb->step_begin + k;
             /* Eq. 1: perturb if any gamma_i is set, else apply selected functions. */
-            if (draw_pert(cx, jb->seed, traj, t, gam)) {
+            if (jb->per_node) {
+                /* node-wise: a flipped node negates, every other node applies its
+                 * selected function to the old state */
+                draw_pert(cx, jb->seed, traj, t, gam);
+                draw_sel(cx, jb->seed, traj, t, ch);
+                for (int i = 0; i < n; ++i)
+                    s2[i] = gam[i] ? (uint8_t)(s[i] ^ 1u) : (uint8_t)eval_fun(&g->node[i].f[ch[i]], s);
+                memcpy(s, s2, (size_t)n);
+            } else if (draw_pert(cx, jb->seed, traj, t, gam)) {
                 for (int i = 0; i < n; ++i) s[i] ^= gam[i];
             } else {
                 draw_sel(cx, jb->seed, traj, t, ch);
@@ -410,11 +422,28 @@ out:
  * NULL for the keyed initial state (then step_begin must be 0).  counts gets
  * [V, n00, n01, n10, n11] per trajectory over states with index >= count_from.
  * trace (optional) gets the state after every step: n_traj x n_steps x n. */
+int orc_simulate_sem(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
+                     uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
+                     const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
+                     const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
+                     uint8_t *trace, int nthreads, int semantics);
+
 int orc_simulate(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
                  uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
                  const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
                  const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
                  uint8_t *trace, int nthreads) {
+    return orc_simulate_sem(text, seed, traj_begin, n_traj, step_begin, n_steps, count_from, meta_ids,
+                            meta_vals, n_meta, init_states, final_states, counts, trace, nthreads, 0);
+}
+
+/* As orc_simulate; semantics 0 = Eq. 1, 1 = node-wise flips. */
+int orc_simulate_sem(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
+                     uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
+                     const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
+                     const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
+                     uint8_t *trace, int nthreads, int semantics) {
+    if (semantics != 0 && semantics != 1) return ORC_EINVAL;
     onet *g = NULL;
     int rc = parse_net(text, &g);
     if (rc) return rc;
@@ -437,6 +466,7 @@ int orc_simulate(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t 
         jb->meta_ids = meta_ids; jb->meta_vals = meta_vals; jb->n_meta = n_meta;
         jb->init_states = init_states; jb->final_states = final_states;
         jb->counts = counts; jb->trace = trace;
+        jb->per_node = semantics;
         jb->t_lo = n_traj * (uint64_t)w / (uint64_t)nthreads;
         jb->t_hi = n_traj * (uint64_t)(w + 1) / (uint64_t)nthreads;
     }
@@ -517,7 +547,14 @@ int orc_shape(const char *text, int *n, int *n_fun, long *sum_parents, double *p
 /*              + (1-p')^n prod_i q_i(s, s'_i),  q_i(s,1) = sum_j c'_j f_j(s) */
 /* States are indexed by sum_i s_i 2^i.  M is row-major, 2^n x 2^n.           */
 /* ------------------------------------------------------------------------ */
-int orc_transition_matrix(const char *text, double *M) {
+int orc_transition_matrix_sem(const char *text, int semantics, double *M);
+
+int orc_transition_matrix(const char *text, double *M) { return orc_transition_matrix_sem(text, 0, M); }
+
+/* Node-wise variant (semantics 1): the nodes move independently given s,
+ *   Pr(s -> s') = prod_i [ p' [s'_i != s_i] + (1-p') q_i(s, s'_i) ]. */
+int orc_transition_matrix_sem(const char *text, int semantics, double *M) {
+    if (semantics != 0 && semantics != 1) return ORC_EINVAL;
     onet *g = NULL;
     int rc = parse_net(text, &g);
     if (rc) return rc;
@@ -555,8 +592,12 @@ int orc_transition_matrix(const char *text, double *M) {
             }
             q1[i] = q;
         }
+        if (semantics == 1) {
+            /* node i is 1 next with probability p' [s_i = 0] + (1-p') q_i(s, 1) */
+            for (int i = 0; i < n; ++i) q1[i] = pe * (double)(st[i] ^ 1u) + (1.0 - pe) * q1[i];
+        }
         /* product distribution over s' built one node at a time */
-        row[0] = pw[0];
+        row[0] = semantics == 1 ? 1.0 : pw[0];
         size_t len = 1;
         for (int i = 0; i < n; ++i) {
             for (size_t a = 0; a < len; ++a) {
@@ -567,7 +608,7 @@ int orc_transition_matrix(const char *text, double *M) {
             len <<= 1;
         }
         for (size_t s2 = 0; s2 < S; ++s2) {
-            if (s2 != s) row[s2] += pw[__builtin_popcountll((unsigned long long)(s ^ s2))];
+            if (semantics == 0 && s2 != s) row[s2] += pw[__builtin_popcountll((unsigned long long)(s ^ s2))];
             M[s * S + s2] = row[s2];
         }
     }

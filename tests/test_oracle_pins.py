@@ -260,6 +260,60 @@ def test_one_step_empirical_law(oracle_mod):
             assert abs((idx == t).mean() - q) <= 5 * sd + 1e-12, (s, t)
 
 
+# ------------------------------------------------ node-wise semantics variant ----
+def _golden_matrix_pernode():
+    rows = [l.split() for l in golden("tiny2_matrix_pernode.txt").splitlines()
+            if l.strip() and not l.startswith("#")]
+    return [[Fraction(int(v), 1024) for v in r] for r in rows]
+
+
+def test_pernode_matrix_hand_worked(oracle_mod):
+    """Node-wise reading of Sec. 2.1: the exact matrix equals the hand-worked one."""
+    M = oracle_mod.transition_matrix(golden("tiny2.pbn"), semantics=1)
+    want = _golden_matrix_pernode()
+    for s in range(4):
+        for t in range(4):
+            assert M[s, t] == float(want[s][t]), (s, t)
+
+
+def test_pernode_one_step_empirical_law(oracle_mod):
+    """The node-wise simulator's one-step frequencies follow the hand-worked rows."""
+    text = golden("tiny2.pbn")
+    Q = _golden_matrix_pernode()
+    T = 20000
+    for s in range(4):
+        init = np.array([[s & 1, (s >> 1) & 1]] * T, dtype=np.uint8)
+        out = oracle_mod.simulate(text, 4321 + s, 0, T, 1, init_states=init, semantics=1)["final"]
+        idx = out[:, 0].astype(int) + 2 * out[:, 1].astype(int)
+        for t in range(4):
+            q = float(Q[s][t])
+            sd = math.sqrt(q * (1 - q) / T)
+            assert abs((idx == t).mean() - q) <= 5 * sd + 1e-12, (s, t)
+
+
+def test_pernode_equals_global_when_no_flip_and_single_node(oracle_mod):
+    """Two special cases fix the node-wise variant against Eq. 1: with p = 0 both
+    readings are the same chain, and for a single node they coincide for every p
+    (a flip of the only node is the whole perturbation vector)."""
+    from paper_1605_00854_gb300 import synth
+    text = synth.tiny12(2).to_text().replace("pbn 12 " + (0.01).hex(), "pbn 12 0x0p+0")
+    assert "pbn 12 0x0p+0" in text
+    a = oracle_mod.simulate(text, 5, 0, 8, 300, trace=True)
+    b = oracle_mod.simulate(text, 5, 0, 8, 300, trace=True, semantics=1)
+    assert np.array_equal(a["trace"], b["trace"])
+    one = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n"
+    assert np.array_equal(oracle_mod.transition_matrix(one), oracle_mod.transition_matrix(one, semantics=1))
+    a = oracle_mod.simulate(one, 6, 0, 4, 500, trace=True)
+    b = oracle_mod.simulate(one, 6, 0, 4, 500, trace=True, semantics=1)
+    assert np.array_equal(a["trace"], b["trace"])
+
+
+def test_pernode_rows_are_distributions(oracle_mod):
+    from paper_1605_00854_gb300 import synth
+    M = oracle_mod.transition_matrix(synth.tiny12(1).to_text(), semantics=1)
+    assert np.allclose(M.sum(axis=1), 1.0, atol=1e-12) and (M >= 0).all()
+
+
 # ---------------------------------------------------------------- counting ----
 def _recount(trace_states, s_start, meta, start_index, count_from):
     """Brute-force counts from a list of states s(start_index), s(start_index+1)..."""
