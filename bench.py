@@ -154,6 +154,19 @@ def oracle_rate(text: str, n: int, target_s: float, meta=META):
     return n * cores * steps / dt, cores, f"{cores} trajectories x {steps} steps of the same network (unreduced, ungrouped Eq. 1 simulator)", dt
 
 
+def oracle_rate_single(text: str, n: int, target_s: float, meta=META):
+    """The same oracle on one host core (one trajectory)."""
+    from oracle import oracle
+    steps = 200
+    t0 = time.perf_counter()
+    oracle.simulate(text, SEED, 0, 1, steps, meta_ids=meta, nthreads=1)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    steps = max(200, int(steps * target_s / dt))
+    t0 = time.perf_counter()
+    oracle.simulate(text, SEED, 0, 1, steps, meta_ids=meta, nthreads=1)
+    return n * steps / (time.perf_counter() - t0), steps
+
+
 def workload_network(args):
     """(network, meta nodes, description) of the single-network workloads."""
     if args.workload == "scalefree2000":
@@ -183,6 +196,8 @@ def run_ours(args):
     args.n_traj, args.n_steps = T, S
     lanes = 0
     tune_s = 0.0
+    if args.compile_flags is not None or args.max_inputs:
+        args.autotune = False  # a pinned configuration (for profiling runs)
     if args.autotune:
         # group size, kernel and lanes per trajectory picked by timing short passes
         t0 = time.perf_counter()
@@ -192,7 +207,8 @@ def run_ours(args):
         budget, cflags = choice.smem_budget, choice.compile_flags
         args.kernel = "compiled" if choice.kernel == _lib.PBN_KERNEL_COMPILED else "interpreter"
     else:
-        max_inputs, budget, cflags = 8, 0, 0
+        max_inputs, budget, cflags = args.max_inputs or 8, 0, args.compile_flags or 0
+        lanes = args.lanes
     t_prep = time.perf_counter()
     red, retained = api.Net.load(text).reduce(meta)
     plan = api.Plan(red, max_inputs=max_inputs, smem_budget=budget) if budget else api.Plan(red, max_inputs=max_inputs)
@@ -318,6 +334,14 @@ def run_ours(args):
         achieved = ops * T * S / kernel_s / 1e12
         peak = sms * 128 * sm_max * 1e6 / 1e12
         clk_sum = clk.summary()
+        # DRAM bytes per launch from the ncu capture of this kernel (a 2,000-step launch of
+        # the same trajectories: the traffic is the state, counts and plan image, which
+        # does not grow with the number of steps)
+        traffic, traffic_note = None, None
+        if (args.workload == "paper100" and args.kernel == "compiled" and cflags == _lib.PBN_COMPILE_INTERLEAVED
+                and max_inputs == 12 and T == 1 << 16):
+            traffic = 2.988e6
+            traffic_note = "ncu dram__bytes_read+write of this kernel, profiles/pbn_plan_kernel_paper100_compiled.md"
         pooled = bufs.pooled.cpu().numpy().view(np.uint64)
         est = api.estimate(pooled, T, 0.01, 0.95)
         out = {
@@ -338,7 +362,7 @@ def run_ours(args):
             "traj_steps_per_s": T * S * ws * args.steps / total,
             "retained_node_updates_per_s": int(info.n_retained) * T * S * ws * args.steps / total,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "ops_per_traj_step": ops,
                          "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz ({src} max SM clock)"},
             "e2e": {"value": e2e_value, "unit": "node-updates/s",
@@ -446,7 +470,8 @@ def run_serve(args):
             "latency": lat, "queries_per_s": len(srv.done) / makespan,
             "node_updates_per_s": srv.node_updates / makespan, "makespan_s": makespan,
             "completed": len(srv.done), "rejected": len(srv.rejected), "failed": len(srv.failed),
-            "unfinished": n_q - len(srv.done) - len(srv.rejected) - len(srv.failed)}
+            "unfinished": n_q - len(srv.done) - len(srv.rejected) - len(srv.failed),
+            "rounds": srv.stats, "mean_prep_s": float(np.mean([r.prep_s for r in srv.done])) if srv.done else None}
     print(json.dumps(line), flush=True)
 
 
@@ -490,7 +515,7 @@ def run_apoptosis(args):
                        "chunk_steps": args.apo_chunk, "r": 1e-5, "s": 0.95, "eps": 1e-3},
             "queries": [{"meta": metas[r.qid], "pi": r.pi, "n_star": r.n_star, "samples": r.L, "m_star": r.m_star,
                          "steps": r.steps, "rounds": r.rounds, "latency_s": r.latency} for r in res],
-            "total_samples": samples, "node_updates_per_s": srv.node_updates / wall,
+            "total_samples": samples, "node_updates_per_s": srv.node_updates / wall, "rounds": srv.stats,
             "completed": len(res), "failed": len(srv.failed),
             "paper_context": "Sec. 4.3: 7 probabilities, 50-452 million samples each, about 10 minutes "
                              "in total for the structure-based method on the paper's CPU (other hardware)"}
@@ -510,6 +535,9 @@ def main():
     ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use group size 8 and the default launch shape instead of the autotuner")
+    ap.add_argument("--max-inputs", type=int, default=0, help="pin the group input cap (skips the autotuner)")
+    ap.add_argument("--compile-flags", type=int, default=None, help="pin pbn_plan_compile flags (skips the autotuner)")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per trajectory when the autotuner is skipped")
     ap.add_argument("--workload", default="paper100",
                     choices=["paper100", "scalefree2000", "batch", "serve", "apoptosis"])
     ap.add_argument("--apo-traj", type=int, default=1 << 14)
@@ -566,8 +594,10 @@ def main():
     if rank == 0 and out is not None:
         if not args.no_cpu_baseline and ws == 1:
             rate, cores, sample, dt = oracle_rate(text, n, args.oracle_seconds)
+            r1, s1 = oracle_rate_single(text, n, min(3.0, args.oracle_seconds / 4))
             out["cpu_baseline"] = {"value": rate, "unit": "node-updates/s", "cores": cores,
-                                   "kind": "oracle", "sample": sample, "seconds": round(dt, 2)}
+                                   "kind": "oracle", "sample": sample, "seconds": round(dt, 2),
+                                   "single_core": {"value": r1, "sample": f"1 trajectory x {s1} steps"}}
         print(json.dumps(out), flush=True)
 
 

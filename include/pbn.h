@@ -144,11 +144,19 @@ int pbn_reduce_rule(const pbn_net* net, const uint32_t* interest, uint32_t n_int
 #define PBN_PLAN_GROUPED 0u /* node grouping of Sec. 3.3 (Eq. 2, Algorithms 3-4) */
 #define PBN_PLAN_PLAIN 1u   /* one node per group: the unmerged per-node method */
 
+/* Perturbation semantics of a plan.  PBN_SEM_EQ1 is Eq. 1: if any node (leaves
+ * included) is perturbed, s(t+1) = s(t) XOR gamma and no function is applied.
+ * PBN_SEM_NODEWISE is the node-by-node reading of Sec. 2.1's description: a
+ * perturbed node takes NOT s_i, every other node applies its selected function
+ * to s(t), in every step.  Both consume the same keyed draws. */
+#define PBN_SEM_EQ1 0u
+#define PBN_SEM_NODEWISE 1u
+
 typedef struct {
     uint32_t mode;          /* PBN_PLAN_GROUPED or PBN_PLAN_PLAIN */
     uint32_t max_inputs;    /* max distinct input nodes of a merged group (1..24, default 8) */
     uint32_t max_width;     /* max nodes per group (1..32, default 32) */
-    uint32_t reserved;
+    uint32_t semantics;     /* PBN_SEM_EQ1 (default) or PBN_SEM_NODEWISE */
     double theta;           /* memory limit of Sec. 3.3 on sum over groups of the
                                number of combined functions (default 65536) */
     uint64_t smem_budget;   /* bytes of plan image that may be staged into shared
@@ -196,7 +204,7 @@ typedef struct {
     uint32_t n_split;        /* groups that are one multi-function node whose inputs exceed
                                 max_inputs: each of its functions keeps its own table over
                                 its own inputs, and the node's choice selects the output */
-    uint32_t reserved;
+    uint32_t semantics;      /* PBN_SEM_EQ1 or PBN_SEM_NODEWISE */
     double ops_per_step;     /* algorithmic 32-bit integer operations of one trajectory-step:
                                 Philox blocks at 56 ops (9 rounds of 2 mul.hi, 2 mul.lo,
                                 2 xor3), 12 per bit-sliced level pair, the expected number of
@@ -249,7 +257,7 @@ typedef struct {
     void* d_status;  /* device uint32 or NULL: ORed with PBN_DEV_* bits on error */
     void* d_trace;   /* device uint64 [n_steps][state_words][n_traj] or NULL: the
                         state after every step (for checking; slows the kernel) */
-    uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8 */
+    uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8, 16, 32 */
     uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj */
     uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP or PBN_KERNEL_COMPILED */
     uint32_t reserved;

@@ -25,6 +25,8 @@ PBN_EDEVICE = -7
 PBN_REDUCE_LEAVES = 0
 PBN_REDUCE_REACH = 1
 PBN_PLAN_GROUPED = 0
+PBN_SEM_EQ1 = 0
+PBN_SEM_NODEWISE = 1
 PBN_PLAN_PLAIN = 1
 PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
@@ -51,7 +53,7 @@ class NetDesc(ctypes.Structure):
 
 
 class GroupParams(ctypes.Structure):
-    _fields_ = [("mode", u32), ("max_inputs", u32), ("max_width", u32), ("reserved", u32),
+    _fields_ = [("mode", u32), ("max_inputs", u32), ("max_width", u32), ("semantics", u32),
                 ("theta", f64), ("smem_budget", u64)]
 
 
@@ -61,7 +63,7 @@ class PlanInfo(ctypes.Structure):
                 ("m_found", u32), ("sum_weights", u64), ("table_bytes", u64),
                 ("image_bytes", u64), ("stage_bytes", u64), ("tables_in_smem", u32),
                 ("total_inputs", u32), ("n_multi", u32), ("total_thresholds", u32),
-                ("n_split", u32), ("reserved", u32), ("ops_per_step", f64)]
+                ("n_split", u32), ("semantics", u32), ("ops_per_step", f64)]
 
 
 class BatchNet(ctypes.Structure):

@@ -4,7 +4,7 @@ For one network it builds plans with several caps on the inputs of a merged grou
 (the group size of Sec. 3.3; larger groups mean fewer table lookups but bigger
 tables), and for each plan times short launches of the candidate kernels on the
 caller's trajectory count: the compiled plan (when the plan can be compiled, with
-each code-shape flag) and the interpreter with 1, 2, 4 or 8 lanes per trajectory,
+each code-shape flag) and the interpreter with 1 to 32 lanes per trajectory,
 with the tables in shared or in global memory.  The fastest configuration is returned and cached by the shape of
 the problem.  For batches it times CUDA-graph replays of the persistent launch with
 several steps per launch.
@@ -54,7 +54,7 @@ def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
 
 
 def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 1,
-                 max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8),
+                 max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8, 16, 32),
                  compile_flags_options=(0, _lib.PBN_COMPILE_INTERLEAVED),
                  try_compiled: bool = True, cache_file: str | None = None, log=None) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
@@ -79,18 +79,27 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
     n = net.info().n
     best = None
     for mi in max_inputs_options:
-        for budget in (0, 1024):
+        default_staged = None
+        for budget in (0, 1024, 220 * 1024):
             try:
                 plan = api.Plan(red, max_inputs=mi, smem_budget=budget) if budget else api.Plan(red, max_inputs=mi)
             except _lib.PbnError:
                 continue
-            if budget and plan.info.tables_in_smem:
+            if budget == 0:
+                default_staged = bool(plan.info.tables_in_smem)
+            # the small budget moves the tables to global memory, the large one into
+            # shared memory: skip them when they give the default plan again
+            if budget == 1024 and plan.info.tables_in_smem:
+                continue
+            if budget > 1024 and (default_staged or not plan.info.tables_in_smem):
                 continue
             bufs = api.alloc_buffers(plan, n_traj)
             cands = []
             if try_compiled and budget == 0:
                 cands += [(_lib.PBN_KERNEL_COMPILED, 1, f) for f in compile_flags_options]
-            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0) for lg in lanes_options]
+            # at most about one lane per state word
+            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0) for lg in lanes_options
+                      if lg == 1 or lg <= 2 * plan.info.state_words]
             for kern, lg, cf in cands:
                 try:
                     if kern == _lib.PBN_KERNEL_COMPILED:

@@ -827,6 +827,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.n_multi = (uint32_t)mrec.size();
     H.n_sel = (uint32_t)selblk.size();
     H.P = (uint32_t)pbn::pert_threshold(g.p);
+    H.semantics = prm.semantics;
     size_t off = align16(sizeof(pbn_img_header));
     H.off_words = (uint32_t)off; off = align16(off + words.size() * 4);
     H.off_groups = (uint32_t)off; off = align16(off + grec.size() * sizeof(pbn_img_group));
@@ -883,6 +884,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     I.total_inputs = (uint32_t)total_inputs;
     I.n_multi = (uint32_t)mrec.size();
     I.n_split = n_split;
+    I.semantics = prm.semantics;
     I.total_thresholds = (uint32_t)thr.size();
     /* algorithmic work of one trajectory-step (the roofline's per-unit figure) */
     {
@@ -924,7 +926,8 @@ extern "C" int pbn_group(const pbn_net* net, const pbn_group_params* prm_in, pbn
     if (prm.mode != PBN_PLAN_GROUPED && prm.mode != PBN_PLAN_PLAIN)
         return fail(PBN_EINVAL, "pbn_group: unknown mode %u", prm.mode);
     if (prm.max_inputs < 1 || prm.max_inputs > 24 || prm.max_width < 1 || prm.max_width > 32 ||
-        !(prm.theta >= 1.0) || (prm.smem_budget && prm.smem_budget < 1024))
+        !(prm.theta >= 1.0) || (prm.smem_budget && prm.smem_budget < 1024) ||
+        (prm.semantics != PBN_SEM_EQ1 && prm.semantics != PBN_SEM_NODEWISE))
         return fail(PBN_EINVAL, "pbn_group: parameter out of range");
     try {
         pbn_plan* plan = new pbn_plan();

@@ -57,7 +57,8 @@ typedef struct {
     uint32_t image_bytes;
     uint32_t stage_bytes;
     uint32_t tables_in_smem;
-} pbn_img_header; /* 92 bytes */
+    uint32_t semantics;  /* PBN_SEM_EQ1 or PBN_SEM_NODEWISE */
+} pbn_img_header; /* 96 bytes */
 
 /* A group record with l2w == PBN_IMG_SPLIT is a split node: one multi-function node
  * whose q functions each keep their own table of 2^k one-bit entries over their own

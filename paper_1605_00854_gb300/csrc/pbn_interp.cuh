@@ -19,6 +19,9 @@
  *      group's new bits, ORed into the next state at the group's offset (cum).
  *      A split node evaluates only its selected function's own table.
  *   3. the meta-state indicator z of the new state updates V, n01, n10, n11.
+ * With node-wise semantics (P.per_node) every step runs 2 and then 1, and a
+ * perturbed retained node takes the negation of its old value instead of its
+ * function's output.
  */
 #ifndef PBN_INTERP_CUH
 #define PBN_INTERP_CUH
@@ -137,49 +140,49 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
             const uint64_t t = P.step_begin + k;
             const pbn_philox_step ps = pbn_philox_begin(P, traj, t);
             uint32_t* Sc = S0 + cur * bufstride;
+            uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
 
             /* ---- 1. perturbation: bit-sliced u < P, most significant level first,
-             *         stopping once every lane of the word is decided ---- */
-            uint32_t any_l = 0;
-            if (P.P != 0u) {
-                for (uint32_t w = lane; w < P.W; w += LG) {
-                    const uint64_t valid = (w == P.W - 1) ? last_lanes : ~0ull;
-                    uint32_t und_lo = (uint32_t)valid, und_hi = (uint32_t)(valid >> 32);
-                    uint32_t pert_lo = 0, pert_hi = 0;
-                    uint32_t pp = P.P; /* level 2h uses bit 31 of pp, level 2h+1 bit 30 */
-                    for (uint32_t h = 0; h < P.hmax && (und_lo | und_hi); ++h) {
-                        const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_PERT << 28) | (w << 4) | h);
-                        const uint32_t m0 = (uint32_t)((int32_t)pp >> 31);
-                        const uint32_t m1 = (uint32_t)((int32_t)(pp << 1) >> 31);
-                        pp <<= 2;
-                        pert_lo |= und_lo & ~x.x & m0;
-                        pert_hi |= und_hi & ~x.y & m0;
-                        und_lo &= ~(x.x ^ m0);
-                        und_hi &= ~(x.y ^ m0);
-                        pert_lo |= und_lo & ~x.z & m1;
-                        pert_hi |= und_hi & ~x.w & m1;
-                        und_lo &= ~(x.z ^ m1);
-                        und_hi &= ~(x.w ^ m1);
-                    }
-                    if (pert_lo | pert_hi) {
-                        any_l = 1u;
-                        uint64_t f = ((((uint64_t)pert_hi) << 32) | pert_lo) & RET[w];
-                        while (f) {
-                            const uint32_t b = __ffsll((long long)f) - 1;
-                            f &= f - 1;
-                            const uint32_t ps_ = POS[64 * w + b];
-                            xor_bit<LG>(&Sc[ps_ >> 5], 1u << (ps_ & 31));
+             *         stopping once every lane of the word is decided; flip(pos) is
+             *         called for every perturbed retained node ---- */
+            auto perturb = [&](auto&& flip) -> uint32_t {
+                uint32_t any_l = 0;
+                if (P.P != 0u) {
+                    for (uint32_t w = lane; w < P.W; w += LG) {
+                        const uint64_t valid = (w == P.W - 1) ? last_lanes : ~0ull;
+                        uint32_t und_lo = (uint32_t)valid, und_hi = (uint32_t)(valid >> 32);
+                        uint32_t pert_lo = 0, pert_hi = 0;
+                        uint32_t pp = P.P; /* level 2h uses bit 31 of pp, level 2h+1 bit 30 */
+                        for (uint32_t h = 0; h < P.hmax && (und_lo | und_hi); ++h) {
+                            const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_PERT << 28) | (w << 4) | h);
+                            const uint32_t m0 = (uint32_t)((int32_t)pp >> 31);
+                            const uint32_t m1 = (uint32_t)((int32_t)(pp << 1) >> 31);
+                            pp <<= 2;
+                            pert_lo |= und_lo & ~x.x & m0;
+                            pert_hi |= und_hi & ~x.y & m0;
+                            und_lo &= ~(x.x ^ m0);
+                            und_hi &= ~(x.y ^ m0);
+                            pert_lo |= und_lo & ~x.z & m1;
+                            pert_hi |= und_hi & ~x.w & m1;
+                            und_lo &= ~(x.z ^ m1);
+                            und_hi &= ~(x.w ^ m1);
+                        }
+                        if (pert_lo | pert_hi) {
+                            any_l = 1u;
+                            uint64_t f = ((((uint64_t)pert_hi) << 32) | pert_lo) & RET[w];
+                            while (f) {
+                                const uint32_t b = __ffsll((long long)f) - 1;
+                                f &= f - 1;
+                                flip(POS[64 * w + b]);
+                            }
                         }
                     }
                 }
-            }
-            uint32_t any = any_l;
-            if (LG > 1) {
-                group_sync<LG>();
-                any = (__ballot_sync(group_mask<LG>(), any_l) & group_mask<LG>()) ? 1u : 0u;
-            }
+                return any_l;
+            };
 
-            if (!any) {
+            /* ---- 2. selection and merged-table evaluation: Sn from Sc ---- */
+            auto select_eval = [&]() {
                 /* ---- 2a. selection: draw the SEL blocks, turn each slot's uniform into
                  *          the node's 0-based choice (integer thresholds), one byte each ---- */
                 auto choices = [&](const uint4 x, uint32_t i) -> uint32_t {
@@ -213,8 +216,6 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                 group_sync<LG>();
                 /* ---- 2b. merged-table evaluation ---- */
                 const uint8_t* Sc8 = reinterpret_cast<const uint8_t*>(Sc);
-                uint32_t* Sn = S0 + (cur ^ 1u) * bufstride;
-                /* new bits of group gi, already at their place in the output word */
                 /* input pattern of q inputs from their chunked records */
                 auto gather = [&](const uint4* ch, uint32_t q) -> uint32_t {
                     uint32_t x = 0;
@@ -275,6 +276,31 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                         atomicOr(&Sn[go >> 20], group_bits(go & 0xFFFFFu));
                     }
                 }
+                group_sync<LG>();
+            };
+
+            if (!P.per_node) {
+                /* Eq. 1: any perturbed node (leaves included) flips the perturbed
+                 * retained nodes and no function is applied */
+                const uint32_t any_l = perturb([&](uint32_t ps_) { xor_bit<LG>(&Sc[ps_ >> 5], 1u << (ps_ & 31)); });
+                uint32_t any = any_l;
+                if (LG > 1) {
+                    group_sync<LG>();
+                    any = (__ballot_sync(group_mask<LG>(), any_l) & group_mask<LG>()) ? 1u : 0u;
+                }
+                if (!any) {
+                    select_eval();
+                    cur ^= 1u;
+                }
+            } else {
+                /* node-wise: every node applies its function, then each perturbed
+                 * node takes the negation of its old value instead */
+                select_eval();
+                perturb([&](uint32_t ps_) {
+                    uint32_t* wn = &Sn[ps_ >> 5];
+                    const uint32_t m = ~(*wn ^ Sc[ps_ >> 5]) & (1u << (ps_ & 31));
+                    if (m) xor_bit<LG>(wn, m);
+                });
                 group_sync<LG>();
                 cur ^= 1u;
             }

@@ -215,6 +215,14 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
          "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
          "      uint32_t any = 0;\n";
     const bool interleave = (flags & PBN_COMPILE_INTERLEAVED) != 0;
+    /* node-wise semantics: perturbed nodes are collected in masks g<row>, every
+     * step evaluates the functions, and the masked bits take NOT s */
+    const bool nodewise = H.semantics == PBN_SEM_NODEWISE;
+    if (nodewise) {
+        o << "      uint32_t";
+        for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "g" << r << " = 0";
+        o << ";\n";
+    }
     auto emit_sel_draws = [&](const char* ind) {
         for (uint32_t i = 0; i < H.n_sel; ++i)
             o << ind << "const uint4 U" << i << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
@@ -235,7 +243,8 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             for (uint32_t b = 0; b < 32; ++b) {
                 if (!((rm >> b) & 1u)) continue;
                 const uint32_t ps = pos[64 * w + 32 * half + b];
-                o << "            case " << b << ": s" << (ps >> 5) << " ^= " << hex32(1u << (ps & 31)) << "; break;\n";
+                o << "            case " << b << ": " << (nodewise ? "g" : "s") << (ps >> 5) << (nodewise ? " |= " : " ^= ")
+                  << hex32(1u << (ps & 31)) << "; break;\n";
             }
             o << "          } } }\n";
         }
@@ -322,7 +331,7 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         }
     }
     /* 2. selection draws and merged-table evaluation */
-    o << "      if (!any) {\n";
+    o << (nodewise ? "      {\n" : "      if (!any) {\n");
     if (!interleave) emit_sel_draws("        ");
     for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
     for (uint32_t r = 0; r < H.W32; ++r) {
@@ -420,7 +429,10 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
         }
     }
-    for (uint32_t r = 0; r < H.W32; ++r) o << "        s" << r << " = n" << r << ";\n";
+    for (uint32_t r = 0; r < H.W32; ++r) {
+        if (nodewise) o << "        s" << r << " = (n" << r << " & ~g" << r << ") | (~s" << r << " & g" << r << ");\n";
+        else o << "        s" << r << " = n" << r << ";\n";
+    }
     o << "      }\n";
     /* 3. counts */
     o << "      { const uint32_t z = " << z << ";\n"

@@ -65,7 +65,7 @@ struct SimParams {
     uint32_t hmax;             /* level pairs that can still decide a perturbation */
     uint32_t n, W, W32, n_sel, P;
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret, off_pos,
-        off_tables, n_groups, off_subs;
+        off_tables, n_groups, off_subs, per_node;
     uint32_t n_meta_rows;
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
@@ -240,6 +240,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.off_selslot = H.off_selslot;
     P.off_gorder = H.off_gorder;
     P.off_subs = H.off_subs;
+    P.per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
     P.n_groups = H.n_groups;
     P.off_thr = H.off_thr;
     P.off_inputs = H.off_inputs;
@@ -307,7 +308,8 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
         while (LG < 8 && slots * LG < 256 && H.W32 >= 4 * LG) LG *= 2;
         if (LG > 1 && slots * LG < 512 && LG < 8 && H.W32 >= 4 * LG) LG *= 2;
     }
-    if (LG != 1 && LG != 2 && LG != 4 && LG != 8) return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4 or 8");
+    if (LG == 0 || LG > 32 || (LG & (LG - 1)))
+        return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4, 8, 16 or 32");
     if (fixed + per_traj * (32 / LG) > smem_lim)
         return fail(PBN_ETOOBIG, "pbn_simulate: plan needs %zu bytes of shared memory for one warp", fixed + per_traj * (32 / LG));
     uint32_t nt = a->trajs_per_block;
@@ -341,7 +343,9 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
         case 1: e = launch_lg<1>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
         case 2: e = launch_lg<2>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
         case 4: e = launch_lg<4>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
-        default: e = launch_lg<8>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+        case 8: e = launch_lg<8>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+        case 16: e = launch_lg<16>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
+        default: e = launch_lg<32>(P, tr, ts, (uint32_t)grid, nt * LG, smem, st); break;
     }
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_simulate: %s", cudaGetErrorString(e));
     return PBN_OK;

@@ -105,6 +105,8 @@ class Server:
         self.pending = 0
         self.lock = threading.Lock()
         self.node_updates = 0.0
+        # host-side time split of the rounds (seconds): batch build, launch + wait, decisions
+        self.stats = {"rounds": 0, "build_s": 0.0, "device_s": 0.0, "decide_s": 0.0}
 
     # -- preparation (host worker threads) -------------------------------------------
     def _prepare(self, q: Query):
@@ -163,13 +165,16 @@ class Server:
             entries.append(dict(plan=a.plan, bufs=a.bufs, seed=a.q.seed, meta_ids=a.q.meta_ids,
                                 meta_vals=a.q.meta_vals, step_begin=a.step, count_from=a.count_from,
                                 init=_lib.PBN_INIT_KEYED if a.step == 0 else _lib.PBN_INIT_STATE))
+        t0 = time.perf_counter()
         with torch.cuda.stream(self.stream):
             B = api.Batch(entries, device=self.dev)
+            t1 = time.perf_counter()
             B.run(self.chunk, step_offset=0, stream=self.stream)
             pooled = torch.stack([a.bufs.pooled for a in self.active]).to("cpu", non_blocking=True)
         self.stream.synchronize()
         if int(B.status.item()) != 0:
             raise RuntimeError("batch kernel reported an error status")
+        t2 = time.perf_counter()
         pooled = pooled.numpy().view(np.uint64)
         finished = []
         for a, c in zip(self.active, pooled):
@@ -185,6 +190,11 @@ class Server:
             self.in_use -= a.nbytes
             with self.lock:
                 self.pending -= 1
+        st = self.stats
+        st["rounds"] += 1
+        st["build_s"] += t1 - t0
+        st["device_s"] += t2 - t1
+        st["decide_s"] += time.perf_counter() - t2
         return finished
 
     def _decide(self, a: _Active, c) -> bool:

@@ -151,3 +151,25 @@ def test_batch_with_split_nodes(oracle_mod):
         orc = oracle_mod.simulate(text, 9 + k, 0, 100 + 50 * k, 300, meta_ids=[0, 1], nthreads=NCPU)
         assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
         assert np.array_equal(got["counts"], orc["counts"]), k
+
+
+
+def test_batch_mixes_semantics(oracle_mod):
+    """A batch holding Eq. 1 and node-wise plans gives each network its own law."""
+    nets = _networks(seed=11, count=4)
+    entries, plans = [], []
+    for k, d in enumerate(nets):
+        sem = _lib.PBN_SEM_NODEWISE if k % 2 else _lib.PBN_SEM_EQ1
+        plan, ids = plan_for(d["text"], d["meta"], semantics=sem)
+        bufs = api.alloc_buffers(plan, d["T"])
+        entries.append(dict(plan=plan, bufs=bufs, seed=d["seed"], meta_ids=d["meta"]))
+        plans.append((plan, ids, sem))
+    B = api.Batch(entries)
+    B.run(250)
+    assert int(B.status.item()) == 0
+    for k, (d, (plan, ids, sem), e) in enumerate(zip(nets, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(d["text"], d["seed"], 0, d["T"], 250, meta_ids=d["meta"], nthreads=NCPU,
+                                  semantics=int(sem))
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+        assert np.array_equal(got["counts"], orc["counts"]), k

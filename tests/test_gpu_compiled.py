@@ -116,3 +116,14 @@ def test_compiled_split_nodes(oracle_mod, kmax):
     plan.compile()
     orc = oracle_mod.simulate(text, 21, 0, 160, 400, meta_ids=meta, trace=True, nthreads=NCPU)
     _compare(run(plan, seed=21, n_traj=160, n_steps=400, meta=meta, trace=True, kernel=COMPILED), orc, ids)
+
+
+
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_INTERLEAVED])
+def test_compiled_nodewise_semantics(oracle_mod, flags):
+    text = synth.paper100(seed=2, p=5e-3).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta, semantics=_lib.PBN_SEM_NODEWISE)
+    plan.compile(flags)
+    orc = oracle_mod.simulate(text, 32, 0, 160, 600, meta_ids=meta, trace=True, nthreads=NCPU, semantics=1)
+    _compare(run(plan, seed=32, n_traj=160, n_steps=600, meta=meta, trace=True, kernel=COMPILED), orc, ids)

@@ -45,7 +45,8 @@ def test_tiny12_full_run_every_step(oracle_mod, mode, reduce):
     _compare(gpu, orc, ids)
 
 
-@pytest.mark.parametrize("lanes,tpb", [(1, 32), (1, 96), (2, 16), (2, 64), (4, 8), (4, 40), (8, 4), (8, 64), (0, 0)])
+@pytest.mark.parametrize("lanes,tpb", [(1, 32), (1, 96), (2, 16), (2, 64), (4, 8), (4, 40), (8, 4), (8, 64),
+                                       (16, 2), (16, 10), (32, 1), (32, 16), (0, 0)])
 def test_launch_shape_invariance(oracle_mod, lanes, tpb):
     """Lanes per trajectory and trajectories per CTA change nothing (ragged last CTA)."""
     net = synth.paper100(seed=2, p=2e-3)
@@ -89,14 +90,15 @@ def test_paper100_against_oracle(oracle_mod, mode):
     _compare(gpu, orc, ids, trace=False)
 
 
-def test_scalefree2000_against_oracle(oracle_mod):
+@pytest.mark.parametrize("lanes", [0, 32])
+def test_scalefree2000_against_oracle(oracle_mod, lanes):
     """Large scale-free network (n = 2000, p = 1e-5, meta = 4 nodes)."""
     text = synth.scalefree2000(seed=3).to_text()
     meta = [0, 1, 2, 3]
     plan, ids = plan_for(text, meta)
     T, S = 64, 150
     orc = oracle_mod.simulate(text, 3, 0, T, S, meta_ids=meta, trace=True, nthreads=NCPU)
-    gpu = run(plan, seed=3, n_traj=T, n_steps=S, meta=meta, trace=True)
+    gpu = run(plan, seed=3, n_traj=T, n_steps=S, meta=meta, trace=True, lanes=lanes)
     _compare(gpu, orc, ids)
 
 
@@ -227,3 +229,23 @@ def test_apoptosis_stand_in_against_oracle(oracle_mod):
     for kernel in (_lib.PBN_KERNEL_INTERP, _lib.PBN_KERNEL_COMPILED):
         _compare(run(plan, seed=13, n_traj=256, n_steps=2000, meta=meta, count_from=100, kernel=kernel),
                  orc, ids, trace=False)
+
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+@pytest.mark.parametrize("which", ["tiny12", "paper100"])
+def test_nodewise_semantics(oracle_mod, lanes, which):
+    """Node-wise perturbation semantics: every step applies the functions and the
+    perturbed nodes negate; bit-exact against the oracle's node-wise simulator."""
+    if which == "tiny12":
+        text, meta = synth.tiny12(1).to_text(), [0, 1, 2]
+    else:
+        text, meta = synth.paper100(seed=2, p=5e-3).to_text(), [0, 1, 2]
+    plan, ids = plan_for(text, meta, semantics=_lib.PBN_SEM_NODEWISE)
+    orc = oracle_mod.simulate(text, 31, 0, 96, 700, meta_ids=meta, trace=True, nthreads=NCPU, semantics=1)
+    gpu = run(plan, seed=31, n_traj=96, n_steps=700, meta=meta, trace=True, lanes=lanes,
+              kernel=_lib.PBN_KERNEL_INTERP)
+    _compare(gpu, orc, ids)
+    # and it differs from Eq. 1 on the same draws
+    eq1 = oracle_mod.simulate(text, 31, 0, 96, 700, meta_ids=meta, nthreads=NCPU)
+    assert not np.array_equal(eq1["final"], orc["final"])

@@ -335,7 +335,7 @@ def test_estimate_rejects_bad_arguments():
 # ------------------------------------------------------------ compiled plans ----
 @pytest.mark.parametrize("flags", [0, 1, 2, 3])
 @pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half",
-                                   "split_small", "split_wide"])
+                                   "split_small", "split_wide", "nodewise"])
 def test_generated_plan_kernels_compile(tmp_path, which, flags):
     """The source generated for a plan's own kernel compiles for sm_103a."""
     import shutil
@@ -359,6 +359,10 @@ def test_generated_plan_kernels_compile(tmp_path, which, flags):
         text, meta = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n", [0]
     red, _ = api.Net.load(text).reduce(meta)
     kw = dict(max_inputs=3) if which.startswith("split") else {}
+    if which == "nodewise":
+        text, meta = synth.paper100(seed=2).to_text(), [0, 1, 2]
+        red, _ = api.Net.load(text).reduce(meta)
+        kw = dict(semantics=_lib.PBN_SEM_NODEWISE)
     plan = api.Plan(red, mode=1 if which.endswith("plain") else 0, **kw)
     if which.startswith("split"):
         assert plan.info.n_split > 0
