@@ -213,9 +213,11 @@ def run_ours(args):
     red, retained = api.Net.load(text).reduce(meta)
     plan = api.Plan(red, max_inputs=max_inputs, smem_budget=budget) if budget else api.Plan(red, max_inputs=max_inputs)
     compile_ms = 0.0
+    kattrs = None
     if args.kernel == "compiled":
         try:
             compile_ms = plan.compile(cflags)
+            kattrs = plan.compiled_attrs()
         except _lib.PbnError:
             args.kernel = "interpreter"  # plan too wide to compile: the interpreter runs it
     prep_s = time.perf_counter() - t_prep
@@ -301,7 +303,7 @@ def run_ours(args):
                     ("interpreter_plain_unreduced", plain_plan, _lib.PBN_KERNEL_INTERP)]
         # the same grouped plan compiled with each code-shape flag
         for fname, fl in (("rolled", 0), ("unrolled", _lib.PBN_COMPILE_PERT_UNROLLED),
-                          ("interleaved", _lib.PBN_COMPILE_INTERLEAVED)):
+                          ("interleaved", _lib.PBN_COMPILE_INTERLEAVED), ("pipelined", _lib.PBN_COMPILE_PIPELINED)):
             pf = api.Plan(red, max_inputs=max_inputs)
             try:
                 pf.compile(fl)
@@ -356,6 +358,7 @@ def run_ours(args):
                        "host_prep_s": round(prep_s, 4), "compile_ms": round(compile_ms, 1),
                        "kernel": args.kernel, "max_inputs_per_group": max_inputs,
                        "compile_flags": cflags if args.kernel == "compiled" else None,
+                       "compiled_kernel": kattrs,
                        "split_nodes": int(info.n_split),
                        "lanes_per_traj": lanes or "auto", "autotune_s": round(tune_s, 2)},
             "compare": compare,

@@ -301,6 +301,18 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
  * with other flags replaces the kernel. */
 #define PBN_COMPILE_PERT_UNROLLED 0x1u
 #define PBN_COMPILE_INTERLEAVED 0x2u
+/* PBN_COMPILE_PIPELINED: software-pipelined steps; the SEL blocks and the first
+ * three perturbation level pairs of step t + 1 are drawn while step t's groups are
+ * evaluated (every draw is independent of the state), and the evaluation runs in
+ * every step with a select keeping s XOR flips in perturbed steps.  Takes
+ * precedence over the two flags above. */
+#define PBN_COMPILE_PIPELINED 0x4u
+
+/* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
+ * thread, local-memory (spill) bytes per thread and the flags it was compiled with;
+ * any pointer may be NULL.  Errors: PBN_EINVAL (NULL plan, plan not compiled),
+ * PBN_ECUDA. */
+int pbn_plan_compiled_attrs(const pbn_plan* plan, uint32_t* regs, uint32_t* local_bytes, uint32_t* flags);
 
 /* The CUDA source generated for the plan's own kernel: *len receives its length;
  * dst (capacity cap, may be NULL) receives it NUL-terminated.

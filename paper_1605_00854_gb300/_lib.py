@@ -32,6 +32,7 @@ PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
 PBN_COMPILE_PERT_UNROLLED = 0x1
 PBN_COMPILE_INTERLEAVED = 0x2
+PBN_COMPILE_PIPELINED = 0x4
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1
@@ -96,6 +97,7 @@ class EstimateOut(ctypes.Structure):
 SIGNATURES = {
     "pbn_load": (i32, [cp, ctypes.c_size_t, ctypes.POINTER(vp)]),
     "pbn_load_arrays": (i32, [ctypes.POINTER(NetDesc), ctypes.POINTER(vp)]),
+    "pbn_plan_compiled_attrs": (i32, [vp, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32)]),
     "pbn_net_info_get": (i32, [vp, ctypes.POINTER(NetInfo)]),
     "pbn_reduce": (i32, [vp, vp, u32, ctypes.POINTER(vp), vp, ctypes.POINTER(u32)]),
     "pbn_reduce_rule": (i32, [vp, vp, u32, u32, ctypes.POINTER(vp), vp, ctypes.POINTER(u32)]),

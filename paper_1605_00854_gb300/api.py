@@ -160,6 +160,13 @@ class Plan:
         check(_lib.load().pbn_plan_compile(self._h, flags, ctypes.byref(ms)), "pbn_plan_compile")
         return ms.value
 
+    def compiled_attrs(self) -> dict:
+        """Registers, spill bytes and flags of the compiled kernel (pbn_plan_compiled_attrs)."""
+        r, l, f = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+        check(_lib.load().pbn_plan_compiled_attrs(self._h, ctypes.byref(r), ctypes.byref(l), ctypes.byref(f)),
+              "pbn_plan_compiled_attrs")
+        return {"regs": r.value, "local_bytes": l.value, "flags": f.value}
+
     def source(self, flags: int = 0) -> str:
         """CUDA source of the plan's own kernel (pbn_plan_source)."""
         L = _lib.load()

@@ -233,8 +233,9 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                     }
                     return x;
                 };
-                /* new bits of group gi, already at their place in the output word */
-                auto group_bits = [&](uint32_t gi) -> uint32_t {
+                /* where group gi's entry lies: table word, bit offset, entry mask and
+                 * the group's shift in its output word */
+                auto group_lookup = [&](uint32_t gi) -> uint4 {
                     const uint4 G = GROUPS[gi]; /* tab_off, in_chunk, mul_first, q|l2w|n_mul|shift */
                     const uint32_t q = G.w & 0xFFu;
                     const uint32_t l2w = (G.w >> 8) & 0xFFu;
@@ -244,8 +245,7 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                         /* split node: only the selected function is evaluated */
                         const uint2 F = SUBS[G.x + Cb[MULTI[G.z].x]]; /* in_chunk | k << 27, tab_off */
                         const uint32_t x = gather(INPUTS + (F.x & 0x7FFFFFFu), F.x >> 27);
-                        const uint32_t tw = TAB_SMEM ? TAB[F.y + (x >> 5)] : __ldg(TAB + F.y + (x >> 5));
-                        return ((tw >> (x & 31u)) & 1u) << shift;
+                        return make_uint4(F.y + (x >> 5), x & 31u, 1u, shift);
                     }
                     uint32_t c = 0;
                     for (uint32_t m = 0; m < n_mul; ++m) {
@@ -254,9 +254,14 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                     }
                     const uint32_t x = gather(INPUTS + G.y, q);
                     const uint32_t bo = ((c << q) | x) << l2w;
-                    const uint32_t tw = TAB_SMEM ? TAB[G.x + (bo >> 5)] : __ldg(TAB + G.x + (bo >> 5));
-                    const uint32_t emask = (2u << ((1u << l2w) - 1u)) - 1u;
-                    return ((tw >> (bo & 31u)) & emask) << shift;
+                    return make_uint4(G.x + (bo >> 5), bo & 31u, (2u << ((1u << l2w) - 1u)) - 1u, shift);
+                };
+                auto tab_word = [&](uint32_t i) -> uint32_t { return TAB_SMEM ? TAB[i] : __ldg(TAB + i); };
+                auto entry_bits = [&](const uint4 L, uint32_t tw) -> uint32_t { return ((tw >> L.y) & L.z) << L.w; };
+                /* new bits of group gi, already at their place in the output word */
+                auto group_bits = [&](uint32_t gi) -> uint32_t {
+                    const uint4 L = group_lookup(gi);
+                    return entry_bits(L, tab_word(L.x));
                 };
                 if (LG == 1) {
                     /* word by word, the word's groups ORed in a register */
@@ -271,7 +276,23 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                      * run in step) and OR their bits into the shared next-state words */
                     for (uint32_t w = lane; w < W32; w += LG) Sn[w] = 0u;
                     group_sync<LG>();
-                    for (uint32_t k = lane; k < P.n_groups; k += LG) {
+                    /* four groups per lane at a time: their table loads are in flight
+                     * together (they dominate when the tables are in L2) */
+                    uint32_t k = lane;
+                    for (; k + 3 * LG < P.n_groups; k += 4 * LG) {
+                        uint32_t go[4], tw[4];
+                        uint4 L[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            go[i] = GORDER[k + i * LG];
+                            L[i] = group_lookup(go[i] & 0xFFFFFu);
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) tw[i] = tab_word(L[i].x);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) atomicOr(&Sn[go[i] >> 20], entry_bits(L[i], tw[i]));
+                    }
+                    for (; k < P.n_groups; k += LG) {
                         const uint32_t go = GORDER[k];
                         atomicOr(&Sn[go >> 20], group_bits(go & 0xFFFFFu));
                     }

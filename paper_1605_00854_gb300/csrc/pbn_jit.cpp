@@ -210,30 +210,22 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         z = zs.str();
     }
     o << "    uint32_t zp = " << z << ";\n    if (P.count_first) cV += zp;\n";
-    o << "    for (uint32_t k = 0; k < P.n_steps; ++k) {\n"
-         "      const uint64_t t = P.step_begin + k;\n"
-         "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
-         "      uint32_t any = 0;\n";
     const bool interleave = (flags & PBN_COMPILE_INTERLEAVED) != 0;
-    /* node-wise semantics: perturbed nodes are collected in masks g<row>, every
-     * step evaluates the functions, and the masked bits take NOT s */
+    const bool pipelined = (flags & PBN_COMPILE_PIPELINED) != 0;
+    /* node-wise semantics: every step evaluates the functions and the perturbed
+     * nodes (collected in masks) take NOT s */
     const bool nodewise = H.semantics == PBN_SEM_NODEWISE;
-    if (nodewise) {
-        o << "      uint32_t";
-        for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "g" << r << " = 0";
-        o << ";\n";
-    }
-    auto emit_sel_draws = [&](const char* ind) {
-        for (uint32_t i = 0; i < H.n_sel; ++i)
-            o << ind << "const uint4 U" << i << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
-    };
-    /* interleaved: the SEL blocks are drawn before the perturbation check (they are
-     * needed in every non-perturbed step), so that their Philox chains and the first
-     * perturbation levels form one block of independent work */
-    if (interleave) emit_sel_draws("      ");
-    /* 1. perturbation: the levels of P compiled in */
     const uint32_t Pv = H.P;
-    auto emit_flips = [&](uint32_t w, const char* pl, const char* ph, const char* sfx) {
+    const uint32_t hmax = Pv ? (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u : 0u;
+
+    /* the SEL blocks of one step as uint4 <name><i> drawn from Philox state <ps> */
+    auto emit_sel_draws = [&](const char* ind, const char* decl, const char* name, const char* ps) {
+        for (uint32_t i = 0; i < H.n_sel; ++i)
+            o << ind << decl << name << i << " = pbn_philox_draw(P, " << ps << ", "
+              << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
+    };
+    /* perturbed retained lanes of word w (masks pl/ph): op into s<row> or a mask */
+    auto emit_flips = [&](uint32_t w, const std::string& pl, const std::string& ph, const char* target, const char* op) {
         const uint32_t rl = (uint32_t)ret[w], rh = (uint32_t)(ret[w] >> 32);
         for (int half = 0; half < 2; ++half) {
             const uint32_t rm = half ? rh : rl;
@@ -243,206 +235,287 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             for (uint32_t b = 0; b < 32; ++b) {
                 if (!((rm >> b) & 1u)) continue;
                 const uint32_t ps = pos[64 * w + 32 * half + b];
-                o << "            case " << b << ": " << (nodewise ? "g" : "s") << (ps >> 5) << (nodewise ? " |= " : " ^= ")
+                o << "            case " << b << ": " << target << (ps >> 5) << " " << op << " "
                   << hex32(1u << (ps & 31)) << "; break;\n";
             }
             o << "          } } }\n";
         }
-        (void)sfx;
     };
     auto valid_of = [&](uint32_t w) {
         const uint32_t nl = (w == H.W - 1) ? (H.n - 64 * w) : 64u;
         return nl >= 64 ? ~0ull : ((1ull << nl) - 1ull);
     };
-    if (Pv && (flags & PBN_COMPILE_PERT_UNROLLED)) {
-        /* one word at a time, every level pair unrolled with its P bits as constants */
-        const uint32_t hmax = (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u;
-        for (uint32_t w = 0; w < H.W; ++w) {
-            const uint64_t valid = valid_of(w);
-            o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
-              << ", pl = 0, ph = 0;\n";
-            for (uint32_t h = 0; h < hmax; ++h) {
-                const uint32_t b0 = (Pv >> (31 - 2 * h)) & 1u;
-                const uint32_t b1 = (Pv >> (30 - 2 * h)) & 1u;
-                o << "        if (ul | uh) { const uint4 x = pbn_philox_draw(P, ps, "
-                  << hex32((PBN_DOM_PERT << 28) | (w << 4) | h) << ");";
-                if (b0) o << " pl |= ul & ~x.x; ph |= uh & ~x.y; ul &= x.x; uh &= x.y;";
-                else o << " ul &= ~x.x; uh &= ~x.y;";
-                if (b1) o << " pl |= ul & ~x.z; ph |= uh & ~x.w; ul &= x.z; uh &= x.w;";
-                else o << " ul &= ~x.z; uh &= ~x.w;";
-                o << " }\n";
-            }
-            o << "        if (pl | ph) {\n          any = 1u;\n";
-            emit_flips(w, "pl", "ph", "");
-            o << "        }\n      }\n";
+    /* one straight-line level pair h of word w with P's two bits as constants,
+     * updating masks ul/uh (undecided) and pl/ph (perturbed) with suffix sfx */
+    auto emit_level = [&](const char* ind, uint32_t w, uint32_t h, const std::string& sfx, const char* ps) {
+        const uint32_t b0 = (Pv >> (31 - 2 * h)) & 1u;
+        const uint32_t b1 = (Pv >> (30 - 2 * h)) & 1u;
+        const char* S = sfx.c_str();
+        o << ind << fmt("{ const uint4 x = pbn_philox_draw(P, %s, %s);", ps, hex32((PBN_DOM_PERT << 28) | (w << 4) | h).c_str());
+        if (b0) o << fmt(" pl%s |= ul%s & ~x.x; ph%s |= uh%s & ~x.y; ul%s &= x.x; uh%s &= x.y;", S, S, S, S, S, S);
+        else o << fmt(" ul%s &= ~x.x; uh%s &= ~x.y;", S, S);
+        if (b1) o << fmt(" pl%s |= ul%s & ~x.z; ph%s |= uh%s & ~x.w; ul%s &= x.z; uh%s &= x.w;", S, S, S, S, S, S);
+        else o << fmt(" ul%s &= ~x.z; uh%s &= ~x.w;", S, S);
+        o << " }\n";
+    };
+    /* the rolled loop over the remaining level pairs h0.. of words w (and w + 1) */
+    auto emit_level_loop = [&](uint32_t w, bool two, uint32_t h0, const std::string& s0, const std::string& s1,
+                               const char* ps) {
+        o << "        { uint32_t pp = " << hex32(h0 ? (Pv << (2 * h0)) : Pv) << ";\n"
+          << "#pragma unroll 1\n"
+          << "        for (uint32_t h = " << h0 << "u; h < " << hmax << "u; ++h) {\n"
+          << "          if (!(ul" << s0 << " | uh" << s0 << (two ? " | ul" + s1 + " | uh" + s1 : std::string()) << ")) break;\n"
+          << "          const uint32_t m0 = (uint32_t)((int32_t)pp >> 31), m1 = (uint32_t)((int32_t)(pp << 1) >> 31);\n"
+          << "          pp <<= 2;\n"
+          << "          const uint4 x0 = pbn_philox_draw(P, " << ps << ", " << hex32((PBN_DOM_PERT << 28) | (w << 4)) << " | h);\n";
+        if (two)
+            o << "          const uint4 x1 = pbn_philox_draw(P, " << ps << ", " << hex32((PBN_DOM_PERT << 28) | ((w + 1) << 4))
+              << " | h);\n";
+        for (int k = 0; k < (two ? 2 : 1); ++k) {
+            const char* S = (k ? s1 : s0).c_str();
+            o << fmt("          pl%s |= ul%s & ~x%d.x & m0; ph%s |= uh%s & ~x%d.y & m0; ul%s &= ~(x%d.x ^ m0); uh%s &= ~(x%d.y ^ m0);\n",
+                     S, S, k, S, S, k, S, k, S, k)
+              << fmt("          pl%s |= ul%s & ~x%d.z & m1; ph%s |= uh%s & ~x%d.w & m1; ul%s &= ~(x%d.z ^ m1); uh%s &= ~(x%d.w ^ m1);\n",
+                     S, S, k, S, S, k, S, k, S, k);
         }
-    } else if (Pv) {
-        /* words in pairs: one rolled loop draws both words' level pairs, two
-         * independent Philox chains per iteration; the P bit of each level comes
-         * from a shifted copy of P */
-        const uint32_t hmax = (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u;
-        for (uint32_t w = 0; w < H.W; w += 2) {
-            const bool two = w + 1 < H.W;
-            const uint64_t v0 = valid_of(w), v1 = two ? valid_of(w + 1) : 0ull;
-            o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
-              << ", pl0 = 0, ph0 = 0";
-            if (two) o << ", ul1 = " << hex32((uint32_t)v1) << ", uh1 = " << hex32((uint32_t)(v1 >> 32)) << ", pl1 = 0, ph1 = 0";
-            /* interleaved: the first level pairs (needed by a 64-lane word with
-             * probability ~1) are straight-line code without an exit test */
-            const uint32_t npeel = interleave ? std::min<uint32_t>(hmax, 3u) : 0u;
-            o << ";\n";
-            for (uint32_t h = 0; h < npeel; ++h) {
-                const uint32_t b0 = (Pv >> (31 - 2 * h)) & 1u;
-                const uint32_t b1 = (Pv >> (30 - 2 * h)) & 1u;
-                for (int k = 0; k < (two ? 2 : 1); ++k) {
-                    o << fmt("        { const uint4 x = pbn_philox_draw(P, ps, %s);",
-                             hex32((PBN_DOM_PERT << 28) | ((w + k) << 4) | h).c_str());
-                    if (b0) o << fmt(" pl%d |= ul%d & ~x.x; ph%d |= uh%d & ~x.y; ul%d &= x.x; uh%d &= x.y;", k, k, k, k, k, k);
-                    else o << fmt(" ul%d &= ~x.x; uh%d &= ~x.y;", k, k);
-                    if (b1) o << fmt(" pl%d |= ul%d & ~x.z; ph%d |= uh%d & ~x.w; ul%d &= x.z; uh%d &= x.w;", k, k, k, k, k, k);
-                    else o << fmt(" ul%d &= ~x.z; uh%d &= ~x.w;", k, k);
-                    o << " }\n";
-                }
-            }
-            o << "        uint32_t pp = " << hex32(npeel ? (Pv << (2 * npeel)) : Pv) << ";\n"
-              << "#pragma unroll 1\n"
-              << "        for (uint32_t h = " << npeel << "u; h < " << hmax << "u; ++h) {\n"
-              << "          if (!(ul0 | uh0" << (two ? " | ul1 | uh1" : "") << ")) break;\n"
-              << "          const uint32_t m0 = (uint32_t)((int32_t)pp >> 31), m1 = (uint32_t)((int32_t)(pp << 1) >> 31);\n"
-              << "          pp <<= 2;\n"
-              << "          const uint4 x0 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_PERT << 28) | (w << 4)) << " | h);\n";
-            if (two) o << "          const uint4 x1 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_PERT << 28) | ((w + 1) << 4)) << " | h);\n";
-            for (int k = 0; k < (two ? 2 : 1); ++k) {
-                o << fmt("          pl%d |= ul%d & ~x%d.x & m0; ph%d |= uh%d & ~x%d.y & m0; ul%d &= ~(x%d.x ^ m0); uh%d &= ~(x%d.y ^ m0);\n",
-                         k, k, k, k, k, k, k, k, k, k)
-                  << fmt("          pl%d |= ul%d & ~x%d.z & m1; ph%d |= uh%d & ~x%d.w & m1; ul%d &= ~(x%d.z ^ m1); uh%d &= ~(x%d.w ^ m1);\n",
-                         k, k, k, k, k, k, k, k, k, k);
-            }
-            o << "        }\n";
-            o << "        if (pl0 | ph0) {\n          any = 1u;\n";
-            emit_flips(w, "pl0", "ph0", "");
-            o << "        }\n";
-            if (two) {
-                o << "        if (pl1 | ph1) {\n          any = 1u;\n";
-                emit_flips(w + 1, "pl1", "ph1", "");
-                o << "        }\n";
-            }
-            o << "      }\n";
+        o << "        } }\n";
+    };
+    /* choice of a multi-function node from its SEL slot's thresholds */
+    auto choice_expr = [&](const pbn_img_multi& M) {
+        const uint32_t slot = M.ch_off;
+        const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
+        const uint32_t* ss = selslot + 4 * slot; /* t1, t2, n_thr, first */
+        const uint32_t n_thr = ss[2];
+        std::string j;
+        for (uint32_t q = 0; q < n_thr; ++q) {
+            const uint32_t T = n_thr <= 2 ? ss[q] : thr[ss[3] + q];
+            j += (q ? " + " : "") + fmt("(uint32_t)(%s >= %s)", u.c_str(), hex32(T).c_str());
         }
-    }
-    /* 2. selection draws and merged-table evaluation */
-    o << (nodewise ? "      {\n" : "      if (!any) {\n");
-    if (!interleave) emit_sel_draws("        ");
-    for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
-    for (uint32_t r = 0; r < H.W32; ++r) {
-        for (uint32_t gi = words[r].x; gi < words[r].x + words[r].y; ++gi) {
-            const pbn_img_group& G = groups[gi];
-            o << "        { ";
-            /* choice of a multi-function node from its SEL slot's thresholds */
-            auto choice_expr = [&](const pbn_img_multi& M) {
-                const uint32_t slot = M.ch_off;
-                const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
-                const uint32_t* ss = selslot + 4 * slot; /* t1, t2, n_thr, first */
-                const uint32_t n_thr = ss[2];
-                std::string j;
-                for (uint32_t q = 0; q < n_thr; ++q) {
-                    const uint32_t T = n_thr <= 2 ? ss[q] : thr[ss[3] + q];
-                    j += (q ? " + " : "") + fmt("(uint32_t)(%s >= %s)", u.c_str(), hex32(T).c_str());
-                }
-                return j;
-            };
-            /* input pattern of k inputs from chunked records */
-            auto pattern = [&](uint32_t in_chunk, uint32_t k) {
-                std::string xexpr;
-                for (uint32_t b = 0; b < k; ++b) {
-                    const uint32_t rec = inrec[4 * in_chunk + b];
-                    const uint32_t row = rec >> 7, bit = ((b & 3) + (rec & 31)) & 31;
-                    xexpr += (b ? " | " : "") + gather(row, bit, b);
-                }
-                return xexpr.empty() ? std::string("0u") : xexpr;
-            };
-            if (G.l2w == PBN_IMG_SPLIT) {
-                /* split node: every function's pattern is a few register operations;
-                 * the selected one's table bit is kept (immediates when every table
-                 * fits in 64 bits, else one lookup at the selected table) */
-                std::string j = choice_expr(multi[G.mul_first]);
-                if (j.empty()) j = "0u";
-                o << "const uint32_t j = " << j << "; ";
-                bool small = true;
-                for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + f)] >> 27) <= 6;
-                std::string v = "0u";
-                if (small) {
-                    for (uint32_t f = G.q; f-- > 0;) {
-                        const uint32_t* F = subs + 2 * (G.tab_off + f);
-                        const uint32_t k = F[0] >> 27, ch = F[0] & 0x7FFFFFFu;
-                        const uint64_t t64 = (k == 6 ? ((uint64_t)tab[F[1] + 1] << 32) : 0ull) | tab[F[1]];
-                        const std::string vf =
-                            fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k) + ")) & 1ull)";
-                        v = f + 1 == G.q ? vf : fmt("(j == %uu ? ", f) + vf + " : " + v + ")";
+        return j;
+    };
+    /* input pattern of k inputs from chunked records */
+    auto pattern = [&](uint32_t in_chunk, uint32_t k) {
+        std::string xexpr;
+        for (uint32_t b = 0; b < k; ++b) {
+            const uint32_t rec = inrec[4 * in_chunk + b];
+            const uint32_t row = rec >> 7, bit = ((b & 3) + (rec & 31)) & 31;
+            xexpr += (b ? " | " : "") + gather(row, bit, b);
+        }
+        return xexpr.empty() ? std::string("0u") : xexpr;
+    };
+    /* merged-table evaluation of every group from s and the SEL uniforms U: n<row> */
+    auto emit_eval = [&]() {
+        for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
+        for (uint32_t r = 0; r < H.W32; ++r) {
+            for (uint32_t gi = words[r].x; gi < words[r].x + words[r].y; ++gi) {
+                const pbn_img_group& G = groups[gi];
+                o << "        { ";
+                if (G.l2w == PBN_IMG_SPLIT) {
+                    /* split node: every function's pattern is a few register operations;
+                     * the selected one's table bit is kept (immediates when every table
+                     * fits in 64 bits, else one lookup at the selected table) */
+                    std::string j = choice_expr(multi[G.mul_first]);
+                    if (j.empty()) j = "0u";
+                    o << "const uint32_t j = " << j << "; ";
+                    bool small = true;
+                    for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + f)] >> 27) <= 6;
+                    std::string v = "0u";
+                    if (small) {
+                        for (uint32_t f = G.q; f-- > 0;) {
+                            const uint32_t* F = subs + 2 * (G.tab_off + f);
+                            const uint32_t k = F[0] >> 27, ch = F[0] & 0x7FFFFFFu;
+                            const uint64_t t64 = (k == 6 ? ((uint64_t)tab[F[1] + 1] << 32) : 0ull) | tab[F[1]];
+                            const std::string vf =
+                                fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k) + ")) & 1ull)";
+                            v = f + 1 == G.q ? vf : fmt("(j == %uu ? ", f) + vf + " : " + v + ")";
+                        }
+                    } else {
+                        std::string xs = "0u", offs = "0u";
+                        for (uint32_t f = G.q; f-- > 0;) {
+                            const uint32_t* F = subs + 2 * (G.tab_off + f);
+                            const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27) + ")";
+                            xs = f + 1 == G.q ? xf : fmt("(j == %uu ? ", f) + xf + " : " + xs + ")";
+                            offs = f + 1 == G.q ? fmt("%uu", F[1]) : fmt("(j == %uu ? %uu : ", f, F[1]) + offs + ")";
+                        }
+                        o << "const uint32_t x = " << xs << "; const uint32_t to = " << offs << "; ";
+                        v = tab_smem ? "((TAB[to + (x >> 5)] >> (x & 31u)) & 1u)"
+                                     : "((__ldg(TAB + to + (x >> 5)) >> (x & 31u)) & 1u)";
                     }
+                    o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
+                    continue;
+                }
+                /* combined choice */
+                std::string cexpr;
+                for (uint32_t m = 0; m < G.n_mul; ++m) {
+                    const pbn_img_multi& M = multi[G.mul_first + m];
+                    const std::string j = choice_expr(M);
+                    if (j.empty()) continue;
+                    cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
+                }
+                /* input pattern */
+                const uint32_t q = G.q;
+                o << "const uint32_t x = " << pattern(G.in_chunk, q) << "; ";
+                if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
+                else o << "const uint32_t e = x; ";
+                /* table entry */
+                const uint32_t l2w = G.l2w;
+                const uint32_t ebits = 1u << l2w;
+                const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
+                /* size of this group's table in words: up to the next table's offset, or the end */
+                auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
+                const uint32_t tab_words = (nx == tab_starts.end() ? table_bytes / 4 : *nx) - G.tab_off;
+                std::string v;
+                if (tab_words == 1) {
+                    v = fmt("((%s >> (e << %u)) & %s)", hex32(tab[G.tab_off]).c_str(), l2w, hex32(emask).c_str());
+                } else if (tab_words == 2) {
+                    const uint64_t t64 = ((uint64_t)tab[G.tab_off + 1] << 32) | tab[G.tab_off];
+                    v = fmt("((uint32_t)(0x%016llxull >> (e << %u)) & %s)", (unsigned long long)t64, l2w, hex32(emask).c_str());
+                } else if (tab_smem) {
+                    v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w,
+                            hex32(emask).c_str());
                 } else {
-                    std::string xs = "0u", offs = "0u";
-                    for (uint32_t f = G.q; f-- > 0;) {
-                        const uint32_t* F = subs + 2 * (G.tab_off + f);
-                        const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27) + ")";
-                        xs = f + 1 == G.q ? xf : fmt("(j == %uu ? ", f) + xf + " : " + xs + ")";
-                        offs = f + 1 == G.q ? fmt("%uu", F[1]) : fmt("(j == %uu ? %uu : ", f, F[1]) + offs + ")";
-                    }
-                    o << "const uint32_t x = " << xs << "; const uint32_t to = " << offs << "; ";
-                    v = tab_smem ? "((TAB[to + (x >> 5)] >> (x & 31u)) & 1u)" : "((__ldg(TAB + to + (x >> 5)) >> (x & 31u)) & 1u)";
+                    v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w,
+                            hex32(emask).c_str());
                 }
                 o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
-                continue;
             }
-            /* combined choice */
-            std::string cexpr;
-            for (uint32_t m = 0; m < G.n_mul; ++m) {
-                const pbn_img_multi& M = multi[G.mul_first + m];
-                const std::string j = choice_expr(M);
-                if (j.empty()) continue;
-                cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
-            }
-            /* input pattern */
-            const uint32_t q = G.q;
-            o << "const uint32_t x = " << pattern(G.in_chunk, q) << "; ";
-            if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
-            else o << "const uint32_t e = x; ";
-            /* table entry */
-            const uint32_t l2w = G.l2w;
-            const uint32_t ebits = 1u << l2w;
-            const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
-            /* size of this group's table in words: up to the next table's offset, or the end */
-            auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
-            const uint32_t tab_words = (nx == tab_starts.end() ? table_bytes / 4 : *nx) - G.tab_off;
-            std::string v;
-            if (tab_words == 1) {
-                v = fmt("((%s >> (e << %u)) & %s)", hex32(tab[G.tab_off]).c_str(), l2w, hex32(emask).c_str());
-            } else if (tab_words == 2) {
-                const uint64_t t64 = ((uint64_t)tab[G.tab_off + 1] << 32) | tab[G.tab_off];
-                v = fmt("((uint32_t)(0x%016llxull >> (e << %u)) & %s)", (unsigned long long)t64, l2w, hex32(emask).c_str());
-            } else if (tab_smem) {
-                v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w, hex32(emask).c_str());
-            } else {
-                v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w,
-                        hex32(emask).c_str());
-            }
-            o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
         }
+    };
+    /* meta-state counts and the optional trace of the new state */
+    auto emit_counts = [&]() {
+        o << "      { const uint32_t z = " << z << ";\n"
+             "        const uint32_t cv = k >= P.kv0 ? 1u : 0u, cp = k >= P.kp0 ? 1u : 0u;\n"
+             "        cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u); zp = z; }\n";
+        o << "      if (P.trace) {\n";
+        for (uint32_t r = 0; r < H.W32; r += 2)
+            o << "        P.trace[((uint64_t)k * " << H.W32 / 2 << "u + " << r / 2 << "u) * P.n_traj + lt] = ((uint64_t)s"
+              << r + 1 << " << 32) | s" << r << ";\n";
+        o << "      }\n";
+    };
+
+    if (pipelined) {
+        /* Software-pipelined steps: every random draw is independent of the state, so
+         * the SEL blocks and the first perturbation level pairs of step t + 1 are drawn
+         * while step t's groups are evaluated (one block of independent work); the
+         * evaluation always runs and a select keeps s XOR flips in perturbed steps. */
+        const uint32_t npeel = std::min<uint32_t>(hmax, 3u);
+        o << "    pbn_philox_step ps = pbn_philox_begin(P, traj, P.step_begin);\n";
+        emit_sel_draws("    ", "uint4 ", "U", "ps");
+        for (uint32_t w = 0; w < H.W; ++w) {
+            const uint64_t v = Pv ? valid_of(w) : 0ull;
+            o << fmt("    uint32_t ul%u = %s, uh%u = %s, pl%u = 0, ph%u = 0;\n", w, hex32((uint32_t)v).c_str(), w,
+                     hex32((uint32_t)(v >> 32)).c_str(), w, w);
+            for (uint32_t h = 0; h < npeel; ++h) emit_level("    ", w, h, std::to_string(w), "ps");
+        }
+        o << "    for (uint32_t k = 0; k < P.n_steps; ++k) {\n"
+             "      const uint64_t t = P.step_begin + k;\n"
+             "      uint32_t any = 0;\n      uint32_t";
+        for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "f" << r << " = 0";
+        o << ";\n";
+        /* the remaining level pairs of step t, then its flips */
+        if (Pv && hmax > npeel)
+            for (uint32_t w = 0; w < H.W; w += 2)
+                emit_level_loop(w, w + 1 < H.W, npeel, std::to_string(w), std::to_string(w + 1), "ps");
+        for (uint32_t w = 0; w < H.W && Pv; ++w) {
+            o << "      if (pl" << w << " | ph" << w << ") {\n          any = 1u;\n";
+            emit_flips(w, "pl" + std::to_string(w), "ph" + std::to_string(w), "f", "|=");
+            o << "      }\n";
+        }
+        /* draws of step t + 1 */
+        o << "      const pbn_philox_step psn = pbn_philox_begin(P, traj, t + 1);\n";
+        emit_sel_draws("      ", "const uint4 ", "V", "psn");
+        for (uint32_t w = 0; w < H.W && Pv; ++w) {
+            const uint64_t v = valid_of(w);
+            const std::string S = "n" + std::to_string(w);
+            o << fmt("      uint32_t ul%s = %s, uh%s = %s, pl%s = 0, ph%s = 0;\n", S.c_str(), hex32((uint32_t)v).c_str(),
+                     S.c_str(), hex32((uint32_t)(v >> 32)).c_str(), S.c_str(), S.c_str());
+            for (uint32_t h = 0; h < npeel; ++h) emit_level("      ", w, h, S, "psn");
+        }
+        /* evaluation of step t and the new state */
+        o << "      {\n";
+        emit_eval();
+        for (uint32_t r = 0; r < H.W32; ++r) {
+            if (nodewise) o << "        s" << r << " = (n" << r << " & ~f" << r << ") | (~s" << r << " & f" << r << ");\n";
+            else o << "        s" << r << " = any ? (s" << r << " ^ f" << r << ") : n" << r << ";\n";
+        }
+        o << "      }\n";
+        emit_counts();
+        /* rotate */
+        o << "      ps = psn;\n";
+        for (uint32_t i = 0; i < H.n_sel; ++i) o << "      U" << i << " = V" << i << ";\n";
+        for (uint32_t w = 0; w < H.W && Pv; ++w)
+            o << fmt("      ul%u = uln%u; uh%u = uhn%u; pl%u = pln%u; ph%u = phn%u;\n", w, w, w, w, w, w, w, w);
+        o << "    }\n";
+    } else {
+        o << "    for (uint32_t k = 0; k < P.n_steps; ++k) {\n"
+             "      const uint64_t t = P.step_begin + k;\n"
+             "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
+             "      uint32_t any = 0;\n";
+        if (nodewise) {
+            o << "      uint32_t";
+            for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "g" << r << " = 0";
+            o << ";\n";
+        }
+        const char* ftarget = nodewise ? "g" : "s";
+        const char* fop = nodewise ? "|=" : "^=";
+        /* interleaved: the SEL blocks are drawn before the perturbation check (they are
+         * needed in every non-perturbed step), so that their Philox chains and the first
+         * perturbation levels form one block of independent work */
+        if (interleave) emit_sel_draws("      ", "const uint4 ", "U", "ps");
+        /* 1. perturbation: the levels of P compiled in */
+        if (Pv && (flags & PBN_COMPILE_PERT_UNROLLED)) {
+            /* one word at a time, every level pair unrolled with its P bits as constants */
+            for (uint32_t w = 0; w < H.W; ++w) {
+                const uint64_t valid = valid_of(w);
+                o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
+                  << ", pl = 0, ph = 0;\n";
+                for (uint32_t h = 0; h < hmax; ++h) {
+                    o << "        if (ul | uh) ";
+                    emit_level("", w, h, "", "ps");
+                }
+                o << "        if (pl | ph) {\n          any = 1u;\n";
+                emit_flips(w, "pl", "ph", ftarget, fop);
+                o << "        }\n      }\n";
+            }
+        } else if (Pv) {
+            /* words in pairs: one rolled loop draws both words' level pairs, two
+             * independent Philox chains per iteration; interleaved: the first level
+             * pairs (needed by a 64-lane word with probability ~1) are straight-line */
+            const uint32_t npeel = interleave ? std::min<uint32_t>(hmax, 3u) : 0u;
+            for (uint32_t w = 0; w < H.W; w += 2) {
+                const bool two = w + 1 < H.W;
+                const uint64_t v0 = valid_of(w), v1 = two ? valid_of(w + 1) : 0ull;
+                o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
+                  << ", pl0 = 0, ph0 = 0";
+                if (two) o << ", ul1 = " << hex32((uint32_t)v1) << ", uh1 = " << hex32((uint32_t)(v1 >> 32)) << ", pl1 = 0, ph1 = 0";
+                o << ";\n";
+                for (uint32_t h = 0; h < npeel; ++h)
+                    for (uint32_t k2 = 0; k2 < (two ? 2u : 1u); ++k2) emit_level("        ", w + k2, h, std::to_string(k2), "ps");
+                emit_level_loop(w, two, npeel, "0", "1", "ps");
+                o << "        if (pl0 | ph0) {\n          any = 1u;\n";
+                emit_flips(w, "pl0", "ph0", ftarget, fop);
+                o << "        }\n";
+                if (two) {
+                    o << "        if (pl1 | ph1) {\n          any = 1u;\n";
+                    emit_flips(w + 1, "pl1", "ph1", ftarget, fop);
+                    o << "        }\n";
+                }
+                o << "      }\n";
+            }
+        }
+        /* 2. selection draws and merged-table evaluation */
+        o << (nodewise ? "      {\n" : "      if (!any) {\n");
+        if (!interleave) emit_sel_draws("        ", "const uint4 ", "U", "ps");
+        emit_eval();
+        for (uint32_t r = 0; r < H.W32; ++r) {
+            if (nodewise) o << "        s" << r << " = (n" << r << " & ~g" << r << ") | (~s" << r << " & g" << r << ");\n";
+            else o << "        s" << r << " = n" << r << ";\n";
+        }
+        o << "      }\n";
+        /* 3. counts */
+        emit_counts();
+        o << "    }\n";
     }
-    for (uint32_t r = 0; r < H.W32; ++r) {
-        if (nodewise) o << "        s" << r << " = (n" << r << " & ~g" << r << ") | (~s" << r << " & g" << r << ");\n";
-        else o << "        s" << r << " = n" << r << ";\n";
-    }
-    o << "      }\n";
-    /* 3. counts */
-    o << "      { const uint32_t z = " << z << ";\n"
-         "        const uint32_t cv = k >= P.kv0 ? 1u : 0u, cp = k >= P.kp0 ? 1u : 0u;\n"
-         "        cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u); zp = z; }\n";
-    o << "      if (P.trace) {\n";
-    for (uint32_t r = 0; r < H.W32; r += 2)
-        o << "        P.trace[((uint64_t)k * " << H.W32 / 2 << "u + " << r / 2 << "u) * P.n_traj + lt] = ((uint64_t)s"
-          << r + 1 << " << 32) | s" << r << ";\n";
-    o << "      }\n    }\n";
     /* epilogue */
     for (uint32_t r = 0; r < H.W32; r += 2)
         o << "    P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt] = ((uint64_t)s" << r + 1 << " << 32) | s" << r << ";\n";
@@ -590,11 +663,25 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 
 extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
-    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED))
+    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
     const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;
     return rc;
+}
+
+extern "C" int pbn_plan_compiled_attrs(const pbn_plan* plan, uint32_t* regs, uint32_t* local_bytes, uint32_t* flags) {
+    if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compiled_attrs: NULL plan");
+    pbn_jit_state* J = pbn::jit_state(plan);
+    std::lock_guard<std::mutex> g(J->mu);
+    if (J->state != 1) return pbn::fail(PBN_EINVAL, "pbn_plan_compiled_attrs: the plan is not compiled");
+    cudaFuncAttributes fa;
+    const cudaError_t e = cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(J->kern));
+    if (e != cudaSuccess) return pbn::fail(PBN_ECUDA, "cudaFuncGetAttributes: %s", cudaGetErrorString(e));
+    if (regs) *regs = (uint32_t)fa.numRegs;
+    if (local_bytes) *local_bytes = (uint32_t)fa.localSizeBytes;
+    if (flags) *flags = J->flags;
+    return PBN_OK;
 }
 
 extern "C" int pbn_plan_source(const pbn_plan* plan, uint32_t flags, char* dst, size_t cap, size_t* len) {

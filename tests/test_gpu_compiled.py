@@ -41,11 +41,12 @@ def test_tiny12_compiled_every_step(oracle_mod, mode, reduce):
     _compare(run(plan, seed=1, n_traj=64, n_steps=10000, meta=meta, trace=True, kernel=COMPILED), orc, ids)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_paper100_compiled_matches_oracle_and_interpreter(oracle_mod, mode):
+@pytest.mark.parametrize("mode,flags", [(0, 0), (1, 0), (0, 4)])
+def test_paper100_compiled_matches_oracle_and_interpreter(oracle_mod, mode, flags):
     text = synth.paper100(seed=2).to_text()
     meta = [0, 1, 2]
     plan, ids = plan_for(text, meta, mode=mode)
+    plan.compile(flags)
     T, S = 1000, 3000
     orc = oracle_mod.simulate(text, 11, 77, T, S, meta_ids=meta, count_from=100, nthreads=NCPU)
     c = run(plan, seed=11, traj_begin=77, n_traj=T, n_steps=S, meta=meta, count_from=100, kernel=COMPILED)
@@ -54,17 +55,20 @@ def test_paper100_compiled_matches_oracle_and_interpreter(oracle_mod, mode):
     _compare(i, orc, ids, trace=False)
 
 
-def test_compiled_resume_and_keyed_init(oracle_mod):
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PIPELINED])
+def test_compiled_resume_and_keyed_init(oracle_mod, flags):
     text = synth.paper100(seed=4, n=90, p=5e-3).to_text()
     meta = [0, 2]
     plan, ids = plan_for(text, meta)
+    plan.compile(flags)
     orc = oracle_mod.simulate(text, 5, 0, 200, 900, meta_ids=meta, count_from=250, trace=True, nthreads=NCPU)
     a = run(plan, seed=5, n_traj=200, n_steps=900, meta=meta, count_from=250, chunks=[100, 150, 1, 649],
             trace=True, kernel=COMPILED)
     _compare(a, orc, ids)
 
 
-@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PERT_UNROLLED, _lib.PBN_COMPILE_INTERLEAVED])
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PERT_UNROLLED, _lib.PBN_COMPILE_INTERLEAVED,
+                                   _lib.PBN_COMPILE_PIPELINED])
 @pytest.mark.parametrize("p", [0.0, 0.05, 0.3, 0.75])
 def test_compiled_perturbation_regimes(oracle_mod, p, flags):
     text = synth.paper100(seed=9, n=170, p=p).to_text()
@@ -75,13 +79,16 @@ def test_compiled_perturbation_regimes(oracle_mod, p, flags):
     _compare(run(plan, seed=2, n_traj=96, n_steps=300, meta=meta, trace=True, kernel=COMPILED), orc, ids)
 
 
-def test_compiled_edge_cases(oracle_mod):
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_PIPELINED])
+def test_compiled_edge_cases(oracle_mod, flags):
     text = "pbn 1 0x1p-3\nf 0 0x1p-1 1 0 2\nf 0 0x1p-1 1 0 1\n"
     plan, ids = plan_for(text, [0])
+    plan.compile(flags)
     orc = oracle_mod.simulate(text, 1, 0, 1, 500, meta_ids=[0], trace=True)
     _compare(run(plan, seed=1, n_traj=1, n_steps=500, meta=[0], trace=True, kernel=COMPILED), orc, ids)
     text = synth.tiny12(3).to_text()
     plan, ids = plan_for(text, [0, 1, 2])
+    plan.compile(flags)
     rng = np.random.default_rng(0)
     init = rng.integers(0, 2, size=(40, 12)).astype(np.uint8)
     tb, sb = 2**40 + 17, 2**33 + 5
@@ -119,7 +126,7 @@ def test_compiled_split_nodes(oracle_mod, kmax):
 
 
 
-@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_INTERLEAVED])
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED])
 def test_compiled_nodewise_semantics(oracle_mod, flags):
     text = synth.paper100(seed=2, p=5e-3).to_text()
     meta = [0, 1, 2]
@@ -127,3 +134,13 @@ def test_compiled_nodewise_semantics(oracle_mod, flags):
     plan.compile(flags)
     orc = oracle_mod.simulate(text, 32, 0, 160, 600, meta_ids=meta, trace=True, nthreads=NCPU, semantics=1)
     _compare(run(plan, seed=32, n_traj=160, n_steps=600, meta=meta, trace=True, kernel=COMPILED), orc, ids)
+
+
+
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED])
+def test_compiled_kernel_attributes(flags):
+    text = synth.paper100(seed=2).to_text()
+    plan, _ = plan_for(text, [0, 1, 2])
+    plan.compile(flags)
+    a = plan.compiled_attrs()
+    assert a["flags"] == flags and 16 <= a["regs"] <= 255

@@ -333,7 +333,7 @@ def test_estimate_rejects_bad_arguments():
 
 
 # ------------------------------------------------------------ compiled plans ----
-@pytest.mark.parametrize("flags", [0, 1, 2, 3])
+@pytest.mark.parametrize("flags", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half",
                                    "split_small", "split_wide", "nodewise"])
 def test_generated_plan_kernels_compile(tmp_path, which, flags):
