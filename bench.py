@@ -446,8 +446,8 @@ def run_serve(args):
         meta = sorted(int(x) for x in rng.choice(4, size=k, replace=False))
         text = synth.paper100(seed=9000 + i, n=n, p=float(10 ** rng.uniform(-4, -2))).to_text()
         queries.append(serve.Query(qid=i, text=text, meta_ids=meta, seed=SEED + i, r=0.01, s=0.95))
-    srv = serve.Server(n_traj=args.serve_traj, chunk_steps=args.chunk_steps, mem_cap_bytes=100e9,
-                       workers=os.cpu_count() or 8)
+    srv = serve.Server(n_traj=args.serve_traj, chunk_steps=args.serve_chunk, mem_cap_bytes=100e9,
+                       workers=os.cpu_count() or 8, max_traj=args.serve_max_traj)
     t_start = time.perf_counter()
     due = t_start + np.cumsum(gaps)
     k = 0
@@ -468,8 +468,8 @@ def run_serve(args):
             "dtype": "u32", "data": "synthetic",
             "config": {"workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95",
                        "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "queries": n_q,
-                       "trajectories_per_query": args.serve_traj, "chunk_steps": args.chunk_steps,
-                       "memory_cap_bytes": 100e9},
+                       "trajectories_per_query": args.serve_traj, "max_trajectories_per_query": args.serve_max_traj,
+                       "chunk_steps": args.serve_chunk, "memory_cap_bytes": 100e9},
             "latency": lat, "queries_per_s": len(srv.done) / makespan,
             "node_updates_per_s": srv.node_updates / makespan, "makespan_s": makespan,
             "completed": len(srv.done), "rejected": len(srv.rejected), "failed": len(srv.failed),
@@ -501,7 +501,7 @@ def run_apoptosis(args):
     net, X, par, metas = apoptosis_queries()
     text = net.to_text()
     srv = serve.Server(n_traj=args.apo_traj, chunk_steps=args.apo_chunk, burn_in0=256,
-                       mem_cap_bytes=100e9, workers=8, max_steps=1 << 24)
+                       mem_cap_bytes=100e9, workers=8, max_steps=1 << 24, max_traj=args.apo_max_traj)
     t0 = time.perf_counter()
     for i, m in enumerate(metas):
         srv.submit(serve.Query(qid=i, text=text, meta_ids=m, seed=SEED + 17 * i, r=1e-5, s=0.95, eps=1e-3))
@@ -515,9 +515,11 @@ def run_apoptosis(args):
             "data": "synthetic", "vs_baseline": None,
             "config": {"workload": "apoptosis-shaped PBN: n=96, 37.5% leaves, density 1.78, p=1e-4",
                        "node_X": X, "parents_ABC": list(par), "trajectories_per_query": args.apo_traj,
+                       "max_trajectories_per_query": args.apo_max_traj,
                        "chunk_steps": args.apo_chunk, "r": 1e-5, "s": 0.95, "eps": 1e-3},
             "queries": [{"meta": metas[r.qid], "pi": r.pi, "n_star": r.n_star, "samples": r.L, "m_star": r.m_star,
-                         "steps": r.steps, "rounds": r.rounds, "latency_s": r.latency} for r in res],
+                         "steps": r.steps, "rounds": r.rounds, "trajectories": r.n_traj, "latency_s": r.latency}
+                        for r in res],
             "total_samples": samples, "node_updates_per_s": srv.node_updates / wall, "rounds": srv.stats,
             "completed": len(res), "failed": len(srv.failed),
             "paper_context": "Sec. 4.3: 7 probabilities, 50-452 million samples each, about 10 minutes "
@@ -544,13 +546,16 @@ def main():
     ap.add_argument("--workload", default="paper100",
                     choices=["paper100", "scalefree2000", "batch", "serve", "apoptosis"])
     ap.add_argument("--apo-traj", type=int, default=1 << 14)
+    ap.add_argument("--apo-max-traj", type=int, default=1 << 17)
     ap.add_argument("--apo-chunk", type=int, default=4096)
     ap.add_argument("--apo-timeout", type=float, default=600.0)
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--chunk-steps", type=int, default=1000)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
-    ap.add_argument("--serve-traj", type=int, default=512)
+    ap.add_argument("--serve-traj", type=int, default=2048)
+    ap.add_argument("--serve-chunk", type=int, default=128)
+    ap.add_argument("--serve-max-traj", type=int, default=1 << 16)
     ap.add_argument("--compare-steps", type=int, default=100000,
                     help="steps of the comparison passes (interpreter, plain method); 0 = skip")
     args = ap.parse_args()

@@ -6,19 +6,25 @@ server:
 
 * prepares queries on host worker threads (pbn_load, pbn_reduce on the meta nodes,
   pbn_group, plan image upload, device buffers for the query's trajectories);
-* admits prepared queries while the device bytes they need (plan image, states,
-  counts) fit under the memory cap, in arrival order;
+* admits prepared queries while the device bytes they may need (plan image,
+  states and counts at the largest trajectory count they may grow to) fit under the
+  memory cap, in arrival order;
 * runs rounds: one persistent batched launch (pbn_batch_run) advances every active
   query by `chunk_steps` steps, then one copy brings back every query's pooled
   counts [V, n00, n01, n10, n11];
 * after each round applies the two-state Markov chain stopping rule to each query:
   if the burn-in m* exceeds the start of its counting window, the window restarts
   at the current step (counts cleared); if the counted states reach N*, the query
-  completes with pi = V / L; otherwise it continues.
+  completes with pi = V / L; otherwise it continues;
+* grows a query that would need many more rounds: when the states still to count
+  exceed `grow_rounds` rounds at its current trajectory count, it gets a new block
+  of as many trajectories again (the next trajectory ids, their own burn-in), up to
+  `max_traj`.
 
-Each query's draws are keyed by its own seed and trajectory ids and every query
-advances by the same chunk in every round, so a query's result does not depend on
-the other queries in flight.
+Each query's draws are keyed by its own seed and trajectory ids, every query
+advances by the same chunk in every round, and the growth rule reads only the
+query's own counts, so a query's result does not depend on the other queries in
+flight.
 """
 from __future__ import annotations
 
@@ -62,20 +68,38 @@ class Result:
     alpha: float
     beta: float
     counts: list = field(default_factory=list)
+    n_traj: int = 0
+
+
+class _Block:
+    """A range of a query's trajectories with its own buffers and counting window."""
+
+    def __init__(self, bufs, traj_begin: int, n_traj: int, count_from: int):
+        self.bufs = bufs
+        self.traj_begin = traj_begin
+        self.n_traj = n_traj
+        self.step = 0              # steps simulated so far
+        self.count_from = count_from
 
 
 class _Active:
-    def __init__(self, q: Query, plan, bufs, n, prep_s, nbytes, count_from):
+    def __init__(self, q: Query, plan, bufs, n, prep_s, nbytes, count_from, n_traj):
         self.q = q
         self.plan = plan
-        self.bufs = bufs
+        self.blocks = [_Block(bufs, 0, n_traj, count_from)]
         self.n = n
         self.prep_s = prep_s
         self.nbytes = nbytes
-        self.step = 0              # steps simulated so far
-        self.count_from = count_from
         self.rounds = 0
         self.node_updates = 0.0
+
+    @property
+    def step(self) -> int:
+        return self.blocks[0].step
+
+    @property
+    def n_traj(self) -> int:
+        return sum(b.n_traj for b in self.blocks)
 
 
 class Server:
@@ -83,7 +107,7 @@ class Server:
 
     def __init__(self, n_traj: int = 512, chunk_steps: int = 256, burn_in0: int = 64,
                  min_pairs: int = 4096, mem_cap_bytes: float = 100e9, workers: int = 8,
-                 max_steps: int = 1 << 20, device="cuda"):
+                 max_steps: int = 1 << 20, grow_rounds: int = 4, max_traj: int = 1 << 16, device="cuda"):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -93,6 +117,8 @@ class Server:
         self.min_pairs = min_pairs
         self.cap = mem_cap_bytes
         self.max_steps = max_steps
+        self.grow_rounds = grow_rounds
+        self.max_traj = max(max_traj, n_traj)
         self.pool = ThreadPoolExecutor(max_workers=workers)
         self.prepared: "queue.Queue" = queue.Queue()
         self.waiting = []          # prepared, not yet admitted (arrival order)
@@ -100,6 +126,8 @@ class Server:
         self.done = []
         self.rejected = []         # queries needing more bytes than the cap
         self.failed = []           # (qid, error) of queries whose preparation failed
+        self.cancelled = []        # qids cancelled before completing
+        self._cancel = set()
         self.in_use = 0
         self.stream = torch.cuda.Stream(self.dev)
         self.pending = 0
@@ -119,7 +147,10 @@ class Server:
             with self.torch.cuda.stream(self.stream):
                 plan.device_image(self.dev)
                 bufs = api.alloc_buffers(plan, self.n_traj, self.dev)
-            nbytes = query_bytes(plan, self.n_traj)
+            # admission reserves the device bytes of the largest size the query may
+            # grow to, so that growth never waits for memory and results stay
+            # independent of the other queries
+            nbytes = query_bytes(plan, self.max_traj)
             self.prepared.put((q, plan, bufs, n, time.perf_counter() - t0, nbytes))
         except Exception as exc:  # a query that cannot be prepared fails alone
             with self.lock:
@@ -132,6 +163,39 @@ class Server:
         with self.lock:
             self.pending += 1
         self.pool.submit(self._prepare, q)
+
+    def cancel(self, qid: int):
+        """Cancel a query: it is dropped before its next round (or when its
+        preparation finishes) and its device bytes are released.  Other queries'
+        results are unaffected (their draws are keyed by their own ids)."""
+        with self.lock:
+            self._cancel.add(qid)
+
+    def _drop_cancelled(self):
+        with self.lock:
+            if not self._cancel:
+                return
+            # a query that already completed or failed is not cancelled
+            over = {r.qid for r in self.done} | {f[0] for f in self.failed}
+            self._cancel -= over
+            cancel = set(self._cancel)
+        keep = []
+        for item in self.waiting:
+            if item[0].qid in cancel:
+                self._retire(item[0].qid)
+            else:
+                keep.append(item)
+        self.waiting = keep
+        for a in [a for a in self.active if a.q.qid in cancel]:
+            self.active.remove(a)
+            self.in_use -= a.nbytes
+            self._retire(a.q.qid)
+
+    def _retire(self, qid: int):
+        self.cancelled.append(qid)
+        with self.lock:
+            self._cancel.discard(qid)
+            self.pending -= 1
 
     # -- admission ----------------------------------------------------------------------
     def _admit(self):
@@ -152,7 +216,7 @@ class Server:
                 continue
             if self.in_use + nbytes <= self.cap:
                 self.in_use += nbytes
-                self.active.append(_Active(q, plan, bufs, n, prep_s, nbytes, self.burn_in0))
+                self.active.append(_Active(q, plan, bufs, n, prep_s, nbytes, self.burn_in0, self.n_traj))
             else:
                 keep.append(item)
         self.waiting = keep
@@ -160,27 +224,34 @@ class Server:
     # -- one round --------------------------------------------------------------------
     def _round(self):
         torch = self.torch
-        entries = []
-        for a in self.active:
-            entries.append(dict(plan=a.plan, bufs=a.bufs, seed=a.q.seed, meta_ids=a.q.meta_ids,
-                                meta_vals=a.q.meta_vals, step_begin=a.step, count_from=a.count_from,
-                                init=_lib.PBN_INIT_KEYED if a.step == 0 else _lib.PBN_INIT_STATE))
+        entries, owner = [], []
+        for qi, a in enumerate(self.active):
+            for b in a.blocks:
+                entries.append(dict(plan=a.plan, bufs=b.bufs, seed=a.q.seed, meta_ids=a.q.meta_ids,
+                                    meta_vals=a.q.meta_vals, traj_begin=b.traj_begin, step_begin=b.step,
+                                    count_from=b.count_from,
+                                    init=_lib.PBN_INIT_KEYED if b.step == 0 else _lib.PBN_INIT_STATE))
+                owner.append(qi)
         t0 = time.perf_counter()
         with torch.cuda.stream(self.stream):
             B = api.Batch(entries, device=self.dev)
             t1 = time.perf_counter()
             B.run(self.chunk, step_offset=0, stream=self.stream)
-            pooled = torch.stack([a.bufs.pooled for a in self.active]).to("cpu", non_blocking=True)
+            pooled = torch.stack([b.bufs.pooled for a in self.active for b in a.blocks]).to("cpu", non_blocking=True)
         self.stream.synchronize()
         if int(B.status.item()) != 0:
             raise RuntimeError("batch kernel reported an error status")
         t2 = time.perf_counter()
         pooled = pooled.numpy().view(np.uint64)
+        per_query = np.zeros((len(self.active), 5), dtype=np.uint64)
+        for qi, c in zip(owner, pooled):
+            per_query[qi] += c
         finished = []
-        for a, c in zip(self.active, pooled):
-            a.step += self.chunk
+        for a, c in zip(self.active, per_query):
+            for b in a.blocks:
+                b.step += self.chunk
             a.rounds += 1
-            nu = float(a.n) * self.n_traj * self.chunk
+            nu = float(a.n) * a.n_traj * self.chunk
             a.node_updates += nu
             self.node_updates += nu
             if self._decide(a, c):
@@ -202,35 +273,62 @@ class Server:
         pairs = int(c[1] + c[2] + c[3] + c[4])
         if pairs < self.min_pairs and a.step < self.max_steps:
             return False
-        est = api.estimate(c, self.n_traj, a.q.r, a.q.s, a.q.eps, burn_in_used=a.count_from)
+        # trajectories whose window has started (each contributes its first counted state)
+        n_eff = sum(b.n_traj for b in a.blocks if b.step >= b.count_from)
+        burn = min(b.count_from for b in a.blocks)
+        est = api.estimate(c, max(1, n_eff), a.q.r, a.q.s, a.q.eps, burn_in_used=burn)
         if not est.defined or est.m_star == 2**64 - 1:
-            if a.step >= self.max_steps:
+            # the meta-state was never (or always) seen, so the chain's switching rates
+            # are not estimable: stop at the worst-case sample size of a proportion,
+            # (z / r)^2 / 4, and report pi = V / L
+            n_min = math.ceil(0.25 * (est.z / a.q.r) ** 2)
+            if a.step >= self.max_steps or (est.L >= n_min and (int(c[0]) == 0 or int(c[0]) == est.L)):
                 self._finish(a, est, c)
                 return True
             return False
-        if est.m_star > a.count_from:
+        if est.m_star > burn:
+            # restart the windows that began before the burn-in: at the current step
+            # or at m*, whichever is later (ordered before the next round on the
+            # server's stream)
             if a.step >= est.m_star:
-                # restart the counting window after the burn-in (ordered before the
-                # next round on the server's stream)
-                a.count_from = a.step
                 with self.torch.cuda.stream(self.stream):
-                    a.bufs.counts.zero_()
-                    a.bufs.pooled.zero_()
+                    for b in a.blocks:
+                        if b.count_from < est.m_star:
+                            b.count_from = max(b.step, int(est.m_star))
+                            b.bufs.counts.zero_()
+                            b.bufs.pooled.zero_()
             return False
         if est.L >= est.n_star or a.step >= self.max_steps:
             self._finish(a, est, c)
             return True
+        self._maybe_grow(a, est)
         return False
+
+    def _maybe_grow(self, a: _Active, est):
+        """Double the query's trajectories when the states still to count exceed
+        grow_rounds rounds at its current size (reads only the query's own counts)."""
+        per_round = a.n_traj * self.chunk
+        if est.n_star - est.L <= self.grow_rounds * per_round or 2 * a.n_traj > self.max_traj:
+            return
+        nb = a.n_traj
+        with self.torch.cuda.stream(self.stream):
+            bufs = api.alloc_buffers(a.plan, nb, self.dev)
+        # new trajectories take the next ids and count after the query's burn-in
+        burn = max(min(b.count_from for b in a.blocks), int(est.m_star))
+        a.blocks.append(_Block(bufs, a.n_traj, nb, burn))
+        self.stats["grown"] = self.stats.get("grown", 0) + 1
 
     def _finish(self, a: _Active, est, c):
         self.done.append(Result(
             qid=a.q.qid, pi=est.pi, n_star=int(est.n_star), m_star=int(est.m_star), L=int(est.L),
             steps=a.step, rounds=a.rounds, latency=time.perf_counter() - a.q.arrival, prep_s=a.prep_s,
-            node_updates=a.node_updates, alpha=est.alpha, beta=est.beta, counts=[int(x) for x in c]))
+            node_updates=a.node_updates, alpha=est.alpha, beta=est.beta, counts=[int(x) for x in c],
+            n_traj=a.n_traj))
 
     def step(self) -> list:
         """Admit what is ready and run one round (if anything is active)."""
         self._admit()
+        self._drop_cancelled()
         if not self.active:
             return []
         return self._round()

@@ -72,3 +72,55 @@ def test_ranges_partition_the_ids():
             assert a + n == b
         w = [shard.weak_range(r, world, 50) for r in range(world)]
         assert [b for b, _ in w] == [50 * r for r in range(world)]
+
+
+def _publisher(rank, port, total, world, fail):
+    import datetime
+    from torch.distributed import TCPStore
+    store = TCPStore("127.0.0.1", port, world, False, timeout=datetime.timedelta(seconds=30))
+    if fail:
+        raise SystemExit(3)  # the injected failure: this rank exits before publishing
+    from oracle import oracle
+    tb, nt = shard.strong_range(rank, world, total)
+    r = oracle.simulate(synth.tiny12(1).to_text(), 9, tb, nt, 300, meta_ids=[0, 1, 2])
+    shard.publish(store, rank, tb, nt, {"final": r["final"], "counts": r["counts"]})
+
+
+def test_failed_rank_range_is_recomputed(oracle_mod):
+    """Three ranks share 45 trajectories; rank 2 fails before publishing.  The
+    collector times out on it, finds its id range missing and recomputes it; the
+    union equals one single-process run bit for bit."""
+    import datetime
+    from torch.distributed import TCPStore
+    world, total = 3, 45
+    port = _free_port()
+    store = TCPStore("127.0.0.1", port, world, True, timeout=datetime.timedelta(seconds=30),
+                     wait_for_workers=False)
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_publisher, args=(r, port, total, world, r == 2)) for r in (1, 2)]
+    for p in procs:
+        p.start()
+    text = synth.tiny12(1).to_text()
+    tb0, nt0 = shard.strong_range(0, world, total)
+    r0 = oracle_mod.simulate(text, 9, tb0, nt0, 300, meta_ids=[0, 1, 2])
+    parts = {0: (tb0, nt0, {"final": r0["final"], "counts": r0["counts"]})}
+    parts.update(shard.collect(store, [1, 2], timeout_s=20))
+    for p in procs:
+        p.join(timeout=120)
+    assert procs[0].exitcode == 0 and procs[1].exitcode == 3
+    assert sorted(parts) == [0, 1]
+    miss = shard.missing_ranges([(b, n) for b, n, _ in parts.values()], total)
+    assert miss == [shard.strong_range(2, world, total)]
+    for b, n in miss:
+        r = oracle_mod.simulate(text, 9, b, n, 300, meta_ids=[0, 1, 2])
+        parts["re" + str(b)] = (b, n, {"final": r["final"], "counts": r["counts"]})
+    ordered = sorted(parts.values(), key=lambda t: t[0])
+    ref = oracle_mod.simulate(text, 9, 0, total, 300, meta_ids=[0, 1, 2])
+    assert np.array_equal(np.concatenate([a["final"] for _, _, a in ordered]), ref["final"])
+    assert np.array_equal(np.concatenate([a["counts"] for _, _, a in ordered]), ref["counts"])
+
+
+def test_missing_ranges():
+    assert shard.missing_ranges([(0, 10), (20, 5)], 30) == [(10, 10), (25, 5)]
+    assert shard.missing_ranges([], 7) == [(0, 7)]
+    assert shard.missing_ranges([(0, 7)], 7) == []
