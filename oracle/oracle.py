@@ -67,6 +67,12 @@ def lib():
             L.orc_transition_matrix.restype = i32
             L.orc_simulate_sem.argtypes = L.orc_simulate.argtypes + [i32]
             L.orc_simulate_sem.restype = i32
+            L.orc_simulate_ex.argtypes = L.orc_simulate.argtypes + [i32, i32]
+            L.orc_simulate_ex.restype = i32
+            L.orc_draws_ex.argtypes = [cp, u64, u64, u64, i32, vp, vp]
+            L.orc_draws_ex.restype = i32
+            L.orc_geo_thresholds.argtypes = [ctypes.c_double, vp]
+            L.orc_geo_thresholds.restype = None
             L.orc_transition_matrix_sem.argtypes = [cp, i32, vp]
             L.orc_transition_matrix_sem.restype = i32
             L.orc_leaves.argtypes = [cp, vp, i32, vp]
@@ -102,9 +108,11 @@ def shape(text: str):
 
 def simulate(text: str, seed: int, traj_begin: int, n_traj: int, n_steps: int, *,
              meta_ids=(), meta_vals=None, step_begin: int = 0, count_from: int = 0,
-             init_states=None, trace: bool = False, nthreads: int = 1, semantics: int = 0):
+             init_states=None, trace: bool = False, nthreads: int = 1, semantics: int = 0,
+             sampler: int = 0):
     """Run the Eq. 1 simulator of the unreduced network (semantics=1: the node-wise
-    variant, a flipped node negates and the others apply their functions).
+    variant, a flipped node negates and the others apply their functions; sampler=1:
+    the geometric perturbation sampler instead of the bit-sliced levels).
 
     Returns dict(final=(n_traj, n) uint8, counts=(n_traj, 5) uint64 as
     [V, n00, n01, n10, n11], trace=(n_traj, n_steps, n) uint8 or None)."""
@@ -119,9 +127,9 @@ def simulate(text: str, seed: int, traj_begin: int, n_traj: int, n_steps: int, *
     final = np.zeros((n_traj, n), dtype=np.uint8)
     counts = np.zeros((n_traj, 5), dtype=np.uint64)
     tr = np.zeros((n_traj, n_steps, n), dtype=np.uint8) if trace else None
-    rc = lib().orc_simulate_sem(text.encode(), seed, traj_begin, n_traj, step_begin, n_steps,
-                                count_from, _ptr(meta_ids), _ptr(meta_vals), len(meta_ids),
-                                _ptr(init), _ptr(final), _ptr(counts), _ptr(tr), nthreads, semantics)
+    rc = lib().orc_simulate_ex(text.encode(), seed, traj_begin, n_traj, step_begin, n_steps,
+                               count_from, _ptr(meta_ids), _ptr(meta_vals), len(meta_ids),
+                               _ptr(init), _ptr(final), _ptr(counts), _ptr(tr), nthreads, semantics, sampler)
     if rc:
         raise ValueError(f"orc_simulate failed (rc={rc})")
     return {"final": final, "counts": counts, "trace": tr}
@@ -149,6 +157,24 @@ def thresholds(text: str, node: int):
     if l < 0:
         raise ValueError(f"orc_thresholds failed (rc={l})")
     return int(P.value), [int(t) for t in T[: l - 1]]
+
+
+def gamma(text: str, seed: int, traj: int, step: int, sampler: int = 0):
+    """Perturbation vector of one (trajectory, step) under the given sampler; any."""
+    n = shape(text)[0]
+    g = np.zeros(n, dtype=np.uint8)
+    a = ctypes.c_int()
+    rc = lib().orc_draws_ex(text.encode(), seed, traj, step, sampler, _ptr(g), ctypes.byref(a))
+    if rc:
+        raise ValueError(f"orc_draws_ex failed (rc={rc})")
+    return g, bool(a.value)
+
+
+def geo_thresholds(p: float) -> list:
+    """The geometric sampler's thresholds G[0..63] (integers below 2^64)."""
+    G = np.zeros(64, dtype=np.uint64)
+    lib().orc_geo_thresholds(p, _ptr(G))
+    return [int(x) for x in G]
 
 
 def transition_matrix(text: str, semantics: int = 0) -> np.ndarray:

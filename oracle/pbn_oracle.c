@@ -36,6 +36,13 @@
  *     C_j = C_{j-1} + c_j summed left to right in fp64.
  *   INIT (domain 3, step 0): word w of s(0) is x1:x0 of index w/2 if w is
  *     even, x3:x2 otherwise; bit b is node 64w + b.
+ *   GEO (domain 4, the second perturbation sampler): for 64-node word w with L
+ *     valid lanes, decisions j = 0, 1, ... take the 64-bit U_j = x1:x0 (w even)
+ *     or x3:x2 (w odd) of index (w / 2) << 8 | j.  With m lanes left from lane
+ *     pos, the decision stops the word if U_j >= G[m-1]; otherwise lane pos + k is
+ *     perturbed for the least k with U_j < G[k], and pos moves to pos + k + 1.
+ *     G[k] = floor(2^64 (1 - (1 - P/2^32)^(k+1))): the first-perturbed-lane law
+ *     of i.i.d. Bernoulli(P/2^32) lanes, to 2^-64.
  *   Truth tables: function with parents (a_0..a_{k-1}) outputs bit
  *     x = sum_b s[a_b] 2^b of its table.
  */
@@ -51,7 +58,7 @@
 #define ORC_EINVAL -1
 #define ORC_ENOMEM -3
 
-enum { DOM_PERT = 1, DOM_SEL = 2, DOM_INIT = 3 };
+enum { DOM_PERT = 1, DOM_SEL = 2, DOM_INIT = 3, DOM_GEO = 4 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, written from the round function of Salmon et al. (SC'11):  */
@@ -257,17 +264,59 @@ static void sel_thresholds(const onode *nd, uint64_t *T) {
     }
 }
 
+/* Thresholds of the geometric sampler, G[k] = floor(2^64 (1 - (1 - P/2^32)^(k+1)))
+ * for k = 0..63, in exact integer arithmetic: with a = 2^32 - P,
+ * (1 - P/2^32)^(k+1) = a^(k+1) / 2^(32(k+1)), so
+ * G[k] = 2^64 - ceil(a^(k+1) / 2^(32(k+1) - 64)).  a^(k+1) is kept as
+ * little-endian 32-bit limbs. */
+static void geo_thresholds(uint64_t P, uint64_t G[64]) {
+    if (P == 0) {
+        for (int k = 0; k < 64; ++k) G[k] = 0;
+        return;
+    }
+    const uint64_t a = ((uint64_t)1 << 32) - P; /* 1 <= a < 2^32 */
+    uint32_t limb[70];
+    int nl = 1;
+    limb[0] = 1;
+    for (int k = 0; k < 64; ++k) {
+        /* limb <- limb * a */
+        uint64_t carry = 0;
+        for (int i = 0; i < nl; ++i) {
+            uint64_t v = (uint64_t)limb[i] * a + carry;
+            limb[i] = (uint32_t)v;
+            carry = v >> 32;
+        }
+        if (carry) limb[nl++] = (uint32_t)carry;
+        /* q = ceil(a^(k+1) / 2^(32(k+1) - 64)) */
+        uint64_t q;
+        if (k == 0) {
+            q = a << 32; /* exact: the divisor is 2^-32 */
+        } else {
+            const int drop = k - 1; /* limbs shifted out */
+            uint64_t lo = drop < nl ? limb[drop] : 0, hi = drop + 1 < nl ? limb[drop + 1] : 0;
+            q = (hi << 32) | lo;
+            int rest = 0;
+            for (int i = 0; i < drop && i < nl; ++i) rest |= limb[i] != 0;
+            q += (uint64_t)rest;
+        }
+        G[k] = (uint64_t)0 - q; /* 2^64 - q, q >= 1 */
+    }
+}
+
 /* Per-network data the simulator needs besides the model itself. */
 typedef struct {
     const onet *g;
     uint64_t P;
     int *rank;        /* rank among nodes with >= 2 functions, or -1 */
     uint64_t *thr;    /* thr[i * 16 + j] = T_j of node i (j < 16) */
+    uint64_t G[64];   /* thresholds of the geometric sampler */
+    int sampler;      /* 0: bit-sliced levels (PERT), 1: geometric (GEO) */
 } octx;
 
 static int ctx_init(octx *cx, const onet *g) {
     cx->g = g;
     cx->P = pert_threshold(g->p);
+    geo_thresholds(cx->P, cx->G);
     cx->rank = (int *)malloc((size_t)g->n * sizeof(int));
     cx->thr = (uint64_t *)calloc((size_t)g->n * 16, sizeof(uint64_t));
     if (!cx->rank || !cx->thr) return ORC_ENOMEM;
@@ -287,7 +336,10 @@ static void ctx_free(octx *cx) {
 
 /* gamma_i for all nodes of one (trajectory, step): the plain definition,
  * all 32 levels assembled into u_i and compared with P. */
+static int draw_geo(const octx *cx, uint64_t seed, uint64_t traj, uint64_t step, uint8_t *gamma);
+
 static int draw_pert(const octx *cx, uint64_t seed, uint64_t traj, uint64_t step, uint8_t *gamma) {
+    if (cx->sampler == 1) return draw_geo(cx, seed, traj, step, gamma);
     int n = cx->g->n;
     int W = (n + 63) / 64;
     int any = 0;
@@ -306,6 +358,35 @@ static int draw_pert(const octx *cx, uint64_t seed, uint64_t traj, uint64_t step
             for (int l = 0; l < 32; ++l) u |= ((level[l] >> b) & 1u) << (31 - l);
             gamma[i] = (uint8_t)(u < cx->P);
             any |= gamma[i];
+        }
+    }
+    return any;
+}
+
+/* gamma_i of the geometric sampler (GEO): per word, the first perturbed lane among
+ * the remaining ones is drawn by inverting its distribution with one 64-bit
+ * uniform, until a uniform says that none of the remaining lanes is perturbed. */
+static int draw_geo(const octx *cx, uint64_t seed, uint64_t traj, uint64_t step, uint8_t *gamma) {
+    int n = cx->g->n;
+    int W = (n + 63) / 64;
+    int any = 0;
+    for (int i = 0; i < n; ++i) gamma[i] = 0;
+    for (int w = 0; w < W; ++w) {
+        int L = n - 64 * w < 64 ? n - 64 * w : 64;
+        int pos = 0;
+        uint32_t j = 0;
+        while (pos < L) {
+            int m = L - pos;
+            uint32_t x[4];
+            keyed_block(seed, traj, step, DOM_GEO, ((uint32_t)(w / 2) << 8) | j, x);
+            uint64_t U = (w % 2 == 0) ? (((uint64_t)x[1] << 32) | x[0]) : (((uint64_t)x[3] << 32) | x[2]);
+            ++j;
+            if (U >= cx->G[m - 1]) break;
+            int k = 0;
+            while (U >= cx->G[k]) ++k;
+            gamma[64 * w + pos + k] = 1;
+            any = 1;
+            pos += k + 1;
         }
     }
     return any;
@@ -422,19 +503,19 @@ out:
  * NULL for the keyed initial state (then step_begin must be 0).  counts gets
  * [V, n00, n01, n10, n11] per trajectory over states with index >= count_from.
  * trace (optional) gets the state after every step: n_traj x n_steps x n. */
-int orc_simulate_sem(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
-                     uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
-                     const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
-                     const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
-                     uint8_t *trace, int nthreads, int semantics);
+int orc_simulate_ex(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
+                    uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
+                    const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
+                    const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
+                    uint8_t *trace, int nthreads, int semantics, int sampler);
 
 int orc_simulate(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
                  uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
                  const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
                  const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
                  uint8_t *trace, int nthreads) {
-    return orc_simulate_sem(text, seed, traj_begin, n_traj, step_begin, n_steps, count_from, meta_ids,
-                            meta_vals, n_meta, init_states, final_states, counts, trace, nthreads, 0);
+    return orc_simulate_ex(text, seed, traj_begin, n_traj, step_begin, n_steps, count_from, meta_ids,
+                           meta_vals, n_meta, init_states, final_states, counts, trace, nthreads, 0, 0);
 }
 
 /* As orc_simulate; semantics 0 = Eq. 1, 1 = node-wise flips. */
@@ -443,7 +524,18 @@ int orc_simulate_sem(const char *text, uint64_t seed, uint64_t traj_begin, uint6
                      const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
                      const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
                      uint8_t *trace, int nthreads, int semantics) {
+    return orc_simulate_ex(text, seed, traj_begin, n_traj, step_begin, n_steps, count_from, meta_ids,
+                           meta_vals, n_meta, init_states, final_states, counts, trace, nthreads, semantics, 0);
+}
+
+/* As orc_simulate_sem; sampler 0 = bit-sliced levels (PERT), 1 = geometric (GEO). */
+int orc_simulate_ex(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
+                    uint64_t step_begin, uint64_t n_steps, uint64_t count_from,
+                    const int32_t *meta_ids, const uint8_t *meta_vals, int n_meta,
+                    const uint8_t *init_states, uint8_t *final_states, uint64_t *counts,
+                    uint8_t *trace, int nthreads, int semantics, int sampler) {
     if (semantics != 0 && semantics != 1) return ORC_EINVAL;
+    if (sampler != 0 && sampler != 1) return ORC_EINVAL;
     onet *g = NULL;
     int rc = parse_net(text, &g);
     if (rc) return rc;
@@ -454,6 +546,7 @@ int orc_simulate_sem(const char *text, uint64_t seed, uint64_t traj_begin, uint6
     memset(&cx, 0, sizeof(cx));
     rc = ctx_init(&cx, g);
     if (rc) { ctx_free(&cx); net_free(g); return rc; }
+    cx.sampler = sampler;
     if (nthreads < 1) nthreads = 1;
     if ((uint64_t)nthreads > n_traj) nthreads = n_traj > 0 ? (int)n_traj : 1;
     sim_job *jobs = (sim_job *)calloc((size_t)nthreads, sizeof(sim_job));
@@ -504,6 +597,28 @@ int orc_draws(const char *text, uint64_t seed, uint64_t traj, uint64_t step,
     net_free(g);
     return rc;
 }
+
+/* The keyed draws of one (trajectory, step) under a given perturbation sampler. */
+int orc_draws_ex(const char *text, uint64_t seed, uint64_t traj, uint64_t step, int sampler,
+                 uint8_t *gamma, int *any) {
+    onet *g = NULL;
+    int rc = parse_net(text, &g);
+    if (rc) return rc;
+    octx cx;
+    memset(&cx, 0, sizeof(cx));
+    rc = ctx_init(&cx, g);
+    if (!rc) {
+        cx.sampler = sampler;
+        int a = draw_pert(&cx, seed, traj, step, gamma);
+        if (any) *any = a;
+    }
+    ctx_free(&cx);
+    net_free(g);
+    return rc;
+}
+
+/* The geometric sampler's thresholds G[0..63] for perturbation rate p. */
+void orc_geo_thresholds(double p, uint64_t *G) { geo_thresholds(pert_threshold(p), G); }
 
 /* Integer thresholds of node i: P, then T_1..T_{l-1}.  Returns l. */
 int orc_thresholds(const char *text, int node, uint64_t *P, uint64_t *T) {

@@ -128,6 +128,78 @@ def test_perturbation_rate_binomial(oracle_mod):
     assert abs(pair / T - pe * pe) < 5 * sd2 + 1e-12
 
 
+# ------------------------------------------------------ geometric sampler ----
+def test_geo_thresholds_closed_forms(oracle_mod):
+    """G[k] = floor(2^64 (1 - (1 - p')^(k+1))): for p = 1/2 the powers are dyadic,
+    G[k] = 2^64 - 2^(63 - k); G[0] = P 2^32 for any p; p = 0 gives 0; increasing."""
+    G = oracle_mod.geo_thresholds(0.5)
+    assert G == [2**64 - 2**(63 - k) for k in range(64)]
+    for p in (1e-4, 0.01, 0.3, 0.75):
+        G = oracle_mod.geo_thresholds(p)
+        P = math.floor(p * 2**32)
+        assert G[0] == P * 2**32
+        assert all(G[k] < G[k + 1] or G[k] == 2**64 - 1 for k in range(63))
+        assert G[63] < 2**64
+    assert oracle_mod.geo_thresholds(0.0) == [0] * 64
+
+
+def test_geo_sampler_rate_and_independence(oracle_mod):
+    """The geometric sampler draws i.i.d. Bernoulli(P / 2^32) lanes: per-lane rate
+    on full and partial words and pairwise independence within 5 sigma."""
+    n, p = 70, 0.05
+    text = _net_const(n, p)
+    pe = math.floor(p * 2**32) / 2**32
+    hits = np.zeros(n)
+    pair = pair2 = 0
+    T = 3000
+    for t in range(T):
+        g, _ = oracle_mod.gamma(text, 5, t, 3 * t + 1, sampler=1)
+        hits += g
+        pair += int(g[3]) * int(g[66])
+        pair2 += int(g[10]) * int(g[11])
+    sd = math.sqrt(pe * (1 - pe) / T)
+    for i in range(n):
+        assert abs(hits[i] / T - pe) < 5 * sd + 1e-12, i
+    sd2 = math.sqrt(pe * pe * (1 - pe * pe) / T)
+    assert abs(pair / T - pe * pe) < 5 * sd2 + 1e-12
+    assert abs(pair2 / T - pe * pe) < 5 * sd2 + 1e-12
+
+
+def test_geo_sampler_word_law(oracle_mod):
+    """A 3-node network at p = 0.3: the frequency of each of the 8 perturbation
+    patterns follows the product of independent Bernoulli(p') lanes (5 sigma)."""
+    p = 0.3
+    text = _net_const(3, p)
+    pe = math.floor(p * 2**32) / 2**32
+    T = 20000
+    cnt = np.zeros(8)
+    for t in range(T):
+        g, _ = oracle_mod.gamma(text, 11, t, 7, sampler=1)
+        cnt[int(g[0]) + 2 * int(g[1]) + 4 * int(g[2])] += 1
+    for pat in range(8):
+        k = bin(pat).count("1")
+        q = pe**k * (1 - pe) ** (3 - k)
+        assert abs(cnt[pat] / T - q) < 5 * math.sqrt(q * (1 - q) / T), pat
+
+
+def test_geo_sampler_reaches_exact_pi(oracle_mod):
+    """With the geometric sampler the n = 12 network's meta-state frequency still
+    agrees with pi(meta) of the exact matrix (same law to 2^-64)."""
+    from paper_1605_00854_gb300 import synth
+    text = synth.tiny12(1).to_text()
+    meta = [0, 1, 2]
+    pi, _ = oracle_mod.stationary(oracle_mod.transition_matrix(text))
+    target = oracle_mod.meta_probability(pi, 12, meta)
+    r = oracle_mod.simulate(text, 1, 0, 64, 10000, meta_ids=meta, count_from=100, nthreads=8, sampler=1)
+    c = r["counts"].astype(np.float64)
+    per = c[:, 0] / (c[:, 1:].sum(axis=1) + 1)
+    se = per.std(ddof=1) / math.sqrt(len(per))
+    assert abs(per.mean() - target) < 5 * se + 1e-3
+    # and it is a different stream of draws than the bit-sliced sampler
+    r0 = oracle_mod.simulate(text, 1, 0, 64, 10000, meta_ids=meta, count_from=100, nthreads=8)
+    assert not np.array_equal(r0["counts"], r["counts"])
+
+
 # ---------------------------------------------------------------- selection ----
 def test_selection_thresholds_dyadic(oracle_mod):
     text = golden("tiny2.pbn")
