@@ -310,6 +310,13 @@ def run_ours(args):
             except _lib.PbnError:
                 continue
             variants.append((f"compiled_grouped_{fname}", pf, _lib.PBN_KERNEL_COMPILED))
+        # the second perturbation sampler (a different draw contract, same law)
+        pg = api.Plan(red, max_inputs=max_inputs, sampler=_lib.PBN_PERT_GEOMETRIC)
+        try:
+            pg.compile(_lib.PBN_COMPILE_INTERLEAVED)
+            variants.append(("compiled_grouped_interleaved_geometric_sampler", pg, _lib.PBN_KERNEL_COMPILED))
+        except _lib.PbnError:
+            pass
         for name, pl, kk in variants:
             b2 = api.alloc_buffers(pl, T, dev)
             img2 = pl.device_image(dev)

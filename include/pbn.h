@@ -152,6 +152,21 @@ int pbn_reduce_rule(const pbn_net* net, const uint32_t* interest, uint32_t n_int
 #define PBN_SEM_EQ1 0u
 #define PBN_SEM_NODEWISE 1u
 
+/* Perturbation sampler of a plan (both give i.i.d. Bernoulli(p') lanes, p' = P/2^32,
+ * from different keyed draws, so their trajectories differ).
+ * PBN_PERT_BITSLICED is the keyed contract's PERT domain: bit-sliced comparison of
+ * every lane's 32-bit uniform with P, level by level (a 64-lane word needs about
+ * 4 Philox blocks per step).
+ * PBN_PERT_GEOMETRIC draws, per 64-node word, the first perturbed lane among the
+ * remaining ones by inverting its distribution with one 64-bit uniform (GEO domain,
+ * index (w / 2) << 8 | j, x1:x0 for even w, x3:x2 for odd w), against the
+ * thresholds G[k] = floor(2^64 (1 - (1 - p')^(k+1))) computed in exact integer
+ * arithmetic: with m lanes left from lane pos, U >= G[m-1] ends the word, else lane
+ * pos + k is perturbed for the least k with U < G[k].  One Philox block decides two
+ * words in the common case; the law equals the bit-sliced one to 2^-64. */
+#define PBN_PERT_BITSLICED 0u
+#define PBN_PERT_GEOMETRIC 1u
+
 typedef struct {
     uint32_t mode;          /* PBN_PLAN_GROUPED or PBN_PLAN_PLAIN */
     uint32_t max_inputs;    /* max distinct input nodes of a merged group (1..24, default 8) */
@@ -162,6 +177,8 @@ typedef struct {
     uint64_t smem_budget;   /* bytes of plan image that may be staged into shared
                                memory (0 = default 160 KiB); larger tables are read
                                from global memory */
+    uint32_t sampler;       /* PBN_PERT_BITSLICED (default) or PBN_PERT_GEOMETRIC */
+    uint32_t reserved;
 } pbn_group_params;
 
 /* Fill *prm with the defaults above. */
@@ -205,6 +222,8 @@ typedef struct {
                                 max_inputs: each of its functions keeps its own table over
                                 its own inputs, and the node's choice selects the output */
     uint32_t semantics;      /* PBN_SEM_EQ1 or PBN_SEM_NODEWISE */
+    uint32_t sampler;        /* PBN_PERT_BITSLICED or PBN_PERT_GEOMETRIC */
+    uint32_t reserved;
     double ops_per_step;     /* algorithmic 32-bit integer operations of one trajectory-step:
                                 Philox blocks at 56 ops (9 rounds of 2 mul.hi, 2 mul.lo,
                                 2 xor3), 12 per bit-sliced level pair, the expected number of

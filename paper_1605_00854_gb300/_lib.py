@@ -27,6 +27,8 @@ PBN_REDUCE_REACH = 1
 PBN_PLAN_GROUPED = 0
 PBN_SEM_EQ1 = 0
 PBN_SEM_NODEWISE = 1
+PBN_PERT_BITSLICED = 0
+PBN_PERT_GEOMETRIC = 1
 PBN_PLAN_PLAIN = 1
 PBN_INIT_KEYED = 0
 PBN_INIT_STATE = 1
@@ -55,7 +57,7 @@ class NetDesc(ctypes.Structure):
 
 class GroupParams(ctypes.Structure):
     _fields_ = [("mode", u32), ("max_inputs", u32), ("max_width", u32), ("semantics", u32),
-                ("theta", f64), ("smem_budget", u64)]
+                ("theta", f64), ("smem_budget", u64), ("sampler", u32), ("reserved", u32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -64,7 +66,8 @@ class PlanInfo(ctypes.Structure):
                 ("m_found", u32), ("sum_weights", u64), ("table_bytes", u64),
                 ("image_bytes", u64), ("stage_bytes", u64), ("tables_in_smem", u32),
                 ("total_inputs", u32), ("n_multi", u32), ("total_thresholds", u32),
-                ("n_split", u32), ("semantics", u32), ("ops_per_step", f64)]
+                ("n_split", u32), ("semantics", u32), ("sampler", u32), ("reserved", u32),
+                ("ops_per_step", f64)]
 
 
 class BatchNet(ctypes.Structure):

@@ -110,11 +110,12 @@ class Net:
 
 def group_params(mode: int = _lib.PBN_PLAN_GROUPED, max_inputs: int = 8, max_width: int = 32,
                  theta: float = 65536.0, smem_budget: int = 0,
-                 semantics: int = _lib.PBN_SEM_EQ1) -> _lib.GroupParams:
+                 semantics: int = _lib.PBN_SEM_EQ1, sampler: int = _lib.PBN_PERT_BITSLICED) -> _lib.GroupParams:
     p = _lib.GroupParams()
     _lib.load().pbn_group_params_default(ctypes.byref(p))
     p.mode, p.max_inputs, p.max_width, p.theta = mode, max_inputs, max_width, theta
     p.semantics = semantics
+    p.sampler = sampler
     if smem_budget:
         p.smem_budget = smem_budget
     return p

@@ -55,7 +55,8 @@ struct alignas(16) NetDesc {
     uint32_t off_selslot, off_thr, off_inputs, off_selblk;
     uint32_t off_ret, off_pos, off_tables, specs_in_smem;
     uint32_t nt, off_gorder, n_groups, lg;
-    uint32_t off_subs, per_node, pad1, pad2;
+    uint32_t off_subs, per_node, sampler, off_geo;
+    uint64_t geo_full, geo_last;
     uint32_t meta_row[kMetaRows];
     uint32_t meta_mask[kMetaRows];
     uint32_t meta_val[kMetaRows];
@@ -87,7 +88,8 @@ struct ItemView {
     uint32_t n_traj, n_steps, kv0, kp0, pairs, count_first, init;
     uint32_t n, W, W32, n_sel, P, hmax;
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret,
-        off_pos, off_tables, n_groups, off_subs, per_node;
+        off_pos, off_tables, n_groups, off_subs, per_node, sampler, off_geo;
+    uint64_t geo_full, geo_last;
     uint32_t n_meta_rows;
     const uint32_t* meta_row;
     const uint32_t* meta_mask;
@@ -192,6 +194,10 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
         V.off_gorder = D.off_gorder;
         V.off_subs = D.off_subs;
         V.per_node = D.per_node;
+        V.sampler = D.sampler;
+        V.off_geo = D.off_geo;
+        V.geo_full = D.geo_full;
+        V.geo_last = D.geo_last;
         V.n_groups = D.n_groups;
         V.off_thr = D.off_thr;
         V.off_inputs = D.off_inputs;
@@ -353,6 +359,14 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
             D.off_gorder = H.off_gorder;
             D.off_subs = H.off_subs;
             D.per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
+            D.sampler = H.sampler;
+            D.off_geo = H.off_geo;
+            {
+                const uint64_t* G = reinterpret_cast<const uint64_t*>(plan->image.data() + H.off_geo);
+                const uint32_t nl = H.n & 63u;
+                D.geo_full = G[63];
+                D.geo_last = G[(nl ? nl : 64u) - 1];
+            }
             D.n_groups = H.n_groups;
             D.off_thr = H.off_thr;
             D.off_inputs = H.off_inputs;

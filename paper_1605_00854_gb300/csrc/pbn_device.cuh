@@ -20,6 +20,7 @@ typedef unsigned char uint8_t;
 #define PBN_DOM_PERT 1u /* Philox counter domains (c3 = domain << 28 | index) */
 #define PBN_DOM_SEL 2u
 #define PBN_DOM_INIT 3u
+#define PBN_DOM_GEO 4u
 
 /* Launch parameters of a compiled plan kernel. */
 typedef struct {

@@ -570,6 +570,41 @@ void partition(const pbn_net& g, const pbn_group_params& prm, PlanParts* pp) {
 
 size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
+/* Thresholds of the geometric perturbation sampler:
+ * G[k] = floor(2^64 (1 - (1 - P/2^32)^(k+1))), k = 0..63.  With a = 2^32 - P the
+ * power is a^(k+1) / 2^(32(k+1)), so G[k] = 2^64 - ceil(a^(k+1) 2^(64 - 32(k+1)));
+ * a^(k+1) is built exactly in 32-bit limbs (at most 2048 bits). */
+void geometric_thresholds(uint32_t P, uint64_t G[64]) {
+    if (P == 0) {
+        for (int k = 0; k < 64; ++k) G[k] = 0;
+        return;
+    }
+    const uint64_t a = (UINT64_C(1) << 32) - P;
+    std::vector<uint32_t> pw(1, 1u); /* a^(k+1), least significant limb first */
+    for (int k = 0; k < 64; ++k) {
+        uint64_t carry = 0;
+        for (uint32_t& l : pw) {
+            const uint64_t v = (uint64_t)l * a + carry;
+            l = (uint32_t)v;
+            carry = v >> 32;
+        }
+        if (carry) pw.push_back((uint32_t)carry);
+        uint64_t q;
+        if (k == 0) {
+            q = a << 32;
+        } else {
+            /* a^(k+1) / 2^(32 (k - 1)), rounded up: limbs k-1 and k, plus one if any
+             * lower limb is nonzero */
+            const size_t lo = (size_t)k - 1;
+            q = (lo < pw.size() ? pw[lo] : 0u) | ((uint64_t)(lo + 1 < pw.size() ? pw[lo + 1] : 0u) << 32);
+            bool rem = false;
+            for (size_t i = 0; i < lo && i < pw.size(); ++i) rem = rem || pw[i] != 0;
+            q += rem ? 1u : 0u;
+        }
+        G[k] = (uint64_t)0 - q;
+    }
+}
+
 int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     PlanParts pp;
     partition(g, prm, &pp);
@@ -828,6 +863,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.n_sel = (uint32_t)selblk.size();
     H.P = (uint32_t)pbn::pert_threshold(g.p);
     H.semantics = prm.semantics;
+    H.sampler = prm.sampler;
     size_t off = align16(sizeof(pbn_img_header));
     H.off_words = (uint32_t)off; off = align16(off + words.size() * 4);
     H.off_groups = (uint32_t)off; off = align16(off + grec.size() * sizeof(pbn_img_group));
@@ -841,6 +877,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
     H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
     H.off_pos = (uint32_t)off; off = align16(off + plan->pos.size() * 4);
+    H.off_geo = (uint32_t)off; off = align16(off + 64 * 8);
     if (off >= (UINT64_C(1) << 31)) return fail(PBN_ETOOBIG, "device image of %zu bytes", off);
     H.image_bytes = (uint32_t)off;
     const uint64_t budget = prm.smem_budget ? prm.smem_budget : 160 * 1024;
@@ -862,6 +899,11 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     if (!subs.empty()) memcpy(img + H.off_subs, subs.data(), subs.size() * 4);
     memcpy(img + H.off_ret, ret.data(), ret.size() * 8);
     memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
+    {
+        uint64_t G[64];
+        geometric_thresholds(H.P, G);
+        memcpy(img + H.off_geo, G, sizeof(G));
+    }
     if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);
     plan->hdr = H;
     plan->per_traj_smem = 4 * (2 * (W32 + 1) + (H.n_sel | 1u));
@@ -885,6 +927,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     I.n_multi = (uint32_t)mrec.size();
     I.n_split = n_split;
     I.semantics = prm.semantics;
+    I.sampler = prm.sampler;
     I.total_thresholds = (uint32_t)thr.size();
     /* algorithmic work of one trajectory-step (the roofline's per-unit figure) */
     {
@@ -896,7 +939,9 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
                 for (int h = 0; h < 16; ++h) blocks += 1.0 - std::pow(1.0 - std::ldexp(1.0, -2 * h), (double)k);
             }
         }
-        const double pert = blocks * (56.0 + 12.0) + 4.0;
+        double pert = blocks * (56.0 + 12.0) + 4.0;
+        if (prm.sampler == PBN_PERT_GEOMETRIC) /* one block per word pair, a 64-bit compare per word */
+            pert = H.P ? 56.0 * (double)((W + 1) / 2) + 4.0 * (double)W + 4.0 : 4.0;
         const double nonpert = 56.0 * H.n_sel + 2.0 * (double)thr.size() + (double)mrec.size() +
                                3.0 * (double)total_inputs + 5.0 * (double)(H.n_groups + n_split) +
                                2.0 * (double)(W32 / 2);
@@ -927,7 +972,8 @@ extern "C" int pbn_group(const pbn_net* net, const pbn_group_params* prm_in, pbn
         return fail(PBN_EINVAL, "pbn_group: unknown mode %u", prm.mode);
     if (prm.max_inputs < 1 || prm.max_inputs > 24 || prm.max_width < 1 || prm.max_width > 32 ||
         !(prm.theta >= 1.0) || (prm.smem_budget && prm.smem_budget < 1024) ||
-        (prm.semantics != PBN_SEM_EQ1 && prm.semantics != PBN_SEM_NODEWISE))
+        (prm.semantics != PBN_SEM_EQ1 && prm.semantics != PBN_SEM_NODEWISE) ||
+        (prm.sampler != PBN_PERT_BITSLICED && prm.sampler != PBN_PERT_GEOMETRIC))
         return fail(PBN_EINVAL, "pbn_group: parameter out of range");
     try {
         pbn_plan* plan = new pbn_plan();

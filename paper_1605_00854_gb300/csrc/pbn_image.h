@@ -32,6 +32,7 @@
  *   ret     [W]          uint64 mask of retained lanes of original word w
  *   pos     [n]          uint32 state position (32 * row + bit) of original node i,
  *                        0xFFFFFFFF for a leaf
+ *   geo     [64]         uint64 thresholds G[k] of the geometric perturbation sampler
  * ret and pos serve only the initial state and perturbed steps and are read from
  * global memory; the staged prefix ends at off_tables (specs) or off_ret (specs
  * and tables).
@@ -58,7 +59,9 @@ typedef struct {
     uint32_t stage_bytes;
     uint32_t tables_in_smem;
     uint32_t semantics;  /* PBN_SEM_EQ1 or PBN_SEM_NODEWISE */
-} pbn_img_header; /* 96 bytes */
+    uint32_t sampler;    /* PBN_PERT_BITSLICED or PBN_PERT_GEOMETRIC */
+    uint32_t off_geo;    /* uint64 [64] thresholds of the geometric sampler (global) */
+} pbn_img_header; /* 104 bytes */
 
 /* A group record with l2w == PBN_IMG_SPLIT is a split node: one multi-function node
  * whose q functions each keep their own table of 2^k one-bit entries over their own

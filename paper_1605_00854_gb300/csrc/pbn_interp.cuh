@@ -147,7 +147,36 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
              *         called for every perturbed retained node ---- */
             auto perturb = [&](auto&& flip) -> uint32_t {
                 uint32_t any_l = 0;
-                if (P.P != 0u) {
+                if (P.sampler != 0u) {
+                    /* geometric sampler: per word the first perturbed lane among the
+                     * remaining ones, one 64-bit uniform per decision; one block
+                     * decides a pair of words in the common (no perturbation) case */
+                    const uint64_t* GEO = reinterpret_cast<const uint64_t*>(P.image + P.off_geo);
+                    for (uint32_t wp = lane; 2 * wp < P.W; wp += LG) {
+                        const uint4 x0 = pbn_philox_draw(P, ps, (PBN_DOM_GEO << 28) | (wp << 8));
+                        for (uint32_t h2 = 0; h2 < 2 && 2 * wp + h2 < P.W; ++h2) {
+                            const uint32_t w = 2 * wp + h2;
+                            const bool last = w == P.W - 1;
+                            uint64_t U = h2 ? (((uint64_t)x0.w << 32) | x0.z) : (((uint64_t)x0.y << 32) | x0.x);
+                            if (U >= (last ? P.geo_last : P.geo_full)) continue;
+                            const uint32_t L = (last && nl) ? nl : 64u;
+                            uint32_t pos = 0, j = 0;
+                            for (;;) {
+                                if (U >= __ldg(GEO + (L - pos - 1))) break;
+                                uint32_t k = 0;
+                                while (U >= __ldg(GEO + k)) ++k;
+                                any_l = 1u;
+                                const uint32_t b = pos + k;
+                                if ((RET[w] >> b) & 1ull) flip(POS[64 * w + b]);
+                                pos = b + 1;
+                                if (pos >= L) break;
+                                ++j;
+                                const uint4 x = pbn_philox_draw(P, ps, (PBN_DOM_GEO << 28) | (wp << 8) | j);
+                                U = h2 ? (((uint64_t)x.w << 32) | x.z) : (((uint64_t)x.y << 32) | x.x);
+                            }
+                        }
+                    }
+                } else if (P.P != 0u) {
                     for (uint32_t w = lane; w < P.W; w += LG) {
                         const uint64_t valid = (w == P.W - 1) ? last_lanes : ~0ull;
                         uint32_t und_lo = (uint32_t)valid, und_hi = (uint32_t)(valid >> 32);

@@ -161,6 +161,12 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
 
     std::ostringstream o;
     o << "#include \"pbn_device.cuh\"\n";
+    if (H.sampler == PBN_PERT_GEOMETRIC) {
+        const uint64_t* G = V.at<uint64_t>(H.off_geo);
+        o << "__device__ const unsigned long long GEO_T[64] = {";
+        for (int k = 0; k < 64; ++k) o << (k ? ", " : "") << fmt("0x%016llxull", (unsigned long long)G[k]);
+        o << "};\n";
+    }
     o << "extern \"C\" __global__ void __launch_bounds__(512) pbn_plan_kernel(const pbn_jit_params P) {\n";
     o << "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n";
     if (tab_smem) {
@@ -210,8 +216,11 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         z = zs.str();
     }
     o << "    uint32_t zp = " << z << ";\n    if (P.count_first) cV += zp;\n";
-    const bool interleave = (flags & PBN_COMPILE_INTERLEAVED) != 0;
-    const bool pipelined = (flags & PBN_COMPILE_PIPELINED) != 0;
+    /* the geometric sampler has no level loop to pipeline: its pipelined form is
+     * the interleaved one */
+    const bool geometric = H.sampler == PBN_PERT_GEOMETRIC;
+    const bool pipelined = (flags & PBN_COMPILE_PIPELINED) != 0 && !geometric;
+    const bool interleave = (flags & PBN_COMPILE_INTERLEAVED) != 0 || ((flags & PBN_COMPILE_PIPELINED) != 0 && geometric);
     /* node-wise semantics: every step evaluates the functions and the perturbed
      * nodes (collected in masks) take NOT s */
     const bool nodewise = H.semantics == PBN_SEM_NODEWISE;
@@ -463,7 +472,36 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
          * perturbation levels form one block of independent work */
         if (interleave) emit_sel_draws("      ", "const uint4 ", "U", "ps");
         /* 1. perturbation: the levels of P compiled in */
-        if (Pv && (flags & PBN_COMPILE_PERT_UNROLLED)) {
+        if (Pv && geometric) {
+            /* per word pair one block; the common case is one 64-bit compare per word
+             * against G[L-1]; otherwise the perturbed lanes are found one by one */
+            const uint64_t* G = V.at<uint64_t>(H.off_geo);
+            for (uint32_t wp = 0; 2 * wp < H.W; ++wp) {
+                o << "      { const uint4 g0 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << ");\n";
+                for (uint32_t h2 = 0; h2 < 2 && 2 * wp + h2 < H.W; ++h2) {
+                    const uint32_t w = 2 * wp + h2;
+                    const uint32_t L = (w == H.W - 1 && (H.n & 63u)) ? (H.n & 63u) : 64u;
+                    const char* lo = h2 ? "z" : "x";
+                    const char* hi = h2 ? "w" : "y";
+                    o << fmt("        { uint64_t U = ((uint64_t)g0.%s << 32) | g0.%s;\n", hi, lo)
+                      << fmt("          if (U < 0x%016llxull) {\n", (unsigned long long)G[L - 1])
+                      << "            uint32_t pl = 0, ph = 0, pos = 0, j = 0;\n"
+                      << "            for (;;) {\n"
+                      << fmt("              if (U >= GEO_T[%uu - pos - 1]) break;\n", L)
+                      << "              uint32_t k = 0;\n              while (U >= GEO_T[k]) ++k;\n"
+                      << "              const uint32_t b = pos + k;\n"
+                      << "              if (b < 32) pl |= 1u << b; else ph |= 1u << (b - 32);\n"
+                      << fmt("              pos = b + 1;\n              if (pos >= %uu) break;\n", L)
+                      << "              ++j;\n"
+                      << "              const uint4 x = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << " | j);\n"
+                      << fmt("              U = ((uint64_t)x.%s << 32) | x.%s;\n", hi, lo)
+                      << "            }\n            any = 1u;\n";
+                    emit_flips(w, "pl", "ph", ftarget, fop);
+                    o << "          }\n        }\n";
+                }
+                o << "      }\n";
+            }
+        } else if (Pv && (flags & PBN_COMPILE_PERT_UNROLLED)) {
             /* one word at a time, every level pair unrolled with its P bits as constants */
             for (uint32_t w = 0; w < H.W; ++w) {
                 const uint64_t valid = valid_of(w);

@@ -65,7 +65,8 @@ struct SimParams {
     uint32_t hmax;             /* level pairs that can still decide a perturbation */
     uint32_t n, W, W32, n_sel, P;
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret, off_pos,
-        off_tables, n_groups, off_subs, per_node;
+        off_tables, n_groups, off_subs, per_node, sampler, off_geo;
+    uint64_t geo_full, geo_last;  /* geometric sampler: thresholds of a full and the last word */
     uint32_t n_meta_rows;
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
@@ -241,6 +242,14 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.off_gorder = H.off_gorder;
     P.off_subs = H.off_subs;
     P.per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
+    P.sampler = H.sampler;
+    P.off_geo = H.off_geo;
+    {
+        const uint64_t* G = reinterpret_cast<const uint64_t*>(plan->image.data() + H.off_geo);
+        const uint32_t nl = H.n & 63u;
+        P.geo_full = G[63];
+        P.geo_last = G[(nl ? nl : 64u) - 1];
+    }
     P.n_groups = H.n_groups;
     P.off_thr = H.off_thr;
     P.off_inputs = H.off_inputs;

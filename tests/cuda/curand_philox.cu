@@ -3,7 +3,8 @@
 // Reads lines "key_lo key_hi c0 c1 c2 c3" (decimal) on stdin and prints the four
 // output words of the block at that counter.  cuRAND's state is positioned with
 // curand_init(seed, subsequence, offset): the block counter is
-// (offset / 4 low, high, subsequence low, high).
+// (offset / 4 low, high, subsequence low, high); offset counts 32-bit outputs, so
+// the counter's high word c1 must stay below 2^30.
 #include <cstdio>
 #include <cstdint>
 #include <vector>

@@ -6,12 +6,12 @@ import numpy as np
 HEADER_FIELDS = ["magic", "n", "W", "W32", "n_groups", "n_multi", "n_sel", "P",
                  "off_words", "off_groups", "off_multi", "off_selslot", "off_thr", "off_inputs",
                  "off_selblk", "off_gorder", "off_subs", "off_tables", "off_ret", "off_pos", "image_bytes",
-                 "stage_bytes", "tables_in_smem", "semantics"]
+                 "stage_bytes", "tables_in_smem", "semantics", "sampler", "off_geo"]
 
 
 def decode(img: np.ndarray) -> dict:
     b = img.tobytes()
-    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<24I", b, 0)))
+    H = dict(zip(HEADER_FIELDS, struct.unpack_from("<26I", b, 0)))
     u32 = np.frombuffer(b, dtype=np.uint32)
     words = u32[H["off_words"] // 4: H["off_words"] // 4 + 2 * H["W32"]].reshape(-1, 2)
     groups = []

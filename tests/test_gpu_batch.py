@@ -173,3 +173,22 @@ def test_batch_mixes_semantics(oracle_mod):
                                   semantics=int(sem))
         assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
         assert np.array_equal(got["counts"], orc["counts"]), k
+
+
+
+def test_batch_geometric_sampler(oracle_mod):
+    nets = _networks(seed=13, count=3)
+    entries, plans = [], []
+    for d in nets:
+        plan, ids = plan_for(d["text"], d["meta"], sampler=_lib.PBN_PERT_GEOMETRIC)
+        bufs = api.alloc_buffers(plan, d["T"])
+        entries.append(dict(plan=plan, bufs=bufs, seed=d["seed"], meta_ids=d["meta"]))
+        plans.append((plan, ids))
+    B = api.Batch(entries)
+    B.run(200)
+    assert int(B.status.item()) == 0
+    for k, (d, (plan, ids), e) in enumerate(zip(nets, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(d["text"], d["seed"], 0, d["T"], 200, meta_ids=d["meta"], nthreads=NCPU, sampler=1)
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+        assert np.array_equal(got["counts"], orc["counts"]), k

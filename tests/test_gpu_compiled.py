@@ -144,3 +144,15 @@ def test_compiled_kernel_attributes(flags):
     plan.compile(flags)
     a = plan.compiled_attrs()
     assert a["flags"] == flags and 16 <= a["regs"] <= 255
+
+
+
+@pytest.mark.parametrize("flags", [0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED])
+@pytest.mark.parametrize("p", [0.01, 0.3])
+def test_compiled_geometric_sampler(oracle_mod, flags, p):
+    text = synth.paper100(seed=12, n=150, p=p).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta, sampler=_lib.PBN_PERT_GEOMETRIC)
+    plan.compile(flags)
+    orc = oracle_mod.simulate(text, 41, 0, 128, 400, meta_ids=meta, trace=True, nthreads=NCPU, sampler=1)
+    _compare(run(plan, seed=41, n_traj=128, n_steps=400, meta=meta, trace=True, kernel=COMPILED), orc, ids)

@@ -25,6 +25,8 @@ def test_oracle_philox_equals_curand(oracle_mod, tmp_path):
                     os.path.join(HERE, "cuda", "curand_philox.cu"), "-o", str(exe)], check=True)
     rng = np.random.default_rng(2024)
     rows = rng.integers(0, 2**32, size=(200, 6), dtype=np.uint64)
+    rows[:, 3] %= 2**30       # cuRAND takes the block counter's low 64 bits as an output
+                              # offset (4 outputs per block), so c1 < 2^30 is expressible
     rows[:50, 5] = 0          # zero high counter words (small subsequences)
     rows[50:60, :2] = 0       # zero keys
     text = "\n".join(" ".join(str(int(v)) for v in r) for r in rows) + "\n"

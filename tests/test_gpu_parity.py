@@ -249,3 +249,28 @@ def test_nodewise_semantics(oracle_mod, lanes, which):
     # and it differs from Eq. 1 on the same draws
     eq1 = oracle_mod.simulate(text, 31, 0, 96, 700, meta_ids=meta, nthreads=NCPU)
     assert not np.array_equal(eq1["final"], orc["final"])
+
+
+
+@pytest.mark.parametrize("lanes", [1, 4, 32])
+@pytest.mark.parametrize("p", [0.0, 0.01, 0.3, 0.75])
+def test_geometric_sampler(oracle_mod, lanes, p):
+    """The geometric perturbation sampler: bit-exact against the oracle's
+    geometric sampler (the rare path of several perturbed lanes per word runs
+    often at large p); a partial last word (n = 150)."""
+    text = synth.paper100(seed=12, n=150, p=p).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta, sampler=_lib.PBN_PERT_GEOMETRIC)
+    orc = oracle_mod.simulate(text, 41, 5, 96, 400, meta_ids=meta, trace=True, nthreads=NCPU, sampler=1)
+    gpu = run(plan, seed=41, traj_begin=5, n_traj=96, n_steps=400, meta=meta, trace=True, lanes=lanes,
+              kernel=_lib.PBN_KERNEL_INTERP)
+    _compare(gpu, orc, ids)
+
+
+def test_geometric_sampler_nodewise(oracle_mod):
+    text = synth.tiny12(2).to_text()
+    meta = [0, 1]
+    plan, ids = plan_for(text, meta, sampler=_lib.PBN_PERT_GEOMETRIC, semantics=_lib.PBN_SEM_NODEWISE)
+    orc = oracle_mod.simulate(text, 8, 0, 64, 800, meta_ids=meta, trace=True, semantics=1, sampler=1)
+    _compare(run(plan, seed=8, n_traj=64, n_steps=800, meta=meta, trace=True, kernel=_lib.PBN_KERNEL_INTERP),
+             orc, ids)

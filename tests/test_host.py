@@ -335,7 +335,7 @@ def test_estimate_rejects_bad_arguments():
 # ------------------------------------------------------------ compiled plans ----
 @pytest.mark.parametrize("flags", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half",
-                                   "split_small", "split_wide", "nodewise"])
+                                   "split_small", "split_wide", "nodewise", "geometric"])
 def test_generated_plan_kernels_compile(tmp_path, which, flags):
     """The source generated for a plan's own kernel compiles for sm_103a."""
     import shutil
@@ -363,6 +363,10 @@ def test_generated_plan_kernels_compile(tmp_path, which, flags):
         text, meta = synth.paper100(seed=2).to_text(), [0, 1, 2]
         red, _ = api.Net.load(text).reduce(meta)
         kw = dict(semantics=_lib.PBN_SEM_NODEWISE)
+    if which == "geometric":
+        text, meta = synth.paper100(seed=2, n=150).to_text(), [0, 1, 2]
+        red, _ = api.Net.load(text).reduce(meta)
+        kw = dict(sampler=_lib.PBN_PERT_GEOMETRIC)
     plan = api.Plan(red, mode=1 if which.endswith("plain") else 0, **kw)
     if which.startswith("split"):
         assert plan.info.n_split > 0
@@ -452,3 +456,18 @@ def test_apoptosis_stand_in_has_the_papers_shape(oracle_mod):
         leaf = oracle_mod.leaves(net.to_text(), m)
         assert leaf.sum() == 36 and not leaf[:60].any()
     assert len(metas) == 7 and all(a in {x for f in net.funcs[X] for x in f.parents} for a in par)
+
+
+
+@pytest.mark.parametrize("p", [0.0, 1e-4, 0.01, 0.3, 0.75, 0.5])
+def test_geometric_thresholds_match_oracle(oracle_mod, p):
+    """The library's thresholds of the geometric sampler (in the plan image) equal
+    the oracle's, computed by separate exact integer code."""
+    text = synth.paper100(seed=2, n=70, p=p).to_text()
+    plan = api.Plan(api.Net.load(text), sampler=_lib.PBN_PERT_GEOMETRIC)
+    D = imgdecode.decode(plan.image())
+    o = D["H"]["off_geo"] // 8
+    G = [int(x) for x in np.frombuffer(plan.image().tobytes(), dtype=np.uint64)[o: o + 64]]
+    assert G == oracle_mod.geo_thresholds(p)
+    assert plan.info.sampler == _lib.PBN_PERT_GEOMETRIC and D["H"]["sampler"] == 1
+    assert plan.info.ops_per_step < api.Plan(api.Net.load(text)).info.ops_per_step or p == 0.0
