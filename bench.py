@@ -124,6 +124,8 @@ def ops_per_traj_step(info, n: int, P: int) -> float:
     W = (n + 63) // 64
     blocks = sum(expected_blocks(64 if w < W - 1 or n % 64 == 0 else n % 64) for w in range(W)) if P else 0.0
     pert = blocks * (56 + 12) + 4
+    if info.sampler == _lib.PBN_PERT_GEOMETRIC:  # one block per word pair, a 64-bit compare per word
+        pert = 56 * ((W + 1) // 2) + 4 * W + 4 if P else 4
     nonpert = (info.n_sel_blocks * 56 + 2 * info.total_thresholds + info.n_multi
                + 3 * info.total_inputs + 5 * (info.n_groups + info.n_split) + 2 * info.state_words)
     return pert + (1.0 - pe) ** n * nonpert + 8
@@ -176,6 +178,9 @@ def workload_network(args):
     return synth.paper100(seed=2), META, WORKLOAD
 
 
+SAMPLERS = {"bitsliced": _lib.PBN_PERT_BITSLICED, "geometric": _lib.PBN_PERT_GEOMETRIC}
+
+
 # ------------------------------------------------------------------- ours ----
 def run_ours(args):
     import torch
@@ -201,7 +206,8 @@ def run_ours(args):
     if args.autotune:
         # group size, kernel and lanes per trajectory picked by timing short passes
         t0 = time.perf_counter()
-        choice = autotune.tune_network(text, meta, T, steps=2000 if args.workload == "paper100" else 200)
+        choice = autotune.tune_network(text, meta, T, steps=2000 if args.workload == "paper100" else 200,
+                                       sampler=SAMPLERS[args.sampler])
         tune_s = time.perf_counter() - t0
         max_inputs, lanes = choice.max_inputs, choice.lanes_per_traj
         budget, cflags = choice.smem_budget, choice.compile_flags
@@ -211,7 +217,9 @@ def run_ours(args):
         lanes = args.lanes
     t_prep = time.perf_counter()
     red, retained = api.Net.load(text).reduce(meta)
-    plan = api.Plan(red, max_inputs=max_inputs, smem_budget=budget) if budget else api.Plan(red, max_inputs=max_inputs)
+    sampler = SAMPLERS[args.sampler]
+    plan = api.Plan(red, max_inputs=max_inputs, smem_budget=budget, sampler=sampler) if budget \
+        else api.Plan(red, max_inputs=max_inputs, sampler=sampler)
     compile_ms = 0.0
     kattrs = None
     if args.kernel == "compiled":
@@ -365,6 +373,7 @@ def run_ours(args):
                        "host_prep_s": round(prep_s, 4), "compile_ms": round(compile_ms, 1),
                        "kernel": args.kernel, "max_inputs_per_group": max_inputs,
                        "compile_flags": cflags if args.kernel == "compiled" else None,
+                       "perturbation_sampler": args.sampler,
                        "compiled_kernel": kattrs,
                        "split_nodes": int(info.n_split),
                        "lanes_per_traj": lanes or "auto", "autotune_s": round(tune_s, 2)},
@@ -454,7 +463,8 @@ def run_serve(args):
         text = synth.paper100(seed=9000 + i, n=n, p=float(10 ** rng.uniform(-4, -2))).to_text()
         queries.append(serve.Query(qid=i, text=text, meta_ids=meta, seed=SEED + i, r=0.01, s=0.95))
     srv = serve.Server(n_traj=args.serve_traj, chunk_steps=args.serve_chunk, mem_cap_bytes=100e9,
-                       workers=os.cpu_count() or 8, max_traj=args.serve_max_traj)
+                       workers=os.cpu_count() or 8, max_traj=args.serve_max_traj, kernel=args.serve_kernel,
+                       sampler=SAMPLERS[args.sampler])
     t_start = time.perf_counter()
     due = t_start + np.cumsum(gaps)
     k = 0
@@ -476,7 +486,8 @@ def run_serve(args):
             "config": {"workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95",
                        "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "queries": n_q,
                        "trajectories_per_query": args.serve_traj, "max_trajectories_per_query": args.serve_max_traj,
-                       "chunk_steps": args.serve_chunk, "memory_cap_bytes": 100e9},
+                       "chunk_steps": args.serve_chunk, "memory_cap_bytes": 100e9,
+                       "kernel": args.serve_kernel, "perturbation_sampler": args.sampler},
             "latency": lat, "queries_per_s": len(srv.done) / makespan,
             "node_updates_per_s": srv.node_updates / makespan, "makespan_s": makespan,
             "completed": len(srv.done), "rejected": len(srv.rejected), "failed": len(srv.failed),
@@ -508,7 +519,8 @@ def run_apoptosis(args):
     net, X, par, metas = apoptosis_queries()
     text = net.to_text()
     srv = serve.Server(n_traj=args.apo_traj, chunk_steps=args.apo_chunk, burn_in0=256,
-                       mem_cap_bytes=100e9, workers=8, max_steps=1 << 24, max_traj=args.apo_max_traj)
+                       mem_cap_bytes=100e9, workers=8, max_steps=1 << 24, max_traj=args.apo_max_traj,
+                       kernel=args.serve_kernel, sampler=SAMPLERS[args.sampler])
     t0 = time.perf_counter()
     for i, m in enumerate(metas):
         srv.submit(serve.Query(qid=i, text=text, meta_ids=m, seed=SEED + 17 * i, r=1e-5, s=0.95, eps=1e-3))
@@ -522,7 +534,8 @@ def run_apoptosis(args):
             "data": "synthetic", "vs_baseline": None,
             "config": {"workload": "apoptosis-shaped PBN: n=96, 37.5% leaves, density 1.78, p=1e-4",
                        "node_X": X, "parents_ABC": list(par), "trajectories_per_query": args.apo_traj,
-                       "max_trajectories_per_query": args.apo_max_traj,
+                       "max_trajectories_per_query": args.apo_max_traj, "kernel": args.serve_kernel,
+                       "perturbation_sampler": args.sampler,
                        "chunk_steps": args.apo_chunk, "r": 1e-5, "s": 0.95, "eps": 1e-3},
             "queries": [{"meta": metas[r.qid], "pi": r.pi, "n_star": r.n_star, "samples": r.L, "m_star": r.m_star,
                          "steps": r.steps, "rounds": r.rounds, "trajectories": r.n_traj, "latency_s": r.latency}
@@ -561,6 +574,10 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--serve-seconds", type=float, default=20.0)
     ap.add_argument("--serve-traj", type=int, default=2048)
+    ap.add_argument("--serve-kernel", default="auto", choices=["batch", "auto"],
+                    help="serving rounds: batched interpreter only, or compiled plans for large blocks")
+    ap.add_argument("--sampler", default="bitsliced", choices=["bitsliced", "geometric"],
+                    help="perturbation sampler (draw contract) of the plans")
     ap.add_argument("--serve-chunk", type=int, default=128)
     ap.add_argument("--serve-max-traj", type=int, default=1 << 16)
     ap.add_argument("--compare-steps", type=int, default=100000,

@@ -56,11 +56,12 @@ def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
 def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 1,
                  max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8, 16, 32),
                  compile_flags_options=(0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED),
-                 try_compiled: bool = True, cache_file: str | None = None, log=None) -> Choice:
+                 try_compiled: bool = True, cache_file: str | None = None, log=None,
+                 sampler: int = _lib.PBN_PERT_BITSLICED) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
     placement) for simulating n_traj trajectories of this network."""
     net = api.Net.load(text)
-    key = _shape_key(net, meta, n_traj)
+    key = _shape_key(net, meta, n_traj) + f"-s{sampler}"
     with _LOCK:
         if key in _CACHE:
             return _CACHE[key]
@@ -82,7 +83,8 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
         default_staged = None
         for budget in (0, 1024, 220 * 1024):
             try:
-                plan = api.Plan(red, max_inputs=mi, smem_budget=budget) if budget else api.Plan(red, max_inputs=mi)
+                plan = api.Plan(red, max_inputs=mi, smem_budget=budget, sampler=sampler) if budget \
+                    else api.Plan(red, max_inputs=mi, sampler=sampler)
             except _lib.PbnError:
                 continue
             if budget == 0:
@@ -133,10 +135,10 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
     return best
 
 
-def plan_for_choice(text: str, meta, ch: Choice) -> api.Plan:
+def plan_for_choice(text: str, meta, ch: Choice, sampler: int = _lib.PBN_PERT_BITSLICED) -> api.Plan:
     red, _ = api.Net.load(text).reduce(list(meta))
-    plan = api.Plan(red, max_inputs=ch.max_inputs, smem_budget=ch.smem_budget) if ch.smem_budget \
-        else api.Plan(red, max_inputs=ch.max_inputs)
+    plan = api.Plan(red, max_inputs=ch.max_inputs, smem_budget=ch.smem_budget, sampler=sampler) if ch.smem_budget \
+        else api.Plan(red, max_inputs=ch.max_inputs, sampler=sampler)
     if ch.kernel == _lib.PBN_KERNEL_COMPILED:
         plan.compile(ch.compile_flags)
     return plan

@@ -11,7 +11,10 @@ server:
   memory cap, in arrival order;
 * runs rounds: one persistent batched launch (pbn_batch_run) advances every active
   query by `chunk_steps` steps, then one copy brings back every query's pooled
-  counts [V, n00, n01, n10, n11];
+  counts [V, n00, n01, n10, n11]; with kernel="auto" the trajectory blocks of
+  queries whose plan compiled (pbn_plan_compile) and that hold at least
+  `compiled_min_traj` trajectories run as their own compiled-plan launches on a
+  few side streams instead, the rest in the batched launch;
 * after each round applies the two-state Markov chain stopping rule to each query:
   if the burn-in m* exceeds the start of its counting window, the window restarts
   at the current step (counts cleared); if the counted states reach N*, the query
@@ -83,9 +86,11 @@ class _Block:
 
 
 class _Active:
-    def __init__(self, q: Query, plan, bufs, n, prep_s, nbytes, count_from, n_traj):
+    def __init__(self, q: Query, plan, bufs, n, prep_s, nbytes, count_from, n_traj, compiled=False):
         self.q = q
         self.plan = plan
+        self.compiled = compiled
+        self.compiling = None      # future of a background compilation
         self.blocks = [_Block(bufs, 0, n_traj, count_from)]
         self.n = n
         self.prep_s = prep_s
@@ -107,7 +112,10 @@ class Server:
 
     def __init__(self, n_traj: int = 512, chunk_steps: int = 256, burn_in0: int = 64,
                  min_pairs: int = 4096, mem_cap_bytes: float = 100e9, workers: int = 8,
-                 max_steps: int = 1 << 20, grow_rounds: int = 4, max_traj: int = 1 << 16, device="cuda"):
+                 max_steps: int = 1 << 20, grow_rounds: int = 4, max_traj: int = 1 << 16, device="cuda",
+                 kernel: str = "batch", sampler: int = _lib.PBN_PERT_BITSLICED,
+                 compile_flags: int = _lib.PBN_COMPILE_INTERLEAVED, compiled_min_traj: int = 4096,
+                 side_streams: int = 4):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -119,6 +127,13 @@ class Server:
         self.max_steps = max_steps
         self.grow_rounds = grow_rounds
         self.max_traj = max(max_traj, n_traj)
+        if kernel not in ("batch", "auto"):
+            raise ValueError("kernel must be 'batch' or 'auto'")
+        self.kernel = kernel
+        self.sampler = sampler
+        self.compile_flags = compile_flags
+        self.compiled_min_traj = compiled_min_traj
+        self.side = [torch.cuda.Stream(self.dev) for _ in range(side_streams)] if kernel == "auto" else []
         self.pool = ThreadPoolExecutor(max_workers=workers)
         self.prepared: "queue.Queue" = queue.Queue()
         self.waiting = []          # prepared, not yet admitted (arrival order)
@@ -142,20 +157,28 @@ class Server:
             t0 = time.perf_counter()
             net = api.Net.load(q.text)
             red, _ = net.reduce(q.meta_ids)
-            plan = api.Plan(red)
+            plan = api.Plan(red, sampler=self.sampler)
+            # compile now only if the query starts large enough to use it; otherwise
+            # it is compiled in the background once it grows
+            compiled = self.kernel == "auto" and self.n_traj >= self.compiled_min_traj and self._compile(plan)
             n = net.info().n
-            with self.torch.cuda.stream(self.stream):
-                plan.device_image(self.dev)
-                bufs = api.alloc_buffers(plan, self.n_traj, self.dev)
             # admission reserves the device bytes of the largest size the query may
             # grow to, so that growth never waits for memory and results stay
-            # independent of the other queries
+            # independent of the other queries; nothing is allocated on the device
+            # before admission
             nbytes = query_bytes(plan, self.max_traj)
-            self.prepared.put((q, plan, bufs, n, time.perf_counter() - t0, nbytes))
+            self.prepared.put((q, plan, None, n, time.perf_counter() - t0, nbytes, compiled))
         except Exception as exc:  # a query that cannot be prepared fails alone
             with self.lock:
                 self.failed.append((q.qid, repr(exc)))
                 self.pending -= 1
+
+    def _compile(self, plan) -> bool:
+        try:
+            plan.compile(self.compile_flags)
+            return True
+        except _lib.PbnError:  # too wide to compile: the batched interpreter runs it
+            return False
 
     def submit(self, q: Query):
         if not q.arrival:
@@ -208,7 +231,7 @@ class Server:
         self.waiting.sort(key=lambda it: it[0].arrival)
         keep = []
         for item in self.waiting:
-            q, plan, bufs, n, prep_s, nbytes = item
+            q, plan, bufs, n, prep_s, nbytes, compiled = item
             if nbytes > self.cap:
                 self.rejected.append(q.qid)
                 with self.lock:
@@ -216,7 +239,10 @@ class Server:
                 continue
             if self.in_use + nbytes <= self.cap:
                 self.in_use += nbytes
-                self.active.append(_Active(q, plan, bufs, n, prep_s, nbytes, self.burn_in0, self.n_traj))
+                with self.torch.cuda.stream(self.stream):
+                    plan.device_image(self.dev)
+                    bufs = api.alloc_buffers(plan, self.n_traj, self.dev)
+                self.active.append(_Active(q, plan, bufs, n, prep_s, nbytes, self.burn_in0, self.n_traj, compiled))
             else:
                 keep.append(item)
         self.waiting = keep
@@ -224,23 +250,50 @@ class Server:
     # -- one round --------------------------------------------------------------------
     def _round(self):
         torch = self.torch
-        entries, owner = [], []
+        entries, owner, direct, blocks = [], [], [], []
+        for a in self.active:
+            if a.compiling is not None and a.compiling.done():
+                a.compiled = a.compiling.result()
+                a.compiling = None
         for qi, a in enumerate(self.active):
             for b in a.blocks:
-                entries.append(dict(plan=a.plan, bufs=b.bufs, seed=a.q.seed, meta_ids=a.q.meta_ids,
-                                    meta_vals=a.q.meta_vals, traj_begin=b.traj_begin, step_begin=b.step,
-                                    count_from=b.count_from,
-                                    init=_lib.PBN_INIT_KEYED if b.step == 0 else _lib.PBN_INIT_STATE))
+                init = _lib.PBN_INIT_KEYED if b.step == 0 else _lib.PBN_INIT_STATE
+                if a.compiled and b.n_traj >= self.compiled_min_traj:
+                    direct.append((a, b, init))
+                else:
+                    entries.append(dict(plan=a.plan, bufs=b.bufs, seed=a.q.seed, meta_ids=a.q.meta_ids,
+                                        meta_vals=a.q.meta_vals, traj_begin=b.traj_begin, step_begin=b.step,
+                                        count_from=b.count_from, init=init))
                 owner.append(qi)
+                blocks.append(b)
         t0 = time.perf_counter()
+        B = None
         with torch.cuda.stream(self.stream):
-            B = api.Batch(entries, device=self.dev)
+            if direct:
+                # compiled-plan launches on side streams, after the server stream's
+                # pending work (count resets, new buffers), joined back before the copy
+                ready = self.stream.record_event()
+                for i, (a, b, init) in enumerate(direct):
+                    st = self.side[i % len(self.side)]
+                    st.wait_event(ready)
+                    api.simulate(a.plan, b.bufs, seed=a.q.seed, n_steps=self.chunk, meta_ids=a.q.meta_ids,
+                                 meta_vals=a.q.meta_vals, traj_begin=b.traj_begin, step_begin=b.step,
+                                 count_from=b.count_from, init=init, stream=st, kernel=_lib.PBN_KERNEL_COMPILED)
+            if entries:
+                B = api.Batch(entries, device=self.dev)
             t1 = time.perf_counter()
-            B.run(self.chunk, step_offset=0, stream=self.stream)
-            pooled = torch.stack([b.bufs.pooled for a in self.active for b in a.blocks]).to("cpu", non_blocking=True)
+            if B is not None:
+                B.run(self.chunk, step_offset=0, stream=self.stream)
+            for st in self.side[: len(direct)]:
+                self.stream.wait_event(st.record_event())
+            pooled = torch.stack([b.bufs.pooled for b in blocks]).to("cpu", non_blocking=True)
+            if direct:
+                status = torch.stack([b.bufs.status for _, b, _ in direct]).to("cpu", non_blocking=True)
         self.stream.synchronize()
-        if int(B.status.item()) != 0:
+        if B is not None and int(B.status.item()) != 0:
             raise RuntimeError("batch kernel reported an error status")
+        if direct and int(status.abs().sum()) != 0:
+            raise RuntimeError("a compiled-plan launch reported an error status")
         t2 = time.perf_counter()
         pooled = pooled.numpy().view(np.uint64)
         per_query = np.zeros((len(self.active), 5), dtype=np.uint64)
@@ -316,6 +369,9 @@ class Server:
         # new trajectories take the next ids and count after the query's burn-in
         burn = max(min(b.count_from for b in a.blocks), int(est.m_star))
         a.blocks.append(_Block(bufs, a.n_traj, nb, burn))
+        if (self.kernel == "auto" and not a.compiled and a.compiling is None
+                and max(b.n_traj for b in a.blocks) >= self.compiled_min_traj):
+            a.compiling = self.pool.submit(self._compile, a.plan)
         self.stats["grown"] = self.stats.get("grown", 0) + 1
 
     def _finish(self, a: _Active, est, c):

@@ -136,3 +136,30 @@ def test_cancelled_query_leaves_the_others_unchanged():
     assert srv.in_use == 0
     for q in qs[1:]:
         assert got[q.qid].counts == ref[q.qid].counts and got[q.qid].pi == ref[q.qid].pi
+
+
+def test_compiled_rounds_equal_batched_rounds():
+    """Rounds that run large trajectory blocks as compiled-plan launches on side
+    streams give the same results as the batched interpreter (keyed draws)."""
+    qs = _queries(count=5, seed=94)
+    ref = _run(qs)
+    got = _run(qs, kernel="auto", compiled_min_traj=64)
+    for q in qs:
+        assert got[q.qid].counts == ref[q.qid].counts and got[q.qid].pi == ref[q.qid].pi
+
+
+def test_geometric_sampler_serving_alone_equals_mix(oracle_mod):
+    """With the geometric perturbation sampler a query's result is still the same
+    alone and in a mix, and the n = 12 estimate meets the exact probability."""
+    from paper_1605_00854_gb300 import _lib
+    text = synth.tiny12(1).to_text()
+    meta = [0, 1, 2]
+    q = serve.Query(qid=0, text=text, meta_ids=meta, seed=4242, r=0.01, s=0.95)
+    alone = _run([q], sampler=_lib.PBN_PERT_GEOMETRIC, kernel="auto", compiled_min_traj=64)[0]
+    others = _queries(count=3, seed=95)
+    for x in others:
+        x.qid += 1
+    mix = _run([q] + others, sampler=_lib.PBN_PERT_GEOMETRIC)[0]
+    assert alone.counts == mix.counts and alone.pi == mix.pi
+    pi, _ = oracle_mod.stationary(oracle_mod.transition_matrix(text))
+    assert abs(alone.pi - oracle_mod.meta_probability(pi, 12, meta)) < 3 * 0.01

@@ -471,3 +471,17 @@ def test_geometric_thresholds_match_oracle(oracle_mod, p):
     assert G == oracle_mod.geo_thresholds(p)
     assert plan.info.sampler == _lib.PBN_PERT_GEOMETRIC and D["H"]["sampler"] == 1
     assert plan.info.ops_per_step < api.Plan(api.Net.load(text)).info.ops_per_step or p == 0.0
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_bench_ops_model_equals_library(sampler):
+    """The roofline's per-unit figure: bench.py's written-out model and the library's
+    pbn_plan_info.ops_per_step agree for both perturbation samplers."""
+    import bench
+    for text, meta in ((synth.paper100(seed=2).to_text(), [0, 1, 2]), (synth.tiny12(1).to_text(), [0, 1, 2]),
+                       (synth.paper100(seed=3, n=300, p=0.01).to_text(), [0, 1])):
+        net = api.Net.load(text)
+        red, _ = net.reduce(meta)
+        plan = api.Plan(red, sampler=sampler)
+        assert bench.ops_per_traj_step(plan.info, net.info().n, net.info().P) == pytest.approx(
+            plan.info.ops_per_step, rel=1e-12)
