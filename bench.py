@@ -339,7 +339,8 @@ def run_ours(args):
             torch.cuda.synchronize()
             dt = e0.elapsed_time(e1) / 1e3
             compare[name] = {"value": n * T * args.compare_steps / dt, "unit": "node-updates/s",
-                             "n_steps": args.compare_steps, "groups": int(pl.info.n_groups)}
+                             "n_steps": args.compare_steps, "groups": int(pl.info.n_groups),
+                             "achieved_tops": pl.info.ops_per_step * T * args.compare_steps / dt / 1e12}
             del b2
 
     out = None
@@ -412,7 +413,7 @@ def run_batch(args):
     for i, (n, T, p) in enumerate(shapes):
         text = synth.batch_network(seed=5000 + i, n=n, p=p).to_text()
         red, _ = api.Net.load(text).reduce(META)
-        plan = api.Plan(red)
+        plan = api.Plan(red, sampler=SAMPLERS[args.sampler])
         entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=SEED + i, meta_ids=META))
         plain.append(text)
         tot += n * T * S
@@ -440,7 +441,8 @@ def run_batch(args):
             "config": {"workload": "batch of 256 paper-scale PBNs, n log-uniform [20,4000], trajectories log-uniform "
                        "[1024,65536], p log-uniform [1e-5,1e-2]", "n_steps": S, "chunk_steps": chunk,
                        "work_items": int(B.info.n_items), "smem_per_cta": int(B.info.smem_bytes),
-                       "host_prep_s": round(prep, 2), "graph": "chunk launches captured in one CUDA graph"},
+                       "host_prep_s": round(prep, 2), "graph": "chunk launches captured in one CUDA graph",
+                       "perturbation_sampler": args.sampler},
             "per_network_launches": {"value": tot / t_each, "unit": "node-updates/s", "seconds": t_each},
             "speedup_vs_per_network": t_each / t_batch}
     print(json.dumps(line), flush=True)

@@ -75,3 +75,32 @@ def test_scalefree2000_full_size_sampled_trajectories(oracle_mod):
     for t, o in zip(sample, outs):
         assert np.array_equal(final[t, ids], o["final"][0, ids]), t
         assert np.array_equal(counts[t], o["counts"][0]), t
+
+
+def test_paper100_full_size_geometric_sampler(oracle_mod):
+    """The benchmark size with the geometric perturbation sampler and its compiled
+    kernel: sampled trajectories recomputed by the oracle's geometric sampler."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_00854_gb300 import _lib
+    text = synth.paper100(seed=2).to_text()
+    red, ids = api.Net.load(text).reduce(META)
+    plan = api.Plan(red, max_inputs=12, sampler=_lib.PBN_PERT_GEOMETRIC)
+    plan.compile(_lib.PBN_COMPILE_INTERLEAVED)
+    T, S = 1 << 16, 10**6
+    bufs = api.alloc_buffers(plan, T)
+    api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=META, kernel=_lib.PBN_KERNEL_COMPILED)
+    torch.cuda.synchronize()
+    assert int(bufs.status.item()) == 0
+    counts = bufs.counts.cpu().numpy().view(np.uint64).T
+    final = plan.unpack(bufs.state.cpu().numpy().view(np.uint64))
+    assert np.all(counts[:, 1:].sum(axis=1) == S)
+    sample = [3, 65534, 20000, 47011]
+    def one(t):
+        return oracle_mod.simulate(text, SEED, t, 1, S, meta_ids=META, sampler=1)
+    with ThreadPoolExecutor(max_workers=min(len(sample), os.cpu_count() or 1)) as ex:
+        outs = list(ex.map(one, sample))
+    for t, o in zip(sample, outs):
+        assert np.array_equal(final[t, ids], o["final"][0, ids]), t
+        assert np.array_equal(counts[t], o["counts"][0]), t
