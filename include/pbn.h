@@ -175,7 +175,7 @@ typedef struct {
     double theta;           /* memory limit of Sec. 3.3 on sum over groups of the
                                number of combined functions (default 65536) */
     uint64_t smem_budget;   /* bytes of plan image that may be staged into shared
-                               memory (0 = default 160 KiB); larger tables are read
+                               memory (0 = default 192 KiB); larger tables are read
                                from global memory */
     uint32_t sampler;       /* PBN_PERT_BITSLICED (default) or PBN_PERT_GEOMETRIC */
     uint32_t reserved;

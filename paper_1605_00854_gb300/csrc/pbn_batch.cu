@@ -57,6 +57,7 @@ struct alignas(16) NetDesc {
     uint32_t nt, off_gorder, n_groups, lg;
     uint32_t off_subs, per_node, sampler, off_geo;
     uint64_t geo_full, geo_last;
+    uint32_t off_wgroups, pad0, pad1, pad2;
     uint32_t meta_row[kMetaRows];
     uint32_t meta_mask[kMetaRows];
     uint32_t meta_val[kMetaRows];
@@ -88,7 +89,7 @@ struct ItemView {
     uint32_t n_traj, n_steps, kv0, kp0, pairs, count_first, init;
     uint32_t n, W, W32, n_sel, P, hmax;
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret,
-        off_pos, off_tables, n_groups, off_subs, per_node, sampler, off_geo;
+        off_pos, off_tables, n_groups, off_subs, per_node, sampler, off_geo, off_wgroups;
     uint64_t geo_full, geo_last;
     uint32_t n_meta_rows;
     const uint32_t* meta_row;
@@ -192,6 +193,7 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
         V.off_multi = D.off_multi;
         V.off_selslot = D.off_selslot;
         V.off_gorder = D.off_gorder;
+        V.off_wgroups = D.off_wgroups;
         V.off_subs = D.off_subs;
         V.per_node = D.per_node;
         V.sampler = D.sampler;
@@ -357,6 +359,7 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
             D.off_multi = H.off_multi;
             D.off_selslot = H.off_selslot;
             D.off_gorder = H.off_gorder;
+            D.off_wgroups = H.off_wgroups;
             D.off_subs = H.off_subs;
             D.per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
             D.sampler = H.sampler;

@@ -672,7 +672,12 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     std::vector<pbn_img_multi> mrec;
     std::vector<uint32_t> thr, inrec, tables;
     std::vector<uint32_t> selslot(16 * selblk.size(), 0u);
+    /* record of SEL slot s = 4 i + l at l * n_sel + i: lanes that take consecutive
+     * blocks read consecutive records */
+    auto slot_rec = [&](uint32_t slot) { return 4 * ((slot & 3u) * (uint32_t)selblk.size() + (slot >> 2)); };
     std::vector<uint32_t> subs; /* uint2 per function of a split node: in_chunk | k << 27, tab_off */
+    std::vector<uint32_t> wgroups; /* group indices of each output word (WORDS ranges into it) */
+    uint32_t n_multi_nodes = 0;
     uint32_t n_split = 0;
     uint64_t total_inputs = 0;
     uint32_t n_groups_multi = 0;
@@ -709,7 +714,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
                 const uint32_t slot = sel_slot(v);
                 M.ch_off = slot;
                 M.radix = 1;
-                uint32_t* ss = &selslot[4 * slot];
+                uint32_t* ss = &selslot[slot_rec(slot)];
                 ss[0] = n_thr >= 1 ? thr[first] : 0u;
                 ss[1] = n_thr >= 2 ? thr[first + 1] : 0u;
                 ss[2] = n_thr;
@@ -783,7 +788,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
                 const uint32_t slot = sel_slot(v);
                 M.ch_off = slot;
                 M.radix = (uint32_t)prod;
-                uint32_t* ss = &selslot[4 * slot];
+                uint32_t* ss = &selslot[slot_rec(slot)];
                 ss[0] = n_thr >= 1 ? thr[first] : 0u;
                 ss[1] = n_thr >= 2 ? thr[first + 1] : 0u;
                 ss[2] = n_thr;
@@ -842,11 +847,86 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
         std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
             const bool sa = grec[a].l2w == PBN_IMG_SPLIT, sb = grec[b].l2w == PBN_IMG_SPLIT;
             if (sa != sb) return sa;
+            if (sa) return grec[a].q > grec[b].q;
             const uint32_t qa = (grec[a].q + 3) / 4, qb = (grec[b].q + 3) / 4;
             if (qa != qb) return qa > qb;
             return grec[a].n_mul > grec[b].n_mul;
         });
-        for (size_t k = 0; k < idx.size(); ++k) gorder[k] = idx[k] | (gword[idx[k]] << 20);
+        /* Row-interleaved layout: group records in this shape order, and the records
+         * each group reads (input chunks, multi-function nodes, split-node functions)
+         * in rows of 32 groups with a stride of 32, so that the lanes of a warp that
+         * take consecutive groups read consecutive records (no bank conflicts).  Chunk
+         * j of group k = 32 r + l sits at base_r + 32 j + l.  Split-node functions keep
+         * their own input chunks contiguous after the rows. */
+        const size_t G = grec.size();
+        n_multi_nodes = (uint32_t)mrec.size();
+        std::vector<uint32_t> newidx(G);
+        for (size_t k = 0; k < G; ++k) newidx[idx[k]] = (uint32_t)k;
+        std::vector<pbn_img_group> g2(G);
+        std::vector<pbn_img_multi> m2;
+        std::vector<uint32_t> in2, s2;
+        for (size_t r0 = 0; r0 < G; r0 += 32) {
+            const size_t r1 = std::min(G, r0 + 32);
+            uint32_t maxc = 0, maxm = 0, maxf = 0;
+            for (size_t k = r0; k < r1; ++k) {
+                const pbn_img_group& O = grec[idx[k]];
+                const bool sp = O.l2w == PBN_IMG_SPLIT;
+                maxc = std::max<uint32_t>(maxc, sp ? 0u : (O.q + 3u) / 4u);
+                maxm = std::max<uint32_t>(maxm, O.n_mul);
+                maxf = std::max<uint32_t>(maxf, sp ? O.q : 0u);
+            }
+            const uint32_t cb = (uint32_t)(in2.size() / 4), mb = (uint32_t)m2.size(), sb = (uint32_t)(s2.size() / 2);
+            in2.resize(in2.size() + (size_t)4 * 32 * maxc, W32 << 7); /* padding reads the zero row */
+            m2.resize(m2.size() + (size_t)32 * maxm, pbn_img_multi{0u, 0u});
+            s2.resize(s2.size() + (size_t)2 * 32 * maxf, 0u);
+            for (size_t k = r0; k < r1; ++k) {
+                const uint32_t l = (uint32_t)(k - r0);
+                const pbn_img_group& O = grec[idx[k]];
+                pbn_img_group N = O;
+                const bool sp = O.l2w == PBN_IMG_SPLIT;
+                if (!sp) {
+                    N.in_chunk = cb + l;
+                    for (uint32_t j = 0; j < (O.q + 3u) / 4u; ++j)
+                        for (uint32_t e = 0; e < 4; ++e) in2[4 * (cb + l + 32 * j) + e] = inrec[4 * (O.in_chunk + j) + e];
+                }
+                N.mul_first = mb + l;
+                for (uint32_t m = 0; m < O.n_mul; ++m) m2[mb + l + 32 * m] = mrec[O.mul_first + m];
+                if (sp) {
+                    N.tab_off = sb + l;
+                    for (uint32_t f = 0; f < O.q; ++f) {
+                        s2[2 * (sb + l + 32 * f)] = subs[2 * (O.tab_off + f)];
+                        s2[2 * (sb + l + 32 * f) + 1] = subs[2 * (O.tab_off + f) + 1];
+                    }
+                }
+                g2[k] = N;
+            }
+        }
+        /* split-node functions' own chunks, contiguous after the rows */
+        for (size_t i = 0; i < s2.size(); i += 2) {
+            const uint32_t k = s2[i] >> 27, old = s2[i] & 0x7FFFFFFu;
+            if (s2[i] == 0 && s2[i + 1] == 0) continue; /* padding record */
+            const uint32_t nc = (k + 3u) / 4u, at = (uint32_t)(in2.size() / 4);
+            for (uint32_t j = 0; j < nc; ++j)
+                for (uint32_t e = 0; e < 4; ++e) in2.push_back(inrec[4 * (old + j) + e]);
+            if (at >= (1u << 27)) return fail(PBN_ETOOBIG, "input records beyond 2^27 chunks");
+            s2[i] = at | (k << 27);
+        }
+        /* the groups of each output word, for the word-by-word evaluation */
+        std::vector<uint32_t> wg;
+        wg.reserve(G);
+        for (uint32_t k = 0; k < W32; ++k) {
+            const uint32_t first = words[2 * k], cnt = words[2 * k + 1];
+            words[2 * k] = (uint32_t)wg.size();
+            for (uint32_t gi = first; gi < first + cnt; ++gi) wg.push_back(newidx[gi]);
+        }
+        for (size_t k = 0; k < G; ++k) gorder[k] = (uint32_t)k | (gword[idx[k]] << 20);
+        for (uint32_t v = 0; v < n; ++v)
+            if (plan->group_of[v] != UINT32_MAX) plan->group_of[v] = newidx[plan->group_of[v]];
+        grec.swap(g2);
+        mrec.swap(m2);
+        inrec.swap(in2);
+        subs.swap(s2);
+        wgroups.swap(wg);
     }
     std::vector<uint64_t> ret(W, 0);
     for (uint32_t v = 0; v < n; ++v)
@@ -873,6 +953,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.off_inputs = (uint32_t)off; off = align16(off + inrec.size() * 4);
     H.off_selblk = (uint32_t)off; off = align16(off + selblk.size() * 4);
     H.off_gorder = (uint32_t)off; off = align16(off + gorder.size() * 4);
+    H.off_wgroups = (uint32_t)off; off = align16(off + wgroups.size() * 4);
     H.off_subs = (uint32_t)off; off = align16(off + subs.size() * 4);
     H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
     H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
@@ -880,7 +961,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     H.off_geo = (uint32_t)off; off = align16(off + 64 * 8);
     if (off >= (UINT64_C(1) << 31)) return fail(PBN_ETOOBIG, "device image of %zu bytes", off);
     H.image_bytes = (uint32_t)off;
-    const uint64_t budget = prm.smem_budget ? prm.smem_budget : 160 * 1024;
+    const uint64_t budget = prm.smem_budget ? prm.smem_budget : 192 * 1024;
     H.tables_in_smem = H.off_ret <= budget ? 1u : 0u;
     H.stage_bytes = H.tables_in_smem ? H.off_ret : H.off_tables;
     if (H.stage_bytes > budget) return fail(PBN_ETOOBIG, "plan specs of %u bytes exceed the shared-memory budget", H.stage_bytes);
@@ -896,6 +977,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     if (!inrec.empty()) memcpy(img + H.off_inputs, inrec.data(), inrec.size() * 4);
     if (!selblk.empty()) memcpy(img + H.off_selblk, selblk.data(), selblk.size() * 4);
     if (!gorder.empty()) memcpy(img + H.off_gorder, gorder.data(), gorder.size() * 4);
+    if (!wgroups.empty()) memcpy(img + H.off_wgroups, wgroups.data(), wgroups.size() * 4);
     if (!subs.empty()) memcpy(img + H.off_subs, subs.data(), subs.size() * 4);
     memcpy(img + H.off_ret, ret.data(), ret.size() * 8);
     memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
@@ -924,7 +1006,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
     I.stage_bytes = H.stage_bytes;
     I.tables_in_smem = H.tables_in_smem;
     I.total_inputs = (uint32_t)total_inputs;
-    I.n_multi = (uint32_t)mrec.size();
+    I.n_multi = n_multi_nodes;
     I.n_split = n_split;
     I.semantics = prm.semantics;
     I.sampler = prm.sampler;
@@ -942,7 +1024,7 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
         double pert = blocks * (56.0 + 12.0) + 4.0;
         if (prm.sampler == PBN_PERT_GEOMETRIC) /* one block per word pair, a 64-bit compare per word */
             pert = H.P ? 56.0 * (double)((W + 1) / 2) + 4.0 * (double)W + 4.0 : 4.0;
-        const double nonpert = 56.0 * H.n_sel + 2.0 * (double)thr.size() + (double)mrec.size() +
+        const double nonpert = 56.0 * H.n_sel + 2.0 * (double)thr.size() + (double)n_multi_nodes +
                                3.0 * (double)total_inputs + 5.0 * (double)(H.n_groups + n_split) +
                                2.0 * (double)(W32 / 2);
         I.ops_per_step = pert + std::pow(1.0 - pe, (double)n) * nonpert + 8.0;
@@ -959,7 +1041,7 @@ extern "C" void pbn_group_params_default(pbn_group_params* prm) {
     prm->max_inputs = 8;
     prm->max_width = 32;
     prm->theta = 65536.0;
-    prm->smem_budget = 160 * 1024;
+    prm->smem_budget = 192 * 1024;
 }
 
 extern "C" int pbn_group(const pbn_net* net, const pbn_group_params* prm_in, pbn_plan** out) {

@@ -7,14 +7,25 @@
  * memory (L2-resident) and only the specs are staged.
  *
  * Sections (byte offsets in pbn_img_header, each 16-byte aligned):
- *   words   [W32]        uint2 {first group, number of groups} of state word k
- *   groups  [n_groups]   pbn_img_group, sorted by output word
- *   multi   [n_multi]    pbn_img_multi, the multi-function nodes of each group in
+ *   words   [W32]        uint2 {first, count}: range of wgroups listing the groups of
+ *                        state word k
+ *   groups  [n_groups]   pbn_img_group in evaluation (shape) order: groups sorted by
+ *                        split first, then input chunks and multi-function nodes
+ *                        descending, so that groups taken together look alike
+ *   multi   [...]        pbn_img_multi, the multi-function nodes of each group in
  *                        group bit order: where their choice is and its radix
+ *
+ * Row-interleaved records: the records a group reads are laid out in rows of 32
+ * consecutive groups with a stride of 32, so that lanes taking consecutive groups
+ * read consecutive records: input chunk j of group k = 32 r + l is chunk
+ * in_chunk + 32 j (in_chunk = base_r + l); multi record m is mul_first + 32 m;
+ * function f of a split node is record tab_off + 32 f.  A split node's functions
+ * keep their own input chunks contiguous (stride 1) after the rows.
  *   selslot [4 n_sel]    uint4 {t1, t2, n_thr, thr_first} per SEL slot (4 per drawn
- *                        block, slot = 4 * block index + rank mod 4): the node's
- *                        integer thresholds (inline when n_thr <= 2); n_thr = 0 for a
- *                        slot without a retained multi-function node
+ *                        block, slot = 4 * block index + rank mod 4), stored at
+ *                        (slot mod 4) * n_sel + slot / 4: the node's integer
+ *                        thresholds (inline when n_thr <= 2); n_thr = 0 for a slot
+ *                        without a retained multi-function node
  *   thr     [...]        uint32 selection thresholds T_j < 2^32 of every slot
  *   inputs  [...]        uint32 input records, 4 per chunk, each group starting a
  *                        chunk and padded with records of the always-zero row
@@ -22,9 +33,9 @@
  *                        holding input b and rot = (bit - b mod 4) mod 32 rotates
  *                        that bit to position b mod 4 of its chunk
  *   selblk  [n_sel]      uint32 SEL block indices r / 4 drawn per step
- *   gorder  [n_groups]   uint32 group index | output word << 20, groups sorted by
- *                        shape (inputs, multi-function nodes): the evaluation order
- *                        when several lanes share a trajectory
+ *   gorder  [n_groups]   uint32 group index | output word << 20 of group k (the group
+ *                        index is k: records are stored in this order)
+ *   wgroups [n_groups]   uint32 group indices of each state word (ranges in words)
  *   subs    [...]        uint2 function records of split nodes (see below)
  *   tables  [...]        uint32 words of packed table entries; entry e of a group
  *                        with log2 entry width l2w occupies bits
@@ -54,14 +65,14 @@ typedef struct {
     uint32_t n_sel;      /* SEL blocks per step */
     uint32_t P;          /* perturbation threshold */
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr;
-    uint32_t off_inputs, off_selblk, off_gorder, off_subs, off_tables, off_ret, off_pos;
+    uint32_t off_inputs, off_selblk, off_gorder, off_wgroups, off_subs, off_tables, off_ret, off_pos;
     uint32_t image_bytes;
     uint32_t stage_bytes;
     uint32_t tables_in_smem;
     uint32_t semantics;  /* PBN_SEM_EQ1 or PBN_SEM_NODEWISE */
     uint32_t sampler;    /* PBN_PERT_BITSLICED or PBN_PERT_GEOMETRIC */
     uint32_t off_geo;    /* uint64 [64] thresholds of the geometric sampler (global) */
-} pbn_img_header; /* 104 bytes */
+} pbn_img_header; /* 108 bytes */
 
 /* A group record with l2w == PBN_IMG_SPLIT is a split node: one multi-function node
  * whose q functions each keep their own table of 2^k one-bit entries over their own

@@ -73,6 +73,7 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
     const uint4* INPUTS = reinterpret_cast<const uint4*>(SP + P.off_inputs);
     const uint32_t* SELBLK = reinterpret_cast<const uint32_t*>(SP + P.off_selblk);
     const uint32_t* GORDER = reinterpret_cast<const uint32_t*>(SP + P.off_gorder);
+    const uint32_t* WGROUPS = reinterpret_cast<const uint32_t*>(SP + P.off_wgroups);
     const uint2* SUBS = reinterpret_cast<const uint2*>(SP + P.off_subs);
     const uint64_t* RET = reinterpret_cast<const uint64_t*>(P.image + P.off_ret);
     const uint32_t* POS = reinterpret_cast<const uint32_t*>(P.image + P.off_pos);
@@ -219,7 +220,7 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                     uint32_t word = 0;
 #pragma unroll
                     for (int l = 0; l < 4; ++l) {
-                        const uint4 S = SELSLOT[4 * i + l]; /* t1, t2, n_thr, first */
+                        const uint4 S = SELSLOT[l * P.n_sel + i]; /* t1, t2, n_thr, first */
                         uint32_t j;
                         if (S.z <= 2u) {
                             j = ((S.z >= 1u) & (u[l] >= S.x)) + ((S.z >= 2u) & (u[l] >= S.y));
@@ -245,11 +246,14 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                 group_sync<LG>();
                 /* ---- 2b. merged-table evaluation ---- */
                 const uint8_t* Sc8 = reinterpret_cast<const uint8_t*>(Sc);
-                /* input pattern of q inputs from their chunked records */
-                auto gather = [&](const uint4* ch, uint32_t q) -> uint32_t {
+                /* input pattern of q inputs from their chunked records (chunks
+                 * `stride` apart: 32 in the row-interleaved group layout, 1 for the
+                 * functions of a split node) */
+                auto gather = [&](const uint4* ch, uint32_t q, uint32_t stride) -> uint32_t {
                     uint32_t x = 0;
                     for (uint32_t b0 = 0; b0 < q; b0 += 4) {
-                        const uint4 R = *ch++;
+                        const uint4 R = *ch;
+                        ch += stride;
                         const uint32_t v0 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.x >> 5));
                         const uint32_t v1 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.y >> 5));
                         const uint32_t v2 = *reinterpret_cast<const uint32_t*>(Sc8 + (R.z >> 5));
@@ -272,16 +276,16 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                     const uint32_t shift = G.w >> 24;
                     if (l2w == PBN_IMG_SPLIT) {
                         /* split node: only the selected function is evaluated */
-                        const uint2 F = SUBS[G.x + Cb[MULTI[G.z].x]]; /* in_chunk | k << 27, tab_off */
-                        const uint32_t x = gather(INPUTS + (F.x & 0x7FFFFFFu), F.x >> 27);
+                        const uint2 F = SUBS[G.x + 32u * Cb[MULTI[G.z].x]]; /* in_chunk | k << 27, tab_off */
+                        const uint32_t x = gather(INPUTS + (F.x & 0x7FFFFFFu), F.x >> 27, 1u);
                         return make_uint4(F.y + (x >> 5), x & 31u, 1u, shift);
                     }
                     uint32_t c = 0;
                     for (uint32_t m = 0; m < n_mul; ++m) {
-                        const uint2 M = MULTI[G.z + m]; /* choice byte, radix */
+                        const uint2 M = MULTI[G.z + 32u * m]; /* choice byte, radix */
                         c += (uint32_t)Cb[M.x] * M.y;
                     }
-                    const uint32_t x = gather(INPUTS + G.y, q);
+                    const uint32_t x = gather(INPUTS + G.y, q, 32u);
                     const uint32_t bo = ((c << q) | x) << l2w;
                     return make_uint4(G.x + (bo >> 5), bo & 31u, (2u << ((1u << l2w) - 1u)) - 1u, shift);
                 };
@@ -297,7 +301,7 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                     for (uint32_t w = 0; w < W32; ++w) {
                         const uint2 wr = WORDS[w];
                         uint32_t acc = 0;
-                        for (uint32_t gi = wr.x; gi < wr.x + wr.y; ++gi) acc |= group_bits(gi);
+                        for (uint32_t i = wr.x; i < wr.x + wr.y; ++i) acc |= group_bits(WGROUPS[i]);
                         Sn[w] = acc;
                     }
                 } else {

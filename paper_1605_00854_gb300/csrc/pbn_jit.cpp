@@ -155,7 +155,7 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     for (uint32_t g = 0; g < H.n_groups; ++g) {
         if (groups[g].l2w != PBN_IMG_SPLIT) tab_starts.push_back(groups[g].tab_off);
         else
-            for (uint32_t f = 0; f < groups[g].q; ++f) tab_starts.push_back(subs[2 * (groups[g].tab_off + f) + 1]);
+            for (uint32_t f = 0; f < groups[g].q; ++f) tab_starts.push_back(subs[2 * (groups[g].tab_off + 32 * f) + 1]);
     }
     std::sort(tab_starts.begin(), tab_starts.end());
 
@@ -293,7 +293,7 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     auto choice_expr = [&](const pbn_img_multi& M) {
         const uint32_t slot = M.ch_off;
         const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
-        const uint32_t* ss = selslot + 4 * slot; /* t1, t2, n_thr, first */
+        const uint32_t* ss = selslot + 4 * ((slot & 3u) * H.n_sel + (slot >> 2)); /* t1, t2, n_thr, first */
         const uint32_t n_thr = ss[2];
         std::string j;
         for (uint32_t q = 0; q < n_thr; ++q) {
@@ -302,11 +302,12 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         }
         return j;
     };
-    /* input pattern of k inputs from chunked records */
-    auto pattern = [&](uint32_t in_chunk, uint32_t k) {
+    /* input pattern of k inputs from chunked records `stride` chunks apart (32 in
+     * the row-interleaved group layout, 1 for a split node's functions) */
+    auto pattern = [&](uint32_t in_chunk, uint32_t k, uint32_t stride) {
         std::string xexpr;
         for (uint32_t b = 0; b < k; ++b) {
-            const uint32_t rec = inrec[4 * in_chunk + b];
+            const uint32_t rec = inrec[4 * (in_chunk + stride * (b / 4)) + (b & 3)];
             const uint32_t row = rec >> 7, bit = ((b & 3) + (rec & 31)) & 31;
             xexpr += (b ? " | " : "") + gather(row, bit, b);
         }
@@ -315,9 +316,10 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     /* merged-table evaluation of every group from s and the SEL uniforms U: n<row> */
     auto emit_eval = [&]() {
         for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
+        const uint32_t* wgroups = V.at<uint32_t>(H.off_wgroups);
         for (uint32_t r = 0; r < H.W32; ++r) {
-            for (uint32_t gi = words[r].x; gi < words[r].x + words[r].y; ++gi) {
-                const pbn_img_group& G = groups[gi];
+            for (uint32_t i = words[r].x; i < words[r].x + words[r].y; ++i) {
+                const pbn_img_group& G = groups[wgroups[i]];
                 o << "        { ";
                 if (G.l2w == PBN_IMG_SPLIT) {
                     /* split node: every function's pattern is a few register operations;
@@ -327,22 +329,22 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
                     if (j.empty()) j = "0u";
                     o << "const uint32_t j = " << j << "; ";
                     bool small = true;
-                    for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + f)] >> 27) <= 6;
+                    for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + 32 * f)] >> 27) <= 6;
                     std::string v = "0u";
                     if (small) {
                         for (uint32_t f = G.q; f-- > 0;) {
-                            const uint32_t* F = subs + 2 * (G.tab_off + f);
+                            const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
                             const uint32_t k = F[0] >> 27, ch = F[0] & 0x7FFFFFFu;
                             const uint64_t t64 = (k == 6 ? ((uint64_t)tab[F[1] + 1] << 32) : 0ull) | tab[F[1]];
                             const std::string vf =
-                                fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k) + ")) & 1ull)";
+                                fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k, 1) + ")) & 1ull)";
                             v = f + 1 == G.q ? vf : fmt("(j == %uu ? ", f) + vf + " : " + v + ")";
                         }
                     } else {
                         std::string xs = "0u", offs = "0u";
                         for (uint32_t f = G.q; f-- > 0;) {
-                            const uint32_t* F = subs + 2 * (G.tab_off + f);
-                            const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27) + ")";
+                            const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
+                            const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27, 1) + ")";
                             xs = f + 1 == G.q ? xf : fmt("(j == %uu ? ", f) + xf + " : " + xs + ")";
                             offs = f + 1 == G.q ? fmt("%uu", F[1]) : fmt("(j == %uu ? %uu : ", f, F[1]) + offs + ")";
                         }
@@ -356,14 +358,14 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
                 /* combined choice */
                 std::string cexpr;
                 for (uint32_t m = 0; m < G.n_mul; ++m) {
-                    const pbn_img_multi& M = multi[G.mul_first + m];
+                    const pbn_img_multi& M = multi[G.mul_first + 32 * m];
                     const std::string j = choice_expr(M);
                     if (j.empty()) continue;
                     cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
                 }
                 /* input pattern */
                 const uint32_t q = G.q;
-                o << "const uint32_t x = " << pattern(G.in_chunk, q) << "; ";
+                o << "const uint32_t x = " << pattern(G.in_chunk, q, 32) << "; ";
                 if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
                 else o << "const uint32_t e = x; ";
                 /* table entry */

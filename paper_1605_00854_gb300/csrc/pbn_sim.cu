@@ -65,7 +65,7 @@ struct SimParams {
     uint32_t hmax;             /* level pairs that can still decide a perturbation */
     uint32_t n, W, W32, n_sel, P;
     uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret, off_pos,
-        off_tables, n_groups, off_subs, per_node, sampler, off_geo;
+        off_tables, n_groups, off_subs, per_node, sampler, off_geo, off_wgroups;
     uint64_t geo_full, geo_last;  /* geometric sampler: thresholds of a full and the last word */
     uint32_t n_meta_rows;
     uint32_t meta_row[kMaxMetaRows];
@@ -240,6 +240,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.off_multi = H.off_multi;
     P.off_selslot = H.off_selslot;
     P.off_gorder = H.off_gorder;
+    P.off_wgroups = H.off_wgroups;
     P.off_subs = H.off_subs;
     P.per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
     P.sampler = H.sampler;

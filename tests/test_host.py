@@ -229,7 +229,7 @@ def test_merged_tables_equal_member_functions(mode, seed, max_inputs):
         if G["l2w"] == imgdecode.SPLIT:
             n_split += 1
             (v,) = members
-            assert D["multi"][G["mul_first"]]["radix"] == 1
+            assert D["multi"][imgdecode.multi_index(G, 0)]["radix"] == 1
             for j, (in_chunk, k, tab_off) in enumerate(imgdecode.subs(D, g)):
                 f = net.funcs[v][j]
                 assert [inv[32 * row + bit] for row, bit in imgdecode.sub_inputs(D, in_chunk, k)] == list(f.parents)
@@ -240,7 +240,7 @@ def test_merged_tables_equal_member_functions(mode, seed, max_inputs):
         ins = [inv[32 * row + bit] for row, bit in imgdecode.inputs(D, g)]
         multi = [v for v in members if len(net.funcs[v]) >= 2]
         assert len(multi) == G["n_mul"]
-        radix = [D["multi"][G["mul_first"] + m]["radix"] for m in range(G["n_mul"])]
+        radix = [D["multi"][imgdecode.multi_index(G, m)]["radix"] for m in range(G["n_mul"])]
         ells = [len(net.funcs[v]) for v in multi]
         prod = math.prod(ells)
         assert radix == [math.prod(ells[:m]) for m in range(len(ells))]
@@ -277,9 +277,9 @@ def test_thresholds_and_sel_slots_match_oracle(oracle_mod):
         members = sorted(np.flatnonzero(grp == g).tolist(), key=lambda v: pos[v])
         multi = [v for v in members if len(net.funcs[v]) >= 2]
         for m, v in enumerate(multi):
-            rec = D["multi"][G["mul_first"] + m]
+            rec = D["multi"][imgdecode.multi_index(G, m)]
             P, T = oracle_mod.thresholds(text, v)
-            assert imgdecode.thresholds(D, G["mul_first"] + m) == [t for t in T if t < 2**32]
+            assert imgdecode.thresholds(D, imgdecode.multi_index(G, m)) == [t for t in T if t < 2**32]
             blk = int(D["sel"][rec["u_slot"] // 4])
             assert blk == rank[v] // 4 and rec["u_slot"] % 4 == rank[v] % 4
     assert D["H"]["P"] == math.floor(net.p * 2**32)
@@ -293,8 +293,9 @@ def test_plan_specs_over_budget_are_rejected():
     with pytest.raises(_lib.PbnError) as e:
         api.Plan(red, smem_budget=1024)
     assert e.value.status == -5
-    plan = api.Plan(red, smem_budget=4096)
-    assert plan.info.tables_in_smem == 0 and plan.info.stage_bytes <= 4096
+    specs = imgdecode.decode(api.Plan(red).image())["H"]["off_tables"]
+    plan = api.Plan(red, smem_budget=specs)
+    assert plan.info.tables_in_smem == 0 and plan.info.stage_bytes <= specs
 
 
 # ---------------------------------------------------------------- estimator ----
