@@ -311,7 +311,8 @@ def run_ours(args):
                     ("interpreter_plain_unreduced", plain_plan, _lib.PBN_KERNEL_INTERP)]
         # the same grouped plan compiled with each code-shape flag
         for fname, fl in (("rolled", 0), ("unrolled", _lib.PBN_COMPILE_PERT_UNROLLED),
-                          ("interleaved", _lib.PBN_COMPILE_INTERLEAVED), ("pipelined", _lib.PBN_COMPILE_PIPELINED)):
+                          ("interleaved", _lib.PBN_COMPILE_INTERLEAVED), ("pipelined", _lib.PBN_COMPILE_PIPELINED),
+                          ("interleaved_magic_gather", _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER)):
             pf = api.Plan(red, max_inputs=max_inputs)
             try:
                 pf.compile(fl)

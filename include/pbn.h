@@ -326,6 +326,13 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
  * every step with a select keeping s XOR flips in perturbed steps.  Takes
  * precedence over the two flags above. */
 #define PBN_COMPILE_PIPELINED 0x4u
+/* PBN_COMPILE_MAGIC_GATHER (combines with the others): within a merged group, the
+ * 3 to 8 inputs that sit in one state word are gathered by one multiplication
+ * ((s & mask) * mul >> shift, with a multiplier found on the host that makes the
+ * field an injective index) instead of one shift and mask per bit; the group's table
+ * is rebuilt in that index order and the kernel reads its tables from its own
+ * array.  Same results. */
+#define PBN_COMPILE_MAGIC_GATHER 0x8u
 
 /* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
  * thread, local-memory (spill) bytes per thread and the flags it was compiled with;

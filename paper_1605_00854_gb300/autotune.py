@@ -55,7 +55,8 @@ def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
 
 def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 1,
                  max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8, 16, 32),
-                 compile_flags_options=(0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED),
+                 compile_flags_options=(0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED,
+                                        _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER),
                  try_compiled: bool = True, cache_file: str | None = None, log=None,
                  sampler: int = _lib.PBN_PERT_BITSLICED) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table

@@ -116,6 +116,72 @@ std::string gather(uint32_t row, uint32_t bit, uint32_t b) {
 
 const char* lanes = "xyzw";
 
+/* Multiply gather: the k input bits a_0 < ... < a_{k-1} of one state word are moved
+ * into a field of `width` bits by one multiplication, field = (((s & mask) * mul) >>
+ * shift) & (2^width - 1).  mul is a sum of powers of two that sends bit a_i to a
+ * target position t_i >= a_i inside [shift, shift + width); the other partial
+ * products and their carries may land anywhere, so a candidate is kept only if the
+ * field takes 2^k distinct values over the 2^k input patterns (an injective index:
+ * the group's table is rebuilt in that index order).  Candidates are tried in a
+ * fixed order (targets in input order, then permutations from a fixed-seed
+ * generator), so the generated kernel is deterministic. */
+struct MagicTerm {
+    uint32_t row, mask, mul, shift, width;
+};
+
+uint32_t magic_field(const MagicTerm& t, uint32_t s) {
+    return (((s & t.mask) * t.mul) >> t.shift) & ((1u << t.width) - 1u);
+}
+
+bool find_magic(uint32_t row, const std::vector<uint32_t>& a, MagicTerm* out) {
+    const uint32_t k = (uint32_t)a.size();
+    if (k < 3 || k > 8) return false;
+    uint32_t mask = 0;
+    for (uint32_t x : a) mask |= 1u << x;
+    uint64_t rng = 0x9E3779B97F4A7C15ull ^ ((uint64_t)mask << 8) ^ k;
+    auto next = [&]() {
+        rng ^= rng << 13;
+        rng ^= rng >> 7;
+        rng ^= rng << 17;
+        return rng;
+    };
+    std::vector<uint8_t> seen;
+    for (uint32_t width = k; width <= k; ++width) { /* a perfect field keeps the table size */
+        for (uint32_t shift = 0; shift + width <= 32; ++shift) {
+            for (int attempt = 0; attempt < 24; ++attempt) {
+                /* targets: the first attempt keeps the input order, later ones draw
+                 * a random injective placement of the k bits in the field */
+                std::vector<uint32_t> slot(width);
+                for (uint32_t i = 0; i < width; ++i) slot[i] = i;
+                if (attempt)
+                    for (uint32_t i = width - 1; i > 0; --i) std::swap(slot[i], slot[next() % (i + 1)]);
+                uint32_t mul = 0;
+                bool ok = true;
+                for (uint32_t i = 0; i < k && ok; ++i) {
+                    const uint32_t t = shift + slot[i];
+                    if (t < a[i]) ok = false;
+                    else mul |= 1u << (t - a[i]); /* equal shifts share one term */
+                }
+                if (!ok) continue;
+                MagicTerm m{row, mask, mul, shift, width};
+                seen.assign((size_t)1 << width, 0);
+                for (uint32_t x = 0; x < (1u << k) && ok; ++x) {
+                    uint32_t sw = 0;
+                    for (uint32_t i = 0; i < k; ++i) sw |= ((x >> i) & 1u) << a[i];
+                    const uint32_t f = magic_field(m, sw);
+                    if (seen[f]) ok = false;
+                    seen[f] = 1;
+                }
+                if (ok) {
+                    *out = m;
+                    return true;
+                }
+            }
+        }
+    }
+    return false;
+}
+
 struct Generated {
     std::string src;
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
@@ -145,11 +211,10 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     const uint64_t* ret = V.at<uint64_t>(H.off_ret);
     const uint32_t* pos = V.at<uint32_t>(H.off_pos);
     const uint32_t* tab = V.at<uint32_t>(H.off_tables);
-    const uint32_t table_bytes = H.off_ret - H.off_tables;
+    uint32_t table_bytes = H.off_ret - H.off_tables;
     const uint32_t* selslot = V.at<uint32_t>(H.off_selslot);
-    const bool tab_smem = table_bytes <= 48u * 1024u;
-    out->tab_bytes = tab_smem ? table_bytes : 0u;
     const uint32_t* subs = V.at<uint32_t>(H.off_subs);
+
     /* start offsets of every table (merged groups and split-node functions), sorted */
     std::vector<uint32_t> tab_starts;
     for (uint32_t g = 0; g < H.n_groups; ++g) {
@@ -159,6 +224,95 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     }
     std::sort(tab_starts.begin(), tab_starts.end());
 
+    /* Multiply gathers (PBN_COMPILE_MAGIC_GATHER): for every merged group, the inputs
+     * of one state word with 3 to 8 bits become one multiply-gather field when an
+     * injective multiplier exists; the other inputs stay single-bit gathers.  Such a
+     * group gets its table rebuilt in the new index order, appended after a copy of
+     * the plan's tables; the kernel then reads its tables from that array (a
+     * __device__ array of the generated source) instead of the plan image. */
+    struct GTerm {
+        bool magic;
+        MagicTerm m;         /* magic == true */
+        uint32_t row, bit;   /* single bit */
+        uint32_t off;        /* position of the field in the new index */
+    };
+    struct GPlan {
+        bool used = false;
+        std::vector<GTerm> terms;
+        uint32_t qn = 0, tab_off = 0, tab_words = 0;
+    };
+    std::vector<GPlan> gp(H.n_groups);
+    std::vector<uint32_t> tabm;
+    const bool magic = (flags & PBN_COMPILE_MAGIC_GATHER) != 0 && table_bytes <= 256u * 1024u;
+    if (magic) {
+        tabm.assign(tab, tab + table_bytes / 4);
+        for (uint32_t g = 0; g < H.n_groups; ++g) {
+            const pbn_img_group& G = groups[g];
+            if (G.l2w == PBN_IMG_SPLIT || G.q < 3) continue;
+            std::vector<uint32_t> rowb(G.q), bitb(G.q);
+            for (uint32_t b = 0; b < G.q; ++b) {
+                const uint32_t rec = inrec[4 * (G.in_chunk + 32 * (b / 4)) + (b & 3)];
+                rowb[b] = rec >> 7;
+                bitb[b] = ((b & 3) + (rec & 31)) & 31;
+            }
+            std::vector<uint32_t> rows(rowb);
+            std::sort(rows.begin(), rows.end());
+            rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+            GPlan GP;
+            uint32_t off = 0;
+            bool any = false;
+            for (uint32_t r : rows) {
+                std::vector<uint32_t> a;
+                for (uint32_t b = 0; b < G.q; ++b)
+                    if (rowb[b] == r) a.push_back(bitb[b]);
+                std::sort(a.begin(), a.end());
+                MagicTerm m;
+                if (find_magic(r, a, &m)) {
+                    GP.terms.push_back(GTerm{true, m, r, 0, off});
+                    off += m.width;
+                    any = true;
+                } else {
+                    for (uint32_t x : a) GP.terms.push_back(GTerm{false, MagicTerm{}, r, x, off++});
+                }
+            }
+            if (!any || off > 24) continue;
+            /* combined choices held by the table (padding entries are zero) */
+            auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
+            const uint64_t words_old = (nx == tab_starts.end() ? table_bytes / 4 : *nx) - G.tab_off;
+            const uint64_t prod = std::max<uint64_t>(1, (words_old * 32) >> (G.q + G.l2w));
+            const uint64_t bits_new = (prod << off) << G.l2w;
+            /* the copy plus the rebuilt tables stay within what is staged in shared memory */
+            if (bits_new > (UINT64_C(1) << 24) || (tabm.size() + (bits_new + 31) / 32) * 4 > 48u * 1024u) continue;
+            GP.tab_off = (uint32_t)tabm.size();
+            GP.tab_words = (uint32_t)((bits_new + 31) / 32);
+            tabm.resize(tabm.size() + GP.tab_words, 0u);
+            uint32_t* dst = tabm.data() + GP.tab_off;
+            const uint32_t emask = G.l2w >= 5 ? 0xFFFFFFFFu : ((1u << (1u << G.l2w)) - 1u);
+            for (uint64_t c = 0; c < prod; ++c) {
+                for (uint32_t x = 0; x < (1u << G.q); ++x) {
+                    const uint64_t bo = ((c << G.q) | x) << G.l2w;
+                    if ((bo >> 5) >= words_old) continue;
+                    const uint32_t v = (tab[G.tab_off + (bo >> 5)] >> (bo & 31)) & emask;
+                    /* the input pattern x as state words, then its new index */
+                    std::vector<uint32_t> sw(H.W32, 0u);
+                    for (uint32_t b = 0; b < G.q; ++b) sw[rowb[b]] |= ((x >> b) & 1u) << bitb[b];
+                    uint32_t xn = 0;
+                    for (const GTerm& t : GP.terms)
+                        xn |= (t.magic ? magic_field(t.m, sw[t.m.row]) : ((sw[t.row] >> t.bit) & 1u)) << t.off;
+                    const uint64_t bn = ((c << off) | xn) << G.l2w;
+                    dst[bn >> 5] |= v << (bn & 31);
+                }
+            }
+            GP.used = true;
+            GP.qn = off;
+            gp[g] = std::move(GP);
+        }
+        tabm.resize((tabm.size() + 3) & ~(size_t)3, 0u); /* bulk copies move multiples of 16 bytes */
+        table_bytes = (uint32_t)(tabm.size() * 4);
+    }
+    const bool tab_smem = table_bytes <= 48u * 1024u;
+    out->tab_bytes = tab_smem ? table_bytes : 0u;
+
     std::ostringstream o;
     o << "#include \"pbn_device.cuh\"\n";
     if (H.sampler == PBN_PERT_GEOMETRIC) {
@@ -167,14 +321,21 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         for (int k = 0; k < 64; ++k) o << (k ? ", " : "") << fmt("0x%016llxull", (unsigned long long)G[k]);
         o << "};\n";
     }
+    if (magic) {
+        /* the plan's tables followed by the rebuilt tables of multiply-gather groups */
+        o << "__device__ __align__(16) const uint32_t TABM[" << std::max<size_t>(tabm.size(), 4) << "] = {";
+        for (size_t i = 0; i < tabm.size(); ++i) o << (i ? (i % 8 ? ", " : ",\n  ") : "") << hex32(tabm[i]);
+        o << "};\n";
+    }
+    const char* tab_src = magic ? "reinterpret_cast<const uint8_t*>(TABM)" : "P.image + P.off_tables";
     o << "extern \"C\" __global__ void __launch_bounds__(512) pbn_plan_kernel(const pbn_jit_params P) {\n";
     o << "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n";
     if (tab_smem) {
-        o << "  if (!pbn_stage(smem, P.image + P.off_tables, P.tab_bytes, &bar)) {\n"
+        o << "  if (!pbn_stage(smem, " << tab_src << ", P.tab_bytes, &bar)) {\n"
              "    if (threadIdx.x == 0 && P.status) atomicOr(P.status, 1u);\n    return;\n  }\n"
              "  const uint32_t* TAB = reinterpret_cast<const uint32_t*>(smem);\n";
     } else {
-        o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(P.image + P.off_tables);\n";
+        o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(" << tab_src << ");\n";
     }
     o << "  const uint32_t lt = blockIdx.x * blockDim.x + threadIdx.x;\n"
          "  const bool active = lt < P.n_traj;\n"
@@ -319,7 +480,8 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         const uint32_t* wgroups = V.at<uint32_t>(H.off_wgroups);
         for (uint32_t r = 0; r < H.W32; ++r) {
             for (uint32_t i = words[r].x; i < words[r].x + words[r].y; ++i) {
-                const pbn_img_group& G = groups[wgroups[i]];
+                const uint32_t gi = wgroups[i];
+                const pbn_img_group& G = groups[gi];
                 o << "        { ";
                 if (G.l2w == PBN_IMG_SPLIT) {
                     /* split node: every function's pattern is a few register operations;
@@ -363,9 +525,27 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
                     if (j.empty()) continue;
                     cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
                 }
-                /* input pattern */
-                const uint32_t q = G.q;
-                o << "const uint32_t x = " << pattern(G.in_chunk, q, 32) << "; ";
+                /* input pattern: single-bit gathers, or multiply-gather fields */
+                const GPlan& GP = gp[gi];
+                const uint32_t q = GP.used ? GP.qn : G.q;
+                if (GP.used) {
+                    std::string xe;
+                    for (const GTerm& t : GP.terms) {
+                        std::string term;
+                        if (t.magic) {
+                            const MagicTerm& m = t.m;
+                            term = fmt("((((s%u & %s) * %s) >> %u) & %s)", m.row, hex32(m.mask).c_str(), hex32(m.mul).c_str(),
+                                       m.shift, hex32((1u << m.width) - 1u).c_str());
+                            if (t.off) term = "(" + term + fmt(" << %u)", t.off);
+                        } else {
+                            term = gather(t.row, t.bit, t.off);
+                        }
+                        xe += (xe.empty() ? "" : " | ") + term;
+                    }
+                    o << "const uint32_t x = " << xe << "; ";
+                } else {
+                    o << "const uint32_t x = " << pattern(G.in_chunk, q, 32) << "; ";
+                }
                 if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
                 else o << "const uint32_t e = x; ";
                 /* table entry */
@@ -374,18 +554,21 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
                 const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
                 /* size of this group's table in words: up to the next table's offset, or the end */
                 auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
-                const uint32_t tab_words = (nx == tab_starts.end() ? table_bytes / 4 : *nx) - G.tab_off;
+                const uint32_t toff = GP.used ? GP.tab_off : G.tab_off;
+                const uint32_t tab_words = GP.used ? GP.tab_words
+                                                   : (nx == tab_starts.end() ? (H.off_ret - H.off_tables) / 4 : *nx) - G.tab_off;
+                const uint32_t* tabv = magic ? tabm.data() : tab;
                 std::string v;
                 if (tab_words == 1) {
-                    v = fmt("((%s >> (e << %u)) & %s)", hex32(tab[G.tab_off]).c_str(), l2w, hex32(emask).c_str());
+                    v = fmt("((%s >> (e << %u)) & %s)", hex32(tabv[toff]).c_str(), l2w, hex32(emask).c_str());
                 } else if (tab_words == 2) {
-                    const uint64_t t64 = ((uint64_t)tab[G.tab_off + 1] << 32) | tab[G.tab_off];
+                    const uint64_t t64 = ((uint64_t)tabv[toff + 1] << 32) | tabv[toff];
                     v = fmt("((uint32_t)(0x%016llxull >> (e << %u)) & %s)", (unsigned long long)t64, l2w, hex32(emask).c_str());
                 } else if (tab_smem) {
-                    v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w,
+                    v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", toff, l2w, l2w,
                             hex32(emask).c_str());
                 } else {
-                    v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", G.tab_off, l2w, l2w,
+                    v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", toff, l2w, l2w,
                             hex32(emask).c_str());
                 }
                 o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
@@ -703,7 +886,7 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 
 extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
-    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED))
+    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
     const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;

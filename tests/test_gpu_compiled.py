@@ -156,3 +156,30 @@ def test_compiled_geometric_sampler(oracle_mod, flags, p):
     plan.compile(flags)
     orc = oracle_mod.simulate(text, 41, 0, 128, 400, meta_ids=meta, trace=True, nthreads=NCPU, sampler=1)
     _compare(run(plan, seed=41, n_traj=128, n_steps=400, meta=meta, trace=True, kernel=COMPILED), orc, ids)
+
+
+
+@pytest.mark.parametrize("which", ["tiny12", "paper100", "paper100_mi12", "nodewise", "geometric", "split"])
+@pytest.mark.parametrize("flags", [_lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER,
+                                   _lib.PBN_COMPILE_PIPELINED | _lib.PBN_COMPILE_MAGIC_GATHER])
+def test_compiled_magic_gather(oracle_mod, which, flags):
+    """Multiply gathers with rebuilt tables: bit-exact against the oracle."""
+    kw, sem, samp = {}, 0, 0
+    if which == "tiny12":
+        text, meta = synth.tiny12(1).to_text(), [0, 1, 2]
+    elif which == "split":
+        text, meta = synth.random_pbn(5, 40, 1e-2, k_choices=tuple(range(1, 11))).to_text(), [0, 1]
+        kw = dict(max_inputs=6)
+    else:
+        text, meta = synth.paper100(seed=2, p=3e-3).to_text(), [0, 1, 2]
+        if which == "paper100_mi12":
+            kw = dict(max_inputs=12)
+        if which == "nodewise":
+            kw, sem = dict(semantics=_lib.PBN_SEM_NODEWISE), 1
+        if which == "geometric":
+            kw, samp = dict(sampler=_lib.PBN_PERT_GEOMETRIC), 1
+    plan, ids = plan_for(text, meta, **kw)
+    plan.compile(flags)
+    orc = oracle_mod.simulate(text, 51, 0, 160, 500, meta_ids=meta, trace=True, nthreads=NCPU,
+                              semantics=sem, sampler=samp)
+    _compare(run(plan, seed=51, n_traj=160, n_steps=500, meta=meta, trace=True, kernel=COMPILED), orc, ids)
