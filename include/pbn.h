@@ -333,6 +333,11 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
  * is rebuilt in that index order and the kernel reads its tables from its own
  * array.  Same results. */
 #define PBN_COMPILE_MAGIC_GATHER 0x8u
+/* PBN_COMPILE_WIDE: plans of up to 2048 nodes and any number of SEL blocks; the
+ * groups are evaluated in the order of the SEL blocks they read and each block is
+ * drawn just before its first use (the interleaved and pipelined forms do not
+ * apply).  Meant for wide networks with few trajectories. */
+#define PBN_COMPILE_WIDE 0x10u
 
 /* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
  * thread, local-memory (spill) bytes per thread and the flags it was compiled with;

@@ -36,6 +36,7 @@ PBN_COMPILE_PERT_UNROLLED = 0x1
 PBN_COMPILE_INTERLEAVED = 0x2
 PBN_COMPILE_PIPELINED = 0x4
 PBN_COMPILE_MAGIC_GATHER = 0x8
+PBN_COMPILE_WIDE = 0x10
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1

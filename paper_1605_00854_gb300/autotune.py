@@ -56,7 +56,8 @@ def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
 def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 1,
                  max_inputs_options=(4, 6, 8, 12), lanes_options=(1, 2, 4, 8, 16, 32),
                  compile_flags_options=(0, _lib.PBN_COMPILE_INTERLEAVED, _lib.PBN_COMPILE_PIPELINED,
-                                        _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER),
+                                        _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER,
+                                        _lib.PBN_COMPILE_PIPELINED | _lib.PBN_COMPILE_MAGIC_GATHER),
                  try_compiled: bool = True, cache_file: str | None = None, log=None,
                  sampler: int = _lib.PBN_PERT_BITSLICED) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
@@ -100,6 +101,9 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
             cands = []
             if try_compiled and budget == 0:
                 cands += [(_lib.PBN_KERNEL_COMPILED, 1, f) for f in compile_flags_options]
+                # plans too wide for the default forms: the wide form, while its code stays small
+                if plan.info.n_sel_blocks > 24 and plan.info.n_groups <= 512:
+                    cands.append((_lib.PBN_KERNEL_COMPILED, 1, _lib.PBN_COMPILE_WIDE))
             # at most about one lane per state word
             cands += [(_lib.PBN_KERNEL_INTERP, lg, 0) for lg in lanes_options
                       if lg == 1 or lg <= 2 * plan.info.state_words]

@@ -194,11 +194,14 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         *why = "state wider than 64 words";
         return false;
     }
-    if (H.W > 16) {
-        *why = "more than 1024 original nodes";
+    /* wide plans: SEL blocks drawn lazily in group order, so their uniforms are live
+     * only while the groups that need them are evaluated */
+    const bool wide = (flags & PBN_COMPILE_WIDE) != 0;
+    if (H.W > (wide ? 32u : 16u)) {
+        *why = wide ? "more than 2048 original nodes" : "more than 1024 original nodes";
         return false;
     }
-    if (H.n_sel > 24) {
+    if (!wide && H.n_sel > 24) {
         *why = "more than 24 selection blocks per step";
         return false;
     }
@@ -380,8 +383,9 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     /* the geometric sampler has no level loop to pipeline: its pipelined form is
      * the interleaved one */
     const bool geometric = H.sampler == PBN_PERT_GEOMETRIC;
-    const bool pipelined = (flags & PBN_COMPILE_PIPELINED) != 0 && !geometric;
-    const bool interleave = (flags & PBN_COMPILE_INTERLEAVED) != 0 || ((flags & PBN_COMPILE_PIPELINED) != 0 && geometric);
+    const bool pipelined = (flags & PBN_COMPILE_PIPELINED) != 0 && !geometric && !wide;
+    const bool interleave = !wide && ((flags & PBN_COMPILE_INTERLEAVED) != 0 ||
+                                      ((flags & PBN_COMPILE_PIPELINED) != 0 && geometric));
     /* node-wise semantics: every step evaluates the functions and the perturbed
      * nodes (collected in masks) take NOT s */
     const bool nodewise = H.semantics == PBN_SEM_NODEWISE;
@@ -474,14 +478,43 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         }
         return xexpr.empty() ? std::string("0u") : xexpr;
     };
-    /* merged-table evaluation of every group from s and the SEL uniforms U: n<row> */
+    /* merged-table evaluation of every group from s and the SEL uniforms U: n<row>.
+     * Wide plans take the groups in the order of the last SEL block they read and
+     * draw each block just before its first use. */
     auto emit_eval = [&]() {
         for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
         const uint32_t* wgroups = V.at<uint32_t>(H.off_wgroups);
-        for (uint32_t r = 0; r < H.W32; ++r) {
-            for (uint32_t i = words[r].x; i < words[r].x + words[r].y; ++i) {
-                const uint32_t gi = wgroups[i];
+        std::vector<std::pair<uint32_t, uint32_t>> order; /* (row, group) */
+        for (uint32_t r = 0; r < H.W32; ++r)
+            for (uint32_t i = words[r].x; i < words[r].x + words[r].y; ++i) order.push_back({r, wgroups[i]});
+        std::vector<uint8_t> drawn(H.n_sel, 0);
+        auto blocks_of = [&](uint32_t gi) {
+            std::vector<uint32_t> b;
+            const pbn_img_group& G = groups[gi];
+            for (uint32_t m = 0; m < G.n_mul; ++m) b.push_back(multi[G.mul_first + 32 * m].ch_off / 4);
+            return b;
+        };
+        if (wide) {
+            std::stable_sort(order.begin(), order.end(), [&](const std::pair<uint32_t, uint32_t>& x,
+                                                             const std::pair<uint32_t, uint32_t>& y) {
+                const auto bx = blocks_of(x.second), by = blocks_of(y.second);
+                const uint32_t mx = bx.empty() ? 0 : *std::max_element(bx.begin(), bx.end());
+                const uint32_t my = by.empty() ? 0 : *std::max_element(by.begin(), by.end());
+                return mx < my;
+            });
+        }
+        for (const auto& ri : order) {
+            {
+                const uint32_t r = ri.first;
+                const uint32_t gi = ri.second;
                 const pbn_img_group& G = groups[gi];
+                if (wide)
+                    for (uint32_t b : blocks_of(gi))
+                        if (!drawn[b]) {
+                            drawn[b] = 1;
+                            o << "        const uint4 U" << b << " = pbn_philox_draw(P, ps, "
+                              << hex32((PBN_DOM_SEL << 28) | selblk[b]) << ");\n";
+                        }
                 o << "        { ";
                 if (G.l2w == PBN_IMG_SPLIT) {
                     /* split node: every function's pattern is a few register operations;
@@ -728,7 +761,7 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         }
         /* 2. selection draws and merged-table evaluation */
         o << (nodewise ? "      {\n" : "      if (!any) {\n");
-        if (!interleave) emit_sel_draws("        ", "const uint4 ", "U", "ps");
+        if (!interleave && !wide) emit_sel_draws("        ", "const uint4 ", "U", "ps");
         emit_eval();
         for (uint32_t r = 0; r < H.W32; ++r) {
             if (nodewise) o << "        s" << r << " = (n" << r << " & ~g" << r << ") | (~s" << r << " & g" << r << ");\n";
@@ -886,7 +919,8 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 
 extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
-    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER))
+    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER |
+                  PBN_COMPILE_WIDE))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
     const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;

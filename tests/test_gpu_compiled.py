@@ -183,3 +183,17 @@ def test_compiled_magic_gather(oracle_mod, which, flags):
     orc = oracle_mod.simulate(text, 51, 0, 160, 500, meta_ids=meta, trace=True, nthreads=NCPU,
                               semantics=sem, sampler=samp)
     _compare(run(plan, seed=51, n_traj=160, n_steps=500, meta=meta, trace=True, kernel=COMPILED), orc, ids)
+
+
+
+@pytest.mark.parametrize("sampler", [0, 1])
+def test_compiled_wide_plan(oracle_mod, sampler):
+    """A plan with more than 24 SEL blocks compiles only in the wide form (SEL
+    blocks drawn lazily in group order); bit-exact against the oracle."""
+    text = synth.paper100(seed=21, n=400, p=1e-3).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta, sampler=sampler)
+    assert plan.info.n_sel_blocks > 24
+    plan.compile(_lib.PBN_COMPILE_WIDE)
+    orc = oracle_mod.simulate(text, 61, 0, 96, 300, meta_ids=meta, trace=True, nthreads=NCPU, sampler=sampler)
+    _compare(run(plan, seed=61, n_traj=96, n_steps=300, meta=meta, trace=True, kernel=COMPILED), orc, ids)

@@ -336,7 +336,7 @@ def test_estimate_rejects_bad_arguments():
 # ------------------------------------------------------------ compiled plans ----
 @pytest.mark.parametrize("flags", [0, 1, 2, 4, 10])
 @pytest.mark.parametrize("which", ["paper100", "paper100_plain", "tiny12", "p0", "one_node", "p_half",
-                                   "split_small", "split_wide", "nodewise", "geometric"])
+                                   "split_small", "split_wide", "nodewise", "geometric", "wide"])
 def test_generated_plan_kernels_compile(tmp_path, which, flags):
     """The source generated for a plan's own kernel compiles for sm_103a."""
     import shutil
@@ -364,6 +364,13 @@ def test_generated_plan_kernels_compile(tmp_path, which, flags):
         text, meta = synth.paper100(seed=2).to_text(), [0, 1, 2]
         red, _ = api.Net.load(text).reduce(meta)
         kw = dict(semantics=_lib.PBN_SEM_NODEWISE)
+    if which == "wide":
+        # more than 24 SEL blocks: only the wide form compiles it
+        text, meta = synth.paper100(seed=21, n=400, p=1e-3).to_text(), [0, 1, 2]
+        red, _ = api.Net.load(text).reduce(meta)
+        with pytest.raises(_lib.PbnError):
+            api.Plan(red).source(flags)
+        flags |= _lib.PBN_COMPILE_WIDE
     if which == "geometric":
         text, meta = synth.paper100(seed=2, n=150).to_text(), [0, 1, 2]
         red, _ = api.Net.load(text).reduce(meta)
