@@ -104,3 +104,38 @@ def test_paper100_full_size_geometric_sampler(oracle_mod):
     for t, o in zip(sample, outs):
         assert np.array_equal(final[t, ids], o["final"][0, ids]), t
         assert np.array_equal(counts[t], o["counts"][0]), t
+
+
+@pytest.mark.parametrize("workload", ["paper100", "scalefree2000"])
+def test_full_size_in_the_bench_launch_configuration(oracle_mod, workload):
+    """The configuration bench.py times: the autotuner's choice of group size,
+    kernel, code shape and lanes per trajectory, at the benchmark size; sampled
+    trajectories recomputed by the oracle, count invariants for all of them."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1605_00854_gb300 import autotune
+    if workload == "paper100":
+        text, meta, T, S, steps = synth.paper100(seed=2).to_text(), META, 1 << 16, 10**6, 2000
+        sample = [5, 65000, 33333]
+    else:
+        text, meta, T, S, steps = synth.scalefree2000(seed=3).to_text(), [0, 1, 2, 3], 1 << 14, 10**5, 200
+        sample = [7, 16000]
+    ch = autotune.tune_network(text, meta, T, steps=steps)
+    plan = autotune.plan_for_choice(text, meta, ch)
+    _, ids = api.Net.load(text).reduce(meta)
+    bufs = api.alloc_buffers(plan, T)
+    api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=meta, kernel=ch.kernel, lanes_per_traj=ch.lanes_per_traj)
+    torch.cuda.synchronize()
+    assert int(bufs.status.item()) == 0
+    counts = bufs.counts.cpu().numpy().view(np.uint64).T
+    final = plan.unpack(bufs.state.cpu().numpy().view(np.uint64))
+    assert np.all(counts[:, 1:].sum(axis=1) == S)
+    assert np.array_equal(bufs.pooled.cpu().numpy().view(np.uint64), counts.sum(axis=0))
+    def one(t):
+        return oracle_mod.simulate(text, SEED, t, 1, S, meta_ids=meta)
+    with ThreadPoolExecutor(max_workers=min(len(sample), os.cpu_count() or 1)) as ex:
+        outs = list(ex.map(one, sample))
+    for t, o in zip(sample, outs):
+        assert np.array_equal(final[t, ids], o["final"][0, ids]), (t, ch)
+        assert np.array_equal(counts[t], o["counts"][0]), (t, ch)
