@@ -387,7 +387,11 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
                          "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "ops_per_traj_step": ops,
-                         "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz ({src} max SM clock)"},
+                         "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz ({src} max SM clock)",
+                         # the HBM side, for context: state, counts and plan image per launch
+                         "hbm": None if traffic is None else {
+                             "achieved_gbs": traffic / kernel_s / 1e9, "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),
+                             "frac": traffic / kernel_s / 1e9 / float(pk.get("hbm_gbs", 6800.0))}},
             "e2e": {"value": e2e_value, "unit": "node-updates/s",
                     "h2d_bytes_per_step": int(img_host.numel()),
                     "d2h_bytes_per_step": int(st_h.numel() * 8 + cnt_h.numel() * 8 + pool_h.numel() * 8)},
@@ -438,6 +442,21 @@ def run_batch(args):
         api.simulate(e["plan"], e["bufs"], seed=e["seed"], n_steps=S, meta_ids=META, kernel=_lib.PBN_KERNEL_INTERP)
     e1.record(); torch.cuda.synchronize()
     t_each = e0.elapsed_time(e1) / 1e3
+    # the plain method (unreduced, one node per group) per network, on 1,000 steps
+    S0 = min(S, 1000)
+    plain_plans, tot0 = [], 0.0
+    for i, (n, T, p) in enumerate(shapes):
+        try:
+            pp = api.Plan(api.Net.load(plain[i]), mode=_lib.PBN_PLAN_PLAIN, sampler=SAMPLERS[args.sampler])
+        except _lib.PbnError:  # a plain plan whose specs exceed shared memory is left out
+            continue
+        plain_plans.append((pp, api.alloc_buffers(pp, T), entries[i]))
+        tot0 += n * T * S0
+    e0.record()
+    for pp, bb, e in plain_plans:
+        api.simulate(pp, bb, seed=e["seed"], n_steps=S0, meta_ids=META, kernel=_lib.PBN_KERNEL_INTERP)
+    e1.record(); torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 1e3
     line = {"metric": "PBN node-updates/s, batched persistent launch (256 networks)", "value": tot / t_batch,
             "unit": "node-updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": t_batch * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
@@ -447,6 +466,9 @@ def run_batch(args):
                        "host_prep_s": round(prep, 2), "graph": "chunk launches captured in one CUDA graph",
                        "perturbation_sampler": args.sampler},
             "per_network_launches": {"value": tot / t_each, "unit": "node-updates/s", "seconds": t_each},
+            "per_network_plain_launches": {"value": tot0 / t_plain, "unit": "node-updates/s", "seconds": t_plain,
+                                           "n_steps": S0, "plan": "unreduced, one node per group",
+                                           "networks": len(plain_plans)},
             "speedup_vs_per_network": t_each / t_batch}
     print(json.dumps(line), flush=True)
 
