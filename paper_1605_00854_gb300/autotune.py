@@ -36,9 +36,11 @@ class Choice:
 
 
 def _shape_key(net: api.Net, meta, n_traj: int) -> str:
+    import torch
     info = net.info()
     tb = max(0, n_traj.bit_length() - 1)
-    return f"n{info.n}-f{info.n_functions}-m{len(meta)}-p{info.P}-t{tb}"
+    gpu = torch.cuda.get_device_name().replace(" ", "_") if torch.cuda.is_available() else "cpu"
+    return f"{gpu}-n{info.n}-f{info.n_functions}-m{len(meta)}-p{info.P}-t{tb}"
 
 
 def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:

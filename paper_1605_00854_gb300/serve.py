@@ -387,7 +387,12 @@ class Server:
         self._drop_cancelled()
         if not self.active:
             return []
-        return self._round()
+        nvtx = self.torch.cuda.nvtx
+        nvtx.range_push(f"pbn serve round {self.stats['rounds']}: {len(self.active)} queries")
+        try:
+            return self._round()
+        finally:
+            nvtx.range_pop()
 
     def drain(self, timeout: float = 600.0):
         """Run rounds until every submitted query has completed."""
