@@ -8,8 +8,11 @@
  * input gathers are constant shifts and masks, the selection thresholds and the
  * levels of P are immediates, and merged tables of at most 64 bits are immediates
  * too; larger tables are staged into shared memory by a bulk copy.  The step
- * semantics (Eq. 1) and the keyed draws are identical, so the results are bit for
- * bit those of the interpreter and of the unreduced definition.
+ * semantics (Eq. 1, or the plan's node-wise variant) and the keyed draws (of the
+ * plan's perturbation sampler) are identical, so the results are bit for bit those
+ * of the interpreter and of the unreduced definition.  Flags choose the code shape:
+ * how the perturbation levels are scheduled, multiply gathers, and the wide form
+ * for plans with many SEL blocks.
  *
  * Compilation costs host time (tens to hundreds of milliseconds), which pays off
  * for long runs of one network, as the paper observes for its own pre-processing
