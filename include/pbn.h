@@ -274,12 +274,14 @@ typedef struct {
     void* d_pooled;  /* device uint64 [5] or NULL: the same counts summed over the
                         trajectories of this call, accumulated with atomics */
     void* d_status;  /* device uint32 or NULL: ORed with PBN_DEV_* bits on error */
-    void* d_trace;   /* device uint64 [n_steps][state_words][n_traj] or NULL: the
-                        state after every step (for checking; slows the kernel) */
+    void* d_trace;   /* device uint64 [n_steps / trace_stride][state_words][n_traj] or NULL:
+                        snapshots of the state after every trace_stride-th step of the
+                        call (snapshot i after step i * trace_stride + trace_stride - 1
+                        of the call; for checking and sampling; slows the kernel) */
     uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8, 16, 32 */
     uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj */
     uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP or PBN_KERNEL_COMPILED */
-    uint32_t reserved;
+    uint32_t trace_stride;     /* steps between snapshots (0 or 1: every step) */
 } pbn_sim_args;
 
 #define PBN_KERNEL_AUTO 0u     /* the compiled plan kernel if pbn_plan_compile succeeded, else the interpreter */

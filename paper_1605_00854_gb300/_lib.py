@@ -89,7 +89,7 @@ class SimArgs(ctypes.Structure):
                 ("n_steps", u64), ("count_from", u64), ("init", u32), ("n_meta", u32),
                 ("meta_ids", vp), ("meta_vals", vp), ("d_state", vp), ("d_counts", vp),
                 ("d_pooled", vp), ("d_status", vp), ("d_trace", vp),
-                ("lanes_per_traj", u32), ("trajs_per_block", u32), ("kernel", u32), ("reserved", u32)]
+                ("lanes_per_traj", u32), ("trajs_per_block", u32), ("kernel", u32), ("trace_stride", u32)]
 
 
 class EstimateOut(ctypes.Structure):

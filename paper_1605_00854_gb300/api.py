@@ -220,7 +220,8 @@ def alloc_buffers(plan: Plan, n_traj: int, device="cuda") -> SimBuffers:
 def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids, meta_vals=None,
              traj_begin: int = 0, step_begin: int = 0, count_from: int = 0, init: int | None = None,
              trace=None, lanes_per_traj: int = 0, trajs_per_block: int = 0, stream=None,
-             d_image=None, n_traj: int | None = None, kernel: int = _lib.PBN_KERNEL_AUTO):
+             d_image=None, n_traj: int | None = None, kernel: int = _lib.PBN_KERNEL_AUTO,
+             trace_stride: int = 1):
     """Enqueue pbn_simulate on `stream` (default: torch's current stream)."""
     import torch
     L = _lib.load()
@@ -243,6 +244,7 @@ def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids,
     a.d_trace = None if trace is None else trace.data_ptr()
     a.lanes_per_traj, a.trajs_per_block = lanes_per_traj, trajs_per_block
     a.kernel = kernel
+    a.trace_stride = trace_stride
     img = plan.device_image(bufs.state.device) if d_image is None else d_image
     st = torch.cuda.current_stream(bufs.state.device) if stream is None else stream
     check(L.pbn_simulate(plan._h, ctypes.c_void_p(img.data_ptr()), ctypes.byref(a),

@@ -92,6 +92,7 @@ struct ItemView {
         off_pos, off_tables, n_groups, off_subs, per_node, sampler, off_geo, off_wgroups;
     uint64_t geo_full, geo_last;
     uint32_t n_meta_rows;
+    uint32_t trace_stride;
     const uint32_t* meta_row;
     const uint32_t* meta_mask;
     const uint32_t* meta_val;
@@ -164,6 +165,7 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
         V.state = D.state;
         V.counts = D.counts;
         V.trace = nullptr;
+        V.trace_stride = 1;
         V.traj_begin = D.traj_begin;
         const uint64_t sb = D.step_begin + B.step_offset;
         V.step_begin = sb;

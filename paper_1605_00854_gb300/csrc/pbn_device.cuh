@@ -36,6 +36,7 @@ typedef struct {
     uint32_t key1[10];
     uint32_t n_traj, n_steps;
     uint32_t kv0, kp0, pairs, count_first, init;
+    uint32_t trace_stride;       /* steps between trace snapshots (>= 1) */
     uint32_t tab_bytes;          /* bytes of the tables section staged into shared memory (0: read global) */
     uint32_t off_tables, off_ret, off_pos, image_bytes;
     uint32_t meta_mask[PBN_JIT_MAX_ROWS];  /* meta-state mask and value per 32-bit state row */

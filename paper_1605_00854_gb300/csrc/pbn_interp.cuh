@@ -370,10 +370,11 @@ __device__ __forceinline__ void pbn_interp_run(const VT& P, uint8_t* smem, uint3
                 c01 += cp & (zp ^ 1u) & z;
                 c10 += cp & zp & (z ^ 1u);
                 zp = z;
-                if (TRACE) {
+                if (TRACE && (k + 1) % P.trace_stride == 0) {
+                    const uint64_t snap = (k + 1) / P.trace_stride - 1;
                     for (uint32_t r = 0; r < W32; r += 2) {
                         const uint64_t v = ((uint64_t)Sb[r + 1] << 32) | Sb[r];
-                        P.trace[((uint64_t)k * (W32 / 2) + r / 2) * P.n_traj + lt] = v;
+                        P.trace[(snap * (W32 / 2) + r / 2) * P.n_traj + lt] = v;
                     }
                 }
             }

@@ -616,9 +616,10 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         o << "      { const uint32_t z = " << z << ";\n"
              "        const uint32_t cv = k >= P.kv0 ? 1u : 0u, cp = k >= P.kp0 ? 1u : 0u;\n"
              "        cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u); zp = z; }\n";
-        o << "      if (P.trace) {\n";
+        o << "      if (P.trace && (k + 1) % P.trace_stride == 0) {\n"
+             "        const uint64_t snap = (k + 1) / P.trace_stride - 1;\n";
         for (uint32_t r = 0; r < H.W32; r += 2)
-            o << "        P.trace[((uint64_t)k * " << H.W32 / 2 << "u + " << r / 2 << "u) * P.n_traj + lt] = ((uint64_t)s"
+            o << "        P.trace[(snap * " << H.W32 / 2 << "u + " << r / 2 << "u) * P.n_traj + lt] = ((uint64_t)s"
               << r + 1 << " << 32) | s" << r << ";\n";
         o << "      }\n";
     };

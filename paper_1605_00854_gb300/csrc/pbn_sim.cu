@@ -68,6 +68,7 @@ struct SimParams {
         off_tables, n_groups, off_subs, per_node, sampler, off_geo, off_wgroups;
     uint64_t geo_full, geo_last;  /* geometric sampler: thresholds of a full and the last word */
     uint32_t n_meta_rows;
+    uint32_t trace_stride;     /* steps between trace snapshots (>= 1) */
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
     uint32_t meta_val[kMaxMetaRows];
@@ -178,7 +179,8 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     if (a->init == PBN_INIT_KEYED && a->step_begin != 0) return fail(PBN_EINVAL, "pbn_simulate: keyed initial state needs step_begin == 0");
     if (a->kernel > PBN_KERNEL_COMPILED) return fail(PBN_EINVAL, "pbn_simulate: unknown kernel selector %u", a->kernel);
     if (a->n_meta < 1 || a->n_meta > 1024 || !a->meta_ids) return fail(PBN_EINVAL, "pbn_simulate: need 1..1024 meta-state nodes");
-    if (a->d_trace && a->n_steps * (uint64_t)plan->info.state_words * a->n_traj >= (1ull << 40))
+    const uint32_t tstride = a->trace_stride ? a->trace_stride : 1u;
+    if (a->d_trace && (a->n_steps / tstride) * (uint64_t)plan->info.state_words * a->n_traj >= (1ull << 40))
         return fail(PBN_EINVAL, "pbn_simulate: trace too large");
 
     const pbn_img_header& H = plan->hdr;
@@ -211,6 +213,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     P.pooled = static_cast<unsigned long long*>(a->d_pooled);
     P.status = static_cast<uint32_t*>(a->d_status);
     P.trace = static_cast<uint64_t*>(a->d_trace);
+    P.trace_stride = tstride;
     P.traj_begin = a->traj_begin;
     P.step_begin = a->step_begin;
     const uint32_t k0 = (uint32_t)a->seed, k1 = (uint32_t)(a->seed >> 32);
@@ -280,6 +283,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
         J.pooled = P.pooled;
         J.status = P.status;
         J.trace = P.trace;
+        J.trace_stride = P.trace_stride;
         J.traj_begin = P.traj_begin;
         J.step_begin = P.step_begin;
         memcpy(J.key0, P.key0, sizeof(J.key0));

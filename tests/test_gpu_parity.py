@@ -274,3 +274,21 @@ def test_geometric_sampler_nodewise(oracle_mod):
     orc = oracle_mod.simulate(text, 8, 0, 64, 800, meta_ids=meta, trace=True, semantics=1, sampler=1)
     _compare(run(plan, seed=8, n_traj=64, n_steps=800, meta=meta, trace=True, kernel=_lib.PBN_KERNEL_INTERP),
              orc, ids)
+
+
+@pytest.mark.parametrize("kernel", [_lib.PBN_KERNEL_INTERP, _lib.PBN_KERNEL_COMPILED])
+def test_trace_snapshots_with_a_stride(kernel):
+    """Snapshots every 7th step equal every 7th row of the full trace."""
+    import torch
+    from paper_1605_00854_gb300 import api
+    text = synth.paper100(seed=2, p=3e-3).to_text()
+    meta = [0, 1, 2]
+    plan, ids = plan_for(text, meta)
+    T, S, k = 96, 300, 7
+    full = torch.zeros((S, plan.info.state_words, T), dtype=torch.int64, device="cuda")
+    snap = torch.zeros((S // k, plan.info.state_words, T), dtype=torch.int64, device="cuda")
+    for tr, st in ((full, 1), (snap, k)):
+        bufs = api.alloc_buffers(plan, T)
+        api.simulate(plan, bufs, seed=3, n_steps=S, meta_ids=meta, trace=tr, trace_stride=st, kernel=kernel)
+    torch.cuda.synchronize()
+    assert torch.equal(snap, full[k - 1:: k][: S // k])
