@@ -330,15 +330,12 @@ class Server:
         n_eff = sum(b.n_traj for b in a.blocks if b.step >= b.count_from)
         burn = min(b.count_from for b in a.blocks)
         est = api.estimate(c, max(1, n_eff), a.q.r, a.q.s, a.q.eps, burn_in_used=burn)
-        # the worst-case sample size of a proportion, (z / r)^2 / 4: no decision is taken
-        # on fewer counted states
-        n_min = math.ceil(0.25 * (est.z / a.q.r) ** 2)
-        if est.L < n_min and a.step < self.max_steps:
-            return False
         if not est.defined or est.m_star == 2**64 - 1:
             # the meta-state was never (or always) seen, so the chain's switching rates
-            # are not estimable: stop at n_min and report pi = V / L
-            if a.step >= self.max_steps or int(c[0]) == 0 or int(c[0]) == est.L:
+            # are not estimable: stop at the worst-case sample size of a proportion,
+            # (z / r)^2 / 4, and report pi = V / L
+            n_min = math.ceil(0.25 * (est.z / a.q.r) ** 2)
+            if a.step >= self.max_steps or (est.L >= n_min and (int(c[0]) == 0 or int(c[0]) == est.L)):
                 self._finish(a, est, c)
                 return True
             return False
