@@ -279,7 +279,8 @@ typedef struct {
                         call (snapshot i after step i * trace_stride + trace_stride - 1
                         of the call; for checking and sampling; slows the kernel) */
     uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8, 16, 32 */
-    uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj */
+    uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj with
+                                  trajs_per_block * lanes_per_traj <= 1024 */
     uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP or PBN_KERNEL_COMPILED */
     uint32_t trace_stride;     /* steps between snapshots (0 or 1: every step) */
 } pbn_sim_args;

@@ -39,6 +39,7 @@ namespace {
 constexpr uint32_t kWeyl0 = 0x9E3779B9u;
 constexpr uint32_t kWeyl1 = 0xBB67AE85u;
 constexpr int kMaxMetaRows = 16;
+constexpr uint32_t kMaxCtaThreads = 1024;
 
 struct SimParams {
     const uint8_t* image;      /* device copy of the plan image */
@@ -74,8 +75,10 @@ struct SimParams {
     uint32_t meta_val[kMaxMetaRows];
 };
 
+/* up to 1024 threads per CTA (64 registers a thread): a plan whose specs fill most of
+ * shared memory runs one CTA per SM, and its warps are then all the SM has */
 template <int LG, bool TRACE, bool TAB_SMEM>
-__global__ void __launch_bounds__(512) pbn_sim_kernel(const SimParams P) {
+__global__ void __launch_bounds__(kMaxCtaThreads) pbn_sim_kernel(const SimParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t stage_bar;
 
@@ -329,12 +332,12 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     uint32_t nt = a->trajs_per_block;
     if (nt == 0) {
         /* k CTAs per SM, trajectories spread evenly: the grid is close to a multiple
-         * of the SM count, with at most 512 threads per CTA */
+         * of the SM count, with at most kMaxCtaThreads threads per CTA */
         const uint32_t unit = 32 / LG; /* trajectories per warp */
         for (uint64_t k = 1;; ++k) {
             uint64_t want = (a->n_traj + (uint64_t)sms * k - 1) / ((uint64_t)sms * k);
             want = ((want + unit - 1) / unit) * unit;
-            if (want * LG <= 512 && fixed + per_traj * want <= smem_lim) {
+            if (want * LG <= kMaxCtaThreads && fixed + per_traj * want <= smem_lim) {
                 nt = (uint32_t)want;
                 break;
             }
@@ -344,8 +347,8 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
             }
         }
     }
-    if ((nt * LG) % 32 != 0 || nt * LG > 512 || nt == 0)
-        return fail(PBN_EINVAL, "pbn_simulate: trajs_per_block * lanes_per_traj must be a multiple of 32 and <= 512");
+    if ((nt * LG) % 32 != 0 || nt * LG > kMaxCtaThreads || nt == 0)
+        return fail(PBN_EINVAL, "pbn_simulate: trajs_per_block * lanes_per_traj must be a multiple of 32 and <= 1024");
     const size_t smem = fixed + per_traj * nt;
     if (smem > smem_lim) return fail(PBN_ETOOBIG, "pbn_simulate: %zu bytes of shared memory exceed the device limit", smem);
     P.nt = nt;
