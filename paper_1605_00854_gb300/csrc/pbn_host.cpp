@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <numeric>
@@ -844,13 +845,26 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
             for (uint32_t gi = words[2 * k]; gi < words[2 * k] + words[2 * k + 1]; ++gi) gword[gi] = k;
         std::vector<uint32_t> idx(grec.size());
         std::iota(idx.begin(), idx.end(), 0u);
+        /* shape class: split nodes first (by function count), then input chunks and
+         * multi-function nodes descending */
+        auto shape = [&](uint32_t a) -> uint32_t {
+            const pbn_img_group& R = grec[a];
+            if (R.l2w == PBN_IMG_SPLIT) return 0x10000u - R.q;
+            return 0x20000u + ((255u - (R.q + 3u) / 4u) << 8) + (255u - R.n_mul);
+        };
+        /* within a class, the groups of different output words alternate (the i-th
+         * group of every word, then the (i+1)-th, ...): lanes that take consecutive
+         * groups then OR into different words instead of queueing on one address */
+        std::vector<uint32_t> occ(grec.size());
+        {
+            std::map<std::pair<uint32_t, uint32_t>, uint32_t> seen;
+            for (uint32_t a = 0; a < (uint32_t)grec.size(); ++a) occ[a] = seen[{shape(a), gword[a]}]++;
+        }
         std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
-            const bool sa = grec[a].l2w == PBN_IMG_SPLIT, sb = grec[b].l2w == PBN_IMG_SPLIT;
-            if (sa != sb) return sa;
-            if (sa) return grec[a].q > grec[b].q;
-            const uint32_t qa = (grec[a].q + 3) / 4, qb = (grec[b].q + 3) / 4;
-            if (qa != qb) return qa > qb;
-            return grec[a].n_mul > grec[b].n_mul;
+            const uint32_t ca = shape(a), cb = shape(b);
+            if (ca != cb) return ca < cb;
+            if (occ[a] != occ[b]) return occ[a] < occ[b];
+            return gword[a] < gword[b];
         });
         /* Row-interleaved layout: group records in this shape order, and the records
          * each group reads (input chunks, multi-function nodes, split-node functions)
@@ -927,6 +941,60 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
         inrec.swap(in2);
         subs.swap(s2);
         wgroups.swap(wg);
+    }
+    /* Order of the SEL blocks: a trajectory's choice row holds block i's four choice
+     * bytes in word i, and the lanes that take the 32 groups of a row read their
+     * nodes' choices together.  Row by row, each block not yet placed goes to a
+     * shared-memory bank (word mod 32) that no other block of the row uses, while the
+     * banks' word counts allow; the draws and slots only move with their blocks. */
+    if (selblk.size() > 32) {
+        const uint32_t ns = (uint32_t)selblk.size();
+        std::vector<int> bank(ns, -1);
+        std::vector<uint32_t> cap(32);
+        for (uint32_t b = 0; b < 32; ++b) cap[b] = ns / 32 + (b < ns % 32 ? 1u : 0u);
+        auto place = [&](uint32_t blk, uint32_t used) {
+            int best = -1;
+            for (int b = 0; b < 32; ++b) {
+                if (!cap[b]) continue;
+                if (best < 0) { best = b; continue; }
+                const bool fb = !((used >> b) & 1u), fbest = !((used >> best) & 1u);
+                if (fb != fbest ? fb : cap[b] > cap[best]) best = b;
+            }
+            bank[blk] = best;
+            cap[best]--;
+            return 1u << best;
+        };
+        const size_t G = grec.size();
+        for (size_t r0 = 0; r0 < G; r0 += 32) {
+            const size_t r1 = std::min(G, r0 + 32);
+            uint32_t used = 0;
+            std::vector<uint32_t> fresh;
+            for (size_t k = r0; k < r1; ++k)
+                for (uint32_t m = 0; m < grec[k].n_mul; ++m) {
+                    const uint32_t blk = mrec[grec[k].mul_first + 32u * m].ch_off >> 2;
+                    if (bank[blk] >= 0) used |= 1u << bank[blk];
+                    else fresh.push_back(blk);
+                }
+            for (uint32_t blk : fresh) used |= bank[blk] >= 0 ? 1u << bank[blk] : place(blk, used);
+        }
+        for (uint32_t i = 0; i < ns; ++i)
+            if (bank[i] < 0) place(i, 0u);
+        std::vector<uint32_t> next(32), newpos(ns);
+        std::iota(next.begin(), next.end(), 0u);
+        for (uint32_t i = 0; i < ns; ++i) {
+            newpos[i] = next[bank[i]];
+            next[bank[i]] += 32;
+        }
+        std::vector<uint32_t> sb2(ns), ss2(selslot.size());
+        for (uint32_t i = 0; i < ns; ++i) sb2[newpos[i]] = selblk[i];
+        for (uint32_t s = 0; s < 4 * ns; ++s) {
+            const uint32_t s2n = 4 * newpos[s >> 2] + (s & 3u);
+            for (uint32_t e = 0; e < 4; ++e) ss2[slot_rec(s2n) + e] = selslot[slot_rec(s) + e];
+        }
+        for (pbn_img_multi& M : mrec)
+            if (M.radix != 0) M.ch_off = 4 * newpos[M.ch_off >> 2] + (M.ch_off & 3u);
+        selblk.swap(sb2);
+        selslot.swap(ss2);
     }
     std::vector<uint64_t> ret(W, 0);
     for (uint32_t v = 0; v < n; ++v)
