@@ -377,7 +377,7 @@ typedef struct {
     uint32_t n_nets;
     uint32_t n_items;          /* work items (up to `threads` trajectories of one network) */
     uint32_t threads;          /* threads per CTA = trajectories per work item */
-    uint32_t reserved;
+    uint32_t max_lanes;        /* the most lanes per trajectory any network of the batch uses */
     uint64_t desc_bytes;       /* bytes of pbn_batch_image */
     uint64_t smem_bytes;       /* dynamic shared memory per CTA */
     double est_ops_per_step;   /* sum over networks of n_traj x ops_per_step */

@@ -80,7 +80,7 @@ class BatchNet(ctypes.Structure):
 
 
 class BatchInfo(ctypes.Structure):
-    _fields_ = [("n_nets", u32), ("n_items", u32), ("threads", u32), ("reserved", u32),
+    _fields_ = [("n_nets", u32), ("n_items", u32), ("threads", u32), ("max_lanes", u32),
                 ("desc_bytes", u64), ("smem_bytes", u64), ("est_ops_per_step", f64)]
 
 

@@ -133,6 +133,31 @@ def test_batch_wide_networks_use_lane_groups():
         assert np.array_equal(got["counts"], ref["counts"])
 
 
+def test_batch_warp_per_trajectory_on_a_wide_state(oracle_mod):
+    """A network whose specs nearly fill shared memory and whose state spans 62 words
+    runs with 16 lanes per trajectory inside the batch (32 trajectory slots x 16 lanes
+    = the CTA's 512 threads) and equals the oracle, next to a small network."""
+    big = synth.scalefree2000(seed=3).to_text()
+    small = synth.paper100(seed=5).to_text()
+    specs = [(big, [0, 1, 2, 3], 64, 8), (small, [0, 1, 2], 96, 12)]
+    entries, plans = [], []
+    for k, (text, meta, T, mi) in enumerate(specs):
+        plan, ids = plan_for(text, meta, max_inputs=mi)
+        entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=31 + k, meta_ids=meta, count_from=5))
+        plans.append((plan, ids))
+    assert plans[0][0].info.state_words >= 16
+    B = api.Batch(entries)
+    assert B.info.max_lanes == 16
+    B.run(50)
+    B.run(30)
+    assert int(B.status.item()) == 0
+    for k, ((text, meta, T, _), (plan, ids), e) in enumerate(zip(specs, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(text, 31 + k, 0, T, 80, meta_ids=meta, count_from=5, nthreads=NCPU)
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+        assert np.array_equal(got["counts"], orc["counts"]), k
+
+
 def test_batch_with_split_nodes(oracle_mod):
     """Networks with split nodes in the batched kernel equal the oracle."""
     texts = [synth.random_pbn(50 + i, 30 + 7 * i, 1e-2, k_choices=tuple(range(1, 11))).to_text() for i in range(3)]
