@@ -318,17 +318,19 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
         /* one lane per trajectory when the SMs fill with trajectories; otherwise
          * lane groups (they split the perturbation words, SEL blocks and groups of
          * a trajectory) until a CTA holds 8 to 16 warps.  States of 32 words or more
-         * may take a whole warp per trajectory (two words per lane: on a 62-word
-         * state 32 lanes ran 1.66x faster than 8); smaller ones up to 8 lanes */
+         * keep doubling up to a warp per trajectory while the trajectories that fit
+         * would fill a CTA of 1,024 threads (on a 62-word state 32 lanes ran 1.26x
+         * faster than 16 and 1.66x faster than 8) */
         LG = 1;
         const uint64_t per_sm = (a->n_traj + sms - 1) / sms;
         const uint64_t fit = fixed + per_traj * 32 <= smem_lim ? (smem_lim - fixed) / per_traj : 32;
         const uint64_t slots = std::min<uint64_t>(per_sm, std::min<uint64_t>(fit, 512));
-        const bool wide_state = H.W32 >= 32;
-        const uint32_t lg_max = wide_state ? 32u : 8u, words_per_lane = wide_state ? 2u : 4u;
-        while (LG < lg_max && slots * LG < 256 && H.W32 >= 4 * LG) LG *= 2;
-        if (LG > 1 && LG < lg_max && slots * LG < 512 && slots * 2 * LG <= kMaxCtaThreads && H.W32 >= words_per_lane * LG)
+        while (LG < 8 && slots * LG < 256 && H.W32 >= 4 * LG) LG *= 2;
+        if (H.W32 >= 32) {
+            while (LG < 32 && 2 * LG <= H.W32 && slots * LG < kMaxCtaThreads) LG *= 2;
+        } else if (LG > 1 && slots * LG < 512 && LG < 8 && H.W32 >= 4 * LG) {
             LG *= 2;
+        }
     }
     if (LG == 0 || LG > 32 || (LG & (LG - 1)))
         return fail(PBN_EINVAL, "pbn_simulate: lanes_per_traj must be 1, 2, 4, 8, 16 or 32");
