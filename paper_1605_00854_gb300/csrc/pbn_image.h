@@ -11,7 +11,11 @@
  *                        state word k
  *   groups  [n_groups]   pbn_img_group in evaluation (shape) order: groups sorted by
  *                        split first, then input chunks and multi-function nodes
- *                        descending, so that groups taken together look alike
+ *                        descending, so that groups taken together look alike;
+ *                        within a shape class the groups of different output words
+ *                        alternate (the i-th group of every word before any
+ *                        (i+1)-th), so lanes taking consecutive groups write
+ *                        different words
  *   multi   [...]        pbn_img_multi, the multi-function nodes of each group in
  *                        group bit order: where their choice is and its radix
  *
@@ -32,7 +36,10 @@
  *                        W32: (4 * row) << 5 | rot, where row is the state word
  *                        holding input b and rot = (bit - b mod 4) mod 32 rotates
  *                        that bit to position b mod 4 of its chunk
- *   selblk  [n_sel]      uint32 SEL block indices r / 4 drawn per step
+ *   selblk  [n_sel]      uint32 SEL block indices r / 4 drawn per step, in an order
+ *                        that puts the choice words read by one row of 32 groups in
+ *                        different shared-memory banks where possible (slots and
+ *                        multi records refer to positions in this list)
  *   gorder  [n_groups]   uint32 group index | output word << 20 of group k (the group
  *                        index is k: records are stored in this order)
  *   wgroups [n_groups]   uint32 group indices of each state word (ranges in words)

@@ -517,3 +517,83 @@ def test_magic_gather_fields_are_injective_and_used():
             sw = sum(((x >> i) & 1) << b for i, b in enumerate(bits))
             seen.add((((sw & mask) * mul) % 2**32 >> shift) & fm)
         assert len(seen) == 1 << k
+
+
+def _rows_max_share(keys):
+    """Sum over rows of 32 consecutive entries of the largest number of entries that
+    share one key (lanes of a warp queueing on one address)."""
+    tot = 0
+    for r0 in range(0, len(keys), 32):
+        row = keys[r0:r0 + 32]
+        tot += max(row.count(k) for k in set(row))
+    return tot
+
+
+def _rows_bank_load(rows_words):
+    """Sum over rows of the largest number of distinct 4-byte words in one bank."""
+    tot = 0
+    for words in rows_words:
+        per_bank = {}
+        for w in set(words):
+            per_bank[w % 32] = per_bank.get(w % 32, 0) + 1
+        tot += max(per_bank.values()) if per_bank else 0
+    return tot
+
+
+@pytest.mark.parametrize("which", ["scalefree", "random"])
+def test_group_order_alternates_words_and_sel_blocks_spread_banks(which):
+    """Evaluation order of the image: shape classes in order; within a class the i-th
+    group of every output word before any (i+1)-th; and the SEL blocks ordered so that
+    the choice words a row of 32 groups reads spread over the banks at least as well as
+    in ascending block order (strictly better on the scale-free network)."""
+    if which == "scalefree":
+        text, meta, mi = synth.scalefree2000(seed=3).to_text(), [0, 1, 2, 3], 8
+    else:
+        text, meta, mi = synth.random_pbn(77, 700, 1e-3, k_choices=(1, 2, 3)).to_text(), [0, 1], 6
+    red, _ = api.Net.load(text).reduce(meta)
+    plan = api.Plan(red, max_inputs=mi)
+    D = imgdecode.decode(plan.image())
+    H, G = D["H"], D["groups"]
+    ng = H["n_groups"]
+    gorder = [int(x) for x in D["u32"][H["off_gorder"] // 4: H["off_gorder"] // 4 + ng]]
+    assert [g & 0xFFFFF for g in gorder] == list(range(ng))
+    word = [g >> 20 for g in gorder]
+
+    def shape(g):
+        R = G[g]
+        return (0, -R["q"]) if R["l2w"] == imgdecode.SPLIT else (1, -((R["q"] + 3) // 4), -R["n_mul"])
+
+    classes = [shape(g) for g in range(ng)]
+    assert classes == sorted(classes)
+    seen, occ = {}, []
+    for g in range(ng):
+        k = (classes[g], word[g])
+        occ.append(seen.get(k, 0))
+        seen[k] = occ[-1] + 1
+    for g in range(1, ng):
+        if classes[g] == classes[g - 1]:
+            assert (occ[g], word[g]) > (occ[g - 1], word[g - 1])
+    # word-by-word order within each class, for comparison
+    wb = sorted(range(ng), key=lambda g: (classes[g], word[g], g))
+    assert _rows_max_share(word) <= _rows_max_share([word[g] for g in wb])
+
+    sel = [int(x) for x in D["sel"]]
+    assert len(set(sel)) == len(sel)
+    rank_of = {b: i for i, b in enumerate(sorted(sel))}
+
+    def rows_words(position):
+        out = []
+        for r0 in range(0, ng, 32):
+            ws = []
+            for g in range(r0, min(ng, r0 + 32)):
+                for m in range(G[g]["n_mul"]):
+                    ws.append(position(D["multi"][imgdecode.multi_index(G[g], m)]["u_slot"] // 4))
+            out.append(ws)
+        return out
+
+    placed = _rows_bank_load(rows_words(lambda i: i))
+    ascending = _rows_bank_load(rows_words(lambda i: rank_of[sel[i]]))
+    assert placed <= ascending
+    if which == "scalefree":
+        assert H["n_sel"] > 32 and placed < ascending
+        assert _rows_max_share(word) * 3 < _rows_max_share([word[g] for g in wb])
