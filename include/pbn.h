@@ -375,8 +375,10 @@ typedef struct {
 
 typedef struct {
     uint32_t n_nets;
-    uint32_t n_items;          /* work items (up to `threads` trajectories of one network) */
-    uint32_t threads;          /* threads per CTA = trajectories per work item */
+    uint32_t n_items;          /* work items: trajectory ranges of one network, each as
+                                  many trajectory slots as fit in shared memory, at
+                                  most `threads` / (the network's lanes per trajectory) */
+    uint32_t threads;          /* threads per CTA */
     uint32_t max_lanes;        /* the most lanes per trajectory any network of the batch uses */
     uint64_t desc_bytes;       /* bytes of pbn_batch_image */
     uint64_t smem_bytes;       /* dynamic shared memory per CTA */
@@ -384,8 +386,10 @@ typedef struct {
 } pbn_batch_info;
 
 /* Describe a batch of networks for the persistent work-queue kernel: each network
- * is cut into work items of up to `threads` trajectories and the items are ordered
- * by descending estimated work.  The networks' plans and device buffers must stay
+ * gets its staging mode (specs and tables, specs only, or none in shared memory), its
+ * trajectory slots per work item and its lanes per trajectory (1-32), is cut into
+ * work items of that many trajectories, and the items are ordered by descending
+ * estimated work.  The networks' plans and device buffers must stay
  * valid while the batch is used.  On success *out owns the batch (pbn_batch_free).
  * Errors: PBN_EINVAL (missing or misaligned buffer, range, meta node), PBN_ETOOBIG
  * (a network's specs and trajectory rows exceed the per-CTA shared memory),
