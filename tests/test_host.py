@@ -597,3 +597,48 @@ def test_group_order_alternates_words_and_sel_blocks_spread_banks(which):
     if which == "scalefree":
         assert H["n_sel"] > 32 and placed < ascending
         assert _rows_max_share(word) * 3 < _rows_max_share([word[g] for g in wb])
+
+
+def test_batch_lane_choice_on_the_host(L):
+    """pbn_batch_create only describes the batch (device buffers are not touched until
+    a launch): a 62-word state whose specs leave room for 32 trajectory slots gets 16
+    lanes per trajectory (32 x 16 = the CTA's 512 threads); a narrow state keeps one
+    lane and many slots per work item."""
+    import ctypes
+    nets = [(synth.scalefree2000(seed=3).to_text(), [0, 1, 2, 3], 8, 64),
+            (synth.paper100(seed=2).to_text(), [0, 1, 2], 12, 5000)]
+    plans, keep = [], []
+    arr = (_lib.BatchNet * len(nets))()
+    fake = 1 << 20  # 16-byte aligned stand-ins for device buffers (never dereferenced here)
+    for i, (text, meta, mi, T) in enumerate(nets):
+        red, _ = api.Net.load(text).reduce(meta)
+        plan = api.Plan(red, max_inputs=mi)
+        plans.append(plan)
+        ids = np.ascontiguousarray(meta, dtype=np.uint32)
+        keep.append(ids)
+        b = arr[i]
+        b.plan, b.d_image, b.seed, b.n_traj = plan._h, fake, 1, T
+        b.n_meta, b.meta_ids = len(meta), ids.ctypes.data
+        b.d_state, b.d_counts, b.d_pooled = fake, fake, fake
+    assert plans[0].info.state_words == 31 and plans[0].info.tables_in_smem == 0
+    h = ctypes.c_void_p()
+    assert L.pbn_batch_create(arr, len(nets), ctypes.byref(h)) == 0, L.pbn_last_error_detail()
+    try:
+        info = _lib.BatchInfo()
+        assert L.pbn_batch_info_get(h, ctypes.byref(info)) == 0
+        assert info.n_nets == 2 and info.threads == 512 and info.max_lanes == 16
+        # 64 trajectories in items of 32 slots, 5,000 in items of at most 512
+        assert info.n_items == 2 + math.ceil(5000 / 512)
+    finally:
+        L.pbn_batch_free(h)
+
+    one = (_lib.BatchNet * 1)()
+    one[0] = arr[1]
+    h = ctypes.c_void_p()
+    assert L.pbn_batch_create(one, 1, ctypes.byref(h)) == 0
+    try:
+        info = _lib.BatchInfo()
+        assert L.pbn_batch_info_get(h, ctypes.byref(info)) == 0
+        assert info.max_lanes == 1
+    finally:
+        L.pbn_batch_free(h)
