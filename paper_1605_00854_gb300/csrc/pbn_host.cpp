@@ -606,424 +606,446 @@ void geometric_thresholds(uint32_t P, uint64_t G[64]) {
     }
 }
 
-int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
-    PlanParts pp;
-    partition(g, prm, &pp);
-    const uint32_t n = g.n;
-    const uint32_t W = (n + 63) / 64;
+/* ---- Algorithm 5's Preparation: the device image, built stage by stage ------------ */
 
-    /* SEL ranks over every node with >= 2 functions, leaves included */
-    std::vector<uint32_t> rank(n, UINT32_MAX);
-    uint32_t r = 0;
-    for (uint32_t v = 0; v < n; ++v)
-        if (g.node[v].size() >= 2) rank[v] = r++;
+/* The sections of the device image under construction (layout in pbn_image.h). */
+struct ImageBuild {
+    uint32_t n = 0, W = 0, W32 = 0;
+    std::vector<uint32_t> rank;               /* SEL rank of each node with >= 2 functions */
+    std::vector<std::vector<size_t>> in_word; /* partition groups of each 32-bit state word */
+    std::vector<uint32_t> gword, gshift;      /* word and bit offset of each partition group */
+    std::vector<uint32_t> selblk;             /* SEL blocks drawn per step */
+    std::vector<uint32_t> words, selslot, thr, inrec, tables;
+    std::vector<uint32_t> subs;    /* uint2 per function of a split node: in_chunk | k << 27, tab_off */
+    std::vector<uint32_t> gorder;  /* group index | output word << 20, in evaluation order */
+    std::vector<uint32_t> wgroups; /* group indices of each output word (words ranges into it) */
+    std::vector<pbn_img_group> grec;
+    std::vector<pbn_img_multi> mrec;
+    uint32_t n_multi_nodes = 0, n_split = 0, n_groups_multi = 0;
+    uint64_t total_inputs = 0;
 
-    /* pack groups into 32-bit state words: first fit by decreasing width */
+    /* record of SEL slot s = 4 i + l at l * n_sel + i: lanes that take consecutive
+     * blocks read consecutive records */
+    uint32_t slot_rec(uint32_t slot) const { return 4 * ((slot & 3u) * (uint32_t)selblk.size() + (slot >> 2)); }
+    /* SEL slot of node v: 4 x (position of its block in selblk) + rank mod 4 */
+    uint32_t sel_slot(uint32_t v) const {
+        const uint32_t b = rank[v] >> 2;
+        const uint32_t idx = (uint32_t)(std::lower_bound(selblk.begin(), selblk.end(), b) - selblk.begin());
+        return 4 * idx + (rank[v] & 3);
+    }
+};
+
+/* Input record of input b at state position ps: the row's byte offset above 5
+ * rotation bits; the rotation brings the bit to position b mod 4 of its 4-input chunk. */
+uint32_t input_record(uint32_t ps, size_t b) { return ((ps >> 5) << 7) | (((ps & 31) - (uint32_t)(b & 3)) & 31); }
+
+/* Groups packed into 32-bit state words, first fit by decreasing width; the word
+ * count is even (the state is stored as uint64 words). */
+void pack_words(const PlanParts& pp, ImageBuild* B) {
     std::vector<size_t> order(pp.groups.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
         return pp.groups[a].nodes.size() > pp.groups[b].nodes.size();
     });
-    std::vector<uint32_t> fill;                 /* used bits per word */
-    std::vector<std::vector<size_t>> in_word;   /* groups of each word in placement order */
-    std::vector<uint32_t> gword(pp.groups.size()), gshift(pp.groups.size());
+    std::vector<uint32_t> fill; /* used bits per word */
+    B->gword.assign(pp.groups.size(), 0u);
+    B->gshift.assign(pp.groups.size(), 0u);
     for (size_t gi : order) {
-        uint32_t w = (uint32_t)pp.groups[gi].nodes.size();
+        const uint32_t w = (uint32_t)pp.groups[gi].nodes.size();
         size_t k = 0;
         while (k < fill.size() && fill[k] + w > 32) ++k;
-        if (k == fill.size()) { fill.push_back(0); in_word.emplace_back(); }
-        gword[gi] = (uint32_t)k;
-        gshift[gi] = fill[k];
+        if (k == fill.size()) {
+            fill.push_back(0);
+            B->in_word.emplace_back();
+        }
+        B->gword[gi] = (uint32_t)k;
+        B->gshift[gi] = fill[k];
         fill[k] += w;
-        in_word[k].push_back(gi);
+        B->in_word[k].push_back(gi);
     }
-    uint32_t W32 = (uint32_t)fill.size();
-    if (W32 == 0) W32 = 2;
-    W32 = (W32 + 1) & ~1u;
-    in_word.resize(W32);
+    const uint32_t W32 = fill.empty() ? 2u : (uint32_t)fill.size();
+    B->W32 = (W32 + 1) & ~1u;
+    B->in_word.resize(B->W32);
+}
 
-    plan->pos.assign(n, UINT32_MAX);
-    plan->group_of.assign(n, UINT32_MAX);
-    /* evaluation order: word by word */
-    std::vector<size_t> eval;
-    for (uint32_t k = 0; k < W32; ++k)
-        for (size_t gi : in_word[k]) eval.push_back(gi);
-    for (size_t e = 0; e < eval.size(); ++e) {
-        const Grp& gr = pp.groups[eval[e]];
-        for (size_t i = 0; i < gr.nodes.size(); ++i) {
-            plan->pos[gr.nodes[i]] = 32 * gword[eval[e]] + gshift[eval[e]] + (uint32_t)i;
-            plan->group_of[gr.nodes[i]] = (uint32_t)e;
+/* State position (32 x word + bit) of every retained node, and its group in the
+ * word-by-word evaluation order. */
+void place_nodes(const PlanParts& pp, const ImageBuild& B, pbn_plan* plan) {
+    plan->pos.assign(B.n, UINT32_MAX);
+    plan->group_of.assign(B.n, UINT32_MAX);
+    uint32_t e = 0;
+    for (uint32_t k = 0; k < B.W32; ++k)
+        for (size_t gi : B.in_word[k]) {
+            const Grp& gr = pp.groups[gi];
+            for (size_t i = 0; i < gr.nodes.size(); ++i) {
+                plan->pos[gr.nodes[i]] = 32 * B.gword[gi] + B.gshift[gi] + (uint32_t)i;
+                plan->group_of[gr.nodes[i]] = e;
+            }
+            ++e;
+        }
+}
+
+/* SEL ranks over every node with >= 2 functions (leaves included), and the SEL
+ * Philox blocks that hold the ranks of retained multi-function nodes. */
+void sel_blocks(const pbn_net& g, ImageBuild* B) {
+    B->rank.assign(B->n, UINT32_MAX);
+    uint32_t r = 0;
+    for (uint32_t v = 0; v < B->n; ++v)
+        if (g.node[v].size() >= 2) B->rank[v] = r++;
+    for (uint32_t v = 0; v < B->n; ++v)
+        if (g.retained[v] && B->rank[v] != UINT32_MAX) B->selblk.push_back(B->rank[v] >> 2);
+    std::sort(B->selblk.begin(), B->selblk.end());
+    B->selblk.erase(std::unique(B->selblk.begin(), B->selblk.end()), B->selblk.end());
+    B->selslot.assign(16 * B->selblk.size(), 0u);
+}
+
+/* Multi record of node v (its SEL slot and mixed-radix weight) and the slot's integer
+ * thresholds T_j = floor(C_j 2^32) with C_j summed left to right (a threshold of 2^32
+ * never fires and is left out), the first two inline in the slot record. */
+void add_choice(const pbn_net& g, uint32_t v, uint32_t radix, ImageBuild* B) {
+    const auto& fl = g.node[v];
+    const uint32_t first = (uint32_t)B->thr.size();
+    double C = 0.0;
+    uint32_t n_thr = 0;
+    for (size_t j = 1; j < fl.size(); ++j) {
+        C = C + fl[j - 1].c;
+        const double t = std::floor(C * 4294967296.0);
+        if (t >= 4294967296.0) break;
+        B->thr.push_back((uint32_t)t);
+        n_thr++;
+    }
+    const uint32_t slot = B->sel_slot(v);
+    uint32_t* ss = &B->selslot[B->slot_rec(slot)];
+    ss[0] = n_thr >= 1 ? B->thr[first] : 0u;
+    ss[1] = n_thr >= 2 ? B->thr[first + 1] : 0u;
+    ss[2] = n_thr;
+    ss[3] = first;
+    pbn_img_multi M{};
+    M.ch_off = slot;
+    M.radix = radix;
+    B->mrec.push_back(M);
+}
+
+/* A split node: a lone multi-function node whose input union exceeds the merge cap
+ * keeps one table of 2^k one-bit entries per predictor function, over that
+ * function's own k inputs, instead of l x 2^q entries over the union; its choice
+ * selects the function to evaluate. */
+int add_split_group(const pbn_net& g, const pbn_plan& plan, uint32_t v, uint32_t shift, ImageBuild* B) {
+    const auto& fl = g.node[v];
+    pbn_img_group G{};
+    G.mul_first = (uint32_t)B->mrec.size();
+    add_choice(g, v, 1u, B);
+    G.tab_off = (uint32_t)(B->subs.size() / 2); /* first sub-function */
+    G.in_chunk = 0;
+    G.q = (uint8_t)fl.size();
+    G.l2w = PBN_IMG_SPLIT;
+    G.n_mul = 1;
+    G.shift = (uint8_t)shift;
+    for (const pbn_fun& f : fl) {
+        const uint32_t chunk = (uint32_t)(B->inrec.size() / 4);
+        for (size_t b = 0; b < f.par.size(); ++b) {
+            const uint32_t ps = plan.pos[f.par[b]];
+            if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", f.par[b]);
+            B->inrec.push_back(input_record(ps, b));
+        }
+        while (B->inrec.size() % 4) B->inrec.push_back(B->W32 << 7); /* the always-zero row */
+        const uint32_t k = (uint32_t)f.par.size();
+        const uint32_t to = (uint32_t)B->tables.size();
+        if (chunk >= (1u << 27)) return fail(PBN_ETOOBIG, "input records beyond 2^27 chunks");
+        B->subs.push_back(chunk | (k << 27));
+        B->subs.push_back(to);
+        const uint64_t nb = 1ull << k;
+        B->tables.resize(B->tables.size() + (size_t)((nb + 31) / 32), 0);
+        uint32_t* tab = B->tables.data() + to;
+        for (uint64_t x = 0; x < nb; ++x) tab[x >> 5] |= (uint32_t)f.bit(x) << (x & 31);
+    }
+    /* one function's inputs are read per step: count their mean */
+    uint64_t ksum = 0;
+    for (const pbn_fun& f : fl) ksum += f.par.size();
+    B->total_inputs += (ksum + fl.size() - 1) / fl.size();
+    B->grec.push_back(G);
+    B->n_split++;
+    return PBN_OK;
+}
+
+/* A merged group (Sec. 3.3): one table over the union of its members' q inputs
+ * (`ins`, sorted by state position); entry (c << q) | x, with c the mixed-radix
+ * combined choice of the multi-function members (in group bit order) and x the packed
+ * input pattern, holds in bit i member i's selected function evaluated on x. */
+int add_merged_group(const pbn_net& g, const pbn_plan& plan, const Grp& gr, const std::vector<uint32_t>& ins,
+                     uint32_t shift, ImageBuild* B) {
+    const size_t q = ins.size();
+    if (q > 24) return fail(PBN_ETOOBIG, "group with %zu inputs (max 24)", q);
+    std::vector<int> inpos(B->n, -1);
+    const uint32_t in_chunk = (uint32_t)(B->inrec.size() / 4);
+    for (size_t b = 0; b < q; ++b) {
+        const uint32_t ps = plan.pos[ins[b]];
+        if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", ins[b]);
+        inpos[ins[b]] = (int)b;
+        B->inrec.push_back(input_record(ps, b));
+    }
+    while (B->inrec.size() % 4) B->inrec.push_back(B->W32 << 7); /* the always-zero row */
+    std::vector<uint32_t> radix(gr.nodes.size(), 0);
+    uint64_t prod = 1;
+    pbn_img_group G{};
+    G.mul_first = (uint32_t)B->mrec.size();
+    for (size_t i = 0; i < gr.nodes.size(); ++i) {
+        const uint32_t v = gr.nodes[i];
+        if (g.node[v].size() < 2) continue;
+        radix[i] = (uint32_t)prod;
+        add_choice(g, v, (uint32_t)prod, B);
+        prod *= g.node[v].size();
+        if (prod > (UINT64_C(1) << 30)) return fail(PBN_ETOOBIG, "group with too many combined functions");
+    }
+    const uint32_t width = (uint32_t)gr.nodes.size();
+    const uint32_t l2w = log2_entry_bits(width);
+    const uint64_t entries = prod << q;
+    const uint64_t bits = entries << l2w;
+    if ((double)bits > kMaxTableBits) return fail(PBN_ETOOBIG, "merged table of %llu bits exceeds 2^30", (unsigned long long)bits);
+    G.tab_off = (uint32_t)B->tables.size();
+    G.in_chunk = in_chunk;
+    G.q = (uint8_t)q;
+    G.l2w = (uint8_t)l2w;
+    G.n_mul = (uint8_t)(B->mrec.size() - G.mul_first);
+    G.shift = (uint8_t)shift;
+    B->grec.push_back(G);
+    B->total_inputs += q;
+    B->tables.resize(B->tables.size() + (size_t)((bits + 31) / 32), 0);
+    uint32_t* tab = B->tables.data() + G.tab_off;
+    for (uint64_t c = 0; c < prod; ++c) {
+        for (uint64_t x = 0; x < (1ull << q); ++x) {
+            uint32_t v_out = 0;
+            for (size_t i = 0; i < width; ++i) {
+                const auto& fl = g.node[gr.nodes[i]];
+                const size_t j = fl.size() >= 2 ? (size_t)((c / radix[i]) % fl.size()) : 0;
+                const pbn_fun& f = fl[j];
+                uint64_t idx = 0;
+                for (size_t b = 0; b < f.par.size(); ++b) idx |= (uint64_t)((x >> inpos[f.par[b]]) & 1u) << b;
+                v_out |= (uint32_t)f.bit(idx) << i;
+            }
+            const uint64_t bo = ((c << q) | x) << l2w;
+            tab[bo >> 5] |= v_out << (bo & 31);
         }
     }
+    return PBN_OK;
+}
 
-    /* selection blocks: the SEL Philox blocks holding retained multi-function ranks */
-    std::vector<uint32_t> selblk;
-    for (uint32_t v = 0; v < n; ++v)
-        if (g.retained[v] && rank[v] != UINT32_MAX) selblk.push_back(rank[v] >> 2);
-    std::sort(selblk.begin(), selblk.end());
-    selblk.erase(std::unique(selblk.begin(), selblk.end()), selblk.end());
-    auto sel_slot = [&](uint32_t v) {
-        uint32_t b = rank[v] >> 2;
-        uint32_t idx = (uint32_t)(std::lower_bound(selblk.begin(), selblk.end(), b) - selblk.begin());
-        return 4 * idx + (rank[v] & 3);
-    };
-
-    std::vector<uint32_t> words(2 * W32);
-    std::vector<pbn_img_group> grec;
-    std::vector<pbn_img_multi> mrec;
-    std::vector<uint32_t> thr, inrec, tables;
-    std::vector<uint32_t> selslot(16 * selblk.size(), 0u);
-    /* record of SEL slot s = 4 i + l at l * n_sel + i: lanes that take consecutive
-     * blocks read consecutive records */
-    auto slot_rec = [&](uint32_t slot) { return 4 * ((slot & 3u) * (uint32_t)selblk.size() + (slot >> 2)); };
-    std::vector<uint32_t> subs; /* uint2 per function of a split node: in_chunk | k << 27, tab_off */
-    std::vector<uint32_t> wgroups; /* group indices of each output word (WORDS ranges into it) */
-    uint32_t n_multi_nodes = 0;
-    uint32_t n_split = 0;
-    uint64_t total_inputs = 0;
-    uint32_t n_groups_multi = 0;
-    for (uint32_t k = 0; k < W32; ++k) {
-        words[2 * k] = (uint32_t)grec.size();
-        words[2 * k + 1] = (uint32_t)in_word[k].size();
-        for (size_t gi : in_word[k]) {
+/* Group records and everything they point to (multi records, thresholds, input
+ * records, tables, split-node functions), word by word. */
+int emit_groups(const pbn_net& g, const pbn_group_params& prm, const PlanParts& pp, const pbn_plan& plan,
+                ImageBuild* B) {
+    B->words.assign(2 * B->W32, 0u);
+    for (uint32_t k = 0; k < B->W32; ++k) {
+        B->words[2 * k] = (uint32_t)B->grec.size();
+        B->words[2 * k + 1] = (uint32_t)B->in_word[k].size();
+        for (size_t gi : B->in_word[k]) {
             const Grp& gr = pp.groups[gi];
-            n_groups_multi += gr.multi;
-            /* inputs sorted by state position */
-            std::vector<uint32_t> ins = gr.inputs;
-            std::sort(ins.begin(), ins.end(), [&](uint32_t a, uint32_t b) { return plan->pos[a] < plan->pos[b]; });
-            const size_t q = ins.size();
-            /* a lone multi-function node whose inputs exceed the merge cap keeps one
-             * table per predictor function (over that function's own inputs) instead of
-             * one table over the union: l * 2^q entries would waste memory */
-            const bool split = gr.nodes.size() == 1 && g.node[gr.nodes[0]].size() >= 2 && q > prm.max_inputs;
-            if (split) {
-                const uint32_t v = gr.nodes[0];
-                const auto& fl = g.node[v];
-                pbn_img_group G{};
-                G.mul_first = (uint32_t)mrec.size();
-                pbn_img_multi M{};
-                const uint32_t first = (uint32_t)thr.size();
-                double C = 0.0;
-                uint32_t n_thr = 0;
-                for (size_t j = 1; j < fl.size(); ++j) {
-                    C = C + fl[j - 1].c;
-                    double t = std::floor(C * 4294967296.0);
-                    if (t >= 4294967296.0) break;
-                    thr.push_back((uint32_t)t);
-                    n_thr++;
+            B->n_groups_multi += gr.multi;
+            std::vector<uint32_t> ins = gr.inputs; /* sorted by state position */
+            std::sort(ins.begin(), ins.end(), [&](uint32_t a, uint32_t b) { return plan.pos[a] < plan.pos[b]; });
+            const bool split = gr.nodes.size() == 1 && g.node[gr.nodes[0]].size() >= 2 && ins.size() > prm.max_inputs;
+            const int rc = split ? add_split_group(g, plan, gr.nodes[0], B->gshift[gi], B)
+                                 : add_merged_group(g, plan, gr, ins, B->gshift[gi], B);
+            if (rc) return rc;
+        }
+    }
+    return PBN_OK;
+}
+
+/* Evaluation order for lane groups and the row-interleaved record layout.  Groups
+ * are sorted by shape (split nodes first by function count, then input chunks and
+ * multi-function nodes descending) so that lanes taking consecutive groups run in
+ * step; within a class the groups of different output words alternate (the i-th
+ * group of every word, then the (i+1)-th, ...), so those lanes OR into different
+ * words instead of queueing on one address.  Group records are stored in this order,
+ * and the records each group reads (input chunks, multi-function nodes, split-node
+ * functions) in rows of 32 groups with a stride of 32: chunk j of group k = 32 r + l
+ * sits at base_r + 32 j + l, so lanes read consecutive records (no bank conflicts).
+ * Split-node functions keep their own input chunks contiguous after the rows. */
+int interleave_rows(ImageBuild* B, pbn_plan* plan) {
+    const size_t G = B->grec.size();
+    const std::vector<pbn_img_group>& grec = B->grec;
+    std::vector<uint32_t> gword(G);
+    for (uint32_t k = 0; k < B->W32; ++k)
+        for (uint32_t gi = B->words[2 * k]; gi < B->words[2 * k] + B->words[2 * k + 1]; ++gi) gword[gi] = k;
+    auto shape = [&](uint32_t a) -> uint32_t {
+        const pbn_img_group& R = grec[a];
+        if (R.l2w == PBN_IMG_SPLIT) return 0x10000u - R.q;
+        return 0x20000u + ((255u - (R.q + 3u) / 4u) << 8) + (255u - R.n_mul);
+    };
+    std::vector<uint32_t> occ(G);
+    {
+        std::map<std::pair<uint32_t, uint32_t>, uint32_t> seen;
+        for (uint32_t a = 0; a < (uint32_t)G; ++a) occ[a] = seen[{shape(a), gword[a]}]++;
+    }
+    std::vector<uint32_t> idx(G);
+    std::iota(idx.begin(), idx.end(), 0u);
+    std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
+        const uint32_t ca = shape(a), cb = shape(b);
+        if (ca != cb) return ca < cb;
+        if (occ[a] != occ[b]) return occ[a] < occ[b];
+        return gword[a] < gword[b];
+    });
+    B->n_multi_nodes = (uint32_t)B->mrec.size();
+    std::vector<uint32_t> newidx(G);
+    for (size_t k = 0; k < G; ++k) newidx[idx[k]] = (uint32_t)k;
+    std::vector<pbn_img_group> g2(G);
+    std::vector<pbn_img_multi> m2;
+    std::vector<uint32_t> in2, s2;
+    for (size_t r0 = 0; r0 < G; r0 += 32) {
+        const size_t r1 = std::min(G, r0 + 32);
+        uint32_t maxc = 0, maxm = 0, maxf = 0;
+        for (size_t k = r0; k < r1; ++k) {
+            const pbn_img_group& O = grec[idx[k]];
+            const bool sp = O.l2w == PBN_IMG_SPLIT;
+            maxc = std::max<uint32_t>(maxc, sp ? 0u : (O.q + 3u) / 4u);
+            maxm = std::max<uint32_t>(maxm, O.n_mul);
+            maxf = std::max<uint32_t>(maxf, sp ? O.q : 0u);
+        }
+        const uint32_t cb = (uint32_t)(in2.size() / 4), mb = (uint32_t)m2.size(), sb = (uint32_t)(s2.size() / 2);
+        in2.resize(in2.size() + (size_t)4 * 32 * maxc, B->W32 << 7); /* padding reads the zero row */
+        m2.resize(m2.size() + (size_t)32 * maxm, pbn_img_multi{0u, 0u});
+        s2.resize(s2.size() + (size_t)2 * 32 * maxf, 0u);
+        for (size_t k = r0; k < r1; ++k) {
+            const uint32_t l = (uint32_t)(k - r0);
+            const pbn_img_group& O = grec[idx[k]];
+            pbn_img_group N = O;
+            const bool sp = O.l2w == PBN_IMG_SPLIT;
+            if (!sp) {
+                N.in_chunk = cb + l;
+                for (uint32_t j = 0; j < (O.q + 3u) / 4u; ++j)
+                    for (uint32_t e = 0; e < 4; ++e) in2[4 * (cb + l + 32 * j) + e] = B->inrec[4 * (O.in_chunk + j) + e];
+            }
+            N.mul_first = mb + l;
+            for (uint32_t m = 0; m < O.n_mul; ++m) m2[mb + l + 32 * m] = B->mrec[O.mul_first + m];
+            if (sp) {
+                N.tab_off = sb + l;
+                for (uint32_t f = 0; f < O.q; ++f) {
+                    s2[2 * (sb + l + 32 * f)] = B->subs[2 * (O.tab_off + f)];
+                    s2[2 * (sb + l + 32 * f) + 1] = B->subs[2 * (O.tab_off + f) + 1];
                 }
-                const uint32_t slot = sel_slot(v);
-                M.ch_off = slot;
-                M.radix = 1;
-                uint32_t* ss = &selslot[slot_rec(slot)];
-                ss[0] = n_thr >= 1 ? thr[first] : 0u;
-                ss[1] = n_thr >= 2 ? thr[first + 1] : 0u;
-                ss[2] = n_thr;
-                ss[3] = first;
-                mrec.push_back(M);
-                G.tab_off = (uint32_t)(subs.size() / 2); /* first sub-function */
-                G.in_chunk = 0;
-                G.q = (uint8_t)fl.size();
-                G.l2w = PBN_IMG_SPLIT;
-                G.n_mul = 1;
-                G.shift = (uint8_t)gshift[gi];
-                for (const pbn_fun& f : fl) {
-                    const uint32_t chunk = (uint32_t)(inrec.size() / 4);
-                    for (size_t b = 0; b < f.par.size(); ++b) {
-                        const uint32_t ps = plan->pos[f.par[b]];
-                        if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", f.par[b]);
-                        inrec.push_back(((ps >> 5) << 7) | (((ps & 31) - (uint32_t)(b & 3)) & 31));
-                    }
-                    while (inrec.size() % 4) inrec.push_back(W32 << 7);
-                    const uint32_t k = (uint32_t)f.par.size();
-                    const uint32_t to = (uint32_t)tables.size();
-                    if (chunk >= (1u << 27)) return fail(PBN_ETOOBIG, "input records beyond 2^27 chunks");
-                    subs.push_back(chunk | (k << 27));
-                    subs.push_back(to);
-                    const uint64_t nb = 1ull << k;
-                    tables.resize(tables.size() + (size_t)((nb + 31) / 32), 0);
-                    uint32_t* tab = tables.data() + to;
-                    for (uint64_t x = 0; x < nb; ++x) tab[x >> 5] |= (uint32_t)f.bit(x) << (x & 31);
-                }
-                /* one function's inputs are read per step: count their mean */
-                uint64_t ksum = 0;
-                for (const pbn_fun& f : fl) ksum += f.par.size();
-                total_inputs += (ksum + fl.size() - 1) / fl.size();
-                grec.push_back(G);
-                n_split++;
+            }
+            g2[k] = N;
+        }
+    }
+    /* split-node functions' own chunks, contiguous after the rows */
+    for (size_t i = 0; i < s2.size(); i += 2) {
+        const uint32_t k = s2[i] >> 27, old = s2[i] & 0x7FFFFFFu;
+        if (s2[i] == 0 && s2[i + 1] == 0) continue; /* padding record */
+        const uint32_t nc = (k + 3u) / 4u, at = (uint32_t)(in2.size() / 4);
+        for (uint32_t j = 0; j < nc; ++j)
+            for (uint32_t e = 0; e < 4; ++e) in2.push_back(B->inrec[4 * (old + j) + e]);
+        if (at >= (1u << 27)) return fail(PBN_ETOOBIG, "input records beyond 2^27 chunks");
+        s2[i] = at | (k << 27);
+    }
+    /* the groups of each output word, for the word-by-word evaluation */
+    std::vector<uint32_t> wg;
+    wg.reserve(G);
+    for (uint32_t k = 0; k < B->W32; ++k) {
+        const uint32_t first = B->words[2 * k], cnt = B->words[2 * k + 1];
+        B->words[2 * k] = (uint32_t)wg.size();
+        for (uint32_t gi = first; gi < first + cnt; ++gi) wg.push_back(newidx[gi]);
+    }
+    B->gorder.resize(G);
+    for (size_t k = 0; k < G; ++k) B->gorder[k] = (uint32_t)k | (gword[idx[k]] << 20);
+    for (uint32_t v = 0; v < B->n; ++v)
+        if (plan->group_of[v] != UINT32_MAX) plan->group_of[v] = newidx[plan->group_of[v]];
+    B->grec.swap(g2);
+    B->mrec.swap(m2);
+    B->inrec.swap(in2);
+    B->subs.swap(s2);
+    B->wgroups.swap(wg);
+    return PBN_OK;
+}
+
+/* Order of the SEL blocks: a trajectory's choice row holds block i's four choice
+ * bytes in word i, and the lanes that take the 32 groups of a row read their nodes'
+ * choices together.  Row by row, each block not yet placed goes to a shared-memory
+ * bank (word mod 32) that no other block of the row uses, while the banks' word
+ * counts allow; the draws and slots only move with their blocks. */
+void place_sel_blocks(ImageBuild* B) {
+    if (B->selblk.size() <= 32) return;
+    const uint32_t ns = (uint32_t)B->selblk.size();
+    std::vector<int> bank(ns, -1);
+    std::vector<uint32_t> cap(32);
+    for (uint32_t b = 0; b < 32; ++b) cap[b] = ns / 32 + (b < ns % 32 ? 1u : 0u);
+    auto place = [&](uint32_t blk, uint32_t used) {
+        int best = -1;
+        for (int b = 0; b < 32; ++b) {
+            if (!cap[b]) continue;
+            if (best < 0) {
+                best = b;
                 continue;
             }
-            if (q > 24) return fail(PBN_ETOOBIG, "group with %zu inputs (max 24)", q);
-            std::vector<int> inpos(n, -1);
-            const uint32_t in_chunk = (uint32_t)(inrec.size() / 4);
-            for (size_t b = 0; b < q; ++b) {
-                uint32_t ps = plan->pos[ins[b]];
-                if (ps == UINT32_MAX) return fail(PBN_EINVAL, "input %u of a retained node was removed", ins[b]);
-                inpos[ins[b]] = (int)b;
-                /* word offset of the row (row * 4 bytes) above 5 rotation bits; the
-                 * rotation brings the bit to position b mod 4 of its 4-input chunk */
-                inrec.push_back(((ps >> 5) << 7) | (((ps & 31) - (uint32_t)(b & 3)) & 31));
-            }
-            while (inrec.size() % 4) inrec.push_back(W32 << 7); /* the always-zero row */
-            /* multi-function members, mixed radix in group bit order */
-            std::vector<uint32_t> radix(gr.nodes.size(), 0);
-            uint64_t prod = 1;
-            pbn_img_group G{};
-            G.mul_first = (uint32_t)mrec.size();
-            for (size_t i = 0; i < gr.nodes.size(); ++i) {
-                uint32_t v = gr.nodes[i];
-                const auto& fl = g.node[v];
-                if (fl.size() < 2) continue;
-                radix[i] = (uint32_t)prod;
-                pbn_img_multi M{};
-                const uint32_t first = (uint32_t)thr.size();
-                double C = 0.0;
-                uint32_t n_thr = 0;
-                for (size_t j = 1; j < fl.size(); ++j) {
-                    C = C + fl[j - 1].c;
-                    double t = std::floor(C * 4294967296.0);
-                    if (t >= 4294967296.0) break; /* T_j = 2^32 never fires */
-                    thr.push_back((uint32_t)t);
-                    n_thr++;
-                }
-                const uint32_t slot = sel_slot(v);
-                M.ch_off = slot;
-                M.radix = (uint32_t)prod;
-                uint32_t* ss = &selslot[slot_rec(slot)];
-                ss[0] = n_thr >= 1 ? thr[first] : 0u;
-                ss[1] = n_thr >= 2 ? thr[first + 1] : 0u;
-                ss[2] = n_thr;
-                ss[3] = first;
-                mrec.push_back(M);
-                prod *= fl.size();
-                if (prod > (UINT64_C(1) << 30)) return fail(PBN_ETOOBIG, "group with too many combined functions");
-            }
-            const uint32_t width = (uint32_t)gr.nodes.size();
-            const uint32_t l2w = log2_entry_bits(width);
-            const uint64_t entries = prod << q;
-            const uint64_t bits = entries << l2w;
-            if ((double)bits > kMaxTableBits) return fail(PBN_ETOOBIG, "merged table of %llu bits exceeds 2^30", (unsigned long long)bits);
-            G.tab_off = (uint32_t)tables.size();
-            G.in_chunk = in_chunk;
-            G.q = (uint8_t)q;
-            G.l2w = (uint8_t)l2w;
-            G.n_mul = (uint8_t)(mrec.size() - G.mul_first);
-            G.shift = (uint8_t)gshift[gi];
-            grec.push_back(G);
-            total_inputs += q;
-            /* the merged table (Sec. 3.3): entry (c << q) | x, bit i = node i's selected
-             * function evaluated on the inputs packed in x */
-            tables.resize(tables.size() + (size_t)((bits + 31) / 32), 0);
-            uint32_t* tab = tables.data() + G.tab_off;
-            std::vector<std::vector<uint8_t>> argpos(width);
-            for (uint64_t c = 0; c < prod; ++c) {
-                for (uint64_t x = 0; x < (1ull << q); ++x) {
-                    uint32_t v_out = 0;
-                    for (size_t i = 0; i < width; ++i) {
-                        uint32_t v = gr.nodes[i];
-                        const auto& fl = g.node[v];
-                        size_t j = fl.size() >= 2 ? (size_t)((c / radix[i]) % fl.size()) : 0;
-                        const pbn_fun& f = fl[j];
-                        uint64_t idx = 0;
-                        for (size_t b = 0; b < f.par.size(); ++b)
-                            idx |= (uint64_t)((x >> inpos[f.par[b]]) & 1u) << b;
-                        v_out |= (uint32_t)f.bit(idx) << i;
-                    }
-                    uint64_t e = (c << q) | x;
-                    uint64_t bo = e << l2w;
-                    tab[bo >> 5] |= v_out << (bo & 31);
-                }
-            }
+            const bool fb = !((used >> b) & 1u), fbest = !((used >> best) & 1u);
+            if (fb != fbest ? fb : cap[b] > cap[best]) best = b;
         }
+        bank[blk] = best;
+        cap[best]--;
+        return 1u << best;
+    };
+    const size_t G = B->grec.size();
+    for (size_t r0 = 0; r0 < G; r0 += 32) {
+        const size_t r1 = std::min(G, r0 + 32);
+        uint32_t used = 0;
+        std::vector<uint32_t> fresh;
+        for (size_t k = r0; k < r1; ++k)
+            for (uint32_t m = 0; m < B->grec[k].n_mul; ++m) {
+                const uint32_t blk = B->mrec[B->grec[k].mul_first + 32u * m].ch_off >> 2;
+                if (bank[blk] >= 0) used |= 1u << bank[blk];
+                else fresh.push_back(blk);
+            }
+        for (uint32_t blk : fresh) used |= bank[blk] >= 0 ? 1u << bank[blk] : place(blk, used);
     }
+    for (uint32_t i = 0; i < ns; ++i)
+        if (bank[i] < 0) place(i, 0u);
+    std::vector<uint32_t> next(32), newpos(ns);
+    std::iota(next.begin(), next.end(), 0u);
+    for (uint32_t i = 0; i < ns; ++i) {
+        newpos[i] = next[bank[i]];
+        next[bank[i]] += 32;
+    }
+    std::vector<uint32_t> sb2(ns), ss2(B->selslot.size());
+    for (uint32_t i = 0; i < ns; ++i) sb2[newpos[i]] = B->selblk[i];
+    for (uint32_t s = 0; s < 4 * ns; ++s) {
+        const uint32_t s2n = 4 * newpos[s >> 2] + (s & 3u);
+        for (uint32_t e = 0; e < 4; ++e) ss2[B->slot_rec(s2n) + e] = B->selslot[B->slot_rec(s) + e];
+    }
+    for (pbn_img_multi& M : B->mrec)
+        if (M.radix != 0) M.ch_off = 4 * newpos[M.ch_off >> 2] + (M.ch_off & 3u);
+    B->selblk.swap(sb2);
+    B->selslot.swap(ss2);
+}
 
-    /* evaluation order for lane groups: by shape, so lanes run in step */
-    std::vector<uint32_t> gorder(grec.size());
-    {
-        std::vector<uint32_t> gword(grec.size());
-        for (uint32_t k = 0; k < W32; ++k)
-            for (uint32_t gi = words[2 * k]; gi < words[2 * k] + words[2 * k + 1]; ++gi) gword[gi] = k;
-        std::vector<uint32_t> idx(grec.size());
-        std::iota(idx.begin(), idx.end(), 0u);
-        /* shape class: split nodes first (by function count), then input chunks and
-         * multi-function nodes descending */
-        auto shape = [&](uint32_t a) -> uint32_t {
-            const pbn_img_group& R = grec[a];
-            if (R.l2w == PBN_IMG_SPLIT) return 0x10000u - R.q;
-            return 0x20000u + ((255u - (R.q + 3u) / 4u) << 8) + (255u - R.n_mul);
-        };
-        /* within a class, the groups of different output words alternate (the i-th
-         * group of every word, then the (i+1)-th, ...): lanes that take consecutive
-         * groups then OR into different words instead of queueing on one address */
-        std::vector<uint32_t> occ(grec.size());
-        {
-            std::map<std::pair<uint32_t, uint32_t>, uint32_t> seen;
-            for (uint32_t a = 0; a < (uint32_t)grec.size(); ++a) occ[a] = seen[{shape(a), gword[a]}]++;
-        }
-        std::stable_sort(idx.begin(), idx.end(), [&](uint32_t a, uint32_t b) {
-            const uint32_t ca = shape(a), cb = shape(b);
-            if (ca != cb) return ca < cb;
-            if (occ[a] != occ[b]) return occ[a] < occ[b];
-            return gword[a] < gword[b];
-        });
-        /* Row-interleaved layout: group records in this shape order, and the records
-         * each group reads (input chunks, multi-function nodes, split-node functions)
-         * in rows of 32 groups with a stride of 32, so that the lanes of a warp that
-         * take consecutive groups read consecutive records (no bank conflicts).  Chunk
-         * j of group k = 32 r + l sits at base_r + 32 j + l.  Split-node functions keep
-         * their own input chunks contiguous after the rows. */
-        const size_t G = grec.size();
-        n_multi_nodes = (uint32_t)mrec.size();
-        std::vector<uint32_t> newidx(G);
-        for (size_t k = 0; k < G; ++k) newidx[idx[k]] = (uint32_t)k;
-        std::vector<pbn_img_group> g2(G);
-        std::vector<pbn_img_multi> m2;
-        std::vector<uint32_t> in2, s2;
-        for (size_t r0 = 0; r0 < G; r0 += 32) {
-            const size_t r1 = std::min(G, r0 + 32);
-            uint32_t maxc = 0, maxm = 0, maxf = 0;
-            for (size_t k = r0; k < r1; ++k) {
-                const pbn_img_group& O = grec[idx[k]];
-                const bool sp = O.l2w == PBN_IMG_SPLIT;
-                maxc = std::max<uint32_t>(maxc, sp ? 0u : (O.q + 3u) / 4u);
-                maxm = std::max<uint32_t>(maxm, O.n_mul);
-                maxf = std::max<uint32_t>(maxf, sp ? O.q : 0u);
-            }
-            const uint32_t cb = (uint32_t)(in2.size() / 4), mb = (uint32_t)m2.size(), sb = (uint32_t)(s2.size() / 2);
-            in2.resize(in2.size() + (size_t)4 * 32 * maxc, W32 << 7); /* padding reads the zero row */
-            m2.resize(m2.size() + (size_t)32 * maxm, pbn_img_multi{0u, 0u});
-            s2.resize(s2.size() + (size_t)2 * 32 * maxf, 0u);
-            for (size_t k = r0; k < r1; ++k) {
-                const uint32_t l = (uint32_t)(k - r0);
-                const pbn_img_group& O = grec[idx[k]];
-                pbn_img_group N = O;
-                const bool sp = O.l2w == PBN_IMG_SPLIT;
-                if (!sp) {
-                    N.in_chunk = cb + l;
-                    for (uint32_t j = 0; j < (O.q + 3u) / 4u; ++j)
-                        for (uint32_t e = 0; e < 4; ++e) in2[4 * (cb + l + 32 * j) + e] = inrec[4 * (O.in_chunk + j) + e];
-                }
-                N.mul_first = mb + l;
-                for (uint32_t m = 0; m < O.n_mul; ++m) m2[mb + l + 32 * m] = mrec[O.mul_first + m];
-                if (sp) {
-                    N.tab_off = sb + l;
-                    for (uint32_t f = 0; f < O.q; ++f) {
-                        s2[2 * (sb + l + 32 * f)] = subs[2 * (O.tab_off + f)];
-                        s2[2 * (sb + l + 32 * f) + 1] = subs[2 * (O.tab_off + f) + 1];
-                    }
-                }
-                g2[k] = N;
-            }
-        }
-        /* split-node functions' own chunks, contiguous after the rows */
-        for (size_t i = 0; i < s2.size(); i += 2) {
-            const uint32_t k = s2[i] >> 27, old = s2[i] & 0x7FFFFFFu;
-            if (s2[i] == 0 && s2[i + 1] == 0) continue; /* padding record */
-            const uint32_t nc = (k + 3u) / 4u, at = (uint32_t)(in2.size() / 4);
-            for (uint32_t j = 0; j < nc; ++j)
-                for (uint32_t e = 0; e < 4; ++e) in2.push_back(inrec[4 * (old + j) + e]);
-            if (at >= (1u << 27)) return fail(PBN_ETOOBIG, "input records beyond 2^27 chunks");
-            s2[i] = at | (k << 27);
-        }
-        /* the groups of each output word, for the word-by-word evaluation */
-        std::vector<uint32_t> wg;
-        wg.reserve(G);
-        for (uint32_t k = 0; k < W32; ++k) {
-            const uint32_t first = words[2 * k], cnt = words[2 * k + 1];
-            words[2 * k] = (uint32_t)wg.size();
-            for (uint32_t gi = first; gi < first + cnt; ++gi) wg.push_back(newidx[gi]);
-        }
-        for (size_t k = 0; k < G; ++k) gorder[k] = (uint32_t)k | (gword[idx[k]] << 20);
-        for (uint32_t v = 0; v < n; ++v)
-            if (plan->group_of[v] != UINT32_MAX) plan->group_of[v] = newidx[plan->group_of[v]];
-        grec.swap(g2);
-        mrec.swap(m2);
-        inrec.swap(in2);
-        subs.swap(s2);
-        wgroups.swap(wg);
-    }
-    /* Order of the SEL blocks: a trajectory's choice row holds block i's four choice
-     * bytes in word i, and the lanes that take the 32 groups of a row read their
-     * nodes' choices together.  Row by row, each block not yet placed goes to a
-     * shared-memory bank (word mod 32) that no other block of the row uses, while the
-     * banks' word counts allow; the draws and slots only move with their blocks. */
-    if (selblk.size() > 32) {
-        const uint32_t ns = (uint32_t)selblk.size();
-        std::vector<int> bank(ns, -1);
-        std::vector<uint32_t> cap(32);
-        for (uint32_t b = 0; b < 32; ++b) cap[b] = ns / 32 + (b < ns % 32 ? 1u : 0u);
-        auto place = [&](uint32_t blk, uint32_t used) {
-            int best = -1;
-            for (int b = 0; b < 32; ++b) {
-                if (!cap[b]) continue;
-                if (best < 0) { best = b; continue; }
-                const bool fb = !((used >> b) & 1u), fbest = !((used >> best) & 1u);
-                if (fb != fbest ? fb : cap[b] > cap[best]) best = b;
-            }
-            bank[blk] = best;
-            cap[best]--;
-            return 1u << best;
-        };
-        const size_t G = grec.size();
-        for (size_t r0 = 0; r0 < G; r0 += 32) {
-            const size_t r1 = std::min(G, r0 + 32);
-            uint32_t used = 0;
-            std::vector<uint32_t> fresh;
-            for (size_t k = r0; k < r1; ++k)
-                for (uint32_t m = 0; m < grec[k].n_mul; ++m) {
-                    const uint32_t blk = mrec[grec[k].mul_first + 32u * m].ch_off >> 2;
-                    if (bank[blk] >= 0) used |= 1u << bank[blk];
-                    else fresh.push_back(blk);
-                }
-            for (uint32_t blk : fresh) used |= bank[blk] >= 0 ? 1u << bank[blk] : place(blk, used);
-        }
-        for (uint32_t i = 0; i < ns; ++i)
-            if (bank[i] < 0) place(i, 0u);
-        std::vector<uint32_t> next(32), newpos(ns);
-        std::iota(next.begin(), next.end(), 0u);
-        for (uint32_t i = 0; i < ns; ++i) {
-            newpos[i] = next[bank[i]];
-            next[bank[i]] += 32;
-        }
-        std::vector<uint32_t> sb2(ns), ss2(selslot.size());
-        for (uint32_t i = 0; i < ns; ++i) sb2[newpos[i]] = selblk[i];
-        for (uint32_t s = 0; s < 4 * ns; ++s) {
-            const uint32_t s2n = 4 * newpos[s >> 2] + (s & 3u);
-            for (uint32_t e = 0; e < 4; ++e) ss2[slot_rec(s2n) + e] = selslot[slot_rec(s) + e];
-        }
-        for (pbn_img_multi& M : mrec)
-            if (M.radix != 0) M.ch_off = 4 * newpos[M.ch_off >> 2] + (M.ch_off & 3u);
-        selblk.swap(sb2);
-        selslot.swap(ss2);
-    }
-    std::vector<uint64_t> ret(W, 0);
-    for (uint32_t v = 0; v < n; ++v)
+/* Header, section offsets (16-byte aligned) and the image bytes; decides whether the
+ * tables are staged in shared memory with the specs (within the budget). */
+int assemble_image(const pbn_net& g, const pbn_group_params& prm, const ImageBuild& B, pbn_plan* plan) {
+    std::vector<uint64_t> ret(B.W, 0);
+    for (uint32_t v = 0; v < B.n; ++v)
         if (g.retained[v]) ret[v >> 6] |= 1ull << (v & 63);
-
-    /* assemble the image */
     pbn_img_header H{};
     H.magic = PBN_IMG_MAGIC;
-    H.n = n;
-    H.W = W;
-    H.W32 = W32;
-    H.n_groups = (uint32_t)grec.size();
-    H.n_multi = (uint32_t)mrec.size();
-    H.n_sel = (uint32_t)selblk.size();
+    H.n = B.n;
+    H.W = B.W;
+    H.W32 = B.W32;
+    H.n_groups = (uint32_t)B.grec.size();
+    H.n_multi = (uint32_t)B.mrec.size();
+    H.n_sel = (uint32_t)B.selblk.size();
     H.P = (uint32_t)pbn::pert_threshold(g.p);
     H.semantics = prm.semantics;
     H.sampler = prm.sampler;
     size_t off = align16(sizeof(pbn_img_header));
-    H.off_words = (uint32_t)off; off = align16(off + words.size() * 4);
-    H.off_groups = (uint32_t)off; off = align16(off + grec.size() * sizeof(pbn_img_group));
-    H.off_multi = (uint32_t)off; off = align16(off + mrec.size() * sizeof(pbn_img_multi));
-    H.off_selslot = (uint32_t)off; off = align16(off + selslot.size() * 4);
-    H.off_thr = (uint32_t)off; off = align16(off + thr.size() * 4);
-    H.off_inputs = (uint32_t)off; off = align16(off + inrec.size() * 4);
-    H.off_selblk = (uint32_t)off; off = align16(off + selblk.size() * 4);
-    H.off_gorder = (uint32_t)off; off = align16(off + gorder.size() * 4);
-    H.off_wgroups = (uint32_t)off; off = align16(off + wgroups.size() * 4);
-    H.off_subs = (uint32_t)off; off = align16(off + subs.size() * 4);
-    H.off_tables = (uint32_t)off; off = align16(off + tables.size() * 4);
+    H.off_words = (uint32_t)off; off = align16(off + B.words.size() * 4);
+    H.off_groups = (uint32_t)off; off = align16(off + B.grec.size() * sizeof(pbn_img_group));
+    H.off_multi = (uint32_t)off; off = align16(off + B.mrec.size() * sizeof(pbn_img_multi));
+    H.off_selslot = (uint32_t)off; off = align16(off + B.selslot.size() * 4);
+    H.off_thr = (uint32_t)off; off = align16(off + B.thr.size() * 4);
+    H.off_inputs = (uint32_t)off; off = align16(off + B.inrec.size() * 4);
+    H.off_selblk = (uint32_t)off; off = align16(off + B.selblk.size() * 4);
+    H.off_gorder = (uint32_t)off; off = align16(off + B.gorder.size() * 4);
+    H.off_wgroups = (uint32_t)off; off = align16(off + B.wgroups.size() * 4);
+    H.off_subs = (uint32_t)off; off = align16(off + B.subs.size() * 4);
+    H.off_tables = (uint32_t)off; off = align16(off + B.tables.size() * 4);
     H.off_ret = (uint32_t)off; off = align16(off + ret.size() * 8);
     H.off_pos = (uint32_t)off; off = align16(off + plan->pos.size() * 4);
     H.off_geo = (uint32_t)off; off = align16(off + 64 * 8);
@@ -1036,67 +1058,93 @@ int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
 
     plan->image.assign(off, 0);
     uint8_t* img = plan->image.data();
+    auto put = [&](uint32_t at, const void* src, size_t bytes) {
+        if (bytes) memcpy(img + at, src, bytes);
+    };
     memcpy(img, &H, sizeof(H));
-    memcpy(img + H.off_words, words.data(), words.size() * 4);
-    if (!grec.empty()) memcpy(img + H.off_groups, grec.data(), grec.size() * sizeof(pbn_img_group));
-    if (!mrec.empty()) memcpy(img + H.off_multi, mrec.data(), mrec.size() * sizeof(pbn_img_multi));
-    if (!selslot.empty()) memcpy(img + H.off_selslot, selslot.data(), selslot.size() * 4);
-    if (!thr.empty()) memcpy(img + H.off_thr, thr.data(), thr.size() * 4);
-    if (!inrec.empty()) memcpy(img + H.off_inputs, inrec.data(), inrec.size() * 4);
-    if (!selblk.empty()) memcpy(img + H.off_selblk, selblk.data(), selblk.size() * 4);
-    if (!gorder.empty()) memcpy(img + H.off_gorder, gorder.data(), gorder.size() * 4);
-    if (!wgroups.empty()) memcpy(img + H.off_wgroups, wgroups.data(), wgroups.size() * 4);
-    if (!subs.empty()) memcpy(img + H.off_subs, subs.data(), subs.size() * 4);
-    memcpy(img + H.off_ret, ret.data(), ret.size() * 8);
-    memcpy(img + H.off_pos, plan->pos.data(), plan->pos.size() * 4);
-    {
-        uint64_t G[64];
-        geometric_thresholds(H.P, G);
-        memcpy(img + H.off_geo, G, sizeof(G));
-    }
-    if (!tables.empty()) memcpy(img + H.off_tables, tables.data(), tables.size() * 4);
+    put(H.off_words, B.words.data(), B.words.size() * 4);
+    put(H.off_groups, B.grec.data(), B.grec.size() * sizeof(pbn_img_group));
+    put(H.off_multi, B.mrec.data(), B.mrec.size() * sizeof(pbn_img_multi));
+    put(H.off_selslot, B.selslot.data(), B.selslot.size() * 4);
+    put(H.off_thr, B.thr.data(), B.thr.size() * 4);
+    put(H.off_inputs, B.inrec.data(), B.inrec.size() * 4);
+    put(H.off_selblk, B.selblk.data(), B.selblk.size() * 4);
+    put(H.off_gorder, B.gorder.data(), B.gorder.size() * 4);
+    put(H.off_wgroups, B.wgroups.data(), B.wgroups.size() * 4);
+    put(H.off_subs, B.subs.data(), B.subs.size() * 4);
+    put(H.off_ret, ret.data(), ret.size() * 8);
+    put(H.off_pos, plan->pos.data(), plan->pos.size() * 4);
+    uint64_t geo[64];
+    geometric_thresholds(H.P, geo);
+    put(H.off_geo, geo, sizeof(geo));
+    put(H.off_tables, B.tables.data(), B.tables.size() * 4);
     plan->hdr = H;
-    plan->per_traj_smem = 4 * (2 * (W32 + 1) + (H.n_sel | 1u));
+    plan->per_traj_smem = 4 * (2 * (B.W32 + 1) + (H.n_sel | 1u));
+    return PBN_OK;
+}
 
+/* pbn_plan_info, with the algorithmic work of one trajectory-step (the roofline's
+ * per-unit figure): Philox4x32-10 blocks at 56 ops, the expected perturbation levels
+ * (or the geometric sampler's block per word pair), and, weighted by the probability
+ * of a non-perturbed step, the SEL blocks, thresholds, gathers and lookups. */
+void fill_info(const pbn_net& g, const pbn_group_params& prm, const PlanParts& pp, const ImageBuild& B,
+               pbn_plan* plan) {
+    const pbn_img_header& H = plan->hdr;
     pbn_plan_info& I = plan->info;
     memset(&I, 0, sizeof(I));
-    I.n = n;
-    for (uint32_t v = 0; v < n; ++v) I.n_retained += g.retained[v];
+    I.n = B.n;
+    for (uint32_t v = 0; v < B.n; ++v) I.n_retained += g.retained[v];
     I.n_groups = H.n_groups;
-    I.n_groups_multi = n_groups_multi;
-    I.state_words = W32 / 2;
+    I.n_groups_multi = B.n_groups_multi;
+    I.state_words = B.W32 / 2;
     I.n_sel_blocks = H.n_sel;
     I.m_lower_bound = pp.m_lower;
     I.m_found = pp.m_found;
     I.sum_weights = pp.sum_w;
-    I.table_bytes = tables.size() * 4;
+    I.table_bytes = B.tables.size() * 4;
     I.image_bytes = H.image_bytes;
     I.stage_bytes = H.stage_bytes;
     I.tables_in_smem = H.tables_in_smem;
-    I.total_inputs = (uint32_t)total_inputs;
-    I.n_multi = n_multi_nodes;
-    I.n_split = n_split;
+    I.total_inputs = (uint32_t)B.total_inputs;
+    I.n_multi = B.n_multi_nodes;
+    I.n_split = B.n_split;
     I.semantics = prm.semantics;
     I.sampler = prm.sampler;
-    I.total_thresholds = (uint32_t)thr.size();
-    /* algorithmic work of one trajectory-step (the roofline's per-unit figure) */
-    {
-        const double pe = (double)H.P / 4294967296.0;
-        double blocks = 0.0;
-        if (H.P) {
-            for (uint32_t w = 0; w < W; ++w) {
-                const uint32_t k = (w == W - 1 && (n & 63u)) ? (n & 63u) : 64u;
-                for (int h = 0; h < 16; ++h) blocks += 1.0 - std::pow(1.0 - std::ldexp(1.0, -2 * h), (double)k);
-            }
+    I.total_thresholds = (uint32_t)B.thr.size();
+    const uint32_t n = B.n, W = B.W;
+    const double pe = (double)H.P / 4294967296.0;
+    double blocks = 0.0;
+    if (H.P) {
+        for (uint32_t w = 0; w < W; ++w) {
+            const uint32_t k = (w == W - 1 && (n & 63u)) ? (n & 63u) : 64u;
+            for (int h = 0; h < 16; ++h) blocks += 1.0 - std::pow(1.0 - std::ldexp(1.0, -2 * h), (double)k);
         }
-        double pert = blocks * (56.0 + 12.0) + 4.0;
-        if (prm.sampler == PBN_PERT_GEOMETRIC) /* one block per word pair, a 64-bit compare per word */
-            pert = H.P ? 56.0 * (double)((W + 1) / 2) + 4.0 * (double)W + 4.0 : 4.0;
-        const double nonpert = 56.0 * H.n_sel + 2.0 * (double)thr.size() + (double)n_multi_nodes +
-                               3.0 * (double)total_inputs + 5.0 * (double)(H.n_groups + n_split) +
-                               2.0 * (double)(W32 / 2);
-        I.ops_per_step = pert + std::pow(1.0 - pe, (double)n) * nonpert + 8.0;
     }
+    double pert = blocks * (56.0 + 12.0) + 4.0;
+    if (prm.sampler == PBN_PERT_GEOMETRIC) /* one block per word pair, a 64-bit compare per word */
+        pert = H.P ? 56.0 * (double)((W + 1) / 2) + 4.0 * (double)W + 4.0 : 4.0;
+    const double nonpert = 56.0 * H.n_sel + 2.0 * (double)B.thr.size() + (double)B.n_multi_nodes +
+                           3.0 * (double)B.total_inputs + 5.0 * (double)(H.n_groups + B.n_split) +
+                           2.0 * (double)(B.W32 / 2);
+    I.ops_per_step = pert + std::pow(1.0 - pe, (double)n) * nonpert + 8.0;
+}
+
+int build_plan(const pbn_net& g, const pbn_group_params& prm, pbn_plan* plan) {
+    PlanParts pp;
+    partition(g, prm, &pp);
+    ImageBuild B;
+    B.n = g.n;
+    B.W = (g.n + 63) / 64;
+    pack_words(pp, &B);
+    place_nodes(pp, B, plan);
+    sel_blocks(g, &B);
+    int rc = emit_groups(g, prm, pp, *plan, &B);
+    if (rc == PBN_OK) rc = interleave_rows(&B, plan);
+    if (rc != PBN_OK) return rc;
+    place_sel_blocks(&B);
+    rc = assemble_image(g, prm, B, plan);
+    if (rc != PBN_OK) return rc;
+    fill_info(g, prm, pp, B, plan);
     return PBN_OK;
 }
 
