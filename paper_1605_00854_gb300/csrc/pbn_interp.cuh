@@ -7,7 +7,11 @@
  * Per CTA the staged plan image sits at the start of shared memory; each
  * trajectory slot owns two state buffers of W32 + 1 32-bit words (the last one
  * always zero; odd stride, so a warp reading one row of 32 slots hits 32 banks)
- * and a row of 4 * n_sel + 1 SEL uniforms.  Per step:
+ * and a choice row of n_sel | 1 words (one choice byte per SEL slot, four per SEL
+ * block).  With LG > 1 lanes per trajectory the lanes split the perturbation words
+ * and SEL blocks and take the groups in the image's evaluation order (shape classes,
+ * output words alternating within a class), ORing into the shared next-state words.
+ * Per step:
  *   1. perturbation (Sec. 3.2, Step 2): every original 64-node word draws its
  *      Bernoulli(P / 2^32) lanes bit-sliced, most significant level first, and
  *      stops once every lane is decided or no later level can change the outcome.
