@@ -190,52 +190,43 @@ struct Generated {
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
 };
 
-bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string* why) {
-    View V{&plan.hdr, plan.image.data()};
-    const pbn_img_header& H = plan.hdr;
-    if (H.W32 > PBN_JIT_MAX_ROWS) {
-        *why = "state wider than 64 words";
-        return false;
-    }
-    /* wide plans: SEL blocks drawn lazily in group order, so their uniforms are live
-     * only while the groups that need them are evaluated */
-    const bool wide = (flags & PBN_COMPILE_WIDE) != 0;
-    if (H.W > (wide ? 32u : 16u)) {
-        *why = wide ? "more than 2048 original nodes" : "more than 1024 original nodes";
-        return false;
-    }
-    if (!wide && H.n_sel > 24) {
-        *why = "more than 24 selection blocks per step";
-        return false;
-    }
-    const uint2* words = V.at<uint2>(H.off_words);
-    const pbn_img_group* groups = V.at<pbn_img_group>(H.off_groups);
-    const pbn_img_multi* multi = V.at<pbn_img_multi>(H.off_multi);
-    const uint32_t* thr = V.at<uint32_t>(H.off_thr);
-    const uint32_t* inrec = V.at<uint32_t>(H.off_inputs);
-    const uint32_t* selblk = V.at<uint32_t>(H.off_selblk);
-    const uint64_t* ret = V.at<uint64_t>(H.off_ret);
-    const uint32_t* pos = V.at<uint32_t>(H.off_pos);
-    const uint32_t* tab = V.at<uint32_t>(H.off_tables);
-    uint32_t table_bytes = H.off_ret - H.off_tables;
-    const uint32_t* selslot = V.at<uint32_t>(H.off_selslot);
-    const uint32_t* subs = V.at<uint32_t>(H.off_subs);
+/* The CUDA source of one plan's kernel.  The plan image is read on the host: every
+ * gather, threshold, perturbation level and small table becomes an immediate, and
+ * the step loop is emitted in the code shape the flags select. */
+class KernelSource {
+public:
+    KernelSource(const pbn_plan& plan, uint32_t flags)
+        : H(plan.hdr), V{&plan.hdr, plan.image.data()}, flags_(flags), wide((flags & PBN_COMPILE_WIDE) != 0) {}
 
-    /* start offsets of every table (merged groups and split-node functions), sorted */
-    std::vector<uint32_t> tab_starts;
-    for (uint32_t g = 0; g < H.n_groups; ++g) {
-        if (groups[g].l2w != PBN_IMG_SPLIT) tab_starts.push_back(groups[g].tab_off);
-        else
-            for (uint32_t f = 0; f < groups[g].q; ++f) tab_starts.push_back(subs[2 * (groups[g].tab_off + 32 * f) + 1]);
+    bool generate(Generated* out, std::string* why) {
+        if (!fits(why)) return false;
+        bind_sections();
+        collect_table_starts();
+        plan_multiply_gathers();
+        tab_smem = table_bytes <= 48u * 1024u;
+        out->tab_bytes = tab_smem ? table_bytes : 0u;
+        emit_globals();
+        emit_prologue();
+        /* the geometric sampler has no level loop to pipeline: its pipelined form is
+         * the interleaved one */
+        geometric = H.sampler == PBN_PERT_GEOMETRIC;
+        pipelined = (flags_ & PBN_COMPILE_PIPELINED) != 0 && !geometric && !wide;
+        interleave = !wide && ((flags_ & PBN_COMPILE_INTERLEAVED) != 0 ||
+                               ((flags_ & PBN_COMPILE_PIPELINED) != 0 && geometric));
+        /* node-wise semantics: every step evaluates the functions and the perturbed
+         * nodes (collected in masks) take NOT s */
+        nodewise = H.semantics == PBN_SEM_NODEWISE;
+        Pv = H.P;
+        hmax = Pv ? (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u : 0u;
+        if (pipelined) emit_pipelined_steps();
+        else emit_steps();
+        emit_epilogue();
+        out->src = o.str();
+        return true;
     }
-    std::sort(tab_starts.begin(), tab_starts.end());
 
-    /* Multiply gathers (PBN_COMPILE_MAGIC_GATHER): for every merged group, the inputs
-     * of one state word with 3 to 8 bits become one multiply-gather field when an
-     * injective multiplier exists; the other inputs stay single-bit gathers.  Such a
-     * group gets its table rebuilt in the new index order, appended after a copy of
-     * the plan's tables; the kernel then reads its tables from that array (a
-     * __device__ array of the generated source) instead of the plan image. */
+private:
+    /* a group that gathers some of its inputs by multiplication (PBN_COMPILE_MAGIC_GATHER) */
     struct GTerm {
         bool magic;
         MagicTerm m;         /* magic == true */
@@ -247,10 +238,79 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         std::vector<GTerm> terms;
         uint32_t qn = 0, tab_off = 0, tab_words = 0;
     };
-    std::vector<GPlan> gp(H.n_groups);
-    std::vector<uint32_t> tabm;
-    const bool magic = (flags & PBN_COMPILE_MAGIC_GATHER) != 0 && table_bytes <= 256u * 1024u;
-    if (magic) {
+
+    const pbn_img_header& H;
+    View V;
+    const uint32_t flags_;
+    const bool wide; /* SEL blocks drawn lazily in group order: their uniforms live only
+                        while the groups that need them are evaluated */
+    const uint2* words = nullptr;
+    const pbn_img_group* groups = nullptr;
+    const pbn_img_multi* multi = nullptr;
+    const uint32_t *thr = nullptr, *inrec = nullptr, *selblk = nullptr, *pos = nullptr, *tab = nullptr;
+    const uint32_t *selslot = nullptr, *subs = nullptr;
+    const uint64_t* ret = nullptr;
+    uint32_t table_bytes = 0;
+    std::vector<uint32_t> tab_starts; /* start offsets of every table, sorted */
+    std::vector<GPlan> gp;
+    std::vector<uint32_t> tabm;       /* the plan's tables, then the rebuilt ones */
+    bool magic = false, tab_smem = false;
+    bool geometric = false, pipelined = false, interleave = false, nodewise = false;
+    uint32_t Pv = 0, hmax = 0;
+    std::string z; /* meta-state indicator of s */
+    std::ostringstream o;
+
+    bool fits(std::string* why) const {
+        if (H.W32 > PBN_JIT_MAX_ROWS) {
+            *why = "state wider than 64 words";
+            return false;
+        }
+        if (H.W > (wide ? 32u : 16u)) {
+            *why = wide ? "more than 2048 original nodes" : "more than 1024 original nodes";
+            return false;
+        }
+        if (!wide && H.n_sel > 24) {
+            *why = "more than 24 selection blocks per step";
+            return false;
+        }
+        return true;
+    }
+
+    void bind_sections() {
+        words = V.at<uint2>(H.off_words);
+        groups = V.at<pbn_img_group>(H.off_groups);
+        multi = V.at<pbn_img_multi>(H.off_multi);
+        thr = V.at<uint32_t>(H.off_thr);
+        inrec = V.at<uint32_t>(H.off_inputs);
+        selblk = V.at<uint32_t>(H.off_selblk);
+        ret = V.at<uint64_t>(H.off_ret);
+        pos = V.at<uint32_t>(H.off_pos);
+        tab = V.at<uint32_t>(H.off_tables);
+        table_bytes = H.off_ret - H.off_tables;
+        selslot = V.at<uint32_t>(H.off_selslot);
+        subs = V.at<uint32_t>(H.off_subs);
+    }
+
+    /* start offsets of every table (merged groups and split-node functions), sorted */
+    void collect_table_starts() {
+        for (uint32_t g = 0; g < H.n_groups; ++g) {
+            if (groups[g].l2w != PBN_IMG_SPLIT) tab_starts.push_back(groups[g].tab_off);
+            else
+                for (uint32_t f = 0; f < groups[g].q; ++f) tab_starts.push_back(subs[2 * (groups[g].tab_off + 32 * f) + 1]);
+        }
+        std::sort(tab_starts.begin(), tab_starts.end());
+    }
+
+    /* Multiply gathers (PBN_COMPILE_MAGIC_GATHER): for every merged group, the inputs
+     * of one state word with 3 to 8 bits become one multiply-gather field when an
+     * injective multiplier exists; the other inputs stay single-bit gathers.  Such a
+     * group gets its table rebuilt in the new index order, appended after a copy of
+     * the plan's tables; the kernel then reads its tables from that array (a
+     * __device__ array of the generated source) instead of the plan image. */
+    void plan_multiply_gathers() {
+        gp.assign(H.n_groups, GPlan{});
+        magic = (flags_ & PBN_COMPILE_MAGIC_GATHER) != 0 && table_bytes <= 256u * 1024u;
+        if (!magic) return;
         tabm.assign(tab, tab + table_bytes / 4);
         for (uint32_t g = 0; g < H.n_groups; ++g) {
             const pbn_img_group& G = groups[g];
@@ -316,93 +376,84 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         tabm.resize((tabm.size() + 3) & ~(size_t)3, 0u); /* bulk copies move multiples of 16 bytes */
         table_bytes = (uint32_t)(tabm.size() * 4);
     }
-    const bool tab_smem = table_bytes <= 48u * 1024u;
-    out->tab_bytes = tab_smem ? table_bytes : 0u;
 
-    std::ostringstream o;
-    o << "#include \"pbn_device.cuh\"\n";
-    if (H.sampler == PBN_PERT_GEOMETRIC) {
-        const uint64_t* G = V.at<uint64_t>(H.off_geo);
-        o << "__device__ const unsigned long long GEO_T[64] = {";
-        for (int k = 0; k < 64; ++k) o << (k ? ", " : "") << fmt("0x%016llxull", (unsigned long long)G[k]);
-        o << "};\n";
-    }
-    if (magic) {
-        /* the plan's tables followed by the rebuilt tables of multiply-gather groups */
-        o << "__device__ __align__(16) const uint32_t TABM[" << std::max<size_t>(tabm.size(), 4) << "] = {";
-        for (size_t i = 0; i < tabm.size(); ++i) o << (i ? (i % 8 ? ", " : ",\n  ") : "") << hex32(tabm[i]);
-        o << "};\n";
-    }
-    const char* tab_src = magic ? "reinterpret_cast<const uint8_t*>(TABM)" : "P.image + P.off_tables";
-    o << "extern \"C\" __global__ void __launch_bounds__(512) pbn_plan_kernel(const pbn_jit_params P) {\n";
-    o << "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n";
-    if (tab_smem) {
-        o << "  if (!pbn_stage(smem, " << tab_src << ", P.tab_bytes, &bar)) {\n"
-             "    if (threadIdx.x == 0 && P.status) atomicOr(P.status, 1u);\n    return;\n  }\n"
-             "  const uint32_t* TAB = reinterpret_cast<const uint32_t*>(smem);\n";
-    } else {
-        o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(" << tab_src << ");\n";
-    }
-    o << "  const uint32_t lt = blockIdx.x * blockDim.x + threadIdx.x;\n"
-         "  const bool active = lt < P.n_traj;\n"
-         "  const uint64_t traj = P.traj_begin + lt;\n"
-         "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n";
-    o << "  uint32_t";
-    for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "s" << r << " = 0";
-    o << ";\n  if (active) {\n";
-    /* initial state */
-    o << "    if (P.init == 0) {\n      const pbn_philox_step ps = pbn_philox_begin(P, traj, 0);\n";
-    for (uint32_t pr = 0; 2 * pr < H.W; ++pr) {
-        const uint64_t r0 = ret[2 * pr], r1 = (2 * pr + 1 < H.W) ? ret[2 * pr + 1] : 0;
-        if (!(r0 | r1)) continue;
-        o << "      const uint4 I" << pr << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_INIT << 28) | pr) << ");\n";
-        for (uint32_t half = 0; half < 2; ++half) {
-            const uint32_t w = 2 * pr + half;
-            const uint64_t rw = half ? r1 : r0;
-            for (uint32_t b = 0; b < 64; ++b) {
-                if (!((rw >> b) & 1u)) continue;
-                const uint32_t ps = pos[64 * w + b], row = ps >> 5, bit = ps & 31;
-                const char comp = lanes[2 * half + (b >= 32 ? 1 : 0)];
-                o << fmt("      s%u |= ((I%u.%c >> %u) & 1u) << %u;\n", row, pr, comp, b & 31, bit);
-            }
+    /* the geometric sampler's thresholds and the rebuilt tables, as __device__ arrays */
+    void emit_globals() {
+        o << "#include \"pbn_device.cuh\"\n";
+        if (H.sampler == PBN_PERT_GEOMETRIC) {
+            const uint64_t* G = V.at<uint64_t>(H.off_geo);
+            o << "__device__ const unsigned long long GEO_T[64] = {";
+            for (int k = 0; k < 64; ++k) o << (k ? ", " : "") << fmt("0x%016llxull", (unsigned long long)G[k]);
+            o << "};\n";
+        }
+        if (magic) {
+            /* the plan's tables followed by the rebuilt tables of multiply-gather groups */
+            o << "__device__ __align__(16) const uint32_t TABM[" << std::max<size_t>(tabm.size(), 4) << "] = {";
+            for (size_t i = 0; i < tabm.size(); ++i) o << (i ? (i % 8 ? ", " : ",\n  ") : "") << hex32(tabm[i]);
+            o << "};\n";
         }
     }
-    o << "    } else {\n";
-    for (uint32_t r = 0; r < H.W32; r += 2)
-        o << "      { const uint64_t v = P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt]; s" << r
-          << " = (uint32_t)v; s" << r + 1 << " = (uint32_t)(v >> 32); }\n";
-    o << "    }\n";
-    /* meta indicator */
-    std::string z = "1u";
-    {
+
+    /* kernel entry, table staging, the initial state (keyed INIT draws or the stored
+     * state) and the meta-state indicator of s(step_begin) */
+    void emit_prologue() {
+        const char* tab_src = magic ? "reinterpret_cast<const uint8_t*>(TABM)" : "P.image + P.off_tables";
+        o << "extern \"C\" __global__ void __launch_bounds__(512) pbn_plan_kernel(const pbn_jit_params P) {\n";
+        o << "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n";
+        if (tab_smem) {
+            o << "  if (!pbn_stage(smem, " << tab_src << ", P.tab_bytes, &bar)) {\n"
+                 "    if (threadIdx.x == 0 && P.status) atomicOr(P.status, 1u);\n    return;\n  }\n"
+                 "  const uint32_t* TAB = reinterpret_cast<const uint32_t*>(smem);\n";
+        } else {
+            o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(" << tab_src << ");\n";
+        }
+        o << "  const uint32_t lt = blockIdx.x * blockDim.x + threadIdx.x;\n"
+             "  const bool active = lt < P.n_traj;\n"
+             "  const uint64_t traj = P.traj_begin + lt;\n"
+             "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n";
+        o << "  uint32_t";
+        for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "s" << r << " = 0";
+        o << ";\n  if (active) {\n";
+        /* initial state */
+        o << "    if (P.init == 0) {\n      const pbn_philox_step ps = pbn_philox_begin(P, traj, 0);\n";
+        for (uint32_t pr = 0; 2 * pr < H.W; ++pr) {
+            const uint64_t r0 = ret[2 * pr], r1 = (2 * pr + 1 < H.W) ? ret[2 * pr + 1] : 0;
+            if (!(r0 | r1)) continue;
+            o << "      const uint4 I" << pr << " = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_INIT << 28) | pr) << ");\n";
+            for (uint32_t half = 0; half < 2; ++half) {
+                const uint32_t w = 2 * pr + half;
+                const uint64_t rw = half ? r1 : r0;
+                for (uint32_t b = 0; b < 64; ++b) {
+                    if (!((rw >> b) & 1u)) continue;
+                    const uint32_t ps = pos[64 * w + b], row = ps >> 5, bit = ps & 31;
+                    const char comp = lanes[2 * half + (b >= 32 ? 1 : 0)];
+                    o << fmt("      s%u |= ((I%u.%c >> %u) & 1u) << %u;\n", row, pr, comp, b & 31, bit);
+                }
+            }
+        }
+        o << "    } else {\n";
+        for (uint32_t r = 0; r < H.W32; r += 2)
+            o << "      { const uint64_t v = P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt]; s" << r
+              << " = (uint32_t)v; s" << r + 1 << " = (uint32_t)(v >> 32); }\n";
+        o << "    }\n";
         std::ostringstream zs;
         zs << "(";
         for (uint32_t r = 0; r < H.W32; ++r)
             zs << (r ? " & " : "") << "(uint32_t)((s" << r << " & P.meta_mask[" << r << "]) == P.meta_val[" << r << "])";
         zs << ")";
         z = zs.str();
+        o << "    uint32_t zp = " << z << ";\n    if (P.count_first) cV += zp;\n";
     }
-    o << "    uint32_t zp = " << z << ";\n    if (P.count_first) cV += zp;\n";
-    /* the geometric sampler has no level loop to pipeline: its pipelined form is
-     * the interleaved one */
-    const bool geometric = H.sampler == PBN_PERT_GEOMETRIC;
-    const bool pipelined = (flags & PBN_COMPILE_PIPELINED) != 0 && !geometric && !wide;
-    const bool interleave = !wide && ((flags & PBN_COMPILE_INTERLEAVED) != 0 ||
-                                      ((flags & PBN_COMPILE_PIPELINED) != 0 && geometric));
-    /* node-wise semantics: every step evaluates the functions and the perturbed
-     * nodes (collected in masks) take NOT s */
-    const bool nodewise = H.semantics == PBN_SEM_NODEWISE;
-    const uint32_t Pv = H.P;
-    const uint32_t hmax = Pv ? (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u : 0u;
 
     /* the SEL blocks of one step as uint4 <name><i> drawn from Philox state <ps> */
-    auto emit_sel_draws = [&](const char* ind, const char* decl, const char* name, const char* ps) {
+    void emit_sel_draws(const char* ind, const char* decl, const char* name, const char* ps) {
         for (uint32_t i = 0; i < H.n_sel; ++i)
             o << ind << decl << name << i << " = pbn_philox_draw(P, " << ps << ", "
               << hex32((PBN_DOM_SEL << 28) | selblk[i]) << ");\n";
-    };
+    }
+
     /* perturbed retained lanes of word w (masks pl/ph): op into s<row> or a mask */
-    auto emit_flips = [&](uint32_t w, const std::string& pl, const std::string& ph, const char* target, const char* op) {
+    void emit_flips(uint32_t w, const std::string& pl, const std::string& ph, const char* target, const char* op) {
         const uint32_t rl = (uint32_t)ret[w], rh = (uint32_t)(ret[w] >> 32);
         for (int half = 0; half < 2; ++half) {
             const uint32_t rm = half ? rh : rl;
@@ -417,14 +468,17 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             }
             o << "          } } }\n";
         }
-    };
-    auto valid_of = [&](uint32_t w) {
+    }
+
+    /* lanes of original word w that hold nodes */
+    uint64_t valid_of(uint32_t w) const {
         const uint32_t nl = (w == H.W - 1) ? (H.n - 64 * w) : 64u;
         return nl >= 64 ? ~0ull : ((1ull << nl) - 1ull);
-    };
+    }
+
     /* one straight-line level pair h of word w with P's two bits as constants,
      * updating masks ul/uh (undecided) and pl/ph (perturbed) with suffix sfx */
-    auto emit_level = [&](const char* ind, uint32_t w, uint32_t h, const std::string& sfx, const char* ps) {
+    void emit_level(const char* ind, uint32_t w, uint32_t h, const std::string& sfx, const char* ps) {
         const uint32_t b0 = (Pv >> (31 - 2 * h)) & 1u;
         const uint32_t b1 = (Pv >> (30 - 2 * h)) & 1u;
         const char* S = sfx.c_str();
@@ -434,10 +488,10 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         if (b1) o << fmt(" pl%s |= ul%s & ~x.z; ph%s |= uh%s & ~x.w; ul%s &= x.z; uh%s &= x.w;", S, S, S, S, S, S);
         else o << fmt(" ul%s &= ~x.z; uh%s &= ~x.w;", S, S);
         o << " }\n";
-    };
+    }
+
     /* the rolled loop over the remaining level pairs h0.. of words w (and w + 1) */
-    auto emit_level_loop = [&](uint32_t w, bool two, uint32_t h0, const std::string& s0, const std::string& s1,
-                               const char* ps) {
+    void emit_level_loop(uint32_t w, bool two, uint32_t h0, const std::string& s0, const std::string& s1, const char* ps) {
         o << "        { uint32_t pp = " << hex32(h0 ? (Pv << (2 * h0)) : Pv) << ";\n"
           << "#pragma unroll 1\n"
           << "        for (uint32_t h = " << h0 << "u; h < " << hmax << "u; ++h) {\n"
@@ -456,9 +510,10 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
                      S, S, k, S, S, k, S, k, S, k);
         }
         o << "        } }\n";
-    };
+    }
+
     /* choice of a multi-function node from its SEL slot's thresholds */
-    auto choice_expr = [&](const pbn_img_multi& M) {
+    std::string choice_expr(const pbn_img_multi& M) const {
         const uint32_t slot = M.ch_off;
         const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
         const uint32_t* ss = selslot + 4 * ((slot & 3u) * H.n_sel + (slot >> 2)); /* t1, t2, n_thr, first */
@@ -469,10 +524,11 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             j += (q ? " + " : "") + fmt("(uint32_t)(%s >= %s)", u.c_str(), hex32(T).c_str());
         }
         return j;
-    };
+    }
+
     /* input pattern of k inputs from chunked records `stride` chunks apart (32 in
      * the row-interleaved group layout, 1 for a split node's functions) */
-    auto pattern = [&](uint32_t in_chunk, uint32_t k, uint32_t stride) {
+    std::string pattern(uint32_t in_chunk, uint32_t k, uint32_t stride) const {
         std::string xexpr;
         for (uint32_t b = 0; b < k; ++b) {
             const uint32_t rec = inrec[4 * (in_chunk + stride * (b / 4)) + (b & 3)];
@@ -480,23 +536,115 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             xexpr += (b ? " | " : "") + gather(row, bit, b);
         }
         return xexpr.empty() ? std::string("0u") : xexpr;
-    };
+    }
+
+    std::vector<uint32_t> blocks_of(uint32_t gi) const {
+        std::vector<uint32_t> b;
+        const pbn_img_group& G = groups[gi];
+        for (uint32_t m = 0; m < G.n_mul; ++m) b.push_back(multi[G.mul_first + 32 * m].ch_off / 4);
+        return b;
+    }
+
+    /* split node: every function's pattern is a few register operations; the selected
+     * one's table bit is kept (immediates when every table fits in 64 bits, else one
+     * lookup at the selected table) */
+    void emit_split_group(uint32_t r, const pbn_img_group& G) {
+        std::string j = choice_expr(multi[G.mul_first]);
+        if (j.empty()) j = "0u";
+        o << "const uint32_t j = " << j << "; ";
+        bool small = true;
+        for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + 32 * f)] >> 27) <= 6;
+        std::string v = "0u";
+        if (small) {
+            for (uint32_t f = G.q; f-- > 0;) {
+                const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
+                const uint32_t k = F[0] >> 27, ch = F[0] & 0x7FFFFFFu;
+                const uint64_t t64 = (k == 6 ? ((uint64_t)tab[F[1] + 1] << 32) : 0ull) | tab[F[1]];
+                const std::string vf =
+                    fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k, 1) + ")) & 1ull)";
+                v = f + 1 == G.q ? vf : fmt("(j == %uu ? ", f) + vf + " : " + v + ")";
+            }
+        } else {
+            std::string xs = "0u", offs = "0u";
+            for (uint32_t f = G.q; f-- > 0;) {
+                const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
+                const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27, 1) + ")";
+                xs = f + 1 == G.q ? xf : fmt("(j == %uu ? ", f) + xf + " : " + xs + ")";
+                offs = f + 1 == G.q ? fmt("%uu", F[1]) : fmt("(j == %uu ? %uu : ", f, F[1]) + offs + ")";
+            }
+            o << "const uint32_t x = " << xs << "; const uint32_t to = " << offs << "; ";
+            v = tab_smem ? "((TAB[to + (x >> 5)] >> (x & 31u)) & 1u)"
+                         : "((__ldg(TAB + to + (x >> 5)) >> (x & 31u)) & 1u)";
+        }
+        o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
+    }
+
+    /* merged group: combined choice, input pattern (single-bit or multiply gathers)
+     * and the table entry (an immediate for tables of at most 64 bits) */
+    void emit_merged_group(uint32_t r, uint32_t gi, const pbn_img_group& G) {
+        std::string cexpr;
+        for (uint32_t m = 0; m < G.n_mul; ++m) {
+            const pbn_img_multi& M = multi[G.mul_first + 32 * m];
+            const std::string j = choice_expr(M);
+            if (j.empty()) continue;
+            cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
+        }
+        const GPlan& GP = gp[gi];
+        const uint32_t q = GP.used ? GP.qn : G.q;
+        if (GP.used) {
+            std::string xe;
+            for (const GTerm& t : GP.terms) {
+                std::string term;
+                if (t.magic) {
+                    const MagicTerm& m = t.m;
+                    term = fmt("((((s%u & %s) * %s) >> %u) & %s)", m.row, hex32(m.mask).c_str(), hex32(m.mul).c_str(),
+                               m.shift, hex32((1u << m.width) - 1u).c_str());
+                    if (t.off) term = "(" + term + fmt(" << %u)", t.off);
+                } else {
+                    term = gather(t.row, t.bit, t.off);
+                }
+                xe += (xe.empty() ? "" : " | ") + term;
+            }
+            o << "const uint32_t x = " << xe << "; ";
+        } else {
+            o << "const uint32_t x = " << pattern(G.in_chunk, q, 32) << "; ";
+        }
+        if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
+        else o << "const uint32_t e = x; ";
+        const uint32_t l2w = G.l2w;
+        const uint32_t ebits = 1u << l2w;
+        const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
+        /* size of this group's table in words: up to the next table's offset, or the end */
+        auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
+        const uint32_t toff = GP.used ? GP.tab_off : G.tab_off;
+        const uint32_t tab_words = GP.used ? GP.tab_words
+                                           : (nx == tab_starts.end() ? (H.off_ret - H.off_tables) / 4 : *nx) - G.tab_off;
+        const uint32_t* tabv = magic ? tabm.data() : tab;
+        std::string v;
+        if (tab_words == 1) {
+            v = fmt("((%s >> (e << %u)) & %s)", hex32(tabv[toff]).c_str(), l2w, hex32(emask).c_str());
+        } else if (tab_words == 2) {
+            const uint64_t t64 = ((uint64_t)tabv[toff + 1] << 32) | tabv[toff];
+            v = fmt("((uint32_t)(0x%016llxull >> (e << %u)) & %s)", (unsigned long long)t64, l2w, hex32(emask).c_str());
+        } else if (tab_smem) {
+            v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", toff, l2w, l2w, hex32(emask).c_str());
+        } else {
+            v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", toff, l2w, l2w,
+                    hex32(emask).c_str());
+        }
+        o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
+    }
+
     /* merged-table evaluation of every group from s and the SEL uniforms U: n<row>.
      * Wide plans take the groups in the order of the last SEL block they read and
      * draw each block just before its first use. */
-    auto emit_eval = [&]() {
+    void emit_eval() {
         for (uint32_t r = 0; r < H.W32; ++r) o << "        uint32_t n" << r << " = 0;\n";
         const uint32_t* wgroups = V.at<uint32_t>(H.off_wgroups);
         std::vector<std::pair<uint32_t, uint32_t>> order; /* (row, group) */
         for (uint32_t r = 0; r < H.W32; ++r)
             for (uint32_t i = words[r].x; i < words[r].x + words[r].y; ++i) order.push_back({r, wgroups[i]});
         std::vector<uint8_t> drawn(H.n_sel, 0);
-        auto blocks_of = [&](uint32_t gi) {
-            std::vector<uint32_t> b;
-            const pbn_img_group& G = groups[gi];
-            for (uint32_t m = 0; m < G.n_mul; ++m) b.push_back(multi[G.mul_first + 32 * m].ch_off / 4);
-            return b;
-        };
         if (wide) {
             std::stable_sort(order.begin(), order.end(), [&](const std::pair<uint32_t, uint32_t>& x,
                                                              const std::pair<uint32_t, uint32_t>& y) {
@@ -507,112 +655,24 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             });
         }
         for (const auto& ri : order) {
-            {
-                const uint32_t r = ri.first;
-                const uint32_t gi = ri.second;
-                const pbn_img_group& G = groups[gi];
-                if (wide)
-                    for (uint32_t b : blocks_of(gi))
-                        if (!drawn[b]) {
-                            drawn[b] = 1;
-                            o << "        const uint4 U" << b << " = pbn_philox_draw(P, ps, "
-                              << hex32((PBN_DOM_SEL << 28) | selblk[b]) << ");\n";
-                        }
-                o << "        { ";
-                if (G.l2w == PBN_IMG_SPLIT) {
-                    /* split node: every function's pattern is a few register operations;
-                     * the selected one's table bit is kept (immediates when every table
-                     * fits in 64 bits, else one lookup at the selected table) */
-                    std::string j = choice_expr(multi[G.mul_first]);
-                    if (j.empty()) j = "0u";
-                    o << "const uint32_t j = " << j << "; ";
-                    bool small = true;
-                    for (uint32_t f = 0; f < G.q; ++f) small = small && (subs[2 * (G.tab_off + 32 * f)] >> 27) <= 6;
-                    std::string v = "0u";
-                    if (small) {
-                        for (uint32_t f = G.q; f-- > 0;) {
-                            const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
-                            const uint32_t k = F[0] >> 27, ch = F[0] & 0x7FFFFFFu;
-                            const uint64_t t64 = (k == 6 ? ((uint64_t)tab[F[1] + 1] << 32) : 0ull) | tab[F[1]];
-                            const std::string vf =
-                                fmt("(uint32_t)((0x%016llxull >> (", (unsigned long long)t64) + pattern(ch, k, 1) + ")) & 1ull)";
-                            v = f + 1 == G.q ? vf : fmt("(j == %uu ? ", f) + vf + " : " + v + ")";
-                        }
-                    } else {
-                        std::string xs = "0u", offs = "0u";
-                        for (uint32_t f = G.q; f-- > 0;) {
-                            const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
-                            const std::string xf = "(" + pattern(F[0] & 0x7FFFFFFu, F[0] >> 27, 1) + ")";
-                            xs = f + 1 == G.q ? xf : fmt("(j == %uu ? ", f) + xf + " : " + xs + ")";
-                            offs = f + 1 == G.q ? fmt("%uu", F[1]) : fmt("(j == %uu ? %uu : ", f, F[1]) + offs + ")";
-                        }
-                        o << "const uint32_t x = " << xs << "; const uint32_t to = " << offs << "; ";
-                        v = tab_smem ? "((TAB[to + (x >> 5)] >> (x & 31u)) & 1u)"
-                                     : "((__ldg(TAB + to + (x >> 5)) >> (x & 31u)) & 1u)";
+            const uint32_t r = ri.first;
+            const uint32_t gi = ri.second;
+            const pbn_img_group& G = groups[gi];
+            if (wide)
+                for (uint32_t b : blocks_of(gi))
+                    if (!drawn[b]) {
+                        drawn[b] = 1;
+                        o << "        const uint4 U" << b << " = pbn_philox_draw(P, ps, "
+                          << hex32((PBN_DOM_SEL << 28) | selblk[b]) << ");\n";
                     }
-                    o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
-                    continue;
-                }
-                /* combined choice */
-                std::string cexpr;
-                for (uint32_t m = 0; m < G.n_mul; ++m) {
-                    const pbn_img_multi& M = multi[G.mul_first + 32 * m];
-                    const std::string j = choice_expr(M);
-                    if (j.empty()) continue;
-                    cexpr += (cexpr.empty() ? "" : " + ") + (M.radix == 1 ? "(" + j + ")" : fmt("%uu * (", M.radix) + j + ")");
-                }
-                /* input pattern: single-bit gathers, or multiply-gather fields */
-                const GPlan& GP = gp[gi];
-                const uint32_t q = GP.used ? GP.qn : G.q;
-                if (GP.used) {
-                    std::string xe;
-                    for (const GTerm& t : GP.terms) {
-                        std::string term;
-                        if (t.magic) {
-                            const MagicTerm& m = t.m;
-                            term = fmt("((((s%u & %s) * %s) >> %u) & %s)", m.row, hex32(m.mask).c_str(), hex32(m.mul).c_str(),
-                                       m.shift, hex32((1u << m.width) - 1u).c_str());
-                            if (t.off) term = "(" + term + fmt(" << %u)", t.off);
-                        } else {
-                            term = gather(t.row, t.bit, t.off);
-                        }
-                        xe += (xe.empty() ? "" : " | ") + term;
-                    }
-                    o << "const uint32_t x = " << xe << "; ";
-                } else {
-                    o << "const uint32_t x = " << pattern(G.in_chunk, q, 32) << "; ";
-                }
-                if (!cexpr.empty()) o << "const uint32_t e = ((" << cexpr << ") << " << q << ") | x; ";
-                else o << "const uint32_t e = x; ";
-                /* table entry */
-                const uint32_t l2w = G.l2w;
-                const uint32_t ebits = 1u << l2w;
-                const uint32_t emask = ebits >= 32 ? 0xFFFFFFFFu : ((1u << ebits) - 1u);
-                /* size of this group's table in words: up to the next table's offset, or the end */
-                auto nx = std::upper_bound(tab_starts.begin(), tab_starts.end(), G.tab_off);
-                const uint32_t toff = GP.used ? GP.tab_off : G.tab_off;
-                const uint32_t tab_words = GP.used ? GP.tab_words
-                                                   : (nx == tab_starts.end() ? (H.off_ret - H.off_tables) / 4 : *nx) - G.tab_off;
-                const uint32_t* tabv = magic ? tabm.data() : tab;
-                std::string v;
-                if (tab_words == 1) {
-                    v = fmt("((%s >> (e << %u)) & %s)", hex32(tabv[toff]).c_str(), l2w, hex32(emask).c_str());
-                } else if (tab_words == 2) {
-                    const uint64_t t64 = ((uint64_t)tabv[toff + 1] << 32) | tabv[toff];
-                    v = fmt("((uint32_t)(0x%016llxull >> (e << %u)) & %s)", (unsigned long long)t64, l2w, hex32(emask).c_str());
-                } else if (tab_smem) {
-                    v = fmt("((TAB[%uu + ((e << %u) >> 5)] >> ((e << %u) & 31u)) & %s)", toff, l2w, l2w,
-                            hex32(emask).c_str());
-                } else {
-                    v = fmt("((__ldg(TAB + %uu + ((e << %u) >> 5)) >> ((e << %u) & 31u)) & %s)", toff, l2w, l2w,
-                            hex32(emask).c_str());
-                }
-                o << "n" << r << " |= " << v << " << " << (uint32_t)G.shift << "; }\n";
-            }
+            o << "        { ";
+            if (G.l2w == PBN_IMG_SPLIT) emit_split_group(r, G);
+            else emit_merged_group(r, gi, G);
         }
-    };
+    }
+
     /* meta-state counts and the optional trace of the new state */
-    auto emit_counts = [&]() {
+    void emit_counts() {
         o << "      { const uint32_t z = " << z << ";\n"
              "        const uint32_t cv = k >= P.kv0 ? 1u : 0u, cp = k >= P.kp0 ? 1u : 0u;\n"
              "        cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u); zp = z; }\n";
@@ -622,13 +682,13 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             o << "        P.trace[(snap * " << H.W32 / 2 << "u + " << r / 2 << "u) * P.n_traj + lt] = ((uint64_t)s"
               << r + 1 << " << 32) | s" << r << ";\n";
         o << "      }\n";
-    };
+    }
 
-    if (pipelined) {
-        /* Software-pipelined steps: every random draw is independent of the state, so
-         * the SEL blocks and the first perturbation level pairs of step t + 1 are drawn
-         * while step t's groups are evaluated (one block of independent work); the
-         * evaluation always runs and a select keeps s XOR flips in perturbed steps. */
+    /* Software-pipelined steps: every random draw is independent of the state, so
+     * the SEL blocks and the first perturbation level pairs of step t + 1 are drawn
+     * while step t's groups are evaluated (one block of independent work); the
+     * evaluation always runs and a select keeps s XOR flips in perturbed steps. */
+    void emit_pipelined_steps() {
         const uint32_t npeel = std::min<uint32_t>(hmax, 3u);
         o << "    pbn_philox_step ps = pbn_philox_begin(P, traj, P.step_begin);\n";
         emit_sel_draws("    ", "uint4 ", "U", "ps");
@@ -677,7 +737,86 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
         for (uint32_t w = 0; w < H.W && Pv; ++w)
             o << fmt("      ul%u = uln%u; uh%u = uhn%u; pl%u = pln%u; ph%u = phn%u;\n", w, w, w, w, w, w, w, w);
         o << "    }\n";
-    } else {
+    }
+
+    /* geometric sampler: per word pair one block; the common case is one 64-bit
+     * compare per word against G[L-1]; otherwise the perturbed lanes are found one by
+     * one */
+    void emit_geometric_perturbation(const char* ftarget, const char* fop) {
+        const uint64_t* G = V.at<uint64_t>(H.off_geo);
+        for (uint32_t wp = 0; 2 * wp < H.W; ++wp) {
+            o << "      { const uint4 g0 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << ");\n";
+            for (uint32_t h2 = 0; h2 < 2 && 2 * wp + h2 < H.W; ++h2) {
+                const uint32_t w = 2 * wp + h2;
+                const uint32_t L = (w == H.W - 1 && (H.n & 63u)) ? (H.n & 63u) : 64u;
+                const char* lo = h2 ? "z" : "x";
+                const char* hi = h2 ? "w" : "y";
+                o << fmt("        { uint64_t U = ((uint64_t)g0.%s << 32) | g0.%s;\n", hi, lo)
+                  << fmt("          if (U < 0x%016llxull) {\n", (unsigned long long)G[L - 1])
+                  << "            uint32_t pl = 0, ph = 0, pos = 0, j = 0;\n"
+                  << "            for (;;) {\n"
+                  << fmt("              if (U >= GEO_T[%uu - pos - 1]) break;\n", L)
+                  << "              uint32_t k = 0;\n              while (U >= GEO_T[k]) ++k;\n"
+                  << "              const uint32_t b = pos + k;\n"
+                  << "              if (b < 32) pl |= 1u << b; else ph |= 1u << (b - 32);\n"
+                  << fmt("              pos = b + 1;\n              if (pos >= %uu) break;\n", L)
+                  << "              ++j;\n"
+                  << "              const uint4 x = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << " | j);\n"
+                  << fmt("              U = ((uint64_t)x.%s << 32) | x.%s;\n", hi, lo)
+                  << "            }\n            any = 1u;\n";
+                emit_flips(w, "pl", "ph", ftarget, fop);
+                o << "          }\n        }\n";
+            }
+            o << "      }\n";
+        }
+    }
+
+    /* one word at a time, every level pair unrolled with its P bits as constants */
+    void emit_unrolled_perturbation(const char* ftarget, const char* fop) {
+        for (uint32_t w = 0; w < H.W; ++w) {
+            const uint64_t valid = valid_of(w);
+            o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
+              << ", pl = 0, ph = 0;\n";
+            for (uint32_t h = 0; h < hmax; ++h) {
+                o << "        if (ul | uh) ";
+                emit_level("", w, h, "", "ps");
+            }
+            o << "        if (pl | ph) {\n          any = 1u;\n";
+            emit_flips(w, "pl", "ph", ftarget, fop);
+            o << "        }\n      }\n";
+        }
+    }
+
+    /* words in pairs: one rolled loop draws both words' level pairs, two independent
+     * Philox chains per iteration; interleaved: the first level pairs (needed by a
+     * 64-lane word with probability ~1) are straight-line */
+    void emit_paired_perturbation(const char* ftarget, const char* fop) {
+        const uint32_t npeel = interleave ? std::min<uint32_t>(hmax, 3u) : 0u;
+        for (uint32_t w = 0; w < H.W; w += 2) {
+            const bool two = w + 1 < H.W;
+            const uint64_t v0 = valid_of(w), v1 = two ? valid_of(w + 1) : 0ull;
+            o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
+              << ", pl0 = 0, ph0 = 0";
+            if (two) o << ", ul1 = " << hex32((uint32_t)v1) << ", uh1 = " << hex32((uint32_t)(v1 >> 32)) << ", pl1 = 0, ph1 = 0";
+            o << ";\n";
+            for (uint32_t h = 0; h < npeel; ++h)
+                for (uint32_t k2 = 0; k2 < (two ? 2u : 1u); ++k2) emit_level("        ", w + k2, h, std::to_string(k2), "ps");
+            emit_level_loop(w, two, npeel, "0", "1", "ps");
+            o << "        if (pl0 | ph0) {\n          any = 1u;\n";
+            emit_flips(w, "pl0", "ph0", ftarget, fop);
+            o << "        }\n";
+            if (two) {
+                o << "        if (pl1 | ph1) {\n          any = 1u;\n";
+                emit_flips(w + 1, "pl1", "ph1", ftarget, fop);
+                o << "        }\n";
+            }
+            o << "      }\n";
+        }
+    }
+
+    /* the step loop: perturbation (P's levels compiled in), then, in a non-perturbed
+     * step (every step with node-wise semantics), selection and evaluation; counts */
+    void emit_steps() {
         o << "    for (uint32_t k = 0; k < P.n_steps; ++k) {\n"
              "      const uint64_t t = P.step_begin + k;\n"
              "      const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
@@ -693,77 +832,9 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
          * needed in every non-perturbed step), so that their Philox chains and the first
          * perturbation levels form one block of independent work */
         if (interleave) emit_sel_draws("      ", "const uint4 ", "U", "ps");
-        /* 1. perturbation: the levels of P compiled in */
-        if (Pv && geometric) {
-            /* per word pair one block; the common case is one 64-bit compare per word
-             * against G[L-1]; otherwise the perturbed lanes are found one by one */
-            const uint64_t* G = V.at<uint64_t>(H.off_geo);
-            for (uint32_t wp = 0; 2 * wp < H.W; ++wp) {
-                o << "      { const uint4 g0 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << ");\n";
-                for (uint32_t h2 = 0; h2 < 2 && 2 * wp + h2 < H.W; ++h2) {
-                    const uint32_t w = 2 * wp + h2;
-                    const uint32_t L = (w == H.W - 1 && (H.n & 63u)) ? (H.n & 63u) : 64u;
-                    const char* lo = h2 ? "z" : "x";
-                    const char* hi = h2 ? "w" : "y";
-                    o << fmt("        { uint64_t U = ((uint64_t)g0.%s << 32) | g0.%s;\n", hi, lo)
-                      << fmt("          if (U < 0x%016llxull) {\n", (unsigned long long)G[L - 1])
-                      << "            uint32_t pl = 0, ph = 0, pos = 0, j = 0;\n"
-                      << "            for (;;) {\n"
-                      << fmt("              if (U >= GEO_T[%uu - pos - 1]) break;\n", L)
-                      << "              uint32_t k = 0;\n              while (U >= GEO_T[k]) ++k;\n"
-                      << "              const uint32_t b = pos + k;\n"
-                      << "              if (b < 32) pl |= 1u << b; else ph |= 1u << (b - 32);\n"
-                      << fmt("              pos = b + 1;\n              if (pos >= %uu) break;\n", L)
-                      << "              ++j;\n"
-                      << "              const uint4 x = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << " | j);\n"
-                      << fmt("              U = ((uint64_t)x.%s << 32) | x.%s;\n", hi, lo)
-                      << "            }\n            any = 1u;\n";
-                    emit_flips(w, "pl", "ph", ftarget, fop);
-                    o << "          }\n        }\n";
-                }
-                o << "      }\n";
-            }
-        } else if (Pv && (flags & PBN_COMPILE_PERT_UNROLLED)) {
-            /* one word at a time, every level pair unrolled with its P bits as constants */
-            for (uint32_t w = 0; w < H.W; ++w) {
-                const uint64_t valid = valid_of(w);
-                o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
-                  << ", pl = 0, ph = 0;\n";
-                for (uint32_t h = 0; h < hmax; ++h) {
-                    o << "        if (ul | uh) ";
-                    emit_level("", w, h, "", "ps");
-                }
-                o << "        if (pl | ph) {\n          any = 1u;\n";
-                emit_flips(w, "pl", "ph", ftarget, fop);
-                o << "        }\n      }\n";
-            }
-        } else if (Pv) {
-            /* words in pairs: one rolled loop draws both words' level pairs, two
-             * independent Philox chains per iteration; interleaved: the first level
-             * pairs (needed by a 64-lane word with probability ~1) are straight-line */
-            const uint32_t npeel = interleave ? std::min<uint32_t>(hmax, 3u) : 0u;
-            for (uint32_t w = 0; w < H.W; w += 2) {
-                const bool two = w + 1 < H.W;
-                const uint64_t v0 = valid_of(w), v1 = two ? valid_of(w + 1) : 0ull;
-                o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
-                  << ", pl0 = 0, ph0 = 0";
-                if (two) o << ", ul1 = " << hex32((uint32_t)v1) << ", uh1 = " << hex32((uint32_t)(v1 >> 32)) << ", pl1 = 0, ph1 = 0";
-                o << ";\n";
-                for (uint32_t h = 0; h < npeel; ++h)
-                    for (uint32_t k2 = 0; k2 < (two ? 2u : 1u); ++k2) emit_level("        ", w + k2, h, std::to_string(k2), "ps");
-                emit_level_loop(w, two, npeel, "0", "1", "ps");
-                o << "        if (pl0 | ph0) {\n          any = 1u;\n";
-                emit_flips(w, "pl0", "ph0", ftarget, fop);
-                o << "        }\n";
-                if (two) {
-                    o << "        if (pl1 | ph1) {\n          any = 1u;\n";
-                    emit_flips(w + 1, "pl1", "ph1", ftarget, fop);
-                    o << "        }\n";
-                }
-                o << "      }\n";
-            }
-        }
-        /* 2. selection draws and merged-table evaluation */
+        if (Pv && geometric) emit_geometric_perturbation(ftarget, fop);
+        else if (Pv && (flags_ & PBN_COMPILE_PERT_UNROLLED)) emit_unrolled_perturbation(ftarget, fop);
+        else if (Pv) emit_paired_perturbation(ftarget, fop);
         o << (nodewise ? "      {\n" : "      if (!any) {\n");
         if (!interleave && !wide) emit_sel_draws("        ", "const uint4 ", "U", "ps");
         emit_eval();
@@ -772,28 +843,33 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
             else o << "        s" << r << " = n" << r << ";\n";
         }
         o << "      }\n";
-        /* 3. counts */
         emit_counts();
         o << "    }\n";
     }
-    /* epilogue */
-    for (uint32_t r = 0; r < H.W32; r += 2)
-        o << "    P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt] = ((uint64_t)s" << r + 1 << " << 32) | s" << r << ";\n";
-    o << "    if (P.counts) {\n"
-         "      const uint64_t nt = P.n_traj;\n"
-         "      P.counts[lt] += cV; P.counts[nt + lt] += P.pairs - c01 - c10 - c11;\n"
-         "      P.counts[2 * nt + lt] += c01; P.counts[3 * nt + lt] += c10; P.counts[4 * nt + lt] += c11;\n"
-         "    }\n  }\n";
-    o << "  if (P.pooled) {\n"
-         "    uint64_t v[5] = {active ? cV : 0u, active ? (uint64_t)(P.pairs - c01 - c10 - c11) : 0u,\n"
-         "                     active ? c01 : 0u, active ? c10 : 0u, active ? c11 : 0u};\n"
-         "#pragma unroll\n    for (int i = 0; i < 5; ++i) {\n"
-         "#pragma unroll\n      for (int d = 16; d > 0; d >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], d);\n    }\n"
-         "    if ((threadIdx.x & 31u) == 0) {\n"
-         "      for (int i = 0; i < 5; ++i) if (v[i]) atomicAdd(P.pooled + i, (unsigned long long)v[i]);\n    }\n  }\n";
-    o << "}\n";
-    out->src = o.str();
-    return true;
+
+    /* the state and counts written back, pooled counts reduced per warp */
+    void emit_epilogue() {
+        for (uint32_t r = 0; r < H.W32; r += 2)
+            o << "    P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt] = ((uint64_t)s" << r + 1 << " << 32) | s" << r << ";\n";
+        o << "    if (P.counts) {\n"
+             "      const uint64_t nt = P.n_traj;\n"
+             "      P.counts[lt] += cV; P.counts[nt + lt] += P.pairs - c01 - c10 - c11;\n"
+             "      P.counts[2 * nt + lt] += c01; P.counts[3 * nt + lt] += c10; P.counts[4 * nt + lt] += c11;\n"
+             "    }\n  }\n";
+        o << "  if (P.pooled) {\n"
+             "    uint64_t v[5] = {active ? cV : 0u, active ? (uint64_t)(P.pairs - c01 - c10 - c11) : 0u,\n"
+             "                     active ? c01 : 0u, active ? c10 : 0u, active ? c11 : 0u};\n"
+             "#pragma unroll\n    for (int i = 0; i < 5; ++i) {\n"
+             "#pragma unroll\n      for (int d = 16; d > 0; d >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], d);\n    }\n"
+             "    if ((threadIdx.x & 31u) == 0) {\n"
+             "      for (int i = 0; i < 5; ++i) if (v[i]) atomicAdd(P.pooled + i, (unsigned long long)v[i]);\n    }\n  }\n";
+        o << "}\n";
+    }
+};
+
+bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string* why) {
+    KernelSource ks(plan, flags);
+    return ks.generate(out, why);
 }
 
 }  // namespace
