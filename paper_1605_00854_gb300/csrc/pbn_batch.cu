@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -287,143 +288,149 @@ struct pbn_batch {
     mutable int sms = 0;
 };
 
+namespace {
+
+/* Meta-state rows of network i: per 32-bit state row holding a meta node, the mask
+ * of those nodes and the values they must take. */
+int describe_meta(const pbn_batch_net& a, uint32_t i, NetDesc* D) {
+    using pbn::fail;
+    const pbn_plan* plan = a.plan;
+    if (a.n_meta < 1 || a.n_meta > 1024 || !a.meta_ids)
+        return fail(PBN_EINVAL, "pbn_batch_create: network %u needs 1..1024 meta nodes", i);
+    for (uint32_t m = 0; m < a.n_meta; ++m) {
+        const uint32_t id = a.meta_ids[m];
+        if (id >= plan->hdr.n || plan->pos[id] == UINT32_MAX)
+            return fail(PBN_EINVAL, "pbn_batch_create: network %u meta node %u is not retained", i, id);
+        const uint32_t row = plan->pos[id] >> 5, bit = plan->pos[id] & 31u;
+        const uint32_t val = a.meta_vals ? (a.meta_vals[m] ? 1u : 0u) : 1u;
+        uint32_t k = 0;
+        while (k < D->n_meta_rows && D->meta_row[k] != row) ++k;
+        if (k == D->n_meta_rows) {
+            if (k == kMetaRows) return fail(PBN_EINVAL, "pbn_batch_create: network %u meta nodes span > 16 words", i);
+            D->meta_row[k] = row;
+            D->n_meta_rows++;
+        }
+        D->meta_mask[k] |= 1u << bit;
+        D->meta_val[k] |= val << bit;
+    }
+    return PBN_OK;
+}
+
+/* Descriptor of network i for a CTA of T threads: buffers, counting window, meta
+ * rows, image section offsets, and the staging mode with its trajectory slots per
+ * work item and lanes per trajectory. */
+int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D) {
+    using pbn::fail;
+    const pbn_plan* plan = a.plan;
+    if (!plan || !a.d_image || ((uintptr_t)a.d_image & 15u) || !a.d_state)
+        return fail(PBN_EINVAL, "pbn_batch_create: network %u lacks a plan, image or state", i);
+    if (a.n_traj == 0 || a.n_traj >= (1ull << 31) || a.traj_begin + a.n_traj > (1ull << 48))
+        return fail(PBN_EINVAL, "pbn_batch_create: network %u trajectory range", i);
+    if (a.init != PBN_INIT_KEYED && a.init != PBN_INIT_STATE)
+        return fail(PBN_EINVAL, "pbn_batch_create: network %u init mode", i);
+    if (a.init == PBN_INIT_KEYED && a.step_begin != 0)
+        return fail(PBN_EINVAL, "pbn_batch_create: network %u keyed init needs step_begin 0", i);
+    const pbn_img_header& H = plan->hdr;
+    memset(D, 0, sizeof(*D));
+    const int rc = describe_meta(a, i, D);
+    if (rc != PBN_OK) return rc;
+    D->image = static_cast<const uint8_t*>(a.d_image);
+    D->state = static_cast<uint64_t*>(a.d_state);
+    D->counts = static_cast<uint64_t*>(a.d_counts);
+    D->pooled = static_cast<unsigned long long*>(a.d_pooled);
+    D->traj_begin = a.traj_begin;
+    D->step_begin = a.step_begin;
+    D->count_from = a.count_from;
+    D->seed = a.seed;
+    D->n_traj = (uint32_t)a.n_traj;
+    D->init = a.init;
+    D->image_bytes = H.image_bytes;
+    D->hmax = H.P ? (31u - (uint32_t)__builtin_ctz(H.P)) / 2u + 1u : 0u;
+    D->n = H.n;
+    D->W = H.W;
+    D->W32 = H.W32;
+    D->n_sel = H.n_sel;
+    D->P = H.P;
+    D->off_words = H.off_words;
+    D->off_groups = H.off_groups;
+    D->off_multi = H.off_multi;
+    D->off_selslot = H.off_selslot;
+    D->off_gorder = H.off_gorder;
+    D->off_wgroups = H.off_wgroups;
+    D->off_subs = H.off_subs;
+    D->per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
+    D->sampler = H.sampler;
+    D->off_geo = H.off_geo;
+    {
+        const uint64_t* G = reinterpret_cast<const uint64_t*>(plan->image.data() + H.off_geo);
+        const uint32_t nl = H.n & 63u;
+        D->geo_full = G[63];
+        D->geo_last = G[(nl ? nl : 64u) - 1];
+    }
+    D->n_groups = H.n_groups;
+    D->off_thr = H.off_thr;
+    D->off_inputs = H.off_inputs;
+    D->off_selblk = H.off_selblk;
+    D->off_ret = H.off_ret;
+    D->off_pos = H.off_pos;
+    D->off_tables = H.off_tables;
+    /* staging mode and trajectories per work item under the per-CTA cap:
+     * specs and tables staged, specs only, or nothing (read through L1) */
+    const uint64_t per = plan->per_traj_smem;
+    auto fit = [&](uint64_t staged) -> uint32_t {
+        const uint64_t off = (staged + 127u) & ~(uint64_t)127u;
+        if (off + per * 32 > kSmemCap) return 0u;
+        uint64_t nt = (kSmemCap - off) / per;
+        nt = std::min<uint64_t>(T, nt & ~(uint64_t)31);
+        return (uint32_t)nt;
+    };
+    const uint32_t nt_all = H.tables_in_smem ? fit(H.off_ret) : 0u;
+    const uint32_t nt_specs = fit(H.off_tables);
+    const uint32_t nt_none = fit(0);
+    if (nt_all >= std::min<uint32_t>(T, 256u) || (nt_all && nt_all >= nt_specs)) {
+        D->specs_in_smem = 1; D->tables_in_smem = 1; D->stage_bytes = H.off_ret; D->nt = nt_all;
+    } else if (nt_specs) {
+        D->specs_in_smem = 1; D->tables_in_smem = 0; D->stage_bytes = H.off_tables; D->nt = nt_specs;
+    } else if (nt_none) {
+        D->specs_in_smem = 0; D->tables_in_smem = 0; D->stage_bytes = 0; D->nt = nt_none;
+    } else {
+        return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per trajectory", i,
+                    (unsigned long long)per);
+    }
+    D->smem_state_off = D->stage_bytes ? ((D->stage_bytes + 127u) & ~127u) : 0u;
+    /* lanes per trajectory: fill the CTA's threads when few trajectories fit (wide
+     * states); lane groups evaluate groups in shape order.  States of 32 words or more
+     * take up to a warp per trajectory (two words per lane: 32 lanes ran a 62-word
+     * state 1.66x faster than 8), smaller ones up to 8 lanes with at least 8 words each */
+    D->lg = 1;
+    if (D->specs_in_smem) {
+        const bool wide_state = D->W32 >= 32;
+        const uint32_t lg_max = wide_state ? 32u : 8u, words_per_lane = wide_state ? 2u : 8u;
+        while (D->lg < lg_max && D->nt * D->lg * 2 <= T && D->W32 >= words_per_lane * D->lg) D->lg *= 2;
+    }
+    return PBN_OK;
+}
+
+}  // namespace
+
 extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out) {
     using pbn::fail;
     if (!nets || !out || n_nets == 0) return fail(PBN_EINVAL, "pbn_batch_create: need networks");
     *out = nullptr;
     try {
-        pbn_batch* B = new pbn_batch();
+        std::unique_ptr<pbn_batch> B(new pbn_batch());
         const uint32_t T = B->threads;
         uint64_t smem_max = 0;
         uint32_t max_lanes = 1;
         std::vector<double> cost_per_traj(n_nets);
         for (uint32_t i = 0; i < n_nets; ++i) {
             const pbn_batch_net& a = nets[i];
-            const pbn_plan* plan = a.plan;
-            if (!plan || !a.d_image || ((uintptr_t)a.d_image & 15u) || !a.d_state) {
-                delete B;
-                return fail(PBN_EINVAL, "pbn_batch_create: network %u lacks a plan, image or state", i);
-            }
-            if (a.n_traj == 0 || a.n_traj >= (1ull << 31) || a.traj_begin + a.n_traj > (1ull << 48)) {
-                delete B;
-                return fail(PBN_EINVAL, "pbn_batch_create: network %u trajectory range", i);
-            }
-            if (a.init != PBN_INIT_KEYED && a.init != PBN_INIT_STATE) {
-                delete B;
-                return fail(PBN_EINVAL, "pbn_batch_create: network %u init mode", i);
-            }
-            if (a.init == PBN_INIT_KEYED && a.step_begin != 0) {
-                delete B;
-                return fail(PBN_EINVAL, "pbn_batch_create: network %u keyed init needs step_begin 0", i);
-            }
-            const pbn_img_header& H = plan->hdr;
             NetDesc D;
-            memset(&D, 0, sizeof(D));
-            if (a.n_meta < 1 || a.n_meta > 1024 || !a.meta_ids) {
-                delete B;
-                return fail(PBN_EINVAL, "pbn_batch_create: network %u needs 1..1024 meta nodes", i);
-            }
-            for (uint32_t m = 0; m < a.n_meta; ++m) {
-                const uint32_t id = a.meta_ids[m];
-                if (id >= H.n || plan->pos[id] == UINT32_MAX) {
-                    delete B;
-                    return fail(PBN_EINVAL, "pbn_batch_create: network %u meta node %u is not retained", i, id);
-                }
-                const uint32_t row = plan->pos[id] >> 5, bit = plan->pos[id] & 31u;
-                const uint32_t val = a.meta_vals ? (a.meta_vals[m] ? 1u : 0u) : 1u;
-                uint32_t k = 0;
-                while (k < D.n_meta_rows && D.meta_row[k] != row) ++k;
-                if (k == D.n_meta_rows) {
-                    if (k == kMetaRows) {
-                        delete B;
-                        return fail(PBN_EINVAL, "pbn_batch_create: network %u meta nodes span > 16 words", i);
-                    }
-                    D.meta_row[k] = row;
-                    D.n_meta_rows++;
-                }
-                D.meta_mask[k] |= 1u << bit;
-                D.meta_val[k] |= val << bit;
-            }
-            D.image = static_cast<const uint8_t*>(a.d_image);
-            D.state = static_cast<uint64_t*>(a.d_state);
-            D.counts = static_cast<uint64_t*>(a.d_counts);
-            D.pooled = static_cast<unsigned long long*>(a.d_pooled);
-            D.traj_begin = a.traj_begin;
-            D.step_begin = a.step_begin;
-            D.count_from = a.count_from;
-            D.seed = a.seed;
-            D.n_traj = (uint32_t)a.n_traj;
-            D.init = a.init;
-            D.image_bytes = H.image_bytes;
-            D.hmax = H.P ? (31u - (uint32_t)__builtin_ctz(H.P)) / 2u + 1u : 0u;
-            D.n = H.n;
-            D.W = H.W;
-            D.W32 = H.W32;
-            D.n_sel = H.n_sel;
-            D.P = H.P;
-            D.off_words = H.off_words;
-            D.off_groups = H.off_groups;
-            D.off_multi = H.off_multi;
-            D.off_selslot = H.off_selslot;
-            D.off_gorder = H.off_gorder;
-            D.off_wgroups = H.off_wgroups;
-            D.off_subs = H.off_subs;
-            D.per_node = H.semantics == PBN_SEM_NODEWISE ? 1u : 0u;
-            D.sampler = H.sampler;
-            D.off_geo = H.off_geo;
-            {
-                const uint64_t* G = reinterpret_cast<const uint64_t*>(plan->image.data() + H.off_geo);
-                const uint32_t nl = H.n & 63u;
-                D.geo_full = G[63];
-                D.geo_last = G[(nl ? nl : 64u) - 1];
-            }
-            D.n_groups = H.n_groups;
-            D.off_thr = H.off_thr;
-            D.off_inputs = H.off_inputs;
-            D.off_selblk = H.off_selblk;
-            D.off_ret = H.off_ret;
-            D.off_pos = H.off_pos;
-            D.off_tables = H.off_tables;
-            /* staging mode and trajectories per work item under the per-CTA cap:
-             * specs and tables staged, specs only, or nothing (read through L1) */
-            const uint64_t per = plan->per_traj_smem;
-            auto fit = [&](uint64_t staged) -> uint32_t {
-                const uint64_t off = (staged + 127u) & ~(uint64_t)127u;
-                if (off + per * 32 > kSmemCap) return 0u;
-                uint64_t nt = (kSmemCap - off) / per;
-                nt = std::min<uint64_t>(T, nt & ~(uint64_t)31);
-                return (uint32_t)nt;
-            };
-            const uint32_t nt_all = H.tables_in_smem ? fit(H.off_ret) : 0u;
-            const uint32_t nt_specs = fit(H.off_tables);
-            const uint32_t nt_none = fit(0);
-            if (nt_all >= std::min<uint32_t>(T, 256u) || (nt_all && nt_all >= nt_specs)) {
-                D.specs_in_smem = 1; D.tables_in_smem = 1; D.stage_bytes = H.off_ret; D.nt = nt_all;
-            } else if (nt_specs) {
-                D.specs_in_smem = 1; D.tables_in_smem = 0; D.stage_bytes = H.off_tables; D.nt = nt_specs;
-            } else if (nt_none) {
-                D.specs_in_smem = 0; D.tables_in_smem = 0; D.stage_bytes = 0; D.nt = nt_none;
-            } else {
-                delete B;
-                return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per trajectory", i,
-                            (unsigned long long)per);
-            }
-            D.smem_state_off = D.stage_bytes ? ((D.stage_bytes + 127u) & ~127u) : 0u;
-            /* lanes per trajectory: fill the CTA's threads when few trajectories fit
-             * (wide states); lane groups evaluate groups in shape order.  States of 32
-             * words or more take up to a warp per trajectory (two words per lane:
-             * 32 lanes ran a 62-word state 1.66x faster than 8), smaller ones up to 8
-             * lanes with at least 8 words each */
-            D.lg = 1;
-            if (D.specs_in_smem) {
-                const bool wide_state = D.W32 >= 32;
-                const uint32_t lg_max = wide_state ? 32u : 8u, words_per_lane = wide_state ? 2u : 8u;
-                while (D.lg < lg_max && D.nt * D.lg * 2 <= T && D.W32 >= words_per_lane * D.lg) D.lg *= 2;
-            }
+            const int rc = describe_network(a, i, T, &D);
+            if (rc != PBN_OK) return rc;
             max_lanes = std::max(max_lanes, D.lg);
-            const uint64_t need = D.smem_state_off + per * D.nt;
-            smem_max = std::max(smem_max, need);
-            cost_per_traj[i] = plan->info.ops_per_step;
+            smem_max = std::max<uint64_t>(smem_max, D.smem_state_off + (uint64_t)a.plan->per_traj_smem * D.nt);
+            cost_per_traj[i] = a.plan->info.ops_per_step;
             B->nets.push_back(D);
             for (uint64_t t0 = 0; t0 < a.n_traj; t0 += D.nt) {
                 WorkItem w{i, (uint32_t)t0, (uint32_t)std::min<uint64_t>(D.nt, a.n_traj - t0), 0u};
@@ -447,7 +454,7 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
         memcpy(B->image.data(), B->nets.data(), nb);
         memcpy(B->image.data() + nb, B->items.data(), ib);
         B->info.desc_bytes = B->image.size();
-        *out = B;
+        *out = B.release();
         return PBN_OK;
     } catch (const std::bad_alloc&) {
         return fail(PBN_ENOMEM, "pbn_batch_create: out of memory");
