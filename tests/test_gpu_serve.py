@@ -2,7 +2,6 @@
 same alone and in a mix (keyed draws, per-query chunking), admission under a memory
 cap changes nothing, and the estimate meets the exact stationary probability within
 the requested precision."""
-import math
 
 import numpy as np
 import pytest

@@ -1,6 +1,5 @@
 """CPU tests of the library's host side: the C ABI, parsing, Definition 1 reduction,
 grouping (Eq. 2, Algorithms 3-4), merged tables, thresholds and the estimator."""
-import itertools
 import math
 import os
 import re

@@ -15,7 +15,7 @@ from fractions import Fraction
 import numpy as np
 import pytest
 
-from conftest import golden, ROOT
+from conftest import golden
 
 MASK32 = 0xFFFFFFFF
 

@@ -7,7 +7,6 @@ use this entry point: its work-queue scratch is a small static array inside the
 library.  Its results must equal those of pbn_batch_run (caller-provided scratch)
 exactly, on consecutive calls that reuse the array.  This file is collected last so
 that a stop-at-first-failure run has already run every other test."""
-import ctypes
 
 import numpy as np
 import pytest
