@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -294,24 +295,18 @@ namespace {
  * of those nodes and the values they must take. */
 int describe_meta(const pbn_batch_net& a, uint32_t i, NetDesc* D) {
     using pbn::fail;
-    const pbn_plan* plan = a.plan;
     if (a.n_meta < 1 || a.n_meta > 1024 || !a.meta_ids)
         return fail(PBN_EINVAL, "pbn_batch_create: network %u needs 1..1024 meta nodes", i);
-    for (uint32_t m = 0; m < a.n_meta; ++m) {
-        const uint32_t id = a.meta_ids[m];
-        if (id >= plan->hdr.n || plan->pos[id] == UINT32_MAX)
-            return fail(PBN_EINVAL, "pbn_batch_create: network %u meta node %u is not retained", i, id);
-        const uint32_t row = plan->pos[id] >> 5, bit = plan->pos[id] & 31u;
-        const uint32_t val = a.meta_vals ? (a.meta_vals[m] ? 1u : 0u) : 1u;
-        uint32_t k = 0;
-        while (k < D->n_meta_rows && D->meta_row[k] != row) ++k;
-        if (k == D->n_meta_rows) {
-            if (k == kMetaRows) return fail(PBN_EINVAL, "pbn_batch_create: network %u meta nodes span > 16 words", i);
-            D->meta_row[k] = row;
-            D->n_meta_rows++;
-        }
-        D->meta_mask[k] |= 1u << bit;
-        D->meta_val[k] |= val << bit;
+    char who[64];
+    snprintf(who, sizeof who, "pbn_batch_create: network %u", i);
+    pbn::MetaRows M;
+    const int rc = pbn::meta_rows(a.plan, a.meta_ids, a.meta_vals, a.n_meta, kMetaRows, who, &M);
+    if (rc != PBN_OK) return rc;
+    D->n_meta_rows = M.n_rows;
+    for (uint32_t k = 0; k < M.n_rows; ++k) {
+        D->meta_row[k] = M.row[k];
+        D->meta_mask[k] = M.mask[k];
+        D->meta_val[k] = M.val[k];
     }
     return PBN_OK;
 }

@@ -40,6 +40,33 @@ int fail(int code, const char* fmt, ...) {
 
 /* Node i is perturbed iff its 32-bit draw u < P = floor(p * 2^32); p * 2^32 is exact. */
 uint64_t pert_threshold(double p) { return (uint64_t)std::floor(p * 4294967296.0); }
+
+int meta_rows(const pbn_plan* plan, const uint32_t* ids, const uint8_t* vals, uint32_t n_meta, uint32_t max_rows,
+              const char* who, MetaRows* out) {
+    *out = MetaRows{};
+    if (max_rows > 64) max_rows = 64;
+    for (uint32_t m = 0; m < n_meta; ++m) {
+        const uint32_t id = ids[m];
+        if (id >= plan->hdr.n || plan->pos[id] == UINT32_MAX)
+            return fail(PBN_EINVAL, "%s: meta node %u is not a retained node", who, id);
+        const uint32_t row = plan->pos[id] >> 5, bit = plan->pos[id] & 31u;
+        const uint32_t val = vals ? (vals[m] ? 1u : 0u) : 1u;
+        uint32_t k = 0;
+        while (k < out->n_rows && out->row[k] != row) ++k;
+        if (k == out->n_rows) {
+            if (k == max_rows) return fail(PBN_EINVAL, "%s: meta nodes span more than %u state words", who, max_rows);
+            out->row[k] = row;
+            out->mask[k] = 0;
+            out->val[k] = 0;
+            out->n_rows++;
+        }
+        if (((out->mask[k] >> bit) & 1u) && ((out->val[k] >> bit) & 1u) != val)
+            return fail(PBN_EINVAL, "%s: contradictory values for meta node %u", who, id);
+        out->mask[k] |= 1u << bit;
+        out->val[k] |= val << bit;
+    }
+    return PBN_OK;
+}
 }  // namespace pbn
 
 using pbn::fail;

@@ -43,6 +43,18 @@ struct pbn_jit_params_s;
 namespace pbn {
 int fail(int code, const char* fmt, ...);
 uint64_t pert_threshold(double p);
+
+/* The meta-state as state rows: for each 32-bit row of the plan's state that holds
+ * one of the n_meta nodes, the row index, the mask of those nodes and the values they
+ * must take (vals NULL: all 1).  At most max_rows rows.  Errors (PBN_EINVAL, the
+ * message prefixed by `who`): a node that is not retained, more than max_rows rows,
+ * one node listed with two different values. */
+struct MetaRows {
+    uint32_t n_rows = 0;
+    uint32_t row[64], mask[64], val[64];
+};
+int meta_rows(const pbn_plan* plan, const uint32_t* ids, const uint8_t* vals, uint32_t n_meta, uint32_t max_rows,
+              const char* who, MetaRows* out);
 /* compiled plans (pbn_jit.cpp) */
 pbn_jit_state* jit_state(const pbn_plan* plan);
 void jit_free(pbn_jit_state* J);

@@ -190,24 +190,16 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     SimParams P;
     memset(&P, 0, sizeof(P));
     /* meta-state: mask and value per state row */
-    for (uint32_t m = 0; m < a->n_meta; ++m) {
-        const uint32_t id = a->meta_ids[m];
-        if (id >= H.n || plan->pos[id] == UINT32_MAX)
-            return fail(PBN_EINVAL, "pbn_simulate: meta node %u is not a retained node", id);
-        const uint32_t row = plan->pos[id] >> 5, bit = plan->pos[id] & 31u;
-        const uint32_t val = a->meta_vals ? (a->meta_vals[m] ? 1u : 0u) : 1u;
-        uint32_t k = 0;
-        while (k < P.n_meta_rows && P.meta_row[k] != row) ++k;
-        if (k == P.n_meta_rows) {
-            if (k == kMaxMetaRows) return fail(PBN_EINVAL, "pbn_simulate: meta nodes span more than %d state words", kMaxMetaRows);
-            P.meta_row[k] = row;
-            P.n_meta_rows++;
+    {
+        pbn::MetaRows M;
+        const int rc = pbn::meta_rows(plan, a->meta_ids, a->meta_vals, a->n_meta, kMaxMetaRows, "pbn_simulate", &M);
+        if (rc != PBN_OK) return rc;
+        P.n_meta_rows = M.n_rows;
+        for (uint32_t k = 0; k < M.n_rows; ++k) {
+            P.meta_row[k] = M.row[k];
+            P.meta_mask[k] = M.mask[k];
+            P.meta_val[k] = M.val[k];
         }
-        if ((P.meta_mask[k] >> bit) & 1u) {
-            if (((P.meta_val[k] >> bit) & 1u) != val) return fail(PBN_EINVAL, "pbn_simulate: contradictory meta values");
-        }
-        P.meta_mask[k] |= 1u << bit;
-        P.meta_val[k] |= val << bit;
     }
 
     P.image = static_cast<const uint8_t*>(d_image);

@@ -641,3 +641,48 @@ def test_batch_lane_choice_on_the_host(L):
         assert info.max_lanes == 1
     finally:
         L.pbn_batch_free(h)
+
+
+def test_meta_state_validation_is_shared_by_single_and_batched_launches(L):
+    """pbn_simulate and pbn_batch_create turn the meta nodes into state rows with the
+    same checks, before any device work (fake, never dereferenced buffers): a node
+    listed twice with different values, or a removed node, is refused by both; a node
+    listed twice with the same value is accepted by the batch."""
+    import ctypes
+    text = synth.paper100(seed=2).to_text()
+    red, kept = api.Net.load(text).reduce([0, 1, 2])
+    plan = api.Plan(red)
+    removed = int(next(v for v in range(100) if v not in set(int(x) for x in kept)))
+    fake = 1 << 20
+
+    def sim(ids, vals):
+        a = _lib.SimArgs()
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        a.n_traj, a.n_steps, a.n_meta = 4, 1, len(ids)
+        a.meta_ids, a.meta_vals = ids.ctypes.data, vals.ctypes.data
+        a.d_state = fake
+        rc = L.pbn_simulate(plan._h, ctypes.c_void_p(fake), ctypes.byref(a), None)
+        return rc, L.pbn_last_error_detail().decode()
+
+    def batch(ids, vals):
+        arr = (_lib.BatchNet * 1)()
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        vals = np.ascontiguousarray(vals, dtype=np.uint8)
+        b = arr[0]
+        b.plan, b.d_image, b.seed, b.n_traj = plan._h, fake, 1, 4
+        b.n_meta, b.meta_ids, b.meta_vals = len(ids), ids.ctypes.data, vals.ctypes.data
+        b.d_state, b.d_counts, b.d_pooled = fake, fake, fake
+        h = ctypes.c_void_p()
+        rc = L.pbn_batch_create(arr, 1, ctypes.byref(h))
+        detail = L.pbn_last_error_detail().decode()
+        if rc == 0:
+            L.pbn_batch_free(h)
+        return rc, detail
+
+    for call in (sim, batch):
+        rc, detail = call([0, 1, 0], [1, 1, 0])
+        assert rc == _lib.PBN_EINVAL and "contradictory values for meta node 0" in detail, (call, detail)
+        rc, detail = call([0, removed], [1, 1])
+        assert rc == _lib.PBN_EINVAL and f"meta node {removed} is not a retained node" in detail, (call, detail)
+    assert batch([0, 1, 0], [1, 0, 1])[0] == 0
