@@ -2,12 +2,15 @@
 
 Workload (one bench step = one pass of the whole hot path): the paper-scale network
 (n = 100, 70% single-function nodes, in-degree 1-5, 25% sinks, p = 1e-4, meta-state
-= nodes 0,1,2 ON), reduced and grouped (max 8 inputs per merged group), 2^16
-trajectories x 10^6 steps per GPU from the keyed initial state, with per-trajectory
-and pooled meta-state counts.  node-updates = n x trajectories x steps.
+= nodes 0,1,2 ON), reduced and grouped (the autotuner picks the group input cap, the
+kernel and its code shape, e.g. 12 inputs and the compiled interleaved plan with
+multiply gathers), 2^16 trajectories x 10^6 steps per GPU from the keyed initial
+state, with per-trajectory and pooled meta-state counts.  node-updates = n x
+trajectories x steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--n-steps S] [--n-traj T]
+                  [--n-steps S] [--n-traj T] [--sampler bitsliced|geometric]
+                  [--workload paper100|scalefree2000|batch|serve|apoptosis]
 
 Under torchrun each rank simulates its own trajectory-id range (weak scaling); the
 timed region is bracketed by a barrier and device synchronisation and the maximum
