@@ -20,6 +20,14 @@ def golden(name: str) -> str:
 
 @pytest.fixture(scope="session")
 def oracle_mod():
-    from oracle import oracle
-    oracle.build()
-    return oracle
+    alt = os.environ.get("PBN_ORACLE_DIR")
+    if alt:
+        # a copy of the oracle with a planted mistake (tests/test_oracle_mutants.py)
+        import importlib.util
+        spec = importlib.util.spec_from_file_location("oracle_under_test", os.path.join(alt, "oracle.py"))
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+    else:
+        from oracle import oracle as mod
+    mod.build()
+    return mod

@@ -143,6 +143,41 @@ def test_geo_thresholds_closed_forms(oracle_mod):
     assert oracle_mod.geo_thresholds(0.0) == [0] * 64
 
 
+def _geo_uniform(oracle_mod, seed, traj, step, word, j):
+    """The j-th 64-bit uniform of word `word` in the GEO stream, from the Philox
+    block alone: x1:x0 for even words, x3:x2 for odd words of block (word/2) << 8 | j."""
+    c2 = ((step >> 32) & 0xFFFF) | (((traj >> 32) & 0xFFFF) << 16)
+    x = oracle_mod.philox([traj & MASK32, step & MASK32, c2, (4 << 28) | ((word // 2) << 8) | j],
+                          [seed & MASK32, seed >> 32])
+    x = [int(v) for v in x]
+    return (x[1] << 32 | x[0]) if word % 2 == 0 else (x[3] << 32 | x[2])
+
+
+def test_geo_sampler_closed_form_at_one_half(oracle_mod):
+    """At p = 1/2, G[k] = 2^64 - 2^(63-k), so U < G[k] iff the top k+1 bits of U are
+    not all ones: the gap to the next perturbed lane is the number of leading ones
+    of the uniform, and a word ends when that count reaches the lanes left.  The
+    perturbation vector follows from the Philox blocks alone (70 nodes: a full and a
+    partial word)."""
+    n = 70
+    text = _net_const(n, 0.5)
+    for seed, traj, step in [(7, 0, 0), (2**40 + 5, 2**33 + 9, 2**35 + 11), (99, 12345, 678), (3, 1, 2)]:
+        g, _ = oracle_mod.gamma(text, seed, traj, step, sampler=1)
+        want = np.zeros(n, dtype=np.uint8)
+        for w in range(2):
+            L = min(64, n - 64 * w)
+            pos, j = 0, 0
+            while pos < L:
+                U = _geo_uniform(oracle_mod, seed, traj, step, w, j)
+                j += 1
+                ones = 64 - (((~U) & (2**64 - 1)).bit_length())  # leading one bits
+                if ones >= L - pos:
+                    break
+                want[64 * w + pos + ones] = 1
+                pos += ones + 1
+        assert np.array_equal(g, want), (seed, traj, step)
+
+
 def test_geo_sampler_rate_and_independence(oracle_mod):
     """The geometric sampler draws i.i.d. Bernoulli(P / 2^32) lanes: per-lane rate
     on full and partial words and pairwise independence within 5 sigma."""
@@ -258,6 +293,24 @@ def test_initial_state_words(oracle_mod):
         for b in range(64):
             if 64 * w + b < n:
                 assert s0[64 * w + b] == (word >> b) & 1
+
+
+def test_truth_table_input_order(oracle_mod):
+    """Text format: bit x of a truth table is the output for inputs a_0..a_{k-1} with
+    a_b the b-th bit of x.  At p = 0 one step is deterministic: node 2 = f(s0, s1)
+    with table 0x2 is 1 exactly when s0 = 1 and s1 = 0, and node 3 with parents
+    (1, 0) and the same table is 1 exactly when s1 = 1 and s0 = 0."""
+    text = ("pbn 4 0x0p+0\n"
+            "f 0 0x1p+0 1 0 2\n"
+            "f 1 0x1p+0 1 1 2\n"
+            "f 2 0x1p+0 2 0 1 2\n"
+            "f 3 0x1p+0 2 1 0 2\n")
+    init = np.array([[a, b, 0, 0] for a in (0, 1) for b in (0, 1)], dtype=np.uint8)
+    r = oracle_mod.simulate(text, 1, 0, 4, 1, meta_ids=[0], init_states=init)
+    for (a, b, _, _), fin in zip(init, r["final"]):
+        assert fin[0] == a and fin[1] == b
+        assert fin[2] == (1 if (a, b) == (1, 0) else 0), (a, b)
+        assert fin[3] == (1 if (a, b) == (0, 1) else 0), (a, b)
 
 
 # ------------------------------------------------------ Eq. 1 transition law ----
@@ -566,6 +619,20 @@ def test_estimator_sample_size_against_exact_variance(oracle_mod, a, b):
     assert z * math.sqrt(exact) <= r * (1 + 5.0 / N * (1 + abs(lam)) / (1 - abs(lam)) ** 2)
     asym = est["n_star_real"]
     assert asym <= N < asym + 1
+
+
+def test_estimate_counts_every_counted_state(oracle_mod):
+    """L is the number of counted states, the first counted state of each trajectory
+    included: T trajectories of S steps counted from step 0 give L = T (S + 1), and
+    pi = V / L."""
+    from paper_1605_00854_gb300 import synth
+    text = synth.tiny12(1).to_text()
+    T, S = 16, 300
+    r = oracle_mod.simulate(text, 3, 0, T, S, meta_ids=[0, 1, 2], count_from=0)
+    c = r["counts"].sum(axis=0)
+    est = oracle_mod.estimate(c, T, 0.01, 0.95, 1e-3)
+    assert est["L"] == T * (S + 1)
+    assert est["pi"] == int(c[0]) / (T * (S + 1))
 
 
 def test_worked_sample_size_number(oracle_mod):
