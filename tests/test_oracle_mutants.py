@@ -60,11 +60,23 @@ MUTANTS = [
     ("function_inputs_reversed", "pbn_oracle.c", "x |= (uint64_t)s[f->par[b]] << b;",
      "x |= (uint64_t)s[f->par[b]] << (f->k - 1 - b);"),
     ("nodewise_flip_keeps_value", "pbn_oracle.c", "s2[i] = gam[i] ? (uint8_t)(s[i] ^ 1u) :", "s2[i] = gam[i] ? s[i] :"),
+    ("eq1_functions_read_the_new_state", "pbn_oracle.c",
+     "for (int i = 0; i < n; ++i) s2[i] = (uint8_t)eval_fun(&g->node[i].f[ch[i]], s);\n                memcpy(s, s2, (size_t)n);\n            }\n            int z",
+     "for (int i = 0; i < n; ++i) s[i] = (uint8_t)eval_fun(&g->node[i].f[ch[i]], s);\n            }\n            int z"),
+    # the network text
+    ("hex_digits_read_most_significant_first", "pbn_oracle.c", "int v = hexval(th[nd_hex - 1 - d]);",
+     "int v = hexval(th[d]);"),
     # counts of the two-state chain
     ("pair_counts_transposed", "pbn_oracle.c", "cnt[1 + 2 * z_prev + z] += 1;", "cnt[1 + z_prev + 2 * z] += 1;"),
+    ("meta_values_ignored", "pbn_oracle.c", "if (s[jb->meta_ids[m]] != jb->meta_vals[m]) return 0;",
+     "if (s[jb->meta_ids[m]] != 1) return 0;"),
+    ("first_state_not_counted", "pbn_oracle.c",
+     "        if (jb->step_begin == jb->count_from) cnt[0] += (uint64_t)z_prev;\n", ""),
     ("visit_window_off_by_one", "pbn_oracle.c", "if (t + 1 >= jb->count_from) cnt[0] += (uint64_t)z;",
      "if (t >= jb->count_from) cnt[0] += (uint64_t)z;"),
     # exact transition matrix
+    ("nodewise_matrix_flip_toward_value", "pbn_oracle.c",
+     "q1[i] = pe * (double)(st[i] ^ 1u) + (1.0 - pe) * q1[i];", "q1[i] = pe * (double)st[i] + (1.0 - pe) * q1[i];"),
     ("matrix_unperturbed_counted_twice", "pbn_oracle.c", "if (semantics == 0 && s2 != s) row[s2]",
      "if (semantics == 0) row[s2]"),
     ("matrix_choice_interval_index", "pbn_oracle.c",
@@ -76,6 +88,8 @@ MUTANTS = [
      "                child[(size_t)v * n + u] = 1;\n            }\n    memset(is_leaf"),
     ("reach_edges_reversed", "pbn_oracle.c", "if (child[(size_t)v * n + u] && keep[u])",
      "if (child[(size_t)u * n + v] && keep[u])"),
+    ("leaves_interest_ignored", "pbn_oracle.c", "if (is_leaf[v] || intr[v]) continue;", "if (is_leaf[v]) continue;"),
+    ("reach_interest_not_kept", "pbn_oracle.c", "        keep[interest[m]] = 1;\n", ""),
     # the two-state chain estimator and the stationary distribution (numpy side)
     ("estimate_beta_wrong_count", "oracle.py", "b = n10 / (n10 + n11)", "b = n11 / (n10 + n11)"),
     ("estimate_sample_size_power", "oracle.py", "nreal = a * b * (2.0 - a - b) / (a + b) ** 3",
@@ -84,6 +98,7 @@ MUTANTS = [
     ("estimate_initial_states_dropped", "oracle.py", "L = n00 + n01 + n10 + n11 + int(n_traj)",
      "L = n00 + n01 + n10 + n11"),
     ("stationary_transposed", "oracle.py", "nxt = pi @ M", "nxt = M @ pi"),
+    ("estimate_mixing_rate_signed", "oracle.py", "lam = abs(1.0 - a - b)", "lam = 1.0 - a - b"),
 ]
 
 

@@ -296,21 +296,26 @@ def test_initial_state_words(oracle_mod):
 
 
 def test_truth_table_input_order(oracle_mod):
-    """Text format: bit x of a truth table is the output for inputs a_0..a_{k-1} with
-    a_b the b-th bit of x.  At p = 0 one step is deterministic: node 2 = f(s0, s1)
-    with table 0x2 is 1 exactly when s0 = 1 and s1 = 0, and node 3 with parents
-    (1, 0) and the same table is 1 exactly when s1 = 1 and s0 = 0."""
-    text = ("pbn 4 0x0p+0\n"
+    """Text format: bit x of a truth table (hex, least significant digit last) is the
+    output for inputs a_0..a_{k-1} with a_b the b-th bit of x.  At p = 0 one step is
+    deterministic: node 3 = f(s0, s1) with table 0x2 is 1 exactly when s0 = 1 and
+    s1 = 0; node 4 with parents (1, 0) and the same table exactly when s1 = 1 and
+    s0 = 0; node 5 with parents (0, 1, 2) and the two-digit table 0x10 (bit 4) exactly
+    when s0 = s1 = 0 and s2 = 1."""
+    text = ("pbn 6 0x0p+0\n"
             "f 0 0x1p+0 1 0 2\n"
             "f 1 0x1p+0 1 1 2\n"
-            "f 2 0x1p+0 2 0 1 2\n"
-            "f 3 0x1p+0 2 1 0 2\n")
-    init = np.array([[a, b, 0, 0] for a in (0, 1) for b in (0, 1)], dtype=np.uint8)
-    r = oracle_mod.simulate(text, 1, 0, 4, 1, meta_ids=[0], init_states=init)
-    for (a, b, _, _), fin in zip(init, r["final"]):
-        assert fin[0] == a and fin[1] == b
-        assert fin[2] == (1 if (a, b) == (1, 0) else 0), (a, b)
-        assert fin[3] == (1 if (a, b) == (0, 1) else 0), (a, b)
+            "f 2 0x1p+0 1 2 2\n"
+            "f 3 0x1p+0 2 0 1 2\n"
+            "f 4 0x1p+0 2 1 0 2\n"
+            "f 5 0x1p+0 3 0 1 2 10\n")
+    init = np.array([[a, b, c, 0, 0, 0] for a in (0, 1) for b in (0, 1) for c in (0, 1)], dtype=np.uint8)
+    r = oracle_mod.simulate(text, 1, 0, len(init), 1, meta_ids=[0], init_states=init)
+    for (a, b, c, _, _, _), fin in zip(init, r["final"]):
+        assert list(fin[:3]) == [a, b, c]
+        assert fin[3] == (1 if (a, b) == (1, 0) else 0), (a, b)
+        assert fin[4] == (1 if (a, b) == (0, 1) else 0), (a, b)
+        assert fin[5] == (1 if (a, b, c) == (0, 0, 1) else 0), (a, b, c)
 
 
 # ------------------------------------------------------ Eq. 1 transition law ----
@@ -440,9 +445,11 @@ def test_pernode_rows_are_distributions(oracle_mod):
 
 
 # ---------------------------------------------------------------- counting ----
-def _recount(trace_states, s_start, meta, start_index, count_from):
-    """Brute-force counts from a list of states s(start_index), s(start_index+1)..."""
-    z = [int(all(st[m] for m in meta)) for st in [s_start] + list(trace_states)]
+def _recount(trace_states, s_start, meta, start_index, count_from, vals=None):
+    """Brute-force counts from a list of states s(start_index), s(start_index+1)...
+    (meta-state: node meta[m] holds vals[m], default 1)."""
+    vals = [1] * len(meta) if vals is None else list(vals)
+    z = [int(all(st[m] == v for m, v in zip(meta, vals))) for st in [s_start] + list(trace_states)]
     V = sum(zi for k, zi in enumerate(z) if start_index + k >= count_from)
     n = [0, 0, 0, 0]
     for k in range(1, len(z)):
@@ -451,17 +458,18 @@ def _recount(trace_states, s_start, meta, start_index, count_from):
     return [V] + n
 
 
-@pytest.mark.parametrize("count_from", [0, 1, 37])
-def test_counts_match_bruteforce_recount(oracle_mod, count_from):
+@pytest.mark.parametrize("count_from,vals", [(0, None), (1, None), (37, None), (0, [0, 1, 0]), (5, [1, 0, 0])])
+def test_counts_match_bruteforce_recount(oracle_mod, count_from, vals):
     from paper_1605_00854_gb300 import synth
     text = synth.tiny12(1).to_text()
     meta = [0, 1, 2]
-    r = oracle_mod.simulate(text, 9, 0, 6, 300, meta_ids=meta, count_from=count_from, trace=True)
+    r = oracle_mod.simulate(text, 9, 0, 6, 300, meta_ids=meta, meta_vals=vals, count_from=count_from, trace=True)
     init = np.zeros((6, 12), dtype=np.uint8)
     for t in range(6):
         init[t] = oracle_mod.draws(text, 9, t, 0)[2]
+    assert 0 < int(r["counts"][:, 0].sum()) < 6 * 301  # the meta-state is visited, and left
     for t in range(6):
-        want = _recount(r["trace"][t], init[t], meta, 0, count_from)
+        want = _recount(r["trace"][t], init[t], meta, 0, count_from, vals)
         assert list(map(int, r["counts"][t])) == want
         c = r["counts"][t]
         L = 300 + 1 - count_from
