@@ -686,3 +686,33 @@ def test_meta_state_validation_is_shared_by_single_and_batched_launches(L):
         rc, detail = call([0, removed], [1, 1])
         assert rc == _lib.PBN_EINVAL and f"meta node {removed} is not a retained node" in detail, (call, detail)
     assert batch([0, 1, 0], [1, 0, 1])[0] == 0
+
+
+def test_simulate_argument_checks_before_any_device_work(L):
+    """pbn_simulate refuses malformed calls with PBN_EINVAL before it touches the
+    device (fake, never dereferenced buffers), and a call with no trajectories is a
+    no-op."""
+    import ctypes
+    text = synth.paper100(seed=2).to_text()
+    red, _ = api.Net.load(text).reduce([0, 1, 2])
+    plan = api.Plan(red)
+    fake = 1 << 20
+    ids = np.ascontiguousarray([0, 1, 2], dtype=np.uint32)
+
+    def call(image=fake, plan_h=None, **kw):
+        a = _lib.SimArgs()
+        a.n_traj, a.n_steps, a.n_meta, a.meta_ids, a.d_state = 4, 1, 3, ids.ctypes.data, fake
+        for k, v in kw.items():
+            setattr(a, k, v)
+        rc = L.pbn_simulate(plan._h if plan_h is None else plan_h, ctypes.c_void_p(image), ctypes.byref(a), None)
+        return rc, L.pbn_last_error_detail().decode()
+
+    assert call(n_traj=0)[0] == 0
+    bad = [dict(image=fake + 8), dict(d_state=None), dict(n_traj=1 << 31), dict(n_steps=1 << 32),
+           dict(traj_begin=(1 << 48) - 2), dict(step_begin=1 << 48, init=_lib.PBN_INIT_STATE),
+           dict(init=7), dict(step_begin=5), dict(kernel=9), dict(n_meta=0), dict(meta_ids=None),
+           dict(d_trace=fake, n_steps=1 << 31, n_traj=1 << 20)]
+    for kw in bad:
+        rc, detail = call(**kw)
+        assert rc == _lib.PBN_EINVAL and detail.startswith("pbn_simulate"), (kw, rc, detail)
+    assert L.pbn_simulate(None, ctypes.c_void_p(fake), None, None) == _lib.PBN_EINVAL
