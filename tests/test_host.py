@@ -716,3 +716,38 @@ def test_simulate_argument_checks_before_any_device_work(L):
         rc, detail = call(**kw)
         assert rc == _lib.PBN_EINVAL and detail.startswith("pbn_simulate"), (kw, rc, detail)
     assert L.pbn_simulate(None, ctypes.c_void_p(fake), None, None) == _lib.PBN_EINVAL
+
+
+def test_synthetic_workloads_have_their_stated_shape():
+    """The seeded stand-ins have the shapes the workload recipe states: the
+    paper-scale network (70 % single-function nodes, in-degree 1-5 with mean 2.5,
+    25 % sinks that exclude the meta nodes, p = 1e-4), the scale-free network
+    (in-degree 1-6, 1-3 functions, a heavy-tailed out-degree, p = 1e-5) and the batch
+    shapes (log-uniform n, trajectories and p within their ranges)."""
+    from collections import Counter
+    net = synth.paper100(seed=2)
+    assert net.n == 100 and net.p == 1e-4
+    ells = Counter(len(fl) for fl in net.funcs)
+    assert set(ells) <= {1, 2, 3} and 0.55 <= ells[1] / 100 <= 0.85
+    ks = [len(f.parents) for fl in net.funcs for f in fl]
+    assert min(ks) >= 1 and max(ks) <= 5 and 2.1 <= np.mean(ks) <= 2.9
+    parents = {a for fl in net.funcs for f in fl for a in f.parents}
+    assert len([i for i in range(3, 100) if i not in parents]) >= 25  # the sinks (meta nodes excluded)
+    for fl in net.funcs:
+        assert abs(sum(f.c for f in fl) - 1.0) < 1e-12
+
+    sf = synth.scalefree2000(seed=3)
+    assert sf.n == 2000 and sf.p == 1e-5
+    ks = [len(f.parents) for fl in sf.funcs for f in fl]
+    assert min(ks) >= 1 and max(ks) <= 6 and set(len(fl) for fl in sf.funcs) == {1, 2, 3}
+    out = np.array([len(c) for c in sf.children()])
+    assert out.max() > 20 * out.mean()  # hubs of the power law
+
+    shapes = synth.batch_shapes(seed=4)
+    assert len(shapes) == 256
+    n, t, p = (np.array(x, dtype=float) for x in zip(*shapes))
+    assert n.min() >= 20 and n.max() <= 4000 and t.min() >= 1024 and t.max() <= 65536
+    assert p.min() >= 1e-5 and p.max() <= 1e-2
+    # log-uniform: the median sits near the geometric mean of each range
+    assert abs(np.log(np.median(n)) - 0.5 * np.log(20 * 4000)) < 0.6
+    assert abs(np.log(np.median(t)) - 0.5 * np.log(1024 * 65536)) < 0.6
