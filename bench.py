@@ -551,7 +551,7 @@ def apoptosis_queries():
 
 def run_apoptosis(args):
     """Seven steady-state probabilities of the apoptosis-shaped network at precision
-    r = 1e-5 and confidence 0.95 (Sec. 4.3's setting), estimated together by the
+    r = 1e-5 and confidence 0.95 (Sec. 4.2's setting), estimated together by the
     two-state Markov chain stopping rule through the serving loop."""
     from paper_1605_00854_gb300 import serve
     net, X, par, metas = apoptosis_queries()
@@ -580,7 +580,7 @@ def run_apoptosis(args):
                         for r in res],
             "total_samples": samples, "node_updates_per_s": srv.node_updates / wall, "rounds": srv.stats,
             "completed": len(res), "failed": len(srv.failed),
-            "paper_context": "Sec. 4.3: 7 probabilities, 50-452 million samples each, about 10 minutes "
+            "paper_context": "Sec. 4.2: 7 probabilities, 50-452 million samples each, about 10 minutes "
                              "in total for the structure-based method on the paper's CPU (other hardware)"}
     print(json.dumps(line), flush=True)
 

@@ -409,7 +409,10 @@ int pbn_batch_image(const pbn_batch* batch, void* host_dst, size_t cap);
  * empty) that must be zero before the first launch; the last CTA of every launch
  * resets them, so launches can follow each other (or be captured in a CUDA graph)
  * without a reset.  Launches sharing one d_queue must not overlap.  ctas_per_sm = 0
- * uses the occupancy limit.  d_status (may be NULL) receives PBN_DEV_* bits.
+ * uses the occupancy limit.  d_status (may be NULL) receives PBN_DEV_* bits.  The
+ * kernel's shared-memory limit is raised on the current device as the batch needs
+ * and never lowered, and the occupancy is found once per batch and device, so
+ * batches, devices and this call and pbn_batch_run_static may be mixed freely.
  * Errors: PBN_EINVAL, PBN_ETOOBIG, PBN_ECUDA. */
 int pbn_batch_run(const pbn_batch* batch, const void* d_desc, uint32_t* d_queue, uint64_t step_offset,
                   uint64_t n_steps, uint32_t ctas_per_sm, uint32_t* d_status, void* stream);

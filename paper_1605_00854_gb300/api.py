@@ -133,7 +133,7 @@ class Plan:
         self.net = net
         self.info = _lib.PlanInfo()
         check(L.pbn_plan_info_get(self._h, ctypes.byref(self.info)), "pbn_plan_info_get")
-        self._dev = None
+        self._dev = {}  # device -> uploaded image
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -178,11 +178,16 @@ class Plan:
         return buf.value.decode()
 
     def device_image(self, device="cuda"):
-        """The image uploaded once to device memory (cached)."""
+        """The image uploaded to `device` (once per device, then cached)."""
         import torch
-        if self._dev is None:
-            self._dev = torch.from_numpy(self.image()).to(device)
-        return self._dev
+        dev = torch.device(device)
+        if dev.type == "cuda" and dev.index is None:
+            dev = torch.device("cuda", torch.cuda.current_device())
+        img = self._dev.get(dev)
+        if img is None:
+            img = torch.from_numpy(self.image()).to(dev)
+            self._dev[dev] = img
+        return img
 
     def unpack(self, words: np.ndarray) -> np.ndarray:
         """Grouped state words [state_words, T] (uint64) -> bits [T, n] in original node

@@ -129,6 +129,10 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
         if (threadIdx.x == 0) item_sh = atomicAdd(&B.queue[0], 1u);
         __syncthreads();
         const uint32_t it = item_sh;
+        /* the previous item read and wrote shared memory through the generic proxy; the
+         * bulk copies that re-stage it go through the async proxy, so every thread
+         * orders its accesses before them (fence, then the barrier, then the copy) */
+        pbn_fence_proxy_async();
         __syncthreads(); /* everyone has read item_sh (and finished with the previous plan) */
         if (it >= B.n_items) break;
         const WorkItem W = B.items[it];
@@ -262,20 +266,7 @@ __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) 
     }
 }
 
-int sm_count() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
-    return sms;
-}
-
-int smem_optin() {
-    int dev = 0, lim = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || lim <= 0)
-        lim = 227 * 1024;
-    return lim;
-}
+constexpr int kMaxDevices = 64;
 
 }  // namespace
 
@@ -285,8 +276,11 @@ struct pbn_batch {
     std::vector<WorkItem> items;
     std::vector<uint8_t> image; /* nets then items */
     uint32_t threads = 512;
-    mutable int occ_per_sm = 0;  /* occupancy of the batch kernel, queried on the first run */
-    mutable int sms = 0;
+    /* CTAs of the batch kernel per SM and the SM count, per device, found on the first
+     * run on that device (so that later launches can be graph-captured) */
+    mutable std::mutex mu;
+    mutable int occ_per_sm[kMaxDevices] = {0};
+    mutable int sms[kMaxDevices] = {0};
 };
 
 namespace {
@@ -471,6 +465,38 @@ extern "C" int pbn_batch_image(const pbn_batch* b, void* dst, size_t cap) {
     return PBN_OK;
 }
 
+namespace {
+/* Grid of the batch kernel on the current device: raises the kernel's shared-memory
+ * limit there to the batch's need (never lowering what another batch set), and finds
+ * the CTAs per SM and the SM count of that device on the batch's first run on it. */
+int launch_shape(const pbn_batch* b, uint32_t ctas_per_sm, const char* who, uint32_t* grid) {
+    using pbn::fail;
+    const size_t smem = b->info.smem_bytes;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PBN_EINVAL, "%s: device %d beyond %d", who, dev, kMaxDevices);
+    const int se = pbn::ensure_dyn_smem(reinterpret_cast<const void*>(pbn_batch_kernel), smem);
+    if (se != 0) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(static_cast<cudaError_t>(se)));
+    int per_sm = 0, sms = 0;
+    {
+        std::lock_guard<std::mutex> g(b->mu);
+        if (!b->occ_per_sm[dev]) {
+            int occ = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbn_batch_kernel, (int)b->threads, smem);
+            if (e != cudaSuccess || occ < 1) return fail(PBN_ETOOBIG, "%s: the batch kernel does not fit an SM", who);
+            b->occ_per_sm[dev] = occ;
+            b->sms[dev] = pbn::device_sms();
+        }
+        per_sm = b->occ_per_sm[dev];
+        sms = b->sms[dev];
+    }
+    if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
+    *grid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, std::max<uint32_t>(1u, b->info.n_items));
+    return PBN_OK;
+}
+}  // namespace
+
 extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d_queue, uint64_t step_offset,
                              uint64_t n_steps, uint32_t ctas_per_sm, uint32_t* d_status, void* stream) {
     using pbn::fail;
@@ -488,26 +514,11 @@ extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
     const size_t smem = b->info.smem_bytes;
-    cudaError_t e;
-    if (!b->occ_per_sm) {
-        /* device queries once per batch, so later launches can be graph-captured */
-        static size_t configured = 48 * 1024;
-        if (smem > configured) {
-            e = cudaFuncSetAttribute(pbn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
-            configured = smem;
-        }
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pbn_batch_kernel, (int)b->threads, smem);
-        if (e != cudaSuccess || per_sm < 1) return fail(PBN_ETOOBIG, "pbn_batch_run: the batch kernel does not fit an SM");
-        b->occ_per_sm = per_sm;
-        b->sms = sm_count();
-    }
-    int per_sm = b->occ_per_sm;
-    if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)b->sms * per_sm, std::max<uint32_t>(1u, b->info.n_items));
+    uint32_t grid = 0;
+    int rc = launch_shape(b, ctas_per_sm, "pbn_batch_run", &grid);
+    if (rc != PBN_OK) return rc;
     pbn_batch_kernel<<<grid, b->threads, smem, static_cast<cudaStream_t>(stream)>>>(P);
-    e = cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
     return PBN_OK;
 }
@@ -525,7 +536,6 @@ extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d
 namespace {
 __device__ __align__(256) uint32_t g_pbn_static_queues[2 * PBN_STATIC_QUEUE_SLOTS];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 uint32_t* g_static_addr[kMaxDevices] = {nullptr};
 }  // namespace
@@ -574,23 +584,9 @@ extern "C" int pbn_batch_run_static(const pbn_batch* b, const void* d_desc, uint
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
     const size_t smem = b->info.smem_bytes;
-    static size_t configured_static = 48 * 1024;
-    if (smem > configured_static) {
-        e = cudaFuncSetAttribute(pbn_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
-        configured_static = smem;
-    }
-    if (!b->occ_per_sm) {
-        int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pbn_batch_kernel, (int)b->threads, smem);
-        if (e != cudaSuccess || per_sm < 1)
-            return fail(PBN_ETOOBIG, "pbn_batch_run_static: the batch kernel does not fit an SM");
-        b->occ_per_sm = per_sm;
-        b->sms = sm_count();
-    }
-    int per_sm = b->occ_per_sm;
-    if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>((uint64_t)b->sms * per_sm, std::max<uint32_t>(1u, b->info.n_items));
+    uint32_t grid = 0;
+    const int rc = launch_shape(b, ctas_per_sm, "pbn_batch_run_static", &grid);
+    if (rc != PBN_OK) return rc;
     pbn_batch_kernel<<<grid, b->threads, smem, st>>>(P);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));

@@ -98,6 +98,12 @@ __device__ __forceinline__ void pbn_mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+/* Orders this thread's earlier generic-proxy accesses to shared memory before later
+ * async-proxy operations (bulk copies) that a barrier orders after them. */
+__device__ __forceinline__ void pbn_fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void pbn_mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile(
         "{\n\t.reg .b64 st;\n\t"

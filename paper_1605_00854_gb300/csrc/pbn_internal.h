@@ -61,6 +61,15 @@ void jit_free(pbn_jit_state* J);
 int jit_compile(const pbn_plan* plan, uint32_t flags);
 bool jit_ready(const pbn_plan* plan);
 uint32_t jit_current_flags(const pbn_plan* plan); /* flags of the compiled kernel, else 0 */
+
+/* Launch facts of the current device, queried once per device (thread-safe). */
+int device_sms();         /* SM count */
+int device_smem_optin();  /* opt-in dynamic shared memory per block, bytes */
+/* Raise `func`'s dynamic shared-memory limit on the current device to at least
+ * `bytes`; the limit is per device and per kernel and is only ever raised, so that
+ * callers sharing a kernel never lower each other's setting.  Returns a
+ * cudaError_t value (0 = success). */
+int ensure_dyn_smem(const void* func, size_t bytes);
 }  // namespace pbn
 
 #endif

@@ -29,6 +29,9 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "pbn_device.cuh"
 #include "pbn_interp.cuh"
@@ -122,12 +125,8 @@ __global__ void __launch_bounds__(kMaxCtaThreads) pbn_sim_kernel(const SimParams
 template <int LG, bool TRACE, bool TAB_SMEM>
 cudaError_t launch_t(const SimParams& P, uint32_t grid, uint32_t tpb, size_t smem, cudaStream_t st) {
     auto kern = pbn_sim_kernel<LG, TRACE, TAB_SMEM>;
-    static size_t configured = 48 * 1024;
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
+    const int e = pbn::ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+    if (e != 0) return static_cast<cudaError_t>(e);
     kern<<<grid, tpb, smem, st>>>(P);
     return cudaGetLastError();
 }
@@ -141,27 +140,59 @@ cudaError_t launch_lg(const SimParams& P, bool trace, bool tab_smem, uint32_t gr
                     : launch_t<LG, false, false>(P, grid, tpb, smem, st);
 }
 
-int device_smem_limit() {
-    static int lim = 0;
-    if (!lim) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&lim, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || lim <= 0)
-            lim = 48 * 1024;
-    }
-    return lim;
+}  // namespace
+
+/* ---- per-device launch facts and shared-memory opt-in ------------------------------ */
+namespace pbn {
+namespace {
+constexpr int kMaxDevices = 64;
+struct DeviceFacts {
+    int sms = 0, smem_optin = 0;
+};
+std::mutex g_dev_mu;
+DeviceFacts g_dev[kMaxDevices];
+std::map<std::pair<int, const void*>, size_t> g_smem_set; /* (device, kernel) -> limit set */
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    return dev;
 }
 
-int device_sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 1;
+const DeviceFacts& facts() {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    DeviceFacts& F = g_dev[dev];
+    if (!F.sms) {
+        int v = 0;
+        F.sms = (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0) ? v : 1;
+        F.smem_optin = (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+                           ? v
+                           : 48 * 1024;
     }
-    return sms;
+    return F;
 }
+}  // namespace
 
+int device_sms() { return facts().sms; }
+int device_smem_optin() { return facts().smem_optin; }
+
+int ensure_dyn_smem(const void* func, size_t bytes) {
+    if (bytes <= 48u * 1024u) return 0;
+    const int dev = current_device();
+    std::lock_guard<std::mutex> g(g_dev_mu);
+    size_t& set = g_smem_set[std::make_pair(dev, func)];
+    if (bytes <= set) return 0;
+    const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    set = bytes;
+    return 0;
+}
+}  // namespace pbn
+
+namespace {
+int device_smem_limit() { return pbn::device_smem_optin(); }
+int device_sm_count() { return pbn::device_sms(); }
 }  // namespace
 
 namespace pbn {

@@ -173,7 +173,7 @@ def scalefree2000(seed: int = 3, n: int = 2000, p: float = 1e-5, exponent: float
 
 def apoptosis96(seed: int = 5, n: int = 96, n_leaves: int = 36, total_inputs: int = 171,
                 p: float = 1e-4) -> Network:
-    """Stand-in with the shape of the paper's apoptosis network (Sec. 4.3: 96 nodes,
+    """Stand-in with the shape of the paper's apoptosis network (Sec. 4.2: 96 nodes,
     37.5% leaves, density 1.78); the real model is not available.  60 core nodes
     lie on one random directed cycle (each core node's first parent in every
     function is its cycle predecessor, so every core node has a core child and is

@@ -453,7 +453,7 @@ def test_reduce_reach_rule_matches_oracle(oracle_mod, seed):
 
 # ------------------------------------------------------------ workload shapes ----
 def test_apoptosis_stand_in_has_the_papers_shape(oracle_mod):
-    """Sec. 4.3's apoptosis network: 96 nodes, 37.5% leaves, density 1.78.  The
+    """Sec. 4.2's apoptosis network: 96 nodes, 37.5% leaves, density 1.78.  The
     stand-in's leaves (Definition 1, by the oracle) for every meta-state of the
     workload are exactly its 36 non-core nodes."""
     import bench
@@ -751,3 +751,16 @@ def test_synthetic_workloads_have_their_stated_shape():
     # log-uniform: the median sits near the geometric mean of each range
     assert abs(np.log(np.median(n)) - 0.5 * np.log(20 * 4000)) < 0.6
     assert abs(np.log(np.median(t)) - 0.5 * np.log(1024 * 65536)) < 0.6
+
+
+def test_device_image_cache_is_per_device():
+    """Plan.device_image uploads once per device: the same device gives the cached
+    tensor, another device gets its own copy (never the first device's)."""
+    torch = pytest.importorskip("torch")
+    plan = api.Plan(api.Net.load(synth.tiny12(1).to_text()))
+    a = plan.device_image("cpu")
+    assert plan.device_image(torch.device("cpu")) is a
+    assert np.array_equal(a.numpy(), plan.image())
+    m = plan.device_image("meta")
+    assert m is not a and m.device.type == "meta" and tuple(m.shape) == tuple(a.shape)
+    assert plan.device_image("meta") is m and plan.device_image("cpu") is a
