@@ -72,6 +72,12 @@ class Result:
     beta: float
     counts: list = field(default_factory=list)
     n_traj: int = 0
+    n_eff: int = 0          # trajectories whose counting window had started (the estimate's n_traj)
+    restarts: int = 0       # counting-window restarts by the burn-in rule
+    # per trajectory block: traj_begin, n_traj, count_from, steps (and, with
+    # Server(record_blocks=True), its final "state" [state_words, n_traj] and per-trajectory
+    # "counts" [5, n_traj] as uint64 host arrays)
+    blocks: list = field(default_factory=list)
 
 
 class _Block:
@@ -97,6 +103,7 @@ class _Active:
         self.nbytes = nbytes
         self.rounds = 0
         self.node_updates = 0.0
+        self.restarts = 0
 
     @property
     def step(self) -> int:
@@ -115,7 +122,7 @@ class Server:
                  max_steps: int = 1 << 20, grow_rounds: int = 4, max_traj: int = 1 << 16, device="cuda",
                  kernel: str = "batch", sampler: int = _lib.PBN_PERT_BITSLICED,
                  compile_flags: int = _lib.PBN_COMPILE_INTERLEAVED, compiled_min_traj: int = 4096,
-                 side_streams: int = 4):
+                 side_streams: int = 4, record_blocks: bool = False):
         import torch
         self.torch = torch
         self.dev = torch.device(device)
@@ -133,6 +140,7 @@ class Server:
         self.sampler = sampler
         self.compile_flags = compile_flags
         self.compiled_min_traj = compiled_min_traj
+        self.record_blocks = record_blocks
         self.side = [torch.cuda.Stream(self.dev) for _ in range(side_streams)] if kernel == "auto" else []
         self.pool = ThreadPoolExecutor(max_workers=workers)
         self.prepared: "queue.Queue" = queue.Queue()
@@ -336,7 +344,7 @@ class Server:
             # (z / r)^2 / 4, and report pi = V / L
             n_min = math.ceil(0.25 * (est.z / a.q.r) ** 2)
             if a.step >= self.max_steps or (est.L >= n_min and (int(c[0]) == 0 or int(c[0]) == est.L)):
-                self._finish(a, est, c)
+                self._finish(a, est, c, n_eff)
                 return True
             return False
         if est.m_star > burn:
@@ -344,6 +352,7 @@ class Server:
             # or at m*, whichever is later (ordered before the next round on the
             # server's stream)
             if a.step >= est.m_star:
+                a.restarts += 1
                 with self.torch.cuda.stream(self.stream):
                     for b in a.blocks:
                         if b.count_from < est.m_star:
@@ -352,7 +361,7 @@ class Server:
                             b.bufs.pooled.zero_()
             return False
         if est.L >= est.n_star or a.step >= self.max_steps:
-            self._finish(a, est, c)
+            self._finish(a, est, c, n_eff)
             return True
         self._maybe_grow(a, est)
         return False
@@ -374,12 +383,21 @@ class Server:
             a.compiling = self.pool.submit(self._compile, a.plan)
         self.stats["grown"] = self.stats.get("grown", 0) + 1
 
-    def _finish(self, a: _Active, est, c):
+    def _finish(self, a: _Active, est, c, n_eff: int):
+        latency = time.perf_counter() - a.q.arrival
+        blocks = []
+        for b in a.blocks:
+            rec = {"traj_begin": b.traj_begin, "n_traj": b.n_traj, "count_from": b.count_from, "steps": b.step}
+            if self.record_blocks:
+                # this round's launches have completed (the round synchronised its stream)
+                rec["state"] = b.bufs.state.cpu().numpy().view(np.uint64).copy()
+                rec["counts"] = b.bufs.counts.cpu().numpy().view(np.uint64).copy()
+            blocks.append(rec)
         self.done.append(Result(
             qid=a.q.qid, pi=est.pi, n_star=int(est.n_star), m_star=int(est.m_star), L=int(est.L),
-            steps=a.step, rounds=a.rounds, latency=time.perf_counter() - a.q.arrival, prep_s=a.prep_s,
+            steps=a.step, rounds=a.rounds, latency=latency, prep_s=a.prep_s,
             node_updates=a.node_updates, alpha=est.alpha, beta=est.beta, counts=[int(x) for x in c],
-            n_traj=a.n_traj))
+            n_traj=a.n_traj, n_eff=int(n_eff), restarts=a.restarts, blocks=blocks))
 
     def step(self) -> list:
         """Admit what is ready and run one round (if anything is active)."""
