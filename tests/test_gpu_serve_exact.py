@@ -1,6 +1,6 @@
 """Served results against the oracle, exactly (Sec. 4.2's two-state chain estimate).
 
-Nine queries are served together by the continuous-batching server; one of them is
+Ten queries are served together by the continuous-batching server; one of them is
 cancelled after two rounds.  The server's settings make the two-state rule restart
 counting windows (a burn-in of 2 steps before the first decision, so m* exceeds it)
 and grow slow queries (new trajectory blocks with the next ids and their own
@@ -46,9 +46,11 @@ def _queries():
         vals = [int(v) for v in rng.integers(0, 2, size=k)] if i % 3 == 2 else None
         qs.append(serve.Query(qid=i, text=text, meta_ids=meta, meta_vals=vals,
                               seed=int(rng.integers(1, 2**62)), r=float(rng.choice([0.03, 0.05]))))
-    qs[3].r = 0.002  # far from done when it is cancelled
     # a slowly mixing small network at a tighter precision: grows its trajectories
-    qs.append(serve.Query(qid=8, text=synth.tiny12(1).to_text(), meta_ids=[0, 1, 2], seed=99, r=0.01))
+    tiny = synth.tiny12(1).to_text()
+    qs.append(serve.Query(qid=8, text=tiny, meta_ids=[0, 1, 2], seed=99, r=0.01))
+    # the same network at r = 0.001 (N* of millions of states): far from done when cancelled
+    qs.append(serve.Query(qid=9, text=tiny, meta_ids=[0, 1, 2], seed=7, r=0.001))
     return qs
 
 
@@ -58,12 +60,11 @@ def _serve(qs, cancel_qid, kernel):
     try:
         for q in qs:
             srv.submit(q)
-        rounds = 0
-        while srv.pending and rounds < 100000:
-            srv.step()
-            rounds += 1
-            if rounds == 2:
-                srv.cancel(cancel_qid)
+        steps = 0
+        while srv.pending and steps < 10**6 and not any(a.q.qid == cancel_qid and a.rounds >= 2 for a in srv.active):
+            srv.step()  # idle until queries are prepared, then rounds
+            steps += 1
+        srv.cancel(cancel_qid)  # after two of its rounds, with its neighbours in flight
         srv.drain(timeout=600)
     finally:
         srv.close()
@@ -79,7 +80,7 @@ def _close(a, b):
 @pytest.mark.parametrize("kernel", ["batch", "auto"])
 def test_served_queries_equal_the_oracle(oracle_mod, kernel):
     qs = _queries()
-    cancel = 3
+    cancel = 9
     srv = _serve(qs, cancel, kernel)
     assert cancel in srv.cancelled and srv.in_use == 0 and not srv.failed
     done = {r.qid: r for r in srv.done}
