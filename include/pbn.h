@@ -383,6 +383,8 @@ typedef struct {
     uint64_t desc_bytes;       /* bytes of pbn_batch_image */
     uint64_t smem_bytes;       /* dynamic shared memory per CTA */
     double est_ops_per_step;   /* sum over networks of n_traj x ops_per_step */
+    uint32_t n_compiled;       /* networks run by compiled code (pbn_batch_compile) */
+    uint32_t reserved;
 } pbn_batch_info;
 
 /* Describe a batch of networks for the persistent work-queue kernel: each network
@@ -396,6 +398,24 @@ typedef struct {
  * PBN_ENOMEM. */
 int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out);
 int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
+
+/* Give the batch compiled code (the batched form of Algorithm 5 with each network's
+ * Preparation output as constants, as pbn_plan_compile does for one network): every
+ * network whose plan compiles with `flags` (PBN_COMPILE_PERT_UNROLLED,
+ * PBN_COMPILE_INTERLEAVED, PBN_COMPILE_PIPELINED, PBN_COMPILE_WIDE; multiply gathers
+ * are not offered here) becomes a device function of one generated module, with its
+ * Philox keys and meta-state rows as constants, run one trajectory per thread; a
+ * persistent kernel in the same module pops the work items from the device queue and
+ * calls the network's function, or, for networks that do not compile, the
+ * interpreter (prebuilt relocatable device code, pbn_batch_item.cubin next to the
+ * library, linked with nvJitLink).  Call it before pbn_batch_image: it re-cuts the
+ * compiled networks' work items (pbn_batch_info_get gives the new n_items,
+ * desc_bytes, smem_bytes and n_compiled).  Results are bit-identical to the
+ * uncompiled batch.  *compile_ms (may be NULL) receives the host time.  Host memory
+ * and one CUDA library owned by the batch; no device memory is allocated.
+ * Errors: PBN_EINVAL (NULL, compiled already, unsupported flags, no network
+ * compiles), PBN_ECUDA (NVRTC, nvJitLink or loading failed), PBN_ENOMEM. */
+int pbn_batch_compile(pbn_batch* batch, uint32_t flags, double* compile_ms);
 
 /* Serialise the batch's device table (network descriptors, then work items) into
  * host memory (cap >= desc_bytes); the caller copies it to a 16-byte aligned device

@@ -81,7 +81,8 @@ class BatchNet(ctypes.Structure):
 
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_nets", u32), ("n_items", u32), ("threads", u32), ("max_lanes", u32),
-                ("desc_bytes", u64), ("smem_bytes", u64), ("est_ops_per_step", f64)]
+                ("desc_bytes", u64), ("smem_bytes", u64), ("est_ops_per_step", f64),
+                ("n_compiled", u32), ("reserved", u32)]
 
 
 class SimArgs(ctypes.Structure):
@@ -117,6 +118,7 @@ SIGNATURES = {
     "pbn_batch_create": (i32, [ctypes.POINTER(BatchNet), u32, ctypes.POINTER(vp)]),
     "pbn_batch_info_get": (i32, [vp, ctypes.POINTER(BatchInfo)]),
     "pbn_batch_image": (i32, [vp, vp, ctypes.c_size_t]),
+    "pbn_batch_compile": (i32, [vp, u32, ctypes.POINTER(f64)]),
     "pbn_batch_run": (i32, [vp, vp, vp, u64, u64, u32, vp, vp]),
     "pbn_batch_free": (None, [vp]),
     "pbn_batch_run_static": (i32, [vp, vp, u32, u64, u64, u32, vp, vp]),

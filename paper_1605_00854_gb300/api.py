@@ -271,9 +271,11 @@ class Batch:
     device work queue (pbn_batch_create / pbn_batch_run).
 
     `entries` is a list of dicts with keys plan, bufs (SimBuffers), seed, meta_ids and
-    optionally meta_vals, traj_begin, step_begin, count_from, init."""
+    optionally meta_vals, traj_begin, step_begin, count_from, init.  With
+    compile_flags (pbn_batch_compile) the networks whose plans compile run their own
+    generated code in the same persistent launch, the others the interpreter."""
 
-    def __init__(self, entries, device="cuda"):
+    def __init__(self, entries, device="cuda", compile_flags: int | None = None):
         import torch
         L = _lib.load()
         self.entries = entries
@@ -302,6 +304,11 @@ class Batch:
         h = ctypes.c_void_p()
         check(L.pbn_batch_create(arr, len(entries), ctypes.byref(h)), "pbn_batch_create")
         self._h = h
+        self.compile_ms = 0.0
+        if compile_flags is not None:
+            ms = ctypes.c_double()
+            check(L.pbn_batch_compile(self._h, compile_flags, ctypes.byref(ms)), "pbn_batch_compile")
+            self.compile_ms = ms.value
         self.info = _lib.BatchInfo()
         check(L.pbn_batch_info_get(self._h, ctypes.byref(self.info)), "pbn_batch_info_get")
         host = np.zeros(self.info.desc_bytes, dtype=np.uint8)

@@ -22,19 +22,25 @@ GENCODE = "arch=compute_103a,code=sm_103a"
 
 CU_SOURCES = ["pbn_sim.cu", "pbn_batch.cu"]
 CPP_SOURCES = ["pbn_host.cpp", "pbn_jit.cpp"]
-HEADERS = ["pbn_internal.h", "pbn_image.h", "pbn_device.cuh", "pbn_interp.cuh"]
+HEADERS = ["pbn_internal.h", "pbn_image.h", "pbn_device.cuh", "pbn_interp.cuh", "pbn_batch.cuh",
+           "pbn_batch_interp.cuh"]
+# the interpreter's batch work-item function as relocatable device code, linked at run
+# time into the batch modules of pbn_batch_compile
+ITEM_SOURCE = "pbn_batch_item.cu"
+ITEM_CUBIN = os.path.join(OUT, "pbn_batch_item.cubin")
 CUDA_INC = "/usr/local/cuda/include"
 
 
 def _embed_device_header():
-    """Write the device header as a C++ raw string for the plan compiler."""
-    src = os.path.join(CSRC, "pbn_device.cuh")
-    dst = os.path.join(OUT, "pbn_device_cuh.inc")
-    text = open(src).read()
-    body = 'R"PBNSRC(' + text + ')PBNSRC"\n'
-    if not os.path.exists(dst) or open(dst).read() != body:
-        with open(dst, "w") as f:
-            f.write(body)
+    """Write the device headers as C++ raw strings for the plan and batch compilers."""
+    for name, inc in (("pbn_device.cuh", "pbn_device_cuh.inc"), ("pbn_batch.cuh", "pbn_batch_cuh.inc")):
+        src = os.path.join(CSRC, name)
+        dst = os.path.join(OUT, inc)
+        text = open(src).read()
+        body = 'R"PBNSRC(' + text + ')PBNSRC"\n'
+        if not os.path.exists(dst) or open(dst).read() != body:
+            with open(dst, "w") as f:
+                f.write(body)
 
 
 def _nvcc() -> str:
@@ -74,11 +80,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if force or _newer(o, [s] + hdrs):
             jobs.append([nvcc, "-gencode", GENCODE, "-O3", "-lineinfo", "-std=c++17",
                          "-Xcompiler", "-fPIC", "-Xptxas", "-v", *inc, "-c", s, "-o", o])
+    item = os.path.join(CSRC, ITEM_SOURCE)
+    if force or _newer(ITEM_CUBIN, [item] + hdrs):
+        jobs.append([nvcc, "-arch=sm_103a", "-rdc=true", "-cubin", "-O3", "-lineinfo", "-std=c++17",
+                     "-maxrregcount=128", *inc, item, "-o", ITEM_CUBIN])
     for src in CPP_SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(OUT, src + ".o")
         objs.append(o)
-        if force or _newer(o, [s] + hdrs + [os.path.join(OUT, "pbn_device_cuh.inc")]):
+        if force or _newer(o, [s] + hdrs + [os.path.join(OUT, "pbn_device_cuh.inc"),
+                                            os.path.join(OUT, "pbn_batch_cuh.inc")]):
             jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-Wall", *inc, "-I", CUDA_INC, "-c", s, "-o", o])
     logs = []
     if jobs:

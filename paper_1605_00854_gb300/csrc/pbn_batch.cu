@@ -29,244 +29,34 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
-#include "pbn_device.cuh"
-#include "pbn_interp.cuh"
+#include "pbn_batch_interp.cuh"
 #include "pbn_internal.h"
 
 namespace {
 
-constexpr uint32_t kWeyl0 = 0x9E3779B9u;
-constexpr uint32_t kWeyl1 = 0xBB67AE85u;
-constexpr uint32_t kMetaRows = 16;
+constexpr uint32_t kMetaRows = PBN_BATCH_META_ROWS;
 constexpr uint64_t kSmemCap = 224u * 1024u; /* per-CTA shared memory: one 512-thread CTA per SM, so
                                                  the specs of every network fit in shared memory */
+constexpr int kMaxDevices = 64;
 
-/* Per-network descriptor in device memory (written by the host, read-only). */
-struct alignas(16) NetDesc {
-    const uint8_t* image;
-    uint64_t* state;
-    uint64_t* counts;
-    unsigned long long* pooled;
-    uint64_t traj_begin, step_begin, count_from, seed;
-    uint32_t n_traj, init, stage_bytes, image_bytes;
-    uint32_t smem_state_off, hmax, tables_in_smem, n_meta_rows;
-    uint32_t n, W, W32, n_sel;
-    uint32_t P, off_words, off_groups, off_multi;
-    uint32_t off_selslot, off_thr, off_inputs, off_selblk;
-    uint32_t off_ret, off_pos, off_tables, specs_in_smem;
-    uint32_t nt, off_gorder, n_groups, lg;
-    uint32_t off_subs, per_node, sampler, off_geo;
-    uint64_t geo_full, geo_last;
-    uint32_t off_wgroups, pad0, pad1, pad2;
-    uint32_t meta_row[kMetaRows];
-    uint32_t meta_mask[kMetaRows];
-    uint32_t meta_val[kMetaRows];
-};
+using NetDesc = pbn_netdesc;
+using WorkItem = pbn_workitem;
+using BatchParams = pbn_batch_params;
 
-struct alignas(16) WorkItem {
-    uint32_t net, t0, n, pad;
-};
-
-struct BatchParams {
-    const NetDesc* nets;
-    const WorkItem* items;
-    uint32_t* queue;     /* [2]: next item, CTAs done */
-    uint32_t* status;
-    uint64_t step_offset;
-    uint32_t n_items;
-    uint32_t n_steps;
-};
-
-/* The per-item view pbn_interp_run reads (same field names as the launch
- * parameters of the single-network kernel). */
-struct ItemView {
-    const uint8_t* image;
-    uint64_t* state;
-    uint64_t* counts;
-    uint64_t* trace;
-    uint64_t traj_begin, step_begin;
-    uint32_t key0[10], key1[10];
-    uint32_t n_traj, n_steps, kv0, kp0, pairs, count_first, init;
-    uint32_t n, W, W32, n_sel, P, hmax;
-    uint32_t off_words, off_groups, off_multi, off_selslot, off_thr, off_inputs, off_selblk, off_gorder, off_ret,
-        off_pos, off_tables, n_groups, off_subs, per_node, sampler, off_geo, off_wgroups;
-    uint64_t geo_full, geo_last;
-    uint32_t n_meta_rows;
-    uint32_t trace_stride;
-    const uint32_t* meta_row;
-    const uint32_t* meta_mask;
-    const uint32_t* meta_val;
-};
-
-__device__ __forceinline__ void warp_pool(unsigned long long* pooled, bool lead, const uint32_t c[4], uint32_t pairs) {
-    uint64_t v[5] = {lead ? c[0] : 0u, lead ? (uint64_t)(pairs - c[1] - c[2] - c[3]) : 0u, lead ? c[1] : 0u,
-                     lead ? c[2] : 0u, lead ? c[3] : 0u};
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], o);
-    }
-    if ((threadIdx.x & 31u) == 0 && pooled) {
-#pragma unroll
-        for (int i = 0; i < 5; ++i)
-            if (v[i]) atomicAdd(pooled + i, (unsigned long long)v[i]);
-    }
-}
-
+/* The batch kernel of the library: every work item runs the interpreter. */
 __global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t item_sh;
     __shared__ uint32_t meta_sh[3 * kMetaRows];
-    if (threadIdx.x == 0) pbn_mbar_init(&bar, 1);
-    __syncthreads();
-    uint32_t phase = 0;
-    uint32_t staged = 0xFFFFFFFFu;
-    bool failed = false;
-    for (;;) {
-        if (threadIdx.x == 0) item_sh = atomicAdd(&B.queue[0], 1u);
-        __syncthreads();
-        const uint32_t it = item_sh;
-        /* the previous item read and wrote shared memory through the generic proxy; the
-         * bulk copies that re-stage it go through the async proxy, so every thread
-         * orders its accesses before them (fence, then the barrier, then the copy) */
-        pbn_fence_proxy_async();
-        __syncthreads(); /* everyone has read item_sh (and finished with the previous plan) */
-        if (it >= B.n_items) break;
-        const WorkItem W = B.items[it];
-        const NetDesc& D = B.nets[W.net];
-        if (W.net != staged) {
-            if (threadIdx.x == 0 && D.stage_bytes) {
-                pbn_mbar_arrive_expect_tx(&bar, D.stage_bytes);
-                for (uint32_t off = 0; off < D.stage_bytes; off += 65536u) {
-                    const uint32_t sz = (D.stage_bytes - off) < 65536u ? (D.stage_bytes - off) : 65536u;
-                    pbn_bulk_g2s(smem + off, D.image + off, sz, &bar);
-                }
-            }
-            if (threadIdx.x < 3 * kMetaRows) {
-                const uint32_t k = threadIdx.x;
-                meta_sh[k] = k < kMetaRows ? D.meta_row[k] : (k < 2 * kMetaRows ? D.meta_mask[k - kMetaRows]
-                                                                                  : D.meta_val[k - 2 * kMetaRows]);
-            }
-            bool ok = true;
-            if (D.stage_bytes) {
-                ok = false;
-                for (uint32_t i = 0; i < (1u << 22); ++i) {
-                    if (pbn_mbar_try_wait(&bar, phase)) { ok = true; break; }
-                    if (i > 64) __nanosleep(128);
-                }
-            }
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            if (D.stage_bytes) phase ^= 1u;
-            staged = W.net;
-        }
-        /* the view of this item */
-        ItemView V;
-        V.image = D.image;
-        V.state = D.state;
-        V.counts = D.counts;
-        V.trace = nullptr;
-        V.trace_stride = 1;
-        V.traj_begin = D.traj_begin;
-        const uint64_t sb = D.step_begin + B.step_offset;
-        V.step_begin = sb;
-        const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32);
-#pragma unroll
-        for (int r = 0; r < 10; ++r) {
-            V.key0[r] = k0 + (uint32_t)r * kWeyl0;
-            V.key1[r] = k1 + (uint32_t)r * kWeyl1;
-        }
-        V.n_traj = D.n_traj;
-        V.n_steps = B.n_steps;
-        const uint64_t cf = D.count_from, ns = B.n_steps;
-        const uint64_t kv0 = cf > sb + 1 ? cf - sb - 1 : 0, kp0 = cf > sb ? cf - sb : 0;
-        V.kv0 = (uint32_t)(kv0 < ns ? kv0 : ns);
-        V.kp0 = (uint32_t)(kp0 < ns ? kp0 : ns);
-        V.pairs = (uint32_t)(ns - V.kp0);
-        V.count_first = sb == cf ? 1u : 0u;
-        V.init = (B.step_offset == 0) ? D.init : 1u;
-        V.n = D.n;
-        V.W = D.W;
-        V.W32 = D.W32;
-        V.n_sel = D.n_sel;
-        V.P = D.P;
-        V.hmax = D.hmax;
-        V.off_words = D.off_words;
-        V.off_groups = D.off_groups;
-        V.off_multi = D.off_multi;
-        V.off_selslot = D.off_selslot;
-        V.off_gorder = D.off_gorder;
-        V.off_wgroups = D.off_wgroups;
-        V.off_subs = D.off_subs;
-        V.per_node = D.per_node;
-        V.sampler = D.sampler;
-        V.off_geo = D.off_geo;
-        V.geo_full = D.geo_full;
-        V.geo_last = D.geo_last;
-        V.n_groups = D.n_groups;
-        V.off_thr = D.off_thr;
-        V.off_inputs = D.off_inputs;
-        V.off_selblk = D.off_selblk;
-        V.off_ret = D.off_ret;
-        V.off_pos = D.off_pos;
-        V.off_tables = D.off_tables;
-        V.n_meta_rows = D.n_meta_rows;
-        V.meta_row = meta_sh;
-        V.meta_mask = meta_sh + kMetaRows;
-        V.meta_val = meta_sh + 2 * kMetaRows;
-        /* D.lg lanes per trajectory, D.nt trajectory slots per item */
-        const uint32_t lg = D.lg;
-        const uint32_t slot = threadIdx.x / lg;
-        const uint32_t lane = threadIdx.x % lg;
-        const bool active = slot < W.n;
-        const uint64_t lt = (uint64_t)W.t0 + slot;
-        uint32_t c[4] = {0, 0, 0, 0};
-        if (!D.specs_in_smem) {
-            pbn_interp_run<1, false, false, false>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c);
-        } else if (D.tables_in_smem) {
-            switch (lg) {
-                case 1: pbn_interp_run<1, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 2: pbn_interp_run<2, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 4: pbn_interp_run<4, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 8: pbn_interp_run<8, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 16: pbn_interp_run<16, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                default: pbn_interp_run<32, false, true, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-            }
-        } else {
-            switch (lg) {
-                case 1: pbn_interp_run<1, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 2: pbn_interp_run<2, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 4: pbn_interp_run<4, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 8: pbn_interp_run<8, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                case 16: pbn_interp_run<16, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-                default: pbn_interp_run<32, false, false, true>(V, smem, D.smem_state_off, D.nt, slot, lane, lt, active, c); break;
-            }
-        }
-        warp_pool(D.pooled, active && lane == 0, c, V.pairs);
-    }
-    if (failed) {
-        for (uint32_t i = 0; i < (1u << 22); ++i) /* let copies in flight land */
-            if (pbn_mbar_try_wait(&bar, phase)) break;
-        if (threadIdx.x == 0 && B.status) atomicOr(B.status, PBN_DEV_STAGE_TIMEOUT);
-    }
-    /* the last CTA out resets the queue for the next launch */
-    if (threadIdx.x == 0) {
-        __threadfence();
-        const uint32_t done = atomicAdd(&B.queue[1], 1u);
-        if (done == gridDim.x - 1) {
-            atomicExch(&B.queue[0], 0u);
-            atomicExch(&B.queue[1], 0u);
-            __threadfence();
-        }
-    }
+    pbn_batch_loop(B, smem, &bar, &item_sh, meta_sh,
+                   [&](const WorkItem& W, const NetDesc& D, const uint32_t* ms, uint32_t c[4]) -> bool {
+                       return pbn_batch_interp_run(B.step_offset, B.n_steps, W, D, smem, ms, c);
+                   });
 }
-
-constexpr int kMaxDevices = 64;
 
 }  // namespace
 
@@ -275,7 +65,13 @@ struct pbn_batch {
     std::vector<NetDesc> nets;
     std::vector<WorkItem> items;
     std::vector<uint8_t> image; /* nets then items */
+    std::vector<const pbn_plan*> plans;
     uint32_t threads = 512;
+    /* batch module (pbn_batch_compile): compiled networks' functions and the
+     * dispatching persistent kernel, or null (the library's interpreter kernel) */
+    void* module = nullptr;
+    void* module_kernel = nullptr;
+    ~pbn_batch() { pbn::jit_library_unload(module); }
     /* CTAs of the batch kernel per SM and the SM count, per device, found on the first
      * run on that device (so that later launches can be graph-captured) */
     mutable std::mutex mu;
@@ -402,6 +198,57 @@ int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D)
 
 }  // namespace
 
+namespace {
+/* Interpreted work is costed at this many times a compiled network's per trajectory
+ * and step when the items are ordered (the interpreter ran the paper-scale plan
+ * about 3.6x slower than its compiled kernel). */
+constexpr double kInterpCost = 3.0;
+
+/* Cut every network into work items of its descriptor's trajectory slots, order them
+ * by descending estimated work (largest processing time first, so that the
+ * persistent CTAs finish together) and lay out the device table. */
+void cut_items(pbn_batch* B) {
+    const uint32_t n_nets = (uint32_t)B->nets.size();
+    std::vector<double> cost(n_nets);
+    uint64_t smem_max = 0;
+    uint32_t max_lanes = 1, n_compiled = 0;
+    double ops = 0;
+    B->items.clear();
+    for (uint32_t i = 0; i < n_nets; ++i) {
+        const NetDesc& D = B->nets[i];
+        const pbn_plan* plan = B->plans[i];
+        cost[i] = plan->info.ops_per_step * (D.compiled ? 1.0 : kInterpCost);
+        ops += plan->info.ops_per_step * (double)D.n_traj;
+        if (D.compiled) {
+            ++n_compiled;
+            smem_max = std::max<uint64_t>(smem_max, D.stage_bytes);
+        } else {
+            max_lanes = std::max(max_lanes, D.lg);
+            smem_max = std::max<uint64_t>(smem_max, D.smem_state_off + (uint64_t)plan->per_traj_smem * D.nt);
+        }
+        for (uint64_t t0 = 0; t0 < D.n_traj; t0 += D.nt) {
+            WorkItem w{i, (uint32_t)t0, (uint32_t)std::min<uint64_t>(D.nt, D.n_traj - t0), 0u};
+            B->items.push_back(w);
+        }
+    }
+    std::stable_sort(B->items.begin(), B->items.end(), [&](const WorkItem& x, const WorkItem& y) {
+        return cost[x.net] * x.n > cost[y.net] * y.n;
+    });
+    B->info.n_nets = n_nets;
+    B->info.n_items = (uint32_t)B->items.size();
+    B->info.smem_bytes = smem_max;
+    B->info.threads = B->threads;
+    B->info.max_lanes = max_lanes;
+    B->info.est_ops_per_step = ops;
+    B->info.n_compiled = n_compiled;
+    const size_t nb = B->nets.size() * sizeof(NetDesc), ib = B->items.size() * sizeof(WorkItem);
+    B->image.resize(nb + ib);
+    memcpy(B->image.data(), B->nets.data(), nb);
+    memcpy(B->image.data() + nb, B->items.data(), ib);
+    B->info.desc_bytes = B->image.size();
+}
+}  // namespace
+
 extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out) {
     using pbn::fail;
     if (!nets || !out || n_nets == 0) return fail(PBN_EINVAL, "pbn_batch_create: need networks");
@@ -409,44 +256,85 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
     try {
         std::unique_ptr<pbn_batch> B(new pbn_batch());
         const uint32_t T = B->threads;
-        uint64_t smem_max = 0;
-        uint32_t max_lanes = 1;
-        std::vector<double> cost_per_traj(n_nets);
         for (uint32_t i = 0; i < n_nets; ++i) {
             const pbn_batch_net& a = nets[i];
             NetDesc D;
             const int rc = describe_network(a, i, T, &D);
             if (rc != PBN_OK) return rc;
-            max_lanes = std::max(max_lanes, D.lg);
-            smem_max = std::max<uint64_t>(smem_max, D.smem_state_off + (uint64_t)a.plan->per_traj_smem * D.nt);
-            cost_per_traj[i] = a.plan->info.ops_per_step;
             B->nets.push_back(D);
-            for (uint64_t t0 = 0; t0 < a.n_traj; t0 += D.nt) {
-                WorkItem w{i, (uint32_t)t0, (uint32_t)std::min<uint64_t>(D.nt, a.n_traj - t0), 0u};
-                B->items.push_back(w);
-            }
+            B->plans.push_back(a.plan);
         }
-        /* largest estimated work first */
-        std::stable_sort(B->items.begin(), B->items.end(), [&](const WorkItem& x, const WorkItem& y) {
-            return cost_per_traj[x.net] * x.n > cost_per_traj[y.net] * y.n;
-        });
-        B->info.n_nets = n_nets;
-        B->info.n_items = (uint32_t)B->items.size();
-        B->info.smem_bytes = smem_max;
-        B->info.threads = T;
-        B->info.max_lanes = max_lanes;
-        double ops = 0;
-        for (uint32_t i = 0; i < n_nets; ++i) ops += cost_per_traj[i] * (double)nets[i].n_traj;
-        B->info.est_ops_per_step = ops;
-        const size_t nb = B->nets.size() * sizeof(NetDesc), ib = B->items.size() * sizeof(WorkItem);
-        B->image.resize(nb + ib);
-        memcpy(B->image.data(), B->nets.data(), nb);
-        memcpy(B->image.data() + nb, B->items.data(), ib);
-        B->info.desc_bytes = B->image.size();
+        cut_items(B.get());
         *out = B.release();
         return PBN_OK;
     } catch (const std::bad_alloc&) {
         return fail(PBN_ENOMEM, "pbn_batch_create: out of memory");
+    }
+}
+
+extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_ms) {
+    using pbn::fail;
+    if (!b) return fail(PBN_EINVAL, "pbn_batch_compile: NULL batch");
+    if (b->module) return fail(PBN_EINVAL, "pbn_batch_compile: the batch is compiled already");
+    if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_WIDE))
+        return fail(PBN_EINVAL, "pbn_batch_compile: unsupported flags 0x%x", flags);
+    try {
+        std::vector<std::string> functions;
+        std::string first_why;
+        std::vector<uint32_t> compiled;
+        std::vector<uint32_t> tab(b->nets.size(), 0);
+        for (uint32_t i = 0; i < (uint32_t)b->nets.size(); ++i) {
+            const NetDesc& D = b->nets[i];
+            pbn::JitBatchNet spec;
+            spec.index = i;
+            spec.seed = D.seed;
+            spec.meta.n_rows = D.n_meta_rows;
+            for (uint32_t m = 0; m < D.n_meta_rows; ++m) {
+                spec.meta.row[m] = D.meta_row[m];
+                spec.meta.mask[m] = D.meta_mask[m];
+                spec.meta.val[m] = D.meta_val[m];
+            }
+            std::string fn, why;
+            if (pbn::jit_batch_function(b->plans[i], flags, spec, &fn, &tab[i], &why)) {
+                functions.push_back(std::move(fn));
+                compiled.push_back(i);
+            } else if (first_why.empty()) {
+                first_why = why;
+            }
+        }
+        if (compiled.empty())
+            return fail(PBN_EINVAL, "pbn_batch_compile: no network of the batch compiles (%s)", first_why.c_str());
+        const bool interp = compiled.size() < b->nets.size();
+        void *lib = nullptr, *kern = nullptr;
+        double ms = 0;
+        std::string log;
+        const int rc = pbn::jit_batch_module(functions, compiled, interp, b->threads, &lib, &kern, &ms, &log);
+        if (rc != PBN_OK) return rc;
+        /* compiled networks: one trajectory per thread, their tables (when the code
+         * reads them from shared memory) staged from the plan image */
+        for (uint32_t i : compiled) {
+            NetDesc& D = b->nets[i];
+            D.compiled = 1;
+            D.lg = 1;
+            D.nt = b->threads;
+            D.specs_in_smem = 0;
+            D.tables_in_smem = tab[i] ? 1u : 0u;
+            D.stage_bytes = tab[i];
+            D.stage_off = tab[i] ? D.off_tables : 0u;
+            D.smem_state_off = 0;
+        }
+        cut_items(b);
+        b->module = lib;
+        b->module_kernel = kern;
+        {
+            /* a new kernel: its occupancy is found again on each device */
+            std::lock_guard<std::mutex> g(b->mu);
+            for (int d = 0; d < kMaxDevices; ++d) b->occ_per_sm[d] = b->sms[d] = 0;
+        }
+        if (compile_ms) *compile_ms = ms;
+        return PBN_OK;
+    } catch (const std::bad_alloc&) {
+        return fail(PBN_ENOMEM, "pbn_batch_compile: out of memory");
     }
 }
 
@@ -466,6 +354,16 @@ extern "C" int pbn_batch_image(const pbn_batch* b, void* dst, size_t cap) {
 }
 
 namespace {
+/* The batch's kernel: its compiled module's dispatcher, or the library's. */
+const void* batch_kernel(const pbn_batch* b) {
+    return b->module_kernel ? b->module_kernel : reinterpret_cast<const void*>(pbn_batch_kernel);
+}
+
+cudaError_t launch_batch(const pbn_batch* b, const BatchParams& P, uint32_t grid, cudaStream_t st) {
+    void* args[] = {const_cast<BatchParams*>(&P)};
+    return cudaLaunchKernel(batch_kernel(b), dim3(grid), dim3(b->threads), args, b->info.smem_bytes, st);
+}
+
 /* Grid of the batch kernel on the current device: raises the kernel's shared-memory
  * limit there to the batch's need (never lowering what another batch set), and finds
  * the CTAs per SM and the SM count of that device on the batch's first run on it. */
@@ -476,14 +374,15 @@ int launch_shape(const pbn_batch* b, uint32_t ctas_per_sm, const char* who, uint
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(PBN_EINVAL, "%s: device %d beyond %d", who, dev, kMaxDevices);
-    const int se = pbn::ensure_dyn_smem(reinterpret_cast<const void*>(pbn_batch_kernel), smem);
+    const void* kern = batch_kernel(b);
+    const int se = pbn::ensure_dyn_smem(kern, smem);
     if (se != 0) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(static_cast<cudaError_t>(se)));
     int per_sm = 0, sms = 0;
     {
         std::lock_guard<std::mutex> g(b->mu);
         if (!b->occ_per_sm[dev]) {
             int occ = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pbn_batch_kernel, (int)b->threads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)b->threads, smem);
             if (e != cudaSuccess || occ < 1) return fail(PBN_ETOOBIG, "%s: the batch kernel does not fit an SM", who);
             b->occ_per_sm[dev] = occ;
             b->sms[dev] = pbn::device_sms();
@@ -513,12 +412,10 @@ extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d
     P.step_offset = step_offset;
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
-    const size_t smem = b->info.smem_bytes;
     uint32_t grid = 0;
     int rc = launch_shape(b, ctas_per_sm, "pbn_batch_run", &grid);
     if (rc != PBN_OK) return rc;
-    pbn_batch_kernel<<<grid, b->threads, smem, static_cast<cudaStream_t>(stream)>>>(P);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_batch(b, P, grid, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
     return PBN_OK;
 }
@@ -583,12 +480,10 @@ extern "C" int pbn_batch_run_static(const pbn_batch* b, const void* d_desc, uint
     P.step_offset = step_offset;
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
-    const size_t smem = b->info.smem_bytes;
     uint32_t grid = 0;
     const int rc = launch_shape(b, ctas_per_sm, "pbn_batch_run_static", &grid);
     if (rc != PBN_OK) return rc;
-    pbn_batch_kernel<<<grid, b->threads, smem, st>>>(P);
-    e = cudaGetLastError();
+    e = launch_batch(b, P, grid, st);
     if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
     return PBN_OK;
 }

@@ -75,19 +75,20 @@ struct pbn_item_window {
     uint32_t n_steps, kv0, kp0, pairs, count_first, init;
 };
 
-__device__ __forceinline__ pbn_item_window pbn_item_window_of(const pbn_netdesc& D, const pbn_batch_params& B) {
+__device__ __forceinline__ pbn_item_window pbn_item_window_at(const pbn_netdesc& D, uint64_t step_offset,
+                                                             uint32_t n_steps) {
     pbn_item_window w;
-    const uint64_t sb = D.step_begin + B.step_offset;
+    const uint64_t sb = D.step_begin + step_offset;
     w.step_begin = sb;
-    w.n_steps = B.n_steps;
+    w.n_steps = n_steps;
     /* state s(u) counted iff u >= count_from; pair (s(t), s(t+1)) iff t >= count_from */
-    const uint64_t cf = D.count_from, ns = B.n_steps;
+    const uint64_t cf = D.count_from, ns = n_steps;
     const uint64_t kv0 = cf > sb + 1 ? cf - sb - 1 : 0, kp0 = cf > sb ? cf - sb : 0;
     w.kv0 = (uint32_t)(kv0 < ns ? kv0 : ns);
     w.kp0 = (uint32_t)(kp0 < ns ? kp0 : ns);
     w.pairs = (uint32_t)(ns - w.kp0);
     w.count_first = sb == cf ? 1u : 0u;
-    w.init = (B.step_offset == 0) ? D.init : 1u;
+    w.init = (step_offset == 0) ? D.init : 1u;
     return w;
 }
 
@@ -167,7 +168,7 @@ __device__ __forceinline__ void pbn_batch_loop(const pbn_batch_params& B, uint8_
         }
         uint32_t c[4] = {0, 0, 0, 0};
         const bool lead = run(W, D, meta_sh, c);
-        pbn_warp_pool(D.pooled, lead, c, pbn_item_window_of(D, B).pairs);
+        pbn_warp_pool(D.pooled, lead, c, pbn_item_window_at(D, B.step_offset, B.n_steps).pairs);
     }
     if (failed) {
         for (uint32_t i = 0; i < (1u << 22); ++i) /* let copies in flight land */

@@ -32,10 +32,11 @@ struct pbn_item_view {
     const uint32_t* meta_val;
 };
 
-/* Run work item W of network D with the interpreter (the network's image staged at
- * the start of smem as D's staging mode says); c[] receives the counts of the
- * trajectory this thread leads; returns whether it leads one. */
-__device__ __forceinline__ bool pbn_batch_interp_run(const pbn_batch_params& B, const pbn_workitem& W,
+/* Run work item W of network D with the interpreter for n_steps steps from the
+ * network's step_begin + step_offset (the network's image staged at the start of
+ * smem as D's staging mode says); c[] receives the counts of the trajectory this
+ * thread leads; returns whether it leads one. */
+__device__ __forceinline__ bool pbn_batch_interp_run(uint64_t step_offset, uint32_t n_steps, const pbn_workitem& W,
                                                      const pbn_netdesc& D, uint8_t* smem, const uint32_t* meta_sh,
                                                      uint32_t c[4]) {
     pbn_item_view V;
@@ -45,7 +46,7 @@ __device__ __forceinline__ bool pbn_batch_interp_run(const pbn_batch_params& B, 
     V.trace = nullptr;
     V.trace_stride = 1;
     V.traj_begin = D.traj_begin;
-    const pbn_item_window w = pbn_item_window_of(D, B);
+    const pbn_item_window w = pbn_item_window_at(D, step_offset, n_steps);
     V.step_begin = w.step_begin;
     const uint32_t k0 = (uint32_t)D.seed, k1 = (uint32_t)(D.seed >> 32);
 #pragma unroll

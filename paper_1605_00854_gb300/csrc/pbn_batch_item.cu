@@ -7,9 +7,9 @@
  */
 #include "pbn_batch_interp.cuh"
 
-extern "C" __device__ bool pbn_batch_interp_item(const pbn_batch_params* B, const pbn_workitem* W,
+extern "C" __device__ bool pbn_batch_interp_item(uint64_t step_offset, uint32_t n_steps, const pbn_workitem* W,
                                                  const pbn_netdesc* D, const uint32_t* meta_sh, uint32_t* c) {
     /* the kernel's dynamic shared memory (the staged image and trajectory rows) */
     extern __shared__ __align__(128) uint8_t pbn_item_smem[];
-    return pbn_batch_interp_run(*B, *W, *D, pbn_item_smem, meta_sh, c);
+    return pbn_batch_interp_run(step_offset, n_steps, *W, *D, pbn_item_smem, meta_sh, c);
 }

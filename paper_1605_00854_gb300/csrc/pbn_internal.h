@@ -62,6 +62,28 @@ int jit_compile(const pbn_plan* plan, uint32_t flags);
 bool jit_ready(const pbn_plan* plan);
 uint32_t jit_current_flags(const pbn_plan* plan); /* flags of the compiled kernel, else 0 */
 
+/* Compiled networks of a batch (pbn_jit.cpp): what a network fixes at generation
+ * time, its device function, and the batch module of such functions and the
+ * persistent dispatcher kernel. */
+struct JitBatchNet {
+    uint32_t index = 0;  /* position in the batch: the function is pbn_net_<index> */
+    uint64_t seed = 0;   /* Philox key of the network's draws */
+    MetaRows meta;       /* the network's meta-state rows */
+};
+/* Source of network `spec.index`'s work-item function and the bytes of its tables to
+ * stage into shared memory (0: read from the plan image); false, with the reason,
+ * if the plan does not compile with these flags. */
+bool jit_batch_function(const pbn_plan* plan, uint32_t flags, const JitBatchNet& spec, std::string* src,
+                        uint32_t* tab_bytes, std::string* why);
+/* Compile the module of `functions` (one per network in `compiled`, in parallel
+ * relocatable units) and a persistent kernel of `threads` threads per CTA dispatching
+ * work items to pbn_net_<i> and, when `interp`, to the interpreter's relocatable
+ * work-item function; link them with nvJitLink and load the result.
+ * Errors: PBN_ECUDA (NVRTC, nvJitLink or loading failed; *log holds the reason). */
+int jit_batch_module(const std::vector<std::string>& functions, const std::vector<uint32_t>& compiled, bool interp,
+                     uint32_t threads, void** library, void** kernel, double* ms, std::string* log);
+void jit_library_unload(void* library);
+
 /* Launch facts of the current device, queried once per device (thread-safe). */
 int device_sms();         /* SM count */
 int device_smem_optin();  /* opt-in dynamic shared memory per block, bytes */

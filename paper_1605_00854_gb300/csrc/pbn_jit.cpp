@@ -25,10 +25,12 @@
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "pbn_device.cuh"
@@ -190,13 +192,19 @@ struct Generated {
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
 };
 
+using BatchSpec = pbn::JitBatchNet;
+
 /* The CUDA source of one plan's kernel.  The plan image is read on the host: every
  * gather, threshold, perturbation level and small table becomes an immediate, and
- * the step loop is emitted in the code shape the flags select. */
+ * the step loop is emitted in the code shape the flags select.  With a BatchSpec the
+ * same step loop becomes a device function of a batch module (one work item of the
+ * network: one trajectory per thread), with the Philox keys and the meta-state as
+ * constants too. */
 class KernelSource {
 public:
-    KernelSource(const pbn_plan& plan, uint32_t flags)
-        : H(plan.hdr), V{&plan.hdr, plan.image.data()}, flags_(flags), wide((flags & PBN_COMPILE_WIDE) != 0) {}
+    KernelSource(const pbn_plan& plan, uint32_t flags, const BatchSpec* bs = nullptr)
+        : H(plan.hdr), V{&plan.hdr, plan.image.data()}, flags_(bs ? (flags & ~(uint32_t)PBN_COMPILE_MAGIC_GATHER) : flags),
+          wide((flags & PBN_COMPILE_WIDE) != 0), bs_(bs), sfx_(bs ? "_" + std::to_string(bs->index) : std::string()) {}
 
     bool generate(Generated* out, std::string* why) {
         if (!fits(why)) return false;
@@ -244,6 +252,8 @@ private:
     const uint32_t flags_;
     const bool wide; /* SEL blocks drawn lazily in group order: their uniforms live only
                         while the groups that need them are evaluated */
+    const BatchSpec* bs_; /* batch-module function instead of a kernel */
+    const std::string sfx_; /* suffix of the module-level names (unique per network) */
     const uint2* words = nullptr;
     const pbn_img_group* groups = nullptr;
     const pbn_img_multi* multi = nullptr;
@@ -379,10 +389,10 @@ private:
 
     /* the geometric sampler's thresholds and the rebuilt tables, as __device__ arrays */
     void emit_globals() {
-        o << "#include \"pbn_device.cuh\"\n";
+        if (!bs_) o << "#include \"pbn_device.cuh\"\n";
         if (H.sampler == PBN_PERT_GEOMETRIC) {
             const uint64_t* G = V.at<uint64_t>(H.off_geo);
-            o << "__device__ const unsigned long long GEO_T[64] = {";
+            o << "__device__ const unsigned long long GEO_T" << sfx_ << "[64] = {";
             for (int k = 0; k < 64; ++k) o << (k ? ", " : "") << fmt("0x%016llxull", (unsigned long long)G[k]);
             o << "};\n";
         }
@@ -397,6 +407,7 @@ private:
     /* kernel entry, table staging, the initial state (keyed INIT draws or the stored
      * state) and the meta-state indicator of s(step_begin) */
     void emit_prologue() {
+        if (bs_) return emit_batch_prologue();
         const char* tab_src = magic ? "reinterpret_cast<const uint8_t*>(TABM)" : "P.image + P.off_tables";
         o << "extern \"C\" __global__ void __launch_bounds__(512) pbn_plan_kernel(const pbn_jit_params P) {\n";
         o << "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n";
@@ -408,8 +419,44 @@ private:
             o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(" << tab_src << ");\n";
         }
         o << "  const uint32_t lt = blockIdx.x * blockDim.x + threadIdx.x;\n"
-             "  const bool active = lt < P.n_traj;\n"
-             "  const uint64_t traj = P.traj_begin + lt;\n"
+             "  const bool active = lt < P.n_traj;\n";
+        emit_initial_state();
+    }
+
+    /* Batch-module function of one work item: the launch fields come from the
+     * network's descriptor and the launch, the keys are literals (immediates once the
+     * aggregate is scalarised), the tables are read from the staged shared memory or
+     * the plan image, one trajectory per thread of the item. */
+    void emit_batch_prologue() {
+        const uint64_t seed = bs_->seed;
+        const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+        o << "extern \"C\" __device__ __noinline__ bool pbn_net" << sfx_
+          << "(const pbn_netdesc& D, const pbn_workitem W, const uint64_t step_offset, const uint32_t n_steps, "
+             "uint32_t* cnt) {\n";
+        o << "  extern __shared__ __align__(128) uint8_t smem[];\n";
+        o << "  const pbn_item_window w = pbn_item_window_at(D, step_offset, n_steps);\n";
+        o << "  struct PV { uint32_t key0[10], key1[10]; uint64_t* state; uint64_t* counts; uint64_t* trace;\n"
+             "    uint32_t trace_stride; uint64_t traj_begin, step_begin;\n"
+             "    uint32_t n_traj, n_steps, kv0, kp0, pairs, count_first, init; };\n";
+        o << "  const PV P = {{";
+        for (int r = 0; r < 10; ++r) o << (r ? ", " : "") << hex32(k0 + (uint32_t)r * 0x9E3779B9u);
+        o << "}, {";
+        for (int r = 0; r < 10; ++r) o << (r ? ", " : "") << hex32(k1 + (uint32_t)r * 0xBB67AE85u);
+        o << "},\n    D.state, D.counts, nullptr, 1u, D.traj_begin, w.step_begin,\n"
+             "    D.n_traj, w.n_steps, w.kv0, w.kp0, w.pairs, w.count_first, w.init};\n";
+        if (tab_smem) o << "  const uint32_t* TAB = reinterpret_cast<const uint32_t*>(smem);\n";
+        else
+            o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(D.image + " << H.off_tables
+              << "u);\n";
+        o << "  const uint32_t lt = W.t0 + threadIdx.x;\n"
+             "  const bool active = threadIdx.x < W.n;\n";
+        emit_initial_state();
+    }
+
+    /* the counters, the initial state (keyed INIT draws or the stored state) and the
+     * meta-state indicator of s(step_begin) */
+    void emit_initial_state() {
+        o << "  const uint64_t traj = P.traj_begin + lt;\n"
              "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n";
         o << "  uint32_t";
         for (uint32_t r = 0; r < H.W32; ++r) o << (r ? ", " : " ") << "s" << r << " = 0";
@@ -438,8 +485,17 @@ private:
         o << "    }\n";
         std::ostringstream zs;
         zs << "(";
-        for (uint32_t r = 0; r < H.W32; ++r)
-            zs << (r ? " & " : "") << "(uint32_t)((s" << r << " & P.meta_mask[" << r << "]) == P.meta_val[" << r << "])";
+        if (bs_) {
+            /* the network's meta-state rows as immediates */
+            for (uint32_t m = 0; m < bs_->meta.n_rows; ++m)
+                zs << (m ? " & " : "") << "(uint32_t)((s" << bs_->meta.row[m] << " & " << hex32(bs_->meta.mask[m])
+                   << ") == " << hex32(bs_->meta.val[m]) << ")";
+            if (!bs_->meta.n_rows) zs << "1u";
+        } else {
+            for (uint32_t r = 0; r < H.W32; ++r)
+                zs << (r ? " & " : "") << "(uint32_t)((s" << r << " & P.meta_mask[" << r << "]) == P.meta_val[" << r
+                   << "])";
+        }
         zs << ")";
         z = zs.str();
         o << "    uint32_t zp = " << z << ";\n    if (P.count_first) cV += zp;\n";
@@ -755,8 +811,8 @@ private:
                   << fmt("          if (U < 0x%016llxull) {\n", (unsigned long long)G[L - 1])
                   << "            uint32_t pl = 0, ph = 0, pos = 0, j = 0;\n"
                   << "            for (;;) {\n"
-                  << fmt("              if (U >= GEO_T[%uu - pos - 1]) break;\n", L)
-                  << "              uint32_t k = 0;\n              while (U >= GEO_T[k]) ++k;\n"
+                  << fmt("              if (U >= GEO_T%s[%uu - pos - 1]) break;\n", sfx_.c_str(), L)
+                  << "              uint32_t k = 0;\n              while (U >= GEO_T" << sfx_ << "[k]) ++k;\n"
                   << "              const uint32_t b = pos + k;\n"
                   << "              if (b < 32) pl |= 1u << b; else ph |= 1u << (b - 32);\n"
                   << fmt("              pos = b + 1;\n              if (pos >= %uu) break;\n", L)
@@ -849,6 +905,18 @@ private:
 
     /* the state and counts written back, pooled counts reduced per warp */
     void emit_epilogue() {
+        if (bs_) {
+            for (uint32_t r = 0; r < H.W32; r += 2)
+                o << "    P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt] = ((uint64_t)s" << r + 1 << " << 32) | s" << r
+                  << ";\n";
+            o << "    if (P.counts) {\n"
+                 "      const uint64_t nt = P.n_traj;\n"
+                 "      P.counts[lt] += cV; P.counts[nt + lt] += P.pairs - c01 - c10 - c11;\n"
+                 "      P.counts[2 * nt + lt] += c01; P.counts[3 * nt + lt] += c10; P.counts[4 * nt + lt] += c11;\n"
+                 "    }\n  }\n";
+            o << "  cnt[0] = cV; cnt[1] = c01; cnt[2] = c10; cnt[3] = c11;\n  return active;\n}\n";
+            return;
+        }
         for (uint32_t r = 0; r < H.W32; r += 2)
             o << "    P.state[(uint64_t)" << r / 2 << " * P.n_traj + lt] = ((uint64_t)s" << r + 1 << " << 32) | s" << r << ";\n";
         o << "    if (P.counts) {\n"
@@ -872,7 +940,254 @@ bool generate(const pbn_plan& plan, uint32_t flags, Generated* out, std::string*
     return ks.generate(out, why);
 }
 
+const char kBatchHeader[] =
+#include "pbn_batch_cuh.inc"
+    ;
+
+/* ---- nvJitLink, loaded on first use ----------------------------------------------------- */
+typedef struct _nvJitLinkHandle* nvJitLinkHandle_t;
+struct JitLink {
+    int (*create)(nvJitLinkHandle_t*, uint32_t, const char**);
+    int (*destroy)(nvJitLinkHandle_t*);
+    int (*add_data)(nvJitLinkHandle_t, int, const void*, size_t, const char*);
+    int (*complete)(nvJitLinkHandle_t);
+    int (*cubin_size)(nvJitLinkHandle_t, size_t*);
+    int (*cubin)(nvJitLinkHandle_t, void*);
+    int (*log_size)(nvJitLinkHandle_t, size_t*);
+    int (*log)(nvJitLinkHandle_t, char*);
+    bool ok = false;
+    std::string err;
+};
+
+JitLink& jitlink() {
+    static JitLink N;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char* names[] = {"libnvJitLink.so.13", "libnvJitLink.so", "/usr/local/cuda/lib64/libnvJitLink.so.13",
+                               "/usr/local/cuda/lib64/libnvJitLink.so"};
+        void* h = nullptr;
+        for (const char* nm : names)
+            if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+        if (!h) {
+            N.err = "libnvJitLink not found";
+            return;
+        }
+        /* the library exports versioned names (the header maps the plain ones to them) */
+        auto sym = [&](const char* base) -> void* {
+            void* p = dlsym(h, (std::string("__") + base + "_13_0").c_str());
+            return p ? p : dlsym(h, base);
+        };
+#define PBN_LSYM(field, name)                                     \
+    *reinterpret_cast<void**>(&N.field) = sym(name);              \
+    if (!N.field) {                                               \
+        N.err = std::string("libnvJitLink lacks ") + name;        \
+        return;                                                   \
+    }
+        PBN_LSYM(create, "nvJitLinkCreate");
+        PBN_LSYM(destroy, "nvJitLinkDestroy");
+        PBN_LSYM(add_data, "nvJitLinkAddData");
+        PBN_LSYM(complete, "nvJitLinkComplete");
+        PBN_LSYM(cubin_size, "nvJitLinkGetLinkedCubinSize");
+        PBN_LSYM(cubin, "nvJitLinkGetLinkedCubin");
+        PBN_LSYM(log_size, "nvJitLinkGetErrorLogSize");
+        PBN_LSYM(log, "nvJitLinkGetErrorLog");
+#undef PBN_LSYM
+        N.ok = true;
+    });
+    return N;
+}
+
+/* The interpreter's relocatable work-item function, built with the library into the
+ * same directory (pbn_batch_item.cubin). */
+bool read_item_cubin(std::vector<char>* out, std::string* why) {
+    Dl_info di;
+    if (!dladdr(reinterpret_cast<void*>(&read_item_cubin), &di) || !di.dli_fname) {
+        *why = "cannot locate the library's directory";
+        return false;
+    }
+    std::string path(di.dli_fname);
+    const size_t cut = path.find_last_of('/');
+    path = (cut == std::string::npos ? std::string(".") : path.substr(0, cut)) + "/pbn_batch_item.cubin";
+    FILE* f = fopen(path.c_str(), "rb");
+    if (!f) {
+        *why = "missing " + path;
+        return false;
+    }
+    fseek(f, 0, SEEK_END);
+    const long sz = ftell(f);
+    fseek(f, 0, SEEK_SET);
+    out->resize(sz > 0 ? (size_t)sz : 0);
+    const bool ok = sz > 0 && fread(out->data(), 1, (size_t)sz, f) == (size_t)sz;
+    fclose(f);
+    if (!ok) *why = "cannot read " + path;
+    return ok;
+}
+
 }  // namespace
+
+namespace pbn {
+
+bool jit_batch_function(const pbn_plan* plan, uint32_t flags, const JitBatchNet& spec, std::string* src,
+                        uint32_t* tab_bytes, std::string* why) {
+    KernelSource ks(*plan, flags, &spec);
+    Generated gen;
+    if (!ks.generate(&gen, why)) return false;
+    *src = std::move(gen.src);
+    *tab_bytes = gen.tab_bytes;
+    return true;
+}
+
+namespace {
+/* NVRTC compile of one program of the batch module (relocatable when `rdc`). */
+bool nvrtc_cubin(const std::string& src, const char* name, bool rdc, std::vector<char>* cubin, std::string* log) {
+    Nvrtc& N = nvrtc();
+    nvrtcProgram_t prog = nullptr;
+    const char* hdrs[] = {kDeviceHeader, kBatchHeader};
+    const char* hnames[] = {"pbn_device.cuh", "pbn_batch.cuh"};
+    if (N.create(&prog, src.c_str(), name, 2, hdrs, hnames) != 0) {
+        *log = "nvrtcCreateProgram failed";
+        return false;
+    }
+    std::vector<const char*> opts = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "--maxrregcount=128"};
+    if (rdc) opts.push_back("--relocatable-device-code=true");
+    const int rc = N.compile(prog, (int)opts.size(), opts.data());
+    size_t ls = 0;
+    N.log_size(prog, &ls);
+    std::string clog(ls, '\0');
+    if (ls) N.log(prog, &clog[0]);
+    if (rc != 0) {
+        N.destroy(&prog);
+        *log = clog;
+        return false;
+    }
+    size_t cs = 0;
+    N.cubin_size(prog, &cs);
+    cubin->resize(cs);
+    N.cubin(prog, cubin->data());
+    N.destroy(&prog);
+    return true;
+}
+}  // namespace
+
+int jit_batch_module(const std::vector<std::string>& functions, const std::vector<uint32_t>& compiled, bool interp,
+                     uint32_t threads, void** library, void** kernel, double* ms, std::string* log) {
+    auto t0 = std::chrono::steady_clock::now();
+    Nvrtc& N = nvrtc();
+    if (!N.ok) {
+        *log = N.err;
+        return fail(PBN_ECUDA, "NVRTC unavailable: %s", N.err.c_str());
+    }
+    /* the dispatching persistent kernel */
+    std::ostringstream o;
+    o << "#include \"pbn_batch.cuh\"\n";
+    for (uint32_t i : compiled)
+        o << "extern \"C\" __device__ bool pbn_net_" << i
+          << "(const pbn_netdesc& D, const pbn_workitem W, const uint64_t step_offset, const uint32_t n_steps, "
+             "uint32_t* cnt);\n";
+    if (interp)
+        o << "extern \"C\" __device__ bool pbn_batch_interp_item(uint64_t step_offset, uint32_t n_steps, "
+             "const pbn_workitem* W, const pbn_netdesc* D, const uint32_t* meta_sh, uint32_t* c);\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", 1) pbn_cbatch_kernel(const pbn_batch_params B) {\n"
+         "  extern __shared__ __align__(128) uint8_t smem[];\n"
+         "  __shared__ __align__(8) uint64_t bar;\n  __shared__ uint32_t item_sh;\n"
+         "  __shared__ uint32_t meta_sh[3 * PBN_BATCH_META_ROWS];\n"
+         "  pbn_batch_loop(B, smem, &bar, &item_sh, meta_sh,\n"
+         "    [&](const pbn_workitem& W, const pbn_netdesc& D, const uint32_t* ms, uint32_t c[4]) -> bool {\n"
+         "      switch (W.net) {\n";
+    for (uint32_t i : compiled) o << "        case " << i << "u: return pbn_net_" << i << "(D, W, B.step_offset, B.n_steps, c);\n";
+    if (interp) o << "        default: return pbn_batch_interp_item(B.step_offset, B.n_steps, &W, &D, ms, c);\n";
+    else o << "        default: return false;\n";
+    o << "      }\n    });\n}\n";
+    /* the network functions in up to `parts` programs compiled in parallel (each a
+     * relocatable unit), then linked with the dispatcher (and the interpreter) */
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t parts = std::min<size_t>(functions.size(), std::min<unsigned>(hw, 32u));
+    std::vector<std::string> srcs(parts + 1);
+    srcs[0] = o.str();
+    for (size_t k = 0; k < functions.size(); ++k) {
+        std::string& dst = srcs[1 + k * parts / functions.size()];
+        if (dst.empty()) dst = "#include \"pbn_batch.cuh\"\n";
+        dst += functions[k];
+    }
+    /* PBN_BATCH_MODULE_DUMP=<path>: write the generated sources there (inspection) */
+    if (const char* dump = getenv("PBN_BATCH_MODULE_DUMP")) {
+        if (FILE* f = fopen(dump, "w")) {
+            for (const std::string& x : srcs) fwrite(x.data(), 1, x.size(), f);
+            fclose(f);
+        }
+    }
+    std::vector<std::vector<char>> cubins(srcs.size());
+    std::vector<std::string> logs(srcs.size());
+    std::vector<char> okv(srcs.size(), 0);
+    {
+        std::vector<std::thread> th;
+        for (size_t k = 0; k < srcs.size(); ++k)
+            th.emplace_back([&, k] {
+                const std::string nm = "pbn_batch_module_" + std::to_string(k) + ".cu";
+                okv[k] = nvrtc_cubin(srcs[k], nm.c_str(), true, &cubins[k], &logs[k]) ? 1 : 0;
+            });
+        for (auto& t : th) t.join();
+    }
+    for (size_t k = 0; k < srcs.size(); ++k)
+        if (!okv[k]) {
+            *log = logs[k];
+            return fail(PBN_ECUDA, "NVRTC compilation of the batch module failed: %.400s", logs[k].c_str());
+        }
+    std::vector<char> item;
+    if (interp) {
+        std::string why;
+        if (!read_item_cubin(&item, &why)) {
+            *log = why;
+            return fail(PBN_ECUDA, "batch module: %s", why.c_str());
+        }
+    }
+    JitLink& L = jitlink();
+    if (!L.ok) {
+        *log = L.err;
+        return fail(PBN_ECUDA, "nvJitLink unavailable: %s", L.err.c_str());
+    }
+    nvJitLinkHandle_t h = nullptr;
+    const char* lopts[] = {"-arch=sm_103a"};
+    int lr = L.create(&h, 1, lopts);
+    const int kCubin = 1; /* NVJITLINK_INPUT_CUBIN */
+    for (size_t k = 0; k < cubins.size() && lr == 0; ++k)
+        lr = L.add_data(h, kCubin, cubins[k].data(), cubins[k].size(), "pbn_batch_module");
+    if (lr == 0 && interp) lr = L.add_data(h, kCubin, item.data(), item.size(), "pbn_batch_item");
+    if (lr == 0) lr = L.complete(h);
+    if (lr != 0) {
+        size_t n = 0;
+        if (h) L.log_size(h, &n);
+        std::string el(n, '\0');
+        if (n) L.log(h, &el[0]);
+        if (h) L.destroy(&h);
+        *log = el;
+        return fail(PBN_ECUDA, "nvJitLink failed (%d): %.400s", lr, el.c_str());
+    }
+    size_t n = 0;
+    L.cubin_size(h, &n);
+    std::vector<char> linked(n);
+    L.cubin(h, linked.data());
+    L.destroy(&h);
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kern = nullptr;
+    cudaError_t e = cudaLibraryLoadData(&lib, linked.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+    if (e == cudaSuccess) e = cudaLibraryGetKernel(&kern, lib, "pbn_cbatch_kernel");
+    if (e != cudaSuccess) {
+        if (lib) cudaLibraryUnload(lib);
+        *log = cudaGetErrorString(e);
+        return fail(PBN_ECUDA, "loading the batch module failed: %s", cudaGetErrorString(e));
+    }
+    *library = lib;
+    *kernel = reinterpret_cast<void*>(kern);
+    if (ms) *ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return PBN_OK;
+}
+
+void jit_library_unload(void* library) {
+    if (library) cudaLibraryUnload(static_cast<cudaLibrary_t>(library));
+}
+
+}  // namespace pbn
 
 /* ---- compiled-plan cache and launch (called from pbn_sim.cu and the C ABI) --------- */
 struct pbn_jit_state {

@@ -764,3 +764,65 @@ def test_device_image_cache_is_per_device():
     m = plan.device_image("meta")
     assert m is not a and m.device.type == "meta" and tuple(m.shape) == tuple(a.shape)
     assert plan.device_image("meta") is m and plan.device_image("cpu") is a
+
+
+# ------------------------------------------------------------ compiled batches ----
+def _fake_batch(sizes, seed=300):
+    """A batch over plans of paper-scale networks of the given sizes with aligned
+    host addresses standing in for device buffers (pbn_batch_create and
+    pbn_batch_compile touch no device memory)."""
+    import ctypes
+    L = _lib.load()
+    buf = np.zeros(1 << 16, dtype=np.uint8)
+    base = (buf.ctypes.data + 255) & ~255
+    keep = [buf]
+    arr = (_lib.BatchNet * len(sizes))()
+    for i, n in enumerate(sizes):
+        text = synth.paper100(seed=seed + i, n=n, p=1e-3).to_text()
+        red, _ = api.Net.load(text).reduce([0, 1, 2])
+        plan = api.Plan(red)
+        mi = np.array([0, 1, 2], dtype=np.uint32)
+        keep += [plan, mi]
+        b = arr[i]
+        b.plan, b.d_image, b.seed, b.n_traj, b.init = plan._h, base, 11 + i, 700, 0
+        b.n_meta, b.meta_ids = 3, mi.ctypes.data
+        b.d_state = b.d_counts = b.d_pooled = base
+    h = ctypes.c_void_p()
+    _lib.check(L.pbn_batch_create(arr, len(sizes), ctypes.byref(h)), "pbn_batch_create")
+    return h, keep
+
+
+def test_batch_module_generates_compiles_and_links():
+    """The batch module of a mixed batch (networks that compile and one that stays with
+    the interpreter) compiles with NVRTC and links with the interpreter's relocatable
+    work-item function; without a GPU only loading it fails."""
+    import ctypes
+    L = _lib.load()
+    h, keep = _fake_batch([30, 90, 1100])
+    try:
+        rc = L.pbn_batch_compile(h, _lib.PBN_COMPILE_INTERLEAVED, None)
+        detail = L.pbn_last_error_detail().decode()
+        assert rc == 0 or (rc == _lib.PBN_ECUDA and "loading the batch module failed" in detail), detail
+        if rc == 0:
+            info = _lib.BatchInfo()
+            L.pbn_batch_info_get(h, ctypes.byref(info))
+            assert info.n_compiled == 2
+    finally:
+        L.pbn_batch_free(h)
+
+
+def test_batch_compile_argument_errors():
+    L = _lib.load()
+    assert L.pbn_batch_compile(None, 0, None) == _lib.PBN_EINVAL
+    h, keep = _fake_batch([30])
+    try:
+        assert L.pbn_batch_compile(h, _lib.PBN_COMPILE_MAGIC_GATHER, None) == _lib.PBN_EINVAL
+        assert L.pbn_batch_compile(h, 0x100, None) == _lib.PBN_EINVAL
+    finally:
+        L.pbn_batch_free(h)
+    h, keep = _fake_batch([1300])  # 21 perturbation words: nothing compiles
+    try:
+        assert L.pbn_batch_compile(h, _lib.PBN_COMPILE_INTERLEAVED, None) == _lib.PBN_EINVAL
+        assert "no network" in L.pbn_last_error_detail().decode()
+    finally:
+        L.pbn_batch_free(h)
