@@ -61,6 +61,8 @@ extern "C" {
 /* Bits a kernel ORs into the caller's device status word. */
 #define PBN_DEV_STAGE_TIMEOUT 0x1u /* the bulk copy of plan tables into shared memory did not complete in time */
 #define PBN_DEV_BAD_PLAN 0x2u      /* the device image does not carry the expected header */
+#define PBN_DEV_BAD_MODULE 0x4u    /* a compiled batch's linked parts disagree on the kernel's shared
+                                      memory; the work item was skipped */
 
 /* ---- networks ---------------------------------------------------------------- */
 typedef struct pbn_net pbn_net;

@@ -43,6 +43,7 @@ PBN_KERNEL_INTERP = 1
 PBN_KERNEL_COMPILED = 2
 PBN_DEV_STAGE_TIMEOUT = 0x1
 PBN_DEV_BAD_PLAN = 0x2
+PBN_DEV_BAD_MODULE = 0x4
 
 
 class NetInfo(ctypes.Structure):

@@ -22,6 +22,7 @@
 
 #define PBN_BATCH_META_ROWS 16
 #define PBN_BATCH_STAGE_TIMEOUT 1u /* status bit: a staging copy did not complete */
+#define PBN_BATCH_BAD_MODULE 4u    /* status bit: a linked function sees other shared memory */
 #define PBN_WEYL0 0x9E3779B9u      /* Philox key increments between rounds */
 #define PBN_WEYL1 0xBB67AE85u
 

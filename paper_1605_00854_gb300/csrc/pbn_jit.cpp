@@ -432,8 +432,10 @@ private:
         const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
         o << "extern \"C\" __device__ __noinline__ bool pbn_net" << sfx_
           << "(const pbn_netdesc& D, const pbn_workitem W, const uint64_t step_offset, const uint32_t n_steps, "
-             "uint32_t* cnt) {\n";
-        o << "  extern __shared__ __align__(128) uint8_t smem[];\n";
+             "uint32_t* cnt, const uint8_t* kernel_smem, uint32_t* status) {\n";
+        o << "  extern __shared__ __align__(128) uint8_t smem[];\n"
+             "  if (static_cast<const uint8_t*>(smem) != kernel_smem) {\n"
+             "    if (status) atomicOr(status, PBN_BATCH_BAD_MODULE);\n    return false;\n  }\n";
         o << "  const pbn_item_window w = pbn_item_window_at(D, step_offset, n_steps);\n";
         o << "  struct PV { uint32_t key0[10], key1[10]; uint64_t* state; uint64_t* counts; uint64_t* trace;\n"
              "    uint32_t trace_stride; uint64_t traj_begin, step_begin;\n"
@@ -1083,10 +1085,11 @@ int jit_batch_module(const std::vector<std::string>& functions, const std::vecto
     for (uint32_t i : compiled)
         o << "extern \"C\" __device__ bool pbn_net_" << i
           << "(const pbn_netdesc& D, const pbn_workitem W, const uint64_t step_offset, const uint32_t n_steps, "
-             "uint32_t* cnt);\n";
+             "uint32_t* cnt, const uint8_t* kernel_smem, uint32_t* status);\n";
     if (interp)
         o << "extern \"C\" __device__ bool pbn_batch_interp_item(uint64_t step_offset, uint32_t n_steps, "
-             "const pbn_workitem* W, const pbn_netdesc* D, const uint32_t* meta_sh, uint32_t* c);\n";
+             "const pbn_workitem* W, const pbn_netdesc* D, const uint32_t* meta_sh, uint32_t* c, "
+             "const uint8_t* kernel_smem, uint32_t* status);\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << threads << ", 1) pbn_cbatch_kernel(const pbn_batch_params B) {\n"
          "  extern __shared__ __align__(128) uint8_t smem[];\n"
          "  __shared__ __align__(8) uint64_t bar;\n  __shared__ uint32_t item_sh;\n"
@@ -1094,8 +1097,10 @@ int jit_batch_module(const std::vector<std::string>& functions, const std::vecto
          "  pbn_batch_loop(B, smem, &bar, &item_sh, meta_sh,\n"
          "    [&](const pbn_workitem& W, const pbn_netdesc& D, const uint32_t* ms, uint32_t c[4]) -> bool {\n"
          "      switch (W.net) {\n";
-    for (uint32_t i : compiled) o << "        case " << i << "u: return pbn_net_" << i << "(D, W, B.step_offset, B.n_steps, c);\n";
-    if (interp) o << "        default: return pbn_batch_interp_item(B.step_offset, B.n_steps, &W, &D, ms, c);\n";
+    for (uint32_t i : compiled)
+        o << "        case " << i << "u: return pbn_net_" << i << "(D, W, B.step_offset, B.n_steps, c, smem, B.status);\n";
+    if (interp)
+        o << "        default: return pbn_batch_interp_item(B.step_offset, B.n_steps, &W, &D, ms, c, smem, B.status);\n";
     else o << "        default: return false;\n";
     o << "      }\n    });\n}\n";
     /* the network functions in up to `parts` programs compiled in parallel (each a

@@ -92,6 +92,7 @@ def test_compiled_batch_against_oracle(oracle_mod):
     assert B.info.n_compiled == 3
     B.run(300)
     B.run(200)
+    assert int(B.status.item()) == 0
     for k, (d, (plan, ids), e) in enumerate(zip(nets, plans, entries)):
         got = _collect(plan, e["bufs"])
         orc = oracle_mod.simulate(d["text"], d["seed"], k * 10**5, d["T"], 500, meta_ids=d["meta"],
@@ -118,6 +119,7 @@ def test_compiled_batch_variants_against_oracle(oracle_mod, variant):
     B = api.Batch(entries, compile_flags=_lib.PBN_COMPILE_INTERLEAVED)
     assert B.info.n_compiled == len(nets)
     B.run(250)
+    assert int(B.status.item()) == 0
     for k, (d, (plan, ids), e) in enumerate(zip(nets, plans, entries)):
         got = _collect(plan, e["bufs"])
         orc = oracle_mod.simulate(d["text"], d["seed"], k * 10**5, d["T"], 250, meta_ids=d["meta"],
@@ -147,6 +149,7 @@ def test_compiled_batch_graph_replay_and_static_queue():
     g = b2.capture([100, 100, 57], step_offset=0)
     g.replay()
     torch.cuda.synchronize()
+    assert int(b1.status.item()) == int(b2.status.item()) == int(b3.status.item()) == 0
     for k, (plan, ids) in enumerate(plans):
         a, b, c = _collect(plan, e1[k]["bufs"]), _collect(plan, e2[k]["bufs"]), _collect(plan, e3[k]["bufs"])
         for x in (b, c):
