@@ -48,7 +48,7 @@ def _queries():
                               seed=int(rng.integers(1, 2**62)), r=float(rng.choice([0.03, 0.05]))))
     # a slowly mixing small network at a tighter precision: grows its trajectories
     tiny = synth.tiny12(1).to_text()
-    qs.append(serve.Query(qid=8, text=tiny, meta_ids=[0, 1, 2], seed=99, r=0.01))
+    qs.append(serve.Query(qid=8, text=tiny, meta_ids=[0, 1, 2], seed=99, r=0.003))
     # the same network at r = 0.001 (N* of millions of states): far from done when cancelled
     qs.append(serve.Query(qid=9, text=tiny, meta_ids=[0, 1, 2], seed=7, r=0.001))
     return qs
