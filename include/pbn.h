@@ -263,7 +263,11 @@ typedef struct {
     uint64_t n_traj;       /* trajectories in this call (< 2^31) */
     uint64_t step_begin;   /* index t of the first step: maps s(t) -> s(t+1) */
     uint64_t n_steps;      /* steps in this call (< 2^32; step_begin + n_steps <= 2^48) */
-    uint64_t count_from;   /* states s(u) with u >= count_from are counted */
+    uint64_t count_from;   /* states s(u) with u >= count_from are counted: those the
+                              call produces (u > step_begin), and the keyed s(0) when
+                              count_from = 0; a PBN_INIT_STATE call never counts its
+                              initial state (the call before it produced and counted
+                              it), so calls resumed from d_state add up to one call */
     uint32_t init;         /* PBN_INIT_KEYED or PBN_INIT_STATE */
     uint32_t n_meta;       /* meta-state nodes (1..1024) */
     const uint32_t* meta_ids;  /* host: original ids of the meta-state nodes (retained) */
@@ -365,7 +369,8 @@ typedef struct {
     uint64_t traj_begin;       /* global id of its first trajectory (< 2^48) */
     uint64_t n_traj;           /* trajectories (1 .. 2^31 - 1) */
     uint64_t step_begin;       /* index of its first step */
-    uint64_t count_from;       /* states s(u) with u >= count_from are counted */
+    uint64_t count_from;       /* states s(u) with u >= count_from are counted (as in
+                                  pbn_sim_args: launches resumed from d_state add up) */
     uint32_t init;             /* PBN_INIT_KEYED (step_begin must be 0) or PBN_INIT_STATE */
     uint32_t n_meta;           /* meta-state nodes (1..1024, retained, within 16 state words) */
     const uint32_t* meta_ids;  /* host */

@@ -465,7 +465,10 @@ static void *sim_worker(void *arg) {
         else draw_init(cx, jb->seed, traj, s);
         uint64_t cnt[5] = {0, 0, 0, 0, 0}; /* V, n00, n01, n10, n11 */
         int z_prev = meta_hit(jb, s);
-        if (jb->step_begin == jb->count_from) cnt[0] += (uint64_t)z_prev;
+        /* the initial state belongs to the window only when this run starts the
+         * trajectory (keyed s(0)); a run from given states continues one whose
+         * earlier run produced, and counted, that state */
+        if (!jb->init_states && jb->step_begin >= jb->count_from) cnt[0] += (uint64_t)z_prev;
         for (uint64_t k = 0; k < jb->n_steps; ++k) {
             uint64_t t = jb->step_begin + k;
             /* Eq. 1: perturb if any gamma_i is set, else apply selected functions. */
@@ -501,7 +504,10 @@ out:
 /* Simulate n_traj trajectories (ids traj_begin ...) for steps
  * step_begin .. step_begin + n_steps - 1.  init_states (n_traj x n bytes) or
  * NULL for the keyed initial state (then step_begin must be 0).  counts gets
- * [V, n00, n01, n10, n11] per trajectory over states with index >= count_from.
+ * [V, n00, n01, n10, n11] per trajectory over states with index >= count_from:
+ * the states the run produces, the pairs it steps through, and its initial state
+ * only when the run starts the trajectory (keyed), so that runs resumed from saved
+ * states add up to one run over all the steps (Sec. 4.2's chain, cut anywhere).
  * trace (optional) gets the state after every step: n_traj x n_steps x n. */
 int orc_simulate_ex(const char *text, uint64_t seed, uint64_t traj_begin, uint64_t n_traj,
                     uint64_t step_begin, uint64_t n_steps, uint64_t count_from,

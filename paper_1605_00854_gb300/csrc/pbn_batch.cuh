@@ -82,14 +82,16 @@ __device__ __forceinline__ pbn_item_window pbn_item_window_at(const pbn_netdesc&
     const uint64_t sb = D.step_begin + step_offset;
     w.step_begin = sb;
     w.n_steps = n_steps;
-    /* state s(u) counted iff u >= count_from; pair (s(t), s(t+1)) iff t >= count_from */
+    /* produced states s(u) counted iff u >= count_from, pairs (s(t), s(t+1)) iff
+     * t >= count_from, the initial state only when the launch starts the trajectory
+     * (keyed s(0), count_from = 0): chained launches count each state once */
     const uint64_t cf = D.count_from, ns = n_steps;
     const uint64_t kv0 = cf > sb + 1 ? cf - sb - 1 : 0, kp0 = cf > sb ? cf - sb : 0;
     w.kv0 = (uint32_t)(kv0 < ns ? kv0 : ns);
     w.kp0 = (uint32_t)(kp0 < ns ? kp0 : ns);
     w.pairs = (uint32_t)(ns - w.kp0);
-    w.count_first = sb == cf ? 1u : 0u;
     w.init = (step_offset == 0) ? D.init : 1u;
+    w.count_first = (w.init == 0 && cf == 0) ? 1u : 0u;
     return w;
 }
 

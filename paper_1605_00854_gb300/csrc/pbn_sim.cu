@@ -60,7 +60,7 @@ struct SimParams {
     uint32_t kv0;              /* first step whose resulting state is counted */
     uint32_t kp0;              /* first step whose (before, after) pair is counted */
     uint32_t pairs;            /* counted pairs of this launch (n00 = pairs - others) */
-    uint32_t count_first;      /* 1: s(step_begin) itself is counted */
+    uint32_t count_first;      /* 1: the keyed s(0) itself is counted (count_from = 0) */
     uint32_t init;             /* 0: keyed s(0), 1: read state */
     uint32_t nt;               /* trajectory slots per CTA */
     uint32_t stage_bytes;      /* image bytes staged into shared memory */
@@ -249,15 +249,19 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     }
     P.n_traj = (uint32_t)a->n_traj;
     P.n_steps = (uint32_t)a->n_steps;
-    /* counting window: state s(u) counted iff u >= count_from; pair (s(t), s(t+1))
-     * counted iff t >= count_from */
+    /* counting window: the states this launch produces, s(u) for u in
+     * (step_begin, step_begin + n_steps], are counted iff u >= count_from, the pairs
+     * (s(t), s(t+1)) it steps through iff t >= count_from, and its initial state only
+     * when the launch starts the trajectory (keyed s(0), count_from = 0); a resumed
+     * launch never recounts the state the launch before it produced, so the counts
+     * of a chain of launches are those of one launch over all its steps */
     const uint64_t sb = a->step_begin, cf = a->count_from, ns = a->n_steps;
     const uint64_t kv0 = cf > sb + 1 ? cf - sb - 1 : 0;
     const uint64_t kp0 = cf > sb ? cf - sb : 0;
     P.kv0 = (uint32_t)(kv0 < ns ? kv0 : ns);
     P.kp0 = (uint32_t)(kp0 < ns ? kp0 : ns);
     P.pairs = (uint32_t)(ns - P.kp0);
-    P.count_first = sb == cf ? 1u : 0u;
+    P.count_first = (a->init == PBN_INIT_KEYED && cf == 0) ? 1u : 0u;
     P.init = a->init;
     P.n = H.n;
     P.W = H.W;

@@ -348,15 +348,16 @@ class Server:
                 return True
             return False
         if est.m_star > burn:
-            # restart the windows that began before the burn-in: at the current step
-            # or at m*, whichever is later (ordered before the next round on the
-            # server's stream)
+            # restart the windows that began before the burn-in: at the next state to
+            # be produced or at m*, whichever is later (the current state was counted
+            # by the discarded window; ordered before the next round on the server's
+            # stream)
             if a.step >= est.m_star:
                 a.restarts += 1
                 with self.torch.cuda.stream(self.stream):
                     for b in a.blocks:
                         if b.count_from < est.m_star:
-                            b.count_from = max(b.step, int(est.m_star))
+                            b.count_from = max(b.step + 1, int(est.m_star))
                             b.bufs.counts.zero_()
                             b.bufs.pooled.zero_()
             return False

@@ -169,3 +169,26 @@ def test_compile_errors():
     with pytest.raises(_lib.PbnError) as e:  # nothing compiles
         api.Batch(we, compile_flags=_lib.PBN_COMPILE_INTERLEAVED)
     assert e.value.status == _lib.PBN_EINVAL and "no network" in str(e.value)
+
+
+@pytest.mark.parametrize("compiled", [False, True])
+@pytest.mark.parametrize("count_from", [100, 250])
+def test_batch_chain_cut_at_the_window_start(oracle_mod, compiled, count_from):
+    """Batch launches cut exactly where the counting window starts count each state
+    once (the oracle's one run), compiled or interpreted."""
+    text = synth.tiny12(1).to_text()
+    nets = [dict(text=text, T=90, meta=[11], vals=None, seed=31, n=12),
+            dict(text=synth.paper100(seed=57, n=60, p=1e-2).to_text(), T=70, meta=[0], vals=None, seed=32, n=60)]
+    entries, plans = _entries(nets)
+    for e in entries:
+        e["count_from"] = count_from
+    B = api.Batch(entries, compile_flags=_lib.PBN_COMPILE_INTERLEAVED if compiled else None)
+    for c in [100, 150, 50]:
+        B.run(c)
+    assert int(B.status.item()) == 0
+    for k, (d, (plan, ids), e) in enumerate(zip(nets, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(d["text"], d["seed"], k * 10**5, d["T"], 300, meta_ids=d["meta"],
+                                  count_from=count_from, nthreads=NCPU)
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+        assert np.array_equal(got["counts"], orc["counts"]), k

@@ -292,3 +292,21 @@ def test_trace_snapshots_with_a_stride(kernel):
         api.simulate(plan, bufs, seed=3, n_steps=S, meta_ids=meta, trace=tr, trace_stride=st, kernel=kernel)
     torch.cuda.synchronize()
     assert torch.equal(snap, full[k - 1:: k][: S // k])
+
+
+@pytest.mark.parametrize("kernel", [_lib.PBN_KERNEL_INTERP, _lib.PBN_KERNEL_COMPILED])
+@pytest.mark.parametrize("count_from", [0, 99, 100, 101, 250, 300])
+def test_chain_cut_at_the_window_start(oracle_mod, kernel, count_from):
+    """Launches chained from the device state count what one oracle run counts when
+    the cuts fall just before, at and just after the start of the counting window
+    (a meta-state that is ON at the cuts in some trajectories)."""
+    text = synth.tiny12(1).to_text()
+    meta = [11]
+    plan, ids = plan_for(text, meta)
+    if kernel == _lib.PBN_KERNEL_COMPILED:
+        plan.compile(_lib.PBN_COMPILE_INTERLEAVED)
+    T, S = 96, 300
+    orc = oracle_mod.simulate(text, 21, 0, T, S, meta_ids=meta, count_from=count_from, nthreads=NCPU)
+    got = run(plan, seed=21, n_traj=T, n_steps=S, meta=meta, count_from=count_from, chunks=[100, 150, 50],
+              kernel=kernel)
+    _compare(got, orc, ids, trace=False)

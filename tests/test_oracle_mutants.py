@@ -71,7 +71,10 @@ MUTANTS = [
     ("meta_values_ignored", "pbn_oracle.c", "if (s[jb->meta_ids[m]] != jb->meta_vals[m]) return 0;",
      "if (s[jb->meta_ids[m]] != 1) return 0;"),
     ("first_state_not_counted", "pbn_oracle.c",
-     "        if (jb->step_begin == jb->count_from) cnt[0] += (uint64_t)z_prev;\n", ""),
+     "        if (!jb->init_states && jb->step_begin >= jb->count_from) cnt[0] += (uint64_t)z_prev;\n", ""),
+    ("resumed_run_recounts_its_initial_state", "pbn_oracle.c",
+     "if (!jb->init_states && jb->step_begin >= jb->count_from) cnt[0] += (uint64_t)z_prev;",
+     "if (jb->step_begin == jb->count_from) cnt[0] += (uint64_t)z_prev;"),
     ("visit_window_off_by_one", "pbn_oracle.c", "if (t + 1 >= jb->count_from) cnt[0] += (uint64_t)z;",
      "if (t >= jb->count_from) cnt[0] += (uint64_t)z;"),
     # exact transition matrix

@@ -476,18 +476,24 @@ def test_counts_match_bruteforce_recount(oracle_mod, count_from, vals):
         assert int(c[1] + c[2] + c[3] + c[4]) == L - 1
 
 
-def test_resume_equals_one_run(oracle_mod):
+@pytest.mark.parametrize("count_from", [0, 1, 50, 199, 200, 201, 400, 500])
+def test_resume_equals_one_run(oracle_mod, count_from):
     """S steps, then S more from the saved state, equals 2S steps in one run
-    (states at every step and the summed counts)."""
+    (states at every step and the summed counts), wherever the counting window
+    starts: before the cut, just before, at, just after it, at the end, beyond it."""
     from paper_1605_00854_gb300 import synth
     text = synth.tiny12(1).to_text()
-    meta = [0, 1, 2]
-    full = oracle_mod.simulate(text, 4, 100, 5, 400, meta_ids=meta, trace=True, count_from=50)
-    a = oracle_mod.simulate(text, 4, 100, 5, 200, meta_ids=meta, trace=True, count_from=50)
-    b = oracle_mod.simulate(text, 4, 100, 5, 200, meta_ids=meta, trace=True, count_from=50,
+    meta = [11]  # a meta-state that is ON at the cut in some trajectories (8 of 16)
+    full = oracle_mod.simulate(text, 4, 100, 16, 400, meta_ids=meta, trace=True, count_from=count_from)
+    a = oracle_mod.simulate(text, 4, 100, 16, 200, meta_ids=meta, trace=True, count_from=count_from)
+    b = oracle_mod.simulate(text, 4, 100, 16, 200, meta_ids=meta, trace=True, count_from=count_from,
                             step_begin=200, init_states=a["final"])
+    assert 0 < int(a["final"][:, meta[0]].sum()) < 16
     assert np.array_equal(full["trace"], np.concatenate([a["trace"], b["trace"]], axis=1))
     assert np.array_equal(full["counts"], a["counts"] + b["counts"])
+    # and the window is what it says: max(0, 400 + 1 - count_from) states per trajectory
+    L = max(0, 401 - count_from)
+    assert np.all(full["counts"][:, 1:].sum(axis=1) + (1 if L else 0) == L)
 
 
 # ------------------------------------------------------------------ leaves ----
