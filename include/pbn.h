@@ -411,7 +411,9 @@ int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
  * network whose plan compiles with `flags` (PBN_COMPILE_PERT_UNROLLED,
  * PBN_COMPILE_INTERLEAVED, PBN_COMPILE_PIPELINED, PBN_COMPILE_WIDE; multiply gathers
  * are not offered here) becomes a device function of one generated module, with its
- * Philox keys and meta-state rows as constants, run one trajectory per thread; a
+ * Philox keys and meta-state rows as constants, run one trajectory per thread (at
+ * most 96 networks per module, those with the most work: the CUDA 13.0 linker
+ * crashed on a module of 136 network functions); a
  * persistent kernel in the same module pops the work items from the device queue and
  * calls the network's function, or, for networks that do not compile, the
  * interpreter (prebuilt relocatable device code, pbn_batch_item.cubin next to the

@@ -203,6 +203,11 @@ namespace {
  * and step when the items are ordered (the interpreter ran the paper-scale plan
  * about 3.6x slower than its compiled kernel). */
 constexpr double kInterpCost = 3.0;
+/* Compiled networks per batch module.  nvJitLink (CUDA 13.0) crashed the process
+ * linking a dispatcher with 136 network functions (102 linked), so a module takes
+ * at most this many, the networks with the most estimated work; the others run the
+ * interpreter in the same launch. */
+constexpr size_t kMaxCompiledNets = 96;
 
 /* Cut every network into work items of its descriptor's trajectory slots, order them
  * by descending estimated work (largest processing time first, so that the
@@ -283,7 +288,15 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
         std::string first_why;
         std::vector<uint32_t> compiled;
         std::vector<uint32_t> tab(b->nets.size(), 0);
-        for (uint32_t i = 0; i < (uint32_t)b->nets.size(); ++i) {
+        /* networks by descending estimated work: the first kMaxCompiledNets that
+         * compile get their own functions */
+        std::vector<uint32_t> order(b->nets.size());
+        for (uint32_t i = 0; i < (uint32_t)order.size(); ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t x, uint32_t y) {
+            return b->plans[x]->info.ops_per_step * b->nets[x].n_traj > b->plans[y]->info.ops_per_step * b->nets[y].n_traj;
+        });
+        for (uint32_t i : order) {
+            if (compiled.size() >= kMaxCompiledNets) break;
             const NetDesc& D = b->nets[i];
             pbn::JitBatchNet spec;
             spec.index = i;
@@ -304,6 +317,7 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
         }
         if (compiled.empty())
             return fail(PBN_EINVAL, "pbn_batch_compile: no network of the batch compiles (%s)", first_why.c_str());
+        std::sort(compiled.begin(), compiled.end());
         const bool interp = compiled.size() < b->nets.size();
         void *lib = nullptr, *kern = nullptr;
         double ms = 0;

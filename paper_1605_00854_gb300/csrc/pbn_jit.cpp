@@ -1105,7 +1105,8 @@ int jit_batch_module(const std::vector<std::string>& functions, const std::vecto
     o << "      }\n    });\n}\n";
     /* the network functions in up to `parts` programs compiled in parallel (each a
      * relocatable unit), then linked with the dispatcher (and the interpreter) */
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    if (const char* t = getenv("PBN_BATCH_COMPILE_THREADS")) hw = std::max(1, atoi(t));
     const size_t parts = std::min<size_t>(functions.size(), std::min<unsigned>(hw, 32u));
     std::vector<std::string> srcs(parts + 1);
     srcs[0] = o.str();

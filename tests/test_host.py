@@ -811,6 +811,20 @@ def test_batch_module_generates_compiles_and_links():
         L.pbn_batch_free(h)
 
 
+def test_batch_module_caps_the_compiled_networks():
+    """A batch of more compilable networks than a module takes (the linker crashed
+    the process on a dispatcher of 136 network functions) compiles and links: the
+    surplus networks, those with the least work, stay with the interpreter."""
+    L = _lib.load()
+    h, keep = _fake_batch([20 + (i % 7) for i in range(110)], seed=900)
+    try:
+        rc = L.pbn_batch_compile(h, _lib.PBN_COMPILE_INTERLEAVED, None)
+        detail = L.pbn_last_error_detail().decode()
+        assert rc == 0 or (rc == _lib.PBN_ECUDA and "loading the batch module failed" in detail), detail
+    finally:
+        L.pbn_batch_free(h)
+
+
 def test_batch_compile_argument_errors():
     L = _lib.load()
     assert L.pbn_batch_compile(None, 0, None) == _lib.PBN_EINVAL
