@@ -20,9 +20,11 @@ simulator of the unreduced network) on the host cores instead.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -42,6 +44,20 @@ WORKLOAD = "paper-scale PBN n=100 (70% 1 function, 30% 2-3; in-degree 1-5; 25% s
 
 
 # ------------------------------------------------------------------ helpers ----
+def captured_traffic(src_hash: str, n_traj: int):
+    """(DRAM bytes per launch, source file) of an ncu capture listed in profiles/*.md
+    as `ncu-traffic: source-sha256=<hash> n_traj=<T> dram-bytes-per-launch=<bytes>`
+    for this kernel source and trajectory count, else (None, None)."""
+    import glob
+    pat = re.compile(r"ncu-traffic: source-sha256=([0-9a-f]{64}) n_traj=(\d+) dram-bytes-per-launch=(\d+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for m in pat.finditer(f.read()):
+                if m.group(1) == src_hash and int(m.group(2)) == n_traj:
+                    return float(m.group(3)), f"ncu dram__bytes_read+write of this kernel source, {os.path.relpath(path, ROOT)}"
+    return None, None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -364,16 +380,14 @@ def run_ours(args):
         achieved = ops * T * S / kernel_s / 1e12
         peak = sms * 128 * sm_max * 1e6 / 1e12
         clk_sum = clk.summary()
-        # DRAM bytes per launch from the ncu capture of this kernel (a 2,000-step launch of
-        # the same trajectories: the traffic is the state, counts and plan image, which
-        # does not grow with the number of steps)
+        # DRAM bytes per launch from an ncu capture of this very kernel (matched by the
+        # SHA-256 of its generated source; a 2,000-step launch of the same trajectories:
+        # the traffic is the state, counts and plan image, which does not grow with the
+        # number of steps), else null
         traffic, traffic_note = None, None
-        captured = {_lib.PBN_COMPILE_INTERLEAVED: 2.988e6,
-                    _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER: 2.719e6}
-        if (args.workload == "paper100" and args.kernel == "compiled" and cflags in captured
-                and max_inputs == 12 and T == 1 << 16 and args.sampler == "bitsliced"):
-            traffic = captured[cflags]
-            traffic_note = "ncu dram__bytes_read+write of this kernel, profiles/pbn_plan_kernel_paper100_compiled.md"
+        if args.kernel == "compiled":
+            src_hash = hashlib.sha256(plan.source(cflags).encode()).hexdigest()
+            traffic, traffic_note = captured_traffic(src_hash, T)
         pooled = bufs.pooled.cpu().numpy().view(np.uint64)
         est = api.estimate(pooled, T, 0.01, 0.95)
         out = {
@@ -417,79 +431,167 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------- batched form ----
-def run_batch(args):
-    """256 networks of the paper-scale generator with n log-uniform in [20, 4000],
-    trajectories log-uniform in [1024, 65536] and p log-uniform in [1e-5, 1e-2]:
-    one persistent launch per step chunk (device work queue), against one launch per
-    network of the interpreter and of the compiled plain (unmerged) method."""
+def _timed(stream, fn):
+    """CUDA-event seconds of fn() on `stream` after an L2 flush (a 256 MiB write)."""
     import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=stream.device)
+    flush.fill_(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def measure_batch(args):
+    """256 networks of the paper-scale generator with n log-uniform in [20, 4000],
+    trajectories log-uniform in [1024, 65536] and p log-uniform in [1e-5, 1e-2],
+    10^4 steps: the batched persistent launch (device work queue, chunks replayed from
+    a CUDA graph; the autotuner picks the interpreted or compiled batch and the steps
+    per launch) against one launch per network of the grouped plans (K2) and of the
+    plain method (K0: unreduced, one node per group), each compiled where its plan
+    compiles and interpreted otherwise, and both interpreted only."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
     shapes = synth.batch_shapes(seed=4, count=args.batch_count)
-    S = args.n_steps if args.n_steps else 10**4
-    entries, plain = [], []
+    S = args.batch_steps
+    S_each = min(S, args.batch_compare_steps)
+    sampler = SAMPLERS[args.sampler]
     t0 = time.perf_counter()
-    tot = 0.0
+    texts, entries, nu_step, ops_step = [], [], 0, 0.0
     for i, (n, T, p) in enumerate(shapes):
         text = synth.batch_network(seed=5000 + i, n=n, p=p).to_text()
         red, _ = api.Net.load(text).reduce(META)
-        plan = api.Plan(red, sampler=SAMPLERS[args.sampler])
-        entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=SEED + i, meta_ids=META))
-        plain.append(text)
-        tot += n * T * S
-    prep = time.perf_counter() - t0
-    B = api.Batch(entries)
-    chunk = args.chunk_steps
-    B.run(min(chunk, S))
-    torch.cuda.synchronize()
-    for e in entries:
-        e["bufs"].counts.zero_(); e["bufs"].pooled.zero_()
-    g = B.capture([chunk] * (S // chunk) + ([S % chunk] if S % chunk else []))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(); g.replay(); e1.record(); torch.cuda.synchronize()
-    t_batch = e0.elapsed_time(e1) / 1e3
-    assert int(B.status.item()) == 0
-    # one interpreter launch per network (grouped plans), same steps
-    e0.record()
-    for e in entries:
-        api.simulate(e["plan"], e["bufs"], seed=e["seed"], n_steps=S, meta_ids=META, kernel=_lib.PBN_KERNEL_INTERP)
-    e1.record(); torch.cuda.synchronize()
-    t_each = e0.elapsed_time(e1) / 1e3
-    # the plain method (unreduced, one node per group) per network, on 1,000 steps
-    S0 = min(S, 1000)
-    plain_plans, tot0 = [], 0.0
+        plan = api.Plan(red, sampler=sampler)
+        entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T, dev), seed=SEED + i, meta_ids=META))
+        texts.append(text)
+        nu_step += n * T
+        ops_step += plan.info.ops_per_step * T
+    prep_s = time.perf_counter() - t0
+
+    def reset():
+        for e in entries:
+            e["bufs"].counts.zero_(); e["bufs"].pooled.zero_()
+
+    # the two batched forms on a short trial; the faster one runs the workload
+    forms = {}
+    for form, flags in (("interpreted", None), ("compiled", _lib.PBN_COMPILE_INTERLEAVED)):
+        t0 = time.perf_counter()
+        B = api.Batch(entries, device=dev, compile_flags=flags)
+        build_s = time.perf_counter() - t0
+        B.run(20, step_offset=0)
+        torch.cuda.synchronize()
+        trial = min(S, args.batch_trial_steps)
+        dt = _timed(stream, lambda: B.run(trial, step_offset=0))
+        forms[form] = dict(batch=B, trial_rate=nu_step * trial / dt, build_s=build_s,
+                           n_compiled=int(B.info.n_compiled), work_items=int(B.info.n_items))
+    best = max(forms, key=lambda f: forms[f]["trial_rate"])
+    B = forms[best]["batch"]
+    # steps per launch: CUDA-graph replays of one trial length cut into chunks
+    chunk, chunk_t = autotune.tune_chunk(B, S, options=tuple(c for c in (250, 500, 1000, 2500) if c <= S),
+                                         trial_steps=min(S, args.batch_trial_steps))
+    reset()
+    chunks = [chunk] * (S // chunk) + ([S % chunk] if S % chunk else [])
+    g = B.capture(chunks, step_offset=0)
+    t_batch = _timed(stream, g.replay)
+    assert int(B.status.item()) == 0, "batch kernel status word set"
+    value = nu_step * S / t_batch
+
+    # one launch per network: grouped (K2) and plain (K0) plans, compiled where they
+    # compile (compilation before the timed region), else the interpreter
+    plain = []
     for i, (n, T, p) in enumerate(shapes):
         try:
-            pp = api.Plan(api.Net.load(plain[i]), mode=_lib.PBN_PLAN_PLAIN, sampler=SAMPLERS[args.sampler])
-        except _lib.PbnError:  # a plain plan whose specs exceed shared memory is left out
-            continue
-        plain_plans.append((pp, api.alloc_buffers(pp, T), entries[i]))
-        tot0 += n * T * S0
-    e0.record()
-    for pp, bb, e in plain_plans:
-        api.simulate(pp, bb, seed=e["seed"], n_steps=S0, meta_ids=META, kernel=_lib.PBN_KERNEL_INTERP)
-    e1.record(); torch.cuda.synchronize()
-    t_plain = e0.elapsed_time(e1) / 1e3
-    line = {"metric": "PBN node-updates/s, batched persistent launch (256 networks)", "value": tot / t_batch,
-            "unit": "node-updates/s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": t_batch * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "batch of 256 paper-scale PBNs, n log-uniform [20,4000], trajectories log-uniform "
-                       "[1024,65536], p log-uniform [1e-5,1e-2]", "n_steps": S, "chunk_steps": chunk,
-                       "work_items": int(B.info.n_items), "smem_per_cta": int(B.info.smem_bytes),
-                       "host_prep_s": round(prep, 2), "graph": "chunk launches captured in one CUDA graph",
-                       "perturbation_sampler": args.sampler},
-            "per_network_launches": {"value": tot / t_each, "unit": "node-updates/s", "seconds": t_each},
-            "per_network_plain_launches": {"value": tot0 / t_plain, "unit": "node-updates/s", "seconds": t_plain,
-                                           "n_steps": S0, "plan": "unreduced, one node per group",
-                                           "networks": len(plain_plans)},
-            "speedup_vs_per_network": t_each / t_batch}
+            pp = api.Plan(api.Net.load(texts[i]), mode=_lib.PBN_PLAN_PLAIN, sampler=sampler)
+        except _lib.PbnError:  # plain specs that exceed shared memory: left out
+            pp = None
+        plain.append(pp)
+
+    def try_compile(pl):
+        if pl is None:
+            return False
+        try:
+            pl.compile(_lib.PBN_COMPILE_INTERLEAVED)
+            return True
+        except _lib.PbnError:
+            return False
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 8) as ex:
+        k2_ok = list(ex.map(try_compile, [e["plan"] for e in entries]))
+        k0_ok = list(ex.map(try_compile, plain))
+    compile_each_s = time.perf_counter() - t0
+    plain_bufs = [api.alloc_buffers(pp, T, dev) if pp is not None else None for pp, (n, T, p) in zip(plain, shapes)]
+
+    def each(plans, bufs, kernels):
+        nu = 0
+        launches = []
+        for i, (pl, bf, kk) in enumerate(zip(plans, bufs, kernels)):
+            if pl is None:
+                continue
+            nu += shapes[i][0] * shapes[i][1] * S_each
+            launches.append((pl, bf, kk, entries[i]["seed"]))
+
+        def go(steps):
+            for pl, bf, kk, sd in launches:
+                api.simulate(pl, bf, seed=sd, n_steps=steps, meta_ids=META, stream=stream, kernel=kk)
+        go(8)  # warm (first launches, shape queries)
+        torch.cuda.synchronize()
+        dt = _timed(stream, lambda: go(S_each))
+        return {"value": nu / dt, "unit": "node-updates/s", "seconds": dt, "networks": len(launches),
+                "n_steps": S_each}
+    C, I = _lib.PBN_KERNEL_COMPILED, _lib.PBN_KERNEL_INTERP
+    grouped = [e["plan"] for e in entries]
+    gbufs = [e["bufs"] for e in entries]
+    legs = {
+        "compiled_grouped": each(grouped, gbufs, [C if ok else I for ok in k2_ok]),
+        "interpreted_grouped": each(grouped, gbufs, [I] * len(grouped)),
+        "compiled_plain": each(plain, plain_bufs, [C if ok else I for ok in k0_ok]),
+        "interpreted_plain": each(plain, plain_bufs, [I] * len(plain)),
+    }
+    legs["compiled_grouped"]["compiled_networks"] = int(sum(k2_ok))
+    legs["compiled_plain"]["compiled_networks"] = int(sum(k0_ok))
+    best_plain = max(legs["compiled_plain"]["value"], legs["interpreted_plain"]["value"])
+    best_grouped = max(legs["compiled_grouped"]["value"], legs["interpreted_grouped"]["value"])
+    pk, _ = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = ops_step * S / t_batch / 1e12
+    return {
+        "metric": "PBN node-updates/s, batched persistent launch vs one launch per network",
+        "value": value, "unit": "node-updates/s", "seconds": t_batch,
+        "workload": f"batch of {len(shapes)} paper-scale PBNs, n log-uniform [20,4000], trajectories log-uniform "
+                    "[1024,65536], p log-uniform [1e-5,1e-2]",
+        "n_steps": S, "form": best, "chunk_steps": chunk, "launches": len(chunks),
+        "autotune": {"forms": {f: {k: v for k, v in d.items() if k != "batch"} for f, d in forms.items()},
+                     "chunk_seconds_per_step": {str(k): v for k, v in chunk_t.items()}},
+        "threads_per_cta": int(B.info.threads), "smem_per_cta": int(B.info.smem_bytes),
+        "graph": "chunk launches captured in one CUDA graph", "host_prep_s": round(prep_s, 2),
+        "per_network": legs, "per_network_compile_s": round(compile_each_s, 2),
+        "speedup_vs_plain_per_network": value / best_plain,
+        "speedup_vs_grouped_per_network": value / best_grouped,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s", "frac": achieved / peak,
+                     "ops_per_step": ops_step, "traffic": None,
+                     "note": "algorithmic ops of every network's plan x trajectories x steps / CUDA-event time"},
+    }
+
+
+def run_batch(args):
+    out = measure_batch(args)
+    line = {"metric": out["metric"], "value": out["value"], "unit": out["unit"], "n_gpus": 1, "steps": 1,
+            "warmup": 1, "ms_per_step": out["seconds"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic", "config": {"workload": out["workload"]},
+            "batch": out}
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
+def measure_serve(args):
     """Poisson query arrivals (rate per second for a duration), each a fresh PBN of the
     paper-scale generator with n log-uniform in [30, 3000] and a meta-state of 1-4
     nodes, precision r = 0.01 at 95% confidence, served with continuous batching."""
     from paper_1605_00854_gb300 import serve
-    import numpy as np
     rng = np.random.default_rng(5)
     n_q = int(args.serve_rate * args.serve_seconds)
     gaps = rng.exponential(1.0 / args.serve_rate, size=n_q)
@@ -506,7 +608,7 @@ def run_serve(args):
     t_start = time.perf_counter()
     due = t_start + np.cumsum(gaps)
     k = 0
-    t_limit = t_start + args.serve_seconds * 20 + 120
+    t_limit = t_start + args.serve_seconds * 3 + 120
     while (k < n_q or srv.pending) and time.perf_counter() < t_limit:
         now = time.perf_counter()
         while k < n_q and due[k] <= now:
@@ -518,20 +620,64 @@ def run_serve(args):
     makespan = time.perf_counter() - t_start
     srv.close()
     lat = serve.latency_summary(srv.done)
-    line = {"metric": "served steady-state queries: p50/p99 latency, queries/s, node-updates/s",
-            "value": lat.get("p99_s"), "unit": "s (p99 latency)", "higher_is_better": False, "n_gpus": 1,
-            "dtype": "u32", "data": "synthetic",
-            "config": {"workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95",
-                       "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "queries": n_q,
-                       "trajectories_per_query": args.serve_traj, "max_trajectories_per_query": args.serve_max_traj,
-                       "chunk_steps": args.serve_chunk, "memory_cap_bytes": 100e9,
-                       "kernel": args.serve_kernel, "perturbation_sampler": args.sampler},
-            "latency": lat, "queries_per_s": len(srv.done) / makespan,
-            "node_updates_per_s": srv.node_updates / makespan, "makespan_s": makespan,
+    st = dict(srv.stats)
+    return {"metric": "served steady-state queries: p50/p99 latency, queries/s, node-updates/s",
+            "workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95",
+            "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "queries": n_q,
+            "trajectories_per_query": args.serve_traj, "max_trajectories_per_query": args.serve_max_traj,
+            "chunk_steps": args.serve_chunk, "memory_cap_bytes": 100e9, "kernel": args.serve_kernel,
+            "p50_s": lat.get("p50_s"), "p99_s": lat.get("p99_s"), "latency": lat,
+            "queries_per_s": len(srv.done) / makespan, "node_updates_per_s": srv.node_updates / makespan,
+            "makespan_s": makespan, "device_busy_frac": st.get("device_s", 0.0) / makespan,
             "completed": len(srv.done), "rejected": len(srv.rejected), "failed": len(srv.failed),
-            "unfinished": n_q - len(srv.done) - len(srv.rejected) - len(srv.failed),
-            "rounds": srv.stats, "mean_prep_s": float(np.mean([r.prep_s for r in srv.done])) if srv.done else None}
+            "unfinished": n_q - len(srv.done) - len(srv.rejected) - len(srv.failed) - len(srv.cancelled),
+            "rounds": st, "mean_prep_s": float(np.mean([r.prep_s for r in srv.done])) if srv.done else None}
+
+
+def run_serve(args):
+    out = measure_serve(args)
+    line = {"metric": out["metric"], "value": out["p99_s"], "unit": "s (p99 latency)", "higher_is_better": False,
+            "n_gpus": 1, "dtype": "u32", "data": "synthetic", "config": {"workload": out["workload"]}, "serve": out}
     print(json.dumps(line), flush=True)
+
+
+def measure_scalefree(args):
+    """One pass of the scale-free network (n = 2000, 2^14 trajectories x 10^5 steps)
+    in the autotuner's configuration, with its roofline."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    net = synth.scalefree2000(seed=3)
+    text, meta, n = net.to_text(), [0, 1, 2, 3], net.n
+    T, S = 1 << 14, args.scalefree_steps
+    t0 = time.perf_counter()
+    ch = autotune.tune_network(text, meta, T, steps=200, sampler=SAMPLERS[args.sampler])
+    tune_s = time.perf_counter() - t0
+    plan = autotune.plan_for_choice(text, meta, ch, sampler=SAMPLERS[args.sampler])
+    bufs = api.alloc_buffers(plan, T, dev)
+    img = plan.device_image(dev)
+    run = lambda steps: api.simulate(plan, bufs, seed=SEED, n_steps=steps, meta_ids=meta, stream=stream,
+                                     d_image=img, kernel=ch.kernel, lanes_per_traj=ch.lanes_per_traj)
+    run(200)
+    torch.cuda.synchronize()
+    bufs.counts.zero_(); bufs.pooled.zero_()
+    dt = _timed(stream, lambda: run(S))
+    assert int(bufs.status.item()) == 0
+    P = api.Net.load(text).info().P
+    ops = ops_per_traj_step(plan.info, n, P)
+    pk, _ = peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+    achieved = ops * T * S / dt / 1e12
+    return {"workload": "scale-free PBN n=2000 (power-law out-degree 2.5; in-degree 1-6; 1-3 functions; "
+                        "p=1e-5), reduced+grouped", "n_traj": T, "n_steps": S,
+            "value": n * T * S / dt, "unit": "node-updates/s", "seconds": dt,
+            "kernel": "compiled" if ch.kernel == _lib.PBN_KERNEL_COMPILED else "interpreter",
+            "lanes_per_traj": ch.lanes_per_traj, "max_inputs_per_group": ch.max_inputs,
+            "compile_flags": ch.compile_flags, "groups": int(plan.info.n_groups),
+            "n_retained": int(plan.info.n_retained), "autotune_s": round(tune_s, 1),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOP/s",
+                         "frac": achieved / peak, "ops_per_traj_step": ops, "traffic": None}}
 
 
 def apoptosis_queries():
@@ -607,10 +753,17 @@ def main():
     ap.add_argument("--apo-max-traj", type=int, default=1 << 17)
     ap.add_argument("--apo-chunk", type=int, default=4096)
     ap.add_argument("--apo-timeout", type=float, default=600.0)
+    ap.add_argument("--extras", default="batch,serve,scalefree2000",
+                    help="sub-measurements added to the default line at N=1 (comma list, or 'none')")
     ap.add_argument("--batch-count", type=int, default=256)
-    ap.add_argument("--chunk-steps", type=int, default=1000)
+    ap.add_argument("--batch-steps", type=int, default=10**4)
+    ap.add_argument("--batch-compare-steps", type=int, default=2000,
+                    help="steps of each per-network comparison leg")
+    ap.add_argument("--batch-trial-steps", type=int, default=1000,
+                    help="steps of the autotuner's trials (batched form, steps per launch)")
+    ap.add_argument("--scalefree-steps", type=int, default=10**5)
     ap.add_argument("--serve-rate", type=float, default=200.0)
-    ap.add_argument("--serve-seconds", type=float, default=20.0)
+    ap.add_argument("--serve-seconds", type=float, default=300.0)
     ap.add_argument("--serve-traj", type=int, default=2048)
     ap.add_argument("--serve-kernel", default="auto", choices=["batch", "auto"],
                     help="serving rounds: batched interpreter only, or compiled plans for large blocks")
@@ -662,6 +815,15 @@ def main():
 
     out = run_ours(args)
     if rank == 0 and out is not None:
+        extras = [] if args.extras in ("", "none") else args.extras.split(",")
+        measures = {"batch": measure_batch, "serve": measure_serve, "scalefree2000": measure_scalefree}
+        for name in extras if ws == 1 else []:
+            # the batched / served forms and the scale-free network, measured after the
+            # headline's timed region (one GPU; under torchrun only the headline runs)
+            try:
+                out[name] = measures[name](args)
+            except Exception as exc:  # a leg that cannot run reports why
+                out[name] = {"error": f"{type(exc).__name__}: {exc}"}
         if not args.no_cpu_baseline and ws == 1:
             rate, cores, sample, dt = oracle_rate(text, n, args.oracle_seconds)
             r1, s1 = oracle_rate_single(text, n, min(3.0, args.oracle_seconds / 4))

@@ -840,3 +840,22 @@ def test_batch_compile_argument_errors():
         assert "no network" in L.pbn_last_error_detail().decode()
     finally:
         L.pbn_batch_free(h)
+
+
+def test_bench_finds_captured_traffic_by_kernel_source():
+    """Every `ncu-traffic:` record under profiles/ is found by the bench's lookup for
+    its own source hash and trajectory count, and by nothing else."""
+    import re
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    recs = []
+    for name in os.listdir(os.path.join(ROOT, "profiles")):
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            recs += re.findall(r"ncu-traffic: source-sha256=([0-9a-f]{64}) n_traj=(\d+) dram-bytes-per-launch=(\d+)",
+                               f.read())
+    assert recs
+    for h, t, b in recs:
+        assert bench.captured_traffic(h, int(t))[0] == float(b)
+        assert bench.captured_traffic(h, int(t) + 1) == (None, None)
+    assert bench.captured_traffic("0" * 64, 65536) == (None, None)
