@@ -813,17 +813,23 @@ def main():
         print(json.dumps(line), flush=True)
         return
 
+    t_run = time.perf_counter()
     out = run_ours(args)
+    if rank == 0:
+        print(f"[bench] headline: {time.perf_counter() - t_run:.1f} s", file=sys.stderr, flush=True)
     if rank == 0 and out is not None:
         extras = [] if args.extras in ("", "none") else args.extras.split(",")
         measures = {"batch": measure_batch, "serve": measure_serve, "scalefree2000": measure_scalefree}
         for name in extras if ws == 1 else []:
             # the batched / served forms and the scale-free network, measured after the
             # headline's timed region (one GPU; under torchrun only the headline runs)
+            t_leg = time.perf_counter()
             try:
                 out[name] = measures[name](args)
             except Exception as exc:  # a leg that cannot run reports why
                 out[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            out[name]["leg_wall_s"] = round(time.perf_counter() - t_leg, 1)
+            print(f"[bench] {name}: {out[name]['leg_wall_s']} s", file=sys.stderr, flush=True)
         if not args.no_cpu_baseline and ws == 1:
             rate, cores, sample, dt = oracle_rate(text, n, args.oracle_seconds)
             r1, s1 = oracle_rate_single(text, n, min(3.0, args.oracle_seconds / 4))

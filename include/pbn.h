@@ -347,6 +347,17 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
  * drawn just before its first use (the interleaved and pipelined forms do not
  * apply).  Meant for wide networks with few trajectories. */
 #define PBN_COMPILE_WIDE 0x10u
+/* PBN_COMPILE_WARP_SPLIT: for wide plans (up to 4096 original nodes, 128 state rows,
+ * Eq. 1 semantics): a CTA of K warps runs 32 trajectories, one per lane, their states
+ * double-buffered in shared memory as [row][lane]; each warp runs straight-line code
+ * for its own share of the perturbation word pairs and of the state rows (their SEL
+ * blocks and merged groups), with two CTA barriers per step.  K is
+ * PBN_COMPILE_WARPS(K) (1..31), or chosen from the plan's size when 0.  Results equal
+ * every other form's. */
+#define PBN_COMPILE_WARP_SPLIT 0x20u
+#define PBN_COMPILE_WARPS(k) (((uint32_t)(k) & 31u) << 8)
+/* with PBN_COMPILE_WARP_SPLIT: registers limited so that m (1..7) CTAs fit an SM */
+#define PBN_COMPILE_MINCTAS(m) (((uint32_t)(m) & 7u) << 13)
 
 /* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
  * thread, local-memory (spill) bytes per thread and the flags it was compiled with;

@@ -37,6 +37,15 @@ PBN_COMPILE_INTERLEAVED = 0x2
 PBN_COMPILE_PIPELINED = 0x4
 PBN_COMPILE_MAGIC_GATHER = 0x8
 PBN_COMPILE_WIDE = 0x10
+PBN_COMPILE_WARP_SPLIT = 0x20
+
+
+def PBN_COMPILE_WARPS(k: int) -> int:
+    return (k & 31) << 8
+
+
+def PBN_COMPILE_MINCTAS(m: int) -> int:
+    return (m & 7) << 13
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1

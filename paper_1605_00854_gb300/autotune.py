@@ -17,6 +17,7 @@ from __future__ import annotations
 import json
 import os
 import threading
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import asdict, dataclass
 
 from . import _lib, api
@@ -61,7 +62,8 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                                         _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_COMPILE_MAGIC_GATHER,
                                         _lib.PBN_COMPILE_PIPELINED | _lib.PBN_COMPILE_MAGIC_GATHER),
                  try_compiled: bool = True, cache_file: str | None = None, log=None,
-                 sampler: int = _lib.PBN_PERT_BITSLICED) -> Choice:
+                 sampler: int = _lib.PBN_PERT_BITSLICED,
+                 warp_split_options=((0, 0), (4, 3), (8, 2), (8, 3), (16, 2))) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
     placement) for simulating n_traj trajectories of this network."""
     net = api.Net.load(text)
@@ -102,18 +104,38 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
             bufs = api.alloc_buffers(plan, n_traj)
             cands = []
             if try_compiled and budget == 0:
-                cands += [(_lib.PBN_KERNEL_COMPILED, 1, f) for f in compile_flags_options]
-                # plans too wide for the default forms: the wide form, while its code stays small
-                if plan.info.n_sel_blocks > 24 and plan.info.n_groups <= 512:
-                    cands.append((_lib.PBN_KERNEL_COMPILED, 1, _lib.PBN_COMPILE_WIDE))
+                cands += [(_lib.PBN_KERNEL_COMPILED, 1, f, plan) for f in compile_flags_options]
+                # plans too wide for the default forms: the wide register form, while its
+                # code stays small (it compiles for minutes at thousands of nodes)
+                if plan.info.n_sel_blocks > 24 and plan.info.n_groups <= 512 and plan.info.n <= 1024:
+                    cands.append((_lib.PBN_KERNEL_COMPILED, 1, _lib.PBN_COMPILE_WIDE, plan))
+                # wide states: the warp-split form in a few warp counts and occupancies,
+                # each on its own plan object (a plan holds one compiled kernel), compiled
+                # in parallel
+                if warp_split_options and (plan.info.state_words >= 4 or plan.info.n_sel_blocks > 24):
+                    ws = []
+                    for K, m in warp_split_options:
+                        f = _lib.PBN_COMPILE_WARP_SPLIT | _lib.PBN_COMPILE_WARPS(K) | _lib.PBN_COMPILE_MINCTAS(m)
+                        pw = api.Plan(red, max_inputs=mi, sampler=sampler)
+                        ws.append((f, pw))
+
+                    def _compile(fp):
+                        try:
+                            fp[1].compile(fp[0])
+                            return True
+                        except _lib.PbnError:
+                            return False
+                    with ThreadPoolExecutor(max_workers=len(ws)) as ex:
+                        ok = list(ex.map(_compile, ws))
+                    cands += [(_lib.PBN_KERNEL_COMPILED, 1, f, pw) for (f, pw), good in zip(ws, ok) if good]
             # at most about one lane per state word
-            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0) for lg in lanes_options
+            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0, plan) for lg in lanes_options
                       if lg == 1 or lg <= 2 * plan.info.state_words]
-            for kern, lg, cf in cands:
+            for kern, lg, cf, pl in cands:
                 try:
-                    if kern == _lib.PBN_KERNEL_COMPILED:
-                        plan.compile(cf)
-                    dt = _time(plan, bufs, seed, steps, list(meta), kern, lg)
+                    if kern == _lib.PBN_KERNEL_COMPILED and not (cf & _lib.PBN_COMPILE_WARP_SPLIT):
+                        pl.compile(cf)
+                    dt = _time(pl, bufs, seed, steps, list(meta), kern, lg)
                 except _lib.PbnError:
                     continue
                 rate = n * n_traj * steps / dt

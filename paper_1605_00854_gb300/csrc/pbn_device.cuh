@@ -16,7 +16,7 @@ typedef unsigned char uint8_t;
 #include <stdint.h>
 #endif
 
-#define PBN_JIT_MAX_ROWS 64
+#define PBN_JIT_MAX_ROWS 128 /* state rows a compiled plan's meta-state arrays cover */
 #define PBN_DOM_PERT 1u /* Philox counter domains (c3 = domain << 28 | index) */
 #define PBN_DOM_SEL 2u
 #define PBN_DOM_INIT 3u

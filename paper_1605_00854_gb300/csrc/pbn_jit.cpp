@@ -23,10 +23,12 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <sstream>
 #include <string>
@@ -190,6 +192,7 @@ bool find_magic(uint32_t row, const std::vector<uint32_t>& a, MagicTerm* out) {
 struct Generated {
     std::string src;
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
+    uint32_t warps = 0;      /* warp-split form: warps per CTA (32 trajectories); 0: one trajectory per thread */
 };
 
 using BatchSpec = pbn::JitBatchNet;
@@ -207,6 +210,7 @@ public:
           wide((flags & PBN_COMPILE_WIDE) != 0), bs_(bs), sfx_(bs ? "_" + std::to_string(bs->index) : std::string()) {}
 
     bool generate(Generated* out, std::string* why) {
+        if (flags_ & PBN_COMPILE_WARP_SPLIT) return generate_warp_split(out, why);
         if (!fits(why)) return false;
         bind_sections();
         collect_table_starts();
@@ -233,6 +237,323 @@ public:
         return true;
     }
 
+    /* Warp-split form (PBN_COMPILE_WARP_SPLIT), for wide plans: a CTA of K warps runs
+     * 32 trajectories, one per lane, with their grouped states double-buffered in
+     * shared memory as S[row][lane] (a warp's accesses to one row are conflict free).
+     * Each warp runs straight-line code for its own share of the work: some word pairs
+     * of the perturbation draws (phase A: flips XORed into the current state, a
+     * per-trajectory "perturbed" flag) and some pairs of state rows (phase B: the SEL
+     * blocks and merged groups of those rows, written to the next state; a perturbed
+     * trajectory copies its flipped state).  Two CTA barriers per step.  The meta-state
+     * indicator is ANDed from each warp's rows into a per-trajectory word and counted
+     * by warp 0 one step later.  Draws and results are those of every other form. */
+    bool generate_warp_split(Generated* out, std::string* why) {
+        if (H.semantics == PBN_SEM_NODEWISE) {
+            *why = "the warp-split form takes Eq. 1 semantics only";
+            return false;
+        }
+        if (H.W32 > 128 || H.W > 64) {
+            *why = "more than 128 state rows or 4096 original nodes";
+            return false;
+        }
+        bind_sections();
+        collect_table_starts();
+        gp.assign(H.n_groups, GPlan{}); /* no multiply gathers in this form */
+        magic = false;
+        tab_smem = table_bytes <= 48u * 1024u;
+        out->tab_bytes = tab_smem ? table_bytes : 0u;
+        geometric = H.sampler == PBN_PERT_GEOMETRIC;
+        interleave = true;
+        ws_choices_ = true;
+        Pv = H.P;
+        hmax = Pv ? (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u : 0u;
+        const uint32_t npairs = (H.W32 + 1) / 2; /* row pairs: one uint64 state word each */
+        /* groups by output row, and the cost of each row pair */
+        const uint32_t* wgroups = V.at<uint32_t>(H.off_wgroups);
+        std::vector<std::vector<uint32_t>> row_groups(H.W32);
+        for (uint32_t r = 0; r < H.W32; ++r)
+            for (uint32_t i = words[r].x; i < words[r].x + words[r].y; ++i) row_groups[r].push_back(wgroups[i]);
+        std::vector<double> cost(npairs, 0.0);
+        double total = 0;
+        for (uint32_t r = 0; r < H.W32; ++r)
+            for (uint32_t g : row_groups[r]) {
+                const double c = 8.0 + 3.0 * groups[g].q + 12.0 * groups[g].n_mul;
+                cost[r / 2] += c;
+                total += c;
+            }
+        uint32_t K = (flags_ >> 8) & 31u;
+        if (!K) K = (uint32_t)std::min<double>(16.0, std::max(2.0, std::ceil(total / 2500.0)));
+        K = std::max(1u, std::min(K, npairs));
+        warps = K;
+        /* row pairs to warps: largest first to the least loaded warp */
+        std::vector<uint32_t> order(npairs);
+        for (uint32_t i = 0; i < npairs; ++i) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return cost[a] > cost[b]; });
+        std::vector<double> load(K, 0.0);
+        std::vector<std::vector<uint32_t>> pairs_of(K);
+        for (uint32_t pr : order) {
+            const uint32_t w = (uint32_t)(std::min_element(load.begin(), load.end()) - load.begin());
+            pairs_of[w].push_back(pr);
+            load[w] += cost[pr] + 1.0;
+        }
+        for (auto& v : pairs_of) std::sort(v.begin(), v.end());
+        const uint32_t wpairs = (H.W + 1) / 2; /* perturbation word pairs, round robin */
+
+        o << "#include \"pbn_device.cuh\"\n";
+        if (geometric) {
+            const uint64_t* G = V.at<uint64_t>(H.off_geo);
+            o << "__device__ const unsigned long long GEO_T[64] = {";
+            for (int k = 0; k < 64; ++k) o << (k ? ", " : "") << fmt("0x%016llxull", (unsigned long long)G[k]);
+            o << "};\n";
+        }
+        const uint32_t R = H.W32;
+        const uint32_t minctas = (flags_ >> 13) & 7u; /* resident CTAs per SM the registers must allow */
+        o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * K;
+        if (minctas) o << ", " << minctas;
+        o << ") pbn_plan_kernel(const pbn_jit_params P) {\n"
+             "  extern __shared__ __align__(128) uint8_t smem[];\n  __shared__ __align__(8) uint64_t bar;\n"
+          << "  __shared__ uint32_t SA[" << R * 32 << "], SB[" << R * 32 << "];\n"
+             "  __shared__ uint32_t PF[2][32], ZF[2][32];\n";
+        if (tab_smem) {
+            o << "  if (!pbn_stage(smem, P.image + P.off_tables, P.tab_bytes, &bar)) {\n"
+                 "    if (threadIdx.x == 0 && P.status) atomicOr(P.status, 1u);\n    return;\n  }\n"
+                 "  const uint32_t* TAB = reinterpret_cast<const uint32_t*>(smem);\n";
+        } else {
+            o << "  const uint32_t* __restrict__ TAB = reinterpret_cast<const uint32_t*>(P.image + P.off_tables);\n";
+        }
+        o << "  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;\n"
+             "  const uint32_t lt = blockIdx.x * 32u + lane;\n"
+             "  const bool active = lt < P.n_traj;\n"
+             "  const uint64_t traj = P.traj_begin + lt;\n"
+             "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n"
+          << "  for (uint32_t i = threadIdx.x; i < " << R * 32 << "u; i += blockDim.x) SA[i] = 0u;\n"
+             "  if (threadIdx.x < 64u) { PF[threadIdx.x >> 5][lane] = 0u; ZF[threadIdx.x >> 5][lane] = 1u; }\n"
+             "  __syncthreads();\n";
+        /* initial state: keyed (INIT word pairs round robin, bits ORed into the rows) or
+         * loaded (each warp its own row pairs) */
+        o << "  if (P.init == 0) {\n    const pbn_philox_step ps0 = pbn_philox_begin(P, traj, 0);\n    switch (warp) {\n";
+        for (uint32_t w = 0; w < K; ++w) {
+            o << "    case " << w << "u: {\n";
+            for (uint32_t pr = w; 2 * pr < H.W; pr += K) {
+                const uint64_t r0 = ret[2 * pr], r1 = (2 * pr + 1 < H.W) ? ret[2 * pr + 1] : 0;
+                if (!(r0 | r1)) continue;
+                o << "      { const uint4 I = pbn_philox_draw(P, ps0, " << hex32((PBN_DOM_INIT << 28) | pr) << ");\n";
+                /* the bits of each target row, then one atomic OR per row */
+                std::map<uint32_t, std::string> rows;
+                for (uint32_t half = 0; half < 2; ++half) {
+                    const uint32_t wd = 2 * pr + half;
+                    const uint64_t rw = half ? r1 : r0;
+                    for (uint32_t b = 0; b < 64; ++b) {
+                        if (!((rw >> b) & 1u)) continue;
+                        const uint32_t ps = pos[64 * wd + b];
+                        const char comp = lanes[2 * half + (b >= 32 ? 1 : 0)];
+                        std::string& e = rows[ps >> 5];
+                        e += (e.empty() ? "" : " | ") + fmt("(((I.%c >> %u) & 1u) << %u)", comp, b & 31, ps & 31);
+                    }
+                }
+                for (const auto& kv : rows)
+                    o << "        atomicOr(&SA[" << kv.first << "u * 32u + lane], " << kv.second << ");\n";
+                o << "      }\n";
+            }
+            o << "    } break;\n";
+        }
+        o << "    default: break;\n    }\n  } else if (active) {\n    switch (warp) {\n";
+        for (uint32_t w = 0; w < K; ++w) {
+            o << "    case " << w << "u:\n";
+            for (uint32_t pr : pairs_of[w]) {
+                o << "      { const uint64_t v = P.state[(uint64_t)" << pr << " * P.n_traj + lt]; SA[" << 2 * pr
+                  << "u * 32u + lane] = (uint32_t)v;";
+                if (2 * pr + 1 < R) o << " SA[" << 2 * pr + 1 << "u * 32u + lane] = (uint32_t)(v >> 32);";
+                o << " }\n";
+            }
+            o << "      break;\n";
+        }
+        o << "    default: break;\n    }\n  }\n  __syncthreads();\n";
+        /* meta-state indicator of s(step_begin): warp 0, every row */
+        o << "  uint32_t zp = 1u;\n  if (warp == 0) {\n";
+        for (uint32_t r = 0; r < R; ++r)
+            o << "    zp &= (uint32_t)((SA[" << r << "u * 32u + lane] & P.meta_mask[" << r << "]) == P.meta_val[" << r
+              << "]);\n";
+        o << "    if (P.count_first) cV += zp;\n  }\n";
+        o << "  for (uint32_t k = 0; k < P.n_steps; ++k) {\n"
+             "    const uint64_t t = P.step_begin + k;\n"
+             "    const pbn_philox_step ps = pbn_philox_begin(P, traj, t);\n"
+             "    uint32_t* const Sc = (k & 1u) ? SB : SA;\n"
+             "    uint32_t* const Sn = (k & 1u) ? SA : SB;\n"
+             "    if (warp == 0) {\n"
+             "      PF[(k + 1u) & 1u][lane] = 0u;\n"
+             "      if (k > 0) { /* counts of the state the previous step produced */\n"
+             "        const uint32_t z = ZF[(k + 1u) & 1u][lane];\n"
+             "        ZF[(k + 1u) & 1u][lane] = 1u;\n"
+             "        const uint32_t kk = k - 1u;\n"
+             "        const uint32_t cv = kk >= P.kv0 ? 1u : 0u, cp = kk >= P.kp0 ? 1u : 0u;\n"
+             "        cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u); zp = z;\n"
+             "      }\n    }\n";
+        /* phase A: perturbation word pairs round robin over the warps */
+        o << "    switch (warp) {\n";
+        for (uint32_t w = 0; w < K; ++w) {
+            o << "    case " << w << "u: {\n      uint32_t any = 0;\n";
+            pair_sel_.assign(wpairs, 0);
+            bool anyw = false;
+            for (uint32_t pr = w; pr < wpairs; pr += K) pair_sel_[pr] = 1, anyw = true;
+            if (Pv && anyw) {
+                if (geometric) emit_geometric_perturbation("@", "");
+                else emit_paired_perturbation("@", "");
+            }
+            o << "      if (any) PF[k & 1u][lane] = 1u;\n    } break;\n";
+        }
+        pair_sel_.clear();
+        o << "    default: break;\n    }\n    __syncthreads();\n"
+             "    const uint32_t pert = PF[k & 1u][lane];\n"
+             "    const uint32_t scb = (uint32_t)__cvta_generic_to_shared(Sc) + 4u * lane;\n";
+        /* phase B: each warp's row pairs */
+        o << "    switch (warp) {\n";
+        for (uint32_t w = 0; w < K; ++w) {
+            o << "    case " << w << "u: {\n";
+            std::vector<uint32_t> myrows;
+            for (uint32_t pr : pairs_of[w]) {
+                myrows.push_back(2 * pr);
+                if (2 * pr + 1 < R) myrows.push_back(2 * pr + 1);
+            }
+            for (uint32_t r : myrows) o << "      uint32_t n" << r << " = 0;\n";
+            o << "      if (!pert) {\n";
+            /* the rows' groups in the order of the last SEL block they read; each block
+             * drawn before its first use, each state row loaded before its first use */
+            std::vector<std::pair<uint32_t, uint32_t>> order2;
+            for (uint32_t r : myrows)
+                for (uint32_t g : row_groups[r]) order2.push_back({r, g});
+            std::stable_sort(order2.begin(), order2.end(), [&](const std::pair<uint32_t, uint32_t>& x,
+                                                               const std::pair<uint32_t, uint32_t>& y) {
+                const auto bx = blocks_of(x.second), by = blocks_of(y.second);
+                const uint32_t mx = bx.empty() ? 0 : *std::max_element(bx.begin(), bx.end());
+                const uint32_t my = by.empty() ? 0 : *std::max_element(by.begin(), by.end());
+                return mx < my;
+            });
+            /* a block drawn more than kReuse groups earlier is drawn again (a new
+             * version of its choices), so that no choice stays live for long */
+            const uint32_t kReuse = (uint32_t)ws_reuse;
+            std::vector<int64_t> drawn_at(H.n_sel, -1);
+            std::vector<uint32_t> version(H.n_sel, 0);
+            int64_t gcount = 0;
+            for (const auto& rg : order2) {
+                const uint32_t r = rg.first, gi = rg.second;
+                const pbn_img_group& G = groups[gi];
+                for (uint32_t b : blocks_of(gi))
+                    if (drawn_at[b] < 0 || gcount - drawn_at[b] > (int64_t)kReuse) {
+                        /* the block's four uniforms become the choices of its slots at once
+                         * (one register per node instead of four per block) */
+                        drawn_at[b] = gcount;
+                        if (++version[b] == 1) { /* declared at the first draw, assigned at each */
+                            bool first = true;
+                            for (uint32_t l = 0; l < 4; ++l) {
+                                if (slot_choice(4 * b + l).empty()) continue;
+                                o << (first ? "        uint32_t " : ", ") << "J" << 4 * b + l;
+                                first = false;
+                            }
+                            if (!first) o << ";\n";
+                        }
+                        o << "        { const uint4 U" << b << " = pbn_philox_draw(P, ps, "
+                          << hex32((PBN_DOM_SEL << 28) | selblk[b]) << ");";
+                        for (uint32_t l = 0; l < 4; ++l) {
+                            const std::string j = slot_choice(4 * b + l);
+                            if (!j.empty()) o << " J" << 4 * b + l << " = " << j << ";";
+                        }
+                        o << " }\n";
+                    }
+                ++gcount;
+                /* the group's input rows, loaded in its own scope (volatile shared loads
+                 * are not merged across groups, so no row stays live in a register for
+                 * the rest of the warp's code) */
+                o << "        { ";
+                for (uint32_t row : rows_read(gi))
+                    if (row < R)
+                        o << "uint32_t s" << row << "; asm volatile(\"ld.shared.u32 %0, [%1+" << row * 128
+                          << "];\" : \"=r\"(s" << row << ") : \"r\"(scb)); ";
+                o << "{ ";
+                if (G.l2w == PBN_IMG_SPLIT) emit_split_group(r, G);
+                else emit_merged_group(r, gi, G);
+                o << "        }\n";
+            }
+            o << "      } else {\n";
+            for (uint32_t r : myrows) o << "        n" << r << " = Sc[" << r << "u * 32u + lane];\n";
+            o << "      }\n";
+            for (uint32_t r : myrows) o << "      Sn[" << r << "u * 32u + lane] = n" << r << ";\n";
+            /* this warp's part of the meta-state indicator of the new state */
+            o << "      if (";
+            for (size_t i = 0; i < myrows.size(); ++i)
+                o << (i ? " || " : "") << "((n" << myrows[i] << " & P.meta_mask[" << myrows[i] << "]) != P.meta_val["
+                  << myrows[i] << "])";
+            o << ") ZF[k & 1u][lane] = 0u;\n";
+            /* trace: this warp's row pairs of the new state */
+            o << "      if (P.trace && active && (k + 1) % P.trace_stride == 0) {\n"
+                 "        const uint64_t snap = (k + 1) / P.trace_stride - 1;\n";
+            for (uint32_t pr : pairs_of[w])
+                o << "        P.trace[(snap * " << npairs << "u + " << pr << "u) * P.n_traj + lt] = ((uint64_t)"
+                  << (2 * pr + 1 < R ? "n" + std::to_string(2 * pr + 1) : std::string("0u")) << " << 32) | n" << 2 * pr
+                  << ";\n";
+            o << "      }\n    } break;\n";
+        }
+        o << "    default: break;\n    }\n    __syncthreads();\n  }\n";
+        /* the last step's counts, the final state and the pooled counts */
+        o << "  if (warp == 0 && P.n_steps > 0) {\n"
+             "    const uint32_t z = ZF[(P.n_steps + 1u) & 1u][lane];\n"
+             "    const uint32_t kk = P.n_steps - 1u;\n"
+             "    const uint32_t cv = kk >= P.kv0 ? 1u : 0u, cp = kk >= P.kp0 ? 1u : 0u;\n"
+             "    cV += cv & z; c11 += cp & zp & z; c01 += cp & (zp ^ 1u) & z; c10 += cp & zp & (z ^ 1u);\n"
+             "  }\n"
+             "  const uint32_t* const Sf = (P.n_steps & 1u) ? SB : SA;\n"
+             "  if (active) {\n    switch (warp) {\n";
+        for (uint32_t w = 0; w < K; ++w) {
+            o << "    case " << w << "u:\n";
+            for (uint32_t pr : pairs_of[w]) {
+                o << "      P.state[(uint64_t)" << pr << " * P.n_traj + lt] = ";
+                if (2 * pr + 1 < R) o << "((uint64_t)Sf[" << 2 * pr + 1 << "u * 32u + lane] << 32) | ";
+                o << "Sf[" << 2 * pr << "u * 32u + lane];\n";
+            }
+            o << "      break;\n";
+        }
+        o << "    default: break;\n    }\n"
+             "    if (warp == 0 && P.counts) {\n"
+             "      const uint64_t nt = P.n_traj;\n"
+             "      P.counts[lt] += cV; P.counts[nt + lt] += P.pairs - c01 - c10 - c11;\n"
+             "      P.counts[2 * nt + lt] += c01; P.counts[3 * nt + lt] += c10; P.counts[4 * nt + lt] += c11;\n"
+             "    }\n  }\n";
+        o << "  if (warp == 0 && P.pooled) {\n"
+             "    uint64_t v[5] = {active ? cV : 0u, active ? (uint64_t)(P.pairs - c01 - c10 - c11) : 0u,\n"
+             "                     active ? c01 : 0u, active ? c10 : 0u, active ? c11 : 0u};\n"
+             "#pragma unroll\n    for (int i = 0; i < 5; ++i) {\n"
+             "#pragma unroll\n      for (int d = 16; d > 0; d >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], d);\n    }\n"
+             "    if (lane == 0) {\n"
+             "      for (int i = 0; i < 5; ++i) if (v[i]) atomicAdd(P.pooled + i, (unsigned long long)v[i]);\n    }\n  }\n";
+        o << "}\n";
+        out->src = o.str();
+        out->warps = K;
+        return true;
+    }
+
+    /* state rows a group's input bits come from */
+    std::vector<uint32_t> rows_read(uint32_t gi) const {
+        std::vector<uint32_t> rows;
+        const pbn_img_group& G = groups[gi];
+        auto add = [&](uint32_t in_chunk, uint32_t k, uint32_t stride) {
+            for (uint32_t b = 0; b < k; ++b) rows.push_back(inrec[4 * (in_chunk + stride * (b / 4)) + (b & 3)] >> 7);
+        };
+        if (G.l2w == PBN_IMG_SPLIT) {
+            for (uint32_t f = 0; f < G.q; ++f) {
+                const uint32_t* F = subs + 2 * (G.tab_off + 32 * f);
+                add(F[0] & 0x7FFFFFFu, F[0] >> 27, 1);
+            }
+        } else {
+            add(G.in_chunk, G.q, 32);
+        }
+        std::sort(rows.begin(), rows.end());
+        rows.erase(std::unique(rows.begin(), rows.end()), rows.end());
+        return rows;
+    }
+
+public:
+    uint32_t warps = 0; /* warps per CTA of the warp-split form (0: one trajectory per thread) */
+
 private:
     /* a group that gathers some of its inputs by multiplication (PBN_COMPILE_MAGIC_GATHER) */
     struct GTerm {
@@ -253,7 +574,13 @@ private:
     const bool wide; /* SEL blocks drawn lazily in group order: their uniforms live only
                         while the groups that need them are evaluated */
     const BatchSpec* bs_; /* batch-module function instead of a kernel */
+    std::vector<uint8_t> pair_sel_; /* warp split: the perturbation word pairs one warp draws (empty: all) */
+    bool pair_selected(uint32_t wp) const { return pair_sel_.empty() || (wp < pair_sel_.size() && pair_sel_[wp]); }
     const std::string sfx_; /* suffix of the module-level names (unique per network) */
+    bool ws_choices_ = false; /* choices as J<slot> registers computed after each draw */
+  public:
+    int ws_reuse = 16;        /* warp split: groups over which a drawn SEL block is reused */
+  private:
     const uint2* words = nullptr;
     const pbn_img_group* groups = nullptr;
     const pbn_img_multi* multi = nullptr;
@@ -271,7 +598,7 @@ private:
     std::ostringstream o;
 
     bool fits(std::string* why) const {
-        if (H.W32 > PBN_JIT_MAX_ROWS) {
+        if (H.W32 > 64) {
             *why = "state wider than 64 words";
             return false;
         }
@@ -521,8 +848,12 @@ private:
             for (uint32_t b = 0; b < 32; ++b) {
                 if (!((rm >> b) & 1u)) continue;
                 const uint32_t ps = pos[64 * w + 32 * half + b];
-                o << "            case " << b << ": " << target << (ps >> 5) << " " << op << " "
-                  << hex32(1u << (ps & 31)) << "; break;\n";
+                if (target[0] == '@') /* warp split: the flip goes to the shared state word */
+                    o << "            case " << b << ": atomicXor(&Sc[" << (ps >> 5) << "u * 32u + lane], "
+                      << hex32(1u << (ps & 31)) << "); break;\n";
+                else
+                    o << "            case " << b << ": " << target << (ps >> 5) << " " << op << " "
+                      << hex32(1u << (ps & 31)) << "; break;\n";
             }
             o << "          } } }\n";
         }
@@ -572,7 +903,15 @@ private:
 
     /* choice of a multi-function node from its SEL slot's thresholds */
     std::string choice_expr(const pbn_img_multi& M) const {
-        const uint32_t slot = M.ch_off;
+        if (ws_choices_) { /* warp split: the choice was computed right after its block's draw */
+            const uint32_t* ss = selslot + 4 * ((M.ch_off & 3u) * H.n_sel + (M.ch_off >> 2));
+            return ss[2] ? fmt("J%u", M.ch_off) : std::string();
+        }
+        return slot_choice(M.ch_off);
+    }
+
+    /* choice of the node in SEL slot `slot` from its block's uniforms U<slot/4> */
+    std::string slot_choice(uint32_t slot) const {
         const std::string u = fmt("U%u.%c", slot / 4, lanes[slot % 4]);
         const uint32_t* ss = selslot + 4 * ((slot & 3u) * H.n_sel + (slot >> 2)); /* t1, t2, n_thr, first */
         const uint32_t n_thr = ss[2];
@@ -803,6 +1142,7 @@ private:
     void emit_geometric_perturbation(const char* ftarget, const char* fop) {
         const uint64_t* G = V.at<uint64_t>(H.off_geo);
         for (uint32_t wp = 0; 2 * wp < H.W; ++wp) {
+            if (!pair_selected(wp)) continue;
             o << "      { const uint4 g0 = pbn_philox_draw(P, ps, " << hex32((PBN_DOM_GEO << 28) | (wp << 8)) << ");\n";
             for (uint32_t h2 = 0; h2 < 2 && 2 * wp + h2 < H.W; ++h2) {
                 const uint32_t w = 2 * wp + h2;
@@ -832,6 +1172,7 @@ private:
     /* one word at a time, every level pair unrolled with its P bits as constants */
     void emit_unrolled_perturbation(const char* ftarget, const char* fop) {
         for (uint32_t w = 0; w < H.W; ++w) {
+            if (!pair_selected(w / 2)) continue;
             const uint64_t valid = valid_of(w);
             o << "      { uint32_t ul = " << hex32((uint32_t)valid) << ", uh = " << hex32((uint32_t)(valid >> 32))
               << ", pl = 0, ph = 0;\n";
@@ -851,6 +1192,7 @@ private:
     void emit_paired_perturbation(const char* ftarget, const char* fop) {
         const uint32_t npeel = interleave ? std::min<uint32_t>(hmax, 3u) : 0u;
         for (uint32_t w = 0; w < H.W; w += 2) {
+            if (!pair_selected(w / 2)) continue;
             const bool two = w + 1 < H.W;
             const uint64_t v0 = valid_of(w), v1 = two ? valid_of(w + 1) : 0ull;
             o << "      { uint32_t ul0 = " << hex32((uint32_t)v0) << ", uh0 = " << hex32((uint32_t)(v0 >> 32))
@@ -1205,6 +1547,7 @@ struct pbn_jit_state {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kern = nullptr;
     uint32_t tab_bytes = 0;
+    uint32_t warps = 0;  /* warp-split form: warps per CTA of 32 trajectories */
     double compile_ms = 0;
 };
 
@@ -1257,8 +1600,11 @@ int jit_compile(const pbn_plan* plan, uint32_t flags) {
         J->log = "nvrtcCreateProgram failed";
         return fail(PBN_ECUDA, "nvrtcCreateProgram failed");
     }
-    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo"};
-    const int rc = N.compile(prog, 3, opts);
+    /* the warp-split form's long straight-line warp code: ptxas's default schedule
+     * spends every register on overlap and then spills under the occupancy bound; -O1
+     * keeps it within the bound */
+    const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "--ptxas-options=-O1"};
+    const int rc = N.compile(prog, (flags & PBN_COMPILE_WARP_SPLIT) ? 4 : 3, opts);
     size_t ls = 0;
     N.log_size(prog, &ls);
     std::string log(ls, '\0');
@@ -1282,6 +1628,7 @@ int jit_compile(const pbn_plan* plan, uint32_t flags) {
         return fail(PBN_ECUDA, "loading the compiled plan failed: %s", cudaGetErrorString(e));
     }
     J->tab_bytes = gen.tab_bytes;
+    J->warps = gen.warps;
     J->src = std::move(gen.src);
     J->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     J->state = 1;
@@ -1304,11 +1651,18 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
     pbn_jit_state* J = jit_state(plan);
     if (!jit_ready(plan)) return fail(PBN_EINVAL, "plan is not compiled");
     P->tab_bytes = J->tab_bytes;
-    uint64_t per_sm = (n_traj + (uint64_t)sms - 1) / (uint64_t)sms;
-    uint64_t tpb = ((per_sm + 31) / 32) * 32;
-    if (tpb > 512) tpb = 512;
-    if (tpb < 64) tpb = 64;
-    const uint64_t grid = (n_traj + tpb - 1) / tpb;
+    uint64_t tpb, grid;
+    if (J->warps) {
+        /* warp split: 32 trajectories per CTA of `warps` warps */
+        tpb = 32ull * J->warps;
+        grid = (n_traj + 31) / 32;
+    } else {
+        uint64_t per_sm = (n_traj + (uint64_t)sms - 1) / (uint64_t)sms;
+        tpb = ((per_sm + 31) / 32) * 32;
+        if (tpb > 512) tpb = 512;
+        if (tpb < 64) tpb = 64;
+        grid = (n_traj + tpb - 1) / tpb;
+    }
     void* args[] = {P};
     cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(J->kern), dim3((unsigned)grid), dim3((unsigned)tpb), args,
                                      J->tab_bytes, st);
@@ -1321,8 +1675,10 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
     if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER |
-                  PBN_COMPILE_WIDE))
+                  PBN_COMPILE_WIDE | PBN_COMPILE_WARP_SPLIT | PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7)))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
+    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7))) && !(flags & PBN_COMPILE_WARP_SPLIT))
+        return pbn::fail(PBN_EINVAL, "pbn_plan_compile: warp counts and CTAs per SM need PBN_COMPILE_WARP_SPLIT");
     const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;
     return rc;

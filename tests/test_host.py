@@ -385,6 +385,44 @@ def test_generated_plan_kernels_compile(tmp_path, which, flags):
     assert proc.returncode == 0, proc.stderr[-3000:]
 
 
+@pytest.mark.parametrize("which,warps,minctas", [("tiny12", 1, 0), ("p300", 4, 0), ("p300", 2, 3),
+                                                  ("split_wide", 0, 0), ("geometric", 3, 0), ("p0", 2, 0)])
+def test_warp_split_kernels_compile(tmp_path, which, warps, minctas):
+    """The warp-split form's generated source compiles for sm_103a (ptxas -O1, as the
+    library compiles it), for small and mid-size plans, split nodes, the geometric
+    sampler and p = 0; node-wise semantics are refused."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(nvcc):
+        pytest.skip("nvcc not available")
+    kw = {}
+    if which == "tiny12":
+        text, meta = synth.tiny12(1).to_text(), [0, 1, 2]
+    elif which == "p300":
+        text, meta = synth.paper100(seed=31, n=300, p=1e-3).to_text(), [0, 1, 2]
+    elif which == "split_wide":
+        text, meta = synth.random_pbn(5, 40, 1e-2, k_choices=tuple(range(1, 11))).to_text(), [0, 1]
+        kw = dict(max_inputs=3)
+    elif which == "geometric":
+        text, meta = synth.paper100(seed=2, n=150).to_text(), [0, 1, 2]
+        kw = dict(sampler=_lib.PBN_PERT_GEOMETRIC)
+    else:
+        text, meta = synth.paper100(seed=9, n=70, p=0.0).to_text(), [0, 1]
+    red, _ = api.Net.load(text).reduce(meta)
+    plan = api.Plan(red, **kw)
+    flags = _lib.PBN_COMPILE_WARP_SPLIT | _lib.PBN_COMPILE_WARPS(warps) | _lib.PBN_COMPILE_MINCTAS(minctas)
+    (tmp_path / "k.cu").write_text(plan.source(flags))
+    shutil.copy(os.path.join(ROOT, "paper_1605_00854_gb300", "csrc", "pbn_device.cuh"), tmp_path)
+    proc = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-Xptxas", "-O1", "-c",
+                           str(tmp_path / "k.cu"), "-o", str(tmp_path / "k.o")],
+                          capture_output=True, text=True)
+    assert proc.returncode == 0, proc.stderr[-3000:]
+    nw = api.Plan(red, semantics=_lib.PBN_SEM_NODEWISE)
+    with pytest.raises(_lib.PbnError):
+        nw.source(flags)
+
+
 def test_large_plans_are_not_compiled():
     net = synth.scalefree2000(seed=3)
     red, _ = api.Net.load(net.to_text()).reduce([0, 1, 2, 3])
