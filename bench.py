@@ -431,6 +431,10 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------- batched form ----
+def _progress(msg: str):
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def _timed(stream, fn):
     """CUDA-event seconds of fn() on `stream` after an L2 flush (a 256 MiB write)."""
     import torch
@@ -471,6 +475,7 @@ def measure_batch(args):
         nu_step += n * T
         ops_step += plan.info.ops_per_step * T
     prep_s = time.perf_counter() - t0
+    _progress(f"batch: {len(shapes)} plans in {prep_s:.1f} s")
 
     def reset():
         for e in entries:
@@ -488,6 +493,7 @@ def measure_batch(args):
         dt = _timed(stream, lambda: B.run(trial, step_offset=0))
         forms[form] = dict(batch=B, trial_rate=nu_step * trial / dt, build_s=build_s,
                            n_compiled=int(B.info.n_compiled), work_items=int(B.info.n_items))
+        _progress(f"batch: {form} form built in {build_s:.1f} s, trial {nu_step * trial / dt:.3e}")
     best = max(forms, key=lambda f: forms[f]["trial_rate"])
     B = forms[best]["batch"]
     # steps per launch: CUDA-graph replays of one trial length cut into chunks
@@ -496,7 +502,9 @@ def measure_batch(args):
     reset()
     chunks = [chunk] * (S // chunk) + ([S % chunk] if S % chunk else [])
     g = B.capture(chunks, step_offset=0)
+    _progress(f"batch: chunk {chunk} steps")
     t_batch = _timed(stream, g.replay)
+    _progress(f"batch: timed {S} steps in {t_batch:.1f} s")
     assert int(B.status.item()) == 0, "batch kernel status word set"
     value = nu_step * S / t_batch
 
@@ -523,6 +531,7 @@ def measure_batch(args):
         k2_ok = list(ex.map(try_compile, [e["plan"] for e in entries]))
         k0_ok = list(ex.map(try_compile, plain))
     compile_each_s = time.perf_counter() - t0
+    _progress(f"batch: per-network plans compiled in {compile_each_s:.1f} s")
     plain_bufs = [api.alloc_buffers(pp, T, dev) if pp is not None else None for pp, (n, T, p) in zip(plain, shapes)]
 
     def each(plans, bufs, kernels):
@@ -540,6 +549,7 @@ def measure_batch(args):
         go(8)  # warm (first launches, shape queries)
         torch.cuda.synchronize()
         dt = _timed(stream, lambda: go(S_each))
+        _progress(f"batch: per-network leg {dt:.1f} s")
         return {"value": nu / dt, "unit": "node-updates/s", "seconds": dt, "networks": len(launches),
                 "n_steps": S_each}
     C, I = _lib.PBN_KERNEL_COMPILED, _lib.PBN_KERNEL_INTERP
@@ -608,7 +618,10 @@ def measure_serve(args):
     t_start = time.perf_counter()
     due = t_start + np.cumsum(gaps)
     k = 0
-    t_limit = t_start + args.serve_seconds * 3 + 120
+    # arrivals for serve_seconds, then at most 60 s more to finish what is in flight;
+    # queries still open then are reported as unfinished
+    t_limit = t_start + args.serve_seconds + 60
+    last = t_start
     while (k < n_q or srv.pending) and time.perf_counter() < t_limit:
         now = time.perf_counter()
         while k < n_q and due[k] <= now:
@@ -617,6 +630,10 @@ def measure_serve(args):
             k += 1
         if not srv.step():
             time.sleep(0.0005)
+        if time.perf_counter() - last > 30:
+            last = time.perf_counter()
+            _progress(f"serve: {k} submitted, {len(srv.done)} done, {len(srv.active)} active, "
+                      f"{len(srv.waiting)} waiting")
     makespan = time.perf_counter() - t_start
     srv.close()
     lat = serve.latency_summary(srv.done)
