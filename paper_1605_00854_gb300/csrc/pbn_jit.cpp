@@ -327,7 +327,7 @@ public:
              "  const uint64_t traj = P.traj_begin + lt;\n"
              "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n"
           << "  for (uint32_t i = threadIdx.x; i < " << R * 32 << "u; i += blockDim.x) SA[i] = 0u;\n"
-             "  if (threadIdx.x < 64u) { PF[threadIdx.x >> 5][lane] = 0u; ZF[threadIdx.x >> 5][lane] = 1u; }\n"
+             "  for (uint32_t i = threadIdx.x; i < 64u; i += blockDim.x) { PF[i >> 5][i & 31u] = 0u; ZF[i >> 5][i & 31u] = 1u; }\n"
              "  __syncthreads();\n";
         /* initial state: keyed (INIT word pairs round robin, bits ORed into the rows) or
          * loaded (each warp its own row pairs) */
