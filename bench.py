@@ -601,17 +601,28 @@ def measure_serve(args):
     """Poisson query arrivals (rate per second for a duration), each a fresh PBN of the
     paper-scale generator with n log-uniform in [30, 3000] and a meta-state of 1-4
     nodes, precision r = 0.01 at 95% confidence, served with continuous batching."""
+    import multiprocessing
     from paper_1605_00854_gb300 import serve
     rng = np.random.default_rng(5)
     n_q = int(args.serve_rate * args.serve_seconds)
     gaps = rng.exponential(1.0 / args.serve_rate, size=n_q)
-    queries = []
+    shapes, metas = [], []
     for i in range(n_q):
         n = int(round(math.exp(rng.uniform(math.log(30), math.log(3000)))))
         k = int(rng.integers(1, 5))
-        meta = sorted(int(x) for x in rng.choice(4, size=k, replace=False))
-        text = synth.paper100(seed=9000 + i, n=n, p=float(10 ** rng.uniform(-4, -2))).to_text()
-        queries.append(serve.Query(qid=i, text=text, meta_ids=meta, seed=SEED + i, r=0.01, s=0.95))
+        metas.append(sorted(int(x) for x in rng.choice(4, size=k, replace=False)))
+        shapes.append((9000 + i, n, float(10 ** rng.uniform(-4, -2))))
+    # the client: query networks written by worker processes (spawned, so they hold
+    # no CUDA state) ahead of the arrival clock, in arrival order
+    ctx = multiprocessing.get_context("spawn")
+    gen = ctx.Pool(processes=max(2, min(8, (os.cpu_count() or 4) // 2)))
+    texts = gen.imap(synth.query_text_args, shapes, chunksize=8)
+    ahead = [next(texts) for _ in range(min(n_q, int(2 * args.serve_rate)))]  # two seconds of arrivals
+    _progress(f"serve: {n_q} queries, generation under way")
+
+    def query(i):
+        text = ahead[i] if i < len(ahead) else next(texts)
+        return serve.Query(qid=i, text=text, meta_ids=metas[i], seed=SEED + i, r=0.01, s=0.95)
     srv = serve.Server(n_traj=args.serve_traj, chunk_steps=args.serve_chunk, mem_cap_bytes=100e9,
                        workers=os.cpu_count() or 8, max_traj=args.serve_max_traj, kernel=args.serve_kernel,
                        sampler=SAMPLERS[args.sampler])
@@ -625,8 +636,9 @@ def measure_serve(args):
     while (k < n_q or srv.pending) and time.perf_counter() < t_limit:
         now = time.perf_counter()
         while k < n_q and due[k] <= now:
-            queries[k].arrival = due[k]
-            srv.submit(queries[k])
+            q = query(k)
+            q.arrival = due[k]
+            srv.submit(q)
             k += 1
         if not srv.step():
             time.sleep(0.0005)
@@ -636,10 +648,12 @@ def measure_serve(args):
                       f"{len(srv.waiting)} waiting")
     makespan = time.perf_counter() - t_start
     srv.close()
+    gen.terminate()
     lat = serve.latency_summary(srv.done)
     st = dict(srv.stats)
     return {"metric": "served steady-state queries: p50/p99 latency, queries/s, node-updates/s",
-            "workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95",
+            "workload": "Poisson queries, n log-uniform [30,3000], meta 1-4 nodes, r=0.01, s=0.95 "
+                        "(each a fresh paper-scale network, synth.query_text)",
             "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "queries": n_q,
             "trajectories_per_query": args.serve_traj, "max_trajectories_per_query": args.serve_max_traj,
             "chunk_steps": args.serve_chunk, "memory_cap_bytes": 100e9, "kernel": args.serve_kernel,

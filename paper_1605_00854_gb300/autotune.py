@@ -63,7 +63,7 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                                         _lib.PBN_COMPILE_PIPELINED | _lib.PBN_COMPILE_MAGIC_GATHER),
                  try_compiled: bool = True, cache_file: str | None = None, log=None,
                  sampler: int = _lib.PBN_PERT_BITSLICED,
-                 warp_split_options=((0, 0), (4, 3), (8, 2), (8, 3), (16, 2))) -> Choice:
+                 warp_split_options=((0, 0), (4, 0)), warp_split_max_inputs: int = 8) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
     placement) for simulating n_traj trajectories of this network."""
     net = api.Net.load(text)
@@ -112,7 +112,10 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                 # wide states: the warp-split form in a few warp counts and occupancies,
                 # each on its own plan object (a plan holds one compiled kernel), compiled
                 # in parallel
-                if warp_split_options and (plan.info.state_words >= 4 or plan.info.n_sel_blocks > 24):
+                # (each of these compiles for tens of seconds on wide plans, so only at
+                # one group size)
+                if (warp_split_options and mi == warp_split_max_inputs
+                        and (plan.info.state_words >= 4 or plan.info.n_sel_blocks > 24)):
                     ws = []
                     for K, m in warp_split_options:
                         f = _lib.PBN_COMPILE_WARP_SPLIT | _lib.PBN_COMPILE_WARPS(K) | _lib.PBN_COMPILE_MINCTAS(m)

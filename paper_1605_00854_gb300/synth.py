@@ -235,3 +235,52 @@ def batch_shapes(seed: int = 4, count: int = 256, n_range=(20, 4000), t_range=(1
 def batch_network(seed: int, n: int, p: float) -> Network:
     """One network of the batched workload: the paper-scale generator at size n."""
     return paper100(seed=seed, n=n, p=p)
+
+
+def query_text(seed: int, n: int, p: float) -> str:
+    """Network text of one served query: the paper-scale recipe of `paper100` (70% of
+    nodes with one function, the rest 2-3; in-degree 1-5 per function with the same
+    pmf; 25% sinks that are never parents, excluding nodes 0-3, the candidates for a
+    query's meta-state; Dirichlet(1) selection probabilities; truth-table bits
+    Bernoulli(1/2)), drawn with vectorised numpy calls so that a query stream of
+    tens of thousands of networks can be produced as fast as it arrives.  Its random
+    stream differs from `paper100`'s (same law, other draws)."""
+    rng = np.random.default_rng(seed)
+    protect = 4 if n > 4 else 0
+    m = int(round(0.25 * n))
+    sink = np.zeros(n, dtype=bool)
+    if m:
+        sink[protect + rng.choice(n - protect, size=min(m, n - protect), replace=False)] = True
+    pool = np.flatnonzero(~sink)
+    ell = rng.choice(np.array([1, 2, 3]), size=n, p=(0.70, 0.15, 0.15))
+    node = np.repeat(np.arange(n), ell)
+    nf = node.size
+    # Dirichlet(1) per node: normalised unit exponentials
+    g = rng.exponential(size=nf)
+    first = np.concatenate(([0], np.cumsum(ell)[:-1]))
+    c = g / np.repeat(np.add.reduceat(g, first), ell)
+    c[np.repeat(ell == 1, ell)] = 1.0
+    k = np.minimum(rng.choice(np.arange(1, 6), size=nf, p=INDEG_PMF_1_5), pool.size)
+    # k distinct parents per function, uniform over the pool: draw five, redraw clashes
+    par = pool[rng.integers(0, pool.size, size=(nf, 5))]
+    for _ in range(64):
+        clash = np.zeros(nf, dtype=bool)
+        for a in range(5):
+            for b in range(a):
+                clash |= (par[:, a] == par[:, b]) & (a < k)
+        if not clash.any():
+            break
+        par[clash] = pool[rng.integers(0, pool.size, size=(int(clash.sum()), 5))]
+    tt = rng.integers(0, 1 << 32, size=nf, dtype=np.uint64) & ((np.uint64(1) << (np.uint64(1) << k.astype(np.uint64))) - np.uint64(1))
+    digits = np.maximum(1, ((1 << k) + 3) // 4)
+    lines = [f"pbn {n} {float(p).hex()}"]
+    for f in range(nf):
+        kk = int(k[f])
+        lines.append(f"f {node[f]} {float(c[f]).hex()} {kk} " + "".join(f"{a} " for a in par[f, :kk])
+                     + f"{int(tt[f]):0{int(digits[f])}x}")
+    return "\n".join(lines) + "\n"
+
+
+def query_text_args(args) -> str:
+    """query_text(*args), for process pools."""
+    return query_text(*args)

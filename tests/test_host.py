@@ -897,3 +897,30 @@ def test_bench_finds_captured_traffic_by_kernel_source():
         assert bench.captured_traffic(h, int(t))[0] == float(b)
         assert bench.captured_traffic(h, int(t) + 1) == (None, None)
     assert bench.captured_traffic("0" * 64, 65536) == (None, None)
+
+
+def test_query_networks_have_the_paper_scale_shape():
+    """The serving stream's vectorised generator follows the paper-scale recipe:
+    function counts 1/2/3 at 70/15/15 %, in-degrees 1-5 with the stated pmf,
+    selection probabilities summing to 1 per node, a quarter of the nodes never a
+    parent (never nodes 0-3), distinct parents, and the same text on every call."""
+    fun_counts, k_counts, sinks = np.zeros(4), np.zeros(6), []
+    for seed in range(40):
+        text = synth.query_text(100 + seed, 400, 1e-3)
+        assert text == synth.query_text(100 + seed, 400, 1e-3)
+        net = synth.from_text(text)
+        parents = set()
+        for i, fl in enumerate(net.funcs):
+            fun_counts[len(fl)] += 1
+            assert abs(sum(f.c for f in fl) - 1.0) < 1e-12
+            for f in fl:
+                k_counts[len(f.parents)] += 1
+                assert len(set(f.parents)) == len(f.parents) and f.tt < (1 << (1 << len(f.parents)))
+                parents |= set(f.parents)
+        sinks.append(sum(1 for i in range(4, net.n) if i not in parents) / net.n)
+    share = fun_counts[1:] / fun_counts.sum()
+    assert abs(share[0] - 0.70) < 0.02 and abs(share[1] - 0.15) < 0.02 and abs(share[2] - 0.15) < 0.02
+    pmf = k_counts[1:] / k_counts.sum()
+    assert np.all(np.abs(pmf - np.array(synth.INDEG_PMF_1_5)) < 0.015)
+    # 25% sinks by construction (a few more nodes are never drawn by chance)
+    assert 0.25 <= np.mean(sinks) < 0.30
