@@ -483,9 +483,10 @@ def measure_batch(args):
 
     # the two batched forms on a short trial; the faster one runs the workload
     forms = {}
-    for form, flags in (("interpreted", None), ("compiled", _lib.PBN_COMPILE_INTERLEAVED)):
+    for form, flags, threads in (("interpreted", None, 512), ("interpreted_1024", None, 1024),
+                                 ("compiled", _lib.PBN_COMPILE_INTERLEAVED, 512)):
         t0 = time.perf_counter()
-        B = api.Batch(entries, device=dev, compile_flags=flags)
+        B = api.Batch(entries, device=dev, compile_flags=flags, threads=threads)
         build_s = time.perf_counter() - t0
         B.run(20, step_offset=0)
         torch.cuda.synchronize()

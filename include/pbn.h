@@ -415,6 +415,11 @@ typedef struct {
  * (a network's specs and trajectory rows exceed the per-CTA shared memory),
  * PBN_ENOMEM. */
 int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out);
+/* pbn_batch_create with a choice of CTA size for the interpreted batch kernel: 512
+ * (as pbn_batch_create) or 1024 threads (64 registers a thread: twice the warps per
+ * SM, for wide networks' lane groups; such a batch cannot be compiled).
+ * Errors: as pbn_batch_create, PBN_EINVAL for another CTA size. */
+int pbn_batch_create_cta(const pbn_batch_net* nets, uint32_t n_nets, uint32_t threads, pbn_batch** out);
 int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
 
 /* Give the batch compiled code (the batched form of Algorithm 5 with each network's
@@ -433,8 +438,9 @@ int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
  * desc_bytes, smem_bytes and n_compiled).  Results are bit-identical to the
  * uncompiled batch.  *compile_ms (may be NULL) receives the host time.  Host memory
  * and one CUDA library owned by the batch; no device memory is allocated.
- * Errors: PBN_EINVAL (NULL, compiled already, unsupported flags, no network
- * compiles), PBN_ECUDA (NVRTC, nvJitLink or loading failed), PBN_ENOMEM. */
+ * Errors: PBN_EINVAL (NULL, compiled already, a batch of 1,024-thread CTAs,
+ * unsupported flags, no network compiles), PBN_ECUDA (NVRTC, nvJitLink or loading
+ * failed), PBN_ENOMEM. */
 int pbn_batch_compile(pbn_batch* batch, uint32_t flags, double* compile_ms);
 
 /* Serialise the batch's device table (network descriptors, then work items) into

@@ -129,6 +129,7 @@ SIGNATURES = {
     "pbn_batch_info_get": (i32, [vp, ctypes.POINTER(BatchInfo)]),
     "pbn_batch_image": (i32, [vp, vp, ctypes.c_size_t]),
     "pbn_batch_compile": (i32, [vp, u32, ctypes.POINTER(f64)]),
+    "pbn_batch_create_cta": (i32, [ctypes.POINTER(BatchNet), u32, u32, ctypes.POINTER(vp)]),
     "pbn_batch_run": (i32, [vp, vp, vp, u64, u64, u32, vp, vp]),
     "pbn_batch_free": (None, [vp]),
     "pbn_batch_run_static": (i32, [vp, vp, u32, u64, u64, u32, vp, vp]),

@@ -275,7 +275,7 @@ class Batch:
     compile_flags (pbn_batch_compile) the networks whose plans compile run their own
     generated code in the same persistent launch, the others the interpreter."""
 
-    def __init__(self, entries, device="cuda", compile_flags: int | None = None):
+    def __init__(self, entries, device="cuda", compile_flags: int | None = None, threads: int = 512):
         import torch
         L = _lib.load()
         self.entries = entries
@@ -302,7 +302,7 @@ class Batch:
             b.d_counts = None if bufs.counts is None else bufs.counts.data_ptr()
             b.d_pooled = None if bufs.pooled is None else bufs.pooled.data_ptr()
         h = ctypes.c_void_p()
-        check(L.pbn_batch_create(arr, len(entries), ctypes.byref(h)), "pbn_batch_create")
+        check(L.pbn_batch_create_cta(arr, len(entries), threads, ctypes.byref(h)), "pbn_batch_create_cta")
         self._h = h
         self.compile_ms = 0.0
         if compile_flags is not None:

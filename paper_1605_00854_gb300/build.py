@@ -20,7 +20,7 @@ OUT = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT, "libpbn.so")
 GENCODE = "arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["pbn_sim.cu", "pbn_batch.cu"]
+CU_SOURCES = ["pbn_sim.cu", "pbn_batch.cu", "pbn_batch1024.cu"]
 CPP_SOURCES = ["pbn_host.cpp", "pbn_jit.cpp"]
 HEADERS = ["pbn_internal.h", "pbn_image.h", "pbn_device.cuh", "pbn_interp.cuh", "pbn_batch.cuh",
            "pbn_batch_interp.cuh"]

@@ -46,19 +46,15 @@ using NetDesc = pbn_netdesc;
 using WorkItem = pbn_workitem;
 using BatchParams = pbn_batch_params;
 
-/* The batch kernel of the library: every work item runs the interpreter. */
-__global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) {
-    extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ uint32_t item_sh;
-    __shared__ uint32_t meta_sh[3 * kMetaRows];
-    pbn_batch_loop(B, smem, &bar, &item_sh, meta_sh,
-                   [&](const WorkItem& W, const NetDesc& D, const uint32_t* ms, uint32_t c[4]) -> bool {
-                       return pbn_batch_interp_run(B.step_offset, B.n_steps, W, D, smem, ms, c);
-                   });
-}
+/* The batch kernel of the library: every work item runs the interpreter (CTAs of
+ * 512 threads; the 1,024-thread instantiation is in pbn_batch1024.cu). */
+__global__ void __launch_bounds__(512, 1) pbn_batch_kernel(const BatchParams B) { pbn_batch_interp_kernel_body(B); }
 
 }  // namespace
+
+namespace pbn {
+const void* batch_kernel_1024();
+}
 
 struct pbn_batch {
     pbn_batch_info info{};
@@ -255,11 +251,17 @@ void cut_items(pbn_batch* B) {
 }  // namespace
 
 extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out) {
+    return pbn_batch_create_cta(nets, n_nets, 512, out);
+}
+
+extern "C" int pbn_batch_create_cta(const pbn_batch_net* nets, uint32_t n_nets, uint32_t threads, pbn_batch** out) {
     using pbn::fail;
     if (!nets || !out || n_nets == 0) return fail(PBN_EINVAL, "pbn_batch_create: need networks");
+    if (threads != 512 && threads != 1024) return fail(PBN_EINVAL, "pbn_batch_create: CTAs of 512 or 1024 threads");
     *out = nullptr;
     try {
         std::unique_ptr<pbn_batch> B(new pbn_batch());
+        B->threads = threads;
         const uint32_t T = B->threads;
         for (uint32_t i = 0; i < n_nets; ++i) {
             const pbn_batch_net& a = nets[i];
@@ -281,6 +283,7 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
     using pbn::fail;
     if (!b) return fail(PBN_EINVAL, "pbn_batch_compile: NULL batch");
     if (b->module) return fail(PBN_EINVAL, "pbn_batch_compile: the batch is compiled already");
+    if (b->threads != 512) return fail(PBN_EINVAL, "pbn_batch_compile: compiled batches run CTAs of 512 threads");
     if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_WIDE))
         return fail(PBN_EINVAL, "pbn_batch_compile: unsupported flags 0x%x", flags);
     try {
@@ -368,9 +371,11 @@ extern "C" int pbn_batch_image(const pbn_batch* b, void* dst, size_t cap) {
 }
 
 namespace {
-/* The batch's kernel: its compiled module's dispatcher, or the library's. */
+/* The batch's kernel: its compiled module's dispatcher, or the library's for its
+ * CTA size. */
 const void* batch_kernel(const pbn_batch* b) {
-    return b->module_kernel ? b->module_kernel : reinterpret_cast<const void*>(pbn_batch_kernel);
+    if (b->module_kernel) return b->module_kernel;
+    return b->threads == 1024 ? pbn::batch_kernel_1024() : reinterpret_cast<const void*>(pbn_batch_kernel);
 }
 
 cudaError_t launch_batch(const pbn_batch* b, const BatchParams& P, uint32_t grid, cudaStream_t st) {

@@ -121,4 +121,16 @@ __device__ __forceinline__ bool pbn_batch_interp_run(uint64_t step_offset, uint3
     return active && lane == 0;
 }
 
+/* Body of the library's interpreted batch kernels (one per CTA size). */
+__device__ __forceinline__ void pbn_batch_interp_kernel_body(const pbn_batch_params& B) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t item_sh;
+    __shared__ uint32_t meta_sh[3 * PBN_BATCH_META_ROWS];
+    pbn_batch_loop(B, smem, &bar, &item_sh, meta_sh,
+                   [&](const pbn_workitem& W, const pbn_netdesc& D, const uint32_t* ms, uint32_t c[4]) -> bool {
+                       return pbn_batch_interp_run(B.step_offset, B.n_steps, W, D, smem, ms, c);
+                   });
+}
+
 #endif /* PBN_BATCH_INTERP_CUH */

@@ -192,3 +192,24 @@ def test_batch_chain_cut_at_the_window_start(oracle_mod, compiled, count_from):
                                   count_from=count_from, nthreads=NCPU)
         assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
         assert np.array_equal(got["counts"], orc["counts"]), k
+
+
+def test_batch_of_1024_thread_ctas_against_oracle(oracle_mod):
+    """The interpreted batch kernel with CTAs of 1,024 threads (wider lane groups per
+    item) gives the oracle's states and counts; such a batch refuses compilation."""
+    nets = _mix(57, [25, 90, 700, 1300, 2100], 200)
+    entries, plans = _entries(nets)
+    B = api.Batch(entries, threads=1024)
+    assert B.info.threads == 1024
+    for c in [150, 1, 149]:
+        B.run(c)
+    assert int(B.status.item()) == 0
+    for k, (d, (plan, ids), e) in enumerate(zip(nets, plans, entries)):
+        got = _collect(plan, e["bufs"])
+        orc = oracle_mod.simulate(d["text"], d["seed"], k * 10**5, d["T"], 300, meta_ids=d["meta"],
+                                  meta_vals=d["vals"], count_from=21, nthreads=NCPU)
+        assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+        assert np.array_equal(got["counts"], orc["counts"]), k
+    e2, _ = _entries(nets[:1])
+    with pytest.raises(_lib.PbnError):
+        api.Batch(e2, threads=1024, compile_flags=_lib.PBN_COMPILE_INTERLEAVED)

@@ -924,3 +924,28 @@ def test_query_networks_have_the_paper_scale_shape():
     assert np.all(np.abs(pmf - np.array(synth.INDEG_PMF_1_5)) < 0.015)
     # 25% sinks by construction (a few more nodes are never drawn by chance)
     assert 0.25 <= np.mean(sinks) < 0.30
+
+
+def test_batch_cta_sizes():
+    """pbn_batch_create_cta takes CTAs of 512 or 1,024 threads and nothing else."""
+    import ctypes
+    L = _lib.load()
+    buf = np.zeros(1 << 16, dtype=np.uint8)
+    base = (buf.ctypes.data + 255) & ~255
+    red, _ = api.Net.load(synth.paper100(seed=3, n=300, p=1e-3).to_text()).reduce([0, 1, 2])
+    plan = api.Plan(red)
+    mi = np.array([0, 1, 2], dtype=np.uint32)
+    arr = (_lib.BatchNet * 1)()
+    b = arr[0]
+    b.plan, b.d_image, b.seed, b.n_traj, b.init = plan._h, base, 1, 5000, 0
+    b.n_meta, b.meta_ids = 3, mi.ctypes.data
+    b.d_state = b.d_counts = b.d_pooled = base
+    for threads, ok in ((512, True), (1024, True), (256, False), (2048, False)):
+        h = ctypes.c_void_p()
+        rc = L.pbn_batch_create_cta(arr, 1, threads, ctypes.byref(h))
+        assert (rc == 0) == ok, threads
+        if ok:
+            info = _lib.BatchInfo()
+            L.pbn_batch_info_get(h, ctypes.byref(info))
+            assert info.threads == threads and info.n_items >= 5000 // threads
+            L.pbn_batch_free(h)
