@@ -58,6 +58,21 @@ def captured_traffic(src_hash: str, n_traj: int):
     return None, None
 
 
+def captured_instructions(src_hash: str):
+    """(warp instructions per warp-step, thread instructions per trajectory-step) of
+    an ncu capture listed in profiles/*.md as `ncu-inst: source-sha256=<hash>
+    warp-inst-per-warp-step=<w> thread-inst-per-traj-step=<t>`, else None."""
+    import glob
+    pat = re.compile(r"ncu-inst: source-sha256=([0-9a-f]{64}) warp-inst-per-warp-step=(\d+) "
+                     r"thread-inst-per-traj-step=(\d+)")
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        with open(path) as f:
+            for m in pat.finditer(f.read()):
+                if m.group(1) == src_hash:
+                    return float(m.group(2)), float(m.group(3))
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -384,10 +399,23 @@ def run_ours(args):
         # SHA-256 of its generated source; a 2,000-step launch of the same trajectories:
         # the traffic is the state, counts and plan image, which does not grow with the
         # number of steps), else null
-        traffic, traffic_note = None, None
+        traffic, traffic_note, issue = None, None, None
         if args.kernel == "compiled":
             src_hash = hashlib.sha256(plan.source(cflags).encode()).hexdigest()
             traffic, traffic_note = captured_traffic(src_hash, T)
+            inst = captured_instructions(src_hash)
+            if inst is not None:
+                # issue slots: ncu's executed warp instructions per warp-step of this
+                # kernel source x the warp-steps this launch ran, against every
+                # scheduler issuing one warp instruction per clock
+                wpi, tpi = inst
+                warp_steps = math.ceil(T / 32) * S
+                issued = wpi * warp_steps / kernel_s
+                issue_peak = sms * 4 * sm_max * 1e6
+                issue = {"warp_inst_per_warp_step": wpi, "thread_inst_per_traj_step": tpi,
+                         "achieved_warp_inst_per_s": issued, "peak_warp_inst_per_s": issue_peak,
+                         "frac": issued / issue_peak,
+                         "note": "instruction counts from the ncu capture of this kernel source"}
         pooled = bufs.pooled.cpu().numpy().view(np.uint64)
         est = api.estimate(pooled, T, 0.01, 0.95)
         out = {
@@ -413,6 +441,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic, "traffic_note": traffic_note,
                          "ops_per_traj_step": ops,
                          "peak_note": f"{sms} SMs x 128 int32 lanes x {sm_max:.0f} MHz ({src} max SM clock)",
+                         "issue_slots": issue,
                          # the HBM side, for context: state, counts and plan image per launch
                          "hbm": None if traffic is None else {
                              "achieved_gbs": traffic / kernel_s / 1e9, "peak_gbs": float(pk.get("hbm_gbs", 6800.0)),

@@ -949,3 +949,20 @@ def test_batch_cta_sizes():
             L.pbn_batch_info_get(h, ctypes.byref(info))
             assert info.threads == threads and info.n_items >= 5000 // threads
             L.pbn_batch_free(h)
+
+
+def test_bench_finds_captured_instructions_by_kernel_source():
+    """Every `ncu-inst:` record under profiles/ is found for its own source hash."""
+    import re
+    import sys
+    sys.path.insert(0, ROOT)
+    import bench
+    recs = []
+    for name in os.listdir(os.path.join(ROOT, "profiles")):
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            recs += re.findall(r"ncu-inst: source-sha256=([0-9a-f]{64}) warp-inst-per-warp-step=(\d+) "
+                               r"thread-inst-per-traj-step=(\d+)", f.read())
+    assert recs
+    for h, w, t in recs:
+        assert bench.captured_instructions(h) == (float(w), float(t))
+    assert bench.captured_instructions("0" * 64) is None
