@@ -358,6 +358,10 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
 #define PBN_COMPILE_WARPS(k) (((uint32_t)(k) & 31u) << 8)
 /* with PBN_COMPILE_WARP_SPLIT: registers limited so that m (1..7) CTAs fit an SM */
 #define PBN_COMPILE_MINCTAS(m) (((uint32_t)(m) & 7u) << 13)
+/* with PBN_COMPILE_WARP_SPLIT: groups evaluated in batches of 4^b (b = 0..3) whose
+ * state rows are loaded together; ptxas at its default -O3 instead of -O1 */
+#define PBN_COMPILE_WS_BATCH(b) (((uint32_t)(b) & 3u) << 16)
+#define PBN_COMPILE_WS_O3 0x40000u
 
 /* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
  * thread, local-memory (spill) bytes per thread and the flags it was compiled with;

@@ -46,6 +46,13 @@ def PBN_COMPILE_WARPS(k: int) -> int:
 
 def PBN_COMPILE_MINCTAS(m: int) -> int:
     return (m & 7) << 13
+
+
+def PBN_COMPILE_WS_BATCH(b: int) -> int:
+    return (b & 3) << 16
+
+
+PBN_COMPILE_WS_O3 = 0x40000
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1

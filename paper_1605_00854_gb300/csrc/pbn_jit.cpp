@@ -435,9 +435,14 @@ public:
             std::vector<int64_t> drawn_at(H.n_sel, -1);
             std::vector<uint32_t> version(H.n_sel, 0);
             int64_t gcount = 0;
-            for (const auto& rg : order2) {
-                const uint32_t r = rg.first, gi = rg.second;
-                const pbn_img_group& G = groups[gi];
+            /* groups in batches: the SEL blocks of a batch are drawn, then the state rows
+             * its groups read are loaded together, then the groups are evaluated, so
+             * that a batch's loads and lookups are in flight at once */
+            const uint32_t batch = 1u << (2u * ((flags_ >> 16) & 3u)); /* 1, 4, 16, 64 */
+            for (size_t b0 = 0; b0 < order2.size(); b0 += batch) {
+              const size_t b1 = std::min(order2.size(), b0 + (size_t)batch);
+              for (size_t bi = b0; bi < b1; ++bi) {
+                const uint32_t gi = order2[bi].second;
                 for (uint32_t b : blocks_of(gi))
                     if (drawn_at[b] < 0 || gcount - drawn_at[b] > (int64_t)kReuse) {
                         /* the block's four uniforms become the choices of its slots at once
@@ -461,18 +466,29 @@ public:
                         o << " }\n";
                     }
                 ++gcount;
-                /* the group's input rows, loaded in its own scope (volatile shared loads
-                 * are not merged across groups, so no row stays live in a register for
-                 * the rest of the warp's code) */
-                o << "        { ";
-                for (uint32_t row : rows_read(gi))
-                    if (row < R)
-                        o << "uint32_t s" << row << "; asm volatile(\"ld.shared.u32 %0, [%1+" << row * 128
-                          << "];\" : \"=r\"(s" << row << ") : \"r\"(scb)); ";
-                o << "{ ";
-                if (G.l2w == PBN_IMG_SPLIT) emit_split_group(r, G);
-                else emit_merged_group(r, gi, G);
-                o << "        }\n";
+              }
+              /* the batch's input rows, loaded in its own scope (volatile shared loads
+               * are not merged across batches, so no row stays live in a register for
+               * the rest of the warp's code) */
+              std::vector<uint32_t> brows;
+              for (size_t bi = b0; bi < b1; ++bi)
+                  for (uint32_t row : rows_read(order2[bi].second))
+                      if (row < R) brows.push_back(row);
+              std::sort(brows.begin(), brows.end());
+              brows.erase(std::unique(brows.begin(), brows.end()), brows.end());
+              o << "        { ";
+              for (uint32_t row : brows)
+                  o << "uint32_t s" << row << "; asm volatile(\"ld.shared.u32 %0, [%1+" << row * 128
+                    << "];\" : \"=r\"(s" << row << ") : \"r\"(scb)); ";
+              o << "\n";
+              for (size_t bi = b0; bi < b1; ++bi) {
+                  const uint32_t r = order2[bi].first, gi = order2[bi].second;
+                  const pbn_img_group& G = groups[gi];
+                  o << "          { ";
+                  if (G.l2w == PBN_IMG_SPLIT) emit_split_group(r, G);
+                  else emit_merged_group(r, gi, G);
+              }
+              o << "        }\n";
             }
             o << "      } else {\n";
             for (uint32_t r : myrows) o << "        n" << r << " = Sc[" << r << "u * 32u + lane];\n";
@@ -1604,7 +1620,8 @@ int jit_compile(const pbn_plan* plan, uint32_t flags) {
      * spends every register on overlap and then spills under the occupancy bound; -O1
      * keeps it within the bound */
     const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "--ptxas-options=-O1"};
-    const int rc = N.compile(prog, (flags & PBN_COMPILE_WARP_SPLIT) ? 4 : 3, opts);
+    const bool o1 = (flags & PBN_COMPILE_WARP_SPLIT) && !(flags & PBN_COMPILE_WS_O3);
+    const int rc = N.compile(prog, o1 ? 4 : 3, opts);
     size_t ls = 0;
     N.log_size(prog, &ls);
     std::string log(ls, '\0');
@@ -1675,9 +1692,11 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
 extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms) {
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
     if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER |
-                  PBN_COMPILE_WIDE | PBN_COMPILE_WARP_SPLIT | PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7)))
+                  PBN_COMPILE_WIDE | PBN_COMPILE_WARP_SPLIT | PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) |
+                  PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O3))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
-    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7))) && !(flags & PBN_COMPILE_WARP_SPLIT))
+    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) | PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O3)) &&
+        !(flags & PBN_COMPILE_WARP_SPLIT))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: warp counts and CTAs per SM need PBN_COMPILE_WARP_SPLIT");
     const int rc = pbn::jit_compile(plan, flags);
     if (rc == PBN_OK && compile_ms) *compile_ms = pbn::jit_state(plan)->compile_ms;
