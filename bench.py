@@ -512,8 +512,13 @@ def measure_batch(args):
 
     # the two batched forms on a short trial; the faster one runs the workload
     forms = {}
+    # the batched forms: the interpreter in CTAs of 512 or 1,024 threads, the compiled
+    # batch (one module: compiled networks' functions and the interpreter) and the
+    # split compiled batch (two persistent launches per chunk: the compiled networks,
+    # then the rest in 1,024-thread CTAs)
     for form, flags, threads in (("interpreted", None, 512), ("interpreted_1024", None, 1024),
-                                 ("compiled", _lib.PBN_COMPILE_INTERLEAVED, 512)):
+                                 ("compiled", _lib.PBN_COMPILE_INTERLEAVED, 512),
+                                 ("compiled_split", _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_BATCH_SPLIT, 512)):
         t0 = time.perf_counter()
         B = api.Batch(entries, device=dev, compile_flags=flags, threads=threads)
         build_s = time.perf_counter() - t0

@@ -406,7 +406,7 @@ typedef struct {
     uint64_t smem_bytes;       /* dynamic shared memory per CTA */
     double est_ops_per_step;   /* sum over networks of n_traj x ops_per_step */
     uint32_t n_compiled;       /* networks run by compiled code (pbn_batch_compile) */
-    uint32_t reserved;
+    uint32_t n_items_compiled; /* split batches: the compiled networks' work items */
 } pbn_batch_info;
 
 /* Describe a batch of networks for the persistent work-queue kernel: each network
@@ -446,6 +446,13 @@ int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
  * unsupported flags, no network compiles), PBN_ECUDA (NVRTC, nvJitLink or loading
  * failed), PBN_ENOMEM. */
 int pbn_batch_compile(pbn_batch* batch, uint32_t flags, double* compile_ms);
+/* Option of pbn_batch_compile (ORed into flags): a split batch.  The module holds
+ * only the compiled networks' functions; the other networks' items are shaped for
+ * the library's interpreter kernel of 1,024-thread CTAs.  Each run is then two
+ * persistent launches on the same queue and stream (the compiled networks' items,
+ * then the others), so that compiled code keeps its registers and the interpreter
+ * its warps. */
+#define PBN_BATCH_SPLIT 0x80000000u
 
 /* Serialise the batch's device table (network descriptors, then work items) into
  * host memory (cap >= desc_bytes); the caller copies it to a 16-byte aligned device

@@ -53,6 +53,7 @@ def PBN_COMPILE_WS_BATCH(b: int) -> int:
 
 
 PBN_COMPILE_WS_O3 = 0x40000
+PBN_BATCH_SPLIT = 0x80000000
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1
@@ -99,7 +100,7 @@ class BatchNet(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_nets", u32), ("n_items", u32), ("threads", u32), ("max_lanes", u32),
                 ("desc_bytes", u64), ("smem_bytes", u64), ("est_ops_per_step", f64),
-                ("n_compiled", u32), ("reserved", u32)]
+                ("n_compiled", u32), ("n_items_compiled", u32)]
 
 
 class SimArgs(ctypes.Structure):

@@ -67,6 +67,13 @@ struct pbn_batch {
      * dispatching persistent kernel, or null (the library's interpreter kernel) */
     void* module = nullptr;
     void* module_kernel = nullptr;
+    /* split batch: the module runs the compiled networks' items (the first n_items_c),
+     * then the library's 1,024-thread interpreter kernel the others, in a second
+     * launch on the same queue */
+    bool split = false;
+    uint32_t n_items_c = 0;
+    size_t smem_c = 0, smem_i = 0;
+    mutable int occ_i[kMaxDevices] = {0};
     ~pbn_batch() { pbn::jit_library_unload(module); }
     /* CTAs of the batch kernel per SM and the SM count, per device, found on the first
      * run on that device (so that later launches can be graph-captured) */
@@ -76,6 +83,8 @@ struct pbn_batch {
 };
 
 namespace {
+
+int interp_shape(const pbn_plan* plan, uint32_t T, NetDesc* D);
 
 /* Meta-state rows of network i: per 32-bit state row holding a meta node, the mask
  * of those nodes and the values they must take. */
@@ -155,8 +164,20 @@ int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D)
     D->off_ret = H.off_ret;
     D->off_pos = H.off_pos;
     D->off_tables = H.off_tables;
-    /* staging mode and trajectories per work item under the per-CTA cap:
-     * specs and tables staged, specs only, or nothing (read through L1) */
+    const int rc2 = interp_shape(plan, T, D);
+    if (rc2 != PBN_OK)
+        return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per trajectory", i,
+                    (unsigned long long)plan->per_traj_smem);
+    return PBN_OK;
+}
+
+/* The interpreter's shape of a network's work items for CTAs of T threads: staging
+ * mode and trajectory slots per item under the per-CTA shared-memory cap (specs and
+ * tables staged, specs only, or nothing: read through L1), the offset of the
+ * trajectory rows, and the lanes per trajectory.  PBN_ETOOBIG if not even 32
+ * trajectory rows fit. */
+int interp_shape(const pbn_plan* plan, uint32_t T, NetDesc* D) {
+    const pbn_img_header& H = plan->hdr;
     const uint64_t per = plan->per_traj_smem;
     auto fit = [&](uint64_t staged) -> uint32_t {
         const uint64_t off = (staged + 127u) & ~(uint64_t)127u;
@@ -175,9 +196,10 @@ int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D)
     } else if (nt_none) {
         D->specs_in_smem = 0; D->tables_in_smem = 0; D->stage_bytes = 0; D->nt = nt_none;
     } else {
-        return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per trajectory", i,
-                    (unsigned long long)per);
+        return PBN_ETOOBIG;
     }
+    D->stage_off = 0;
+    D->compiled = 0;
     D->smem_state_off = D->stage_bytes ? ((D->stage_bytes + 127u) & ~127u) : 0u;
     /* lanes per trajectory: fill the CTA's threads when few trajectories fit (wide
      * states); lane groups evaluate groups in shape order.  States of 32 words or more
@@ -233,8 +255,18 @@ void cut_items(pbn_batch* B) {
         }
     }
     std::stable_sort(B->items.begin(), B->items.end(), [&](const WorkItem& x, const WorkItem& y) {
+        if (B->split && B->nets[x.net].compiled != B->nets[y.net].compiled) return B->nets[x.net].compiled > 0;
         return cost[x.net] * x.n > cost[y.net] * y.n;
     });
+    B->n_items_c = 0;
+    B->smem_c = B->smem_i = 0;
+    for (const WorkItem& w : B->items)
+        if (B->nets[w.net].compiled) ++B->n_items_c;
+    for (uint32_t i = 0; i < n_nets; ++i) {
+        const NetDesc& D = B->nets[i];
+        if (D.compiled) B->smem_c = std::max<size_t>(B->smem_c, D.stage_bytes);
+        else B->smem_i = std::max<size_t>(B->smem_i, D.smem_state_off + (uint64_t)B->plans[i]->per_traj_smem * D.nt);
+    }
     B->info.n_nets = n_nets;
     B->info.n_items = (uint32_t)B->items.size();
     B->info.smem_bytes = smem_max;
@@ -242,6 +274,7 @@ void cut_items(pbn_batch* B) {
     B->info.max_lanes = max_lanes;
     B->info.est_ops_per_step = ops;
     B->info.n_compiled = n_compiled;
+    B->info.n_items_compiled = B->split ? B->n_items_c : 0u;
     const size_t nb = B->nets.size() * sizeof(NetDesc), ib = B->items.size() * sizeof(WorkItem);
     B->image.resize(nb + ib);
     memcpy(B->image.data(), B->nets.data(), nb);
@@ -284,6 +317,8 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
     if (!b) return fail(PBN_EINVAL, "pbn_batch_compile: NULL batch");
     if (b->module) return fail(PBN_EINVAL, "pbn_batch_compile: the batch is compiled already");
     if (b->threads != 512) return fail(PBN_EINVAL, "pbn_batch_compile: compiled batches run CTAs of 512 threads");
+    const bool split = (flags & PBN_BATCH_SPLIT) != 0;
+    flags &= ~PBN_BATCH_SPLIT;
     if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_WIDE))
         return fail(PBN_EINVAL, "pbn_batch_compile: unsupported flags 0x%x", flags);
     try {
@@ -321,12 +356,25 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
         if (compiled.empty())
             return fail(PBN_EINVAL, "pbn_batch_compile: no network of the batch compiles (%s)", first_why.c_str());
         std::sort(compiled.begin(), compiled.end());
-        const bool interp = compiled.size() < b->nets.size();
+        /* split: the module holds only compiled networks; the others run in the
+         * library's 1,024-thread kernel, with their items shaped for it */
+        const bool interp = !split && compiled.size() < b->nets.size();
+        std::vector<NetDesc> wide_desc;
+        if (split) {
+            std::vector<uint8_t> is_c(b->nets.size(), 0);
+            for (uint32_t i : compiled) is_c[i] = 1;
+            wide_desc = b->nets;
+            for (uint32_t i = 0; i < (uint32_t)b->nets.size(); ++i)
+                if (!is_c[i] && interp_shape(b->plans[i], 1024, &wide_desc[i]) != PBN_OK)
+                    return fail(PBN_ETOOBIG, "pbn_batch_compile: network %u does not fit a 1,024-thread CTA", i);
+        }
         void *lib = nullptr, *kern = nullptr;
         double ms = 0;
         std::string log;
         const int rc = pbn::jit_batch_module(functions, compiled, interp, b->threads, &lib, &kern, &ms, &log);
         if (rc != PBN_OK) return rc;
+        if (split) b->nets = wide_desc;
+        b->split = split;
         /* compiled networks: one trajectory per thread, their tables (when the code
          * reads them from shared memory) staged from the plan image */
         for (uint32_t i : compiled) {
@@ -346,7 +394,7 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
         {
             /* a new kernel: its occupancy is found again on each device */
             std::lock_guard<std::mutex> g(b->mu);
-            for (int d = 0; d < kMaxDevices; ++d) b->occ_per_sm[d] = b->sms[d] = 0;
+            for (int d = 0; d < kMaxDevices; ++d) b->occ_per_sm[d] = b->sms[d] = b->occ_i[d] = 0;
         }
         if (compile_ms) *compile_ms = ms;
         return PBN_OK;
@@ -378,39 +426,75 @@ const void* batch_kernel(const pbn_batch* b) {
     return b->threads == 1024 ? pbn::batch_kernel_1024() : reinterpret_cast<const void*>(pbn_batch_kernel);
 }
 
-cudaError_t launch_batch(const pbn_batch* b, const BatchParams& P, uint32_t grid, cudaStream_t st) {
-    void* args[] = {const_cast<BatchParams*>(&P)};
-    return cudaLaunchKernel(batch_kernel(b), dim3(grid), dim3(b->threads), args, b->info.smem_bytes, st);
+/* One persistent launch of a batch: a kernel, its CTA size and shared memory, and
+ * the range of work items it takes. */
+struct Part {
+    const void* kern;
+    uint32_t threads;
+    size_t smem;
+    uint32_t first, count;
+    bool interp_1024;  /* the split batch's interpreter part (its own occupancy record) */
+};
+
+/* The launches of a batch: one, or for a split batch the compiled networks' items
+ * (module kernel) and then the interpreted ones (1,024-thread kernel). */
+std::vector<Part> batch_parts(const pbn_batch* b) {
+    std::vector<Part> parts;
+    if (!b->split) {
+        parts.push_back(Part{batch_kernel(b), b->threads, b->info.smem_bytes, 0u, b->info.n_items, false});
+        return parts;
+    }
+    if (b->n_items_c) parts.push_back(Part{b->module_kernel, 512u, b->smem_c, 0u, b->n_items_c, false});
+    if (b->info.n_items > b->n_items_c)
+        parts.push_back(Part{pbn::batch_kernel_1024(), 1024u, b->smem_i, b->n_items_c, b->info.n_items - b->n_items_c, true});
+    return parts;
 }
 
-/* Grid of the batch kernel on the current device: raises the kernel's shared-memory
- * limit there to the batch's need (never lowering what another batch set), and finds
- * the CTAs per SM and the SM count of that device on the batch's first run on it. */
-int launch_shape(const pbn_batch* b, uint32_t ctas_per_sm, const char* who, uint32_t* grid) {
+/* Grid of one part on the current device: raises the kernel's shared-memory limit
+ * there to the part's need (never lowering what another batch set), and finds the
+ * CTAs per SM and the SM count of that device on the batch's first run on it. */
+int launch_shape(const pbn_batch* b, const Part& pt, uint32_t ctas_per_sm, const char* who, uint32_t* grid) {
     using pbn::fail;
-    const size_t smem = b->info.smem_bytes;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(PBN_EINVAL, "%s: device %d beyond %d", who, dev, kMaxDevices);
-    const void* kern = batch_kernel(b);
-    const int se = pbn::ensure_dyn_smem(kern, smem);
+    const int se = pbn::ensure_dyn_smem(pt.kern, pt.smem);
     if (se != 0) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(static_cast<cudaError_t>(se)));
     int per_sm = 0, sms = 0;
     {
         std::lock_guard<std::mutex> g(b->mu);
-        if (!b->occ_per_sm[dev]) {
-            int occ = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, (int)b->threads, smem);
-            if (e != cudaSuccess || occ < 1) return fail(PBN_ETOOBIG, "%s: the batch kernel does not fit an SM", who);
-            b->occ_per_sm[dev] = occ;
-            b->sms[dev] = pbn::device_sms();
+        int* occ = pt.interp_1024 ? &b->occ_i[dev] : &b->occ_per_sm[dev];
+        if (!*occ) {
+            int o = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, pt.kern, (int)pt.threads, pt.smem);
+            if (e != cudaSuccess || o < 1) return fail(PBN_ETOOBIG, "%s: the batch kernel does not fit an SM", who);
+            *occ = o;
         }
-        per_sm = b->occ_per_sm[dev];
+        if (!b->sms[dev]) b->sms[dev] = pbn::device_sms();
+        per_sm = *occ;
         sms = b->sms[dev];
     }
     if (ctas_per_sm && (int)ctas_per_sm < per_sm) per_sm = (int)ctas_per_sm;
-    *grid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, std::max<uint32_t>(1u, b->info.n_items));
+    *grid = (uint32_t)std::min<uint64_t>((uint64_t)sms * per_sm, std::max<uint32_t>(1u, pt.count));
+    return PBN_OK;
+}
+
+/* Every launch of the batch on `st`, one after the other on the same queue (the last
+ * CTA of each launch resets it for the next). */
+int launch_all(const pbn_batch* b, BatchParams P, uint32_t ctas_per_sm, const char* who, cudaStream_t st) {
+    using pbn::fail;
+    const WorkItem* items = P.items;
+    for (const Part& pt : batch_parts(b)) {
+        uint32_t grid = 0;
+        const int rc = launch_shape(b, pt, ctas_per_sm, who, &grid);
+        if (rc != PBN_OK) return rc;
+        P.items = items + pt.first;
+        P.n_items = pt.count;
+        void* args[] = {&P};
+        const cudaError_t e = cudaLaunchKernel(pt.kern, dim3(grid), dim3(pt.threads), args, pt.smem, st);
+        if (e != cudaSuccess) return fail(PBN_ECUDA, "%s: %s", who, cudaGetErrorString(e));
+    }
     return PBN_OK;
 }
 }  // namespace
@@ -431,12 +515,7 @@ extern "C" int pbn_batch_run(const pbn_batch* b, const void* d_desc, uint32_t* d
     P.step_offset = step_offset;
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
-    uint32_t grid = 0;
-    int rc = launch_shape(b, ctas_per_sm, "pbn_batch_run", &grid);
-    if (rc != PBN_OK) return rc;
-    const cudaError_t e = launch_batch(b, P, grid, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run: %s", cudaGetErrorString(e));
-    return PBN_OK;
+    return launch_all(b, P, ctas_per_sm, "pbn_batch_run", static_cast<cudaStream_t>(stream));
 }
 
 /* ---- allocation-free variant of pbn_batch_run ------------------------------------------
@@ -499,10 +578,5 @@ extern "C" int pbn_batch_run_static(const pbn_batch* b, const void* d_desc, uint
     P.step_offset = step_offset;
     P.n_items = b->info.n_items;
     P.n_steps = (uint32_t)n_steps;
-    uint32_t grid = 0;
-    const int rc = launch_shape(b, ctas_per_sm, "pbn_batch_run_static", &grid);
-    if (rc != PBN_OK) return rc;
-    e = launch_batch(b, P, grid, st);
-    if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_batch_run_static: %s", cudaGetErrorString(e));
-    return PBN_OK;
+    return launch_all(b, P, ctas_per_sm, "pbn_batch_run_static", st);
 }

@@ -213,3 +213,38 @@ def test_batch_of_1024_thread_ctas_against_oracle(oracle_mod):
     e2, _ = _entries(nets[:1])
     with pytest.raises(_lib.PbnError):
         api.Batch(e2, threads=1024, compile_flags=_lib.PBN_COMPILE_INTERLEAVED)
+
+
+def test_split_batch_against_oracle_graph_and_static_queue(oracle_mod):
+    """A split compiled batch (the compiled networks' items in the generated module,
+    the others in the 1,024-thread interpreter kernel, two launches per chunk on one
+    queue) gives the oracle's states and counts through direct runs, a CUDA graph
+    and the allocation-free entry point."""
+    import torch
+    nets = _mix(58, [30, 75, 160, 900, 1400, 2200], 180)
+    split = _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_BATCH_SPLIT
+    e1, plans = _entries(nets)
+    e2, _ = _entries(nets)
+    e3, _ = _entries(nets)
+    b1, b2, b3 = (api.Batch(e, compile_flags=split) for e in (e1, e2, e3))
+    assert 0 < b1.info.n_items_compiled < b1.info.n_items and b1.info.n_compiled == 3
+    for c in [120, 1, 179]:
+        b1.run(c)
+        b3.run_static(c, slot=4)
+    b2.run(1)
+    torch.cuda.synchronize()
+    for e in e2:
+        e["bufs"].counts.zero_(); e["bufs"].pooled.zero_()
+    g = b2.capture([120, 1, 179], step_offset=0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(b1.status.item()) == int(b2.status.item()) == int(b3.status.item()) == 0
+    assert b1.queue.cpu().tolist() == [0, 0]
+    for k, (d, (plan, ids)) in enumerate(zip(nets, plans)):
+        orc = oracle_mod.simulate(d["text"], d["seed"], k * 10**5, d["T"], 300, meta_ids=d["meta"],
+                                  meta_vals=d["vals"], count_from=21, nthreads=NCPU)
+        for es in (e1, e2, e3):
+            got = _collect(plan, es[k]["bufs"])
+            assert np.array_equal(got["final"][:, ids], orc["final"][:, ids]), k
+            assert np.array_equal(got["counts"], orc["counts"]), k
+            assert np.array_equal(got["pooled"], orc["counts"].sum(axis=0, dtype=np.uint64)), k
