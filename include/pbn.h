@@ -352,16 +352,15 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
  * double-buffered in shared memory as [row][lane]; each warp runs straight-line code
  * for its own share of the perturbation word pairs and of the state rows (their SEL
  * blocks and merged groups), with two CTA barriers per step.  K is
- * PBN_COMPILE_WARPS(K) (1..31), or chosen from the plan's size when 0.  Results equal
- * every other form's. */
+ * PBN_COMPILE_WARPS(K) (1..31), or 2 when 0.  Results equal every other form's. */
 #define PBN_COMPILE_WARP_SPLIT 0x20u
 #define PBN_COMPILE_WARPS(k) (((uint32_t)(k) & 31u) << 8)
 /* with PBN_COMPILE_WARP_SPLIT: registers limited so that m (1..7) CTAs fit an SM */
 #define PBN_COMPILE_MINCTAS(m) (((uint32_t)(m) & 7u) << 13)
 /* with PBN_COMPILE_WARP_SPLIT: groups evaluated in batches of 4^b (b = 0..3) whose
- * state rows are loaded together; ptxas at its default -O3 instead of -O1 */
+ * state rows are loaded together; ptxas at -O1 instead of its default -O3 */
 #define PBN_COMPILE_WS_BATCH(b) (((uint32_t)(b) & 3u) << 16)
-#define PBN_COMPILE_WS_O3 0x40000u
+#define PBN_COMPILE_WS_O1 0x40000u
 
 /* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
  * thread, local-memory (spill) bytes per thread and the flags it was compiled with;

@@ -52,7 +52,7 @@ def PBN_COMPILE_WS_BATCH(b: int) -> int:
     return (b & 3) << 16
 
 
-PBN_COMPILE_WS_O3 = 0x40000
+PBN_COMPILE_WS_O1 = 0x40000
 PBN_BATCH_SPLIT = 0x80000000
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0

@@ -63,7 +63,10 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                                         _lib.PBN_COMPILE_PIPELINED | _lib.PBN_COMPILE_MAGIC_GATHER),
                  try_compiled: bool = True, cache_file: str | None = None, log=None,
                  sampler: int = _lib.PBN_PERT_BITSLICED,
-                 warp_split_options=((0, 0), (4, 0)), warp_split_max_inputs: int = 8) -> Choice:
+                 warp_split_options=(_lib.PBN_COMPILE_WARPS(2) | _lib.PBN_COMPILE_WS_BATCH(1),
+                                     _lib.PBN_COMPILE_WARPS(2),
+                                     _lib.PBN_COMPILE_WARPS(4)),
+                 warp_split_max_inputs: int = 8) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
     placement) for simulating n_traj trajectories of this network."""
     net = api.Net.load(text)
@@ -116,11 +119,13 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                 # one group size)
                 if (warp_split_options and mi == warp_split_max_inputs
                         and (plan.info.state_words >= 4 or plan.info.n_sel_blocks > 24)):
+                    # (on the scale-free network: 2 warps per CTA, ptxas -O3 and groups in
+                    # batches of 4 ran 1.29x the interpreter; 4 or more warps, or -O1,
+                    # ran slower than it)
                     ws = []
-                    for K, m in warp_split_options:
-                        f = _lib.PBN_COMPILE_WARP_SPLIT | _lib.PBN_COMPILE_WARPS(K) | _lib.PBN_COMPILE_MINCTAS(m)
+                    for extra in warp_split_options:
                         pw = api.Plan(red, max_inputs=mi, sampler=sampler)
-                        ws.append((f, pw))
+                        ws.append((_lib.PBN_COMPILE_WARP_SPLIT | extra, pw))
 
                     def _compile(fp):
                         try:

@@ -281,8 +281,12 @@ public:
                 cost[r / 2] += c;
                 total += c;
             }
+        /* two warps per CTA unless asked: on the scale-free network 2 warps ran faster
+         * than 1, 3, 4 or 8 (more warps add barrier waits and re-drawn SEL blocks,
+         * fewer leave too little to overlap) */
         uint32_t K = (flags_ >> 8) & 31u;
-        if (!K) K = (uint32_t)std::min<double>(16.0, std::max(2.0, std::ceil(total / 2500.0)));
+        if (!K) K = 2;
+        (void)total;
         K = std::max(1u, std::min(K, npairs));
         warps = K;
         /* row pairs to warps: largest first to the least loaded warp */
@@ -1617,10 +1621,12 @@ int jit_compile(const pbn_plan* plan, uint32_t flags) {
         return fail(PBN_ECUDA, "nvrtcCreateProgram failed");
     }
     /* the warp-split form's long straight-line warp code: ptxas's default schedule
-     * spends every register on overlap and then spills under the occupancy bound; -O1
-     * keeps it within the bound */
+     * spends every register on overlap (and spills under a tight occupancy bound);
+     * PBN_COMPILE_WS_O1 asks for -O1, which keeps fewer values live but overlaps less
+     * (on the scale-free network the default schedule ran faster at every warp
+     * count) */
     const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "-lineinfo", "--ptxas-options=-O1"};
-    const bool o1 = (flags & PBN_COMPILE_WARP_SPLIT) && !(flags & PBN_COMPILE_WS_O3);
+    const bool o1 = (flags & PBN_COMPILE_WARP_SPLIT) && (flags & PBN_COMPILE_WS_O1);
     const int rc = N.compile(prog, o1 ? 4 : 3, opts);
     size_t ls = 0;
     N.log_size(prog, &ls);
@@ -1693,9 +1699,9 @@ extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* co
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
     if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER |
                   PBN_COMPILE_WIDE | PBN_COMPILE_WARP_SPLIT | PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) |
-                  PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O3))
+                  PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O1))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
-    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) | PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O3)) &&
+    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) | PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O1)) &&
         !(flags & PBN_COMPILE_WARP_SPLIT))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: warp counts and CTAs per SM need PBN_COMPILE_WARP_SPLIT");
     const int rc = pbn::jit_compile(plan, flags);
