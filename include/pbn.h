@@ -361,6 +361,10 @@ int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* compile_ms);
  * state rows are loaded together; ptxas at -O1 instead of its default -O3 */
 #define PBN_COMPILE_WS_BATCH(b) (((uint32_t)(b) & 3u) << 16)
 #define PBN_COMPILE_WS_O1 0x40000u
+/* with PBN_COMPILE_WARP_SPLIT: the SEL blocks drawn before the barrier by one short
+ * loop split over the warps, the choices kept as bytes in shared memory (smaller code,
+ * no block drawn twice) */
+#define PBN_COMPILE_WS_SELSMEM 0x80000u
 
 /* Attributes of the plan's compiled kernel (after pbn_plan_compile): registers per
  * thread, local-memory (spill) bytes per thread and the flags it was compiled with;

@@ -53,6 +53,7 @@ def PBN_COMPILE_WS_BATCH(b: int) -> int:
 
 
 PBN_COMPILE_WS_O1 = 0x40000
+PBN_COMPILE_WS_SELSMEM = 0x80000
 PBN_BATCH_SPLIT = 0x80000000
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0

@@ -193,6 +193,8 @@ struct Generated {
     std::string src;
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
     uint32_t warps = 0;      /* warp-split form: warps per CTA (32 trajectories); 0: one trajectory per thread */
+    uint32_t dyn_smem = 0;   /* dynamic shared memory to launch with (0: tab_bytes) */
+    uint32_t static_smem = 256; /* upper bound of the kernel's static shared memory */
 };
 
 using BatchSpec = pbn::JitBatchNet;
@@ -264,7 +266,26 @@ public:
         out->tab_bytes = tab_smem ? table_bytes : 0u;
         geometric = H.sampler == PBN_PERT_GEOMETRIC;
         interleave = true;
-        ws_choices_ = true;
+        /* PBN_COMPILE_WS_SELSMEM: the SEL blocks are drawn in phase A, split over the
+         * warps by one short loop (thresholds in constant memory), and their choices
+         * kept as bytes in shared memory for phase B; otherwise each warp draws the
+         * blocks its groups need in its own straight-line code */
+        ch_smem_ = (flags_ & PBN_COMPILE_WS_SELSMEM) != 0 && H.n_sel > 0;
+        ws_choices_ = !ch_smem_;
+        const uint32_t ch_off = ch_smem_ ? ((tab_smem ? table_bytes : 0u) + 127u) & ~127u : 0u;
+        const uint32_t ch_bytes = ch_smem_ ? 4u * H.n_sel * 32u : 0u;
+        if (ch_smem_ && 16u * 4u * H.n_sel + 4u * (H.off_inputs - H.off_thr) > 60u * 1024u) {
+            *why = "the selection thresholds exceed constant memory";
+            return false;
+        }
+        out->dyn_smem = ch_smem_ ? ch_off + ch_bytes : 0u;
+        /* SA, SB, PF, ZF and the barrier */
+        out->static_smem = 2u * 4u * 32u * H.W32 + 4u * 4u * 32u + 256u;
+        if ((out->dyn_smem ? out->dyn_smem : (tab_smem ? table_bytes : 0u)) + out->static_smem >
+            227u * 1024u) { /* opt-in shared memory of a CTA on sm_103a */
+            *why = "the states, tables and choices exceed the shared memory of a CTA";
+            return false;
+        }
         Pv = H.P;
         hmax = Pv ? (31u - (uint32_t)__builtin_ctz(Pv)) / 2u + 1u : 0u;
         const uint32_t npairs = (H.W32 + 1) / 2; /* row pairs: one uint64 state word each */
@@ -311,6 +332,22 @@ public:
             o << "};\n";
         }
         const uint32_t R = H.W32;
+        if (ch_smem_) {
+            /* per SEL slot (4 per block, slot-major): t1, t2, number of thresholds, first
+             * extra threshold; the block counters; the extra thresholds */
+            o << "__constant__ uint4 SELS[" << 4 * H.n_sel << "] = {";
+            for (uint32_t slot = 0; slot < 4 * H.n_sel; ++slot) {
+                const uint32_t* ss = selslot + 4 * ((slot & 3u) * H.n_sel + (slot >> 2));
+                o << (slot ? (slot % 4 ? ", " : ",\n  ") : "") << "{" << hex32(ss[0]) << ", " << hex32(ss[1]) << ", "
+                  << ss[2] << "u, " << ss[3] << "u}";
+            }
+            o << "};\n__constant__ uint32_t SELB[" << H.n_sel << "] = {";
+            for (uint32_t b = 0; b < H.n_sel; ++b) o << (b ? ", " : "") << hex32((PBN_DOM_SEL << 28) | selblk[b]);
+            const uint32_t nthr = std::max<uint32_t>(1u, (H.off_inputs - H.off_thr) / 4u);
+            o << "};\n__constant__ uint32_t SELT[" << nthr << "] = {";
+            for (uint32_t i = 0; i < nthr; ++i) o << (i ? (i % 8 ? ", " : ",\n  ") : "") << hex32(i < (H.off_inputs - H.off_thr) / 4u ? thr[i] : 0u);
+            o << "};\n";
+        }
         const uint32_t minctas = (flags_ >> 13) & 7u; /* resident CTAs per SM the registers must allow */
         o << "extern \"C\" __global__ void __launch_bounds__(" << 32 * K;
         if (minctas) o << ", " << minctas;
@@ -329,7 +366,11 @@ public:
              "  const uint32_t lt = blockIdx.x * 32u + lane;\n"
              "  const bool active = lt < P.n_traj;\n"
              "  const uint64_t traj = P.traj_begin + lt;\n"
-             "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n"
+             "  uint32_t cV = 0, c01 = 0, c10 = 0, c11 = 0;\n";
+        if (ch_smem_)
+            o << "  uint8_t* const CH = smem + " << ch_off << "u; /* [slot][lane] choice bytes */\n"
+                 "  const uint8_t* const CHs = CH + lane;\n";
+        o << ""
           << "  for (uint32_t i = threadIdx.x; i < " << R * 32 << "u; i += blockDim.x) SA[i] = 0u;\n"
              "  for (uint32_t i = threadIdx.x; i < 64u; i += blockDim.x) { PF[i >> 5][i & 31u] = 0u; ZF[i >> 5][i & 31u] = 1u; }\n"
              "  __syncthreads();\n";
@@ -407,7 +448,21 @@ public:
             o << "      if (any) PF[k & 1u][lane] = 1u;\n    } break;\n";
         }
         pair_sel_.clear();
-        o << "    default: break;\n    }\n    __syncthreads();\n"
+        o << "    default: break;\n    }\n";
+        if (ch_smem_)
+            o << "    /* the SEL blocks, round robin over the warps: choices as bytes */\n"
+                 "#pragma unroll 1\n"
+                 "    for (uint32_t b = warp; b < " << H.n_sel << "u; b += " << K << "u) {\n"
+                 "      const uint4 x = pbn_philox_draw(P, ps, SELB[b]);\n"
+                 "      const uint32_t u[4] = {x.x, x.y, x.z, x.w};\n"
+                 "#pragma unroll\n"
+                 "      for (int l = 0; l < 4; ++l) {\n"
+                 "        const uint4 S = SELS[4u * b + l];\n"
+                 "        uint32_t j = ((S.z >= 1u) & (u[l] >= S.x)) + ((S.z >= 2u) & (u[l] >= S.y));\n"
+                 "        if (S.z > 2u) { j = 0; for (uint32_t q = 0; q < S.z; ++q) j += (u[l] >= SELT[S.w + q]) ? 1u : 0u; }\n"
+                 "        CH[(4u * b + l) * 32u + lane] = (uint8_t)j;\n"
+                 "      }\n    }\n";
+        o << "    __syncthreads();\n"
              "    const uint32_t pert = PF[k & 1u][lane];\n"
              "    const uint32_t scb = (uint32_t)__cvta_generic_to_shared(Sc) + 4u * lane;\n";
         /* phase B: each warp's row pairs */
@@ -448,7 +503,7 @@ public:
               for (size_t bi = b0; bi < b1; ++bi) {
                 const uint32_t gi = order2[bi].second;
                 for (uint32_t b : blocks_of(gi))
-                    if (drawn_at[b] < 0 || gcount - drawn_at[b] > (int64_t)kReuse) {
+                    if (!ch_smem_ && (drawn_at[b] < 0 || gcount - drawn_at[b] > (int64_t)kReuse)) {
                         /* the block's four uniforms become the choices of its slots at once
                          * (one register per node instead of four per block) */
                         drawn_at[b] = gcount;
@@ -598,6 +653,7 @@ private:
     bool pair_selected(uint32_t wp) const { return pair_sel_.empty() || (wp < pair_sel_.size() && pair_sel_[wp]); }
     const std::string sfx_; /* suffix of the module-level names (unique per network) */
     bool ws_choices_ = false; /* choices as J<slot> registers computed after each draw */
+    bool ch_smem_ = false;    /* choices as bytes CH[slot][lane] in shared memory */
   public:
     int ws_reuse = 16;        /* warp split: groups over which a drawn SEL block is reused */
   private:
@@ -923,9 +979,12 @@ private:
 
     /* choice of a multi-function node from its SEL slot's thresholds */
     std::string choice_expr(const pbn_img_multi& M) const {
-        if (ws_choices_) { /* warp split: the choice was computed right after its block's draw */
+        if (ws_choices_ || ch_smem_) {
             const uint32_t* ss = selslot + 4 * ((M.ch_off & 3u) * H.n_sel + (M.ch_off >> 2));
-            return ss[2] ? fmt("J%u", M.ch_off) : std::string();
+            if (!ss[2]) return std::string();
+            /* warp split: the choice computed right after its block's draw, or read from
+             * the choice bytes the warps wrote in phase A */
+            return ch_smem_ ? fmt("((uint32_t)CHs[%uu])", 32u * M.ch_off) : fmt("J%u", M.ch_off);
         }
         return slot_choice(M.ch_off);
     }
@@ -1568,6 +1627,8 @@ struct pbn_jit_state {
     cudaKernel_t kern = nullptr;
     uint32_t tab_bytes = 0;
     uint32_t warps = 0;  /* warp-split form: warps per CTA of 32 trajectories */
+    uint32_t dyn_smem = 0; /* dynamic shared memory of a launch (0: tab_bytes) */
+    uint32_t static_smem = 256; /* upper bound of the kernel's static shared memory */
     double compile_ms = 0;
 };
 
@@ -1652,6 +1713,8 @@ int jit_compile(const pbn_plan* plan, uint32_t flags) {
     }
     J->tab_bytes = gen.tab_bytes;
     J->warps = gen.warps;
+    J->dyn_smem = gen.dyn_smem;
+    J->static_smem = gen.static_smem;
     J->src = std::move(gen.src);
     J->compile_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     J->state = 1;
@@ -1687,8 +1750,11 @@ int jit_launch(const pbn_plan* plan, pbn_jit_params* P, uint32_t n_traj, int sms
         grid = (n_traj + tpb - 1) / tpb;
     }
     void* args[] = {P};
+    const size_t dyn = J->dyn_smem ? J->dyn_smem : J->tab_bytes;
+    const int se = ensure_dyn_smem(reinterpret_cast<const void*>(J->kern), dyn, J->static_smem);
+    if (se != 0) return fail(PBN_ECUDA, "compiled plan launch: %s", cudaGetErrorString(static_cast<cudaError_t>(se)));
     cudaError_t e = cudaLaunchKernel(reinterpret_cast<const void*>(J->kern), dim3((unsigned)grid), dim3((unsigned)tpb), args,
-                                     J->tab_bytes, st);
+                                     dyn, st);
     if (e != cudaSuccess) return fail(PBN_ECUDA, "compiled plan launch: %s", cudaGetErrorString(e));
     return PBN_OK;
 }
@@ -1699,9 +1765,10 @@ extern "C" int pbn_plan_compile(const pbn_plan* plan, uint32_t flags, double* co
     if (!plan) return pbn::fail(PBN_EINVAL, "pbn_plan_compile: NULL plan");
     if (flags & ~(PBN_COMPILE_PERT_UNROLLED | PBN_COMPILE_INTERLEAVED | PBN_COMPILE_PIPELINED | PBN_COMPILE_MAGIC_GATHER |
                   PBN_COMPILE_WIDE | PBN_COMPILE_WARP_SPLIT | PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) |
-                  PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O1))
+                  PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O1 | PBN_COMPILE_WS_SELSMEM))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: unknown flags");
-    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) | PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O1)) &&
+    if ((flags & (PBN_COMPILE_WARPS(31) | PBN_COMPILE_MINCTAS(7) | PBN_COMPILE_WS_BATCH(3) | PBN_COMPILE_WS_O1 |
+                  PBN_COMPILE_WS_SELSMEM)) &&
         !(flags & PBN_COMPILE_WARP_SPLIT))
         return pbn::fail(PBN_EINVAL, "pbn_plan_compile: warp counts and CTAs per SM need PBN_COMPILE_WARP_SPLIT");
     const int rc = pbn::jit_compile(plan, flags);

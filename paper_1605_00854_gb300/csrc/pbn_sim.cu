@@ -177,8 +177,8 @@ const DeviceFacts& facts() {
 int device_sms() { return facts().sms; }
 int device_smem_optin() { return facts().smem_optin; }
 
-int ensure_dyn_smem(const void* func, size_t bytes) {
-    if (bytes <= 48u * 1024u) return 0;
+int ensure_dyn_smem(const void* func, size_t bytes, size_t static_bytes) {
+    if (bytes + static_bytes <= 48u * 1024u) return 0;
     const int dev = current_device();
     std::lock_guard<std::mutex> g(g_dev_mu);
     size_t& set = g_smem_set[std::make_pair(dev, func)];

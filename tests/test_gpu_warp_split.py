@@ -2,7 +2,8 @@
 trajectories, each warp its own share of the perturbation words and state rows, the
 states in shared memory.  Bit-exact against the CPU oracle (every step's state, the
 counts, the pooled counts) on small and wide plans, ragged trajectory counts, chained
-launches cut at the window start, split nodes, the geometric sampler and p = 0."""
+launches cut at the window start, split nodes, the geometric sampler and p = 0, with
+the selection choices in registers and in shared memory (PBN_COMPILE_WS_SELSMEM)."""
 import os
 
 import numpy as np
@@ -15,6 +16,7 @@ pytestmark = pytest.mark.gpu
 NCPU = os.cpu_count() or 1
 COMPILED = _lib.PBN_KERNEL_COMPILED
 WS = _lib.PBN_COMPILE_WARP_SPLIT
+SELSMEM = _lib.PBN_COMPILE_WS_SELSMEM
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,24 +35,25 @@ def _compare(gpu, orc, ids, trace=True):
         assert np.array_equal(gpu["trace"][:, :, ids], orc["trace"][:, :, ids])
 
 
-@pytest.mark.parametrize("warps", [1, 2])
-def test_tiny12_every_step(oracle_mod, warps):
+@pytest.mark.parametrize("warps,extra", [(1, 0), (2, 0), (1, SELSMEM), (2, SELSMEM)])
+def test_tiny12_every_step(oracle_mod, warps, extra):
     text = synth.tiny12(1).to_text()
     meta = [0, 1, 2]
     plan, ids = plan_for(text, meta)
-    plan.compile(WS | _lib.PBN_COMPILE_WARPS(warps))
+    plan.compile(WS | _lib.PBN_COMPILE_WARPS(warps) | extra)
     orc = oracle_mod.simulate(text, 1, 0, 70, 3000, meta_ids=meta, trace=True, nthreads=NCPU)
     _compare(run(plan, seed=1, n_traj=70, n_steps=3000, meta=meta, trace=True, kernel=COMPILED), orc, ids)
 
 
-@pytest.mark.parametrize("n,warps,minctas", [(100, 0, 0), (300, 4, 0), (300, 3, 3), (700, 0, 2), (1500, 8, 0)])
-def test_wide_plans_against_oracle(oracle_mod, n, warps, minctas):
+@pytest.mark.parametrize("n,warps,minctas,extra", [(100, 0, 0, 0), (300, 4, 0, 0), (300, 3, 3, 0), (700, 0, 2, 0),
+                                                   (1500, 8, 0, 0), (300, 2, 0, SELSMEM), (1500, 3, 0, SELSMEM)])
+def test_wide_plans_against_oracle(oracle_mod, n, warps, minctas, extra):
     """Paper-scale networks up to 1,500 nodes (beyond the register-state forms), a
     ragged trajectory count, chained launches cut where the window starts."""
     text = synth.paper100(seed=40 + n, n=n, p=2e-3).to_text()
     meta = [0, 1, 2]
     plan, ids = plan_for(text, meta)
-    plan.compile(WS | _lib.PBN_COMPILE_WARPS(warps) | _lib.PBN_COMPILE_MINCTAS(minctas))
+    plan.compile(WS | _lib.PBN_COMPILE_WARPS(warps) | _lib.PBN_COMPILE_MINCTAS(minctas) | extra)
     T, S = 150, 600
     orc = oracle_mod.simulate(text, 3, 500, T, S, meta_ids=meta, count_from=200, nthreads=NCPU)
     got = run(plan, seed=3, traj_begin=500, n_traj=T, n_steps=S, meta=meta, count_from=200, chunks=[200, 250, 150],
@@ -58,7 +61,8 @@ def test_wide_plans_against_oracle(oracle_mod, n, warps, minctas):
     _compare(got, orc, ids, trace=False)
 
 
-def test_split_nodes_geometric_and_p0(oracle_mod):
+@pytest.mark.parametrize("extra", [0, SELSMEM])
+def test_split_nodes_geometric_and_p0(oracle_mod, extra):
     """Split nodes (tables per function, some looked up), the geometric sampler and a
     network without perturbations, each against its oracle path, with traces."""
     cases = [
@@ -68,18 +72,19 @@ def test_split_nodes_geometric_and_p0(oracle_mod):
     ]
     for text, meta, kw, okw in cases:
         plan, ids = plan_for(text, meta, **kw)
-        plan.compile(WS | _lib.PBN_COMPILE_WARPS(2))
+        plan.compile(WS | _lib.PBN_COMPILE_WARPS(2) | extra)
         orc = oracle_mod.simulate(text, 8, 0, 40, 400, meta_ids=meta, trace=True, nthreads=NCPU, **okw)
         _compare(run(plan, seed=8, n_traj=40, n_steps=400, meta=meta, trace=True, kernel=COMPILED), orc, ids)
 
 
-def test_scalefree_sampled_against_oracle(oracle_mod):
+@pytest.mark.parametrize("extra", [0, SELSMEM | _lib.PBN_COMPILE_WS_BATCH(1)])
+def test_scalefree_sampled_against_oracle(oracle_mod, extra):
     """The 2,000-node scale-free network: trajectories sampled from a launch of 1,024,
     each equal to the oracle's."""
     text = synth.scalefree2000(seed=3).to_text()
     meta = [0, 1, 2, 3]
     plan, ids = plan_for(text, meta)
-    plan.compile(WS)
+    plan.compile(WS | extra)
     T, S = 1024, 300
     got = run(plan, seed=5, n_traj=T, n_steps=S, meta=meta, count_from=50, kernel=COMPILED)
     assert got["status"] == 0

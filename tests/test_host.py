@@ -385,12 +385,14 @@ def test_generated_plan_kernels_compile(tmp_path, which, flags):
     assert proc.returncode == 0, proc.stderr[-3000:]
 
 
-@pytest.mark.parametrize("which,warps,minctas", [("tiny12", 1, 0), ("p300", 4, 0), ("p300", 2, 3),
-                                                  ("split_wide", 0, 0), ("geometric", 3, 0), ("p0", 2, 0)])
-def test_warp_split_kernels_compile(tmp_path, which, warps, minctas):
-    """The warp-split form's generated source compiles for sm_103a (ptxas -O1, as the
-    library compiles it), for small and mid-size plans, split nodes, the geometric
-    sampler and p = 0; node-wise semantics are refused."""
+@pytest.mark.parametrize("which,warps,minctas,selsmem", [
+    ("tiny12", 1, 0, False), ("p300", 4, 0, False), ("p300", 2, 3, False), ("split_wide", 0, 0, False),
+    ("geometric", 3, 0, False), ("p0", 2, 0, False),
+    ("tiny12", 1, 0, True), ("p300", 2, 0, True), ("split_wide", 2, 0, True), ("geometric", 3, 0, True)])
+def test_warp_split_kernels_compile(tmp_path, which, warps, minctas, selsmem):
+    """The warp-split form's generated source compiles for sm_103a, for small and
+    mid-size plans, split nodes, the geometric sampler and p = 0, with the selection
+    choices in registers or in shared memory; node-wise semantics are refused."""
     import shutil
     import subprocess
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
@@ -412,7 +414,11 @@ def test_warp_split_kernels_compile(tmp_path, which, warps, minctas):
     red, _ = api.Net.load(text).reduce(meta)
     plan = api.Plan(red, **kw)
     flags = _lib.PBN_COMPILE_WARP_SPLIT | _lib.PBN_COMPILE_WARPS(warps) | _lib.PBN_COMPILE_MINCTAS(minctas)
-    (tmp_path / "k.cu").write_text(plan.source(flags))
+    if selsmem:
+        flags |= _lib.PBN_COMPILE_WS_SELSMEM
+    src = plan.source(flags)
+    assert ("__constant__ uint4 SELS" in src) == (selsmem and plan.info.n_sel_blocks > 0)
+    (tmp_path / "k.cu").write_text(src)
     shutil.copy(os.path.join(ROOT, "paper_1605_00854_gb300", "csrc", "pbn_device.cuh"), tmp_path)
     proc = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-Xptxas", "-O1", "-c",
                            str(tmp_path / "k.cu"), "-o", str(tmp_path / "k.o")],
