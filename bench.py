@@ -212,6 +212,8 @@ def workload_network(args):
     return synth.paper100(seed=2), META, WORKLOAD
 
 
+KERNEL_NAMES = {_lib.PBN_KERNEL_COMPILED: "compiled", _lib.PBN_KERNEL_INTERP: "interpreter",
+                _lib.PBN_KERNEL_TEAM: "team"}
 SAMPLERS = {"bitsliced": _lib.PBN_PERT_BITSLICED, "geometric": _lib.PBN_PERT_GEOMETRIC}
 
 
@@ -233,7 +235,7 @@ def run_ours(args):
     T = args.n_traj if args.n_traj else (1 << 16 if args.workload == "paper100" else 1 << 14)
     S = args.n_steps if args.n_steps else (10**6 if args.workload == "paper100" else 10**5)
     args.n_traj, args.n_steps = T, S
-    lanes = 0
+    lanes, team_warps = 0, 0
     tune_s = 0.0
     if args.compile_flags is not None or args.max_inputs:
         args.autotune = False  # a pinned configuration (for profiling runs)
@@ -243,9 +245,9 @@ def run_ours(args):
         choice = autotune.tune_network(text, meta, T, steps=2000 if args.workload == "paper100" else 200,
                                        sampler=SAMPLERS[args.sampler])
         tune_s = time.perf_counter() - t0
-        max_inputs, lanes = choice.max_inputs, choice.lanes_per_traj
+        max_inputs, lanes, team_warps = choice.max_inputs, choice.lanes_per_traj, choice.team_warps
         budget, cflags = choice.smem_budget, choice.compile_flags
-        args.kernel = "compiled" if choice.kernel == _lib.PBN_KERNEL_COMPILED else "interpreter"
+        args.kernel = KERNEL_NAMES[choice.kernel]
     else:
         max_inputs, budget, cflags = args.max_inputs or 8, 0, args.compile_flags or 0
         lanes = args.lanes
@@ -263,7 +265,7 @@ def run_ours(args):
         except _lib.PbnError:
             args.kernel = "interpreter"  # plan too wide to compile: the interpreter runs it
     prep_s = time.perf_counter() - t_prep
-    kern = _lib.PBN_KERNEL_COMPILED if args.kernel == "compiled" else _lib.PBN_KERNEL_INTERP
+    kern = {"compiled": _lib.PBN_KERNEL_COMPILED, "team": _lib.PBN_KERNEL_TEAM}.get(args.kernel, _lib.PBN_KERNEL_INTERP)
     P = api.Net.load(text).info().P
     info = plan.info
     T, S = args.n_traj, args.n_steps
@@ -275,7 +277,7 @@ def run_ours(args):
 
     def one_step():
         api.simulate(plan, bufs, seed=SEED, n_steps=S, meta_ids=meta, traj_begin=traj_begin,
-                     stream=stream, d_image=d_img, kernel=kern, lanes_per_traj=lanes)
+                     stream=stream, d_image=d_img, kernel=kern, lanes_per_traj=lanes, team_warps=team_warps)
 
     for _ in range(args.warmup):
         bufs.counts.zero_(); bufs.pooled.zero_()
@@ -516,18 +518,23 @@ def measure_batch(args):
     # batch (one module: compiled networks' functions and the interpreter) and the
     # split compiled batch (two persistent launches per chunk: the compiled networks,
     # then the rest in 1,024-thread CTAs)
-    for form, flags, threads in (("interpreted", None, 512), ("interpreted_1024", None, 1024),
-                                 ("compiled", _lib.PBN_COMPILE_INTERLEAVED, 512),
-                                 ("compiled_split", _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_BATCH_SPLIT, 512)):
+    # (wide interpreted networks as teams of warps; the split batch also with lane
+    # groups, for comparison)
+    for form, flags, threads, lg in (
+            ("interpreted", None, 512, False), ("interpreted_1024", None, 1024, False),
+            ("compiled", _lib.PBN_COMPILE_INTERLEAVED, 512, False),
+            ("compiled_split", _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_BATCH_SPLIT, 512, False),
+            ("compiled_split_lane_groups", _lib.PBN_COMPILE_INTERLEAVED | _lib.PBN_BATCH_SPLIT, 512, True)):
         t0 = time.perf_counter()
-        B = api.Batch(entries, device=dev, compile_flags=flags, threads=threads)
+        B = api.Batch(entries, device=dev, compile_flags=flags, threads=threads, lane_groups=lg)
         build_s = time.perf_counter() - t0
         B.run(20, step_offset=0)
         torch.cuda.synchronize()
         trial = min(S, args.batch_trial_steps)
         dt = _timed(stream, lambda: B.run(trial, step_offset=0))
         forms[form] = dict(batch=B, trial_rate=nu_step * trial / dt, build_s=build_s,
-                           n_compiled=int(B.info.n_compiled), work_items=int(B.info.n_items))
+                           n_compiled=int(B.info.n_compiled), n_team=int(B.info.n_team),
+                           work_items=int(B.info.n_items))
         _progress(f"batch: {form} form built in {build_s:.1f} s, trial {nu_step * trial / dt:.3e}")
     best = max(forms, key=lambda f: forms[f]["trial_rate"])
     B = forms[best]["batch"]
@@ -570,36 +577,56 @@ def measure_batch(args):
     plain_bufs = [api.alloc_buffers(pp, T, dev) if pp is not None else None for pp, (n, T, p) in zip(plain, shapes)]
 
     def each(plans, bufs, kernels):
+        """One launch per network with its kernel; a team launch that does not fit
+        the network (its records and one team beyond shared memory) falls back to the
+        lane-group interpreter during the warm-up."""
         nu = 0
         launches = []
         for i, (pl, bf, kk) in enumerate(zip(plans, bufs, kernels)):
             if pl is None:
                 continue
             nu += shapes[i][0] * shapes[i][1] * S_each
-            launches.append((pl, bf, kk, entries[i]["seed"]))
+            launches.append([pl, bf, kk, entries[i]["seed"]])
+        for ln in launches:  # warm (first launches, shape queries)
+            try:
+                api.simulate(ln[0], ln[1], seed=ln[3], n_steps=8, meta_ids=META, stream=stream, kernel=ln[2])
+            except _lib.PbnError:
+                if ln[2] != _lib.PBN_KERNEL_TEAM:
+                    raise
+                ln[2] = _lib.PBN_KERNEL_INTERP
+                api.simulate(ln[0], ln[1], seed=ln[3], n_steps=8, meta_ids=META, stream=stream, kernel=ln[2])
 
         def go(steps):
             for pl, bf, kk, sd in launches:
                 api.simulate(pl, bf, seed=sd, n_steps=steps, meta_ids=META, stream=stream, kernel=kk)
-        go(8)  # warm (first launches, shape queries)
         torch.cuda.synchronize()
         dt = _timed(stream, lambda: go(S_each))
         _progress(f"batch: per-network leg {dt:.1f} s")
         return {"value": nu / dt, "unit": "node-updates/s", "seconds": dt, "networks": len(launches),
-                "n_steps": S_each}
-    C, I = _lib.PBN_KERNEL_COMPILED, _lib.PBN_KERNEL_INTERP
+                "n_steps": S_each, "team_networks": sum(1 for ln in launches if ln[2] == _lib.PBN_KERNEL_TEAM)}
+    C, I, TM = _lib.PBN_KERNEL_COMPILED, _lib.PBN_KERNEL_INTERP, _lib.PBN_KERNEL_TEAM
+
+    def interp(pl):
+        """The interpreter a network runs best: teams for states of 8 rows or more
+        (Eq. 1 semantics), lane groups otherwise."""
+        if pl is None:
+            return I
+        wide = 2 * pl.info.state_words >= 8 and pl.info.semantics == _lib.PBN_SEM_EQ1
+        return TM if wide else I
     grouped = [e["plan"] for e in entries]
     gbufs = [e["bufs"] for e in entries]
     legs = {
-        "compiled_grouped": each(grouped, gbufs, [C if ok else I for ok in k2_ok]),
-        "interpreted_grouped": each(grouped, gbufs, [I] * len(grouped)),
-        "compiled_plain": each(plain, plain_bufs, [C if ok else I for ok in k0_ok]),
-        "interpreted_plain": each(plain, plain_bufs, [I] * len(plain)),
+        "compiled_grouped": each(grouped, gbufs, [C if ok else interp(pl) for ok, pl in zip(k2_ok, grouped)]),
+        "interpreted_grouped": each(grouped, gbufs, [interp(pl) for pl in grouped]),
+        "interpreted_grouped_lane_groups": each(grouped, gbufs, [I] * len(grouped)),
+        "compiled_plain": each(plain, plain_bufs, [C if ok else interp(pl) for ok, pl in zip(k0_ok, plain)]),
+        "interpreted_plain": each(plain, plain_bufs, [interp(pl) for pl in plain]),
     }
     legs["compiled_grouped"]["compiled_networks"] = int(sum(k2_ok))
     legs["compiled_plain"]["compiled_networks"] = int(sum(k0_ok))
     best_plain = max(legs["compiled_plain"]["value"], legs["interpreted_plain"]["value"])
-    best_grouped = max(legs["compiled_grouped"]["value"], legs["interpreted_grouped"]["value"])
+    best_grouped = max(legs[k]["value"] for k in ("compiled_grouped", "interpreted_grouped",
+                                                  "interpreted_grouped_lane_groups"))
     pk, _ = peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * 128 * float(pk.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
@@ -723,7 +750,8 @@ def measure_scalefree(args):
     bufs = api.alloc_buffers(plan, T, dev)
     img = plan.device_image(dev)
     run = lambda steps: api.simulate(plan, bufs, seed=SEED, n_steps=steps, meta_ids=meta, stream=stream,
-                                     d_image=img, kernel=ch.kernel, lanes_per_traj=ch.lanes_per_traj)
+                                     d_image=img, kernel=ch.kernel, lanes_per_traj=ch.lanes_per_traj,
+                                     team_warps=ch.team_warps)
     run(200)
     torch.cuda.synchronize()
     bufs.counts.zero_(); bufs.pooled.zero_()
@@ -738,7 +766,7 @@ def measure_scalefree(args):
     return {"workload": "scale-free PBN n=2000 (power-law out-degree 2.5; in-degree 1-6; 1-3 functions; "
                         "p=1e-5), reduced+grouped", "n_traj": T, "n_steps": S,
             "value": n * T * S / dt, "unit": "node-updates/s", "seconds": dt,
-            "kernel": "compiled" if ch.kernel == _lib.PBN_KERNEL_COMPILED else "interpreter",
+            "kernel": KERNEL_NAMES[ch.kernel], "team_warps": ch.team_warps,
             "lanes_per_traj": ch.lanes_per_traj, "max_inputs_per_group": ch.max_inputs,
             "compile_flags": ch.compile_flags, "groups": int(plan.info.n_groups),
             "n_retained": int(plan.info.n_retained), "autotune_s": round(tune_s, 1),
@@ -807,7 +835,7 @@ def main():
     ap.add_argument("--n-steps", type=int, default=0, help="steps per pass (default per workload)")
     ap.add_argument("--oracle-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter"])
+    ap.add_argument("--kernel", default="compiled", choices=["compiled", "interpreter", "team"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="use group size 8 and the default launch shape instead of the autotuner")
     ap.add_argument("--max-inputs", type=int, default=0, help="pin the group input cap (skips the autotuner)")

@@ -287,13 +287,21 @@ typedef struct {
     uint32_t lanes_per_traj;   /* lanes cooperating on one trajectory: 0 = auto, 1, 2, 4, 8, 16, 32 */
     uint32_t trajs_per_block;  /* 0 = auto; else a multiple of 32 / lanes_per_traj with
                                   trajs_per_block * lanes_per_traj <= 1024 */
-    uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP or PBN_KERNEL_COMPILED */
+    uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP, PBN_KERNEL_COMPILED or PBN_KERNEL_TEAM */
     uint32_t trace_stride;     /* steps between snapshots (0 or 1: every step) */
+    uint32_t team_warps;       /* PBN_KERNEL_TEAM: warps per team of 32 trajectories (0 = auto);
+                                  trajs_per_block is then 32 x the teams per CTA (0 = auto) */
+    uint32_t reserved;         /* 0 */
 } pbn_sim_args;
 
 #define PBN_KERNEL_AUTO 0u     /* the compiled plan kernel if pbn_plan_compile succeeded, else the interpreter */
 #define PBN_KERNEL_INTERP 1u   /* the generic kernel that reads the plan image */
 #define PBN_KERNEL_COMPILED 2u /* the plan's own kernel (compiled on first use) */
+/* the team interpreter for wide states: K warps share 32 trajectories (one per lane),
+ * splitting each step's perturbation words, SEL blocks and groups, the states in
+ * shared memory as [row][lane]; Eq. 1 semantics only (node-wise plans: PBN_EINVAL);
+ * K x teams per CTA <= 32 */
+#define PBN_KERNEL_TEAM 3u
 
 /* Simulate trajectories traj_begin .. traj_begin + n_traj - 1 for steps
  * step_begin .. step_begin + n_steps - 1 (Algorithm 5, ParallelSimulation, with
@@ -410,6 +418,8 @@ typedef struct {
     double est_ops_per_step;   /* sum over networks of n_traj x ops_per_step */
     uint32_t n_compiled;       /* networks run by compiled code (pbn_batch_compile) */
     uint32_t n_items_compiled; /* split batches: the compiled networks' work items */
+    uint32_t n_team;           /* interpreted networks run by the team interpreter */
+    uint32_t reserved;         /* 0 */
 } pbn_batch_info;
 
 /* Describe a batch of networks for the persistent work-queue kernel: each network
@@ -427,6 +437,16 @@ int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_batch** out
  * SM, for wide networks' lane groups; such a batch cannot be compiled).
  * Errors: as pbn_batch_create, PBN_EINVAL for another CTA size. */
 int pbn_batch_create_cta(const pbn_batch_net* nets, uint32_t n_nets, uint32_t threads, pbn_batch** out);
+/* pbn_batch_create_cta with flags.  By default an interpreted network whose state
+ * has 8 rows or more (Eq. 1 semantics) runs the team interpreter (PBN_KERNEL_TEAM's
+ * loop: teams of warps on 32 trajectories, as many teams per work item as shared
+ * memory holds, the CTA's warps split evenly over them); PBN_BATCH_LANE_GROUPS keeps
+ * every interpreted network on lane groups.  The choice holds for the split batches
+ * pbn_batch_compile makes.  Errors: as pbn_batch_create_cta, PBN_EINVAL for unknown
+ * flags. */
+#define PBN_BATCH_LANE_GROUPS 0x1u
+int pbn_batch_create_ex(const pbn_batch_net* nets, uint32_t n_nets, uint32_t threads, uint32_t flags,
+                        pbn_batch** out);
 int pbn_batch_info_get(const pbn_batch* batch, pbn_batch_info* out);
 
 /* Give the batch compiled code (the batched form of Algorithm 5 with each network's

@@ -54,11 +54,13 @@ def PBN_COMPILE_WS_BATCH(b: int) -> int:
 
 PBN_COMPILE_WS_O1 = 0x40000
 PBN_COMPILE_WS_SELSMEM = 0x80000
+PBN_BATCH_LANE_GROUPS = 0x1
 PBN_BATCH_SPLIT = 0x80000000
 PBN_STATIC_QUEUE_SLOTS = 16
 PBN_KERNEL_AUTO = 0
 PBN_KERNEL_INTERP = 1
 PBN_KERNEL_COMPILED = 2
+PBN_KERNEL_TEAM = 3
 PBN_DEV_STAGE_TIMEOUT = 0x1
 PBN_DEV_BAD_PLAN = 0x2
 PBN_DEV_BAD_MODULE = 0x4
@@ -101,7 +103,7 @@ class BatchNet(ctypes.Structure):
 class BatchInfo(ctypes.Structure):
     _fields_ = [("n_nets", u32), ("n_items", u32), ("threads", u32), ("max_lanes", u32),
                 ("desc_bytes", u64), ("smem_bytes", u64), ("est_ops_per_step", f64),
-                ("n_compiled", u32), ("n_items_compiled", u32)]
+                ("n_compiled", u32), ("n_items_compiled", u32), ("n_team", u32), ("reserved", u32)]
 
 
 class SimArgs(ctypes.Structure):
@@ -109,7 +111,8 @@ class SimArgs(ctypes.Structure):
                 ("n_steps", u64), ("count_from", u64), ("init", u32), ("n_meta", u32),
                 ("meta_ids", vp), ("meta_vals", vp), ("d_state", vp), ("d_counts", vp),
                 ("d_pooled", vp), ("d_status", vp), ("d_trace", vp),
-                ("lanes_per_traj", u32), ("trajs_per_block", u32), ("kernel", u32), ("trace_stride", u32)]
+                ("lanes_per_traj", u32), ("trajs_per_block", u32), ("kernel", u32), ("trace_stride", u32),
+                ("team_warps", u32), ("reserved", u32)]
 
 
 class EstimateOut(ctypes.Structure):
@@ -139,6 +142,7 @@ SIGNATURES = {
     "pbn_batch_image": (i32, [vp, vp, ctypes.c_size_t]),
     "pbn_batch_compile": (i32, [vp, u32, ctypes.POINTER(f64)]),
     "pbn_batch_create_cta": (i32, [ctypes.POINTER(BatchNet), u32, u32, ctypes.POINTER(vp)]),
+    "pbn_batch_create_ex": (i32, [ctypes.POINTER(BatchNet), u32, u32, u32, ctypes.POINTER(vp)]),
     "pbn_batch_run": (i32, [vp, vp, vp, u64, u64, u32, vp, vp]),
     "pbn_batch_free": (None, [vp]),
     "pbn_batch_run_static": (i32, [vp, vp, u32, u64, u64, u32, vp, vp]),

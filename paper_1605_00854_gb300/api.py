@@ -226,7 +226,7 @@ def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids,
              traj_begin: int = 0, step_begin: int = 0, count_from: int = 0, init: int | None = None,
              trace=None, lanes_per_traj: int = 0, trajs_per_block: int = 0, stream=None,
              d_image=None, n_traj: int | None = None, kernel: int = _lib.PBN_KERNEL_AUTO,
-             trace_stride: int = 1):
+             trace_stride: int = 1, team_warps: int = 0):
     """Enqueue pbn_simulate on `stream` (default: torch's current stream)."""
     import torch
     L = _lib.load()
@@ -250,6 +250,7 @@ def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids,
     a.lanes_per_traj, a.trajs_per_block = lanes_per_traj, trajs_per_block
     a.kernel = kernel
     a.trace_stride = trace_stride
+    a.team_warps = team_warps
     img = plan.device_image(bufs.state.device) if d_image is None else d_image
     st = torch.cuda.current_stream(bufs.state.device) if stream is None else stream
     check(L.pbn_simulate(plan._h, ctypes.c_void_p(img.data_ptr()), ctypes.byref(a),
@@ -273,9 +274,11 @@ class Batch:
     `entries` is a list of dicts with keys plan, bufs (SimBuffers), seed, meta_ids and
     optionally meta_vals, traj_begin, step_begin, count_from, init.  With
     compile_flags (pbn_batch_compile) the networks whose plans compile run their own
-    generated code in the same persistent launch, the others the interpreter."""
+    generated code in the same persistent launch, the others the interpreter (wide
+    states as teams of warps on 32 trajectories, unless lane_groups)."""
 
-    def __init__(self, entries, device="cuda", compile_flags: int | None = None, threads: int = 512):
+    def __init__(self, entries, device="cuda", compile_flags: int | None = None, threads: int = 512,
+                 lane_groups: bool = False):
         import torch
         L = _lib.load()
         self.entries = entries
@@ -302,7 +305,8 @@ class Batch:
             b.d_counts = None if bufs.counts is None else bufs.counts.data_ptr()
             b.d_pooled = None if bufs.pooled is None else bufs.pooled.data_ptr()
         h = ctypes.c_void_p()
-        check(L.pbn_batch_create_cta(arr, len(entries), threads, ctypes.byref(h)), "pbn_batch_create_cta")
+        flags = _lib.PBN_BATCH_LANE_GROUPS if lane_groups else 0
+        check(L.pbn_batch_create_ex(arr, len(entries), threads, flags, ctypes.byref(h)), "pbn_batch_create_ex")
         self._h = h
         self.compile_ms = 0.0
         if compile_flags is not None:

@@ -4,7 +4,8 @@ For one network it builds plans with several caps on the inputs of a merged grou
 (the group size of Sec. 3.3; larger groups mean fewer table lookups but bigger
 tables), and for each plan times short launches of the candidate kernels on the
 caller's trajectory count: the compiled plan (when the plan can be compiled, with
-each code-shape flag) and the interpreter with 1 to 32 lanes per trajectory,
+each code-shape flag), the interpreter with 1 to 32 lanes per trajectory and the
+team interpreter (warps sharing 32 trajectories, for states of 8 rows or more),
 with the tables in shared or in global memory.  The fastest configuration is returned and cached by the shape of
 the problem.  For batches it times CUDA-graph replays of the persistent launch with
 several steps per launch.
@@ -34,6 +35,7 @@ class Choice:
     smem_budget: int       # 0 = default (tables staged when they fit)
     node_updates_per_s: float
     compile_flags: int = 0  # pbn_plan_compile flags of the compiled kernel
+    team_warps: int = 0     # _lib.PBN_KERNEL_TEAM: warps per team (0 = the library's choice)
 
 
 def _shape_key(net: api.Net, meta, n_traj: int) -> str:
@@ -44,13 +46,14 @@ def _shape_key(net: api.Net, meta, n_traj: int) -> str:
     return f"{gpu}-n{info.n}-f{info.n_functions}-m{len(meta)}-p{info.P}-t{tb}"
 
 
-def _time(plan, bufs, seed, steps, meta, kernel, lanes) -> float:
+def _time(plan, bufs, seed, steps, meta, kernel, lanes, team_warps=0) -> float:
     import torch
-    api.simulate(plan, bufs, seed=seed, n_steps=8, meta_ids=meta, kernel=kernel, lanes_per_traj=lanes)
+    kw = dict(kernel=kernel, lanes_per_traj=lanes, team_warps=team_warps)
+    api.simulate(plan, bufs, seed=seed, n_steps=8, meta_ids=meta, **kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    api.simulate(plan, bufs, seed=seed, n_steps=steps, meta_ids=meta, kernel=kernel, lanes_per_traj=lanes)
+    api.simulate(plan, bufs, seed=seed, n_steps=steps, meta_ids=meta, **kw)
     e1.record()
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / 1e3
@@ -66,7 +69,7 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                  warp_split_options=(_lib.PBN_COMPILE_WARPS(2) | _lib.PBN_COMPILE_WS_BATCH(1),
                                      _lib.PBN_COMPILE_WARPS(2),
                                      _lib.PBN_COMPILE_WARPS(4)),
-                 warp_split_max_inputs: int = 8) -> Choice:
+                 warp_split_max_inputs: int = 8, team_warps_options=(0, 8)) -> Choice:
     """Pick the fastest (group size, kernel and its compile flags, lanes, table
     placement) for simulating n_traj trajectories of this network."""
     net = api.Net.load(text)
@@ -107,11 +110,11 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
             bufs = api.alloc_buffers(plan, n_traj)
             cands = []
             if try_compiled and budget == 0:
-                cands += [(_lib.PBN_KERNEL_COMPILED, 1, f, plan) for f in compile_flags_options]
+                cands += [(_lib.PBN_KERNEL_COMPILED, 1, f, plan, 0) for f in compile_flags_options]
                 # plans too wide for the default forms: the wide register form, while its
                 # code stays small (it compiles for minutes at thousands of nodes)
                 if plan.info.n_sel_blocks > 24 and plan.info.n_groups <= 512 and plan.info.n <= 1024:
-                    cands.append((_lib.PBN_KERNEL_COMPILED, 1, _lib.PBN_COMPILE_WIDE, plan))
+                    cands.append((_lib.PBN_KERNEL_COMPILED, 1, _lib.PBN_COMPILE_WIDE, plan, 0))
                 # wide states: the warp-split form in a few warp counts and occupancies,
                 # each on its own plan object (a plan holds one compiled kernel), compiled
                 # in parallel
@@ -135,24 +138,27 @@ def tune_network(text: str, meta, n_traj: int, *, steps: int = 256, seed: int = 
                             return False
                     with ThreadPoolExecutor(max_workers=len(ws)) as ex:
                         ok = list(ex.map(_compile, ws))
-                    cands += [(_lib.PBN_KERNEL_COMPILED, 1, f, pw) for (f, pw), good in zip(ws, ok) if good]
+                    cands += [(_lib.PBN_KERNEL_COMPILED, 1, f, pw, 0) for (f, pw), good in zip(ws, ok) if good]
             # at most about one lane per state word
-            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0, plan) for lg in lanes_options
+            cands += [(_lib.PBN_KERNEL_INTERP, lg, 0, plan, 0) for lg in lanes_options
                       if lg == 1 or lg <= 2 * plan.info.state_words]
-            for kern, lg, cf, pl in cands:
+            if 2 * plan.info.state_words >= 8 and plan.info.semantics == _lib.PBN_SEM_EQ1:
+                cands += [(_lib.PBN_KERNEL_TEAM, 0, 0, plan, k) for k in team_warps_options]
+            for kern, lg, cf, pl, tw in cands:
                 try:
                     if kern == _lib.PBN_KERNEL_COMPILED and not (cf & _lib.PBN_COMPILE_WARP_SPLIT):
                         pl.compile(cf)
-                    dt = _time(pl, bufs, seed, steps, list(meta), kern, lg)
+                    dt = _time(pl, bufs, seed, steps, list(meta), kern, lg, tw)
                 except _lib.PbnError:
                     continue
                 rate = n * n_traj * steps / dt
                 if log is not None:
-                    log.append(dict(max_inputs=mi, smem_budget=budget, kernel=kern, lanes=lg, flags=cf, rate=rate,
+                    log.append(dict(max_inputs=mi, smem_budget=budget, kernel=kern, lanes=lg, flags=cf, team_warps=tw,
+                                    rate=rate,
                                     groups=int(plan.info.n_groups), tables_in_smem=int(plan.info.tables_in_smem)))
                 if best is None or rate > best.node_updates_per_s:
                     best = Choice(max_inputs=mi, kernel=kern, lanes_per_traj=lg, smem_budget=budget,
-                                  node_updates_per_s=rate, compile_flags=cf)
+                                  node_updates_per_s=rate, compile_flags=cf, team_warps=tw)
             del bufs
     if best is None:
         raise RuntimeError("no configuration could run this network")

@@ -22,7 +22,7 @@ GENCODE = "arch=compute_103a,code=sm_103a"
 
 CU_SOURCES = ["pbn_sim.cu", "pbn_batch.cu", "pbn_batch1024.cu"]
 CPP_SOURCES = ["pbn_host.cpp", "pbn_jit.cpp"]
-HEADERS = ["pbn_internal.h", "pbn_image.h", "pbn_device.cuh", "pbn_interp.cuh", "pbn_batch.cuh",
+HEADERS = ["pbn_internal.h", "pbn_image.h", "pbn_device.cuh", "pbn_interp.cuh", "pbn_team.cuh", "pbn_batch.cuh",
            "pbn_batch_interp.cuh"]
 # the interpreter's batch work-item function as relocatable device code, linked at run
 # time into the batch modules of pbn_batch_compile

@@ -63,6 +63,7 @@ struct pbn_batch {
     std::vector<uint8_t> image; /* nets then items */
     std::vector<const pbn_plan*> plans;
     uint32_t threads = 512;
+    bool lane_groups = false; /* PBN_BATCH_LANE_GROUPS: no team interpreter */
     /* batch module (pbn_batch_compile): compiled networks' functions and the
      * dispatching persistent kernel, or null (the library's interpreter kernel) */
     void* module = nullptr;
@@ -84,7 +85,7 @@ struct pbn_batch {
 
 namespace {
 
-int interp_shape(const pbn_plan* plan, uint32_t T, NetDesc* D);
+int interp_shape(const pbn_plan* plan, uint32_t T, bool teams_ok, NetDesc* D);
 
 /* Meta-state rows of network i: per 32-bit state row holding a meta node, the mask
  * of those nodes and the values they must take. */
@@ -109,7 +110,7 @@ int describe_meta(const pbn_batch_net& a, uint32_t i, NetDesc* D) {
 /* Descriptor of network i for a CTA of T threads: buffers, counting window, meta
  * rows, image section offsets, and the staging mode with its trajectory slots per
  * work item and lanes per trajectory. */
-int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D) {
+int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, bool teams_ok, NetDesc* D) {
     using pbn::fail;
     const pbn_plan* plan = a.plan;
     if (!plan || !a.d_image || ((uintptr_t)a.d_image & 15u) || !a.d_state)
@@ -164,7 +165,7 @@ int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D)
     D->off_ret = H.off_ret;
     D->off_pos = H.off_pos;
     D->off_tables = H.off_tables;
-    const int rc2 = interp_shape(plan, T, D);
+    const int rc2 = interp_shape(plan, T, teams_ok, D);
     if (rc2 != PBN_OK)
         return fail(PBN_ETOOBIG, "pbn_batch_create: network %u needs %llu bytes of shared memory per trajectory", i,
                     (unsigned long long)plan->per_traj_smem);
@@ -176,7 +177,7 @@ int describe_network(const pbn_batch_net& a, uint32_t i, uint32_t T, NetDesc* D)
  * tables staged, specs only, or nothing: read through L1), the offset of the
  * trajectory rows, and the lanes per trajectory.  PBN_ETOOBIG if not even 32
  * trajectory rows fit. */
-int interp_shape(const pbn_plan* plan, uint32_t T, NetDesc* D) {
+int interp_shape(const pbn_plan* plan, uint32_t T, bool teams_ok, NetDesc* D) {
     const pbn_img_header& H = plan->hdr;
     const uint64_t per = plan->per_traj_smem;
     auto fit = [&](uint64_t staged) -> uint32_t {
@@ -200,7 +201,37 @@ int interp_shape(const pbn_plan* plan, uint32_t T, NetDesc* D) {
     }
     D->stage_off = 0;
     D->compiled = 0;
+    D->team = 0;
     D->smem_state_off = D->stage_bytes ? ((D->stage_bytes + 127u) & ~127u) : 0u;
+    /* states of 8 rows or more (Eq. 1 semantics): the team interpreter, its records
+     * staged (tables too when at least as many teams fit), as many teams as the
+     * shared memory holds up to a power of two dividing the CTA's warps, and the
+     * warps split evenly over them (on paper-scale networks of 300 to 3,000 nodes
+     * and the 2,000-node scale-free one it ran 1.2-1.33x the lane groups) */
+    if (teams_ok && H.W32 >= 8 && H.semantics != PBN_SEM_NODEWISE) {
+        const uint64_t tb = pbn_team_smem_bytes(H.W32, H.n_sel);
+        const uint32_t warps = T / 32u;
+        auto teams = [&](uint64_t staged) -> uint32_t {
+            const uint64_t off = (staged + 127u) & ~(uint64_t)127u;
+            if (off + tb > kSmemCap) return 0u;
+            uint32_t t = 1;
+            while (2 * t <= warps && off + 2 * t * tb <= kSmemCap) t *= 2;
+            return t;
+        };
+        const uint32_t t_all = H.tables_in_smem ? teams(H.off_ret) : 0u;
+        const uint32_t t_specs = teams(H.off_tables);
+        if (t_all && t_all >= t_specs) {
+            D->specs_in_smem = 1; D->tables_in_smem = 1; D->stage_bytes = H.off_ret; D->nt = 32u * t_all;
+        } else if (t_specs) {
+            D->specs_in_smem = 1; D->tables_in_smem = 0; D->stage_bytes = H.off_tables; D->nt = 32u * t_specs;
+        }
+        if (t_all || t_specs) {
+            D->team = warps / (D->nt / 32u);
+            D->lg = 1;
+            D->smem_state_off = (D->stage_bytes + 127u) & ~127u;
+            return PBN_OK;
+        }
+    }
     /* lanes per trajectory: fill the CTA's threads when few trajectories fit (wide
      * states); lane groups evaluate groups in shape order.  States of 32 words or more
      * take up to a warp per trajectory (two words per lane: 32 lanes ran a 62-word
@@ -227,6 +258,13 @@ constexpr double kInterpCost = 3.0;
  * interpreter in the same launch. */
 constexpr size_t kMaxCompiledNets = 96;
 
+/* Shared memory of an interpreted network's work item: its staged bytes and the
+ * trajectories' rows (lane groups) or the teams' states (team interpreter). */
+uint64_t interp_smem(const NetDesc& D, const pbn_plan* plan) {
+    if (D.team) return D.smem_state_off + (uint64_t)(D.nt / 32u) * pbn_team_smem_bytes(D.W32, D.n_sel);
+    return D.smem_state_off + (uint64_t)plan->per_traj_smem * D.nt;
+}
+
 /* Cut every network into work items of its descriptor's trajectory slots, order them
  * by descending estimated work (largest processing time first, so that the
  * persistent CTAs finish together) and lay out the device table. */
@@ -234,7 +272,7 @@ void cut_items(pbn_batch* B) {
     const uint32_t n_nets = (uint32_t)B->nets.size();
     std::vector<double> cost(n_nets);
     uint64_t smem_max = 0;
-    uint32_t max_lanes = 1, n_compiled = 0;
+    uint32_t max_lanes = 1, n_compiled = 0, n_team = 0;
     double ops = 0;
     B->items.clear();
     for (uint32_t i = 0; i < n_nets; ++i) {
@@ -246,8 +284,9 @@ void cut_items(pbn_batch* B) {
             ++n_compiled;
             smem_max = std::max<uint64_t>(smem_max, D.stage_bytes);
         } else {
-            max_lanes = std::max(max_lanes, D.lg);
-            smem_max = std::max<uint64_t>(smem_max, D.smem_state_off + (uint64_t)plan->per_traj_smem * D.nt);
+            max_lanes = std::max(max_lanes, D.team ? 32u : D.lg);
+            if (D.team) ++n_team;
+            smem_max = std::max<uint64_t>(smem_max, interp_smem(D, plan));
         }
         for (uint64_t t0 = 0; t0 < D.n_traj; t0 += D.nt) {
             WorkItem w{i, (uint32_t)t0, (uint32_t)std::min<uint64_t>(D.nt, D.n_traj - t0), 0u};
@@ -265,7 +304,7 @@ void cut_items(pbn_batch* B) {
     for (uint32_t i = 0; i < n_nets; ++i) {
         const NetDesc& D = B->nets[i];
         if (D.compiled) B->smem_c = std::max<size_t>(B->smem_c, D.stage_bytes);
-        else B->smem_i = std::max<size_t>(B->smem_i, D.smem_state_off + (uint64_t)B->plans[i]->per_traj_smem * D.nt);
+        else B->smem_i = std::max<size_t>(B->smem_i, interp_smem(D, B->plans[i]));
     }
     B->info.n_nets = n_nets;
     B->info.n_items = (uint32_t)B->items.size();
@@ -274,6 +313,7 @@ void cut_items(pbn_batch* B) {
     B->info.max_lanes = max_lanes;
     B->info.est_ops_per_step = ops;
     B->info.n_compiled = n_compiled;
+    B->info.n_team = n_team;
     B->info.n_items_compiled = B->split ? B->n_items_c : 0u;
     const size_t nb = B->nets.size() * sizeof(NetDesc), ib = B->items.size() * sizeof(WorkItem);
     B->image.resize(nb + ib);
@@ -288,18 +328,25 @@ extern "C" int pbn_batch_create(const pbn_batch_net* nets, uint32_t n_nets, pbn_
 }
 
 extern "C" int pbn_batch_create_cta(const pbn_batch_net* nets, uint32_t n_nets, uint32_t threads, pbn_batch** out) {
+    return pbn_batch_create_ex(nets, n_nets, threads, 0u, out);
+}
+
+extern "C" int pbn_batch_create_ex(const pbn_batch_net* nets, uint32_t n_nets, uint32_t threads, uint32_t flags,
+                                   pbn_batch** out) {
     using pbn::fail;
     if (!nets || !out || n_nets == 0) return fail(PBN_EINVAL, "pbn_batch_create: need networks");
     if (threads != 512 && threads != 1024) return fail(PBN_EINVAL, "pbn_batch_create: CTAs of 512 or 1024 threads");
+    if (flags & ~PBN_BATCH_LANE_GROUPS) return fail(PBN_EINVAL, "pbn_batch_create: unknown flags 0x%x", flags);
     *out = nullptr;
     try {
         std::unique_ptr<pbn_batch> B(new pbn_batch());
         B->threads = threads;
+        B->lane_groups = (flags & PBN_BATCH_LANE_GROUPS) != 0;
         const uint32_t T = B->threads;
         for (uint32_t i = 0; i < n_nets; ++i) {
             const pbn_batch_net& a = nets[i];
             NetDesc D;
-            const int rc = describe_network(a, i, T, &D);
+            const int rc = describe_network(a, i, T, !B->lane_groups, &D);
             if (rc != PBN_OK) return rc;
             B->nets.push_back(D);
             B->plans.push_back(a.plan);
@@ -365,7 +412,7 @@ extern "C" int pbn_batch_compile(pbn_batch* b, uint32_t flags, double* compile_m
             for (uint32_t i : compiled) is_c[i] = 1;
             wide_desc = b->nets;
             for (uint32_t i = 0; i < (uint32_t)b->nets.size(); ++i)
-                if (!is_c[i] && interp_shape(b->plans[i], 1024, &wide_desc[i]) != PBN_OK)
+                if (!is_c[i] && interp_shape(b->plans[i], 1024, !b->lane_groups, &wide_desc[i]) != PBN_OK)
                     return fail(PBN_ETOOBIG, "pbn_batch_compile: network %u does not fit a 1,024-thread CTA", i);
         }
         void *lib = nullptr, *kern = nullptr;

@@ -10,6 +10,7 @@
 
 #include "pbn_batch.cuh"
 #include "pbn_interp.cuh"
+#include "pbn_team.cuh"
 
 /* The per-item view pbn_interp_run reads (the field names of the single-network
  * kernel's launch parameters). */
@@ -90,6 +91,19 @@ __device__ __forceinline__ bool pbn_batch_interp_run(uint64_t step_offset, uint3
     V.meta_row = meta_sh;
     V.meta_mask = meta_sh + PBN_BATCH_META_ROWS;
     V.meta_val = meta_sh + 2 * PBN_BATCH_META_ROWS;
+    if (D.team) {
+        /* teams of D.team warps on 32 trajectories each; every warp of the CTA is in
+         * one (the team count divides the CTA's warps) */
+        const uint32_t K = D.team, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+        const uint32_t team = warp / K, wt = warp - team * K;
+        const uint32_t slot = team * 32u + lane;
+        const bool active = slot < W.n;
+        const uint64_t lt = (uint64_t)W.t0 + slot;
+        uint8_t* const tsm = smem + D.smem_state_off + team * pbn_team_smem_bytes(D.W32, D.n_sel);
+        if (D.tables_in_smem) pbn_team_run<false, true>(V, smem, tsm, K, wt, lane, lt, active, c);
+        else pbn_team_run<false, false>(V, smem, tsm, K, wt, lane, lt, active, c);
+        return active && wt == 0;
+    }
     /* D.lg lanes per trajectory, D.nt trajectory slots per item */
     const uint32_t lg = D.lg;
     const uint32_t slot = threadIdx.x / lg;

@@ -89,11 +89,11 @@ int device_sms();         /* SM count */
 int device_smem_optin();  /* opt-in dynamic shared memory per block, bytes */
 /* Raise `func`'s dynamic shared-memory limit on the current device to at least
  * `bytes` when `bytes` plus the kernel's static shared memory (`static_bytes`, an
- * upper bound is enough) exceeds the 48 KB a launch gets without opting in; the
- * limit is per device and per kernel and is only ever raised, so that callers
- * sharing a kernel never lower each other's setting.  Returns a cudaError_t value
- * (0 = success). */
-int ensure_dyn_smem(const void* func, size_t bytes, size_t static_bytes = 0);
+ * upper bound is enough; the library's kernels hold less than the default) exceeds
+ * the 48 KB a launch gets without opting in; the limit is per device and per kernel
+ * and is only ever raised, so that callers sharing a kernel never lower each other's
+ * setting.  Returns a cudaError_t value (0 = success). */
+int ensure_dyn_smem(const void* func, size_t bytes, size_t static_bytes = 1024);
 }  // namespace pbn
 
 #endif

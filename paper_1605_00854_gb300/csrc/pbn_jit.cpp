@@ -194,7 +194,7 @@ struct Generated {
     uint32_t tab_bytes = 0;  /* bytes of tables staged into shared memory */
     uint32_t warps = 0;      /* warp-split form: warps per CTA (32 trajectories); 0: one trajectory per thread */
     uint32_t dyn_smem = 0;   /* dynamic shared memory to launch with (0: tab_bytes) */
-    uint32_t static_smem = 256; /* upper bound of the kernel's static shared memory */
+    uint32_t static_smem = 1024; /* upper bound of the kernel's static shared memory */
 };
 
 using BatchSpec = pbn::JitBatchNet;
@@ -1628,7 +1628,7 @@ struct pbn_jit_state {
     uint32_t tab_bytes = 0;
     uint32_t warps = 0;  /* warp-split form: warps per CTA of 32 trajectories */
     uint32_t dyn_smem = 0; /* dynamic shared memory of a launch (0: tab_bytes) */
-    uint32_t static_smem = 256; /* upper bound of the kernel's static shared memory */
+    uint32_t static_smem = 1024; /* upper bound of the kernel's static shared memory */
     double compile_ms = 0;
 };
 

@@ -36,6 +36,7 @@
 #include "pbn_device.cuh"
 #include "pbn_interp.cuh"
 #include "pbn_internal.h"
+#include "pbn_team.cuh"
 
 namespace {
 
@@ -43,6 +44,7 @@ constexpr uint32_t kWeyl0 = 0x9E3779B9u;
 constexpr uint32_t kWeyl1 = 0xBB67AE85u;
 constexpr int kMaxMetaRows = 16;
 constexpr uint32_t kMaxCtaThreads = 1024;
+constexpr size_t kStaticSmemReserve = 1024;
 
 struct SimParams {
     const uint8_t* image;      /* device copy of the plan image */
@@ -73,6 +75,7 @@ struct SimParams {
     uint64_t geo_full, geo_last;  /* geometric sampler: thresholds of a full and the last word */
     uint32_t n_meta_rows;
     uint32_t trace_stride;     /* steps between trace snapshots (>= 1) */
+    uint32_t team_warps;       /* team kernel: warps per team of 32 trajectories */
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
     uint32_t meta_val[kMaxMetaRows];
@@ -131,6 +134,65 @@ cudaError_t launch_t(const SimParams& P, uint32_t grid, uint32_t tpb, size_t sme
     return cudaGetLastError();
 }
 
+/* The team interpreter (pbn_team.cuh): a CTA of P.nt / 32 teams of P.team_warps
+ * warps, 32 trajectories a team, the staged records at the start of shared memory
+ * and the teams' states after them. */
+template <bool TRACE, bool TAB_SMEM>
+__global__ void __launch_bounds__(kMaxCtaThreads) pbn_team_kernel(const SimParams P) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t stage_bar;
+    if (!pbn_stage(smem, P.image, P.stage_bytes, &stage_bar)) {
+        if (threadIdx.x == 0 && P.status) atomicOr(P.status, PBN_DEV_STAGE_TIMEOUT);
+        return;
+    }
+    const pbn_img_header* hdr = reinterpret_cast<const pbn_img_header*>(smem);
+    if (hdr->magic != PBN_IMG_MAGIC || hdr->image_bytes != P.image_bytes || hdr->n != P.n ||
+        hdr->W32 != P.W32 || hdr->n_sel != P.n_sel || hdr->off_tables != P.off_tables) {
+        if (threadIdx.x == 0 && P.status) atomicOr(P.status, PBN_DEV_BAD_PLAN);
+        return;
+    }
+    const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t K = P.team_warps;
+    const uint32_t team = warp / K, wt = warp - team * K;
+    const uint64_t lt = (uint64_t)blockIdx.x * P.nt + team * 32u + lane;
+    const bool active = lt < P.n_traj;
+    uint8_t* const tsm = smem + P.smem_state_off + team * pbn_team_smem_bytes(P.W32, P.n_sel);
+    uint32_t c[4];
+    pbn_team_run<TRACE, TAB_SMEM>(P, smem, tsm, K, wt, lane, lt, active, c);
+    if (P.pooled) {
+        const bool lead = active && wt == 0;
+        uint64_t v[5] = {lead ? c[0] : 0u, lead ? (uint64_t)(P.pairs - c[1] - c[2] - c[3]) : 0u,
+                         lead ? c[1] : 0u, lead ? c[2] : 0u, lead ? c[3] : 0u};
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_xor_sync(0xFFFFFFFFu, v[i], o);
+        }
+        if (lane == 0 && wt == 0) {
+#pragma unroll
+            for (int i = 0; i < 5; ++i)
+                if (v[i]) atomicAdd(P.pooled + i, (unsigned long long)v[i]);
+        }
+    }
+}
+
+template <bool TRACE, bool TAB_SMEM>
+cudaError_t launch_team_t(const SimParams& P, uint32_t grid, uint32_t tpb, size_t smem, cudaStream_t st) {
+    auto kern = pbn_team_kernel<TRACE, TAB_SMEM>;
+    const int e = pbn::ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
+    if (e != 0) return static_cast<cudaError_t>(e);
+    kern<<<grid, tpb, smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_team(const SimParams& P, bool trace, bool tab_smem, uint32_t grid, uint32_t tpb, size_t smem,
+                        cudaStream_t st) {
+    if (trace) return tab_smem ? launch_team_t<true, true>(P, grid, tpb, smem, st)
+                               : launch_team_t<true, false>(P, grid, tpb, smem, st);
+    return tab_smem ? launch_team_t<false, true>(P, grid, tpb, smem, st)
+                    : launch_team_t<false, false>(P, grid, tpb, smem, st);
+}
+
 template <int LG>
 cudaError_t launch_lg(const SimParams& P, bool trace, bool tab_smem, uint32_t grid, uint32_t tpb, size_t smem,
                       cudaStream_t st) {
@@ -184,7 +246,10 @@ int ensure_dyn_smem(const void* func, size_t bytes, size_t static_bytes) {
     size_t& set = g_smem_set[std::make_pair(dev, func)];
     if (bytes <= set) return 0;
     const cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return (int)e;
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError(); /* reported here: not left for the next launch's check */
+        return (int)e;
+    }
     set = bytes;
     return 0;
 }
@@ -211,7 +276,7 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
     if (a->step_begin + a->n_steps > (1ull << 48)) return fail(PBN_EINVAL, "pbn_simulate: step indices must be < 2^48");
     if (a->init != PBN_INIT_KEYED && a->init != PBN_INIT_STATE) return fail(PBN_EINVAL, "pbn_simulate: bad init mode");
     if (a->init == PBN_INIT_KEYED && a->step_begin != 0) return fail(PBN_EINVAL, "pbn_simulate: keyed initial state needs step_begin == 0");
-    if (a->kernel > PBN_KERNEL_COMPILED) return fail(PBN_EINVAL, "pbn_simulate: unknown kernel selector %u", a->kernel);
+    if (a->kernel > PBN_KERNEL_TEAM) return fail(PBN_EINVAL, "pbn_simulate: unknown kernel selector %u", a->kernel);
     if (a->n_meta < 1 || a->n_meta > 1024 || !a->meta_ids) return fail(PBN_EINVAL, "pbn_simulate: need 1..1024 meta-state nodes");
     const uint32_t tstride = a->trace_stride ? a->trace_stride : 1u;
     if (a->d_trace && (a->n_steps / tstride) * (uint64_t)plan->info.state_words * a->n_traj >= (1ull << 40))
@@ -336,8 +401,39 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
         return pbn::jit_launch(plan, &J, P.n_traj, sms, st);
     }
 
+    /* dynamic shared memory a CTA may take: the opt-in limit less a reserve for the
+     * kernels' static shared memory (a stage barrier and a few words) */
+    const size_t smem_lim = (size_t)device_smem_limit() - kStaticSmemReserve;
+    if (a->kernel == PBN_KERNEL_TEAM) {
+        /* teams of K warps on 32 trajectories: T teams per CTA (T x K <= 32 warps), by
+         * default as many as the shared memory holds up to one wave of CTAs over the
+         * SMs, and K = 32 / T */
+        if (P.per_node) return fail(PBN_EINVAL, "pbn_simulate: the team kernel runs Eq. 1 semantics only");
+        if (a->trajs_per_block % 32u || a->trajs_per_block > 1024u || a->team_warps > 32u)
+            return fail(PBN_EINVAL, "pbn_simulate: team kernel needs trajs_per_block a multiple of 32 (<= 1024) and <= 32 warps");
+        const size_t tb = pbn_team_smem_bytes(H.W32, H.n_sel);
+        const size_t fixed = P.smem_state_off;
+        if (fixed + tb > smem_lim)
+            return fail(PBN_ETOOBIG, "pbn_simulate: a team needs %zu bytes of shared memory", fixed + tb);
+        const uint32_t tmax = (uint32_t)std::min<size_t>(32, (smem_lim - fixed) / tb);
+        const uint64_t n_teams = (a->n_traj + 31) / 32;
+        uint32_t T = a->trajs_per_block / 32u;
+        if (T == 0)
+            T = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tmax, (n_teams + sms - 1) / (uint64_t)sms));
+        uint32_t K = a->team_warps ? a->team_warps : std::max(1u, 32u / T);
+        if (T > tmax) return fail(PBN_ETOOBIG, "pbn_simulate: %u teams exceed the shared memory of a CTA", T);
+        if (T * K > 32u) return fail(PBN_EINVAL, "pbn_simulate: %u teams of %u warps exceed 1,024 threads", T, K);
+        P.team_warps = K;
+        P.nt = 32u * T;
+        const uint64_t grid = (a->n_traj + P.nt - 1) / P.nt;
+        const size_t smem = fixed + (size_t)T * tb;
+        const cudaError_t e =
+            launch_team(P, a->d_trace != nullptr, H.tables_in_smem != 0, (uint32_t)grid, 32u * K * T, smem, st);
+        if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_simulate: %s", cudaGetErrorString(e));
+        return PBN_OK;
+    }
+
     /* launch shape: lanes per trajectory and trajectory slots per CTA */
-    const size_t smem_lim = (size_t)device_smem_limit();
     uint32_t LG = a->lanes_per_traj;
     const size_t per_traj = plan->per_traj_smem;
     const size_t fixed = P.smem_state_off;

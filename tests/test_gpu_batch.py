@@ -110,9 +110,11 @@ def test_batch_graph_capture_replays_the_chunk_loop():
         assert np.array_equal(ga["final"], gb["final"]) and np.array_equal(ga["counts"], gb["counts"])
 
 
-def test_batch_wide_networks_use_lane_groups():
-    """Wide networks get several lanes per trajectory inside the batch (group-parallel
-    evaluation) and still reproduce their single-network launches exactly."""
+@pytest.mark.parametrize("lane_groups", [True, False])
+def test_batch_wide_networks_use_lane_groups(lane_groups):
+    """Wide networks get several lanes per trajectory (lane groups) or teams of warps
+    on 32 trajectories inside the batch and still reproduce their single-network
+    launches exactly."""
     rng = np.random.default_rng(12)
     entries, plans, refs = [], [], []
     for i, n in enumerate([1500, 2500, 60, 900]):
@@ -123,7 +125,8 @@ def test_batch_wide_networks_use_lane_groups():
         entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=seed, meta_ids=[0, 1, 2]))
         plans.append((plan, ids))
         refs.append(run(plan, seed=seed, n_traj=T, n_steps=240, meta=[0, 1, 2], kernel=_lib.PBN_KERNEL_INTERP, lanes=1))
-    B = api.Batch(entries)
+    B = api.Batch(entries, lane_groups=lane_groups)
+    assert (B.info.n_team == 0) if lane_groups else (B.info.n_team == 3)
     B.run(100)
     B.run(140)
     assert int(B.status.item()) == 0
@@ -146,7 +149,7 @@ def test_batch_warp_per_trajectory_on_a_wide_state(oracle_mod):
         entries.append(dict(plan=plan, bufs=api.alloc_buffers(plan, T), seed=31 + k, meta_ids=meta, count_from=5))
         plans.append((plan, ids))
     assert plans[0][0].info.state_words >= 16
-    B = api.Batch(entries)
+    B = api.Batch(entries, lane_groups=True)
     assert B.info.max_lanes == 16
     B.run(50)
     B.run(30)

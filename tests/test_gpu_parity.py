@@ -310,3 +310,36 @@ def test_chain_cut_at_the_window_start(oracle_mod, kernel, count_from):
     got = run(plan, seed=21, n_traj=T, n_steps=S, meta=meta, count_from=count_from, chunks=[100, 150, 50],
               kernel=kernel)
     _compare(got, orc, ids, trace=False)
+
+
+def test_first_launch_at_exactly_48_kb_of_dynamic_shared_memory():
+    """A kernel's first launch asking for exactly 48 KB of dynamic shared memory
+    (here a 104-node plan in CTAs of 480 trajectory slots) needs its opt-in raised,
+    since the kernel's static shared memory comes on top of the dynamic part.  Run
+    in a fresh process, where no earlier launch raised the limit, and compared with
+    the oracle."""
+    import subprocess
+    import sys
+    from conftest import ROOT
+    code = """
+import sys, numpy as np
+sys.path.insert(0, %r)
+sys.path.insert(0, %r)
+from gpu_helpers import plan_for, run
+from paper_1605_00854_gb300 import synth
+from oracle import oracle
+oracle.build()
+text = synth.paper100(seed=2, n=104, p=1e-3).to_text()
+plan, ids = plan_for(text, [0, 1, 2])
+i = plan.info
+per = 4 * (2 * (2 * i.state_words + 1) + (i.n_sel_blocks | 1))
+assert (i.stage_bytes + 127) // 128 * 128 + per * 480 == 49152
+got = run(plan, seed=6, n_traj=1000, n_steps=50, meta=[0, 1, 2], lanes=1, tpb=480, kernel=1)
+orc = oracle.simulate(text, 6, 0, 1000, 50, meta_ids=[0, 1, 2])
+assert got["status"] == 0
+assert np.array_equal(got["final"][:, ids], orc["final"][:, ids])
+assert np.array_equal(got["counts"], orc["counts"])
+print("OK")
+""" % (ROOT, os.path.join(ROOT, "tests"))
+    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert p.returncode == 0 and "OK" in p.stdout, (p.stdout + p.stderr)[-3000:]

@@ -642,11 +642,13 @@ def test_group_order_alternates_words_and_sel_blocks_spread_banks(which):
         assert _rows_max_share(word) * 3 < _rows_max_share([word[g] for g in wb])
 
 
-def test_batch_lane_choice_on_the_host(L):
+@pytest.mark.parametrize("lane_groups", [True, False])
+def test_batch_lane_choice_on_the_host(L, lane_groups):
     """pbn_batch_create only describes the batch (device buffers are not touched until
-    a launch): a 62-word state whose specs leave room for 32 trajectory slots gets 16
-    lanes per trajectory (32 x 16 = the CTA's 512 threads); a narrow state keeps one
-    lane and many slots per work item."""
+    a launch).  With lane groups, a 62-word state whose specs leave room for 32
+    trajectory slots gets 16 lanes per trajectory (32 x 16 = the CTA's 512 threads);
+    by default it runs one team of the CTA's 16 warps on 32 trajectories.  A narrow
+    state keeps one lane and many slots per work item either way."""
     import ctypes
     nets = [(synth.scalefree2000(seed=3).to_text(), [0, 1, 2, 3], 8, 64),
             (synth.paper100(seed=2).to_text(), [0, 1, 2], 12, 5000)]
@@ -665,15 +667,19 @@ def test_batch_lane_choice_on_the_host(L):
         b.d_state, b.d_counts, b.d_pooled = fake, fake, fake
     assert plans[0].info.state_words == 31 and plans[0].info.tables_in_smem == 0
     h = ctypes.c_void_p()
-    assert L.pbn_batch_create(arr, len(nets), ctypes.byref(h)) == 0, L.pbn_last_error_detail()
+    flags = _lib.PBN_BATCH_LANE_GROUPS if lane_groups else 0
+    assert L.pbn_batch_create_ex(arr, len(nets), 512, flags, ctypes.byref(h)) == 0, L.pbn_last_error_detail()
     try:
         info = _lib.BatchInfo()
         assert L.pbn_batch_info_get(h, ctypes.byref(info)) == 0
-        assert info.n_nets == 2 and info.threads == 512 and info.max_lanes == 16
+        assert info.n_nets == 2 and info.threads == 512
+        assert (info.max_lanes, info.n_team) == ((16, 0) if lane_groups else (32, 1))
         # 64 trajectories in items of 32 slots, 5,000 in items of at most 512
         assert info.n_items == 2 + math.ceil(5000 / 512)
     finally:
         L.pbn_batch_free(h)
+    h = ctypes.c_void_p()
+    assert L.pbn_batch_create_ex(arr, len(nets), 512, 0x2, ctypes.byref(h)) != 0
 
     one = (_lib.BatchNet * 1)()
     one[0] = arr[1]
