@@ -289,18 +289,19 @@ typedef struct {
                                   trajs_per_block * lanes_per_traj <= 1024 */
     uint32_t kernel;           /* PBN_KERNEL_AUTO, PBN_KERNEL_INTERP, PBN_KERNEL_COMPILED or PBN_KERNEL_TEAM */
     uint32_t trace_stride;     /* steps between snapshots (0 or 1: every step) */
-    uint32_t team_warps;       /* PBN_KERNEL_TEAM: warps per team of 32 trajectories (0 = auto);
-                                  trajs_per_block is then 32 x the teams per CTA (0 = auto) */
-    uint32_t reserved;         /* 0 */
+    uint32_t team_warps;       /* PBN_KERNEL_TEAM: warps per team (0 = auto); trajs_per_block is
+                                  then the team's trajectories x the teams per CTA (0 = auto) */
+    uint32_t team_trajs_per_lane; /* PBN_KERNEL_TEAM: trajectories per lane, a team of 32 x this
+                                  many (0 = auto: 2 when such a team fits, else 1; or 1, 2) */
 } pbn_sim_args;
 
 #define PBN_KERNEL_AUTO 0u     /* the compiled plan kernel if pbn_plan_compile succeeded, else the interpreter */
 #define PBN_KERNEL_INTERP 1u   /* the generic kernel that reads the plan image */
 #define PBN_KERNEL_COMPILED 2u /* the plan's own kernel (compiled on first use) */
-/* the team interpreter for wide states: K warps share 32 trajectories (one per lane),
- * splitting each step's perturbation words, SEL blocks and groups, the states in
- * shared memory as [row][lane]; Eq. 1 semantics only (node-wise plans: PBN_EINVAL);
- * K x teams per CTA <= 32 */
+/* the team interpreter for wide states: K warps share 32 x TPL trajectories (TPL per
+ * lane), splitting each step's perturbation words, SEL blocks and groups, the states
+ * in shared memory as [row][trajectory]; Eq. 1 semantics only (node-wise plans:
+ * PBN_EINVAL); K x teams per CTA <= 32 */
 #define PBN_KERNEL_TEAM 3u
 
 /* Simulate trajectories traj_begin .. traj_begin + n_traj - 1 for steps

@@ -112,7 +112,7 @@ class SimArgs(ctypes.Structure):
                 ("meta_ids", vp), ("meta_vals", vp), ("d_state", vp), ("d_counts", vp),
                 ("d_pooled", vp), ("d_status", vp), ("d_trace", vp),
                 ("lanes_per_traj", u32), ("trajs_per_block", u32), ("kernel", u32), ("trace_stride", u32),
-                ("team_warps", u32), ("reserved", u32)]
+                ("team_warps", u32), ("team_trajs_per_lane", u32)]
 
 
 class EstimateOut(ctypes.Structure):

@@ -226,7 +226,7 @@ def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids,
              traj_begin: int = 0, step_begin: int = 0, count_from: int = 0, init: int | None = None,
              trace=None, lanes_per_traj: int = 0, trajs_per_block: int = 0, stream=None,
              d_image=None, n_traj: int | None = None, kernel: int = _lib.PBN_KERNEL_AUTO,
-             trace_stride: int = 1, team_warps: int = 0):
+             trace_stride: int = 1, team_warps: int = 0, team_trajs_per_lane: int = 0):
     """Enqueue pbn_simulate on `stream` (default: torch's current stream)."""
     import torch
     L = _lib.load()
@@ -251,6 +251,7 @@ def simulate(plan: Plan, bufs: SimBuffers, *, seed: int, n_steps: int, meta_ids,
     a.kernel = kernel
     a.trace_stride = trace_stride
     a.team_warps = team_warps
+    a.team_trajs_per_lane = team_trajs_per_lane
     img = plan.device_image(bufs.state.device) if d_image is None else d_image
     st = torch.cuda.current_stream(bufs.state.device) if stream is None else stream
     check(L.pbn_simulate(plan._h, ctypes.c_void_p(img.data_ptr()), ctypes.byref(a),

@@ -204,30 +204,32 @@ int interp_shape(const pbn_plan* plan, uint32_t T, bool teams_ok, NetDesc* D) {
     D->team = 0;
     D->smem_state_off = D->stage_bytes ? ((D->stage_bytes + 127u) & ~127u) : 0u;
     /* states of 8 rows or more (Eq. 1 semantics): the team interpreter, its records
-     * staged (tables too when at least as many teams fit), as many teams as the
+     * staged (tables too when at least as many teams fit), two trajectories per lane
+     * when such a team fits (one record decode serves both), as many teams as the
      * shared memory holds up to a power of two dividing the CTA's warps, and the
      * warps split evenly over them (on paper-scale networks of 300 to 3,000 nodes
      * and the 2,000-node scale-free one it ran 1.2-1.33x the lane groups) */
     if (teams_ok && H.W32 >= 8 && H.semantics != PBN_SEM_NODEWISE) {
-        const uint64_t tb = pbn_team_smem_bytes(H.W32, H.n_sel);
         const uint32_t warps = T / 32u;
-        auto teams = [&](uint64_t staged) -> uint32_t {
+        auto teams = [&](uint64_t staged, uint32_t tpl) -> uint32_t {
+            const uint64_t tb = pbn_team_smem_bytes(H.W32, H.n_sel, tpl);
             const uint64_t off = (staged + 127u) & ~(uint64_t)127u;
             if (off + tb > kSmemCap) return 0u;
             uint32_t t = 1;
             while (2 * t <= warps && off + 2 * t * tb <= kSmemCap) t *= 2;
             return t;
         };
-        const uint32_t t_all = H.tables_in_smem ? teams(H.off_ret) : 0u;
-        const uint32_t t_specs = teams(H.off_tables);
-        if (t_all && t_all >= t_specs) {
-            D->specs_in_smem = 1; D->tables_in_smem = 1; D->stage_bytes = H.off_ret; D->nt = 32u * t_all;
-        } else if (t_specs) {
-            D->specs_in_smem = 1; D->tables_in_smem = 0; D->stage_bytes = H.off_tables; D->nt = 32u * t_specs;
-        }
-        if (t_all || t_specs) {
-            D->team = warps / (D->nt / 32u);
-            D->lg = 1;
+        for (uint32_t tpl = 2; tpl >= 1; --tpl) {
+            const uint32_t t_all = H.tables_in_smem ? teams(H.off_ret, tpl) : 0u;
+            const uint32_t t_specs = teams(H.off_tables, tpl);
+            if (!t_all && !t_specs) continue;
+            if (t_all && t_all >= t_specs) {
+                D->specs_in_smem = 1; D->tables_in_smem = 1; D->stage_bytes = H.off_ret; D->nt = 32u * tpl * t_all;
+            } else {
+                D->specs_in_smem = 1; D->tables_in_smem = 0; D->stage_bytes = H.off_tables; D->nt = 32u * tpl * t_specs;
+            }
+            D->team = warps / (D->nt / (32u * tpl));
+            D->lg = tpl;
             D->smem_state_off = (D->stage_bytes + 127u) & ~127u;
             return PBN_OK;
         }
@@ -261,7 +263,7 @@ constexpr size_t kMaxCompiledNets = 96;
 /* Shared memory of an interpreted network's work item: its staged bytes and the
  * trajectories' rows (lane groups) or the teams' states (team interpreter). */
 uint64_t interp_smem(const NetDesc& D, const pbn_plan* plan) {
-    if (D.team) return D.smem_state_off + (uint64_t)(D.nt / 32u) * pbn_team_smem_bytes(D.W32, D.n_sel);
+    if (D.team) return D.smem_state_off + (uint64_t)(D.nt / (32u * D.lg)) * pbn_team_smem_bytes(D.W32, D.n_sel, D.lg);
     return D.smem_state_off + (uint64_t)plan->per_traj_smem * D.nt;
 }
 

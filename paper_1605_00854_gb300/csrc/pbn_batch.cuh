@@ -47,8 +47,9 @@ struct alignas(16) pbn_netdesc {
     uint32_t off_wgroups;
     uint32_t stage_off;  /* byte offset in the image of the staged bytes */
     uint32_t compiled;   /* 1: the batch module holds this network's code */
-    uint32_t team;       /* > 0: the team interpreter with this many warps per team of 32
-                            trajectories (nt / 32 teams per item); 0: lane groups of lg */
+    uint32_t team;       /* > 0: the team interpreter with this many warps per team of 32 lg
+                            trajectories (lg per lane; nt / (32 lg) teams per item); 0: lane
+                            groups of lg lanes per trajectory */
     uint32_t meta_row[PBN_BATCH_META_ROWS];
     uint32_t meta_mask[PBN_BATCH_META_ROWS];
     uint32_t meta_val[PBN_BATCH_META_ROWS];

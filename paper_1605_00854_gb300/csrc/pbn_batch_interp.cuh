@@ -92,17 +92,28 @@ __device__ __forceinline__ bool pbn_batch_interp_run(uint64_t step_offset, uint3
     V.meta_mask = meta_sh + PBN_BATCH_META_ROWS;
     V.meta_val = meta_sh + 2 * PBN_BATCH_META_ROWS;
     if (D.team) {
-        /* teams of D.team warps on 32 trajectories each; every warp of the CTA is in
-         * one (the team count divides the CTA's warps) */
-        const uint32_t K = D.team, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+        /* teams of D.team warps on 32 x D.lg trajectories each (D.lg per lane); every
+         * warp of the CTA is in one (the team count divides the CTA's warps) */
+        const uint32_t K = D.team, tpl = D.lg, warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
         const uint32_t team = warp / K, wt = warp - team * K;
-        const uint32_t slot = team * 32u + lane;
-        const bool active = slot < W.n;
-        const uint64_t lt = (uint64_t)W.t0 + slot;
-        uint8_t* const tsm = smem + D.smem_state_off + team * pbn_team_smem_bytes(D.W32, D.n_sel);
-        if (D.tables_in_smem) pbn_team_run<false, true>(V, smem, tsm, K, wt, lane, lt, active, c);
-        else pbn_team_run<false, false>(V, smem, tsm, K, wt, lane, lt, active, c);
-        return active && wt == 0;
+        const uint32_t slot0 = team * 32u * tpl + lane;
+        const uint64_t lt0 = (uint64_t)W.t0 + slot0;
+        uint32_t act = 0;
+        for (uint32_t j = 0; j < tpl; ++j) act |= (slot0 + 32u * j < W.n ? 1u : 0u) << j;
+        uint8_t* const tsm = smem + D.smem_state_off + team * pbn_team_smem_bytes(D.W32, D.n_sel, tpl);
+        if (tpl == 2) {
+            uint32_t c2[8];
+            if (D.tables_in_smem) pbn_team_run<2, false, true>(V, smem, tsm, K, wt, lane, lt0, act, c2);
+            else pbn_team_run<2, false, false>(V, smem, tsm, K, wt, lane, lt0, act, c2);
+            /* the second trajectory's counts pooled here, the first one's by the caller */
+            pbn_warp_pool(D.pooled, wt == 0 && ((act >> 1) & 1u), c2 + 4, V.pairs);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) c[i] = c2[i];
+        } else {
+            if (D.tables_in_smem) pbn_team_run<1, false, true>(V, smem, tsm, K, wt, lane, lt0, act, c);
+            else pbn_team_run<1, false, false>(V, smem, tsm, K, wt, lane, lt0, act, c);
+        }
+        return wt == 0 && (act & 1u);
     }
     /* D.lg lanes per trajectory, D.nt trajectory slots per item */
     const uint32_t lg = D.lg;

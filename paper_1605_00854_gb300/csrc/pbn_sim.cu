@@ -75,7 +75,8 @@ struct SimParams {
     uint64_t geo_full, geo_last;  /* geometric sampler: thresholds of a full and the last word */
     uint32_t n_meta_rows;
     uint32_t trace_stride;     /* steps between trace snapshots (>= 1) */
-    uint32_t team_warps;       /* team kernel: warps per team of 32 trajectories */
+    uint32_t team_warps;       /* team kernel: warps per team */
+    uint32_t team_tpl;         /* team kernel: trajectories per lane (a team of 32 x this many) */
     uint32_t meta_row[kMaxMetaRows];
     uint32_t meta_mask[kMaxMetaRows];
     uint32_t meta_val[kMaxMetaRows];
@@ -134,10 +135,10 @@ cudaError_t launch_t(const SimParams& P, uint32_t grid, uint32_t tpb, size_t sme
     return cudaGetLastError();
 }
 
-/* The team interpreter (pbn_team.cuh): a CTA of P.nt / 32 teams of P.team_warps
- * warps, 32 trajectories a team, the staged records at the start of shared memory
- * and the teams' states after them. */
-template <bool TRACE, bool TAB_SMEM>
+/* The team interpreter (pbn_team.cuh): a CTA of P.nt / (32 TPL) teams of
+ * P.team_warps warps, 32 TPL trajectories a team, the staged records at the start of
+ * shared memory and the teams' states after them. */
+template <int TPL, bool TRACE, bool TAB_SMEM>
 __global__ void __launch_bounds__(kMaxCtaThreads) pbn_team_kernel(const SimParams P) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t stage_bar;
@@ -154,15 +155,26 @@ __global__ void __launch_bounds__(kMaxCtaThreads) pbn_team_kernel(const SimParam
     const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t K = P.team_warps;
     const uint32_t team = warp / K, wt = warp - team * K;
-    const uint64_t lt = (uint64_t)blockIdx.x * P.nt + team * 32u + lane;
-    const bool active = lt < P.n_traj;
-    uint8_t* const tsm = smem + P.smem_state_off + team * pbn_team_smem_bytes(P.W32, P.n_sel);
-    uint32_t c[4];
-    pbn_team_run<TRACE, TAB_SMEM>(P, smem, tsm, K, wt, lane, lt, active, c);
+    const uint64_t lt0 = (uint64_t)blockIdx.x * P.nt + team * 32u * TPL + lane;
+    uint32_t act = 0;
+#pragma unroll
+    for (int j = 0; j < TPL; ++j) act |= (lt0 + 32u * j < P.n_traj ? 1u : 0u) << j;
+    uint8_t* const tsm = smem + P.smem_state_off + team * pbn_team_smem_bytes(P.W32, P.n_sel, TPL);
+    uint32_t c[4 * TPL];
+    pbn_team_run<TPL, TRACE, TAB_SMEM>(P, smem, tsm, K, wt, lane, lt0, act, c);
     if (P.pooled) {
-        const bool lead = active && wt == 0;
-        uint64_t v[5] = {lead ? c[0] : 0u, lead ? (uint64_t)(P.pairs - c[1] - c[2] - c[3]) : 0u,
-                         lead ? c[1] : 0u, lead ? c[2] : 0u, lead ? c[3] : 0u};
+        uint64_t v[5] = {0, 0, 0, 0, 0};
+        if (wt == 0) {
+#pragma unroll
+            for (int j = 0; j < TPL; ++j) {
+                if (!((act >> j) & 1u)) continue;
+                v[0] += c[4 * j];
+                v[1] += P.pairs - c[4 * j + 1] - c[4 * j + 2] - c[4 * j + 3];
+                v[2] += c[4 * j + 1];
+                v[3] += c[4 * j + 2];
+                v[4] += c[4 * j + 3];
+            }
+        }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
 #pragma unroll
@@ -176,21 +188,22 @@ __global__ void __launch_bounds__(kMaxCtaThreads) pbn_team_kernel(const SimParam
     }
 }
 
-template <bool TRACE, bool TAB_SMEM>
+template <int TPL, bool TRACE, bool TAB_SMEM>
 cudaError_t launch_team_t(const SimParams& P, uint32_t grid, uint32_t tpb, size_t smem, cudaStream_t st) {
-    auto kern = pbn_team_kernel<TRACE, TAB_SMEM>;
+    auto kern = pbn_team_kernel<TPL, TRACE, TAB_SMEM>;
     const int e = pbn::ensure_dyn_smem(reinterpret_cast<const void*>(kern), smem);
     if (e != 0) return static_cast<cudaError_t>(e);
     kern<<<grid, tpb, smem, st>>>(P);
     return cudaGetLastError();
 }
 
-cudaError_t launch_team(const SimParams& P, bool trace, bool tab_smem, uint32_t grid, uint32_t tpb, size_t smem,
-                        cudaStream_t st) {
-    if (trace) return tab_smem ? launch_team_t<true, true>(P, grid, tpb, smem, st)
-                               : launch_team_t<true, false>(P, grid, tpb, smem, st);
-    return tab_smem ? launch_team_t<false, true>(P, grid, tpb, smem, st)
-                    : launch_team_t<false, false>(P, grid, tpb, smem, st);
+template <int TPL>
+cudaError_t launch_team_tpl(const SimParams& P, bool trace, bool tab_smem, uint32_t grid, uint32_t tpb, size_t smem,
+                            cudaStream_t st) {
+    if (trace) return tab_smem ? launch_team_t<TPL, true, true>(P, grid, tpb, smem, st)
+                               : launch_team_t<TPL, true, false>(P, grid, tpb, smem, st);
+    return tab_smem ? launch_team_t<TPL, false, true>(P, grid, tpb, smem, st)
+                    : launch_team_t<TPL, false, false>(P, grid, tpb, smem, st);
 }
 
 template <int LG>
@@ -405,30 +418,38 @@ extern "C" int pbn_simulate(const pbn_plan* plan, const void* d_image, const pbn
      * kernels' static shared memory (a stage barrier and a few words) */
     const size_t smem_lim = (size_t)device_smem_limit() - kStaticSmemReserve;
     if (a->kernel == PBN_KERNEL_TEAM) {
-        /* teams of K warps on 32 trajectories: T teams per CTA (T x K <= 32 warps), by
-         * default as many as the shared memory holds up to one wave of CTAs over the
-         * SMs, and K = 32 / T */
+        /* teams of K warps on 32 TPL trajectories (TPL per lane: 2 when such a team
+         * fits, so that each record decode serves two trajectories): T teams per CTA
+         * (T x K <= 32 warps), by default as many as the shared memory holds up to one
+         * wave of CTAs over the SMs, and K = 32 / T */
         if (P.per_node) return fail(PBN_EINVAL, "pbn_simulate: the team kernel runs Eq. 1 semantics only");
-        if (a->trajs_per_block % 32u || a->trajs_per_block > 1024u || a->team_warps > 32u)
-            return fail(PBN_EINVAL, "pbn_simulate: team kernel needs trajs_per_block a multiple of 32 (<= 1024) and <= 32 warps");
-        const size_t tb = pbn_team_smem_bytes(H.W32, H.n_sel);
+        if (a->team_warps > 32u || a->team_trajs_per_lane > 2u)
+            return fail(PBN_EINVAL, "pbn_simulate: team kernel needs <= 32 warps and 1 or 2 trajectories per lane");
         const size_t fixed = P.smem_state_off;
+        uint32_t tpl = a->team_trajs_per_lane;
+        if (tpl == 0) tpl = fixed + pbn_team_smem_bytes(H.W32, H.n_sel, 2) <= smem_lim ? 2u : 1u;
+        const uint32_t per_team = 32u * tpl;
+        if (a->trajs_per_block % per_team || a->trajs_per_block > 32u * per_team)
+            return fail(PBN_EINVAL, "pbn_simulate: team kernel needs trajs_per_block a multiple of %u", per_team);
+        const size_t tb = pbn_team_smem_bytes(H.W32, H.n_sel, tpl);
         if (fixed + tb > smem_lim)
             return fail(PBN_ETOOBIG, "pbn_simulate: a team needs %zu bytes of shared memory", fixed + tb);
         const uint32_t tmax = (uint32_t)std::min<size_t>(32, (smem_lim - fixed) / tb);
-        const uint64_t n_teams = (a->n_traj + 31) / 32;
-        uint32_t T = a->trajs_per_block / 32u;
+        const uint64_t n_teams = (a->n_traj + per_team - 1) / per_team;
+        uint32_t T = a->trajs_per_block / per_team;
         if (T == 0)
             T = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(tmax, (n_teams + sms - 1) / (uint64_t)sms));
         uint32_t K = a->team_warps ? a->team_warps : std::max(1u, 32u / T);
         if (T > tmax) return fail(PBN_ETOOBIG, "pbn_simulate: %u teams exceed the shared memory of a CTA", T);
         if (T * K > 32u) return fail(PBN_EINVAL, "pbn_simulate: %u teams of %u warps exceed 1,024 threads", T, K);
         P.team_warps = K;
-        P.nt = 32u * T;
+        P.team_tpl = tpl;
+        P.nt = per_team * T;
         const uint64_t grid = (a->n_traj + P.nt - 1) / P.nt;
         const size_t smem = fixed + (size_t)T * tb;
-        const cudaError_t e =
-            launch_team(P, a->d_trace != nullptr, H.tables_in_smem != 0, (uint32_t)grid, 32u * K * T, smem, st);
+        const bool tr = a->d_trace != nullptr, ts = H.tables_in_smem != 0;
+        const cudaError_t e = tpl == 2 ? launch_team_tpl<2>(P, tr, ts, (uint32_t)grid, 32u * K * T, smem, st)
+                                       : launch_team_tpl<1>(P, tr, ts, (uint32_t)grid, 32u * K * T, smem, st);
         if (e != cudaSuccess) return fail(PBN_ECUDA, "pbn_simulate: %s", cudaGetErrorString(e));
         return PBN_OK;
     }

@@ -14,7 +14,8 @@ def plan_for(text, interest=(0, 1, 2), mode=0, reduce=True, **kw):
 
 
 def run(plan, *, seed, n_traj, n_steps, meta, meta_vals=None, traj_begin=0, step_begin=0,
-        count_from=0, init_bits=None, trace=False, lanes=0, tpb=0, chunks=None, kernel=0, team_warps=0):
+        count_from=0, init_bits=None, trace=False, lanes=0, tpb=0, chunks=None, kernel=0, team_warps=0,
+        team_tpl=0):
     """Run pbn_simulate; returns dict(final bits [T, n], counts [T, 5] uint64,
     pooled [5], status, trace bits [T, S, n] or None).  `chunks` splits the steps into
     consecutive launches resumed from the device state."""
@@ -35,7 +36,7 @@ def run(plan, *, seed, n_traj, n_steps, meta, meta_vals=None, traj_begin=0, step
         api.simulate(plan, bufs, seed=seed, n_steps=c, meta_ids=meta, meta_vals=meta_vals,
                      traj_begin=traj_begin, step_begin=sb, count_from=count_from,
                      init=(init if i == 0 else 1), lanes_per_traj=lanes, trajs_per_block=tpb,
-                     kernel=kernel, team_warps=team_warps,
+                     kernel=kernel, team_warps=team_warps, team_trajs_per_lane=team_tpl,
                      trace=None if tr is None else tr[sb - step_begin: sb - step_begin + c])
         sb += c
     torch.cuda.synchronize()
