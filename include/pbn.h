@@ -411,7 +411,8 @@ typedef struct {
     uint32_t n_nets;
     uint32_t n_items;          /* work items: trajectory ranges of one network, each as
                                   many trajectory slots as fit in shared memory, at
-                                  most `threads` / (the network's lanes per trajectory) */
+                                  most `threads` / (the network's lanes per trajectory),
+                                  or 2 x `threads` for teams of two trajectories per lane */
     uint32_t threads;          /* threads per CTA */
     uint32_t max_lanes;        /* the most lanes per trajectory any network of the batch uses */
     uint64_t desc_bytes;       /* bytes of pbn_batch_image */
