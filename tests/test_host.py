@@ -979,3 +979,89 @@ def test_bench_finds_captured_instructions_by_kernel_source():
     for h, w, t in recs:
         assert bench.captured_instructions(h) == (float(w), float(t))
     assert bench.captured_instructions("0" * 64) is None
+
+
+def _batch_net_desc_type():
+    """The per-network batch descriptor (pbn_netdesc in csrc/pbn_batch.cuh) as laid
+    out in the device table pbn_batch_image writes."""
+    import ctypes as c
+    u32, u64, p = c.c_uint32, c.c_uint64, c.c_void_p
+    mid = ("n_traj", "init", "stage_bytes", "image_bytes", "smem_state_off", "hmax", "tables_in_smem", "n_meta_rows",
+           "n", "W", "W32", "n_sel", "P", "off_words", "off_groups", "off_multi", "off_selslot", "off_thr",
+           "off_inputs", "off_selblk", "off_ret", "off_pos", "off_tables", "specs_in_smem", "nt", "off_gorder",
+           "n_groups", "lg", "off_subs", "per_node", "sampler", "off_geo")
+    fields = ([("image", p), ("state", p), ("counts", p), ("pooled", p), ("traj_begin", u64), ("step_begin", u64),
+               ("count_from", u64), ("seed", u64)] + [(f, u32) for f in mid]
+              + [("geo_full", u64), ("geo_last", u64)]
+              + [(f, u32) for f in ("off_wgroups", "stage_off", "compiled", "team")]
+              + [("meta_row", u32 * 16), ("meta_mask", u32 * 16), ("meta_val", u32 * 16)])
+    return type("BatchNetDesc", (c.Structure,), {"_fields_": fields})
+
+
+@pytest.mark.parametrize("threads", [512, 1024])
+def test_batch_team_shapes_on_the_host(L, threads):
+    """The batch's choice of interpreter per network, read back from its device table:
+    a state of 8 rows or more runs the team interpreter with the records staged, two
+    trajectories per lane when such a team fits beside them, the largest power-of-two
+    number of teams (at most the CTA's warps) that fits the per-CTA shared memory,
+    and the CTA's warps split evenly over the teams; a narrower state keeps lane
+    groups, and PBN_BATCH_LANE_GROUPS keeps lane groups everywhere."""
+    import ctypes
+    cap = 224 * 1024
+    nets = [(synth.scalefree2000(seed=3).to_text(), [0, 1, 2, 3], 8, 64),
+            (synth.paper100(seed=3, n=300, p=1e-3).to_text(), [0, 1, 2], 8, 5000),
+            (synth.paper100(seed=5, n=1000, p=1e-3).to_text(), [0, 1, 2], 8, 3000),
+            (synth.paper100(seed=2).to_text(), [0, 1, 2], 12, 700)]
+    plans, keep = [], []
+    arr = (_lib.BatchNet * len(nets))()
+    fake = 1 << 20  # 16-byte aligned stand-ins for device buffers (never dereferenced here)
+    for i, (text, meta, mi, T) in enumerate(nets):
+        red, _ = api.Net.load(text).reduce(meta)
+        plan = api.Plan(red, max_inputs=mi)
+        plans.append(plan)
+        ids = np.ascontiguousarray(meta, dtype=np.uint32)
+        keep.append(ids)
+        b = arr[i]
+        b.plan, b.d_image, b.seed, b.n_traj = plan._h, fake, 1, T
+        b.n_meta, b.meta_ids = len(meta), ids.ctypes.data
+        b.d_state, b.d_counts, b.d_pooled = fake, fake, fake
+    _BatchNetDesc = _batch_net_desc_type()
+    assert ctypes.sizeof(_BatchNetDesc) == 416
+    for flags in (0, _lib.PBN_BATCH_LANE_GROUPS):
+        h = ctypes.c_void_p()
+        assert L.pbn_batch_create_ex(arr, len(nets), threads, flags, ctypes.byref(h)) == 0, L.pbn_last_error_detail()
+        try:
+            info = _lib.BatchInfo()
+            assert L.pbn_batch_info_get(h, ctypes.byref(info)) == 0
+            img = np.zeros(info.desc_bytes, dtype=np.uint8)
+            assert L.pbn_batch_image(h, img.ctypes.data, img.size) == 0
+            descs = [_BatchNetDesc.from_buffer_copy(img[416 * i: 416 * (i + 1)].tobytes()) for i in range(len(nets))]
+            items = img[416 * len(nets):].view(np.uint32).reshape(-1, 4)
+            assert len(items) == info.n_items
+            for i, (D, plan, (_, _, _, T)) in enumerate(zip(descs, plans, nets)):
+                assert D.n_traj == T and D.W32 == 2 * plan.info.state_words
+                # the items of network i cover its trajectories in ranges of at most nt
+                mine = items[items[:, 0] == i]
+                assert mine[:, 2].sum() == T and mine[:, 2].max() <= D.nt
+                assert len(mine) == math.ceil(T / D.nt)
+                if flags or D.W32 < 8:
+                    assert D.team == 0
+                    continue
+                tpl, teams = D.lg, D.nt // (32 * D.lg)
+                assert tpl in (1, 2) and D.specs_in_smem == 1 and D.team * teams == threads // 32
+                assert teams & (teams - 1) == 0
+
+                def team_bytes(t):
+                    return 128 * t * (2 * (D.W32 + 1) + D.n_sel + 1)
+                assert D.smem_state_off == (D.stage_bytes + 127) // 128 * 128
+                assert D.smem_state_off + teams * team_bytes(tpl) <= cap
+                assert teams == threads // 32 or D.smem_state_off + 2 * teams * team_bytes(tpl) > cap
+                if tpl == 1:  # two trajectories per lane would not fit, with or without tables
+                    assert (plan.info.stage_bytes + 127) // 128 * 128 + team_bytes(2) > cap
+            n_team = sum(1 for D in descs if D.team)
+            assert info.n_team == n_team == (0 if flags else 3)
+            if not flags:
+                assert descs[0].team and descs[0].lg == 1     # scale-free: 62 rows, one trajectory per lane
+                assert descs[1].lg == 2 and descs[2].lg == 2  # 300 and 1,000 nodes: two per lane
+        finally:
+            L.pbn_batch_free(h)
