@@ -414,7 +414,8 @@ typedef struct {
                                   most `threads` / (the network's lanes per trajectory),
                                   or 2 x `threads` for teams of two trajectories per lane */
     uint32_t threads;          /* threads per CTA */
-    uint32_t max_lanes;        /* the most lanes per trajectory any network of the batch uses */
+    uint32_t max_lanes;        /* the most lanes per trajectory any network of the batch uses
+                                  (32 for a team: every lane of its warps works on it) */
     uint64_t desc_bytes;       /* bytes of pbn_batch_image */
     uint64_t smem_bytes;       /* dynamic shared memory per CTA */
     double est_ops_per_step;   /* sum over networks of n_traj x ops_per_step */
@@ -426,9 +427,10 @@ typedef struct {
 
 /* Describe a batch of networks for the persistent work-queue kernel: each network
  * gets its staging mode (specs and tables, specs only, or none in shared memory), its
- * trajectory slots per work item and its lanes per trajectory (1-32), is cut into
- * work items of that many trajectories, and the items are ordered by descending
- * estimated work.  The networks' plans and device buffers must stay
+ * trajectory slots per work item and its interpreter (teams of warps on 32 or 64
+ * trajectories for states of 8 rows or more, else 1-32 lanes per trajectory; see
+ * pbn_batch_create_ex), is cut into work items of that many trajectories, and the
+ * items are ordered by descending estimated work.  The networks' plans and device buffers must stay
  * valid while the batch is used.  On success *out owns the batch (pbn_batch_free).
  * Errors: PBN_EINVAL (missing or misaligned buffer, range, meta node), PBN_ETOOBIG
  * (a network's specs and trajectory rows exceed the per-CTA shared memory),
